@@ -1,0 +1,570 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics:
+closed forms, invariants, special cases, brute force and finite differences.
+None of these tests retypes an oracle formula; each one checks the oracle
+against an independent route to the same number."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from synth import scenes as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def one_gaussian(x, y, z, log_scale, ologit, rgb, quat=(1.0, 0.0, 0.0, 0.0)):
+    ls = np.broadcast_to(np.asarray(log_scale, dtype=np.float64), (3,))
+    return {
+        "means": np.array([[x, y, z]]),
+        "log_scales": ls.reshape(1, 3).copy(),
+        "quats": np.array([quat], dtype=np.float64),
+        "opacity_logit": np.array([ologit]),
+        "rgb": np.array([rgb], dtype=np.float64),
+    }
+
+
+def concat(*gs):
+    return {k: np.concatenate([g[k] for g in gs]) for k in gs[0]}
+
+
+# ---------------------------------------------------------------------------
+# Closed form: one isotropic Gaussian on the optical axis (Eq. 2, Eq. 3)
+# ---------------------------------------------------------------------------
+
+def closed_form_single(W, H, f, z, s, o, c):
+    """Image of one isotropic Gaussian at camera (0,0,z): the EWA covariance is
+    (f s / z)^2 I + 0.3 I, the radius ceil(3 sqrt(sigma^2 + sqrt(0.1))), and
+    each pixel inside the radius box gets alpha = o exp(-d^2 / 2 sigma^2)."""
+    sig2 = (f * s / z) ** 2 + 0.3
+    r = math.ceil(3 * math.sqrt(sig2 + math.sqrt(0.1)))
+    img = np.zeros((3, H, W))
+    dep = np.zeros((H, W))
+    T = np.ones((H, W))
+    cx, cy = W / 2, H / 2
+    for py in range(H):
+        for px in range(W):
+            if abs(px - math.floor(cx)) > r or abs(py - math.floor(cy)) > r:
+                continue
+            d2 = (px + 0.5 - cx) ** 2 + (py + 0.5 - cy) ** 2
+            a = min(0.99, o * math.exp(-d2 / (2 * sig2)))
+            if a < 1 / 255:
+                continue
+            img[:, py, px] = a * np.asarray(c)
+            dep[py, px] = a * z
+            T[py, px] = 1 - a
+    return img, dep, T, r, sig2
+
+
+@pytest.mark.parametrize("W,H,f,z,s,ol", [(64, 48, 80.0, 3.0, 0.08, 0.3), (32, 32, 50.0, 2.0, 0.2, 1.5)])
+def test_single_isotropic_closed_form(oracle_lib, W, H, f, z, s, ol):
+    O = oracle_lib
+    c = (0.2, 0.5, 0.9)
+    g = one_gaussian(0.0, 0.0, z, math.log(s), ol, c)
+    cam = S.camera(W, H, f)
+    pr, img = O.forward(g, cam)
+    o = 1 / (1 + math.exp(-ol))
+    ref, dref, Tref, r, sig2 = closed_form_single(W, H, f, z, s, o, c)
+    assert pr["radius"][0] == r
+    np.testing.assert_allclose(pr["conic"][0], [1 / sig2, 0, 1 / sig2], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(img["rgb"], ref, atol=1e-12)
+    np.testing.assert_allclose(img["depth"], dref, atol=1e-12)
+    np.testing.assert_allclose(img["T"], Tref, atol=1e-12)
+    # even W, H: the image is symmetric under both flips
+    np.testing.assert_allclose(img["rgb"], img["rgb"][:, ::-1, :], atol=1e-13)
+    np.testing.assert_allclose(img["rgb"], img["rgb"][:, :, ::-1], atol=1e-13)
+    # brute force agrees
+    _, imgb = O.forward(g, cam, tiled=False)
+    np.testing.assert_array_equal(img["rgb"], imgb["rgb"])
+
+
+def test_single_isotropic_gradients_closed_form(oracle_lib):
+    """For L = sum_P w_P C_P (one channel weight per pixel, symmetric weights)
+    the derivatives follow from alpha = o exp(-(dx^2/sx2 + dy^2/sy2)/2) with
+    sx2 = (f/z)^2 exp(2 ls_x) + 0.3: dL/dc, dL/dlogit, dL/dz, dL/dls_x and
+    dL/dls_y in closed form; dL/dx = dL/dy = 0 and dL/dls_z = 0 exactly by
+    symmetry and because J has no z column on the axis."""
+    O = oracle_lib
+    W, H, f, z, s, ol = 40, 40, 60.0, 2.5, 0.1, -0.5
+    c = np.array([0.3, 0.6, 0.9])
+    g = one_gaussian(0.0, 0.0, z, math.log(s), ol, c)
+    cam = S.camera(W, H, f)
+    w = np.ones((3, H, W))
+    wd = np.full((H, W), 0.7)
+    pr, g2, gb = O.forward_backward(g, cam, w, wd)
+    o = 1 / (1 + math.exp(-ol))
+    sig2 = (f * s / z) ** 2 + 0.3
+    r = pr["radius"][0]
+    dc = 0.0
+    dlogit = 0.0
+    dz = 0.0
+    dlsx = 0.0
+    for py in range(H):
+        for px in range(W):
+            if abs(px - W // 2) > r or abs(py - H // 2) > r:
+                continue
+            dx2 = (px + 0.5 - W / 2) ** 2
+            dy2 = (py + 0.5 - H / 2) ** 2
+            a = o * math.exp(-(dx2 + dy2) / (2 * sig2))
+            if a < 1 / 255:
+                continue
+            dc += a
+            # C = a c, D = a z, weights: 1 per colour channel, 0.7 for depth
+            dLda = c.sum() + 0.7 * z
+            dlogit += dLda * a * (1 - o)
+            dsig2_dz = -2 * (f * s) ** 2 / z ** 3
+            da_dz = a * (dx2 + dy2) / (2 * sig2 ** 2) * dsig2_dz
+            dz += dLda * da_dz + 0.7 * a
+            dsx2 = 2 * (f / z) ** 2 * s * s
+            dlsx += dLda * a * dx2 / (2 * sig2 ** 2) * dsx2
+    np.testing.assert_allclose(gb["rgb"][0], [dc, dc, dc], rtol=1e-10)
+    np.testing.assert_allclose(gb["opacity_logit"][0], dlogit, rtol=1e-10)
+    np.testing.assert_allclose(gb["means"][0, 2], dz, rtol=1e-9)
+    np.testing.assert_allclose(gb["log_scales"][0, 0], dlsx, rtol=1e-9)
+    np.testing.assert_allclose(gb["log_scales"][0, 1], dlsx, rtol=1e-9)
+    assert abs(gb["means"][0, 0]) < 1e-12 and abs(gb["means"][0, 1]) < 1e-12
+    assert abs(gb["log_scales"][0, 2]) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Occlusion and early termination (Eq. 3 note)
+# ---------------------------------------------------------------------------
+
+def test_opaque_front_scales_behind_by_one_hundredth(oracle_lib):
+    """A huge front Gaussian with logit 20 has alpha clamped at 0.99 over the
+    whole image, so whatever lies behind is weighted by exactly T = 0.01."""
+    O = oracle_lib
+    W, H, f = 32, 32, 40.0
+    front = one_gaussian(0.0, 0.0, 2.0, math.log(50.0), 20.0, (1.0, 0.0, 0.0))
+    behind = one_gaussian(0.0, 0.0, 4.0, math.log(0.1), 0.0, (0.0, 1.0, 0.0))
+    cam = S.camera(W, H, f)
+    _, both = O.forward(concat(front, behind), cam)
+    _, only_b = O.forward(behind, cam)
+    np.testing.assert_allclose(both["rgb"][0], 0.99, atol=1e-12)
+    np.testing.assert_allclose(both["rgb"][1], 0.01 * only_b["rgb"][1], atol=1e-14)
+
+
+def test_three_opaque_fronts_terminate_before_behind(oracle_lib):
+    """After opaque fronts drive T to ~1e-4 the ray stops: the Gaussian behind
+    gets exactly zero contribution and exactly zero gradient."""
+    O = oracle_lib
+    W, H, f = 32, 32, 40.0
+    fronts = [one_gaussian(0.0, 0.0, 2.0 + 0.01 * i, math.log(50.0), 20.0, (1.0, 0.0, 0.0))
+              for i in range(3)]
+    behind = one_gaussian(0.0, 0.0, 4.0, math.log(0.1), 3.0, (0.0, 1.0, 0.0))
+    g = concat(*fronts, behind)
+    cam = S.camera(W, H, f)
+    _, img = O.forward(g, cam)
+    assert np.all(img["rgb"][1] == 0.0)
+    w = np.ones((3, H, W))
+    _, g2, gb = O.forward_backward(g, cam, w, np.ones((H, W)))
+    assert np.all(g2[3] == 0.0)
+    for k in ("means", "log_scales", "quats", "rgb"):
+        assert np.all(gb[k][3] == 0.0)
+    # clamped fronts: no gradient through alpha to opacity or shape
+    assert np.all(gb["opacity_logit"][:3] == 0.0)
+    assert np.all(g2[:3, 0:6] == 0.0)
+
+
+def test_termination_tests_the_transmittance_after_the_fragment(oracle_lib):
+    """The ray stops before fragment k when T (1 - a_k) < t_eps (Eq. 3 note).
+    Fronts with a = 0.99 then a ~ 0.5 leave T = 0.005 > t_eps; a third opaque
+    layer would bring it to 5e-5 < t_eps, so it is not blended at all, and
+    T_final stays 0.005 although T itself never fell below t_eps."""
+    O = oracle_lib
+    W, H, f = 16, 16, 20.0
+    g = concat(one_gaussian(0, 0, 2.0, math.log(80.0), 20.0, (1.0, 0.0, 0.0)),
+               one_gaussian(0, 0, 2.5, math.log(80.0), 0.0, (0.0, 1.0, 0.0)),
+               one_gaussian(0, 0, 3.0, math.log(80.0), 20.0, (0.0, 0.0, 1.0)))
+    _, img = O.forward(g, S.camera(W, H, f))
+    assert np.all(img["rgb"][2] == 0.0)
+    assert np.all(img["nfrag"] == 2)
+    a2 = img["rgb"][1] / 0.01
+    np.testing.assert_allclose(a2, 0.5, atol=1e-3)
+    np.testing.assert_allclose(img["T"], 0.01 * (1 - a2), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Compositing invariants
+# ---------------------------------------------------------------------------
+
+def test_transmittance_partition_of_unity(oracle_lib):
+    """With every colour 1 and black background, C = sum_k T_k a_k, so
+    C + T_final = 1 per pixel; with every depth z0, D = z0 (1 - T_final)."""
+    O = oracle_lib
+    g = S.tiny_scene(seed=7, n=600)
+    cam = S.tiny_camera()
+    pr = O.project(g, cam)
+    pr["rgb"] = np.ones_like(pr["rgb"])
+    pr["depth"] = np.full_like(pr["depth"], 3.25)
+    img = O.render_fwd(pr, cam)
+    for ch in range(3):
+        np.testing.assert_allclose(img["rgb"][ch] + img["T"], 1.0, atol=1e-12)
+    np.testing.assert_allclose(img["depth"], 3.25 * (1 - img["T"]), atol=1e-12)
+    assert img["nfrag"].max() > 5
+
+
+def test_tiled_equals_brute_force(oracle_lib):
+    O = oracle_lib
+    g = S.tiny_scene(seed=1000)
+    cam = S.tiny_camera()
+    pr = O.project(g, cam)
+    a = O.render_fwd(pr, cam, tiled=True)
+    b = O.render_fwd(pr, cam, tiled=False)
+    for k in ("rgb", "depth", "T", "nfrag"):
+        np.testing.assert_array_equal(a[k], b[k])
+    d_rgb, d_dep = S.image_grads(cam["W"], cam["H"], 11)
+    ga = O.render_bwd(pr, cam, d_rgb, d_dep, tiled=True)
+    gb = O.render_bwd(pr, cam, d_rgb, d_dep, tiled=False)
+    np.testing.assert_array_equal(ga, gb)
+
+
+def test_tiled_equals_brute_force_on_stage_splats(oracle_lib):
+    O = oracle_lib
+    s = S.splats(400, 70, 50, seed=3)
+    cam = S.camera(70, 50, 60.0)
+    a = O.render_fwd(s, cam, tiled=True)
+    b = O.render_fwd(s, cam, tiled=False)
+    for k in ("rgb", "depth", "T", "nfrag"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+# ---------------------------------------------------------------------------
+# Binning and sort
+# ---------------------------------------------------------------------------
+
+def test_binning_hand_cases(oracle_lib):
+    O = oracle_lib
+    cam = S.camera(64, 48, 50.0)   # 4 x 3 tiles
+    uv = np.array([[20.5, 5.2], [16.0, 40.0], [-3.5, 10.0], [63.9, 47.9]])
+    depth = np.array([2.0, 1.5, 3.0, 2.5])
+    radius = np.array([4, 1, 2, 1])
+    keys, vals, ranges = O.bin_sort(uv, depth, radius, cam)
+    bits = lambda d: int(np.array(d, np.float32).view(np.uint32))
+    # G0: box x [16,24] -> tile col 1, y [1,9] -> row 0 -> tile 1
+    # G1: box x [15,17] -> cols 0,1; y [39,41] -> row 2 -> tiles 8, 9
+    # G2: box x [-6,-2] -> no pixel -> no key
+    # G3: box x [62,64] -> col 3 (64 is off-image), y [46,48] -> row 2 -> tile 11
+    expect = sorted([(1 << 32 | bits(2.0), 0), (8 << 32 | bits(1.5), 1), (9 << 32 | bits(1.5), 1),
+                     (11 << 32 | bits(2.5), 3)])
+    assert [(int(k), int(v)) for k, v in zip(keys, vals)] == expect
+    assert ranges[1].tolist() == [0, 1]
+    assert ranges[8].tolist() == [1, 2] and ranges[9].tolist() == [2, 3]
+    assert ranges[11].tolist() == [3, 4]
+    assert ranges[0].tolist() == [0, 0]
+    # stride 2: sampled columns of G0 are 8..12 -> tile col 0
+    cam2 = dict(cam, sx=2, sy=2)
+    k2, v2, r2 = O.bin_sort(uv[:1], depth[:1], radius[:1], cam2)
+    assert [int(k) >> 32 for k in k2] == [0]
+
+
+def test_sort_invariants_and_stability(oracle_lib):
+    O = oracle_lib
+    cam = S.camera(200, 120, 100.0)
+    s = S.splats(3000, 200, 120, seed=5, tie_frac=0.2)
+    keys, vals, ranges = O.bin_sort(s["uv"], s["depth"], s["radius"], cam)
+    # permutation of the expected multiset and non-decreasing keys
+    assert np.all(np.diff(keys.astype(np.float64)) >= 0) or np.all(keys[1:] >= keys[:-1])
+    _, _, TX, TY = O.grid(cam)
+    pr_rect = []
+    total = 0
+    for k in range(3000):
+        r = int(s["radius"][k])
+        if r <= 0:
+            pr_rect.append(None)
+            continue
+        xi, yi = math.floor(s["uv"][k, 0]), math.floor(s["uv"][k, 1])
+        tx = [t for t in range(TX) if any(abs(p - xi) <= r for p in range(16 * t, min(16 * t + 16, 200)))]
+        ty = [t for t in range(TY) if any(abs(p - yi) <= r for p in range(16 * t, min(16 * t + 16, 120)))]
+        pr_rect.append((tx, ty))
+        total += len(tx) * len(ty)
+    assert len(keys) == total
+    # every value in tile t's range has t in its rect (brute-force rect)
+    for t in range(TX * TY):
+        b, e = ranges[t]
+        for i in range(b, e):
+            k = int(vals[i])
+            tx, ty = pr_rect[k]
+            assert (t % TX) in tx and (t // TX) in ty
+            assert int(keys[i]) >> 32 == t
+    # equal keys keep id order
+    same = keys[1:] == keys[:-1]
+    assert same.sum() > 0
+    assert np.all(vals[1:][same] > vals[:-1][same])
+
+
+# ---------------------------------------------------------------------------
+# Projection against independent routes
+# ---------------------------------------------------------------------------
+
+def test_projection_matches_numerical_jacobian(oracle_lib):
+    """Sigma2 - 0.3 I equals J_num Sigma_c J_num^T, with J_num the numerical
+    Jacobian of the pinhole map and Sigma_c built with scipy's rotation."""
+    from scipy.spatial.transform import Rotation
+    O = oracle_lib
+    g = S.rng(9)
+    n = 40
+    q = S.random_unit_quats(g, n)
+    means = np.stack([g.uniform(-0.5, 0.5, n), g.uniform(-0.4, 0.4, n), g.uniform(1.0, 4.0, n)], 1)
+    ls = g.normal(-2.5, 0.5, (n, 3))
+    gs = {"means": means, "log_scales": ls, "quats": q, "opacity_logit": np.zeros(n),
+          "rgb": np.zeros((n, 3))}
+    ang = 0.2
+    Rcw = S.axis_angle_matrix([0.3, 1.0, -0.2], ang)
+    t = np.array([0.05, -0.02, 0.3])
+    cam = S.camera(160, 120, 140.0, R=Rcw, t=t)
+    pr = O.project(gs, cam)
+    for k in range(n):
+        assert pr["radius"][k] > 0
+        Rq = Rotation.from_quat([q[k, 1], q[k, 2], q[k, 3], q[k, 0]]).as_matrix()
+        Sig = Rq @ np.diag(np.exp(2 * ls[k])) @ Rq.T
+        Sc = Rcw @ Sig @ Rcw.T
+        p = Rcw @ means[k] + t
+
+        def pin(pp):
+            return np.array([140.0 * pp[0] / pp[2] + 80.0, 140.0 * pp[1] / pp[2] + 60.0])
+
+        J = np.zeros((2, 3))
+        h = 1e-6
+        for j in range(3):
+            e = np.zeros(3)
+            e[j] = h
+            J[:, j] = (pin(p + e) - pin(p - e)) / (2 * h)
+        S2 = J @ Sc @ J.T + 0.3 * np.eye(2)
+        A, B, Cc = pr["conic"][k]
+        S2o = np.linalg.inv(np.array([[A, B], [B, Cc]]))
+        np.testing.assert_allclose(S2o, S2, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(pr["uv"][k], pin(p), rtol=1e-12)
+        lmax = np.linalg.eigvalsh(S2).max()
+        mid = 0.5 * (S2[0, 0] + S2[1, 1])
+        if mid * mid - np.linalg.det(S2) > 0.1:
+            r3 = 3 * math.sqrt(lmax)
+            if abs(r3 - round(r3)) > 1e-6:
+                assert pr["radius"][k] == math.ceil(r3)
+
+
+def test_near_plane_and_mask_cull(oracle_lib):
+    O = oracle_lib
+    g = concat(one_gaussian(0, 0, 0.19, -3, 0, (1, 1, 1)), one_gaussian(0, 0, 0.21, -3, 0, (1, 1, 1)),
+               one_gaussian(0, 0, 1.0, -3, 0, (1, 1, 1)))
+    g["mask"] = np.array([0, 0, 1], np.uint8)
+    pr = O.project(g, S.camera(32, 32, 30.0))
+    assert pr["radius"].tolist()[0] == 0 and pr["radius"][1] > 0 and pr["radius"][2] == 0
+
+
+# ---------------------------------------------------------------------------
+# Finite differences (Sec. 2.2 backward, Step 4 and Step 5)
+# ---------------------------------------------------------------------------
+
+def small_fd_scene(seed):
+    g = S.rng(seed)
+    n = 14
+    means = np.stack([g.uniform(-0.6, 0.6, n), g.uniform(-0.45, 0.45, n), g.uniform(1.5, 3.0, n)], 1)
+    # one Gaussian beyond the Jacobian clamp line whose footprint still reaches the image
+    means[0] = [0.75 * 2.6, 0.1, 2.6]   # x/z = 0.75 > 1.3 * (W/2)/fx = 0.72
+    gs = {"means": means, "log_scales": g.normal(-2.2, 0.25, (n, 3)),
+          "quats": S.random_unit_quats(g, n) * g.uniform(0.7, 1.4, (n, 1)),
+          "opacity_logit": g.normal(0.5, 1.0, n), "rgb": g.uniform(0, 1, (n, 3))}
+    gs["log_scales"][0] = [-0.7, -0.7, -0.7]
+    return gs
+
+
+def fd_loss(O, gs, cam, w, wd):
+    pr, img = O.forward(gs, cam)
+    return float((w * img["rgb"]).sum() + (wd * img["depth"]).sum()), img["sig"], tuple(pr["radius"])
+
+
+def test_gradients_match_central_differences(oracle_lib):
+    O = oracle_lib
+    W, H = 40, 30
+    gs = small_fd_scene(21)
+    R = S.axis_angle_matrix([0.2, -0.5, 1.0], 0.05)
+    cam = S.camera(W, H, 36.0, R=R, t=[0.01, -0.02, 0.05])
+    g = S.rng(22)
+    w = g.normal(0, 1, (3, H, W))
+    wd = g.normal(0, 1, (H, W))
+    _, _, an = O.forward_backward(gs, cam, w, wd)
+    h = 1e-5
+    checked = 0
+    for key, width in (("means", 3), ("log_scales", 3), ("quats", 4), ("opacity_logit", 1),
+                       ("rgb", 3)):
+        for k in range(len(gs["means"])):
+            for j in range(width):
+                gp = {kk: np.array(v, dtype=np.float64, copy=True) for kk, v in gs.items()}
+                gm = {kk: np.array(v, dtype=np.float64, copy=True) for kk, v in gs.items()}
+                if width == 1:
+                    gp[key][k] += h
+                    gm[key][k] -= h
+                else:
+                    gp[key][k, j] += h
+                    gm[key][k, j] -= h
+                Lp, sp, rp = fd_loss(O, gp, cam, w, wd)
+                Lm, sm, rm = fd_loss(O, gm, cam, w, wd)
+                L0, s0, r0 = fd_loss(O, gs, cam, w, wd)
+                if not (sp == s0 == sm and rp == r0 == rm):
+                    continue  # the stencil crosses a predicate; not differentiable here
+                fd = (Lp - Lm) / (2 * h)
+                a = an[key][k] if width == 1 else an[key][k, j]
+                assert abs(fd - a) <= 2e-5 * max(1.0, abs(a)), (key, k, j, fd, a)
+                checked += 1
+    assert checked > 150
+    # clamped-Jacobian Gaussian 0 was exercised
+    assert abs(an["means"][0]).sum() > 0
+
+
+def pose_perturb(cam, xi):
+    """Left perturbation T_cw <- exp(xi^) T_cw to first order along xi, with
+    the rotation part exact (Rodrigues) -- a smooth curve whose tangent at
+    zero is xi^."""
+    rho, phi = np.asarray(xi[:3]), np.asarray(xi[3:])
+    ang = np.linalg.norm(phi)
+    Rd = np.eye(3) if ang == 0 else S.axis_angle_matrix(phi / ang, ang)
+    c = dict(cam)
+    c["R"] = Rd @ np.asarray(cam["R"])
+    c["t"] = Rd @ np.asarray(cam["t"]) + rho
+    return c
+
+
+def test_pose_gradient_matches_central_differences(oracle_lib):
+    O = oracle_lib
+    W, H = 40, 30
+    gs = small_fd_scene(31)
+    cam = S.camera(W, H, 36.0, R=S.axis_angle_matrix([1, 0.3, 0.1], 0.04), t=[0.02, 0.01, -0.03])
+    g = S.rng(32)
+    w = g.normal(0, 1, (3, H, W))
+    wd = g.normal(0, 1, (H, W))
+    _, _, an = O.forward_backward(gs, cam, w, wd)
+    h = 1e-6
+    for i in range(6):
+        e = np.zeros(6)
+        e[i] = h
+        Lp, sp, rp = fd_loss(O, gs, pose_perturb(cam, e), w, wd)
+        Lm, sm, rm = fd_loss(O, gs, pose_perturb(cam, -e), w, wd)
+        assert sp == sm and rp == rm
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - an["pose"][i]) <= 1e-5 * max(1.0, abs(fd)), (i, fd, an["pose"][i])
+
+
+def test_pose_gradient_zero_at_target_and_descent_when_perturbed(oracle_lib):
+    """At the exact target pose every L1 residual is 0 and sign(0) = 0, so the
+    pose gradient is exactly 0.  From a pose 2 cm / 1 deg away, a small step
+    along -grad lowers the loss (Eq. 6)."""
+    O = oracle_lib
+    gs = S.tiny_scene(seed=44, n=500)
+    cam = S.tiny_camera()
+    _, tgt = O.forward(gs, cam)
+    _, img = O.forward(gs, cam)
+    L, dr, dd = O.loss_l1(img["rgb"], img["depth"], tgt["rgb"], tgt["depth"])
+    assert L == 0.0
+    _, _, gb = O.forward_backward(gs, cam, dr, dd)
+    assert np.all(gb["pose"] == 0.0)
+    start = S.perturbed_pose(cam, seed=45, trans=0.02, rot_deg=1.0)
+    _, img = O.forward(gs, start)
+    L0, dr, dd = O.loss_l1(img["rgb"], img["depth"], tgt["rgb"], tgt["depth"])
+    _, _, gb = O.forward_backward(gs, start, dr, dd)
+    step = -gb["pose"] / np.linalg.norm(gb["pose"]) * 2e-3
+    _, img1 = O.forward(gs, pose_perturb(start, step))
+    L1, _, _ = O.loss_l1(img1["rgb"], img1["depth"], tgt["rgb"], tgt["depth"])
+    assert L1 < L0
+
+
+# ---------------------------------------------------------------------------
+# Loss (Eq. 6)
+# ---------------------------------------------------------------------------
+
+def test_loss_hand_values(oracle_lib):
+    O = oracle_lib
+    rgb = np.array([[[0.5, 0.2]], [[0.1, 0.1]], [[1.0, 0.0]]])      # [3,1,2]
+    tr = np.array([[[0.25, 0.2]], [[0.3, 0.0]], [[0.5, 0.5]]])
+    dep = np.array([[2.0, 3.0]])
+    td = np.array([[1.5, 0.0]])                                      # second invalid
+    L, dr, dd = O.loss_l1(rgb, dep, tr, td, w_rgb=0.9, w_depth=0.1)
+    # |res| = .25,0,.2,.1,.5,.5 -> sum 1.55 ; depth |.5| on the valid pixel
+    assert math.isclose(L, 0.9 * 1.55 / 6 + 0.1 * 0.5 / 2, rel_tol=1e-14)
+    np.testing.assert_array_equal(np.sign(dr).ravel(), [1, 0, -1, 1, 1, -1])
+    np.testing.assert_allclose(np.abs(dr[dr != 0]), 0.9 / 6)
+    np.testing.assert_allclose(dd, [[0.1 / 2, 0.0]])
+
+
+# ---------------------------------------------------------------------------
+# Pruning (Sec. 4.1, Eq. 7) and interval schedule
+# ---------------------------------------------------------------------------
+
+def test_prune_select_hand_case(oracle_lib):
+    O = oracle_lib
+    t_mu = np.array([3, 1, 2, 1, 0, 5, 1], np.float32)
+    t_sig = np.array([0, 0, 0, 0, 0, 0, 0], np.float32)
+    mask = np.array([0, 0, 0, 0, 0, 0, 1], np.uint8)     # id 6 already masked
+    m, cnt = O.prune_select(t_mu, t_sig, mask, lam=0.8, frac=0.5)
+    # 6 active -> mask 3: scores 0 (id 4), 1 (id 1), 1 (id 3); id 6 untouched
+    assert cnt == 3
+    assert m.tolist() == [0, 1, 0, 1, 1, 0, 1]
+    # lambda weights the covariance term: (0,10) scores 8 > (7,0)
+    m2, _ = O.prune_select(np.array([0, 7], np.float32), np.array([10, 0], np.float32),
+                           np.zeros(2, np.uint8), lam=0.8, frac=0.5)
+    assert m2.tolist() == [0, 1]
+    # cap on the number selected
+    m3, c3 = O.prune_select(t_mu, t_sig, np.zeros(7, np.uint8), frac=0.5, max_select=1)
+    assert c3 == 1 and m3.tolist() == [0, 0, 0, 0, 1, 0, 0]
+    # all equal: ids decide
+    m4, c4 = O.prune_select(np.ones(10, np.float32), np.ones(10, np.float32), np.zeros(10, np.uint8),
+                            frac=0.3)
+    assert c4 == 3 and m4.tolist() == [1, 1, 1, 0, 0, 0, 0, 0, 0, 0]
+
+
+def test_interval_schedule(oracle_lib):
+    O = oracle_lib
+    hp = json.load(open(os.path.join(GOLD, "hyperparams.json")))
+    K0, thr = hp["k0"], hp["change_ratio_threshold"]
+    K = K0
+    seq = []
+    for r in [0.10, 0.01, 0.01, 0.20, 0.05, 0.0]:
+        K = O.next_interval(K, r, K0=K0, thr=thr)
+        seq.append(K)
+    assert seq == [2, 4, 8, 4, 8, 16]
+    assert O.next_interval(1, 0.9) == 1
+    assert O.next_interval(64, 0.0) == 64
+    # the paper's literal constants: K0/2 or 2 K0
+    assert O.next_interval(7, 0.10, K0=5, literal=True) == 2
+    assert O.next_interval(7, 0.01, K0=5, literal=True) == 10
+
+
+def test_change_ratio_hand_case(oracle_lib):
+    O = oracle_lib
+    A = [(0 << 32) | 1, (0 << 32) | 2, (1 << 32) | 3]
+    B = [(0 << 32) | 1, (1 << 32) | 3, (2 << 32) | 5, (2 << 32) | 6]
+    assert O.change_ratio(A, B) == pytest.approx(3 / 3)
+    assert O.change_ratio(A, A) == 0.0
+    assert O.change_ratio([], B) == 4.0
+
+
+# ---------------------------------------------------------------------------
+# Downsampling (Sec. 4.2)
+# ---------------------------------------------------------------------------
+
+def test_downsample_schedule_table(oracle_lib):
+    O = oracle_lib
+    tab = json.load(open(os.path.join(GOLD, "downsample_schedule.json")))
+    k = 10
+    for row in tab["rows"]:
+        sx, sy = O.downsample_schedule(k + 1 + row["e"], k, False, m=tab["m"])
+        assert (sx, sy) == (row["sx"], row["sy"])
+        assert 1.0 / (sx * sy) == row["fraction"]
+    assert O.downsample_schedule(k, k, True) == (1, 1)
+    with pytest.raises(ValueError):
+        O.downsample_schedule(12, 10, False, m=3)
+
+
+@pytest.mark.parametrize("sx,sy", [(2, 2), (4, 2), (4, 4), (3, 1)])
+def test_strided_render_equals_subsampled_full_render(oracle_lib, sx, sy):
+    O = oracle_lib
+    g = S.tiny_scene(seed=77)
+    cam = S.tiny_camera()
+    pr = O.project(g, cam)
+    full = O.render_fwd(pr, cam)
+    cs = dict(cam, sx=sx, sy=sy)
+    sub = O.render_fwd(pr, cs)
+    np.testing.assert_array_equal(sub["rgb"], full["rgb"][:, ::sy, ::sx])
+    np.testing.assert_array_equal(sub["depth"], full["depth"][::sy, ::sx])
+    np.testing.assert_array_equal(O.gather(full["rgb"], sx, sy), full["rgb"][:, ::sy, ::sx])
