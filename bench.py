@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the rasterizer hot path on the SLAM tracking workload:
+640x480 RGB-D, 200k surface-sampled Gaussians, pose-only backward of
+L1 RGB + 0.5 L1 depth against a target rendered from the true pose, the
+camera starting 2 cm / 1 deg away.
+
+One step = one tracking iteration: projection, binning + 64-bit radix sort +
+tile ranges, forward compositing, L1 loss and its image gradient, backward
+compositing, backward projection with the compensated pose-gradient
+reduction and Eq. 7 score terms, and an Adam pose step on the device.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
+oracle on the same workload instead (a bounded sample per step).
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling,
+no collective on the data path); value = all ranks' iterations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd render iters/s and Mpix/s at 640x480/200k G"
+WORKLOAD = "slam_tracking_640x480_200k"
+W_IMG, H_IMG, N_G = 640, 480, 200_000
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-graph", action="store_true", help="time eager launches instead of a CUDA graph")
+    p.add_argument("--skip-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# --------------------------------------------------------------------------
+
+def oracle_iteration(scene, true_img, cam, band_rows):
+    """One oracle tracking iteration whose per-pixel stages (binning, forward,
+    loss, backward) run on a band of `band_rows` image rows; the per-Gaussian
+    stages run in full.  Returns (seconds for the band iteration, seconds
+    extrapolated to the full frame)."""
+    import numpy as np
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    pr = O.project(scene, cam)
+    t1 = time.perf_counter()
+    H = cam["H"]
+    j0 = (H - band_rows) // 2
+    band = dict(cam, H=band_rows)
+    sp = dict(pr)
+    sp["uv"] = pr["uv"] - np.array([0.0, j0])
+    img = O.render_fwd(sp, band)
+    L, dr, dd = O.loss_l1(img["rgb"], img["depth"], true_img["rgb"][:, j0:j0 + band_rows],
+                          true_img["depth"][j0:j0 + band_rows])
+    g2 = O.render_bwd(sp, band, dr, dd)
+    t2 = time.perf_counter()
+    O.project_bwd(scene, cam, g2)
+    t3 = time.perf_counter()
+    per_pixel = t2 - t1
+    return t3 - t0, (t1 - t0) + (t3 - t2) + per_pixel * (H / band_rows)
+
+
+def cpu_baseline(budget_s=20.0):
+    from oracle import oracle as O
+    from synth import scenes as S
+    O.build()
+    scene, true_cam, start_cam = S.tracking_workload(N_G, W_IMG, H_IMG)
+    _, true_img = O.forward(scene, true_cam)
+    times = []
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s and len(times) < 5:
+        _, full = oracle_iteration(scene, true_img, start_cam, H_IMG)
+        times.append(full)
+    t = statistics.median(times)
+    return {"value": 1.0 / t, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full 640x480/200k tracking iterations of the single-threaded FP64 C oracle "
+                      f"(projection, binning+sort, forward, L1 loss, backward, backward projection + pose); "
+                      f"median {t:.2f} s/iter",
+            "mpix_per_s": W_IMG * H_IMG / t / 1e6}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from synth import scenes as S
+    O.build()
+    scene, true_cam, start_cam = S.tracking_workload(N_G, W_IMG, H_IMG)
+    _, true_img = O.forward(scene, true_cam)
+    band = 48  # rows per step: keeps a 100-step run within a few minutes
+    for _ in range(args.warmup):
+        oracle_iteration(scene, true_img, start_cam, band)
+    ext = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, full = oracle_iteration(scene, true_img, start_cam, band)
+        ext.append(full)
+    wall = time.perf_counter() - t0
+    t = sum(ext) / len(ext)
+    v = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mpix_per_s": W_IMG * H_IMG * v / 1e6,
+                       "sample": f"each step: full projection and backward projection of 200k Gaussians, "
+                                 f"binning/forward/loss/backward on a {band}-row band, per-pixel time scaled "
+                                 f"by {H_IMG}/{band}; wall {wall:.1f} s"},
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{band}-row band per step, extrapolated to 640x480"},
+            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU path
+# --------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    __graft_entry__.build()
+    from paper_2510_06644_gb300 import gs
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    from synth import scenes as S
+
+    scene, true_cam, start_cam = S.tracking_workload(N_G, W_IMG, H_IMG)
+    gd = {k: torch.from_numpy(v).cuda() for k, v in scene.items()}
+    n = N_G
+    # key capacity from the starting pose, with headroom for the pose moving
+    probe = gs.gs_project(gs.default_config(), gs.camera(start_cam), gd)
+    n_keys0 = int(gs.gs_bin_count(gs.camera(start_cam), probe, n).item())
+    rast = Rasterizer(n, start_cam, capacity=int(n_keys0 * 1.5) + 4096)
+    # target: render from the true pose
+    img = rast.forward(gd, true_cam)
+    trgb = img["rgb"].clone()
+    tdep = img["depth"].clone()
+    pose = gs.pose_tensor(start_cam)
+    pose0 = pose.clone()
+    adam = torch.zeros(13, device="cuda")
+    cam_s = gs.camera(start_cam, pose=pose)
+    lr_t, lr_r = 1e-3, 1e-3
+
+    def step():
+        rast.step(gd, cam_s, trgb, tdep, gs.GS_TRACK)
+        gs.gs_pose_update(pose, rast.pose, adam, lr_t, lr_r)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    rast.check()
+    graph = None
+    if not args.no_graph:
+        try:
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                step()
+            torch.cuda.current_stream().wait_stream(s)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+                step()
+            graph.replay()
+            torch.cuda.synchronize()
+            rast.check()
+        except Exception as e:  # eager launches still time the same kernels
+            print(f"[bench] graph capture failed, timing eager launches: {e}", file=sys.stderr)
+            graph = None
+    run = graph.replay if graph is not None else step
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    K = args.steps
+    pose.copy_(pose0)
+    adam.zero_()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record()
+        run()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    rast.check()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = t_ms
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    iters_s = world * K / (t_max / 1e3)
+    final_pose = pose.cpu().numpy()
+
+    # ---- stage timings (eager, events on the launching stream) ----
+    Kst = min(K, 30)
+    names = ["project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd_pose", "pose_update"]
+    acc = {k: 0.0 for k in names}
+    cs = cam_s
+    for _ in range(Kst):
+        flush.zero_()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        evs[0].record()
+        gs.gs_project(rast.cfg, cs, gd, rast.rec_dtype, rast.splats)
+        evs[1].record()
+        gs.gs_bin_sort(cs, rast.splats, n, rast.capacity, rast.rec_dtype, ws=rast._sort_ws(cs), keys=rast.keys,
+                       vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges)
+        evs[2].record()
+        gs.gs_render_fwd(rast.cfg, cs, rast.splats, n, rast.vals, rast.ranges, rast.rec_dtype, out=rast.img)
+        evs[3].record()
+        rast.loss_grad(cs, trgb, tdep)
+        evs[4].record()
+        gs.gs_render_bwd(rast.cfg, cs, gd, rast.splats, rast.vals, rast.ranges, rast.img["t_final"],
+                         rast.img["last_idx"], rast.dimg["d_rgb"], rast.dimg["d_depth"], gs.GS_TRACK,
+                         rast.rec_dtype, grad2d=rast.grad2d)
+        evs[5].record()
+        gs.gs_project_bwd(rast.cfg, cs, gd, rast.grad2d, pose=rast.pose, score=rast.score, ws=rast._bwd_ws(cs, gd))
+        evs[6].record()
+        gs.gs_pose_update(pose, rast.pose, adam, lr_t, lr_r)
+        evs[7].record()
+        torch.cuda.synchronize()
+        for i, k in enumerate(names):
+            acc[k] += evs[i].elapsed_time(evs[i + 1])
+    stage_ms = {k: v / Kst for k, v in acc.items()}
+    n_keys = int(rast.n_keys.item())
+    P = W_IMG * H_IMG
+    last = rast.img["last_idx"].long()
+    walked = int(last.sum().item())
+
+    # ---- roofline of the dominant kernel ----
+    dom = max(stage_ms, key=stage_ms.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    # algorithmic bytes per launch (per-unit figures x units)
+    alg = {
+        "project": 56 * n + 48 * n,
+        "bin_sort": 8 * n + 12 * n_keys + 6 * 24 * n_keys + 8 * n_keys,
+        "render_fwd": 48 * n_keys + 4 * n_keys + 24 * P,
+        "loss": 40 * P,
+        "render_bwd": 52 * n_keys + 40 * P + 4 * 6 * n_keys,
+        "project_bwd_pose": (56 + 48) * n + 8 * n,
+        "pose_update": 100,
+    }
+    roof = {"bound": "hbm", "kernel": dom, "achieved": alg[dom] / (stage_ms[dom] * 1e-3) / 1e9,
+            "peak": hbm_peak, "unit": "GB/s", "peak_source": peak_src, "traffic": None,
+            "algorithmic_bytes": alg[dom], "avg_ms": stage_ms[dom]}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    # ---- end to end through the public API with host buffers ----
+    trgb_h = trgb.cpu().pin_memory()
+    tdep_h = tdep.cpu().pin_memory()
+    out_h = torch.empty(7, dtype=torch.float64).pin_memory()
+    Ke = min(K, 50)
+    pose.copy_(pose0)
+    adam.zero_()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Ke)]
+    torch.cuda.synchronize()
+    for i in range(Ke):
+        flush.zero_()
+        ev2[i][0].record()
+        trgb.copy_(trgb_h, non_blocking=True)
+        tdep.copy_(tdep_h, non_blocking=True)
+        run()
+        out_h[:6].copy_(rast.pose, non_blocking=True)
+        out_h[6:].copy_(rast.dimg["loss"], non_blocking=True)
+        ev2[i][1].record()
+    torch.cuda.synchronize()
+    te = sum(a.elapsed_time(b) for a, b in ev2)
+    e2e = {"value": world * Ke / (te / 1e3), "unit": "iters/s",
+           "h2d_bytes_per_step": trgb.numel() * 4 + tdep.numel() * 4, "d2h_bytes_per_step": 7 * 8}
+
+    passes = (32 + max(1, (int(np.ceil(np.log2(max(2, rast._grid[2] * rast._grid[3])))))) + 7) // 8
+    launches_per_step = 1 + (5 + passes) + 1 + 1 + 1 + 2 + 1
+    line = {
+        "metric": METRIC, "value": iters_s, "unit": "iters/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "mpix_per_s": iters_s * P / 1e6,
+        "config": {"workload": WORKLOAD, "gaussians": n, "width": W_IMG, "height": H_IMG,
+                   "keys_per_iter": n_keys, "list_entries_walked": walked, "cuda_graph": graph is not None,
+                   "l2": "flushed before every timed step (256 MB write, outside the step's events)",
+                   "parallelism": f"replicas x{world}", "stage_ms": stage_ms,
+                   "pose_moved": float(np.abs(final_pose - pose0.cpu().numpy()).max())},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * K,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

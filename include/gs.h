@@ -1,0 +1,359 @@
+/*
+ * gs.h -- C ABI of a GB300 (sm_103a) differentiable tile-based 3D Gaussian
+ * rasterizer: the per-iteration hot path of 3DGS-SLAM tracking and mapping as
+ * described by RTGS (arXiv 2510.06644, Sec. 2.1-2.2 and Sec. 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.  Every array argument is a DEVICE pointer unless a comment says
+ *   "host".  The caller allocates and frees all device memory, including
+ *   workspace; the library never allocates, frees or synchronises, except
+ *   gs_status_poll(..., blocking=1), which synchronises the given stream.
+ * Streams.  Work is enqueued asynchronously on the caller's stream (a
+ *   cudaStream_t passed as gs_stream; NULL = the legacy default stream).
+ * Workspace.  Entry points that need scratch take (void* workspace,
+ *   size_t* workspace_bytes).  With workspace == NULL they only store the
+ *   required size in *workspace_bytes and return GS_OK.  Otherwise
+ *   *workspace_bytes must be at least that size (GS_ERR_WORKSPACE if not) and
+ *   the workspace must be 256-byte aligned.
+ * Errors.  Argument checks are synchronous and return a gs_status; the
+ *   thread-local message is in gs_last_error().  Conditions found on the
+ *   device (a bounded wait that gave up, a key count above the capacity) set
+ *   a per-device status word that gs_status_poll() reads.  No C++ exception
+ *   crosses this boundary.
+ * Images.  The camera renders the full-resolution W x H image sampled with
+ *   strides (sx, sy) (Sec. 4.2 dynamic downsampling): the sampled image has
+ *   Ws = ceil(W/sx) columns and Hs = ceil(H/sy) rows, sampled pixel (i, j) is
+ *   full-resolution pixel (sx*i, sy*j) and is evaluated at its centre
+ *   (sx*i + 0.5, sy*j + 0.5).  Images are planar float32: rgb [3][Hs][Ws],
+ *   depth [Hs][Ws].  Tiles are 16 x 16 sampled pixels (Sec. 2.1, Step 1-2
+ *   footnote), TX = ceil(Ws/16) by TY = ceil(Hs/16), row-major tile ids.
+ * Empty inputs.  n = 0 Gaussians, zero keys and empty tiles are valid.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gs_stream; /* identical to cudaStream_t */
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,   /* bad pointer, size, stride or enum */
+    GS_ERR_WORKSPACE = 2,     /* workspace smaller than required */
+    GS_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
+    GS_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    GS_ERR_CAPACITY = 5,      /* more (tile, Gaussian) keys than the output holds */
+    GS_ERR_DEVICE_CHECK = 6,  /* a device-side consistency check failed */
+    GS_ERR_UNIMPLEMENTED = 7
+} gs_status;
+
+enum { GS_TRACK = 0, GS_MAP = 1 };           /* backward modes (Sec. 2.2) */
+enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 }; /* 2D record storage types */
+enum { GS_IDLE = 0, GS_EXECUTING = 1 };       /* gs_status_poll state */
+
+/* Pinhole camera.  R, t map world to camera (x_c = R x_w + t), row-major R.
+ * fx, fy focal lengths and cx, cy principal point, in full-resolution pixels;
+ * the 2D mean of a camera point (x, y, z) is (fx x/z + cx, fy y/z + cy). */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height; /* full-resolution image W, H */
+    int32_t sx, sy;        /* sampling strides, >= 1 */
+    const float* pose;     /* NULL, or a DEVICE float[12] (R row-major, then t)
+                              that replaces R and t when a kernel starts, so a
+                              pose updated on the device (gs_pose_update) is
+                              used without a host round trip */
+} gs_camera;
+
+/* Method constants.  gs_default_config() fills the values used throughout:
+ * near_z 0.2, dilation 0.3, alpha_min 1/255, alpha_max 0.99, t_eps 1e-4,
+ * bg (0,0,0), lambda_score 0.8 (Sec. 6.1), prune_frac 0.1, prune_cap 0.5
+ * (Sec. 6.2 ablation cap), change_thr 0.05 (Sec. 4.1), k0 5 (Sec. 6.1),
+ * k_max 64, w_rgb 1, w_depth 0.5 (tracking loss). */
+typedef struct {
+    float near_z;       /* cull when camera-frame z < near_z */
+    float dilation;     /* low-pass term added to the 2D covariance diagonal */
+    float alpha_min;    /* fragments with alpha below this are skipped */
+    float alpha_max;    /* alpha is clamped to this value */
+    float t_eps;        /* stop before a fragment when T (1 - alpha) < t_eps */
+    float bg[3];        /* background colour */
+    float lambda_score; /* weight of ||dL/dSigma|| in the score (Eq. 7) */
+    float prune_frac;   /* fraction of active Gaussians masked per interval */
+    float prune_cap;    /* cap on the pruned fraction of the reference count */
+    float change_thr;   /* change-ratio threshold of the interval rule */
+    int32_t k0;         /* initial pruning interval K0 */
+    int32_t k_max;      /* largest interval */
+    float w_rgb;        /* photometric weight of the loss (Eq. 6) */
+    float w_depth;      /* geometric weight of the loss (Eq. 6) */
+} gs_config;
+
+/* 3D Gaussians (Sec. 2.1, Eq. 1), structure of arrays, float32:
+ * means [n][3]; log_scales [n][3] (Sigma = Rq diag(exp(2 s)) Rq^T);
+ * quats [n][4] as (w, x, y, z), need not be normalised; opacity_logit [n]
+ * (opacity = sigmoid); rgb [n][3].  mask [n] or NULL: nonzero = masked out of
+ * rendering by the mask-prune step (Sec. 4.1). */
+typedef struct {
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opacity_logit;
+    const float* rgb;
+    const uint8_t* mask;
+    int64_t n;
+} gs_gaussians;
+
+/* One projected 2D Gaussian (Sec. 2.1, Step 1-1), 48 bytes, 16-byte aligned.
+ * Array of structures so that the compositing kernels gather one Gaussian
+ * with three 16-byte loads. */
+typedef struct {
+    float x, y;           /* 2D mean, full-resolution pixels */
+    float conic_a;        /* inverse 2D covariance [[a, b], [b, c]] */
+    float conic_b;
+    float conic_c;
+    float opacity;        /* sigmoid(opacity_logit) */
+    float depth;          /* camera-frame z */
+    int32_t radius;       /* ceil(3 sqrt(lambda_max)); 0 = culled or masked */
+    float r, g, b;        /* colour */
+    uint32_t tiles_touched;
+} gs_splat;
+
+/* The same record with opacity, conic and colour stored as 16-bit floats
+ * (bf16 or fp16, the GS_BF16 / GS_F16 precision form), 32 bytes.  Mean and
+ * depth stay float32.  tiles_touched saturates at 65535. */
+typedef struct {
+    float x, y;
+    float depth;
+    int32_t radius;
+    uint16_t conic_a, conic_b, conic_c, opacity;
+    uint16_t r, g, b;
+    uint16_t tiles_touched;
+} gs_splat16;
+
+/* Gradients of the 3D parameters, same layouts as gs_gaussians; any member
+ * may be NULL to skip it. */
+typedef struct {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity_logit;
+    float* rgb;
+} gs_grads;
+
+/* Per-Gaussian 2D gradient, 12 float32 (48 bytes) per Gaussian:
+ * [0] dL/dx [1] dL/dy [2] dL/dconic_a [3] dL/dconic_b [4] dL/dconic_c
+ * [5] dL/dopacity [6] dL/ddepth [7] unused [8..10] dL/drgb [11] unused. */
+#define GS_GRAD2D_STRIDE 12
+
+/* Fills *cfg with the defaults listed above. */
+void gs_default_config(gs_config* cfg);
+
+/* Library version string and the device architecture it was built for. */
+const char* gs_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* A-1 Projection (Sec. 2.1, Step 1-1; Eq. 1)                               */
+/* ---------------------------------------------------------------------- */
+/* Projects each Gaussian: camera point p = R mu + t; culled (radius 0) when
+ * masked, when p.z < near_z or when the 2D covariance is singular; 2D
+ * covariance J R Sigma R^T J^T + dilation I with the perspective Jacobian J
+ * (x/z, y/z clamped to +-1.3 (W/2)/fx, +-1.3 (H/2)/fy); conic = its
+ * inverse; radius = ceil(3 sqrt(lambda_max)); tiles_touched = number of tiles
+ * of the sampled grid that the integer box [floor(x)-r, floor(x)+r] x
+ * [floor(y)-r, floor(y)+r] reaches.
+ * splats: [n] gs_splat (rec_dtype GS_F32) or gs_splat16 (GS_BF16, GS_F16),
+ * caller-owned, fully overwritten. */
+gs_status gs_project(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                     int rec_dtype, void* splats, gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* A-2..A-4 Tile intersection, key duplication, 64-bit radix sort, ranges   */
+/* (Sec. 2.1, Step 1-2 and Step 2)                                          */
+/* ---------------------------------------------------------------------- */
+/* For every Gaussian with radius > 0 and every tile of its rect (row-major
+ * inside the rect, Gaussians in id order) one key
+ *     key = tile_id << 32 | float32 bits of depth,   value = Gaussian id,
+ * then a stable LSD radix sort on the low 32 + ceil(log2(TX*TY)) key bits,
+ * so each tile's list is in (depth, id) order; finally
+ * tile_ranges[2t], tile_ranges[2t+1] = [first, last+1) of tile t ([0,0) when
+ * empty).  The rect is recomputed from (x, y, radius) of the records.
+ * keys_out [keys_capacity] u64, vals_out [keys_capacity] u32,
+ * n_keys_out: one device int64 receiving the true key count, tile_ranges
+ * [2*TX*TY] u32.  If the count exceeds keys_capacity, only keys_capacity keys
+ * are sorted and the device status becomes GS_ERR_CAPACITY.
+ * Workspace: query with workspace == NULL (depends on n, keys_capacity and
+ * the tile count). */
+gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
+                      int64_t keys_capacity, void* workspace, size_t* workspace_bytes,
+                      uint64_t* keys_out, uint32_t* vals_out, int64_t* n_keys_out,
+                      uint32_t* tile_ranges, gs_stream stream);
+
+/* Key count only (the first two stages of gs_bin_sort), so that a caller can
+ * size keys_capacity.  Same workspace as gs_bin_sort. */
+gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
+                       void* workspace, size_t* workspace_bytes, int64_t* n_keys_out,
+                       gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* A-5 Forward compositing (Sec. 2.1, Step 3; Eq. 2 and Eq. 3)              */
+/* ---------------------------------------------------------------------- */
+/* For each sampled pixel, front to back over its tile's sorted list: a
+ * Gaussian whose integer box does not contain the pixel is skipped;
+ * power = -(a dx^2 + c dy^2)/2 - b dx dy with (dx, dy) = pixel centre - mean;
+ * power > 0 skipped; alpha = min(alpha_max, opacity exp(power)); alpha <
+ * alpha_min skipped; if T (1 - alpha) < t_eps the pixel stops before this
+ * fragment; else C += T alpha c, D += T alpha depth, T *= (1 - alpha).
+ * Finally C += T bg.
+ * Outputs: rgb [3][Hs][Ws], depth [Hs][Ws], t_final [Hs][Ws], last_idx
+ * [Hs][Ws] (list position + 1 of the last blended fragment, relative to the
+ * tile's first entry; 0 if none).  vals and tile_ranges come from
+ * gs_bin_sort with the same camera. */
+gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype,
+                        const void* splats, int64_t n, const uint32_t* vals,
+                        const uint32_t* tile_ranges, float* rgb, float* depth, float* t_final,
+                        uint32_t* last_idx, gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* A-6 Loss (Sec. 4.1, Eq. 6)                                               */
+/* ---------------------------------------------------------------------- */
+/* L = w_rgb mean_{3P}|C - C*| + w_depth mean_{P}|D - D*| (P = Ws*Hs; the
+ * depth term only where D* != 0), and dL/drgb, dL/ddepth with sign(0) = 0.
+ * target_rgb [3][Hs][Ws], target_depth [Hs][Ws] at the sampled pixels.
+ * loss_out: one device double (overwritten).  d_rgb, d_depth: outputs. */
+gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, const float* rgb,
+                     const float* depth, const float* target_rgb, const float* target_depth,
+                     float* d_rgb, float* d_depth, double* loss_out, gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* A-7 Backward compositing (Sec. 2.2, Step 4; Eq. 4 and Eq. 5)             */
+/* ---------------------------------------------------------------------- */
+/* Reverse traversal of each pixel's blended fragments: T_k is recovered from
+ * t_final by dividing by (1 - alpha_k) (Eq. 5); dL/dalpha_k =
+ * T_k (c_k - A_k) . dL/dC + T_k (d_k - A^D_k) dL/dD with the normalised
+ * suffix A_k = sum_{n>k} (T_n/T_{k+1}) alpha_n c_n + (T_final/T_{k+1}) bg
+ * (Eq. 3 differentiated; the printed Eq. 4 omits T_k and the normalisation);
+ * then through alpha = opacity exp(power) to opacity, conic and 2D mean
+ * unless alpha was clamped.  Per-fragment gradients are summed per Gaussian
+ * inside each warp, then per tile in shared memory, then added to grad2d
+ * with one global atomic per (Gaussian, tile, field).
+ * grad2d [n][12] float (GS_GRAD2D_STRIDE layout): zeroed by this call.
+ * mode GS_TRACK skips dL/dopacity and dL/drgb (not needed for the pose).
+ * If grads, pose_grad6 or score_terms is non-NULL, gs_project_bwd runs as
+ * well on the same stream (same workspace). */
+gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                        int rec_dtype, const void* splats, const uint32_t* vals,
+                        const uint32_t* tile_ranges, const float* t_final,
+                        const uint32_t* last_idx, const float* d_rgb, const float* d_depth,
+                        int mode, float* grad2d, gs_grads* grads, double* pose_grad6,
+                        float* score_terms, void* workspace, size_t* workspace_bytes,
+                        gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* A-8 Backward projection and camera pose (Sec. 2.2, Step 5)               */
+/* ---------------------------------------------------------------------- */
+/* Chains grad2d back through the projection of each Gaussian.
+ * grads (GS_MAP): 3D gradients w.r.t. means, log_scales, unnormalised quats,
+ *   opacity_logit and rgb (members may be NULL).
+ * pose_grad6: one device double[6], dL/dxi for the left perturbation
+ *   T_cw <- exp(xi^) T_cw, xi = (rho, phi) at 0:
+ *   dL/drho = sum_k dL/dp_k,
+ *   dL/dphi = sum_k p_k x dL/dp_k + (<G_k, [e_i]x S_k - S_k [e_i]x>)_i,
+ *   with p_k the camera point, S_k its camera-frame covariance and G_k =
+ *   dL/dS_k.  Per-Gaussian terms in float32, per-block sums in float64,
+ *   blocks combined with compensated (Neumaier) float64 summation.
+ * score_terms [n][2] float: (||dL/dmu||_2, ||dL/dSigma||_F) for Eq. 7.
+ * Any of the three outputs may be NULL. */
+gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                         const float* grad2d, gs_grads* grads, double* pose_grad6,
+                         float* score_terms, void* workspace, size_t* workspace_bytes,
+                         gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* A-9 Gradient-reuse pruning (Sec. 4.1, Eq. 7)                              */
+/* ---------------------------------------------------------------------- */
+/* Mask-prune state machine of one pruning interval of K iterations.
+ * iter_in_interval == 0 (selection): score_k = t_mu + lambda_score * t_sigma
+ *   in float32 (product rounded, then sum rounded); among Gaussians with
+ *   mask_inout[k] == 0 the m = min(floor(prune_frac * n_active), max_select)
+ *   smallest in (score, id) order get mask_inout[k] = 1.
+ * iter_in_interval == *k_inout (the (K+1)-th iteration, removal):
+ *   compact_map_out[k] = new index of each unmasked Gaussian in id order, or
+ *   0xFFFFFFFF for a masked one; *n_kept_out (device int64) = kept count;
+ *   *k_inout (host) becomes the next interval: max(1, K/2) if change_ratio >
+ *   change_thr, else min(2K, k_max).
+ * Any other iter_in_interval: nothing to do.
+ * score_terms [n][2] float (from gs_project_bwd).  max_select: host value
+ * (the caller's remaining cap, e.g. prune_cap * n_ref - already pruned). */
+gs_status gs_prune(const gs_config* cfg, const float* score_terms, int64_t n,
+                   uint8_t* mask_inout, int iter_in_interval, int* k_inout,
+                   float change_ratio, int64_t max_select, uint32_t* compact_map_out,
+                   int64_t* n_kept_out, void* workspace, size_t* workspace_bytes,
+                   gs_stream stream);
+
+/* Change ratio of tile-Gaussian intersections between two binnings of the
+ * same n Gaussians on the same tile grid (Sec. 4.1): |A xor B| / max(1, |A|)
+ * over the sets of (tile, Gaussian) pairs.  Each Gaussian's tiles form the
+ * rect of its record (see gs_project), so |A xor B| = sum_k |rect_a(k)| +
+ * |rect_b(k)| - 2 |rect_a(k) & rect_b(k)|.  For the mask-prune rule both
+ * binnings should include the masked Gaussians (project with mask = NULL).
+ * ratio_out: one device float. */
+gs_status gs_change_ratio(const gs_camera* cam, int rec_dtype, const void* splats_a,
+                          const void* splats_b, int64_t n, void* workspace,
+                          size_t* workspace_bytes, float* ratio_out, gs_stream stream);
+
+/* Gathers the rows of a float array [n][width] through a compaction map
+ * (0xFFFFFFFF = dropped): dst[map[k]] = src[k].  dst has *n_kept rows. */
+gs_status gs_compact(const float* src, int64_t n, int32_t width, const uint32_t* compact_map,
+                     float* dst, gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* A-10 Keyframe-driven dynamic downsampling (Sec. 4.2)                      */
+/* ---------------------------------------------------------------------- */
+/* Schedule (host, pure): keyframe -> (1,1); non-keyframe n after keyframe k
+ * -> resolution min(R0/16 m^(n-k-1), R0/4) as a pixel count, realised by the
+ * strides 16 -> (4,4), 8 -> (4,2), 4 -> (2,2).  m must be a power of two.
+ * Writes *sx, *sy (host).  If target_full is non-NULL also gathers
+ * target_out[c][j][i] = target_full[c][sy j][sx i] for `channels` planes of
+ * W x H (device). */
+gs_status gs_downsample(int64_t frame_idx, int64_t last_kf_idx, int is_keyframe, int m,
+                        int32_t* sx, int32_t* sy, const float* target_full, int32_t channels,
+                        int32_t W, int32_t H, float* target_out, gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* Camera pose step (tracking, Sec. 2.2 Step 5: dL/dP drives the pose)       */
+/* ---------------------------------------------------------------------- */
+/* One Adam step on the 6-vector xi = (rho, phi) followed by the left update
+ * T_cw <- exp(xi^) T_cw (SE(3) exponential map), entirely on the device:
+ *   g = pose_grad6 (device double[6]); adam (device float[13]) = m[6], v[6],
+ *   step count; m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   xi_i = -lr_i mhat_i / (sqrt(vhat_i) + eps) with lr_i = lr_trans for rho
+ *   and lr_rot for phi.  pose (device float[12], R row-major then t) is
+ *   updated in place.  adam must start zeroed.  The paper's Pose Computing
+ *   Unit (Sec. 5.1) does not fix the optimizer; Adam is this library's. */
+gs_status gs_pose_update(float* pose, const double* pose_grad6, float* adam, float lr_trans,
+                         float lr_rot, float beta1, float beta2, float eps, gs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* Status (the frame-level status query of Sec. 5.5, as a device word)      */
+/* ---------------------------------------------------------------------- */
+/* Returns the current device status word of the calling thread's current
+ * device (GS_OK if no device-side condition was raised).  blocking != 0
+ * synchronises `stream` first; otherwise *state (host, may be NULL) is set to
+ * GS_EXECUTING while work on `stream` is pending and the word read may be
+ * stale.  gs_status_reset clears the word (enqueued on `stream`). */
+gs_status gs_status_poll(gs_stream stream, int blocking, int* state);
+gs_status gs_status_reset(gs_stream stream);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* gs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

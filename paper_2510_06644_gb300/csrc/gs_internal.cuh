@@ -1,0 +1,174 @@
+// Internal helpers shared by the sm_103a kernels of the rasterizer.
+// Not part of the C ABI (see include/gs.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+#define GS_TILE 16
+#define GS_TILE_PIX (GS_TILE * GS_TILE)
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// Host-side error plumbing (defined in gs_api.cu)
+// ---------------------------------------------------------------------------
+gs_status set_error(gs_status code, const char* fmt, ...);
+gs_status check_launch(const char* what);
+int num_sms();
+
+// Device address of the status word of the current device (defined in
+// gs_api.cu).  Kernels that can raise a condition receive it as an argument
+// and set it with raise_status (the first condition wins).
+unsigned int* status_ptr();
+
+__device__ __forceinline__ void raise_status(unsigned int* st, unsigned int code) {
+    atomicCAS(st, 0u, code);
+}
+
+// Replaces R and t by the device pose when the camera carries one.
+__device__ __forceinline__ void resolve_pose(gs_camera& cam) {
+    if (cam.pose) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cam.R[i] = __ldg(cam.pose + i);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) cam.t[i] = __ldg(cam.pose + 9 + i);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sampled grid of a camera (Sec. 4.2 strides)
+// ---------------------------------------------------------------------------
+struct Grid {
+    int W, H;        // full resolution
+    int sx, sy;      // strides
+    int Ws, Hs;      // sampled image
+    int TX, TY;      // tiles
+};
+
+__host__ __device__ inline Grid make_grid(const gs_camera& c) {
+    Grid g;
+    g.W = c.width;
+    g.H = c.height;
+    g.sx = c.sx;
+    g.sy = c.sy;
+    g.Ws = (c.width + c.sx - 1) / c.sx;
+    g.Hs = (c.height + c.sy - 1) / c.sy;
+    g.TX = (g.Ws + GS_TILE - 1) / GS_TILE;
+    g.TY = (g.Hs + GS_TILE - 1) / GS_TILE;
+    return g;
+}
+
+__host__ __device__ inline int floor_div(int a, int b) {
+    int q = a / b;
+    return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+__host__ __device__ inline int ceil_div_i(int a, int b) { return -floor_div(-a, b); }
+__host__ __device__ inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Integer pixel position of a 2D mean: floor of the coordinate, clamped so
+// that it fits an int far outside any image.
+__device__ __forceinline__ int pix_floor(float u) {
+    return (int)floorf(fminf(fmaxf(u, -1.0e9f), 1.0e9f));
+}
+
+// Tile rect [x0,x1) x [y0,y1) of a 2D Gaussian with mean (u, v) and integer
+// radius r: the sampled pixels inside the image whose full-resolution
+// position lies in the box [floor(u)-r, floor(u)+r] x [floor(v)-r, floor(v)+r]
+// (Sec. 2.1, Step 1-2; strides of Sec. 4.2).  Returns the tile count.
+__device__ __forceinline__ int tile_rect(const Grid& g, float u, float v, int r, int& x0, int& x1,
+                                         int& y0, int& y1) {
+    x0 = x1 = y0 = y1 = 0;
+    if (r <= 0) return 0;
+    int xi = pix_floor(u), yi = pix_floor(v);
+    // 64-bit guard against xi +- r overflow is unnecessary: |xi| <= 1e9, r < 2^30
+    long long bx0 = (long long)xi - r, bx1 = (long long)xi + r;
+    long long by0 = (long long)yi - r, by1 = (long long)yi + r;
+    if (bx1 < 0 || by1 < 0 || bx0 > (long long)(g.W - 1) || by0 > (long long)(g.H - 1)) return 0;
+    int i0 = ceil_div_i((int)max(bx0, -1LL), g.sx);
+    int i1 = floor_div((int)min(bx1, (long long)g.W), g.sx);
+    int j0 = ceil_div_i((int)max(by0, -1LL), g.sy);
+    int j1 = floor_div((int)min(by1, (long long)g.H), g.sy);
+    i0 = clampi(i0, 0, g.Ws);
+    i1 = clampi(i1, -1, g.Ws - 1);
+    j0 = clampi(j0, 0, g.Hs);
+    j1 = clampi(j1, -1, g.Hs - 1);
+    if (i0 > i1 || j0 > j1) return 0;
+    x0 = i0 / GS_TILE;
+    x1 = i1 / GS_TILE + 1;
+    y0 = j0 / GS_TILE;
+    y1 = j1 / GS_TILE + 1;
+    return (x1 - x0) * (y1 - y0);
+}
+
+// ---------------------------------------------------------------------------
+// 2D records
+// ---------------------------------------------------------------------------
+// Unpacked 2D Gaussian as the compositing kernels use it.
+struct Splat {
+    float x, y, ca, cb, cc, op, depth;
+    int radius;
+    float r, g, b;
+};
+
+__device__ __forceinline__ float h2f(uint16_t h, int dt) {
+    if (dt == GS_BF16) return __bfloat162float(__ushort_as_bfloat16(h));
+    return __half2float(__ushort_as_half(h));
+}
+__device__ __forceinline__ uint16_t f2h(float f, int dt) {
+    if (dt == GS_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+    return __half_as_ushort(__float2half_rn(f));
+}
+
+template <int DT>
+__device__ __forceinline__ Splat load_splat(const void* base, uint32_t k) {
+    Splat s;
+    if (DT == GS_F32) {
+        const float4* p = reinterpret_cast<const float4*>(base) + 3 * (size_t)k;
+        float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+        s.x = a.x; s.y = a.y; s.ca = a.z; s.cb = a.w;
+        s.cc = b.x; s.op = b.y; s.depth = b.z; s.radius = __float_as_int(b.w);
+        s.r = c.x; s.g = c.y; s.b = c.z;
+    } else {
+        const uint4* p = reinterpret_cast<const uint4*>(base) + 2 * (size_t)k;
+        uint4 a = __ldg(p), b = __ldg(p + 1);
+        s.x = __uint_as_float(a.x); s.y = __uint_as_float(a.y);
+        s.depth = __uint_as_float(a.z); s.radius = (int)a.w;
+        s.ca = h2f((uint16_t)(b.x & 0xffff), DT); s.cb = h2f((uint16_t)(b.x >> 16), DT);
+        s.cc = h2f((uint16_t)(b.y & 0xffff), DT); s.op = h2f((uint16_t)(b.y >> 16), DT);
+        s.r = h2f((uint16_t)(b.z & 0xffff), DT); s.g = h2f((uint16_t)(b.z >> 16), DT);
+        s.b = h2f((uint16_t)(b.w & 0xffff), DT);
+    }
+    return s;
+}
+
+// Mean, depth and radius only (binning).
+template <int DT>
+__device__ __forceinline__ void load_geom(const void* base, uint32_t k, float& x, float& y,
+                                          float& depth, int& radius) {
+    if (DT == GS_F32) {
+        const float4* p = reinterpret_cast<const float4*>(base) + 3 * (size_t)k;
+        float4 a = __ldg(p), b = __ldg(p + 1);
+        x = a.x; y = a.y; depth = b.z; radius = __float_as_int(b.w);
+    } else {
+        const uint4* p = reinterpret_cast<const uint4*>(base) + 2 * (size_t)k;
+        uint4 a = __ldg(p);
+        x = __uint_as_float(a.x); y = __uint_as_float(a.y);
+        depth = __uint_as_float(a.z); radius = (int)a.w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace gs

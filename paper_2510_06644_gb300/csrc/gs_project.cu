@@ -1,0 +1,503 @@
+// A-1 projection (Sec. 2.1, Step 1-1) and A-8 backward projection + camera
+// pose gradient (Sec. 2.2, Step 5) on sm_103a.
+//
+// One thread per Gaussian.  Both passes call project_core(), so the backward
+// differentiates exactly the float32 arithmetic of the forward.  These
+// kernels stream the 56-byte parameter record once (forward: plus a 48-byte
+// or 32-byte 2D record write; backward: plus the 48-byte 2D gradient) and are
+// HBM-bound at large n.
+#include <stdio.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+struct Proj {
+    bool visible;
+    float p[3];          // camera-frame mean
+    float qn[4];         // normalised quaternion (w, x, y, z)
+    float qinv;          // 1/|q|
+    float scale[3];      // exp(log_scale)
+    float M[9];          // Rq diag(scale), row-major
+    float Sc[9];         // camera-frame covariance R M M^T R^T
+    bool clx, cly;       // x/z or y/z hit the clamp
+    float lx, ly;        // signed clamp value when clamped
+    float J00, J02, J11, J12;
+    float a, b, c;       // 2D covariance + dilation
+    float ca, cb, cc;    // conic
+    float u, v;
+    int radius;
+    float op;
+};
+
+__device__ __forceinline__ void project_core(const gs_camera& cam, const gs_config& cfg,
+                                             const float* mu, const float* ls, const float* q,
+                                             float ologit, Proj& o) {
+    const float* R = cam.R;
+    o.visible = false;
+    o.radius = 0;
+    for (int i = 0; i < 3; ++i)
+        o.p[i] = fmaf(R[3 * i], mu[0], fmaf(R[3 * i + 1], mu[1], fmaf(R[3 * i + 2], mu[2], cam.t[i])));
+    const float x = o.p[0], y = o.p[1], z = o.p[2];
+    if (!(z >= cfg.near_z)) return;
+
+    float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    o.qinv = 1.0f / sqrtf(qq);
+    for (int i = 0; i < 4; ++i) o.qn[i] = q[i] * o.qinv;
+    const float w = o.qn[0], qx = o.qn[1], qy = o.qn[2], qz = o.qn[3];
+    float Rq[9];
+    Rq[0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[1] = 2.f * (qx * qy - w * qz); Rq[2] = 2.f * (qx * qz + w * qy);
+    Rq[3] = 2.f * (qx * qy + w * qz); Rq[4] = 1.f - 2.f * (qx * qx + qz * qz); Rq[5] = 2.f * (qy * qz - w * qx);
+    Rq[6] = 2.f * (qx * qz - w * qy); Rq[7] = 2.f * (qy * qz + w * qx); Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    for (int i = 0; i < 3; ++i) o.scale[i] = expf(ls[i]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) o.M[3 * i + j] = Rq[3 * i + j] * o.scale[j];
+    // W = R M  ->  Sc = W W^T
+    float Wm[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            Wm[3 * i + j] = R[3 * i] * o.M[j] + R[3 * i + 1] * o.M[3 + j] + R[3 * i + 2] * o.M[6 + j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+            float s = Wm[3 * i] * Wm[3 * j] + Wm[3 * i + 1] * Wm[3 * j + 1] + Wm[3 * i + 2] * Wm[3 * j + 2];
+            o.Sc[3 * i + j] = s;
+            o.Sc[3 * j + i] = s;
+        }
+
+    const float limx = 1.3f * (0.5f * (float)cam.width) / cam.fx;
+    const float limy = 1.3f * (0.5f * (float)cam.height) / cam.fy;
+    const float zi = 1.0f / z;
+    float xz = x * zi, yz = y * zi;
+    o.clx = o.cly = false;
+    o.lx = o.ly = 0.f;
+    if (xz > limx) { xz = limx; o.clx = true; o.lx = limx; }
+    else if (xz < -limx) { xz = -limx; o.clx = true; o.lx = -limx; }
+    if (yz > limy) { yz = limy; o.cly = true; o.ly = limy; }
+    else if (yz < -limy) { yz = -limy; o.cly = true; o.ly = -limy; }
+    o.J00 = cam.fx * zi;
+    o.J02 = -cam.fx * xz * zi;
+    o.J11 = cam.fy * zi;
+    o.J12 = -cam.fy * yz * zi;
+    // Sigma2 = J Sc J^T with J = [[J00, 0, J02], [0, J11, J12]]
+    const float* S = o.Sc;
+    float T0x = o.J00 * S[0] + o.J02 * S[6], T0y = o.J00 * S[1] + o.J02 * S[7], T0z = o.J00 * S[2] + o.J02 * S[8];
+    float T1y = o.J11 * S[4] + o.J12 * S[7], T1z = o.J11 * S[5] + o.J12 * S[8];
+    o.a = T0x * o.J00 + T0z * o.J02 + cfg.dilation;
+    o.b = T0y * o.J11 + T0z * o.J12;
+    o.c = T1y * o.J11 + T1z * o.J12 + cfg.dilation;
+    const float det = o.a * o.c - o.b * o.b;
+    if (!(det > 0.f)) return;
+    const float di = 1.0f / det;
+    o.ca = o.c * di;
+    o.cb = -o.b * di;
+    o.cc = o.a * di;
+    const float mid = 0.5f * (o.a + o.c);
+    const float lmax = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+    const float r = ceilf(3.0f * sqrtf(lmax));
+    o.radius = (int)fminf(r, 1073741824.0f);
+    o.u = cam.fx * x * zi + cam.cx;
+    o.v = cam.fy * y * zi + cam.cy;
+    o.op = 1.0f / (1.0f + expf(-ologit));
+    o.visible = true;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, gs_gaussians g,
+                                                 void* out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    resolve_pose(cam);
+    const Grid grid = make_grid(cam);
+    float mu[3], ls[3], q[4];
+    for (int i = 0; i < 3; ++i) { mu[i] = __ldg(g.means + 3 * k + i); ls[i] = __ldg(g.log_scales + 3 * k + i); }
+    for (int i = 0; i < 4; ++i) q[i] = __ldg(g.quats + 4 * k + i);
+    const float ol = __ldg(g.opacity_logit + k);
+    const bool masked = g.mask && __ldg(g.mask + k);
+    Proj o;
+    if (!masked) project_core(cam, cfg, mu, ls, q, ol, o);
+    else { o.visible = false; o.radius = 0; }
+    float cr = __ldg(g.rgb + 3 * k), cg = __ldg(g.rgb + 3 * k + 1), cb = __ldg(g.rgb + 3 * k + 2);
+    int touched = 0;
+    if (o.visible) {
+        int x0, x1, y0, y1;
+        touched = tile_rect(grid, o.u, o.v, o.radius, x0, x1, y0, y1);
+    } else {
+        o.u = o.v = o.ca = o.cb = o.cc = o.op = 0.f;
+        o.p[2] = 0.f;
+        o.radius = 0;
+    }
+    if (DT == GS_F32) {
+        float4* dst = reinterpret_cast<float4*>(out) + 3 * k;
+        dst[0] = make_float4(o.u, o.v, o.ca, o.cb);
+        dst[1] = make_float4(o.cc, o.op, o.p[2], __int_as_float(o.radius));
+        dst[2] = make_float4(cr, cg, cb, __uint_as_float((uint32_t)touched));
+    } else {
+        uint4* dst = reinterpret_cast<uint4*>(out) + 2 * k;
+        dst[0] = make_uint4(__float_as_uint(o.u), __float_as_uint(o.v), __float_as_uint(o.p[2]),
+                            (uint32_t)o.radius);
+        uint32_t t16 = (uint32_t)min(touched, 65535);
+        dst[1] = make_uint4((uint32_t)f2h(o.ca, DT) | ((uint32_t)f2h(o.cb, DT) << 16),
+                            (uint32_t)f2h(o.cc, DT) | ((uint32_t)f2h(o.op, DT) << 16),
+                            (uint32_t)f2h(cr, DT) | ((uint32_t)f2h(cg, DT) << 16),
+                            (uint32_t)f2h(cb, DT) | (t16 << 16));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward projection (Sec. 2.2, Step 5)
+// ---------------------------------------------------------------------------
+
+#define PB_THREADS 256
+
+template <bool WANT_GRADS, bool WANT_POSE, bool WANT_SCORE>
+__global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_config cfg,
+                                                            gs_gaussians g, const float* __restrict__ grad2d,
+                                                            gs_grads grads, float* __restrict__ score,
+                                                            double* __restrict__ pose_part) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float pose[6] = {0, 0, 0, 0, 0, 0};
+    resolve_pose(cam);
+    if (k < g.n) {
+        float mu[3], ls[3], q[4];
+        for (int i = 0; i < 3; ++i) { mu[i] = __ldg(g.means + 3 * k + i); ls[i] = __ldg(g.log_scales + 3 * k + i); }
+        for (int i = 0; i < 4; ++i) q[i] = __ldg(g.quats + 4 * k + i);
+        const float ol = __ldg(g.opacity_logit + k);
+        const bool masked = g.mask && __ldg(g.mask + k);
+        Proj o;
+        o.visible = false;
+        if (!masked) project_core(cam, cfg, mu, ls, q, ol, o);
+        float gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gol = 0.f, grgb[3] = {0, 0, 0};
+        float t_mu = 0.f, t_sig = 0.f;
+        const float4* g4 = reinterpret_cast<const float4*>(grad2d) + 3 * k;
+        if (o.visible) {
+            const float4 ga = __ldg(g4), gb = __ldg(g4 + 1), gc = __ldg(g4 + 2);
+            const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, gop = gb.y, gd = gb.z;
+            grgb[0] = gc.x; grgb[1] = gc.y; grgb[2] = gc.z;
+            const float x = o.p[0], y = o.p[1], z = o.p[2];
+            const float fx = cam.fx, fy = cam.fy;
+            // conic Q = S2^{-1}: G2 = -Q Gq Q with Gq = [[gA, gB/2], [gB/2, gC]]
+            const float Q00 = o.ca, Q01 = o.cb, Q11 = o.cc;
+            const float hB = 0.5f * gB;
+            const float M00 = Q00 * gA + Q01 * hB, M01 = Q00 * hB + Q01 * gC;
+            const float M10 = Q01 * gA + Q11 * hB, M11 = Q01 * hB + Q11 * gC;
+            const float G00 = -(M00 * Q00 + M01 * Q01);
+            const float G01 = -(M00 * Q01 + M01 * Q11);
+            const float G11 = -(M10 * Q01 + M11 * Q11);
+            // dL/dSc = J^T G2 J (J rows: (J00, 0, J02), (0, J11, J12))
+            const float J00 = o.J00, J02 = o.J02, J11 = o.J11, J12 = o.J12;
+            float Gc[9];
+            {
+                // columns of J: c0 = (J00, 0), c1 = (0, J11), c2 = (J02, J12)
+                const float c0x = J00, c1y = J11, c2x = J02, c2y = J12;
+                // G2 c_j
+                const float g0x = G00 * c0x;
+                const float g1x = G01 * c1y, g1y = G11 * c1y;
+                const float g2x = G00 * c2x + G01 * c2y, g2y = G01 * c2x + G11 * c2y;
+                Gc[0] = c0x * g0x;
+                Gc[1] = c0x * g1x;
+                Gc[2] = c0x * g2x;
+                Gc[4] = c1y * g1y;
+                Gc[5] = c1y * g2y;
+                Gc[8] = c2x * g2x + c2y * g2y;
+                Gc[3] = Gc[1]; Gc[6] = Gc[2]; Gc[7] = Gc[5];
+            }
+            // dL/dJ = 2 G2 J Sc ; only entries (0,0), (0,2), (1,1), (1,2) matter
+            const float* S = o.Sc;
+            // J Sc rows
+            const float JS0x = J00 * S[0] + J02 * S[6], JS0y = J00 * S[1] + J02 * S[7], JS0z = J00 * S[2] + J02 * S[8];
+            const float JS1x = J11 * S[3] + J12 * S[6], JS1y = J11 * S[4] + J12 * S[7], JS1z = J11 * S[5] + J12 * S[8];
+            const float GJ00 = 2.f * (G00 * JS0x + G01 * JS1x);
+            const float GJ02 = 2.f * (G00 * JS0z + G01 * JS1z);
+            const float GJ11 = 2.f * (G01 * JS0y + G11 * JS1y);
+            const float GJ12 = 2.f * (G01 * JS0z + G11 * JS1z);
+            const float zi = 1.f / z, zi2 = zi * zi, zi3 = zi2 * zi;
+            float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
+            gp2 += GJ00 * (-fx * zi2) + GJ11 * (-fy * zi2);
+            if (o.clx) gp2 += GJ02 * (fx * o.lx * zi2);
+            else { gp0 += GJ02 * (-fx * zi2); gp2 += GJ02 * (2.f * fx * x * zi3); }
+            if (o.cly) gp2 += GJ12 * (fy * o.ly * zi2);
+            else { gp1 += GJ12 * (-fy * zi2); gp2 += GJ12 * (2.f * fy * y * zi3); }
+            gp0 += gu * fx * zi;
+            gp1 += gv * fy * zi;
+            gp2 += -(gu * fx * x + gv * fy * y) * zi2 + gd;
+            const float* R = cam.R;
+            gmu[0] = R[0] * gp0 + R[3] * gp1 + R[6] * gp2;
+            gmu[1] = R[1] * gp0 + R[4] * gp1 + R[7] * gp2;
+            gmu[2] = R[2] * gp0 + R[5] * gp1 + R[8] * gp2;
+            // GS = R^T Gc R
+            float tmp[9], GS[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    tmp[3 * i + j] = R[i] * Gc[j] + R[3 + i] * Gc[3 + j] + R[6 + i] * Gc[6 + j];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    GS[3 * i + j] = tmp[3 * i] * R[j] + tmp[3 * i + 1] * R[3 + j] + tmp[3 * i + 2] * R[6 + j];
+            if (WANT_SCORE) {
+                t_mu = sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]);
+                float fr = 0.f;
+                for (int i = 0; i < 9; ++i) fr += GS[i] * GS[i];
+                t_sig = sqrtf(fr);
+            }
+            if (WANT_GRADS) {
+                // Sigma = M M^T: dL/dM = 2 GS M
+                float GM[9];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        GM[3 * i + j] = 2.f * (GS[3 * i] * o.M[j] + GS[3 * i + 1] * o.M[3 + j] + GS[3 * i + 2] * o.M[6 + j]);
+                float GR[9];
+                for (int j = 0; j < 3; ++j) {
+                    gls[j] = GM[j] * o.M[j] + GM[3 + j] * o.M[3 + j] + GM[6 + j] * o.M[6 + j];
+                    for (int i = 0; i < 3; ++i) GR[3 * i + j] = GM[3 * i + j] * o.scale[j];
+                }
+                const float w = o.qn[0], qx = o.qn[1], qy = o.qn[2], qz = o.qn[3];
+                float gqn[4];
+                gqn[0] = 2.f * (-qz * GR[1] + qy * GR[2] + qz * GR[3] - qx * GR[5] - qy * GR[6] + qx * GR[7]);
+                gqn[1] = 2.f * (qy * GR[1] + qz * GR[2] + qy * GR[3] - 2.f * qx * GR[4] - w * GR[5] + qz * GR[6] + w * GR[7] - 2.f * qx * GR[8]);
+                gqn[2] = 2.f * (-2.f * qy * GR[0] + qx * GR[1] + w * GR[2] + qx * GR[3] + qz * GR[5] - w * GR[6] + qz * GR[7] - 2.f * qy * GR[8]);
+                gqn[3] = 2.f * (-2.f * qz * GR[0] - w * GR[1] + qx * GR[2] + w * GR[3] - 2.f * qz * GR[4] + qy * GR[5] + qx * GR[6] + qy * GR[7]);
+                const float dq = o.qn[0] * gqn[0] + o.qn[1] * gqn[1] + o.qn[2] * gqn[2] + o.qn[3] * gqn[3];
+                for (int i = 0; i < 4; ++i) gq[i] = (gqn[i] - o.qn[i] * dq) * o.qinv;
+                gol = gop * o.op * (1.f - o.op);
+            }
+            if (WANT_POSE) {
+                pose[0] = gp0; pose[1] = gp1; pose[2] = gp2;
+                // p x gp
+                pose[3] = y * gp2 - z * gp1;
+                pose[4] = z * gp0 - x * gp2;
+                pose[5] = x * gp1 - y * gp0;
+                // <Gc, [e_i]x S - S [e_i]x> for the symmetric Gc and S
+                // [e_x]x S - S [e_x]x etc. written out entrywise
+                const float* Sm = o.Sc;
+                // D = E S - S E;  sum_ij Gc_ij D_ij
+                for (int e = 0; e < 3; ++e) {
+                    float E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                    if (e == 0) { E[5] = -1.f; E[7] = 1.f; }
+                    if (e == 1) { E[2] = 1.f; E[6] = -1.f; }
+                    if (e == 2) { E[1] = -1.f; E[3] = 1.f; }
+                    float s = 0.f;
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            float es = E[3 * i] * Sm[j] + E[3 * i + 1] * Sm[3 + j] + E[3 * i + 2] * Sm[6 + j];
+                            float se = Sm[3 * i] * E[j] + Sm[3 * i + 1] * E[3 + j] + Sm[3 * i + 2] * E[6 + j];
+                            s += Gc[3 * i + j] * (es - se);
+                        }
+                    pose[3 + e] += s;
+                }
+            }
+        } else if (!masked && WANT_GRADS) {
+            // rgb gradient is independent of visibility only through grad2d,
+            // which is zero for culled Gaussians; keep zeros.
+        }
+        if (WANT_GRADS) {
+            if (grads.means) for (int i = 0; i < 3; ++i) grads.means[3 * k + i] = gmu[i];
+            if (grads.log_scales) for (int i = 0; i < 3; ++i) grads.log_scales[3 * k + i] = gls[i];
+            if (grads.quats) for (int i = 0; i < 4; ++i) grads.quats[4 * k + i] = gq[i];
+            if (grads.opacity_logit) grads.opacity_logit[k] = gol;
+            if (grads.rgb) for (int i = 0; i < 3; ++i) grads.rgb[3 * k + i] = o.visible ? grgb[i] : 0.f;
+        }
+        if (WANT_SCORE) {
+            score[2 * k] = t_mu;
+            score[2 * k + 1] = t_sig;
+        }
+    }
+    if (WANT_POSE) {
+        // warp sums in float32, then the 8 warp sums of the block in float64
+        __shared__ double ws[PB_THREADS / 32][6];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            float v = warp_sum(pose[i]);
+            if (lane == 0) ws[wid][i] = (double)v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double s = 0.0;
+            for (int w = 0; w < PB_THREADS / 32; ++w) s += ws[w][threadIdx.x];
+            pose_part[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+        }
+    }
+}
+
+// Combines the per-block float64 pose partials with Neumaier's compensated
+// summation: each thread sums a strided subset, then the threads' (sum,
+// compensation) pairs are merged in a fixed tree, so the result does not
+// depend on scheduling.
+__global__ void __launch_bounds__(256) k_pose_final(const double* __restrict__ part, int nblk,
+                                                    double* __restrict__ out) {
+    __shared__ double ss[256], sc[256];
+    for (int comp = 0; comp < 6; ++comp) {
+        double s = 0.0, c = 0.0;
+        for (int b = threadIdx.x; b < nblk; b += 256) {
+            const double v = part[(size_t)b * 6 + comp];
+            const double t = s + v;
+            if (fabs(s) >= fabs(v)) c += (s - t) + v;
+            else c += (v - t) + s;
+            s = t;
+        }
+        ss[threadIdx.x] = s;
+        sc[threadIdx.x] = c;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                const double a = ss[threadIdx.x], b = ss[threadIdx.x + o];
+                const double t = a + b;
+                const double e = (fabs(a) >= fabs(b)) ? (a - t) + b : (b - t) + a;
+                ss[threadIdx.x] = t;
+                sc[threadIdx.x] += sc[threadIdx.x + o] + e;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[comp] = ss[0] + sc[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+static gs_status check_camera(const gs_camera* cam) {
+    if (!cam) return set_error(GS_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width <= 0 || cam->height <= 0 || cam->sx < 1 || cam->sy < 1)
+        return set_error(GS_ERR_INVALID_ARG, "bad camera size %d x %d or stride %d,%d", cam->width,
+                         cam->height, cam->sx, cam->sy);
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return set_error(GS_ERR_INVALID_ARG, "focal length must be > 0");
+    if (cam->width > (1 << 20) || cam->height > (1 << 20))
+        return set_error(GS_ERR_INVALID_ARG, "image larger than 2^20 pixels per side");
+    return GS_OK;
+}
+
+static gs_status check_gaussians(const gs_gaussians* g) {
+    if (!g) return set_error(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0 || g->n > (int64_t)0xFFFFFFF0LL) return set_error(GS_ERR_INVALID_ARG, "bad Gaussian count");
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->rgb))
+        return set_error(GS_ERR_INVALID_ARG, "a Gaussian parameter array is NULL");
+    return GS_OK;
+}
+
+extern "C" gs_status gs_project(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                                int rec_dtype, void* splats, gs_stream stream) {
+    if (!cfg) return set_error(GS_ERR_INVALID_ARG, "config is NULL");
+    gs_status s;
+    if ((s = check_camera(cam)) != GS_OK) return s;
+    if ((s = check_gaussians(g)) != GS_OK) return s;
+    if (rec_dtype != GS_F32 && rec_dtype != GS_BF16 && rec_dtype != GS_F16)
+        return set_error(GS_ERR_INVALID_ARG, "bad record dtype %d", rec_dtype);
+    if (g->n == 0) return GS_OK;
+    if (!splats || ((uintptr_t)splats & 15)) return set_error(GS_ERR_INVALID_ARG, "splats NULL or not 16-byte aligned");
+    const int th = 256;
+    const unsigned blocks = (unsigned)((g->n + th - 1) / th);
+    if (rec_dtype == GS_F32) k_project<GS_F32><<<blocks, th, 0, (cudaStream_t)stream>>>(*cam, *cfg, *g, splats);
+    else if (rec_dtype == GS_BF16) k_project<GS_BF16><<<blocks, th, 0, (cudaStream_t)stream>>>(*cam, *cfg, *g, splats);
+    else k_project<GS_F16><<<blocks, th, 0, (cudaStream_t)stream>>>(*cam, *cfg, *g, splats);
+    return check_launch("k_project");
+}
+
+size_t gs_project_bwd_ws(int64_t n) {
+    const size_t nblk = (size_t)((n + PB_THREADS - 1) / PB_THREADS);
+    return ((nblk * 6 * sizeof(double)) + 255) & ~(size_t)255;
+}
+
+extern "C" gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                                    const float* grad2d, gs_grads* grads, double* pose_grad6,
+                                    float* score_terms, void* workspace, size_t* workspace_bytes,
+                                    gs_stream stream) {
+    if (!cfg || !workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "config or workspace_bytes is NULL");
+    gs_status s;
+    if ((s = check_camera(cam)) != GS_OK) return s;
+    if ((s = check_gaussians(g)) != GS_OK) return s;
+    const size_t need = gs_project_bwd_ws(g->n);
+    if (!workspace) { *workspace_bytes = need; return GS_OK; }
+    if (*workspace_bytes < need) return set_error(GS_ERR_WORKSPACE, "workspace %zu < %zu bytes", *workspace_bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool want_grads = grads && (grads->means || grads->log_scales || grads->quats ||
+                                      grads->opacity_logit || grads->rgb);
+    const bool want_pose = pose_grad6 != nullptr;
+    const bool want_score = score_terms != nullptr;
+    if (g->n == 0) {
+        if (want_pose && cudaMemsetAsync(pose_grad6, 0, 6 * sizeof(double), st) != cudaSuccess)
+            return set_error(GS_ERR_CUDA, "memset pose");
+        return GS_OK;
+    }
+    if (!grad2d) return set_error(GS_ERR_INVALID_ARG, "grad2d is NULL");
+    gs_grads gg = grads ? *grads : gs_grads{nullptr, nullptr, nullptr, nullptr, nullptr};
+    const unsigned nblk = (unsigned)((g->n + PB_THREADS - 1) / PB_THREADS);
+    double* part = (double*)workspace;
+#define GS_PB_LAUNCH(A, B, C_) \
+    k_project_bwd<A, B, C_><<<nblk, PB_THREADS, 0, st>>>(*cam, *cfg, *g, grad2d, gg, score_terms, part)
+    if (want_grads) {
+        if (want_pose) { if (want_score) GS_PB_LAUNCH(true, true, true); else GS_PB_LAUNCH(true, true, false); }
+        else { if (want_score) GS_PB_LAUNCH(true, false, true); else GS_PB_LAUNCH(true, false, false); }
+    } else {
+        if (want_pose) { if (want_score) GS_PB_LAUNCH(false, true, true); else GS_PB_LAUNCH(false, true, false); }
+        else { if (want_score) GS_PB_LAUNCH(false, false, true); else return GS_OK; }
+    }
+#undef GS_PB_LAUNCH
+    if ((s = check_launch("k_project_bwd")) != GS_OK) return s;
+    if (want_pose) {
+        k_pose_final<<<1, 256, 0, st>>>(part, (int)nblk, pose_grad6);
+        if ((s = check_launch("k_pose_final")) != GS_OK) return s;
+    }
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pose step: Adam on xi, then T <- exp(xi^) T
+// ---------------------------------------------------------------------------
+__global__ void k_pose_update(float* __restrict__ pose, const double* __restrict__ grad, float* __restrict__ adam,
+                              float lr_t, float lr_r, float b1, float b2, float eps) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const float step = adam[12] + 1.f;
+    adam[12] = step;
+    const float c1 = 1.f - powf(b1, step), c2 = 1.f - powf(b2, step);
+    float xi[6];
+    for (int i = 0; i < 6; ++i) {
+        const float g = (float)grad[i];
+        const float m = b1 * adam[i] + (1.f - b1) * g;
+        const float v = b2 * adam[6 + i] + (1.f - b2) * g * g;
+        adam[i] = m;
+        adam[6 + i] = v;
+        xi[i] = -(i < 3 ? lr_t : lr_r) * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+    // exp of (rho, phi): R_d = Rodrigues(phi), V = I + (1-cos)/th^2 K + (th-sin)/th^3 K^2
+    const float px = xi[3], py = xi[4], pz = xi[5];
+    const float th2 = px * px + py * py + pz * pz, th = sqrtf(th2);
+    float A, B, Cc;
+    if (th < 1e-4f) {
+        A = 1.f - th2 / 6.f;
+        B = 0.5f - th2 / 24.f;
+        Cc = 1.f / 6.f - th2 / 120.f;
+    } else {
+        A = sinf(th) / th;
+        B = (1.f - cosf(th)) / th2;
+        Cc = (th - sinf(th)) / (th2 * th);
+    }
+    const float K[9] = {0.f, -pz, py, pz, 0.f, -px, -py, px, 0.f};
+    float K2[9], Rd[9], V[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+    for (int i = 0; i < 9; ++i) {
+        const float I = (i % 4 == 0) ? 1.f : 0.f;
+        Rd[i] = I + A * K[i] + B * K2[i];
+        V[i] = I + B * K[i] + Cc * K2[i];
+    }
+    float R[9], t[3], Rn[9], tn[3];
+    for (int i = 0; i < 9; ++i) R[i] = pose[i];
+    for (int i = 0; i < 3; ++i) t[i] = pose[9 + i];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Rn[3 * i + j] = Rd[3 * i] * R[j] + Rd[3 * i + 1] * R[3 + j] + Rd[3 * i + 2] * R[6 + j];
+        tn[i] = Rd[3 * i] * t[0] + Rd[3 * i + 1] * t[1] + Rd[3 * i + 2] * t[2] +
+                V[3 * i] * xi[0] + V[3 * i + 1] * xi[1] + V[3 * i + 2] * xi[2];
+    }
+    for (int i = 0; i < 9; ++i) pose[i] = Rn[i];
+    for (int i = 0; i < 3; ++i) pose[9 + i] = tn[i];
+}
+
+extern "C" gs_status gs_pose_update(float* pose, const double* pose_grad6, float* adam, float lr_trans, float lr_rot,
+                                    float beta1, float beta2, float eps, gs_stream stream) {
+    if (!pose || !pose_grad6 || !adam) return set_error(GS_ERR_INVALID_ARG, "NULL pointer");
+    if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return set_error(GS_ERR_INVALID_ARG, "bad Adam constants");
+    k_pose_update<<<1, 32, 0, (cudaStream_t)stream>>>(pose, pose_grad6, adam, lr_trans, lr_rot, beta1, beta2, eps);
+    return check_launch("k_pose_update");
+}

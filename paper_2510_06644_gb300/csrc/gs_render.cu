@@ -1,0 +1,386 @@
+// A-5 forward compositing (Sec. 2.1, Step 3: Eq. 2, Eq. 3), A-6 loss
+// (Sec. 4.1, Eq. 6) and A-7 backward compositing (Sec. 2.2, Step 4: Eq. 4,
+// Eq. 5) on sm_103a.
+//
+// One CTA of 256 threads per 16x16 tile, one pixel per thread.  The 8 warps
+// cover 8x4 pixel blocks (not rows), so a small Gaussian's integer box misses
+// most warps and the whole warp skips it with one uniform test.  The tile's
+// sorted list is staged through shared memory in batches of 256 records (one
+// 48-byte gather per thread); every pixel then walks the batch from shared
+// memory.  The forward keeps T_final and the last blended list position per
+// pixel; the backward walks the same list in reverse from there, recovering
+// T_k by division (Eq. 5), and merges the per-pixel gradients of each
+// Gaussian first across the warp (shuffles), then across the tile (shared
+// atomics), then with one global atomic per (Gaussian, tile, field).
+#include "gs_internal.cuh"
+
+namespace gs {
+
+#define R_THREADS 256
+#define R_BATCH 256
+
+struct StagedSplat {
+    float4 a;   // x, y, conic_a, conic_b
+    float4 b;   // conic_c, opacity, depth, unused
+    float4 c;   // r, g, b, unused
+    int4 box;   // full-resolution integer box x0, x1, y0, y1
+};
+
+struct PixelMap {
+    int i, j;        // sampled pixel
+    bool inside;
+    int px, py;      // full-resolution pixel
+    int wx0, wx1, wy0, wy1;  // full-resolution extent of this warp's 8x4 block
+};
+
+__device__ __forceinline__ PixelMap map_pixel(const Grid& g, int tile) {
+    PixelMap m;
+    const int tx = tile % g.TX, ty = tile / g.TX;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int bx = (w & 1) * 8, by = (w >> 1) * 4;
+    m.i = tx * GS_TILE + bx + (lane & 7);
+    m.j = ty * GS_TILE + by + (lane >> 3);
+    m.inside = m.i < g.Ws && m.j < g.Hs;
+    m.px = m.i * g.sx;
+    m.py = m.j * g.sy;
+    m.wx0 = (tx * GS_TILE + bx) * g.sx;
+    m.wx1 = (tx * GS_TILE + bx + 7) * g.sx;
+    m.wy0 = (ty * GS_TILE + by) * g.sy;
+    m.wy1 = (ty * GS_TILE + by + 3) * g.sy;
+    return m;
+}
+
+template <int DT>
+__device__ __forceinline__ void stage(const void* splats, uint32_t gid, StagedSplat& s) {
+    const Splat v = load_splat<DT>(splats, gid);
+    s.a = make_float4(v.x, v.y, v.ca, v.cb);
+    s.b = make_float4(v.cc, v.op, v.depth, 0.f);
+    s.c = make_float4(v.r, v.g, v.b, 0.f);
+    const int xi = pix_floor(v.x), yi = pix_floor(v.y), r = v.radius;
+    s.box = make_int4(xi - r, xi + r, yi - r, yi + r);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g, const void* __restrict__ splats,
+                                                          const uint32_t* __restrict__ vals,
+                                                          const uint32_t* __restrict__ ranges,
+                                                          float* __restrict__ out_rgb, float* __restrict__ out_depth,
+                                                          float* __restrict__ out_t, uint32_t* __restrict__ out_last) {
+    __shared__ StagedSplat sp[R_BATCH];
+    const int tile = blockIdx.x;
+    const PixelMap m = map_pixel(g, tile);
+    const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+    const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    uint32_t last = 0;
+    bool done = !m.inside;
+    for (uint32_t b = start; b < end; b += R_BATCH) {
+        if (__syncthreads_count(done) == R_THREADS) break;
+        const int n_in = (int)min((uint32_t)R_BATCH, end - b);
+        if ((int)threadIdx.x < n_in) stage<DT>(splats, __ldg(vals + b + threadIdx.x), sp[threadIdx.x]);
+        __syncthreads();
+        if (!__all_sync(0xffffffffu, done)) {
+            for (int e = 0; e < n_in; ++e) {
+                const int4 box = sp[e].box;
+                if (box.y < m.wx0 || box.x > m.wx1 || box.w < m.wy0 || box.z > m.wy1) continue;
+                if (done || m.px < box.x || m.px > box.y || m.py < box.z || m.py > box.w) continue;
+                const float4 A = sp[e].a;
+                const float dx = pxc - A.x, dy = pyc - A.y;
+                const float4 B = sp[e].b;
+                const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
+                if (power > 0.f) continue;
+                const float alpha = fminf(cfg.alpha_max, B.y * __expf(power));
+                if (alpha < cfg.alpha_min) continue;
+                const float Tn = T * (1.f - alpha);
+                if (Tn < cfg.t_eps) { done = true; continue; }
+                const float w = alpha * T;
+                const float4 Cc = sp[e].c;
+                C0 += w * Cc.x; C1 += w * Cc.y; C2 += w * Cc.z;
+                D += w * B.z;
+                T = Tn;
+                last = b - start + (uint32_t)e + 1u;
+            }
+        }
+        __syncthreads();
+    }
+    if (m.inside) {
+        const size_t P = (size_t)g.Ws * g.Hs;
+        const size_t pix = (size_t)m.j * g.Ws + m.i;
+        out_rgb[pix] = C0 + T * cfg.bg[0];
+        out_rgb[P + pix] = C1 + T * cfg.bg[1];
+        out_rgb[2 * P + pix] = C2 + T * cfg.bg[2];
+        out_depth[pix] = D;
+        out_t[pix] = T;
+        out_last[pix] = last;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Loss (Eq. 6) with L1 residuals
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_loss_l1(gs_config cfg, int64_t P, const float* __restrict__ rgb,
+                                                 const float* __restrict__ depth, const float* __restrict__ trgb,
+                                                 const float* __restrict__ tdepth, float* __restrict__ d_rgb,
+                                                 float* __restrict__ d_depth, double* __restrict__ loss) {
+    __shared__ float s_w[8];
+    const float inv3 = 1.f / (3.f * (float)P), inv1 = 1.f / (float)P;
+    float acc = 0.f;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float r = rgb[c * P + q] - trgb[c * P + q];
+            acc += cfg.w_rgb * fabsf(r) * inv3;
+            d_rgb[c * P + q] = cfg.w_rgb * (r > 0.f ? inv3 : (r < 0.f ? -inv3 : 0.f));
+        }
+        const float td = tdepth[q];
+        float gd = 0.f;
+        if (td != 0.f) {
+            const float r = depth[q] - td;
+            acc += cfg.w_depth * fabsf(r) * inv1;
+            gd = cfg.w_depth * (r > 0.f ? inv1 : (r < 0.f ? -inv1 : 0.f));
+        }
+        d_depth[q] = gd;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)s_w[w];
+        atomicAdd(loss, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward compositing
+// ---------------------------------------------------------------------------
+// Accumulated fields per staged Gaussian, in grad2d order.
+#define NF 12
+
+template <int DT, int MODE>
+__global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g, const void* __restrict__ splats,
+                                                          const uint32_t* __restrict__ vals,
+                                                          const uint32_t* __restrict__ ranges,
+                                                          const float* __restrict__ t_final,
+                                                          const uint32_t* __restrict__ last_idx,
+                                                          const float* __restrict__ d_rgb,
+                                                          const float* __restrict__ d_depth,
+                                                          float* __restrict__ grad2d) {
+    __shared__ StagedSplat sp[R_BATCH];
+    __shared__ uint32_t sid[R_BATCH];
+    __shared__ float acc[R_BATCH][NF];
+    const int tile = blockIdx.x;
+    const PixelMap m = map_pixel(g, tile);
+    const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+    const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
+    const int lane = threadIdx.x & 31;
+    float T = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f;
+    uint32_t last = 0;
+    if (m.inside) {
+        const size_t P = (size_t)g.Ws * g.Hs;
+        const size_t pix = (size_t)m.j * g.Ws + m.i;
+        T = t_final[pix];
+        last = last_idx[pix];
+        gC0 = d_rgb[pix];
+        gC1 = d_rgb[P + pix];
+        gC2 = d_rgb[2 * P + pix];
+        gD = d_depth[pix];
+    }
+    // normalised suffix sums (background enters with weight T_final)
+    float A0 = cfg.bg[0], A1 = cfg.bg[1], A2 = cfg.bg[2], AD = 0.f;
+    // block maximum of last -> the part of the list any pixel blended
+    __shared__ uint32_t s_max;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, last);
+    __syncthreads();
+    // a last_idx beyond the tile's list (inconsistent inputs) is clamped
+    const uint32_t end_eff = start + min(s_max, end - start);
+    for (uint32_t hi = end_eff; hi > start;) {
+        const uint32_t lo = hi - start > R_BATCH ? hi - R_BATCH : start;
+        const int n_in = (int)(hi - lo);
+        if ((int)threadIdx.x < n_in) {
+            const uint32_t gid = __ldg(vals + lo + threadIdx.x);
+            sid[threadIdx.x] = gid;
+            stage<DT>(splats, gid, sp[threadIdx.x]);
+        }
+        for (int q = threadIdx.x; q < R_BATCH * NF; q += R_THREADS) (&acc[0][0])[q] = 0.f;
+        __syncthreads();
+        const uint32_t base_pos = lo - start;
+        for (int e = n_in - 1; e >= 0; --e) {
+            const int4 box = sp[e].box;
+            if (box.y < m.wx0 || box.x > m.wx1 || box.w < m.wy0 || box.z > m.wy1) continue;
+            bool contrib = (base_pos + (uint32_t)e) < last && m.px >= box.x && m.px <= box.y && m.py >= box.z &&
+                           m.py <= box.w;
+            float f[NF];
+#pragma unroll
+            for (int q = 0; q < NF; ++q) f[q] = 0.f;
+            if (contrib) {
+                const float4 A = sp[e].a;
+                const float4 B = sp[e].b;
+                const float dx = pxc - A.x, dy = pyc - A.y;
+                const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
+                const float G = __expf(power);
+                const float raw = B.y * G;
+                const float alpha = fminf(cfg.alpha_max, raw);
+                contrib = !(power > 0.f) && !(alpha < cfg.alpha_min);
+                if (contrib) {
+                    T = T / (1.f - alpha);
+                    const float w = alpha * T;
+                    const float4 Cc = sp[e].c;
+                    const float dLda = T * ((Cc.x - A0) * gC0 + (Cc.y - A1) * gC1 + (Cc.z - A2) * gC2 +
+                                            (B.z - AD) * gD);
+                    A0 = alpha * Cc.x + (1.f - alpha) * A0;
+                    A1 = alpha * Cc.y + (1.f - alpha) * A1;
+                    A2 = alpha * Cc.z + (1.f - alpha) * A2;
+                    AD = alpha * B.z + (1.f - alpha) * AD;
+                    f[6] = w * gD;
+                    if (MODE == GS_MAP) {
+                        f[8] = w * gC0;
+                        f[9] = w * gC1;
+                        f[10] = w * gC2;
+                    }
+                    if (!(raw > cfg.alpha_max)) {
+                        if (MODE == GS_MAP) f[5] = G * dLda;
+                        const float dp = alpha * dLda;
+                        f[2] = -0.5f * dx * dx * dp;
+                        f[3] = -dx * dy * dp;
+                        f[4] = -0.5f * dy * dy * dp;
+                        f[0] = (A.z * dx + A.w * dy) * dp;
+                        f[1] = (A.w * dx + B.x * dy) * dp;
+                    }
+                }
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, contrib);
+            if (ball == 0u) continue;
+            if (__popc(ball) == 1) {
+                if (contrib) {
+#pragma unroll
+                    for (int q = 0; q < NF; ++q)
+                        if (q != 7 && q != 11 && (MODE == GS_MAP || (q != 5 && q < 8))) atomicAdd(&acc[e][q], f[q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NF; ++q) {
+                    if (q == 7 || q == 11 || (MODE != GS_MAP && (q == 5 || q >= 8))) continue;
+                    const float v = warp_sum(f[q]);
+                    if (lane == 0) atomicAdd(&acc[e][q], v);
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < n_in * NF; q += R_THREADS) {
+            const float v = (&acc[0][0])[q];
+            if (v != 0.f) atomicAdd(grad2d + (size_t)sid[q / NF] * NF + (q % NF), v);
+        }
+        __syncthreads();
+        hi = lo;
+    }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+static gs_status render_checks(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
+                               int64_t n) {
+    if (!cfg) return set_error(GS_ERR_INVALID_ARG, "config is NULL");
+    if (!cam) return set_error(GS_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width <= 0 || cam->height <= 0 || cam->sx < 1 || cam->sy < 1 || cam->width > (1 << 20) ||
+        cam->height > (1 << 20))
+        return set_error(GS_ERR_INVALID_ARG, "bad camera size or stride");
+    if (rec_dtype != GS_F32 && rec_dtype != GS_BF16 && rec_dtype != GS_F16)
+        return set_error(GS_ERR_INVALID_ARG, "bad record dtype %d", rec_dtype);
+    if (n < 0) return set_error(GS_ERR_INVALID_ARG, "bad Gaussian count");
+    if (n > 0 && (!splats || ((uintptr_t)splats & 15)))
+        return set_error(GS_ERR_INVALID_ARG, "splats NULL or not 16-byte aligned");
+    return GS_OK;
+}
+
+extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
+                                   int64_t n, const uint32_t* vals, const uint32_t* tile_ranges, float* rgb,
+                                   float* depth, float* t_final, uint32_t* last_idx, gs_stream stream) {
+    gs_status s;
+    if ((s = render_checks(cfg, cam, rec_dtype, splats, n)) != GS_OK) return s;
+    if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
+        return set_error(GS_ERR_INVALID_ARG, "an image or range pointer is NULL");
+    const Grid g = make_grid(*cam);
+    const unsigned nt = (unsigned)(g.TX * g.TY);
+    cudaStream_t st = (cudaStream_t)stream;
+    const void* sp = splats;
+    if (rec_dtype == GS_F32)
+        k_render_fwd<GS_F32><<<nt, R_THREADS, 0, st>>>(*cfg, g, sp, vals, tile_ranges, rgb, depth, t_final, last_idx);
+    else if (rec_dtype == GS_BF16)
+        k_render_fwd<GS_BF16><<<nt, R_THREADS, 0, st>>>(*cfg, g, sp, vals, tile_ranges, rgb, depth, t_final, last_idx);
+    else
+        k_render_fwd<GS_F16><<<nt, R_THREADS, 0, st>>>(*cfg, g, sp, vals, tile_ranges, rgb, depth, t_final, last_idx);
+    return check_launch("k_render_fwd");
+}
+
+extern "C" gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, const float* rgb, const float* depth,
+                                const float* target_rgb, const float* target_depth, float* d_rgb, float* d_depth,
+                                double* loss_out, gs_stream stream) {
+    if (!cfg || !cam) return set_error(GS_ERR_INVALID_ARG, "config or camera is NULL");
+    if (cam->width <= 0 || cam->height <= 0 || cam->sx < 1 || cam->sy < 1)
+        return set_error(GS_ERR_INVALID_ARG, "bad camera size or stride");
+    if (!rgb || !depth || !target_rgb || !target_depth || !d_rgb || !d_depth || !loss_out)
+        return set_error(GS_ERR_INVALID_ARG, "a loss pointer is NULL");
+    const Grid g = make_grid(*cam);
+    const int64_t P = (int64_t)g.Ws * g.Hs;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(loss_out, 0, sizeof(double), st) != cudaSuccess) return set_error(GS_ERR_CUDA, "memset loss");
+    const int64_t want = (P + 255) / 256;
+    const int sms = num_sms();
+    const unsigned nb = (unsigned)(want < 4 * sms ? want : 4 * sms);
+    k_loss_l1<<<nb, 256, 0, st>>>(*cfg, P, rgb, depth, target_rgb, target_depth, d_rgb, d_depth, loss_out);
+    return check_launch("k_loss_l1");
+}
+
+size_t gs_project_bwd_ws(int64_t n);
+
+extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* gsn,
+                                   int rec_dtype, const void* splats, const uint32_t* vals,
+                                   const uint32_t* tile_ranges, const float* t_final, const uint32_t* last_idx,
+                                   const float* d_rgb, const float* d_depth, int mode, float* grad2d,
+                                   gs_grads* grads, double* pose_grad6, float* score_terms, void* workspace,
+                                   size_t* workspace_bytes, gs_stream stream) {
+    if (!gsn) return set_error(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    gs_status s;
+    const int64_t n = gsn->n;
+    if ((s = render_checks(cfg, cam, rec_dtype, splats, n)) != GS_OK) return s;
+    if (!workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "workspace_bytes is NULL");
+    if (mode != GS_TRACK && mode != GS_MAP) return set_error(GS_ERR_INVALID_ARG, "bad mode %d", mode);
+    const bool chain = (grads != nullptr) || pose_grad6 || score_terms;
+    const size_t need = chain ? gs_project_bwd_ws(n) : 0;
+    if (!workspace && need > 0) { *workspace_bytes = need; return GS_OK; }
+    if (!workspace) { *workspace_bytes = 0; }
+    else if (*workspace_bytes < need) return set_error(GS_ERR_WORKSPACE, "workspace %zu < %zu", *workspace_bytes, need);
+    if (!tile_ranges || !t_final || !last_idx || !d_rgb || !d_depth || (n > 0 && !grad2d))
+        return set_error(GS_ERR_INVALID_ARG, "an input or grad2d pointer is NULL");
+    if (n > 0 && ((uintptr_t)grad2d & 15)) return set_error(GS_ERR_INVALID_ARG, "grad2d not 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * NF * (size_t)n, st) != cudaSuccess)
+        return set_error(GS_ERR_CUDA, "memset grad2d");
+    const Grid g = make_grid(*cam);
+    const unsigned nt = (unsigned)(g.TX * g.TY);
+#define GS_RB(DT, MD) \
+    k_render_bwd<DT, MD><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, t_final, last_idx, d_rgb, d_depth, grad2d)
+    if (n > 0) {
+        if (mode == GS_MAP) {
+            if (rec_dtype == GS_F32) GS_RB(GS_F32, GS_MAP);
+            else if (rec_dtype == GS_BF16) GS_RB(GS_BF16, GS_MAP);
+            else GS_RB(GS_F16, GS_MAP);
+        } else {
+            if (rec_dtype == GS_F32) GS_RB(GS_F32, GS_TRACK);
+            else if (rec_dtype == GS_BF16) GS_RB(GS_BF16, GS_TRACK);
+            else GS_RB(GS_F16, GS_TRACK);
+        }
+        if ((s = check_launch("k_render_bwd")) != GS_OK) return s;
+    }
+#undef GS_RB
+    if (chain) {
+        size_t wb = *workspace_bytes;
+        return gs_project_bwd(cfg, cam, gsn, grad2d, grads, pose_grad6, score_terms, workspace, &wb, stream);
+    }
+    return GS_OK;
+}

@@ -1,0 +1,397 @@
+"""Python binding of the C ABI in include/gs.h (ctypes; argument marshalling
+only -- every step runs in the sm_103a kernels of libgs_gb300.so).
+
+Functions keep the C names.  Device arrays are torch CUDA tensors; work is
+enqueued on torch's current CUDA stream unless ``stream`` is given.  The
+library must have been built (``__graft_entry__.build()``); importing this
+module without it, or calling it without a CUDA device, raises -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libgs_gb300.so")
+
+GS_OK, GS_ERR_INVALID_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_CAPACITY, \
+    GS_ERR_DEVICE_CHECK, GS_ERR_UNIMPLEMENTED = range(8)
+GS_TRACK, GS_MAP = 0, 1
+GS_F32, GS_BF16, GS_F16 = 0, 1, 2
+GS_IDLE, GS_EXECUTING = 0, 1
+GRAD2D_STRIDE = 12
+SPLAT_WORDS = {GS_F32: 12, GS_BF16: 8, GS_F16: 8}   # 32-bit words per 2D record
+TILE = 16
+
+
+class GsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gs error {code}: {msg}")
+        self.code = code
+
+
+class gs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("sx", C.c_int32), ("sy", C.c_int32), ("pose", C.c_void_p)]
+
+
+class gs_config(C.Structure):
+    _fields_ = [("near_z", C.c_float), ("dilation", C.c_float), ("alpha_min", C.c_float),
+                ("alpha_max", C.c_float), ("t_eps", C.c_float), ("bg", C.c_float * 3),
+                ("lambda_score", C.c_float), ("prune_frac", C.c_float), ("prune_cap", C.c_float),
+                ("change_thr", C.c_float), ("k0", C.c_int32), ("k_max", C.c_int32),
+                ("w_rgb", C.c_float), ("w_depth", C.c_float)]
+
+
+class gs_gaussians(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("rgb", C.c_void_p), ("mask", C.c_void_p),
+                ("n", C.c_int64)]
+
+
+class gs_grads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("rgb", C.c_void_p)]
+
+
+_lib = None
+_P = C.c_void_p
+_SIGS = {
+    "gs_default_config": ([_P], None),
+    "gs_version": ([], C.c_char_p),
+    "gs_project": ([_P, _P, _P, C.c_int, _P, _P], C.c_int),
+    "gs_bin_sort": ([_P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_bin_count": ([_P, C.c_int, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
+    "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_loss_l1": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_render_bwd": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P, _P,
+                       _P, _P], C.c_int),
+    "gs_project_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_prune": ([_P, _P, C.c_int64, _P, C.c_int, _P, C.c_float, C.c_int64, _P, _P, _P, _P, _P],
+                 C.c_int),
+    "gs_change_ratio": ([_P, C.c_int, _P, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
+    "gs_compact": ([_P, C.c_int64, C.c_int32, _P, _P, _P], C.c_int),
+    "gs_downsample": ([C.c_int64, C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int32, C.c_int32,
+                       C.c_int32, _P, _P], C.c_int),
+    "gs_pose_update": ([_P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, _P], C.c_int),
+    "gs_status_poll": ([_P, C.c_int, _P], C.c_int),
+    "gs_status_reset": ([_P], C.c_int),
+    "gs_last_error": ([], C.c_char_p),
+}
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(code, what):
+    if code != GS_OK:
+        raise GsError(code, f"{what}: {lib().gs_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# Structures
+# --------------------------------------------------------------------------
+
+def camera(cam, pose=None) -> gs_camera:
+    """gs_camera from a dict {R, t, fx, fy, cx, cy, W, H, sx, sy}; `pose`
+    (device float32 [12] tensor) makes the kernels read R, t from it."""
+    c = gs_camera()
+    c.pose = _ptr(pose).value if pose is not None else None
+    R = [float(v) for v in torch.as_tensor(cam["R"], dtype=torch.float64).reshape(9).tolist()]
+    t = [float(v) for v in torch.as_tensor(cam["t"], dtype=torch.float64).reshape(3).tolist()]
+    for i in range(9):
+        c.R[i] = R[i]
+    for i in range(3):
+        c.t[i] = t[i]
+    c.fx, c.fy, c.cx, c.cy = (float(cam[k]) for k in ("fx", "fy", "cx", "cy"))
+    c.width, c.height = int(cam["W"]), int(cam["H"])
+    c.sx, c.sy = int(cam.get("sx", 1)), int(cam.get("sy", 1))
+    return c
+
+
+def default_config(**overrides) -> gs_config:
+    c = gs_config()
+    lib().gs_default_config(C.byref(c))
+    for k, v in overrides.items():
+        if k == "bg":
+            for i in range(3):
+                c.bg[i] = float(v[i])
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def grid(cam):
+    """(Ws, Hs, TX, TY) of a camera dict or gs_camera."""
+    if isinstance(cam, gs_camera):
+        W, H, sx, sy = cam.width, cam.height, cam.sx, cam.sy
+    else:
+        W, H, sx, sy = int(cam["W"]), int(cam["H"]), int(cam.get("sx", 1)), int(cam.get("sy", 1))
+    Ws, Hs = -(-W // sx), -(-H // sy)
+    return Ws, Hs, -(-Ws // TILE), -(-Hs // TILE)
+
+
+def gaussians(g, mask=None) -> gs_gaussians:
+    """gs_gaussians over a dict of contiguous float32 CUDA tensors."""
+    s = gs_gaussians()
+    s.means = _ptr(g["means"]).value
+    s.log_scales = _ptr(g["log_scales"]).value
+    s.quats = _ptr(g["quats"]).value
+    s.opacity_logit = _ptr(g["opacity_logit"]).value
+    s.rgb = _ptr(g["rgb"]).value
+    m = mask if mask is not None else g.get("mask")
+    s.mask = _ptr(m).value if m is not None else None
+    s.n = int(g["means"].shape[0])
+    return s
+
+
+def grads_struct(gr) -> gs_grads:
+    s = gs_grads()
+    if gr:
+        for k in ("means", "log_scales", "quats", "opacity_logit", "rgb"):
+            v = gr.get(k)
+            setattr(s, k, _ptr(v).value if v is not None else None)
+    return s
+
+
+def workspace(nbytes, device=None):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+# --------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# --------------------------------------------------------------------------
+
+def gs_project(cfg, cam, g, rec_dtype=GS_F32, splats=None, stream=None):
+    n = int(g["means"].shape[0])
+    if splats is None:
+        dt = torch.float32 if rec_dtype == GS_F32 else torch.int32
+        splats = torch.empty((n, SPLAT_WORDS[rec_dtype]), dtype=dt, device=g["means"].device)
+    gs_g = gaussians(g)
+    _check(lib().gs_project(C.byref(cfg), C.byref(cam), C.byref(gs_g), rec_dtype, _ptr(splats),
+                            _stream(stream)), "gs_project")
+    return splats
+
+
+def gs_bin_sort_workspace(cam, rec_dtype, n, capacity):
+    nb = C.c_size_t(0)
+    _check(lib().gs_bin_sort(C.byref(cam), rec_dtype, None, int(n), int(capacity), None, C.byref(nb),
+                             None, None, None, None, None), "gs_bin_sort(size)")
+    return nb.value
+
+
+def gs_bin_sort(cam, splats, n, capacity, rec_dtype=GS_F32, ws=None, keys=None, vals=None, n_keys=None,
+                ranges=None, stream=None):
+    dev = splats.device
+    _, _, TX, TY = grid(cam)
+    need = gs_bin_sort_workspace(cam, rec_dtype, n, capacity)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    keys = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev) if keys is None else keys
+    vals = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev) if vals is None else vals
+    n_keys = torch.zeros(1, dtype=torch.int64, device=dev) if n_keys is None else n_keys
+    ranges = torch.empty((TX * TY, 2), dtype=torch.int32, device=dev) if ranges is None else ranges
+    nb = C.c_size_t(ws.numel())
+    _check(lib().gs_bin_sort(C.byref(cam), rec_dtype, _ptr(splats), int(n), int(capacity), _ptr(ws),
+                             C.byref(nb), _ptr(keys), _ptr(vals), _ptr(n_keys), _ptr(ranges),
+                             _stream(stream)), "gs_bin_sort")
+    return keys, vals, n_keys, ranges
+
+
+def gs_bin_count(cam, splats, n, rec_dtype=GS_F32, stream=None):
+    nb = C.c_size_t(0)
+    _check(lib().gs_bin_count(C.byref(cam), rec_dtype, None, int(n), None, C.byref(nb), None, None),
+           "gs_bin_count(size)")
+    ws = workspace(nb.value, splats.device)
+    out = torch.zeros(1, dtype=torch.int64, device=splats.device)
+    nb = C.c_size_t(ws.numel())
+    _check(lib().gs_bin_count(C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(ws), C.byref(nb),
+                              _ptr(out), _stream(stream)), "gs_bin_count")
+    return out
+
+
+def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None, stream=None):
+    Ws, Hs, _, _ = grid(cam)
+    dev = splats.device
+    if out is None:
+        out = {"rgb": torch.empty((3, Hs, Ws), device=dev), "depth": torch.empty((Hs, Ws), device=dev),
+               "t_final": torch.empty((Hs, Ws), device=dev),
+               "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=dev)}
+    _check(lib().gs_render_fwd(C.byref(cfg), C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(vals),
+                               _ptr(ranges), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["t_final"]),
+                               _ptr(out["last_idx"]), _stream(stream)), "gs_render_fwd")
+    return out
+
+
+def gs_loss_l1(cfg, cam, rgb, depth, target_rgb, target_depth, out=None, stream=None):
+    if out is None:
+        out = {"d_rgb": torch.empty_like(rgb), "d_depth": torch.empty_like(depth),
+               "loss": torch.zeros(1, dtype=torch.float64, device=rgb.device)}
+    _check(lib().gs_loss_l1(C.byref(cfg), C.byref(cam), _ptr(rgb), _ptr(depth), _ptr(target_rgb),
+                            _ptr(target_depth), _ptr(out["d_rgb"]), _ptr(out["d_depth"]), _ptr(out["loss"]),
+                            _stream(stream)), "gs_loss_l1")
+    return out
+
+
+def gs_project_bwd_workspace(cfg, cam, g):
+    nb = C.c_size_t(0)
+    gs_g = gaussians(g)
+    _check(lib().gs_project_bwd(C.byref(cfg), C.byref(cam), C.byref(gs_g), None, None, None, None, None,
+                                C.byref(nb), None), "gs_project_bwd(size)")
+    return nb.value
+
+
+def gs_render_bwd(cfg, cam, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, mode=GS_MAP,
+                  rec_dtype=GS_F32, grad2d=None, grads=None, pose=None, score=None, ws=None, stream=None):
+    """grads: dict of output tensors (or None); pose: float64 [6] tensor or
+    None; score: float32 [n,2] tensor or None."""
+    n = int(g["means"].shape[0])
+    dev = splats.device
+    grad2d = torch.empty((n, GRAD2D_STRIDE), device=dev) if grad2d is None else grad2d
+    gs_g = gaussians(g)
+    gr = grads_struct(grads) if grads is not None else None
+    chain = grads is not None or pose is not None or score is not None
+    need = gs_project_bwd_workspace(cfg, cam, g) if chain else 0
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    nb = C.c_size_t(ws.numel())
+    _check(lib().gs_render_bwd(C.byref(cfg), C.byref(cam), C.byref(gs_g), rec_dtype, _ptr(splats), _ptr(vals),
+                               _ptr(ranges), _ptr(t_final), _ptr(last_idx), _ptr(d_rgb), _ptr(d_depth), mode,
+                               _ptr(grad2d), C.byref(gr) if gr is not None else None, _ptr(pose),
+                               _ptr(score), _ptr(ws), C.byref(nb), _stream(stream)), "gs_render_bwd")
+    return grad2d
+
+
+def gs_project_bwd(cfg, cam, g, grad2d, grads=None, pose=None, score=None, ws=None, stream=None):
+    need = gs_project_bwd_workspace(cfg, cam, g)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, grad2d.device)
+    gs_g = gaussians(g)
+    gr = grads_struct(grads) if grads is not None else None
+    nb = C.c_size_t(ws.numel())
+    _check(lib().gs_project_bwd(C.byref(cfg), C.byref(cam), C.byref(gs_g), _ptr(grad2d),
+                                C.byref(gr) if gr is not None else None, _ptr(pose), _ptr(score), _ptr(ws),
+                                C.byref(nb), _stream(stream)), "gs_project_bwd")
+
+
+def gs_prune(cfg, score, mask, iter_in_interval, K, change_ratio=0.0, max_select=None, compact_map=None,
+             n_kept=None, ws=None, stream=None):
+    """Returns the next K (host int).  mask is updated in place."""
+    n = int(mask.numel())
+    max_select = n if max_select is None else int(max_select)
+    k = C.c_int(int(K))
+    nb = C.c_size_t(0)
+    _check(lib().gs_prune(C.byref(cfg), None, n, None, int(iter_in_interval), C.byref(k), 0.0, 0, None, None,
+                          None, C.byref(nb), None), "gs_prune(size)")
+    if ws is None or ws.numel() < nb.value:
+        ws = workspace(nb.value, mask.device)
+    nb = C.c_size_t(ws.numel())
+    _check(lib().gs_prune(C.byref(cfg), _ptr(score), n, _ptr(mask), int(iter_in_interval), C.byref(k),
+                          float(change_ratio), max_select, _ptr(compact_map), _ptr(n_kept), _ptr(ws),
+                          C.byref(nb), _stream(stream)), "gs_prune")
+    return k.value
+
+
+def gs_change_ratio(cam, splats_a, splats_b, n, rec_dtype=GS_F32, out=None, stream=None):
+    ws = workspace(256, splats_a.device)
+    out = torch.zeros(1, dtype=torch.float32, device=splats_a.device) if out is None else out
+    nb = C.c_size_t(ws.numel())
+    _check(lib().gs_change_ratio(C.byref(cam), rec_dtype, _ptr(splats_a), _ptr(splats_b), int(n), _ptr(ws),
+                                 C.byref(nb), _ptr(out), _stream(stream)), "gs_change_ratio")
+    return out
+
+
+def gs_compact(src, compact_map, n_kept, stream=None):
+    n = int(src.shape[0])
+    width = int(src[0].numel()) if n > 0 else 1
+    dst = torch.empty((int(n_kept),) + tuple(src.shape[1:]), dtype=src.dtype, device=src.device)
+    _check(lib().gs_compact(_ptr(src), n, width, _ptr(compact_map), _ptr(dst), _stream(stream)), "gs_compact")
+    return dst
+
+
+def gs_downsample(frame_idx, last_kf_idx, is_keyframe, m=2, target_full=None, stream=None):
+    """Returns (sx, sy) and, if target_full [C,H,W] is given, the gathered target."""
+    sx, sy = C.c_int32(0), C.c_int32(0)
+    _check(lib().gs_downsample(int(frame_idx), int(last_kf_idx), 1 if is_keyframe else 0, int(m), C.byref(sx),
+                               C.byref(sy), None, 0, 0, 0, None, None), "gs_downsample")
+    if target_full is None:
+        return sx.value, sy.value, None
+    t = target_full if target_full.dim() == 3 else target_full[None]
+    Cn, H, W = t.shape
+    out = torch.empty((Cn, -(-H // sy.value), -(-W // sx.value)), dtype=torch.float32, device=t.device)
+    _check(lib().gs_downsample(int(frame_idx), int(last_kf_idx), 1 if is_keyframe else 0, int(m), C.byref(sx),
+                               C.byref(sy), _ptr(t.contiguous()), Cn, W, H, _ptr(out), _stream(stream)),
+           "gs_downsample")
+    return sx.value, sy.value, out if target_full.dim() == 3 else out[0]
+
+
+def pose_tensor(cam, device="cuda"):
+    """Device float32 [12] pose (R row-major, t) of a camera dict."""
+    R = torch.as_tensor(cam["R"], dtype=torch.float32).reshape(9)
+    t = torch.as_tensor(cam["t"], dtype=torch.float32).reshape(3)
+    return torch.cat([R, t]).to(device)
+
+
+def gs_pose_update(pose, pose_grad, adam, lr_trans=1e-3, lr_rot=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                   stream=None):
+    _check(lib().gs_pose_update(_ptr(pose), _ptr(pose_grad), _ptr(adam), float(lr_trans), float(lr_rot),
+                                float(beta1), float(beta2), float(eps), _stream(stream)), "gs_pose_update")
+
+
+def gs_status_poll(blocking=True, stream=None):
+    st = C.c_int(0)
+    code = lib().gs_status_poll(_stream(stream), 1 if blocking else 0, C.byref(st))
+    return code, st.value
+
+
+def gs_status_reset(stream=None):
+    _check(lib().gs_status_reset(_stream(stream)), "gs_status_reset")
+
+
+# --------------------------------------------------------------------------
+# Record views (for tests and callers that inspect the 2D records)
+# --------------------------------------------------------------------------
+
+def splat_fields(splats, rec_dtype=GS_F32):
+    """Dict of views/decoded fields of a record array."""
+    if rec_dtype == GS_F32:
+        s = splats
+        return {"uv": s[:, 0:2], "conic": s[:, 2:5], "opacity": s[:, 5], "depth": s[:, 6],
+                "radius": s[:, 7].view(torch.int32), "rgb": s[:, 8:11], "touched": s[:, 11].view(torch.int32)}
+    w = splats
+    f32 = w.view(torch.float32)
+    h = w[:, 4:8].contiguous().view(torch.int16).view(torch.bfloat16 if rec_dtype == GS_BF16 else torch.float16)
+    h = h.float()
+    return {"uv": f32[:, 0:2], "depth": f32[:, 2], "radius": w[:, 3], "conic": h[:, 0:3], "opacity": h[:, 3],
+            "rgb": h[:, 4:7], "touched": (w[:, 7] >> 16) & 0xFFFF}

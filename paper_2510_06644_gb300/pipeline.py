@@ -1,0 +1,104 @@
+"""One rasterizer iteration over preallocated device buffers.
+
+``Rasterizer`` owns the buffers of one (map size, image grid) pair and chains
+the C-ABI calls of include/gs.h: projection -> binning + sort -> forward
+compositing -> loss -> backward compositing -> backward projection (+ pose).
+Everything runs on the current CUDA stream without host synchronisation, so
+an iteration can be captured in a CUDA graph; the key capacity is checked
+afterwards through the device status word (``check()``).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import gs
+
+
+class Rasterizer:
+    def __init__(self, n, cam, cfg=None, rec_dtype=gs.GS_F32, capacity=None, device="cuda"):
+        self.n = int(n)
+        self.cfg = cfg if cfg is not None else gs.default_config()
+        self.rec_dtype = rec_dtype
+        self.device = torch.device(device)
+        self.set_grid(cam)
+        words = gs.SPLAT_WORDS[rec_dtype]
+        dt = torch.float32 if rec_dtype == gs.GS_F32 else torch.int32
+        self.splats = torch.empty((self.n, words), dtype=dt, device=self.device)
+        self.capacity = int(capacity) if capacity is not None else max(4 * self.n, 1024)
+        self.keys = torch.empty(max(self.capacity, 1), dtype=torch.int64, device=self.device)
+        self.vals = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
+        self.n_keys = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.grad2d = torch.empty((self.n, gs.GRAD2D_STRIDE), device=self.device)
+        self.pose = torch.zeros(6, dtype=torch.float64, device=self.device)
+        self.score = torch.empty((self.n, 2), device=self.device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self._ws_sort = None
+        self._ws_bwd = None
+
+    def set_grid(self, cam):
+        """(Re)allocates the image buffers for the camera's sampled grid."""
+        Ws, Hs, TX, TY = gs.grid(cam)
+        if getattr(self, "_grid", None) == (Ws, Hs, TX, TY):
+            return
+        self._grid = (Ws, Hs, TX, TY)
+        d = self.device
+        self.ranges = torch.empty((TX * TY, 2), dtype=torch.int32, device=d)
+        self.img = {"rgb": torch.empty((3, Hs, Ws), device=d), "depth": torch.empty((Hs, Ws), device=d),
+                    "t_final": torch.empty((Hs, Ws), device=d),
+                    "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=d)}
+        self.dimg = {"d_rgb": torch.empty((3, Hs, Ws), device=d), "d_depth": torch.empty((Hs, Ws), device=d),
+                     "loss": torch.zeros(1, dtype=torch.float64, device=d)}
+        self._ws_sort = None
+
+    def _sort_ws(self, cam_s):
+        need = gs.gs_bin_sort_workspace(cam_s, self.rec_dtype, self.n, self.capacity)
+        if self._ws_sort is None or self._ws_sort.numel() < need:
+            self._ws_sort = gs.workspace(need, self.device)
+        return self._ws_sort
+
+    def _bwd_ws(self, cam_s, g):
+        need = gs.gs_project_bwd_workspace(self.cfg, cam_s, g)
+        if self._ws_bwd is None or self._ws_bwd.numel() < need:
+            self._ws_bwd = gs.workspace(need, self.device)
+        return self._ws_bwd
+
+    # -- stages ------------------------------------------------------------
+    def forward(self, g, cam):
+        """Projection, binning + sort and forward compositing; returns the
+        image buffers (rgb, depth, t_final, last_idx)."""
+        cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam)
+        self.set_grid(cam_s)
+        gs.gs_project(self.cfg, cam_s, g, self.rec_dtype, self.splats)
+        gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
+                       keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges)
+        gs.gs_render_fwd(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, self.rec_dtype, out=self.img)
+        return self.img
+
+    def loss_grad(self, cam, target_rgb, target_depth):
+        cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam)
+        gs.gs_loss_l1(self.cfg, cam_s, self.img["rgb"], self.img["depth"], target_rgb, target_depth, out=self.dimg)
+        return self.dimg
+
+    def backward(self, g, cam, d_rgb, d_depth, mode=gs.GS_TRACK, grads=None, want_pose=True, want_score=True):
+        cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam)
+        gs.gs_render_bwd(self.cfg, cam_s, g, self.splats, self.vals, self.ranges, self.img["t_final"],
+                         self.img["last_idx"], d_rgb, d_depth, mode, self.rec_dtype, grad2d=self.grad2d,
+                         grads=grads, pose=self.pose if want_pose else None,
+                         score=self.score if want_score else None, ws=self._bwd_ws(cam_s, g))
+        return self.grad2d
+
+    def step(self, g, cam, target_rgb, target_depth, mode=gs.GS_TRACK, grads=None):
+        """One whole iteration: forward, L1 loss (Eq. 6) and backward."""
+        cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam)
+        self.forward(g, cam_s)
+        self.loss_grad(cam_s, target_rgb, target_depth)
+        self.backward(g, cam_s, self.dimg["d_rgb"], self.dimg["d_depth"], mode, grads)
+        return self.pose
+
+    def check(self):
+        """Synchronises and raises if a device condition was raised (key
+        capacity exceeded, a bounded wait that gave up)."""
+        code, _ = gs.gs_status_poll(blocking=True)
+        if code != gs.GS_OK:
+            raise gs.GsError(code, f"device status {code} (n_keys={int(self.n_keys.item())}, "
+                                   f"capacity={self.capacity})")

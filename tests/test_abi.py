@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+that include/gs.h declares (no compute calls: no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gs_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_2510_06644_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_hot_path_entry_points():
+    names = declared_functions()
+    for need in ("gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_bwd", "gs_prune", "gs_downsample",
+                 "gs_project_bwd", "gs_loss_l1", "gs_status_poll", "gs_last_error"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    lib = ctypes.CDLL(built_lib)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_targets_sm_103a_only(built_lib):
+    from paper_2510_06644_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_host_only_entry_points_without_gpu(built_lib):
+    """Pure host functions answer without touching a device."""
+    from paper_2510_06644_gb300 import gs
+    cfg = gs.default_config()
+    assert abs(cfg.alpha_min - 1 / 255) < 1e-9 and cfg.k0 == 5 and abs(cfg.lambda_score - 0.8) < 1e-7
+    assert b"sm_103a" in gs.lib().gs_version()
+    for (n, k, kf, expect) in [(11, 10, False, (4, 4)), (12, 10, False, (4, 2)), (13, 10, False, (2, 2)),
+                               (20, 10, False, (2, 2)), (10, 10, True, (1, 1))]:
+        sx, sy, _ = gs.gs_downsample(n, k, kf, 2)
+        assert (sx, sy) == expect
+    with pytest.raises(gs.GsError):
+        gs.gs_downsample(12, 10, False, 3)
+
+
+def test_argument_errors_are_synchronous(built_lib):
+    from paper_2510_06644_gb300 import gs
+    cam = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 10, "fy": 10, "cx": 5, "cy": 5,
+                     "W": 0, "H": 10})
+    nb = ctypes.c_size_t(0)
+    rc = gs.lib().gs_bin_sort(ctypes.byref(cam), 0, None, 10, 100, None, ctypes.byref(nb), None, None, None,
+                              None, None)
+    assert rc == gs.GS_ERR_INVALID_ARG
+    assert b"camera" in gs.lib().gs_last_error()

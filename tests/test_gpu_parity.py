@@ -1,0 +1,396 @@
+"""Parity of the sm_103a path (called through the C ABI) with the FP64
+oracle, stage by stage and end to end.
+
+Bars: binning, keys, order and ranges bit-exact; images within 1e-4 max-abs
+away from predicate-marginal pixels (counted and bounded); gradients within
+1e-3 relative L2 per output tensor; pruning selection bit-exact given the
+same score terms."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+from tests.gpu_helpers import dev, np_of, pack_splats, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_06644_gb300 import build
+    build.build()
+    from paper_2510_06644_gb300 import gs
+    gs.gs_status_reset()
+    return gs
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def gpu_bin(G, cam, rec, n, cap=None):
+    cs = G.camera(cam)
+    cap = cap if cap is not None else max(8 * n, 1024)
+    keys, vals, nk, ranges = G.gs_bin_sort(cs, rec, n, cap)
+    torch.cuda.synchronize()
+    k = int(nk.item())
+    return np_of(keys[:k]).view(np.uint64), np_of(vals[:k]).view(np.uint32), np_of(ranges).view(np.uint32), vals, ranges
+
+
+# ---------------------------------------------------------------------------
+# A-1 projection
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["tiny", "slam_small", "tiny_strided"])
+def test_project_matches_oracle(G, O, case):
+    if case.startswith("tiny"):
+        g = S.tiny_scene(seed=1000)
+        cam = S.tiny_camera()
+        if case == "tiny_strided":
+            cam = dict(cam, sx=2, sy=2)
+    else:
+        g = S.surface_scene(20000, seed=2500)
+        cam = S.perturbed_pose(S.camera(320, 240, 260.0), seed=7, trans=0.05, rot_deg=3.0)
+    cfg = G.default_config()
+    rec = G.gs_project(cfg, G.camera(cam), dev(g))
+    torch.cuda.synchronize()
+    f = {k: np_of(v) for k, v in G.splat_fields(rec).items()}
+    pr = O.project(g, cam)
+    vis = pr["radius"] > 0
+    assert np.array_equal(f["radius"] > 0, vis)
+    np.testing.assert_allclose(f["uv"][vis], pr["uv"][vis], rtol=2e-6, atol=2e-4)
+    np.testing.assert_allclose(f["depth"][vis], pr["depth"][vis], rtol=2e-6)
+    np.testing.assert_allclose(f["opacity"][vis], pr["opacity"][vis], rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(f["rgb"], pr["rgb"].astype(np.float32), rtol=0, atol=0)
+    sc = np.abs(pr["conic"][vis]).max(axis=1, keepdims=True)
+    np.testing.assert_allclose(f["conic"][vis] / sc, pr["conic"][vis] / sc, rtol=0, atol=5e-5)
+    # radius: exact unless 3 sqrt(lambda_max) sits within 1e-4 of an integer
+    r3 = pr["r3"][vis]
+    near_int = np.abs(r3 - np.round(r3)) < 1e-4 * np.maximum(1, r3)
+    same_r = f["radius"][vis] == pr["radius"][vis]
+    assert np.all(same_r | near_int)
+    # tiles touched: exact where radius and floor(u), floor(v) agree
+    fl_same = np.all(np.floor(f["uv"][vis]) == np.floor(pr["uv"][vis]), axis=1)
+    ok = same_r & fl_same
+    assert np.array_equal(f["touched"][vis][ok], pr["touched"][vis][ok])
+    assert (~ok).sum() <= max(2, int(1e-3 * vis.sum()))
+
+
+# ---------------------------------------------------------------------------
+# A-2..A-4 binning, sort, ranges: bit-exact on identical 2D records
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,W,H,sx,sy,seed,sig", [
+    (3000, 96, 72, 1, 1, 1, (0.6, 12.0)),
+    (20000, 333, 197, 1, 1, 2, (0.6, 12.0)),     # ragged tiles, ~ 10 sort tiles
+    (20000, 640, 480, 2, 2, 3, (0.6, 30.0)),     # strides
+    (5000, 200, 120, 4, 2, 4, (0.6, 60.0)),      # anisotropic strides, large radii
+    (60000, 1200, 680, 1, 1, 5, (0.6, 8.0)),     # 3225 tiles -> 6 passes
+    (1, 40, 40, 1, 1, 6, (0.6, 3.0)),
+])
+def test_bin_sort_bit_exact(G, O, n, W, H, sx, sy, seed, sig):
+    cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
+    s = S.splats(n, W, H, seed=seed, sigma_px=sig, tie_frac=0.1)
+    rec = pack_splats(s)
+    keys, vals, ranges, _, _ = gpu_bin(G, cam, rec, n)
+    ok, ov, orr = O.bin_sort(s["uv"], s["depth"], s["radius"], cam)
+    assert keys.shape == ok.shape
+    assert np.array_equal(keys, ok)
+    assert np.array_equal(vals, ov)
+    assert np.array_equal(ranges, orr)
+    assert G.gs_status_poll()[0] == G.GS_OK
+
+
+def test_bin_sort_empty_and_all_culled(G, O):
+    cam = S.camera(64, 48, 50.0)
+    s = S.splats(100, 64, 48, seed=9)
+    s["radius"][:] = 0
+    keys, vals, ranges, _, _ = gpu_bin(G, cam, pack_splats(s), 100)
+    assert keys.size == 0 and np.all(ranges == 0)
+    rec0 = torch.zeros((0, 12), device="cuda")
+    keys, vals, ranges, _, _ = gpu_bin(G, cam, rec0, 0)
+    assert keys.size == 0 and np.all(ranges == 0)
+
+
+def test_bin_sort_capacity_overflow_is_reported(G):
+    cam = S.camera(256, 256, 100.0)
+    s = S.splats(4000, 256, 256, seed=10, sigma_px=(4, 20))
+    cs = G.camera(cam)
+    true_n = int(G.gs_bin_count(cs, pack_splats(s), 4000).item())
+    assert true_n > 1000
+    G.gs_status_reset()
+    keys, vals, nk, ranges = G.gs_bin_sort(cs, pack_splats(s), 4000, 1000)
+    code, _ = G.gs_status_poll(blocking=True)
+    assert code == G.GS_ERR_CAPACITY
+    assert int(nk.item()) == true_n
+    G.gs_status_reset()
+    assert G.gs_status_poll()[0] == G.GS_OK
+
+
+# ---------------------------------------------------------------------------
+# A-5 forward compositing on identical 2D records
+# ---------------------------------------------------------------------------
+
+def render_gpu(G, cam, rec, n, cfg=None):
+    cfg = cfg or G.default_config()
+    cs = G.camera(cam)
+    _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
+    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges)
+    torch.cuda.synchronize()
+    return {k: np_of(v) for k, v in out.items()}, vals, ranges
+
+
+@pytest.mark.parametrize("n,W,H,seed,sx,sy", [(3000, 96, 72, 11, 1, 1), (30000, 333, 197, 12, 1, 1),
+                                              (20000, 320, 240, 13, 2, 2)])
+def test_render_fwd_matches_oracle(G, O, n, W, H, seed, sx, sy):
+    cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
+    s = S.splats(n, W, H, seed=seed)
+    rec = pack_splats(s)
+    img, _, _ = render_gpu(G, cam, rec, n)
+    ref = O.render_fwd(s, cam)
+    good = ref["margin"] == 0
+    assert good.mean() > 0.97
+    for k, gk in (("rgb", "rgb"), ("depth", "depth"), ("T", "t_final")):
+        a, b = img[gk], ref[k]
+        diff = np.abs(a - b)
+        if a.ndim == 3:
+            diff = diff.max(0)
+        scale = 1.0 if k != "depth" else max(1.0, float(np.abs(s["depth"]).max()))
+        assert diff[good].max() <= IMG_TOL * scale, (k, diff[good].max())
+    assert np.array_equal(img["last_idx"][good].astype(np.int64), ref["last"][good])
+
+
+def test_stride_render_is_subsampled_full_render_bit_exact(G):
+    g = S.tiny_scene(seed=1234)
+    cam = S.tiny_camera()
+    cfg = G.default_config()
+    rec = G.gs_project(cfg, G.camera(cam), dev(g))
+    full, _, _ = render_gpu(G, cam, rec, 2000)
+    for sx, sy in ((2, 2), (4, 2), (4, 4), (3, 1)):
+        sub, _, _ = render_gpu(G, dict(cam, sx=sx, sy=sy), rec, 2000)
+        assert np.array_equal(sub["rgb"], full["rgb"][:, ::sy, ::sx])
+        assert np.array_equal(sub["depth"], full["depth"][::sy, ::sx])
+        assert np.array_equal(sub["t_final"], full["t_final"][::sy, ::sx])
+
+
+# ---------------------------------------------------------------------------
+# A-7 backward compositing on identical 2D records
+# ---------------------------------------------------------------------------
+
+GROUPS = {"mean2d": [0, 1], "conic": [2, 3, 4], "opacity": [5], "depth": [6], "rgb": [8, 9, 10]}
+
+
+@pytest.mark.parametrize("n,W,H,seed,mode", [(3000, 96, 72, 21, "map"), (30000, 333, 197, 22, "map"),
+                                             (20000, 320, 240, 23, "track")])
+def test_render_bwd_matches_oracle(G, O, n, W, H, seed, mode):
+    cam = S.camera(W, H, 100.0)
+    s = S.splats(n, W, H, seed=seed)
+    rec = pack_splats(s)
+    cfg = G.default_config()
+    cs = G.camera(cam)
+    _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
+    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges)
+    d_rgb, d_dep = S.image_grads(W, H, seed + 100)
+    gdummy = dev({"means": np.zeros((n, 3), np.float32), "log_scales": np.zeros((n, 3), np.float32),
+                  "quats": np.zeros((n, 4), np.float32), "opacity_logit": np.zeros(n, np.float32),
+                  "rgb": np.zeros((n, 3), np.float32)})
+    md = G.GS_MAP if mode == "map" else G.GS_TRACK
+    g2 = G.gs_render_bwd(cfg, cs, gdummy, rec, vals, ranges, out["t_final"], out["last_idx"],
+                         torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=md)
+    torch.cuda.synchronize()
+    g2 = np_of(g2)
+    ref = O.render_bwd(s, cam, d_rgb, d_dep)
+    for name, cols in GROUPS.items():
+        if mode == "track" and name in ("opacity", "rgb"):
+            assert np.all(g2[:, cols] == 0)
+            continue
+        e = rel_l2(g2[:, cols], ref[:, cols])
+        assert e <= GRAD_TOL, (name, e)
+
+
+# ---------------------------------------------------------------------------
+# A-8 backward projection + pose
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["tiny", "slam_small"])
+def test_project_bwd_matches_oracle(G, O, case):
+    if case == "tiny":
+        g = S.tiny_scene(seed=31)
+        cam = S.tiny_camera()
+    else:
+        g = S.surface_scene(20000, seed=32)
+        cam = S.perturbed_pose(S.camera(320, 240, 260.0), seed=33, trans=0.05, rot_deg=2.0)
+    n = g["means"].shape[0]
+    rng = S.rng(34)
+    g2 = (rng.normal(0, 1, (n, 12)) * np.array([1, 1, 10, 10, 10, 1, 1, 0, 1, 1, 1, 0]) * 1e-3).astype(np.float32)
+    cfg = G.default_config()
+    gd = dev(g)
+    grads = {k: torch.empty_like(gd[k]) for k in ("means", "log_scales", "quats", "opacity_logit", "rgb")}
+    pose = torch.zeros(6, dtype=torch.float64, device="cuda")
+    score = torch.empty((n, 2), device="cuda")
+    G.gs_project_bwd(cfg, G.camera(cam), gd, torch.from_numpy(g2).cuda(), grads=grads, pose=pose, score=score)
+    torch.cuda.synchronize()
+    ref = O.project_bwd(g, cam, g2)
+    for k in grads:
+        e = rel_l2(np_of(grads[k]), ref[k])
+        assert e <= GRAD_TOL, (k, e)
+    assert rel_l2(np_of(pose), ref["pose"]) <= GRAD_TOL
+    assert rel_l2(np_of(score), ref["score_terms"]) <= GRAD_TOL
+
+
+# ---------------------------------------------------------------------------
+# End to end: parameters -> image -> L1 loss (Eq. 6) -> all gradients + pose
+# ---------------------------------------------------------------------------
+
+def e2e_gpu(G, g, cam, trgb, tdep, mode=None):
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    n = g["means"].shape[0]
+    r = Rasterizer(n, cam)
+    gd = dev(g)
+    grads = {k: torch.empty_like(gd[k]) for k in ("means", "log_scales", "quats", "opacity_logit", "rgb")}
+    r.forward(gd, cam)
+    r.loss_grad(cam, torch.from_numpy(trgb).cuda(), torch.from_numpy(tdep).cuda())
+    r.backward(gd, cam, r.dimg["d_rgb"], r.dimg["d_depth"], mode=G.GS_MAP if mode is None else mode, grads=grads)
+    r.check()
+    return r, {k: np_of(v) for k, v in grads.items()}
+
+
+def test_end_to_end_tiny_scene(G, O):
+    """2,000 Gaussians, 96x72, fx=fy=80, L1 loss against a seeded uniform
+    target (RGB and depth)."""
+    g = S.tiny_scene(seed=1000)
+    cam = S.tiny_camera()
+    trgb, tdep = S.target_image(96, 72, seed=1001)
+    r, grads = e2e_gpu(G, g, cam, trgb, tdep)
+    pr, img = O.forward(g, cam)
+    good = img["margin"] == 0
+    diff = np.abs(np_of(r.img["rgb"]) - img["rgb"]).max(0)
+    assert diff[good].max() <= IMG_TOL
+    assert np.abs(np_of(r.img["depth"]) - img["depth"])[good].max() <= IMG_TOL * 5
+    L, dr, dd = O.loss_l1(img["rgb"], img["depth"], trgb, tdep)
+    assert abs(float(r.dimg["loss"].item()) - L) <= 1e-4 * max(1.0, abs(L))
+    # gradients of the oracle loss at the oracle image (sign decided by the oracle)
+    _, _, ref = O.forward_backward(g, cam, dr, dd)
+    for k in grads:
+        e = rel_l2(grads[k], ref[k])
+        assert e <= GRAD_TOL, (k, e)
+    assert rel_l2(np_of(r.pose), ref["pose"]) <= GRAD_TOL
+
+
+def test_tracking_frame_full_size(G, O):
+    """The 640x480 / 200k-Gaussian tracking workload in the launch
+    configuration the benchmark times: image parity away from marginal
+    pixels, sort invariants, and the 6-DoF pose gradient of L1 RGB + 0.5 L1
+    depth against the target rendered from the true pose."""
+    scene, true_cam, start_cam = S.tracking_workload()
+    n = scene["means"].shape[0]
+    _, tgt = O.forward(scene, true_cam)
+    trgb = tgt["rgb"].astype(np.float32)
+    tdep = tgt["depth"].astype(np.float32)
+    r, _ = e2e_gpu(G, scene, start_cam, trgb, tdep, mode=G.GS_TRACK)
+    pr, img = O.forward(scene, start_cam)
+    good = img["margin"] == 0
+    assert good.mean() > 0.99
+    diff = np.abs(np_of(r.img["rgb"]) - img["rgb"]).max(0)
+    assert diff[good].max() <= IMG_TOL, diff[good].max()
+    # sort invariants at full size
+    nk = int(r.n_keys.item())
+    keys = np_of(r.keys[:nk]).view(np.uint64)
+    assert np.all(keys[1:] >= keys[:-1])
+    touched = np_of(G.splat_fields(r.splats)["touched"]).astype(np.int64)
+    assert nk == touched.sum()
+    rng_ = np_of(r.ranges).view(np.uint32)
+    nonempty = rng_[:, 1] > rng_[:, 0]
+    assert rng_[nonempty, 1].max() == nk
+    # pose gradient of the tracking loss
+    L, dr, dd = O.loss_l1(img["rgb"], img["depth"], tgt["rgb"], tgt["depth"])
+    g2 = O.render_bwd(pr, start_cam, dr, dd)
+    ref = O.project_bwd(scene, start_cam, g2)
+    e = rel_l2(np_of(r.pose), ref["pose"])
+    assert e <= GRAD_TOL, (np_of(r.pose), ref["pose"], e)
+
+
+# ---------------------------------------------------------------------------
+# A-9 pruning, change ratio, compaction
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,frac,cap,premask", [(5000, 0.1, None, 0.0), (100000, 0.1, None, 0.2),
+                                                (1000, 0.5, 37, 0.1), (10, 0.3, None, 0.0), (1, 0.1, None, 0.0)])
+def test_prune_select_bit_exact(G, O, n, frac, cap, premask):
+    st = S.score_terms(n, seed=n)
+    rng = S.rng(n + 1)
+    mask0 = (rng.random(n) < premask).astype(np.uint8)
+    cfg = G.default_config(prune_frac=frac)
+    m = torch.from_numpy(mask0.copy()).cuda()
+    K = G.gs_prune(cfg, torch.from_numpy(st).cuda(), m, 0, 5, max_select=cap if cap is not None else n)
+    torch.cuda.synchronize()
+    ref, cnt = O.prune_select(st[:, 0], st[:, 1], mask0, lam=float(np.float32(0.8)),
+                              frac=float(np.float32(frac)), max_select=cap if cap is not None else n)
+    assert np.array_equal(np_of(m), ref)
+    assert K == 5
+
+
+def test_prune_removal_compaction_and_interval(G, O):
+    n = 7777
+    rng = S.rng(5)
+    mask = (rng.random(n) < 0.3).astype(np.uint8)
+    cfg = G.default_config()
+    cmap = torch.empty(n, dtype=torch.int32, device="cuda")
+    nk = torch.zeros(1, dtype=torch.int64, device="cuda")
+    K = G.gs_prune(cfg, None, torch.from_numpy(mask).cuda(), 5, 5, change_ratio=0.2, compact_map=cmap, n_kept=nk)
+    assert K == O.next_interval(5, 0.2) == 2
+    torch.cuda.synchronize()
+    keep = mask == 0
+    exp = np.full(n, 0xFFFFFFFF, np.uint32)
+    exp[keep] = np.arange(keep.sum(), dtype=np.uint32)
+    assert np.array_equal(np_of(cmap).view(np.uint32), exp)
+    assert int(nk.item()) == keep.sum()
+    src = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).cuda()
+    dst = G.gs_compact(src, cmap, int(nk.item()))
+    assert np.array_equal(np_of(dst), np_of(src)[keep])
+    K = G.gs_prune(cfg, None, torch.from_numpy(mask).cuda(), 2, 2, change_ratio=0.01, compact_map=cmap, n_kept=nk)
+    assert K == O.next_interval(2, 0.01) == 4
+
+
+def test_change_ratio_matches_pair_sets(G, O):
+    g = S.surface_scene(20000, seed=77)
+    cam_a = S.camera(320, 240, 260.0)
+    cam_b = S.perturbed_pose(cam_a, seed=78, trans=0.03, rot_deg=1.5)
+    cfg = G.default_config()
+    gd = dev(g)
+    ra = G.gs_project(cfg, G.camera(cam_a), gd)
+    rb = G.gs_project(cfg, G.camera(cam_b), gd)
+    ratio = float(G.gs_change_ratio(G.camera(cam_a), ra, rb, 20000).item())
+
+    def pairs(rec):
+        f = {k: np_of(v) for k, v in G.splat_fields(rec).items()}
+        keys, vals, _ = O.bin_sort(f["uv"], f["depth"], f["radius"], cam_a)
+        return ((keys >> np.uint64(32)) << np.uint64(32)) | vals.astype(np.uint64)
+
+    ref = O.change_ratio(pairs(ra), pairs(rb))
+    assert ref > 0.01
+    assert abs(ratio - ref) <= 1e-6 * max(1.0, ref)
+
+
+# ---------------------------------------------------------------------------
+# A-10 downsampling
+# ---------------------------------------------------------------------------
+
+def test_downsample_schedule_and_gather(G, O):
+    full = S.rng(3).uniform(0, 1, (3, 72, 96)).astype(np.float32)
+    for n in range(11, 17):
+        sx, sy, out = G.gs_downsample(n, 10, False, 2, torch.from_numpy(full).cuda())
+        assert (sx, sy) == O.downsample_schedule(n, 10, False)
+        assert np.array_equal(np_of(out), O.gather(full, sx, sy).astype(np.float32))
+    sx, sy, out = G.gs_downsample(10, 10, True, 2, torch.from_numpy(full).cuda())
+    assert (sx, sy) == (1, 1) and np.array_equal(np_of(out), full)
