@@ -380,7 +380,8 @@ static int sort_blocks_per_sm() {
 
 using namespace gs;
 
-static gs_status bin_common_checks(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n) {
+static gs_status bin_common_checks(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
+                                   bool size_query) {
     if (!cam) return set_error(GS_ERR_INVALID_ARG, "camera is NULL");
     if (cam->width <= 0 || cam->height <= 0 || cam->sx < 1 || cam->sy < 1 || cam->width > (1 << 20) ||
         cam->height > (1 << 20))
@@ -388,7 +389,7 @@ static gs_status bin_common_checks(const gs_camera* cam, int rec_dtype, const vo
     if (rec_dtype != GS_F32 && rec_dtype != GS_BF16 && rec_dtype != GS_F16)
         return set_error(GS_ERR_INVALID_ARG, "bad record dtype %d", rec_dtype);
     if (n < 0 || n > (int64_t)0xFFFFFFF0LL) return set_error(GS_ERR_INVALID_ARG, "bad Gaussian count");
-    if (n > 0 && (!splats || ((uintptr_t)splats & 15)))
+    if (!size_query && n > 0 && (!splats || ((uintptr_t)splats & 15)))
         return set_error(GS_ERR_INVALID_ARG, "splats NULL or not 16-byte aligned");
     return GS_OK;
 }
@@ -417,7 +418,7 @@ extern "C" gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const voi
                                   void* workspace, size_t* workspace_bytes, int64_t* n_keys_out,
                                   gs_stream stream) {
     gs_status s;
-    if ((s = bin_common_checks(cam, rec_dtype, splats, n)) != GS_OK) return s;
+    if ((s = bin_common_checks(cam, rec_dtype, splats, n, workspace == nullptr)) != GS_OK) return s;
     if (!workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "workspace_bytes is NULL");
     const int64_t nchunk = (n + BIN_CHUNK - 1) / BIN_CHUNK;
     const size_t need = align256(sizeof(u64) * (size_t)(nchunk > 0 ? nchunk : 1));
@@ -433,7 +434,7 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
                                  uint64_t* keys_out, uint32_t* vals_out, int64_t* n_keys_out,
                                  uint32_t* tile_ranges, gs_stream stream) {
     gs_status s;
-    if ((s = bin_common_checks(cam, rec_dtype, splats, n)) != GS_OK) return s;
+    if ((s = bin_common_checks(cam, rec_dtype, splats, n, workspace == nullptr)) != GS_OK) return s;
     if (!workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "workspace_bytes is NULL");
     if (keys_capacity < 0 || keys_capacity >= (int64_t)COUNT_MASK)
         return set_error(GS_ERR_INVALID_ARG, "keys_capacity must be in [0, 2^30)");
