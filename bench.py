@@ -36,11 +36,13 @@ W_IMG, H_IMG, N_G = 640, 480, 200_000
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
-    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-graph", action="store_true", help="time eager launches instead of a CUDA graph")
     p.add_argument("--skip-cpu-baseline", action="store_true")
+    p.add_argument("--profile", action="store_true",
+                   help="only run warmup + steps tracking iterations eagerly (for ncu launch lists), print nothing")
     return p.parse_args()
 
 
@@ -224,6 +226,11 @@ def run_ours(args):
         rast.step(gd, cam_s, trgb, tdep, gs.GS_TRACK)
         gs.gs_pose_update(pose, rast.pose, adam, lr_t, lr_r)
 
+    if args.profile:
+        for _ in range(args.warmup + args.steps):
+            step()
+        rast.check()
+        return
     for _ in range(max(args.warmup, 3)):
         step()
     rast.check()
@@ -285,15 +292,16 @@ def run_ours(args):
         gs.gs_project(rast.cfg, cs, gd, rast.rec_dtype, rast.splats)
         evs[1].record()
         gs.gs_bin_sort(cs, rast.splats, n, rast.capacity, rast.rec_dtype, ws=rast._sort_ws(cs), keys=rast.keys,
-                       vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges)
+                       vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges, order=rast.order)
         evs[2].record()
-        gs.gs_render_fwd(rast.cfg, cs, rast.splats, n, rast.vals, rast.ranges, rast.rec_dtype, out=rast.img)
+        gs.gs_render_fwd(rast.cfg, cs, rast.splats, n, rast.vals, rast.ranges, rast.rec_dtype, out=rast.img,
+                         order=rast.order)
         evs[3].record()
         rast.loss_grad(cs, trgb, tdep)
         evs[4].record()
         gs.gs_render_bwd(rast.cfg, cs, gd, rast.splats, rast.vals, rast.ranges, rast.img["t_final"],
                          rast.img["last_idx"], rast.dimg["d_rgb"], rast.dimg["d_depth"], gs.GS_TRACK,
-                         rast.rec_dtype, grad2d=rast.grad2d)
+                         rast.rec_dtype, grad2d=rast.grad2d, order=rast.order)
         evs[5].record()
         gs.gs_project_bwd(rast.cfg, cs, gd, rast.grad2d, pose=rast.pose, score=rast.score, ws=rast._bwd_ws(cs, gd))
         evs[6].record()
@@ -356,7 +364,7 @@ def run_ours(args):
            "h2d_bytes_per_step": trgb.numel() * 4 + tdep.numel() * 4, "d2h_bytes_per_step": 7 * 8}
 
     passes = (32 + max(1, (int(np.ceil(np.log2(max(2, rast._grid[2] * rast._grid[3])))))) + 7) // 8
-    launches_per_step = 1 + (5 + passes) + 1 + 1 + 1 + 2 + 1
+    launches_per_step = 1 + (6 + passes) + 1 + 1 + 1 + 1 + 1
     line = {
         "metric": METRIC, "value": iters_s, "unit": "iters/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",

@@ -187,12 +187,15 @@ gs_status gs_project(const gs_config* cfg, const gs_camera* cam, const gs_gaussi
  * n_keys_out: one device int64 receiving the true key count, tile_ranges
  * [2*TX*TY] u32.  If the count exceeds keys_capacity, only keys_capacity keys
  * are sorted and the device status becomes GS_ERR_CAPACITY.
+ * tile_order (may be NULL): [TX*TY] u32 permutation of the tile ids, longest
+ * lists first (grouped by floor(log2(length + 1)), any order inside a group);
+ * passing it to the compositing calls makes long tiles start first.
  * Workspace: query with workspace == NULL (depends on n, keys_capacity and
  * the tile count). */
 gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
                       int64_t keys_capacity, void* workspace, size_t* workspace_bytes,
                       uint64_t* keys_out, uint32_t* vals_out, int64_t* n_keys_out,
-                      uint32_t* tile_ranges, gs_stream stream);
+                      uint32_t* tile_ranges, uint32_t* tile_order, gs_stream stream);
 
 /* Key count only (the first two stages of gs_bin_sort), so that a caller can
  * size keys_capacity.  Same workspace as gs_bin_sort. */
@@ -212,11 +215,12 @@ gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const void* splats, 
  * Finally C += T bg.
  * Outputs: rgb [3][Hs][Ws], depth [Hs][Ws], t_final [Hs][Ws], last_idx
  * [Hs][Ws] (list position + 1 of the last blended fragment, relative to the
- * tile's first entry; 0 if none).  vals and tile_ranges come from
- * gs_bin_sort with the same camera. */
+ * tile's first entry; 0 if none).  vals, tile_ranges and tile_order (may be
+ * NULL: tiles in id order) come from gs_bin_sort with the same camera. */
 gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype,
                         const void* splats, int64_t n, const uint32_t* vals,
-                        const uint32_t* tile_ranges, float* rgb, float* depth, float* t_final,
+                        const uint32_t* tile_ranges, const uint32_t* tile_order, float* rgb,
+                        float* depth, float* t_final,
                         uint32_t* last_idx, gs_stream stream);
 
 /* ---------------------------------------------------------------------- */
@@ -248,7 +252,8 @@ gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, const float* rg
  * well on the same stream (same workspace). */
 gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
                         int rec_dtype, const void* splats, const uint32_t* vals,
-                        const uint32_t* tile_ranges, const float* t_final,
+                        const uint32_t* tile_ranges, const uint32_t* tile_order,
+                        const float* t_final,
                         const uint32_t* last_idx, const float* d_rgb, const float* d_depth,
                         int mode, float* grad2d, gs_grads* grads, double* pose_grad6,
                         float* score_terms, void* workspace, size_t* workspace_bytes,

@@ -333,6 +333,31 @@ __global__ void __launch_bounds__(256) k_ranges(const u64* __restrict__ keys, co
     }
 }
 
+// Heavy-first tile order: tiles grouped by floor(log2(length + 1)), longest
+// group first (32 groups; order inside a group is whatever the atomics give,
+// which only affects scheduling, never results).
+__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ ranges, int ntiles,
+                                                     uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[33], cur[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        atomicAdd(&cnt[31 - (31 - __clz(len + 1u))], 1u);  // bucket 0 = longest
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < 33; ++b) { cur[b] = run; run += cnt[b]; }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
+        const uint32_t pos = atomicAdd(&cur[31 - (31 - __clz(len + 1u))], 1u);
+        order[pos] = (uint32_t)t;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Workspace layout
 // ---------------------------------------------------------------------------
@@ -432,7 +457,7 @@ extern "C" gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const voi
 extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
                                  int64_t keys_capacity, void* workspace, size_t* workspace_bytes,
                                  uint64_t* keys_out, uint32_t* vals_out, int64_t* n_keys_out,
-                                 uint32_t* tile_ranges, gs_stream stream) {
+                                 uint32_t* tile_ranges, uint32_t* tile_order, gs_stream stream) {
     gs_status s;
     if ((s = bin_common_checks(cam, rec_dtype, splats, n, workspace == nullptr)) != GS_OK) return s;
     if (!workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "workspace_bytes is NULL");
@@ -453,7 +478,13 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
     u64* partial = (u64*)(ws + L.off_partial);
     if ((s = launch_count_scan(cam, rec_dtype, splats, n, partial, L.nchunk, n_keys_out, keys_capacity, st)) != GS_OK)
         return s;
-    if (n == 0 || keys_capacity == 0) return GS_OK;
+    if (n == 0 || keys_capacity == 0) {
+        if (tile_order) {
+            k_tile_order<<<1, 1024, 0, st>>>(tile_ranges, ntiles, tile_order);
+            return check_launch("k_tile_order");
+        }
+        return GS_OK;
+    }
     if (cudaMemsetAsync(ws + L.off_zero, 0, L.zero_bytes, st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset sort state");
     // ping-pong so that the last pass writes keys_out / vals_out
@@ -507,6 +538,10 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
         const unsigned rb = (unsigned)(want2 < 4 * sms ? (want2 > 0 ? want2 : 1) : 4 * sms);
         k_ranges<<<rb, 256, 0, st>>>(bufk[cur], n_keys_out, keys_capacity, tile_ranges);
         if ((s = check_launch("k_ranges")) != GS_OK) return s;
+    }
+    if (tile_order) {
+        k_tile_order<<<1, 1024, 0, st>>>(tile_ranges, ntiles, tile_order);
+        if ((s = check_launch("k_tile_order")) != GS_OK) return s;
     }
     return GS_OK;
 }

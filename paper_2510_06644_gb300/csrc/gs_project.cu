@@ -149,11 +149,49 @@ __global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, g
 
 #define PB_THREADS 256
 
+// Neumaier's compensated sum of (s, c) pairs held by the lanes of a warp,
+// merged in a fixed butterfly order.
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double v) {
+    const double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+// Final combination of the per-block float64 pose partials by the last block
+// to finish (no spin: the block that takes the last ticket sees every other
+// block's partial, published before its ticket).  Warp w < 6 sums component w.
+__device__ void pose_final_last_block(const double* __restrict__ part, int nblk, double* __restrict__ out,
+                                      unsigned int* __restrict__ ticket) {
+    __shared__ bool s_last;
+    __threadfence();
+    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)nblk - 1u);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < 6) {
+        double s = 0.0, c = 0.0;
+        for (int b = lane; b < nblk; b += 32) neumaier_add(s, c, __ldcg(part + (size_t)b * 6 + w));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+            const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            c += c2;
+            neumaier_add(s, c, s2);
+        }
+        if (lane == 0) out[w] = s + c;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
+}
+
 template <bool WANT_GRADS, bool WANT_POSE, bool WANT_SCORE>
 __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_config cfg,
                                                             gs_gaussians g, const float* __restrict__ grad2d,
                                                             gs_grads grads, float* __restrict__ score,
-                                                            double* __restrict__ pose_part) {
+                                                            double* __restrict__ pose_part,
+                                                            double* __restrict__ pose_out,
+                                                            unsigned int* __restrict__ ticket) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float pose[6] = {0, 0, 0, 0, 0, 0};
     resolve_pose(cam);
@@ -315,40 +353,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_co
             for (int w = 0; w < PB_THREADS / 32; ++w) s += ws[w][threadIdx.x];
             pose_part[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
         }
-    }
-}
-
-// Combines the per-block float64 pose partials with Neumaier's compensated
-// summation: each thread sums a strided subset, then the threads' (sum,
-// compensation) pairs are merged in a fixed tree, so the result does not
-// depend on scheduling.
-__global__ void __launch_bounds__(256) k_pose_final(const double* __restrict__ part, int nblk,
-                                                    double* __restrict__ out) {
-    __shared__ double ss[256], sc[256];
-    for (int comp = 0; comp < 6; ++comp) {
-        double s = 0.0, c = 0.0;
-        for (int b = threadIdx.x; b < nblk; b += 256) {
-            const double v = part[(size_t)b * 6 + comp];
-            const double t = s + v;
-            if (fabs(s) >= fabs(v)) c += (s - t) + v;
-            else c += (v - t) + s;
-            s = t;
-        }
-        ss[threadIdx.x] = s;
-        sc[threadIdx.x] = c;
-        __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
-            if (threadIdx.x < o) {
-                const double a = ss[threadIdx.x], b = ss[threadIdx.x + o];
-                const double t = a + b;
-                const double e = (fabs(a) >= fabs(b)) ? (a - t) + b : (b - t) + a;
-                ss[threadIdx.x] = t;
-                sc[threadIdx.x] += sc[threadIdx.x + o] + e;
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[comp] = ss[0] + sc[0];
-        __syncthreads();
+        pose_final_last_block(pose_part, (int)gridDim.x, pose_out, ticket);
     }
 }
 
@@ -395,7 +400,7 @@ extern "C" gs_status gs_project(const gs_config* cfg, const gs_camera* cam, cons
 
 size_t gs_project_bwd_ws(int64_t n) {
     const size_t nblk = (size_t)((n + PB_THREADS - 1) / PB_THREADS);
-    return ((nblk * 6 * sizeof(double)) + 255) & ~(size_t)255;
+    return ((nblk * 6 * sizeof(double)) + 255 + 256) & ~(size_t)255;  // partials + ticket
 }
 
 extern "C" gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
@@ -423,8 +428,11 @@ extern "C" gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, 
     gs_grads gg = grads ? *grads : gs_grads{nullptr, nullptr, nullptr, nullptr, nullptr};
     const unsigned nblk = (unsigned)((g->n + PB_THREADS - 1) / PB_THREADS);
     double* part = (double*)workspace;
+    unsigned int* ticket = (unsigned int*)((char*)workspace + need - 256);
+    if (want_pose && cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st) != cudaSuccess)
+        return set_error(GS_ERR_CUDA, "memset ticket");
 #define GS_PB_LAUNCH(A, B, C_) \
-    k_project_bwd<A, B, C_><<<nblk, PB_THREADS, 0, st>>>(*cam, *cfg, *g, grad2d, gg, score_terms, part)
+    k_project_bwd<A, B, C_><<<nblk, PB_THREADS, 0, st>>>(*cam, *cfg, *g, grad2d, gg, score_terms, part, pose_grad6, ticket)
     if (want_grads) {
         if (want_pose) { if (want_score) GS_PB_LAUNCH(true, true, true); else GS_PB_LAUNCH(true, true, false); }
         else { if (want_score) GS_PB_LAUNCH(true, false, true); else GS_PB_LAUNCH(true, false, false); }
@@ -433,12 +441,7 @@ extern "C" gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, 
         else { if (want_score) GS_PB_LAUNCH(false, false, true); else return GS_OK; }
     }
 #undef GS_PB_LAUNCH
-    if ((s = check_launch("k_project_bwd")) != GS_OK) return s;
-    if (want_pose) {
-        k_pose_final<<<1, 256, 0, st>>>(part, (int)nblk, pose_grad6);
-        if ((s = check_launch("k_pose_final")) != GS_OK) return s;
-    }
-    return GS_OK;
+    return check_launch("k_project_bwd");
 }
 
 // ---------------------------------------------------------------------------

@@ -2,22 +2,30 @@
 // (Sec. 4.1, Eq. 6) and A-7 backward compositing (Sec. 2.2, Step 4: Eq. 4,
 // Eq. 5) on sm_103a.
 //
-// One CTA of 256 threads per 16x16 tile, one pixel per thread.  The 8 warps
-// cover 8x4 pixel blocks (not rows), so a small Gaussian's integer box misses
-// most warps and the whole warp skips it with one uniform test.  The tile's
-// sorted list is staged through shared memory in batches of 256 records (one
-// 48-byte gather per thread); every pixel then walks the batch from shared
-// memory.  The forward keeps T_final and the last blended list position per
-// pixel; the backward walks the same list in reverse from there, recovering
-// T_k by division (Eq. 5), and merges the per-pixel gradients of each
-// Gaussian first across the warp (shuffles), then across the tile (shared
-// atomics), then with one global atomic per (Gaussian, tile, field).
+// One CTA of 256 threads per 16x16 tile, one pixel per thread; CTAs are
+// issued in the heavy-first tile order produced by the binning, so the block
+// scheduler starts the longest lists first (the GPU counterpart of the
+// paper's subtile streaming, Sec. 5.2).  The 8 warps cover 8x4 pixel blocks.
+// The tile's sorted list is staged through shared memory in batches of 256
+// records (one 48-byte gather per thread).  Each warp then builds a 256-bit
+// mask of the staged Gaussians whose integer box meets its 8x4 block (8
+// box tests and 8 ballots per lane) and visits only those.
+//
+// The backward walks each pixel's blended fragments in reverse from the
+// forward's last position, recovering T_k by division (Eq. 5), and merges the
+// per-pixel gradients of each Gaussian across the warp with a reduce-scatter
+// butterfly (each level halves the fields a lane carries: 9 shuffles for 6
+// fields, 16 for 10, instead of 5 per field), after which 8 or 16 lanes add
+// distinct fields into the tile's shared-memory accumulators at once; one
+// global atomic per (Gaussian, tile, field) follows.  This replaces the
+// paper's Gradient Merging Unit (Sec. 5.3).
 #include "gs_internal.cuh"
 
 namespace gs {
 
 #define R_THREADS 256
 #define R_BATCH 256
+#define R_MASKW (R_BATCH / 32)
 
 struct StagedSplat {
     float4 a;   // x, y, conic_a, conic_b
@@ -60,14 +68,35 @@ __device__ __forceinline__ void stage(const void* splats, uint32_t gid, StagedSp
     s.box = make_int4(xi - r, xi + r, yi - r, yi + r);
 }
 
+// Bit e of word q set when staged entry 32q + e (below `limit`) meets the
+// warp's block.
+__device__ __forceinline__ void warp_masks(const StagedSplat* sp, int limit, const PixelMap& m, unsigned* mask) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < R_MASKW; ++q) {
+        const int e = q * 32 + lane;
+        bool hit = false;
+        if (e < limit) {
+            const int4 box = sp[e].box;
+            hit = !(box.y < m.wx0 || box.x > m.wx1 || box.w < m.wy0 || box.z > m.wy1);
+        }
+        mask[q] = __ballot_sync(0xffffffffu, hit);
+    }
+}
+
+__device__ __forceinline__ int tile_of(const uint32_t* order) {
+    return order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
+}
+
 template <int DT>
 __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g, const void* __restrict__ splats,
                                                           const uint32_t* __restrict__ vals,
                                                           const uint32_t* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ order,
                                                           float* __restrict__ out_rgb, float* __restrict__ out_depth,
                                                           float* __restrict__ out_t, uint32_t* __restrict__ out_last) {
     __shared__ StagedSplat sp[R_BATCH];
-    const int tile = blockIdx.x;
+    const int tile = tile_of(order);
     const PixelMap m = map_pixel(g, tile);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
@@ -80,25 +109,33 @@ __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g,
         if ((int)threadIdx.x < n_in) stage<DT>(splats, __ldg(vals + b + threadIdx.x), sp[threadIdx.x]);
         __syncthreads();
         if (!__all_sync(0xffffffffu, done)) {
-            for (int e = 0; e < n_in; ++e) {
-                const int4 box = sp[e].box;
-                if (box.y < m.wx0 || box.x > m.wx1 || box.w < m.wy0 || box.z > m.wy1) continue;
-                if (done || m.px < box.x || m.px > box.y || m.py < box.z || m.py > box.w) continue;
-                const float4 A = sp[e].a;
-                const float dx = pxc - A.x, dy = pyc - A.y;
-                const float4 B = sp[e].b;
-                const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                if (power > 0.f) continue;
-                const float alpha = fminf(cfg.alpha_max, B.y * __expf(power));
-                if (alpha < cfg.alpha_min) continue;
-                const float Tn = T * (1.f - alpha);
-                if (Tn < cfg.t_eps) { done = true; continue; }
-                const float w = alpha * T;
-                const float4 Cc = sp[e].c;
-                C0 += w * Cc.x; C1 += w * Cc.y; C2 += w * Cc.z;
-                D += w * B.z;
-                T = Tn;
-                last = b - start + (uint32_t)e + 1u;
+            unsigned mask[R_MASKW];
+            warp_masks(sp, n_in, m, mask);
+#pragma unroll 1
+            for (int q = 0; q < R_MASKW; ++q) {
+                unsigned mq = mask[q];
+                while (mq) {
+                    const int e = q * 32 + __ffs(mq) - 1;
+                    mq &= mq - 1u;
+                    const int4 box = sp[e].box;
+                    if (done || m.px < box.x || m.px > box.y || m.py < box.z || m.py > box.w) continue;
+                    const float4 A = sp[e].a;
+                    const float dx = pxc - A.x, dy = pyc - A.y;
+                    const float4 B = sp[e].b;
+                    const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
+                    if (power > 0.f) continue;
+                    const float alpha = fminf(cfg.alpha_max, B.y * __expf(power));
+                    if (alpha < cfg.alpha_min) continue;
+                    const float Tn = T * (1.f - alpha);
+                    if (Tn < cfg.t_eps) { done = true; continue; }
+                    const float w = alpha * T;
+                    const float4 Cc = sp[e].c;
+                    C0 += w * Cc.x; C1 += w * Cc.y; C2 += w * Cc.z;
+                    D += w * B.z;
+                    T = Tn;
+                    last = b - start + (uint32_t)e + 1u;
+                }
+                if (__all_sync(0xffffffffu, done)) break;
             }
         }
         __syncthreads();
@@ -154,22 +191,64 @@ __global__ void __launch_bounds__(256) k_loss_l1(gs_config cfg, int64_t P, const
 // ---------------------------------------------------------------------------
 // Backward compositing
 // ---------------------------------------------------------------------------
-// Accumulated fields per staged Gaussian, in grad2d order.
-#define NF 12
+// Slots merged per fragment: GS_TRACK 8 (du, dv, dA, dB, dC, dd, -, -),
+// GS_MAP 16 (du, dv, dA, dB, dC, dop, dd, dr, dg, db, -...).
+template <int MODE>
+struct Slots {
+    static constexpr int N = MODE == GS_MAP ? 16 : 8;
+    static constexpr int LOG = MODE == GS_MAP ? 4 : 3;
+};
+
+// grad2d column of a slot (-1 = padding).
+template <int MODE>
+__device__ __forceinline__ int slot_col(int s) {
+    if (MODE == GS_MAP) return s < 7 ? s : (s < 10 ? s + 1 : -1);  // du dv dA dB dC dop dd | dr dg db
+    return s < 5 ? s : (s == 5 ? 6 : -1);                             // du dv dA dB dC | dd
+}
+
+// Reduce-scatter of N values across the warp.  On return lane l holds the
+// warp total of slot (l >> (5 - LOG)) when (l & ((1 << (5 - LOG)) - 1)) == 0.
+template <int N, int LOG>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int lvl = 0; lvl < LOG; ++lvl) {
+        const int off = 16 >> lvl;
+        const int half = N >> (lvl + 1);
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            if (i < half) {
+                const float send = up ? v[i] : v[i + half];
+                const float keep = up ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+    }
+    float x = v[0];
+#pragma unroll
+    for (int off = 16 >> LOG; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
 
 template <int DT, int MODE>
 __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g, const void* __restrict__ splats,
                                                           const uint32_t* __restrict__ vals,
                                                           const uint32_t* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ order,
                                                           const float* __restrict__ t_final,
                                                           const uint32_t* __restrict__ last_idx,
                                                           const float* __restrict__ d_rgb,
                                                           const float* __restrict__ d_depth,
                                                           float* __restrict__ grad2d) {
+    constexpr int NS = Slots<MODE>::N;
+    constexpr int LOG = Slots<MODE>::LOG;
+    constexpr int SHIFT = 5 - LOG;  // lanes per slot = 1 << SHIFT
     __shared__ StagedSplat sp[R_BATCH];
     __shared__ uint32_t sid[R_BATCH];
-    __shared__ float acc[R_BATCH][NF];
-    const int tile = blockIdx.x;
+    __shared__ float acc[R_BATCH][NS];
+    __shared__ uint32_t s_max;
+    const int tile = tile_of(order);
     const PixelMap m = map_pixel(g, tile);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
@@ -186,16 +265,18 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
         gC2 = d_rgb[2 * P + pix];
         gD = d_depth[pix];
     }
+    // a last_idx beyond the tile's list (inconsistent inputs) is clamped
+    last = min(last, end - start);
     // normalised suffix sums (background enters with weight T_final)
     float A0 = cfg.bg[0], A1 = cfg.bg[1], A2 = cfg.bg[2], AD = 0.f;
-    // block maximum of last -> the part of the list any pixel blended
-    __shared__ uint32_t s_max;
+    uint32_t wlast = last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    atomicMax(&s_max, last);
+    if (lane == 0) atomicMax(&s_max, wlast);
     __syncthreads();
-    // a last_idx beyond the tile's list (inconsistent inputs) is clamped
-    const uint32_t end_eff = start + min(s_max, end - start);
+    const uint32_t end_eff = start + s_max;
     for (uint32_t hi = end_eff; hi > start;) {
         const uint32_t lo = hi - start > R_BATCH ? hi - R_BATCH : start;
         const int n_in = (int)(hi - lo);
@@ -204,74 +285,77 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
             sid[threadIdx.x] = gid;
             stage<DT>(splats, gid, sp[threadIdx.x]);
         }
-        for (int q = threadIdx.x; q < R_BATCH * NF; q += R_THREADS) (&acc[0][0])[q] = 0.f;
+        for (int q = threadIdx.x; q < R_BATCH * NS; q += R_THREADS) (&acc[0][0])[q] = 0.f;
         __syncthreads();
         const uint32_t base_pos = lo - start;
-        for (int e = n_in - 1; e >= 0; --e) {
-            const int4 box = sp[e].box;
-            if (box.y < m.wx0 || box.x > m.wx1 || box.w < m.wy0 || box.z > m.wy1) continue;
-            bool contrib = (base_pos + (uint32_t)e) < last && m.px >= box.x && m.px <= box.y && m.py >= box.z &&
-                           m.py <= box.w;
-            float f[NF];
+        // entries at or beyond the warp's furthest blended position are skipped
+        const int wlimit = (int)min((uint32_t)n_in, wlast > base_pos ? wlast - base_pos : 0u);
+        unsigned mask[R_MASKW];
+        warp_masks(sp, wlimit, m, mask);
+#pragma unroll 1
+        for (int q = R_MASKW - 1; q >= 0; --q) {
+            unsigned mq = mask[q];
+            while (mq) {
+                const int bit = 31 - __clz(mq);
+                const int e = q * 32 + bit;
+                mq &= ~(1u << bit);
+                const int4 box = sp[e].box;
+                bool contrib = (base_pos + (uint32_t)e) < last && m.px >= box.x && m.px <= box.y &&
+                               m.py >= box.z && m.py <= box.w;
+                float f[NS];
 #pragma unroll
-            for (int q = 0; q < NF; ++q) f[q] = 0.f;
-            if (contrib) {
-                const float4 A = sp[e].a;
-                const float4 B = sp[e].b;
-                const float dx = pxc - A.x, dy = pyc - A.y;
-                const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                const float G = __expf(power);
-                const float raw = B.y * G;
-                const float alpha = fminf(cfg.alpha_max, raw);
-                contrib = !(power > 0.f) && !(alpha < cfg.alpha_min);
+                for (int s = 0; s < NS; ++s) f[s] = 0.f;
                 if (contrib) {
-                    T = T / (1.f - alpha);
-                    const float w = alpha * T;
-                    const float4 Cc = sp[e].c;
-                    const float dLda = T * ((Cc.x - A0) * gC0 + (Cc.y - A1) * gC1 + (Cc.z - A2) * gC2 +
-                                            (B.z - AD) * gD);
-                    A0 = alpha * Cc.x + (1.f - alpha) * A0;
-                    A1 = alpha * Cc.y + (1.f - alpha) * A1;
-                    A2 = alpha * Cc.z + (1.f - alpha) * A2;
-                    AD = alpha * B.z + (1.f - alpha) * AD;
-                    f[6] = w * gD;
-                    if (MODE == GS_MAP) {
-                        f[8] = w * gC0;
-                        f[9] = w * gC1;
-                        f[10] = w * gC2;
-                    }
-                    if (!(raw > cfg.alpha_max)) {
-                        if (MODE == GS_MAP) f[5] = G * dLda;
-                        const float dp = alpha * dLda;
-                        f[2] = -0.5f * dx * dx * dp;
-                        f[3] = -dx * dy * dp;
-                        f[4] = -0.5f * dy * dy * dp;
-                        f[0] = (A.z * dx + A.w * dy) * dp;
-                        f[1] = (A.w * dx + B.x * dy) * dp;
+                    const float4 A = sp[e].a;
+                    const float4 B = sp[e].b;
+                    const float dx = pxc - A.x, dy = pyc - A.y;
+                    const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
+                    const float G = __expf(power);
+                    const float raw = B.y * G;
+                    const float alpha = fminf(cfg.alpha_max, raw);
+                    contrib = !(power > 0.f) && !(alpha < cfg.alpha_min);
+                    if (contrib) {
+                        T = T / (1.f - alpha);
+                        const float w = alpha * T;
+                        const float4 Cc = sp[e].c;
+                        const float dLda = T * ((Cc.x - A0) * gC0 + (Cc.y - A1) * gC1 + (Cc.z - A2) * gC2 +
+                                                (B.z - AD) * gD);
+                        A0 = alpha * Cc.x + (1.f - alpha) * A0;
+                        A1 = alpha * Cc.y + (1.f - alpha) * A1;
+                        A2 = alpha * Cc.z + (1.f - alpha) * A2;
+                        AD = alpha * B.z + (1.f - alpha) * AD;
+                        if (MODE == GS_MAP) {
+                            f[6] = w * gD;
+                            f[7] = w * gC0;
+                            f[8] = w * gC1;
+                            f[9] = w * gC2;
+                        } else {
+                            f[5] = w * gD;
+                        }
+                        if (!(raw > cfg.alpha_max)) {
+                            if (MODE == GS_MAP) f[5] = G * dLda;
+                            const float dp = alpha * dLda;
+                            f[2] = -0.5f * dx * dx * dp;
+                            f[3] = -dx * dy * dp;
+                            f[4] = -0.5f * dy * dy * dp;
+                            f[0] = (A.z * dx + A.w * dy) * dp;
+                            f[1] = (A.w * dx + B.x * dy) * dp;
+                        }
                     }
                 }
-            }
-            const unsigned ball = __ballot_sync(0xffffffffu, contrib);
-            if (ball == 0u) continue;
-            if (__popc(ball) == 1) {
-                if (contrib) {
-#pragma unroll
-                    for (int q = 0; q < NF; ++q)
-                        if (q != 7 && q != 11 && (MODE == GS_MAP || (q != 5 && q < 8))) atomicAdd(&acc[e][q], f[q]);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < NF; ++q) {
-                    if (q == 7 || q == 11 || (MODE != GS_MAP && (q == 5 || q >= 8))) continue;
-                    const float v = warp_sum(f[q]);
-                    if (lane == 0) atomicAdd(&acc[e][q], v);
+                if (__ballot_sync(0xffffffffu, contrib) == 0u) continue;
+                const float v = warp_reduce_scatter<NS, LOG>(f);
+                if ((lane & ((1 << SHIFT) - 1)) == 0) {
+                    const int s = lane >> SHIFT;
+                    if (slot_col<MODE>(s) >= 0) atomicAdd(&acc[e][s], v);
                 }
             }
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < n_in * NF; q += R_THREADS) {
+        for (int q = threadIdx.x; q < n_in * NS; q += R_THREADS) {
             const float v = (&acc[0][0])[q];
-            if (v != 0.f) atomicAdd(grad2d + (size_t)sid[q / NF] * NF + (q % NF), v);
+            const int col = slot_col<MODE>(q % NS);
+            if (v != 0.f && col >= 0) atomicAdd(grad2d + (size_t)sid[q / NS] * GS_GRAD2D_STRIDE + col, v);
         }
         __syncthreads();
         hi = lo;
@@ -298,8 +382,9 @@ static gs_status render_checks(const gs_config* cfg, const gs_camera* cam, int r
 }
 
 extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
-                                   int64_t n, const uint32_t* vals, const uint32_t* tile_ranges, float* rgb,
-                                   float* depth, float* t_final, uint32_t* last_idx, gs_stream stream) {
+                                   int64_t n, const uint32_t* vals, const uint32_t* tile_ranges,
+                                   const uint32_t* tile_order, float* rgb, float* depth, float* t_final,
+                                   uint32_t* last_idx, gs_stream stream) {
     gs_status s;
     if ((s = render_checks(cfg, cam, rec_dtype, splats, n)) != GS_OK) return s;
     if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
@@ -307,13 +392,12 @@ extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, i
     const Grid g = make_grid(*cam);
     const unsigned nt = (unsigned)(g.TX * g.TY);
     cudaStream_t st = (cudaStream_t)stream;
-    const void* sp = splats;
-    if (rec_dtype == GS_F32)
-        k_render_fwd<GS_F32><<<nt, R_THREADS, 0, st>>>(*cfg, g, sp, vals, tile_ranges, rgb, depth, t_final, last_idx);
-    else if (rec_dtype == GS_BF16)
-        k_render_fwd<GS_BF16><<<nt, R_THREADS, 0, st>>>(*cfg, g, sp, vals, tile_ranges, rgb, depth, t_final, last_idx);
-    else
-        k_render_fwd<GS_F16><<<nt, R_THREADS, 0, st>>>(*cfg, g, sp, vals, tile_ranges, rgb, depth, t_final, last_idx);
+#define GS_RF(DT) \
+    k_render_fwd<DT><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx)
+    if (rec_dtype == GS_F32) GS_RF(GS_F32);
+    else if (rec_dtype == GS_BF16) GS_RF(GS_BF16);
+    else GS_RF(GS_F16);
+#undef GS_RF
     return check_launch("k_render_fwd");
 }
 
@@ -340,10 +424,10 @@ size_t gs_project_bwd_ws(int64_t n);
 
 extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* gsn,
                                    int rec_dtype, const void* splats, const uint32_t* vals,
-                                   const uint32_t* tile_ranges, const float* t_final, const uint32_t* last_idx,
-                                   const float* d_rgb, const float* d_depth, int mode, float* grad2d,
-                                   gs_grads* grads, double* pose_grad6, float* score_terms, void* workspace,
-                                   size_t* workspace_bytes, gs_stream stream) {
+                                   const uint32_t* tile_ranges, const uint32_t* tile_order, const float* t_final,
+                                   const uint32_t* last_idx, const float* d_rgb, const float* d_depth, int mode,
+                                   float* grad2d, gs_grads* grads, double* pose_grad6, float* score_terms,
+                                   void* workspace, size_t* workspace_bytes, gs_stream stream) {
     if (!gsn) return set_error(GS_ERR_INVALID_ARG, "gaussians is NULL");
     gs_status s;
     const int64_t n = gsn->n;
@@ -359,12 +443,13 @@ extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, c
         return set_error(GS_ERR_INVALID_ARG, "an input or grad2d pointer is NULL");
     if (n > 0 && ((uintptr_t)grad2d & 15)) return set_error(GS_ERR_INVALID_ARG, "grad2d not 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
-    if (n > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * NF * (size_t)n, st) != cudaSuccess)
+    if (n > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_STRIDE * (size_t)n, st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset grad2d");
     const Grid g = make_grid(*cam);
     const unsigned nt = (unsigned)(g.TX * g.TY);
-#define GS_RB(DT, MD) \
-    k_render_bwd<DT, MD><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, t_final, last_idx, d_rgb, d_depth, grad2d)
+#define GS_RB(DT, MD)                                                                                              \
+    k_render_bwd<DT, MD><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, t_final, last_idx, \
+                                                   d_rgb, d_depth, grad2d)
     if (n > 0) {
         if (mode == GS_MAP) {
             if (rec_dtype == GS_F32) GS_RB(GS_F32, GS_MAP);

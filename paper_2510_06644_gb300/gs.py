@@ -64,12 +64,12 @@ _SIGS = {
     "gs_default_config": ([_P], None),
     "gs_version": ([], C.c_char_p),
     "gs_project": ([_P, _P, _P, C.c_int, _P, _P], C.c_int),
-    "gs_bin_sort": ([_P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_bin_sort": ([_P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_bin_count": ([_P, C.c_int, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
-    "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_loss_l1": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "gs_render_bwd": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P, _P,
-                       _P, _P], C.c_int),
+    "gs_render_bwd": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P,
+                       _P, _P, _P], C.c_int),
     "gs_project_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_prune": ([_P, _P, C.c_int64, _P, C.c_int, _P, C.c_float, C.c_int64, _P, _P, _P, _P, _P],
                  C.c_int),
@@ -207,12 +207,14 @@ def gs_project(cfg, cam, g, rec_dtype=GS_F32, splats=None, stream=None):
 def gs_bin_sort_workspace(cam, rec_dtype, n, capacity):
     nb = C.c_size_t(0)
     _check(lib().gs_bin_sort(C.byref(cam), rec_dtype, None, int(n), int(capacity), None, C.byref(nb),
-                             None, None, None, None, None), "gs_bin_sort(size)")
+                             None, None, None, None, None, None), "gs_bin_sort(size)")
     return nb.value
 
 
 def gs_bin_sort(cam, splats, n, capacity, rec_dtype=GS_F32, ws=None, keys=None, vals=None, n_keys=None,
-                ranges=None, stream=None):
+                ranges=None, order=None, stream=None):
+    """Returns (keys, vals, n_keys, ranges, order); order is the heavy-first
+    tile permutation (allocated unless given)."""
     dev = splats.device
     _, _, TX, TY = grid(cam)
     need = gs_bin_sort_workspace(cam, rec_dtype, n, capacity)
@@ -222,11 +224,12 @@ def gs_bin_sort(cam, splats, n, capacity, rec_dtype=GS_F32, ws=None, keys=None, 
     vals = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev) if vals is None else vals
     n_keys = torch.zeros(1, dtype=torch.int64, device=dev) if n_keys is None else n_keys
     ranges = torch.empty((TX * TY, 2), dtype=torch.int32, device=dev) if ranges is None else ranges
+    order = torch.empty(TX * TY, dtype=torch.int32, device=dev) if order is None else order
     nb = C.c_size_t(ws.numel())
     _check(lib().gs_bin_sort(C.byref(cam), rec_dtype, _ptr(splats), int(n), int(capacity), _ptr(ws),
-                             C.byref(nb), _ptr(keys), _ptr(vals), _ptr(n_keys), _ptr(ranges),
+                             C.byref(nb), _ptr(keys), _ptr(vals), _ptr(n_keys), _ptr(ranges), _ptr(order),
                              _stream(stream)), "gs_bin_sort")
-    return keys, vals, n_keys, ranges
+    return keys, vals, n_keys, ranges, order
 
 
 def gs_bin_count(cam, splats, n, rec_dtype=GS_F32, stream=None):
@@ -241,7 +244,7 @@ def gs_bin_count(cam, splats, n, rec_dtype=GS_F32, stream=None):
     return out
 
 
-def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None, stream=None):
+def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None, order=None, stream=None):
     Ws, Hs, _, _ = grid(cam)
     dev = splats.device
     if out is None:
@@ -249,7 +252,7 @@ def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None,
                "t_final": torch.empty((Hs, Ws), device=dev),
                "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=dev)}
     _check(lib().gs_render_fwd(C.byref(cfg), C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(vals),
-                               _ptr(ranges), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["t_final"]),
+                               _ptr(ranges), _ptr(order), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["t_final"]),
                                _ptr(out["last_idx"]), _stream(stream)), "gs_render_fwd")
     return out
 
@@ -273,7 +276,8 @@ def gs_project_bwd_workspace(cfg, cam, g):
 
 
 def gs_render_bwd(cfg, cam, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, mode=GS_MAP,
-                  rec_dtype=GS_F32, grad2d=None, grads=None, pose=None, score=None, ws=None, stream=None):
+                  rec_dtype=GS_F32, grad2d=None, grads=None, pose=None, score=None, ws=None, order=None,
+                  stream=None):
     """grads: dict of output tensors (or None); pose: float64 [6] tensor or
     None; score: float32 [n,2] tensor or None."""
     n = int(g["means"].shape[0])
@@ -287,7 +291,8 @@ def gs_render_bwd(cfg, cam, g, splats, vals, ranges, t_final, last_idx, d_rgb, d
         ws = workspace(need, dev)
     nb = C.c_size_t(ws.numel())
     _check(lib().gs_render_bwd(C.byref(cfg), C.byref(cam), C.byref(gs_g), rec_dtype, _ptr(splats), _ptr(vals),
-                               _ptr(ranges), _ptr(t_final), _ptr(last_idx), _ptr(d_rgb), _ptr(d_depth), mode,
+                               _ptr(ranges), _ptr(order), _ptr(t_final), _ptr(last_idx), _ptr(d_rgb), _ptr(d_depth),
+                               mode,
                                _ptr(grad2d), C.byref(gr) if gr is not None else None, _ptr(pose),
                                _ptr(score), _ptr(ws), C.byref(nb), _stream(stream)), "gs_render_bwd")
     return grad2d

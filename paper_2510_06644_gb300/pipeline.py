@@ -43,6 +43,7 @@ class Rasterizer:
         self._grid = (Ws, Hs, TX, TY)
         d = self.device
         self.ranges = torch.empty((TX * TY, 2), dtype=torch.int32, device=d)
+        self.order = torch.empty(TX * TY, dtype=torch.int32, device=d)
         self.img = {"rgb": torch.empty((3, Hs, Ws), device=d), "depth": torch.empty((Hs, Ws), device=d),
                     "t_final": torch.empty((Hs, Ws), device=d),
                     "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=d)}
@@ -70,8 +71,9 @@ class Rasterizer:
         self.set_grid(cam_s)
         gs.gs_project(self.cfg, cam_s, g, self.rec_dtype, self.splats)
         gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
-                       keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges)
-        gs.gs_render_fwd(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, self.rec_dtype, out=self.img)
+                       keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges, order=self.order)
+        gs.gs_render_fwd(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, self.rec_dtype, out=self.img,
+                         order=self.order)
         return self.img
 
     def loss_grad(self, cam, target_rgb, target_depth):
@@ -84,7 +86,7 @@ class Rasterizer:
         gs.gs_render_bwd(self.cfg, cam_s, g, self.splats, self.vals, self.ranges, self.img["t_final"],
                          self.img["last_idx"], d_rgb, d_depth, mode, self.rec_dtype, grad2d=self.grad2d,
                          grads=grads, pose=self.pose if want_pose else None,
-                         score=self.score if want_score else None, ws=self._bwd_ws(cam_s, g))
+                         score=self.score if want_score else None, ws=self._bwd_ws(cam_s, g), order=self.order)
         return self.grad2d
 
     def step(self, g, cam, target_rgb, target_depth, mode=gs.GS_TRACK, grads=None):

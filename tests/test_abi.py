@@ -59,6 +59,20 @@ def test_argument_errors_are_synchronous(built_lib):
                      "W": 0, "H": 10})
     nb = ctypes.c_size_t(0)
     rc = gs.lib().gs_bin_sort(ctypes.byref(cam), 0, None, 10, 100, None, ctypes.byref(nb), None, None, None,
-                              None, None)
+                              None, None, None)
     assert rc == gs.GS_ERR_INVALID_ARG
     assert b"camera" in gs.lib().gs_last_error()
+
+
+def test_workspace_size_queries_need_no_device(built_lib):
+    """A NULL workspace only asks for the size: pure host arithmetic."""
+    from paper_2510_06644_gb300 import gs
+    cam = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 525, "fy": 525, "cx": 320,
+                     "cy": 240, "W": 640, "H": 480})
+    small = gs.gs_bin_sort_workspace(cam, gs.GS_F32, 1000, 10_000)
+    big = gs.gs_bin_sort_workspace(cam, gs.GS_F32, 200_000, 1_000_000)
+    assert 0 < small < big and big % 256 == 0
+    # alternate key/value buffers dominate: 12 bytes per key of capacity
+    assert big >= 12 * 1_000_000
+    with pytest.raises(gs.GsError):
+        gs.gs_bin_sort_workspace(cam, gs.GS_F32, 10, 1 << 30)   # capacity limit 2^30

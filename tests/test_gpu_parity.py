@@ -41,9 +41,16 @@ def O():
 def gpu_bin(G, cam, rec, n, cap=None):
     cs = G.camera(cam)
     cap = cap if cap is not None else max(8 * n, 1024)
-    keys, vals, nk, ranges = G.gs_bin_sort(cs, rec, n, cap)
+    keys, vals, nk, ranges, order = G.gs_bin_sort(cs, rec, n, cap)
     torch.cuda.synchronize()
     k = int(nk.item())
+    # the tile order is a permutation, longest lists first by log2 group
+    o = np_of(order).astype(np.int64)
+    rr = np_of(ranges).view(np.uint32).astype(np.int64)
+    assert np.array_equal(np.sort(o), np.arange(rr.shape[0]))
+    grp = np.floor(np.log2(rr[o, 1] - rr[o, 0] + 1))
+    assert np.all(np.diff(grp) <= 0)
+    gpu_bin.order = order
     return np_of(keys[:k]).view(np.uint64), np_of(vals[:k]).view(np.uint32), np_of(ranges).view(np.uint32), vals, ranges
 
 
@@ -129,7 +136,7 @@ def test_bin_sort_capacity_overflow_is_reported(G):
     true_n = int(G.gs_bin_count(cs, pack_splats(s), 4000).item())
     assert true_n > 1000
     G.gs_status_reset()
-    keys, vals, nk, ranges = G.gs_bin_sort(cs, pack_splats(s), 4000, 1000)
+    keys, vals, nk, ranges, _ = G.gs_bin_sort(cs, pack_splats(s), 4000, 1000)
     code, _ = G.gs_status_poll(blocking=True)
     assert code == G.GS_ERR_CAPACITY
     assert int(nk.item()) == true_n
@@ -145,7 +152,7 @@ def render_gpu(G, cam, rec, n, cfg=None):
     cfg = cfg or G.default_config()
     cs = G.camera(cam)
     _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
-    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges)
+    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges, order=gpu_bin.order)
     torch.cuda.synchronize()
     return {k: np_of(v) for k, v in out.items()}, vals, ranges
 
@@ -199,14 +206,15 @@ def test_render_bwd_matches_oracle(G, O, n, W, H, seed, mode):
     cfg = G.default_config()
     cs = G.camera(cam)
     _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
-    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges)
+    order = gpu_bin.order if mode == "map" else None   # both launch orders are exercised
+    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges, order=order)
     d_rgb, d_dep = S.image_grads(W, H, seed + 100)
     gdummy = dev({"means": np.zeros((n, 3), np.float32), "log_scales": np.zeros((n, 3), np.float32),
                   "quats": np.zeros((n, 4), np.float32), "opacity_logit": np.zeros(n, np.float32),
                   "rgb": np.zeros((n, 3), np.float32)})
     md = G.GS_MAP if mode == "map" else G.GS_TRACK
     g2 = G.gs_render_bwd(cfg, cs, gdummy, rec, vals, ranges, out["t_final"], out["last_idx"],
-                         torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=md)
+                         torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=md, order=order)
     torch.cuda.synchronize()
     g2 = np_of(g2)
     ref = O.render_bwd(s, cam, d_rgb, d_dep)
