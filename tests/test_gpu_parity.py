@@ -104,6 +104,8 @@ def test_project_matches_oracle(G, O, case):
     (5000, 200, 120, 4, 2, 4, (0.6, 60.0)),      # anisotropic strides, large radii
     (60000, 1200, 680, 1, 1, 5, (0.6, 8.0)),     # 3225 tiles -> 6 passes
     (1, 40, 40, 1, 1, 6, (0.6, 3.0)),
+    (30000, 40, 36, 1, 1, 7, (0.6, 20.0)),       # buckets of 10k-30k keys: shared-memory runs + merges
+    (9000, 16, 16, 1, 1, 8, (0.6, 40.0)),        # one bucket just above the 8192-key run
 ])
 def test_bin_sort_bit_exact(G, O, n, W, H, sx, sy, seed, sig):
     cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
