@@ -279,6 +279,27 @@ gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, const gs_ga
                          float* score_terms, void* workspace, size_t* workspace_bytes,
                          gs_stream stream);
 
+/* Variant of gs_project_bwd for callers that cannot allocate device memory
+ * (no counterpart in the paper; it exists for integrations such as a
+ * real-time tracking thread that runs under a fixed memory budget, or a host
+ * framework that owns every allocation and offers the library no allocator).
+ * Same arguments and results as gs_project_bwd, minus the workspace: the
+ * scratch (per-block pose partials and a ticket) lives in a static device
+ * array of GS_NOALLOC_SCRATCH_BYTES (~769 KB) that every device which loads
+ * the library holds until the process exits.  n is limited to
+ * GS_NOALLOC_MAX_GAUSSIANS; a larger n returns GS_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (different
+ * streams, or different host threads, without ordering) race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+#define GS_NOALLOC_MAX_GAUSSIANS 4194304
+#define GS_NOALLOC_SCRATCH_BYTES (((GS_NOALLOC_MAX_GAUSSIANS / 256) * 48 + 511) / 256 * 256)
+gs_status gs_project_bwd_noalloc(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                                 const float* grad2d, gs_grads* grads, double* pose_grad6,
+                                 float* score_terms, gs_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* A-9 Gradient-reuse pruning (Sec. 4.1, Eq. 7)                              */
 /* ---------------------------------------------------------------------- */

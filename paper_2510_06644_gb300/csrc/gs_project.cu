@@ -504,3 +504,45 @@ extern "C" gs_status gs_pose_update(float* pose, const double* pose_grad6, float
     k_pose_update<<<1, 32, 0, (cudaStream_t)stream>>>(pose, pose_grad6, adam, lr_trans, lr_rot, beta1, beta2, eps);
     return check_launch("k_pose_update");
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of gs_project_bwd (see include/gs.h)
+// ---------------------------------------------------------------------------
+// Fixed scratch for gs_project_bwd_noalloc: room for the per-block pose
+// partials of GS_NOALLOC_MAX_GAUSSIANS Gaussians plus the ticket word.  In
+// host code this name is only a stand-in: the kernel gets the device address
+// looked up below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GS_NOALLOC_SCRATCH_BYTES];
+
+static gs_status noalloc_scratch(void** out) {
+    static void* cache[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return set_error(GS_ERR_CUDA, "no current device");
+    if (!cache[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return set_error(GS_ERR_CUDA, "scratch address: %s", cudaGetErrorString(e));
+        cache[dev] = p;
+    }
+    *out = cache[dev];
+    return GS_OK;
+}
+
+extern "C" gs_status gs_project_bwd_noalloc(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                                            const float* grad2d, gs_grads* grads, double* pose_grad6,
+                                            float* score_terms, gs_stream stream) {
+    if (!g) return set_error(GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n > (int64_t)GS_NOALLOC_MAX_GAUSSIANS)
+        return set_error(GS_ERR_INVALID_ARG, "n = %lld exceeds GS_NOALLOC_MAX_GAUSSIANS = %d", (long long)g->n,
+                         GS_NOALLOC_MAX_GAUSSIANS);
+    size_t need = 0;
+    gs_status s = gs_project_bwd(cfg, cam, g, grad2d, grads, pose_grad6, score_terms, nullptr, &need, stream);
+    if (s != GS_OK) return s;
+    if (need > (size_t)GS_NOALLOC_SCRATCH_BYTES)
+        return set_error(GS_ERR_INVALID_ARG, "scratch of %zu bytes exceeds the static %d", need, GS_NOALLOC_SCRATCH_BYTES);
+    void* scratch = nullptr;
+    if ((s = noalloc_scratch(&scratch)) != GS_OK) return s;
+    size_t have = (size_t)GS_NOALLOC_SCRATCH_BYTES;
+    return gs_project_bwd(cfg, cam, g, grad2d, grads, pose_grad6, score_terms, scratch, &have, stream);
+}

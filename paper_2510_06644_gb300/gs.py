@@ -71,6 +71,7 @@ _SIGS = {
     "gs_render_bwd": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P,
                        _P, _P, _P], C.c_int),
     "gs_project_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_project_bwd_noalloc": ([_P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_prune": ([_P, _P, C.c_int64, _P, C.c_int, _P, C.c_float, C.c_int64, _P, _P, _P, _P, _P],
                  C.c_int),
     "gs_change_ratio": ([_P, C.c_int, _P, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
@@ -308,6 +309,16 @@ def gs_project_bwd(cfg, cam, g, grad2d, grads=None, pose=None, score=None, ws=No
     _check(lib().gs_project_bwd(C.byref(cfg), C.byref(cam), C.byref(gs_g), _ptr(grad2d),
                                 C.byref(gr) if gr is not None else None, _ptr(pose), _ptr(score), _ptr(ws),
                                 C.byref(nb), _stream(stream)), "gs_project_bwd")
+
+
+def gs_project_bwd_noalloc(cfg, cam, g, grad2d, grads=None, pose=None, score=None, stream=None):
+    """gs_project_bwd without a workspace: the library's static scratch is
+    used (no device allocation at all; calls must not overlap on the GPU)."""
+    gs_g = gaussians(g)
+    gr = grads_struct(grads) if grads is not None else None
+    _check(lib().gs_project_bwd_noalloc(C.byref(cfg), C.byref(cam), C.byref(gs_g), _ptr(grad2d),
+                                        C.byref(gr) if gr is not None else None, _ptr(pose), _ptr(score),
+                                        _stream(stream)), "gs_project_bwd_noalloc")
 
 
 def gs_prune(cfg, score, mask, iter_in_interval, K, change_ratio=0.0, max_select=None, compact_map=None,
