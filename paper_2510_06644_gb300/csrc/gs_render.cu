@@ -58,14 +58,42 @@ __device__ __forceinline__ PixelMap map_pixel(const Grid& g, int tile) {
     return m;
 }
 
+// Pixel box of a staged Gaussian: its integer 3-sigma box (the definition of
+// which pixels see it), shrunk to the pixels whose centre lies in the
+// axis-aligned bounding box of the ellipse where alpha can reach alpha_min,
+//     d^T Q d <= 2 ln(opacity / alpha_min),  half extents
+//     sqrt(2 ln(opacity / alpha_min) (Q^-1)_xx), ... (Q = conic),
+// widened against rounding (1e-4 added to the log threshold, a relative
+// 1e-3 and 1e-3 px on the extent).  Every pixel it drops would fail the alpha
+// test, so the image and gradients are unchanged; the compositing loops just
+// visit fewer entries.  A Gaussian whose opacity is clearly below alpha_min
+// gets an empty box.  Forward and backward use the same box.
+__device__ __forceinline__ int4 pixel_box(const Splat& v, float alpha_min) {
+    const int xi = pix_floor(v.x), yi = pix_floor(v.y), r = v.radius;
+    int4 box = make_int4(xi - r, xi + r, yi - r, yi + r);
+    const float det = v.ca * v.cc - v.cb * v.cb;
+    if (!(det > 0.f) || !(v.op > 0.f) || !(alpha_min > 0.f)) return box;
+    const float thr = logf(v.op / alpha_min);
+    if (thr < -1e-4f) return make_int4(1, 0, 1, 0);  // empty: opacity < alpha_min
+    const float t2 = 2.f * (fmaxf(thr, 0.f) + 1e-4f);
+    const float ex = sqrtf(t2 * v.cc / det) * 1.001f + 1e-3f;
+    const float ey = sqrtf(t2 * v.ca / det) * 1.001f + 1e-3f;
+    if (!(ex < 1e8f) || !(ey < 1e8f)) return box;
+    // pixel p qualifies when |p + 0.5 - x| <= ex
+    box.x = max(box.x, (int)ceilf(v.x - ex - 0.5f));
+    box.y = min(box.y, (int)floorf(v.x + ex - 0.5f));
+    box.z = max(box.z, (int)ceilf(v.y - ey - 0.5f));
+    box.w = min(box.w, (int)floorf(v.y + ey - 0.5f));
+    return box;
+}
+
 template <int DT>
-__device__ __forceinline__ void stage(const void* splats, uint32_t gid, StagedSplat& s) {
+__device__ __forceinline__ void stage(const void* splats, uint32_t gid, float alpha_min, StagedSplat& s) {
     const Splat v = load_splat<DT>(splats, gid);
     s.a = make_float4(v.x, v.y, v.ca, v.cb);
     s.b = make_float4(v.cc, v.op, v.depth, 0.f);
     s.c = make_float4(v.r, v.g, v.b, 0.f);
-    const int xi = pix_floor(v.x), yi = pix_floor(v.y), r = v.radius;
-    s.box = make_int4(xi - r, xi + r, yi - r, yi + r);
+    s.box = pixel_box(v, alpha_min);
 }
 
 // Bit e of word q set when staged entry 32q + e (below `limit`) meets the
@@ -106,7 +134,7 @@ __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g,
     for (uint32_t b = start; b < end; b += R_BATCH) {
         if (__syncthreads_count(done) == R_THREADS) break;
         const int n_in = (int)min((uint32_t)R_BATCH, end - b);
-        if ((int)threadIdx.x < n_in) stage<DT>(splats, __ldg(vals + b + threadIdx.x), sp[threadIdx.x]);
+        if ((int)threadIdx.x < n_in) stage<DT>(splats, __ldg(vals + b + threadIdx.x), cfg.alpha_min, sp[threadIdx.x]);
         __syncthreads();
         if (!__all_sync(0xffffffffu, done)) {
             unsigned mask[R_MASKW];
@@ -283,7 +311,7 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
         if ((int)threadIdx.x < n_in) {
             const uint32_t gid = __ldg(vals + lo + threadIdx.x);
             sid[threadIdx.x] = gid;
-            stage<DT>(splats, gid, sp[threadIdx.x]);
+            stage<DT>(splats, gid, cfg.alpha_min, sp[threadIdx.x]);
         }
         for (int q = threadIdx.x; q < R_BATCH * NS; q += R_THREADS) (&acc[0][0])[q] = 0.f;
         __syncthreads();

@@ -1,0 +1,130 @@
+"""Precision form (16-bit record storage): conic, opacity and colour stored as
+bf16 or fp16, means, depths and radii in float32, all compositing and
+accumulation in float32, the pose-gradient combination compensated in
+float64.  Each output's error against the FP64 oracle is measured and printed
+(`pytest -s`), and bounded by a figure derived from the storage precision:
+
+  u = unit roundoff of the storage type (bf16 2^-8, fp16 2^-11).  Colour and
+  opacity carry a relative error <= u; a conic entry <= u, so the exponent
+  -(a dx^2 + 2 b dx dy + c dy^2)/2 carries <= u |power| with |power| <=
+  ln(255 o) < 5.6 where alpha >= 1/255.  alpha = o exp(power) then has a
+  relative error <= u (1 + 5.6) and a blended colour <= ~8u, which the test
+  rounds up to 16u for maxima (and also covers the rare alpha-threshold flips)
+  and 2u for means.  Gradients are held to 16u relative L2.
+
+Binning reads only the float32 fields, so keys, order and ranges are
+identical to the float32 path.
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+from tests.gpu_helpers import dev, np_of, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+U = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_06644_gb300 import build
+    build.build()
+    from paper_2510_06644_gb300 import gs
+    return gs
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def dt_of(G, name):
+    return {"bf16": G.GS_BF16, "fp16": G.GS_F16}[name]
+
+
+@pytest.mark.parametrize("name", ["bf16", "fp16"])
+def test_records_round_the_float32_fields(G, name):
+    g = S.surface_scene(20000, seed=71)
+    cam = S.camera(320, 240, 260.0)
+    cfg = G.default_config()
+    gd = dev(g)
+    r32 = G.gs_project(cfg, G.camera(cam), gd, G.GS_F32)
+    r16 = G.gs_project(cfg, G.camera(cam), gd, dt_of(G, name))
+    f32 = G.splat_fields(r32, G.GS_F32)
+    f16 = G.splat_fields(r16, dt_of(G, name))
+    for k in ("uv", "depth", "radius"):
+        assert torch.equal(f16[k], f32[k]), k
+    tt = torch.bfloat16 if name == "bf16" else torch.float16
+    for k in ("conic", "opacity", "rgb"):
+        assert torch.equal(f16[k], f32[k].to(tt).float()), k
+    t32 = f32["touched"]
+    assert torch.equal(f16["touched"].long(), torch.clamp(t32.long(), max=65535))
+
+
+@pytest.mark.parametrize("name", ["bf16", "fp16"])
+def test_binning_identical_to_float32(G, name):
+    g = S.surface_scene(30000, seed=72)
+    cam = S.camera(333, 197, 260.0)
+    cfg = G.default_config()
+    gd = dev(g)
+    cs = G.camera(cam)
+    out = {}
+    for dtn, dt in (("f32", G.GS_F32), (name, dt_of(G, name))):
+        rec = G.gs_project(cfg, cs, gd, dt)
+        keys, vals, nk, ranges, _ = G.gs_bin_sort(cs, rec, 30000, 400000, dt)
+        k = int(nk.item())
+        out[dtn] = (np_of(keys[:k]), np_of(vals[:k]), np_of(ranges))
+    for a, b in zip(out["f32"], out[name]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["bf16", "fp16"])
+@pytest.mark.parametrize("scene", ["tiny", "slam"])
+def test_errors_against_fp64_oracle(G, O, name, scene):
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    if scene == "tiny":
+        g = S.tiny_scene(seed=1000)
+        cam = S.tiny_camera()
+        trgb, tdep = S.target_image(96, 72, seed=1001)
+    else:
+        g = S.surface_scene(60000, seed=73)
+        cam = S.perturbed_pose(S.camera(320, 240, 260.0), seed=74, trans=0.02, rot_deg=1.0)
+        trgb, tdep = S.target_image(320, 240, seed=75, depth_range=(1.0, 6.0))
+    u = U[name]
+    n = g["means"].shape[0]
+    gd = dev(g)
+    r = Rasterizer(n, cam, rec_dtype=dt_of(G, name))
+    grads = {k: torch.empty_like(gd[k]) for k in ("means", "log_scales", "quats", "opacity_logit", "rgb")}
+    pr, img = O.forward(g, cam)
+    L, dr, dd = O.loss_l1(img["rgb"], img["depth"], trgb, tdep)
+    _, _, ref = O.forward_backward(g, cam, dr, dd)
+    r.forward(gd, cam)
+    # both sides differentiate the oracle's image gradient, so the comparison
+    # isolates the renderer from sign flips of near-zero L1 residuals
+    r.backward(gd, cam, torch.from_numpy(dr.astype(np.float32)).cuda(),
+               torch.from_numpy(dd.astype(np.float32)).cuda(), mode=G.GS_MAP, grads=grads)
+    r.check()
+    errs = {}
+    e_rgb = np.abs(np_of(r.img["rgb"]) - img["rgb"])
+    errs["rgb_max"], errs["rgb_mean"] = float(e_rgb.max()), float(e_rgb.mean())
+    zmax = float(np.abs(img["depth"]).max())
+    e_d = np.abs(np_of(r.img["depth"]) - img["depth"]) / max(zmax, 1.0)
+    errs["depth_max_rel"], errs["depth_mean_rel"] = float(e_d.max()), float(e_d.mean())
+    e_t = np.abs(np_of(r.img["t_final"]) - img["T"])
+    errs["T_max"] = float(e_t.max())
+    for k in grads:
+        errs["d_" + k] = rel_l2(np_of(grads[k]), ref[k])
+    errs["pose"] = rel_l2(np_of(r.pose), ref["pose"])
+    print(f"\n[{name} {scene}] u={u:.2e} " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert errs["rgb_max"] <= 16 * u and errs["rgb_mean"] <= 2 * u
+    assert errs["depth_max_rel"] <= 16 * u and errs["depth_mean_rel"] <= 2 * u
+    assert errs["T_max"] <= 16 * u
+    for k in list(grads) + ["pose"]:
+        key = "d_" + k if k != "pose" else "pose"
+        assert errs[key] <= 16 * u, (key, errs[key])
