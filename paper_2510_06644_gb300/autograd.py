@@ -84,7 +84,6 @@ class GsRenderFn(torch.autograd.Function):
         ctx.rast = rast if store else None
         ctx.n_keys = n_keys
         ctx.save_for_backward(*[g[k] for k in PARAMS])
-        ctx.mark_non_differentiable()
         return rgb, depth
 
     @staticmethod
