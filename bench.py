@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--skip-cpu-baseline", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="only run warmup + steps tracking iterations eagerly (for ncu launch lists), print nothing")
+    p.add_argument("--serving", action="store_true", help="run only the serving comparison and print its line")
+    p.add_argument("--skip-serving", action="store_true")
+    p.add_argument("--serving-frames", type=int, default=6)
     return p.parse_args()
 
 
@@ -148,6 +151,43 @@ def cpu_baseline(budget_s=20.0):
                       f"(projection, binning+sort, forward, L1 loss, backward, backward projection + pose); "
                       f"median {t:.2f} s/iter",
             "mpix_per_s": W_IMG * H_IMG / t / 1e6}
+
+
+def serving_bench(frames=6, sessions=16):
+    """Serving workload: 16 concurrent sessions, maps log-uniform in
+    50k-1.5M Gaussians, resolutions from {320x240, 640x480, 1200x680},
+    Poisson frames at 30 Hz, 40 tracking iterations per frame and a mapping
+    iteration on every 5th (key)frame, HBM budget 150 GB.  The same sessions
+    (state restored in between) run through the plain per-session loop and
+    through continuous batching."""
+    import torch
+    from paper_2510_06644_gb300 import serve as SV
+    specs = SV.make_session_specs(sessions, n_frames=frames)
+    arrivals = SV.poisson_arrivals(specs)
+    t0 = time.perf_counter()
+    sess = []
+    for sp in specs:
+        scene, cams = SV.session_inputs(sp)
+        s = SV.Session(sp, scene, cams)
+        s.prepare()
+        sess.append(s)
+    setup = time.perf_counter() - t0
+    snaps = [s.snapshot() for s in sess]
+    out = {}
+    for mode in ("plain", "batched"):
+        for s, sn in zip(sess, snaps):
+            s.restore(sn)
+            s.poses = []
+        torch.cuda.synchronize()
+        srv = SV.Server(sess, arrivals, mode=mode, slots=16, budget_bytes=150 << 30)
+        out[mode] = srv.run()
+    return {"workload": "16 sessions, maps 50k-1.5M log-uniform, {320x240,640x480,1200x680}, 30 Hz Poisson, "
+                        "40 tracking iters/frame + mapping every 5th frame, budget 150 GB",
+            "frames_per_session": frames, "gaussians": [s.n for s in specs],
+            "resolutions": [f"{s.W}x{s.H}" for s in specs], "setup_s": setup,
+            "plain": out["plain"], "batched": out["batched"],
+            "speedup_frames_per_s": out["batched"]["frames_per_s"] / out["plain"]["frames_per_s"],
+            "p99_ratio": out["batched"]["p99_ms"] / out["plain"]["p99_ms"]}
 
 
 def run_reference(args):
@@ -380,6 +420,8 @@ def run_ours(args):
         "gpu_launches": launches_per_step * K,
         "clocks": clk,
     }
+    if not args.skip_serving:
+        line["serving"] = serving_bench(args.serving_frames)
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -392,6 +434,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serving:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(dist_env()[2])
+        print(json.dumps({"metric": "serving frame latency p50/p99 ms and frames/s vs plain per-session loop",
+                          **serving_bench(args.serving_frames)}), flush=True)
     else:
         run_ours(args)
 

@@ -365,6 +365,18 @@ gs_status gs_downsample(int64_t frame_idx, int64_t last_kf_idx, int is_keyframe,
 gs_status gs_pose_update(float* pose, const double* pose_grad6, float* adam, float lr_trans,
                          float lr_rot, float beta1, float beta2, float eps, gs_stream stream);
 
+/* Mapping step: Adam over up to GS_ADAM_MAX_TENSORS float32 arrays in one
+ * launch (the map update fed by the backward, Sec. 2.2 Step 5 / Sec. 5.4;
+ * the optimizer itself is not fixed by the paper).  params[t], grads[t],
+ * m[t], v[t] are device arrays of counts[t] elements (host arrays of
+ * pointers and counts); m and v start zeroed.  state: device float[2] that
+ * starts zeroed; state[0] is the step count, advanced by the launch itself so
+ * a CUDA graph that replays the step stays correct. */
+#define GS_ADAM_MAX_TENSORS 8
+gs_status gs_adam(int n_tensors, float* const* params, const float* const* grads, float* const* m,
+                  float* const* v, const int64_t* counts, float lr, float beta1, float beta2,
+                  float eps, float* state, gs_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* Status (the frame-level status query of Sec. 5.5, as a device word)      */
 /* ---------------------------------------------------------------------- */

@@ -79,6 +79,7 @@ _SIGS = {
     "gs_downsample": ([C.c_int64, C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int32, C.c_int32,
                        C.c_int32, _P, _P], C.c_int),
     "gs_pose_update": ([_P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, _P], C.c_int),
+    "gs_adam": ([C.c_int, _P, _P, _P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float, _P, _P], C.c_int),
     "gs_status_poll": ([_P, C.c_int, _P], C.c_int),
     "gs_status_reset": ([_P], C.c_int),
     "gs_last_error": ([], C.c_char_p),
@@ -356,8 +357,9 @@ def gs_compact(src, compact_map, n_kept, stream=None):
     return dst
 
 
-def gs_downsample(frame_idx, last_kf_idx, is_keyframe, m=2, target_full=None, stream=None):
-    """Returns (sx, sy) and, if target_full [C,H,W] is given, the gathered target."""
+def gs_downsample(frame_idx, last_kf_idx, is_keyframe, m=2, target_full=None, out=None, stream=None):
+    """Returns (sx, sy) and, if target_full [C,H,W] (or [H,W]) is given, the
+    target gathered at the sampled pixels (into `out` when given)."""
     sx, sy = C.c_int32(0), C.c_int32(0)
     _check(lib().gs_downsample(int(frame_idx), int(last_kf_idx), 1 if is_keyframe else 0, int(m), C.byref(sx),
                                C.byref(sy), None, 0, 0, 0, None, None), "gs_downsample")
@@ -365,11 +367,19 @@ def gs_downsample(frame_idx, last_kf_idx, is_keyframe, m=2, target_full=None, st
         return sx.value, sy.value, None
     t = target_full if target_full.dim() == 3 else target_full[None]
     Cn, H, W = t.shape
-    out = torch.empty((Cn, -(-H // sy.value), -(-W // sx.value)), dtype=torch.float32, device=t.device)
+    shape = (Cn, -(-H // sy.value), -(-W // sx.value))
+    if out is None:
+        res = torch.empty(shape, dtype=torch.float32, device=t.device)
+    else:
+        if out.numel() != Cn * shape[1] * shape[2] or not out.is_contiguous():
+            raise ValueError("out has the wrong size for the sampled target")
+        res = out
     _check(lib().gs_downsample(int(frame_idx), int(last_kf_idx), 1 if is_keyframe else 0, int(m), C.byref(sx),
-                               C.byref(sy), _ptr(t.contiguous()), Cn, W, H, _ptr(out), _stream(stream)),
+                               C.byref(sy), _ptr(t.contiguous()), Cn, W, H, _ptr(res), _stream(stream)),
            "gs_downsample")
-    return sx.value, sy.value, out if target_full.dim() == 3 else out[0]
+    if out is not None:
+        return sx.value, sy.value, out
+    return sx.value, sy.value, res if target_full.dim() == 3 else res[0]
 
 
 def pose_tensor(cam, device="cuda"):
@@ -383,6 +393,20 @@ def gs_pose_update(pose, pose_grad, adam, lr_trans=1e-3, lr_rot=1e-3, beta1=0.9,
                    stream=None):
     _check(lib().gs_pose_update(_ptr(pose), _ptr(pose_grad), _ptr(adam), float(lr_trans), float(lr_rot),
                                 float(beta1), float(beta2), float(eps), _stream(stream)), "gs_pose_update")
+
+
+def gs_adam(params, grads, ms, vs, state, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """One Adam step over lists of float32 device tensors (same order in
+    every list); state is a zeroed device float32 [2] tensor (step count)."""
+    k = len(params)
+    arr = C.c_void_p * k
+    P_ = arr(*[_ptr(t).value for t in params])
+    G_ = arr(*[_ptr(t).value for t in grads])
+    M_ = arr(*[_ptr(t).value for t in ms])
+    V_ = arr(*[_ptr(t).value for t in vs])
+    cnt = (C.c_int64 * k)(*[int(t.numel()) for t in params])
+    _check(lib().gs_adam(k, P_, G_, M_, V_, cnt, float(lr), float(beta1), float(beta2), float(eps), _ptr(state),
+                         _stream(stream)), "gs_adam")
 
 
 def gs_status_poll(blocking=True, stream=None):

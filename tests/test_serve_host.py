@@ -1,0 +1,49 @@
+"""Host logic of the serving form (no GPU): admission by HBM budget into
+slots, the keyframe/stride schedule of frames, Poisson arrivals."""
+import numpy as np
+import pytest
+
+
+def test_admission_by_budget_and_slots():
+    from paper_2510_06644_gb300.serve import Admission
+    a = Admission(budget_bytes=100, slots=2)
+    assert a.try_admit(0, 60)
+    assert not a.try_admit(1, 50)        # over budget
+    assert a.try_admit(2, 40)
+    assert not a.try_admit(3, 1)         # no slot
+    a.release(0)
+    assert a.used == 40
+    assert a.try_admit(1, 50)
+    assert a.used == 90 and set(a.active) == {1, 2}
+
+
+def test_frame_schedule_follows_keyframes_and_downsampling():
+    pytest.importorskip("torch")
+    from paper_2510_06644_gb300 import build
+    build.build()
+    from paper_2510_06644_gb300.serve import stride_of
+    got = [stride_of(f, 5) for f in range(11)]
+    assert got[0] == (True, 1, 1) and got[5] == (True, 1, 1) and got[10] == (True, 1, 1)
+    assert [g[1:] for g in got[1:5]] == [(4, 4), (4, 2), (2, 2), (2, 2)]
+
+
+def test_poisson_arrivals_and_specs():
+    from paper_2510_06644_gb300.serve import make_session_specs, poisson_arrivals
+    specs = make_session_specs(16, n_frames=50)
+    ns = np.array([s.n for s in specs])
+    assert ns.min() >= 50_000 and ns.max() <= 1_500_000
+    assert {(s.W, s.H) for s in specs} <= {(320, 240), (640, 480), (1200, 680)}
+    arr = poisson_arrivals(specs)
+    gaps = np.concatenate([np.diff(arr[s.sid]) for s in specs])
+    assert abs(gaps.mean() - 1 / 30) < 0.2 / 30
+    assert all(arr[s.sid][0] == 0.0 for s in specs)
+
+
+def test_footprint_grows_with_map_and_resolution():
+    from paper_2510_06644_gb300.serve import Session, SessionSpec
+    a = Session.footprint_bytes(SessionSpec(0, 50_000, 320, 240, 262.5, 10, 1))
+    b = Session.footprint_bytes(SessionSpec(0, 1_500_000, 320, 240, 262.5, 10, 1))
+    c = Session.footprint_bytes(SessionSpec(0, 50_000, 1200, 680, 984.0, 10, 1))
+    assert a < b and a < c
+    # 16 of the largest sessions fit the 150 GB budget of the serving workload
+    assert 16 * Session.footprint_bytes(SessionSpec(0, 1_500_000, 1200, 680, 984.0, 10, 1)) < 150 << 30
