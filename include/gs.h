@@ -215,13 +215,14 @@ gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const void* splats, 
  * Finally C += T bg.
  * Outputs: rgb [3][Hs][Ws], depth [Hs][Ws], t_final [Hs][Ws], last_idx
  * [Hs][Ws] (list position + 1 of the last blended fragment, relative to the
- * tile's first entry; 0 if none).  vals, tile_ranges and tile_order (may be
+ * tile's first entry; 0 if none), n_blended [Hs][Ws] (may be NULL: number of
+ * fragments blended into the pixel).  vals, tile_ranges and tile_order (may be
  * NULL: tiles in id order) come from gs_bin_sort with the same camera. */
 gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype,
                         const void* splats, int64_t n, const uint32_t* vals,
                         const uint32_t* tile_ranges, const uint32_t* tile_order, float* rgb,
-                        float* depth, float* t_final,
-                        uint32_t* last_idx, gs_stream stream);
+                        float* depth, float* t_final, uint32_t* last_idx, uint32_t* n_blended,
+                        gs_stream stream);
 
 /* ---------------------------------------------------------------------- */
 /* A-6 Loss (Sec. 4.1, Eq. 6)                                               */

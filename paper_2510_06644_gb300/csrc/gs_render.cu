@@ -122,14 +122,15 @@ __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g,
                                                           const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ order,
                                                           float* __restrict__ out_rgb, float* __restrict__ out_depth,
-                                                          float* __restrict__ out_t, uint32_t* __restrict__ out_last) {
+                                                          float* __restrict__ out_t, uint32_t* __restrict__ out_last,
+                                                          uint32_t* __restrict__ out_nb) {
     __shared__ StagedSplat sp[R_BATCH];
     const int tile = tile_of(order);
     const PixelMap m = map_pixel(g, tile);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-    uint32_t last = 0;
+    uint32_t last = 0, nb = 0;
     bool done = !m.inside;
     for (uint32_t b = start; b < end; b += R_BATCH) {
         if (__syncthreads_count(done) == R_THREADS) break;
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g,
                     C0 += w * Cc.x; C1 += w * Cc.y; C2 += w * Cc.z;
                     D += w * B.z;
                     T = Tn;
+                    ++nb;
                     last = b - start + (uint32_t)e + 1u;
                 }
                 if (__all_sync(0xffffffffu, done)) break;
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g,
         out_depth[pix] = D;
         out_t[pix] = T;
         out_last[pix] = last;
+        if (out_nb) out_nb[pix] = nb;
     }
 }
 
@@ -412,7 +415,7 @@ static gs_status render_checks(const gs_config* cfg, const gs_camera* cam, int r
 extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
                                    int64_t n, const uint32_t* vals, const uint32_t* tile_ranges,
                                    const uint32_t* tile_order, float* rgb, float* depth, float* t_final,
-                                   uint32_t* last_idx, gs_stream stream) {
+                                   uint32_t* last_idx, uint32_t* n_blended, gs_stream stream) {
     gs_status s;
     if ((s = render_checks(cfg, cam, rec_dtype, splats, n)) != GS_OK) return s;
     if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
@@ -421,7 +424,8 @@ extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, i
     const unsigned nt = (unsigned)(g.TX * g.TY);
     cudaStream_t st = (cudaStream_t)stream;
 #define GS_RF(DT) \
-    k_render_fwd<DT><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx)
+    k_render_fwd<DT><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx, \
+                                               n_blended)
     if (rec_dtype == GS_F32) GS_RF(GS_F32);
     else if (rec_dtype == GS_BF16) GS_RF(GS_BF16);
     else GS_RF(GS_F16);

@@ -66,7 +66,7 @@ _SIGS = {
     "gs_project": ([_P, _P, _P, C.c_int, _P, _P], C.c_int),
     "gs_bin_sort": ([_P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_bin_count": ([_P, C.c_int, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
-    "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_loss_l1": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_render_bwd": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P,
                        _P, _P, _P], C.c_int),
@@ -252,10 +252,11 @@ def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None,
     if out is None:
         out = {"rgb": torch.empty((3, Hs, Ws), device=dev), "depth": torch.empty((Hs, Ws), device=dev),
                "t_final": torch.empty((Hs, Ws), device=dev),
-               "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=dev)}
+               "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=dev),
+               "n_blended": torch.empty((Hs, Ws), dtype=torch.int32, device=dev)}
     _check(lib().gs_render_fwd(C.byref(cfg), C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(vals),
                                _ptr(ranges), _ptr(order), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["t_final"]),
-                               _ptr(out["last_idx"]), _stream(stream)), "gs_render_fwd")
+                               _ptr(out["last_idx"]), _ptr(out.get("n_blended")), _stream(stream)), "gs_render_fwd")
     return out
 
 

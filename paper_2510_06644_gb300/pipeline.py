@@ -46,7 +46,8 @@ class Rasterizer:
         self.order = torch.empty(TX * TY, dtype=torch.int32, device=d)
         self.img = {"rgb": torch.empty((3, Hs, Ws), device=d), "depth": torch.empty((Hs, Ws), device=d),
                     "t_final": torch.empty((Hs, Ws), device=d),
-                    "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=d)}
+                    "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=d),
+                    "n_blended": torch.empty((Hs, Ws), dtype=torch.int32, device=d)}
         self.dimg = {"d_rgb": torch.empty((3, Hs, Ws), device=d), "d_depth": torch.empty((Hs, Ws), device=d),
                      "loss": torch.zeros(1, dtype=torch.float64, device=d)}
         self._ws_sort = None

@@ -177,6 +177,7 @@ def test_render_fwd_matches_oracle(G, O, n, W, H, seed, sx, sy):
         scale = 1.0 if k != "depth" else max(1.0, float(np.abs(s["depth"]).max()))
         assert diff[good].max() <= IMG_TOL * scale, (k, diff[good].max())
     assert np.array_equal(img["last_idx"][good].astype(np.int64), ref["last"][good])
+    assert np.array_equal(img["n_blended"][good].astype(np.int64), ref["nfrag"][good])
 
 
 def test_stride_render_is_subsampled_full_render_bit_exact(G):
