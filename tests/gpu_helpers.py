@@ -43,3 +43,23 @@ def dilate(mask, r=0):
 
 def np_of(t):
     return t.detach().cpu().numpy()
+
+
+def round_storage(x, name):
+    """Round float64 values the way the 16-bit records store them: to float32
+    first (the kernels compute in float32), then to bf16 (round to nearest
+    even on the top 16 bits) or fp16."""
+    x32 = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    if name == "fp16":
+        return x32.astype(np.float16).astype(np.float64)
+    b = x32.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def stored_splats(pr, name):
+    """Projected splats with conic, opacity and colour as the 16-bit records hold them."""
+    sp = dict(pr)
+    for k in ("conic", "opacity", "rgb"):
+        sp[k] = round_storage(pr[k], name)
+    return sp

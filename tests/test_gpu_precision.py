@@ -10,7 +10,13 @@ float64.  Each output's error against the FP64 oracle is measured and printed
   ln(255 o) < 5.6 where alpha >= 1/255.  alpha = o exp(power) then has a
   relative error <= u (1 + 5.6) and a blended colour <= ~8u, which the test
   rounds up to 16u for maxima (and also covers the rare alpha-threshold flips)
-  and 2u for means.  Gradients are held to 16u relative L2.
+  and 2u for means.  Gradients sum per-pixel terms of both signs, so their
+  relative error is the storage error times the cancellation of that sum;
+  the quaternion gradient cancels most (rotating a nearly isotropic Gaussian
+  hardly changes it: ~37u measured on 3M Gaussians at 1920x1080), so
+  gradients are held to 64u relative L2 against full-precision FP64.
+  Against the FP64 oracle fed the same 16-bit-rounded records the float32
+  bars hold (1e-4 image away from marginal pixels, 1e-3 gradients).
 
 Binning reads only the float32 fields, so keys, order and ranges are
 identical to the float32 path.
@@ -20,7 +26,7 @@ import pytest
 import torch
 
 from synth import scenes as S
-from tests.gpu_helpers import dev, np_of, rel_l2
+from tests.gpu_helpers import dev, np_of, rel_l2, stored_splats
 
 pytestmark = pytest.mark.gpu
 
@@ -127,4 +133,14 @@ def test_errors_against_fp64_oracle(G, O, name, scene):
     assert errs["T_max"] <= 16 * u
     for k in list(grads) + ["pose"]:
         key = "d_" + k if k != "pose" else "pose"
-        assert errs[key] <= 16 * u, (key, errs[key])
+        assert errs[key] <= 64 * u, (key, errs[key])
+    # the same definition on the stored (rounded) records: float32 bars
+    sq = stored_splats(pr, name)
+    imq = O.render_fwd(sq, cam)
+    good = imq["margin"] == 0
+    assert good.mean() > 0.97
+    assert np.abs(np_of(r.img["rgb"]) - imq["rgb"]).max(0)[good].max() <= 1e-4
+    g2q = O.render_bwd(sq, cam, dr, dd)
+    g2 = np_of(r.grad2d)
+    for cols in ([0, 1], [2, 3, 4], [5], [6], [8, 9, 10]):
+        assert rel_l2(g2[:, cols], g2q[:, cols]) <= 1e-3, cols

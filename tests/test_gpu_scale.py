@@ -1,0 +1,161 @@
+"""Parity at the larger workloads, on crops the FP64 oracle computes exactly.
+
+The oracle projects every Gaussian with the full camera, then renders only a
+crop: shifting the 2D means by the crop's integer offset and rendering a
+crop-sized camera gives exactly the crop's pixels of the full image (a pixel
+sees a Gaussian iff it lies in the Gaussian's integer box, independent of the
+tiling).  The GPU renders the full frame in the benchmark's launch
+configuration; its backward gets an image gradient that is zero outside the
+crop, so its 2D and 3D gradients are the crop's.
+
+* mapping window: 1,000,000 surface Gaussians, 1200x680, keyframes on a 1 m
+  arc, full per-Gaussian gradients, gradient-magnitude pruning at the 10th
+  percentile (selection bit-exact on the same float32 score terms), strides
+  (2,2), (4,2), (4,4) equal to the subsampled full render;
+* precision form: 3,000,000 Gaussians, 1920x1080, bf16 and fp16 records.
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+from tests.gpu_helpers import dev, np_of, rel_l2, stored_splats
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("means", "log_scales", "quats", "opacity_logit", "rgb")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_06644_gb300 import build
+    build.build()
+    from paper_2510_06644_gb300 import gs
+    return gs
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def oracle_crop(O, pr, cam, x0, y0, w, h):
+    """Projected splats and camera whose render is the crop [x0, x0+w) x
+    [y0, y0+h) of the full image (stride 1)."""
+    sp = dict(pr)
+    sp["uv"] = pr["uv"] - np.array([float(x0), float(y0)])
+    return sp, dict(cam, W=w, H=h)
+
+
+def gpu_full(G, g, cam, rec_dtype, d_rgb=None, d_dep=None, mode=None):
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    n = g["means"].shape[0]
+    cs = G.camera(cam)
+    gd = dev(g)
+    probe = G.gs_project(G.default_config(), cs, gd, rec_dtype)
+    nk = int(G.gs_bin_count(cs, probe, n, rec_dtype).item())
+    del probe
+    r = Rasterizer(n, cam, rec_dtype=rec_dtype, capacity=nk + 1024)
+    r.forward(gd, cam)
+    grads = None
+    if d_rgb is not None:
+        grads = {k: torch.empty_like(gd[k]) for k in KEYS}
+        r.backward(gd, cam, torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(),
+                   mode=G.GS_MAP if mode is None else mode, grads=grads)
+    r.check()
+    return r, gd, grads
+
+
+def test_mapping_window_1M_1200x680(G, O):
+    g = S.surface_scene(1_000_000, seed=3000)
+    cams = S.arc_keyframes(8, 1200, 680, 600.0, seed=3001)
+    cam = cams[2]
+    x0, y0, w, h = 480, 200, 256, 192
+    rng = S.rng(3002)
+    d_rgb = np.zeros((3, 680, 1200), np.float32)
+    d_dep = np.zeros((680, 1200), np.float32)
+    d_rgb[:, y0:y0 + h, x0:x0 + w] = rng.normal(0, 1, (3, h, w)) / (w * h)
+    d_dep[y0:y0 + h, x0:x0 + w] = rng.normal(0, 1, (h, w)) / (w * h)
+    r, gd, grads = gpu_full(G, g, cam, G.GS_F32, d_rgb, d_dep)
+    pr = O.project(g, cam)
+    sp, ccam = oracle_crop(O, pr, cam, x0, y0, w, h)
+    img = O.render_fwd(sp, ccam)
+    good = img["margin"] == 0
+    assert good.mean() > 0.99
+    grgb = np_of(r.img["rgb"])[:, y0:y0 + h, x0:x0 + w]
+    assert np.abs(grgb - img["rgb"]).max(0)[good].max() <= 1e-4
+    g2 = O.render_bwd(sp, ccam, d_rgb[:, y0:y0 + h, x0:x0 + w], d_dep[y0:y0 + h, x0:x0 + w])
+    ref = O.project_bwd(g, cam, g2)
+    for k in KEYS:
+        assert rel_l2(np_of(grads[k]), ref[k]) <= 1e-3, k
+    # gradient-magnitude pruning at the 10th percentile on the oracle's score terms
+    st = ref["score_terms"].astype(np.float32)
+    mask0 = np.zeros(st.shape[0], np.uint8)
+    m = torch.from_numpy(mask0.copy()).cuda()
+    G.gs_prune(G.default_config(prune_frac=0.1), torch.from_numpy(st).cuda(), m, 0, 5)
+    ref_mask, cnt = O.prune_select(st[:, 0], st[:, 1], mask0, lam=float(np.float32(0.8)),
+                                   frac=float(np.float32(0.1)))
+    assert cnt == 100_000
+    assert np.array_equal(np_of(m), ref_mask)
+    # downsampling strides: the strided render is the subsampled full render
+    full = {k: np_of(v) for k, v in r.img.items()}
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    for sx, sy in ((2, 2), (4, 2), (4, 4)):
+        cs = dict(cam, sx=sx, sy=sy)
+        rs = Rasterizer(1_000_000, cs, capacity=r.capacity)
+        rs.forward(gd, cs)
+        rs.check()
+        assert np.array_equal(np_of(rs.img["rgb"]), full["rgb"][:, ::sy, ::sx])
+        assert np.array_equal(np_of(rs.img["depth"]), full["depth"][::sy, ::sx])
+
+
+@pytest.mark.parametrize("name", ["bf16", "fp16"])
+def test_precision_form_3M_1920x1080(G, O, name):
+    u = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}[name]
+    dt = G.GS_BF16 if name == "bf16" else G.GS_F16
+    g = S.surface_scene(3_000_000, seed=4000)
+    cam = S.perturbed_pose(S.camera(1920, 1080, 1000.0), seed=4001, trans=0.02, rot_deg=1.0)
+    x0, y0, w, h = 832, 412, 256, 256
+    rng = S.rng(4002)
+    d_rgb = np.zeros((3, 1080, 1920), np.float32)
+    d_dep = np.zeros((1080, 1920), np.float32)
+    d_rgb[:, y0:y0 + h, x0:x0 + w] = rng.normal(0, 1, (3, h, w)) / (w * h)
+    d_dep[y0:y0 + h, x0:x0 + w] = rng.normal(0, 1, (h, w)) / (w * h)
+    r, gd, grads = gpu_full(G, g, cam, dt, d_rgb, d_dep)
+    pr = O.project(g, cam)
+    sp, ccam = oracle_crop(O, pr, cam, x0, y0, w, h)
+    img = O.render_fwd(sp, ccam)
+    e = np.abs(np_of(r.img["rgb"])[:, y0:y0 + h, x0:x0 + w] - img["rgb"])
+    g2 = O.render_bwd(sp, ccam, d_rgb[:, y0:y0 + h, x0:x0 + w], d_dep[y0:y0 + h, x0:x0 + w])
+    ref = O.project_bwd(g, cam, g2)
+    errs = {"rgb_max": float(e.max()), "rgb_mean": float(e.mean())}
+    for k in KEYS:
+        errs["d_" + k] = rel_l2(np_of(grads[k]), ref[k])
+    errs["pose"] = rel_l2(np_of(r.pose), ref["pose"])
+    print(f"\n[{name} 3M 1920x1080 crop] " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert errs["rgb_max"] <= 16 * u and errs["rgb_mean"] <= 2 * u
+    for k, v in errs.items():
+        if k.startswith("d_") or k == "pose":
+            assert v <= 64 * u, (k, v)
+    # against the FP64 definition on the same 16-bit records.  With 3M
+    # Gaussians a few stored values sit at a 16-bit rounding midpoint, where
+    # the kernel's float32 value and the oracle's float64 value round one
+    # 16-bit ulp apart; those pixels may differ by a one-ulp storage flip
+    # (< 4u), all others meet the float32 bar.
+    sq, _ = oracle_crop(O, stored_splats(pr, name), cam, x0, y0, w, h)
+    imq = O.render_fwd(sq, ccam)
+    good = imq["margin"] == 0
+    assert good.mean() > 0.97
+    dq = np.abs(np_of(r.img["rgb"])[:, y0:y0 + h, x0:x0 + w] - imq["rgb"]).max(0)[good]
+    g2q = O.render_bwd(sq, ccam, d_rgb[:, y0:y0 + h, x0:x0 + w], d_dep[y0:y0 + h, x0:x0 + w])
+    g2 = np_of(r.grad2d)
+    gq = {str(c): rel_l2(g2[:, c], g2q[:, c]) for c in ([0, 1], [2, 3, 4], [5], [6], [8, 9, 10])}
+    print(f"[{name} 3M same-records] max={dq.max():.2e} frac>1e-4={(dq > 1e-4).mean():.2e} " +
+          " ".join(f"{k}={v:.2e}" for k, v in gq.items()))
+    assert (dq > 1e-4).mean() <= 1e-3 and dq.max() <= 4 * u
+    for k, v in gq.items():
+        assert v <= 1e-3, (k, v)
