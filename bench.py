@@ -153,6 +153,84 @@ def cpu_baseline(budget_s=20.0):
             "mpix_per_s": W_IMG * H_IMG / t / 1e6}
 
 
+def _graph_ms(fn, reps, flush):
+    """Mean CUDA-event time of a captured `fn`, L2 flushed before each replay."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        g.replay()
+        b.record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+
+def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pose, pose0, adam, flush, lr_t, lr_r):
+    """N1: a pruning interval of K = 5 tracking iterations that bins only on
+    the first (Sec. 4.1 / Obs. 6).  N4: forward and backward time with the
+    lowest-score 10/30/50 % of the Gaussians masked (Eq. 7 scores of the
+    current backward) and at the Sec. 4.2 strides."""
+    import torch
+    out = {}
+    K = 5
+
+    def interval():
+        for i in range(K):
+            rast.step(gd, cam_s, trgb, tdep, gs.GS_TRACK, rebin=(i == 0))
+            gs.gs_pose_update(pose, rast.pose, adam, lr_t, lr_r)
+
+    pose.copy_(pose0)
+    adam.zero_()
+    ms = _graph_ms(interval, 20, flush) / K
+    out["list_reuse_k5"] = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms}
+
+    def fwd(r, g, cam):
+        return lambda: r.forward(g, cam)
+
+    def bwd(r, g, cam):
+        return lambda: r.backward(g, cam, r.dimg["d_rgb"], r.dimg["d_depth"], gs.GS_TRACK)
+
+    def time_pair(r, g, cam):
+        r.forward(g, cam)
+        sx, sy = cam.sx, cam.sy
+        tr = trgb[:, ::sy, ::sx].contiguous()
+        td = tdep[::sy, ::sx].contiguous()
+        r.loss_grad(cam, tr, td)
+        return _graph_ms(fwd(r, g, cam), 20, flush), _graph_ms(bwd(r, g, cam), 20, flush)
+
+    pose.copy_(pose0)
+    base_f, base_b = time_pair(rast, gd, cam_s)
+    prune = {}
+    score = rast.score.clone()
+    for frac in (0.1, 0.3, 0.5):
+        mask = torch.zeros(rast.n, dtype=torch.uint8, device="cuda")
+        gs.gs_prune(gs.default_config(prune_frac=frac), score, mask, 0, 5)
+        gm = dict(gd, mask=mask)
+        f, b = time_pair(rast, gm, cam_s)
+        prune[f"{int(frac * 100)}%"] = {"fwd_speedup": base_f / f, "bwd_speedup": base_b / b}
+    stride = {}
+    for sx, sy in ((2, 2), (4, 2), (4, 4)):
+        cam_d = dict(start_cam, sx=sx, sy=sy)
+        r = Rasterizer(rast.n, cam_d, capacity=rast.capacity)
+        cs = gs.camera(cam_d, pose=pose)
+        f, b = time_pair(r, gd, cs)
+        stride[f"{sx}x{sy}"] = {"fwd_speedup": base_f / f, "bwd_speedup": base_b / b}
+    rast.forward(gd, cam_s)
+    out["breakdown"] = {"base_fwd_ms": base_f, "base_bwd_ms": base_b, "pruned": prune, "strides": stride,
+                        "note": "fwd = project + bin/sort + forward; bwd = backward compositing + backward "
+                                "projection; speedup over the unpruned full-resolution iteration"}
+    return out
+
+
 # Algorithmic work per launch of each stage (DESIGN.md, section 6): bytes for
 # the streaming stages, FP32 FLOPs per blended fragment for the compositing.
 FLOP_PER_FRAGMENT = {"render_fwd": 27, "render_bwd": 67}
@@ -406,6 +484,10 @@ def run_ours(args):
     blended = int(rast.img["n_blended"].long().sum().item())
     roof = roofline(stage_ms, n, n_keys, P, blended, clk)
 
+    # ---- variants: list reuse (N1) and the speedup breakdown (N4) ----
+    variants = measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pose, pose0, adam, flush,
+                                lr_t, lr_r)
+
     # ---- end to end through the public API with host buffers ----
     trgb_h = trgb.cpu().pin_memory()
     tdep_h = tdep.cpu().pin_memory()
@@ -443,6 +525,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}", "stage_ms": stage_ms,
                    "pose_moved": float(np.abs(final_pose - pose0.cpu().numpy()).max())},
         "roofline": roof,
+        "variants": variants,
         "e2e": e2e,
         "gpu_launches": launches_per_step * K,
         "clocks": clk,

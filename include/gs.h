@@ -26,8 +26,11 @@
  *   Ws = ceil(W/sx) columns and Hs = ceil(H/sy) rows, sampled pixel (i, j) is
  *   full-resolution pixel (sx*i, sy*j) and is evaluated at its centre
  *   (sx*i + 0.5, sy*j + 0.5).  Images are planar float32: rgb [3][Hs][Ws],
- *   depth [Hs][Ws].  Tiles are 16 x 16 sampled pixels (Sec. 2.1, Step 1-2
- *   footnote), TX = ceil(Ws/16) by TY = ceil(Hs/16), row-major tile ids.
+ *   depth [Hs][Ws].  Tiles are tw x th sampled pixels with tw = 16 / p2(sx)
+ *   and th = 16 / p2(sy), at least 4 (p2(s) = smallest power of two >= s),
+ *   so every tile keeps the 16 x 16 full-resolution footprint of the paper's
+ *   tile (Sec. 2.1, Step 1-2 footnote): 16 x 16 at full resolution.
+ *   TX = ceil(Ws/tw) by TY = ceil(Hs/th), row-major tile ids.
  * Empty inputs.  n = 0 Gaussians, zero keys and empty tiles are valid.
  */
 #ifndef GS_H

@@ -78,12 +78,23 @@ static int64_t clamp_i64(int64_t v, int64_t lo, int64_t hi) {
     return v < lo ? lo : (v > hi ? hi : v);
 }
 
+/* Tile side in sampled pixels for stride s: 16 / p2(s), at least 4, with
+ * p2(s) the smallest power of two >= s, so that a tile keeps the 16-pixel
+ * full-resolution footprint of the paper's tile (Sec. 2.1 Step 1-2 footnote)
+ * when the frame is point-sampled at stride s (Sec. 4.2). */
+static int64_t tile_dim(int64_t s) {
+    int64_t p = 1;
+    while (p < s && p < TILE) p *= 2;
+    int64_t t = TILE / p;
+    return t < 4 ? 4 : t;
+}
+
 /* Sampled image size and tile grid for the camera's strides (Sec. 4.2). */
 static void grid_dims(const or_cam* c, int64_t* Ws, int64_t* Hs, int64_t* TX, int64_t* TY) {
     *Ws = ceil_div(c->W, c->sx);
     *Hs = ceil_div(c->H, c->sy);
-    *TX = ceil_div(*Ws, TILE);
-    *TY = ceil_div(*Hs, TILE);
+    *TX = ceil_div(*Ws, tile_dim(c->sx));
+    *TY = ceil_div(*Hs, tile_dim(c->sy));
 }
 
 /* Tile rectangle of a 2D Gaussian (Sec. 2.1, Step 1-2).  The Gaussian covers
@@ -92,7 +103,8 @@ static void grid_dims(const or_cam* c, int64_t* Ws, int64_t* Hs, int64_t* TX, in
  * (p+0.5) lies within r of the mean on each axis.  With strides (sx, sy) the
  * sampled pixel i sits at full-resolution column sx*i, so the covered sampled
  * columns are ceil((floor(u)-r)/sx) .. floor((floor(u)+r)/sx), and the tiles
- * are those columns, clipped to the sampled image, divided by 16.  Returns
+ * are those columns, clipped to the sampled image, divided by the tile side
+ * (16 at full resolution, see tile_dim).  Returns
  * the rect [x0,x1) x [y0,y1) in tile units (empty when no sampled pixel of
  * the image lies in the box) and the box in full-resolution pixels. */
 static void tile_rect(const or_cam* c, double u, double v, int64_t r,
@@ -112,10 +124,10 @@ static void tile_rect(const or_cam* c, double u, double v, int64_t r,
         rect[0] = rect[1] = rect[2] = rect[3] = 0;
         return;
     }
-    rect[0] = i0 / TILE;
-    rect[1] = i1 / TILE + 1;
-    rect[2] = j0 / TILE;
-    rect[3] = j1 / TILE + 1;
+    rect[0] = i0 / tile_dim(c->sx);
+    rect[1] = i1 / tile_dim(c->sx) + 1;
+    rect[2] = j0 / tile_dim(c->sy);
+    rect[3] = j1 / tile_dim(c->sy) + 1;
     (void)TX; (void)TY;
 }
 
@@ -453,7 +465,7 @@ static int64_t tile_candidates(const or_cam* cam, int64_t i, int64_t j, const ui
                                const uint32_t* ranges, int64_t* cand) {
     int64_t Ws, Hs, TX, TY;
     grid_dims(cam, &Ws, &Hs, &TX, &TY);
-    int64_t t = (j / TILE) * TX + (i / TILE);
+    int64_t t = (j / tile_dim(cam->sy)) * TX + (i / tile_dim(cam->sx));
     int64_t b = ranges[2 * t], e = ranges[2 * t + 1];
     for (int64_t q = b; q < e; ++q) cand[q - b] = vals[q];
     return e - b;

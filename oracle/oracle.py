@@ -137,12 +137,20 @@ def _cfg(cfg=None) -> _Cfg:
     return c
 
 
+def tile_dim(s):
+    """Tile side in sampled pixels at stride s (16 / p2(s), at least 4)."""
+    p = 1
+    while p < s and p < 16:
+        p *= 2
+    return max(4, 16 // p)
+
+
 def grid(cam):
     """Sampled image size and tile grid: (Ws, Hs, TX, TY)."""
     sx, sy = int(cam.get("sx", 1)), int(cam.get("sy", 1))
     Ws = -(-int(cam["W"]) // sx)
     Hs = -(-int(cam["H"]) // sy)
-    return Ws, Hs, -(-Ws // 16), -(-Hs // 16)
+    return Ws, Hs, -(-Ws // tile_dim(sx)), -(-Hs // tile_dim(sy))
 
 
 # --------------------------------------------------------------------------

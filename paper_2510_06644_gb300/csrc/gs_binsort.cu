@@ -4,23 +4,28 @@
 // The key of a (tile, Gaussian) pair is tile_id << 32 | float32 bits of the
 // depth, with the Gaussian id as the tie-break (equal depths keep id order).
 // It is sorted as an MSD radix sort whose first digit is the whole tile id:
-//   k_tile_count    +1 on the counter of every tile of each Gaussian's rect;
-//                   for grids of up to 8192 tiles the counts of a CTA's
-//                   Gaussians are first summed in shared memory, so global
-//                   atomics drop from one per key to one per (CTA, tile)
+//   k_tile_hist     per-CTA tile counts of each Gaussian's rect, summed in
+//                   shared memory and written as one row per CTA (grids of
+//   k_col_scan      up to 8192 tiles); a column scan over the CTAs gives
+//                   each CTA's offset inside every bucket and the tile
+//                   totals.  Larger grids count with one global atomic per
+//                   key (k_tile_count).
 //   k_tile_scan     one CTA: exclusive scan of the tile counts -> bucket
 //                   starts, tile ranges, key count, capacity check
 //   k_tile_order    one CTA: heavy-first permutation of the tiles
 //   k_tile_scatter  each pair takes a slot of its tile's bucket and writes
 //                   the 64-bit remainder key depth_bits << 32 | id there (a
-//                   CTA claims one block of slots per tile with a global
-//                   atomic and deals them out with shared-memory atomics)
-//   k_tile_sort     one CTA per bucket, heavy first: the remainder keys are
-//                   unique, so any correct sort of them gives the same
-//                   result; buckets of up to 8192 keys sort in shared memory
-//                   with a bitonic network, longer ones sort 8192-key runs
-//                   in shared memory and merge them by rank in global memory.
-//                   The CTA then writes tile_id << 32 | depth_bits and the id.
+//                   CTA's slots start at its row offset and are dealt out
+//                   with shared-memory atomics: no global atomics)
+//   k_tile_sort     bucket sort, heavy first: the remainder keys are unique,
+//                   so any correct sort of them gives the same result.
+//                   Buckets of up to 512 keys: one warp each, a bitonic
+//                   network in registers (k_tile_sort_small); up to 8192
+//                   keys: one CTA, 16 keys per thread in registers, stages
+//                   across warps through shared memory; longer buckets sort
+//                   8192-key runs in shared memory and merge them by rank in
+//                   global memory.  The sort writes tile_id << 32 |
+//                   depth_bits and the id.
 // The scatter order inside a bucket depends on atomics, the output does not.
 // Everything stays on the device: the key count is never read by the host.
 #include "gs_internal.cuh"
@@ -49,17 +54,18 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_count(gs_camera cam, const
 }
 
 // Shared-memory aggregated forms of the two passes above, for grids of at
-// most AGG_MAX_TILES tiles: each CTA takes `per_cta` consecutive Gaussians,
-// counts their pairs per tile in shared memory, and touches global memory
-// once per non-empty tile bin (a count, or a claim of a block of bucket
-// slots whose base is then handed out with shared-memory atomics).  This
-// turns ~1 contended L2 atomic per key into ~1 per (CTA, tile).
+// most AGG_MAX_TILES tiles.  CTA c takes `per_cta` consecutive Gaussians:
+//   k_tile_hist      counts its pairs per tile in shared memory and writes
+//                    the row hist[c][0..T) (no global atomics);
+//   k_col_scan       exclusive prefix of hist[.][t] over the CTAs (in place)
+//                    and the tile totals;
+//   k_tile_scatter_rows  CTA c starts tile t's slots at start[t] +
+//                    hist[c][t] and deals them out with shared-memory atomics.
 #define AGG_MAX_TILES 8192
 
 template <int DT>
-__global__ void __launch_bounds__(BIN_THREADS) k_tile_count_agg(gs_camera cam, const void* __restrict__ splats,
-                                                                int64_t n, int64_t per_cta, int ntiles,
-                                                                uint32_t* __restrict__ count) {
+__global__ void __launch_bounds__(BIN_THREADS) k_tile_hist(gs_camera cam, const void* __restrict__ splats, int64_t n,
+                                                           int64_t per_cta, int ntiles, uint32_t* __restrict__ hist) {
     extern __shared__ uint32_t h[];
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) h[t] = 0;
     __syncthreads();
@@ -75,38 +81,61 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_count_agg(gs_camera cam, c
             for (int tx = x0; tx < x1; ++tx) atomicAdd(h + ty * grid.TX + tx, 1u);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-        if (h[t]) atomicAdd(count + t, h[t]);
+    uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = h[t];
+}
+
+// Column scan of the per-CTA rows: CTA b takes 32 tiles; its 32 warps split
+// the rows into 32 consecutive ranges, sum them, scan the 32 partial sums in
+// shared memory and write each row's exclusive prefix in place.
+__global__ void __launch_bounds__(1024) k_col_scan(uint32_t* __restrict__ hist, int nrows, int ntiles,
+                                                   uint32_t* __restrict__ total) {
+    __shared__ uint32_t part[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + tx;
+    const int per = (nrows + 31) / 32;
+    const int r0 = min(nrows, ty * per), r1 = min(nrows, r0 + per);
+    uint32_t sum = 0;
+    if (t < ntiles)
+        for (int r = r0; r < r1; ++r) sum += hist[(size_t)r * ntiles + t];
+    part[ty][tx] = sum;
+    __syncthreads();
+    if (ty == 0) {
+        uint32_t run = 0;
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t v = part[k][tx];
+            part[k][tx] = run;
+            run += v;
+        }
+        if (t < ntiles) total[t] = run;
+    }
+    __syncthreads();
+    uint32_t run = part[ty][tx];
+    if (t < ntiles)
+        for (int r = r0; r < r1; ++r) {
+            uint32_t* p = hist + (size_t)r * ntiles + t;
+            const uint32_t v = *p;
+            *p = run;
+            run += v;
+        }
 }
 
 template <int DT>
-__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_agg(gs_camera cam, const void* __restrict__ splats,
-                                                                  int64_t n, int64_t per_cta, int ntiles,
-                                                                  const uint32_t* __restrict__ start,
-                                                                  uint32_t* __restrict__ fill, int64_t cap,
-                                                                  u64* __restrict__ keys) {
+__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rows(gs_camera cam, const void* __restrict__ splats,
+                                                                   int64_t n, int64_t per_cta, int ntiles,
+                                                                   const uint32_t* __restrict__ start,
+                                                                   const uint32_t* __restrict__ hist, int64_t cap,
+                                                                   u64* __restrict__ keys) {
     extern __shared__ uint32_t h[];
     uint32_t* base = h + ntiles;
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) h[t] = 0;
+    const uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        h[t] = 0;
+        base[t] = start[t] + row[t];
+    }
     __syncthreads();
     const Grid grid = make_grid(cam);
     const int64_t k0 = (int64_t)blockIdx.x * per_cta, k1 = min(n, k0 + per_cta);
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-        float x, y, d;
-        int r;
-        load_geom<DT>(splats, (uint32_t)k, x, y, d, r);
-        int x0, x1, y0, y1;
-        if (tile_rect(grid, x, y, r, x0, x1, y0, y1) == 0) continue;
-        for (int ty = y0; ty < y1; ++ty)
-            for (int tx = x0; tx < x1; ++tx) atomicAdd(h + ty * grid.TX + tx, 1u);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const uint32_t c = h[t];
-        base[t] = c ? start[t] + atomicAdd(fill + t, c) : 0u;
-        h[t] = 0;
-    }
-    __syncthreads();
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         float x, y, d;
         int r;
@@ -248,6 +277,126 @@ __device__ __forceinline__ int rank_in(const u64* r, int len, u64 x) {
     return lo;
 }
 
+// ---------------------------------------------------------------------------
+// Bitonic networks with the keys in registers.  Position x of the sequence is
+// held by lane x % 32, register (x / 32) % KPT, warp x / (32 KPT) of the
+// sorting group.  A compare-exchange at distance j is a warp shuffle for
+// j < 32, a register swap inside the thread for 32 <= j < 32 KPT, and goes
+// through shared memory for larger j.  Merge step k sorts position x
+// ascending iff (x & k) == 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
+__device__ __forceinline__ u64 umax64(u64 a, u64 b) { return a < b ? b : a; }
+
+template <int KPT>
+__device__ __forceinline__ void bit_shfl_stage(u64 (&v)[KPT], int base, int k, int j) {
+    const int lane = threadIdx.x & 31;
+    const bool low = (lane & j) == 0;
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) {
+        const u64 p = __shfl_xor_sync(0xffffffffu, v[r], j);
+        const bool asc = ((base + lane + 32 * r) & k) == 0;
+        v[r] = (low == asc) ? umin64(v[r], p) : umax64(v[r], p);
+    }
+}
+
+template <int KPT, int JR>
+__device__ __forceinline__ void bit_reg_stage(u64 (&v)[KPT], int base, int k) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) {
+        if (r & JR) continue;
+        const bool asc = ((base + lane + 32 * r) & k) == 0;
+        const u64 lo = umin64(v[r], v[r | JR]), hi = umax64(v[r], v[r | JR]);
+        v[r] = asc ? lo : hi;
+        v[r | JR] = asc ? hi : lo;
+    }
+}
+
+// The stages j = jtop, jtop/2, ..., 1 (jtop < 32 KPT) of merge step k.
+template <int KPT>
+__device__ __forceinline__ void bit_warp_steps(u64 (&v)[KPT], int base, int k, int jtop) {
+    for (int j = jtop; j > 0; j >>= 1) {
+        switch (j >> 5) {
+            case 0: bit_shfl_stage<KPT>(v, base, k, j); break;
+            case 1: if constexpr (KPT > 1) bit_reg_stage<KPT, 1>(v, base, k); break;
+            case 2: if constexpr (KPT > 2) bit_reg_stage<KPT, 2>(v, base, k); break;
+            case 4: if constexpr (KPT > 4) bit_reg_stage<KPT, 4>(v, base, k); break;
+            case 8: if constexpr (KPT > 8) bit_reg_stage<KPT, 8>(v, base, k); break;
+            default: break;
+        }
+    }
+}
+
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Ascending sort of the W * 32 * KPT keys held by warps 0..W-1; stages that
+// cross warps exchange through s[] (W * 32 * KPT keys) under named barrier 1.
+template <int KPT>
+__device__ __forceinline__ void bit_sort_group(u64 (&v)[KPT], int W, u64* s) {
+    const int lane = threadIdx.x & 31;
+    const int base = (threadIdx.x >> 5) * 32 * KPT;
+    const int m = W * 32 * KPT;
+    for (int k = 2; k <= m; k <<= 1) {
+        int j = k >> 1;
+        for (; j >= 32 * KPT; j >>= 1) {
+#pragma unroll
+            for (int r = 0; r < KPT; ++r) s[base + lane + 32 * r] = v[r];
+            named_bar(1, W * 32);
+#pragma unroll
+            for (int r = 0; r < KPT; ++r) {
+                const int x = base + lane + 32 * r;
+                const u64 p = s[x ^ j];
+                const bool asc = (x & k) == 0, low = (x & j) == 0;
+                v[r] = (low == asc) ? umin64(v[r], p) : umax64(v[r], p);
+            }
+            named_bar(1, W * 32);
+        }
+        bit_warp_steps<KPT>(v, base, k, j);
+    }
+}
+
+// Sorts one bucket of at most 32 * KPT keys with the calling warp and
+// writes tile_id << 32 | depth_bits and the ids.
+template <int KPT>
+__device__ __forceinline__ void warp_sort_bucket(u64* key, uint32_t* val, int n, u64 hi) {
+    const int lane = threadIdx.x & 31;
+    u64 v[KPT];
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) v[r] = lane + 32 * r < n ? key[lane + 32 * r] : ~0ull;
+    for (int k = 2; k <= 32 * KPT; k <<= 1) bit_warp_steps<KPT>(v, 0, k, k >> 1);
+#pragma unroll
+    for (int r = 0; r < KPT; ++r)
+        if (lane + 32 * r < n) {
+            key[lane + 32 * r] = hi | (v[r] >> 32);
+            val[lane + 32 * r] = (uint32_t)v[r];
+        }
+}
+
+#define SW_WARPS 8
+#define SW_MAX 512
+
+// Buckets of 1..SW_MAX keys: one warp per bucket, no shared memory.
+__global__ void __launch_bounds__(SW_WARPS * 32) k_tile_sort_small(const uint32_t* __restrict__ ranges,
+                                                                  const uint32_t* __restrict__ order, int ntiles,
+                                                                  u64* __restrict__ keys,
+                                                                  uint32_t* __restrict__ vals) {
+    const int idx = blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
+    if (idx >= ntiles) return;
+    const int t = order ? (int)order[idx] : idx;
+    const uint32_t b = ranges[2 * t], e = ranges[2 * t + 1];
+    const int n = (int)(e - b);
+    if (n <= 0 || n > SW_MAX) return;
+    const u64 hi = (u64)(uint32_t)t << 32;
+    if (n <= 32) warp_sort_bucket<1>(keys + b, vals + b, n, hi);
+    else if (n <= 64) warp_sort_bucket<2>(keys + b, vals + b, n, hi);
+    else if (n <= 128) warp_sort_bucket<4>(keys + b, vals + b, n, hi);
+    else if (n <= 256) warp_sort_bucket<8>(keys + b, vals + b, n, hi);
+    else warp_sort_bucket<16>(keys + b, vals + b, n, hi);
+}
+
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ order, u64* __restrict__ keys,
                                                           uint32_t* __restrict__ vals, u64* __restrict__ tmp) {
@@ -255,20 +404,26 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __rest
     const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const uint32_t b = ranges[2 * t], e = ranges[2 * t + 1];
     const int n = (int)(e - b);
-    if (n <= 0) return;
+    if (n <= SW_MAX) return;  // k_tile_sort_small
     u64* key = keys + b;
     if (n <= TS_SMEM_KEYS) {
-        int m = 1;
+        // m / 512 warps, 16 keys per thread in registers
+        int m = 2 * SW_MAX;
         while (m < n) m <<= 1;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = i < n ? key[i] : ~0ull;
-        __syncthreads();
-        bitonic_smem(s, m);
+        const int W = m / SW_MAX;
+        if ((int)(threadIdx.x >> 5) >= W) return;
+        const int x0 = (threadIdx.x >> 5) * SW_MAX + (threadIdx.x & 31);
+        u64 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = x0 + 32 * r < n ? key[x0 + 32 * r] : ~0ull;
+        bit_sort_group<16>(v, W, s);
         const u64 hi = (u64)(uint32_t)t << 32;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const u64 v = s[i];
-            key[i] = hi | (v >> 32);
-            vals[b + i] = (uint32_t)v;
-        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+            if (x0 + 32 * r < n) {
+                key[x0 + 32 * r] = hi | (v[r] >> 32);
+                vals[b + x0 + 32 * r] = (uint32_t)v[r];
+            }
         return;
     }
     // long bucket: sorted runs of TS_SMEM_KEYS, then merge by rank
@@ -314,18 +469,30 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __rest
 // Workspace layout
 // ---------------------------------------------------------------------------
 struct BinLayout {
-    size_t off_count, off_fill, off_start, off_tmp, zero_bytes, total;
+    size_t off_count, off_fill, off_start, off_hist, off_tmp, zero_bytes, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static BinLayout bin_layout(int64_t cap, int ntiles) {
+// Gaussians per CTA of the aggregated passes: one per thread, or more when
+// the per-CTA rows would pass 2^24 entries (64 MB).
+static int64_t agg_per_cta(int64_t n, int ntiles) {
+    const int64_t lim = (int64_t)1 << 24;
+    const int64_t want = (n * (int64_t)ntiles + lim - 1) / lim;
+    return want > BIN_THREADS ? want : BIN_THREADS;
+}
+
+static BinLayout bin_layout(int64_t n, int64_t cap, int ntiles) {
     BinLayout L;
     size_t o = 0;
+    const int64_t per = agg_per_cta(n, ntiles);
+    const int64_t rows = n > 0 ? (n + per - 1) / per : 1;
     L.off_count = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
     L.off_fill = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
     L.zero_bytes = o;
     L.off_start = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
+    L.off_hist = o;
+    if (ntiles <= AGG_MAX_TILES) o = align256(o + sizeof(uint32_t) * (size_t)ntiles * (size_t)rows);
     L.off_tmp = o; o = align256(o + sizeof(u64) * (size_t)(cap > 0 ? cap : 1));
     L.total = o;
     return L;
@@ -351,41 +518,38 @@ static gs_status bin_common_checks(const gs_camera* cam, int rec_dtype, const vo
     return GS_OK;
 }
 
-// Gaussians per CTA of the aggregated passes: at least 2048, and few enough
-// CTAs that the per-CTA flush of the tile bins stays small.
-static int64_t agg_per_cta(int64_t n) {
-    const int64_t sms = num_sms();
-    const int64_t want = (n + sms - 1) / sms;
-    return want > 2048 ? want : 2048;
-}
-
 static gs_status set_agg_smem_attrs() {
     static bool done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && done[dev]) return GS_OK;
     const int bytes = (int)(2 * AGG_MAX_TILES * sizeof(uint32_t));
-    bool ok = cudaFuncSetAttribute(k_tile_scatter_agg<GS_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
-              cudaFuncSetAttribute(k_tile_scatter_agg<GS_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
-              cudaFuncSetAttribute(k_tile_scatter_agg<GS_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
-    if (!ok) return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(k_tile_scatter_agg)");
+    bool ok = cudaFuncSetAttribute(k_tile_scatter_rows<GS_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+              cudaFuncSetAttribute(k_tile_scatter_rows<GS_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+              cudaFuncSetAttribute(k_tile_scatter_rows<GS_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    if (!ok) return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(k_tile_scatter_rows)");
     if (dev >= 0 && dev < 64) done[dev] = true;
     return GS_OK;
 }
 
+// Tile counts into `count`: per-CTA rows + column scan (rows kept in `hist`
+// for the scatter) when the grid is small enough, else direct atomics.
 static gs_status launch_count(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
-                              uint32_t* count, cudaStream_t st) {
+                              uint32_t* count, uint32_t* hist, cudaStream_t st) {
     if (n == 0) return GS_OK;
     const Grid g = make_grid(*cam);
     const int ntiles = g.TX * g.TY;
-    if (ntiles <= AGG_MAX_TILES) {
-        const int64_t per = agg_per_cta(n);
+    if (ntiles <= AGG_MAX_TILES && hist) {
+        const int64_t per = agg_per_cta(n, ntiles);
         const unsigned nb = (unsigned)((n + per - 1) / per);
         const size_t sm = sizeof(uint32_t) * (size_t)ntiles;
-        if (rec_dtype == GS_F32) k_tile_count_agg<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, count);
-        else if (rec_dtype == GS_BF16) k_tile_count_agg<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, count);
-        else k_tile_count_agg<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, count);
-        return check_launch("k_tile_count_agg");
+        if (rec_dtype == GS_F32) k_tile_hist<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, hist);
+        else if (rec_dtype == GS_BF16) k_tile_hist<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, hist);
+        else k_tile_hist<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, hist);
+        gs_status s;
+        if ((s = check_launch("k_tile_hist")) != GS_OK) return s;
+        k_col_scan<<<(unsigned)((ntiles + 31) / 32), 1024, 0, st>>>(hist, (int)nb, ntiles, count);
+        return check_launch("k_col_scan");
     }
     const unsigned nb = (unsigned)((n + BIN_THREADS - 1) / BIN_THREADS);
     if (rec_dtype == GS_F32) k_tile_count<GS_F32><<<nb, BIN_THREADS, 0, st>>>(*cam, splats, n, count);
@@ -402,15 +566,17 @@ extern "C" gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const voi
     if (!workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "workspace_bytes is NULL");
     const Grid g = make_grid(*cam);
     const int ntiles = g.TX * g.TY;
-    const size_t need = align256(sizeof(uint32_t) * (size_t)ntiles);
+    const BinLayout L = bin_layout(n, 0, ntiles);
+    const size_t need = L.off_tmp;
     if (!workspace) { *workspace_bytes = need; return GS_OK; }
     if (*workspace_bytes < need) return set_error(GS_ERR_WORKSPACE, "workspace %zu < %zu", *workspace_bytes, need);
     if (!n_keys_out) return set_error(GS_ERR_INVALID_ARG, "n_keys_out is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t* count = (uint32_t*)workspace;
+    uint32_t* count = (uint32_t*)((char*)workspace + L.off_count);
+    uint32_t* hist = ntiles <= AGG_MAX_TILES ? (uint32_t*)((char*)workspace + L.off_hist) : nullptr;
     if (cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)ntiles, st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset counts");
-    if ((s = launch_count(cam, rec_dtype, splats, n, count, st)) != GS_OK) return s;
+    if ((s = launch_count(cam, rec_dtype, splats, n, count, hist, st)) != GS_OK) return s;
     unsigned int* err = status_ptr();
     if (!err) return set_error(GS_ERR_CUDA, "status word address");
     k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, (int64_t)1 << 62, nullptr, nullptr, n_keys_out, err);
@@ -428,7 +594,7 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
         return set_error(GS_ERR_INVALID_ARG, "keys_capacity must be in [0, 2^30)");
     const Grid grid = make_grid(*cam);
     const int ntiles = grid.TX * grid.TY;
-    const BinLayout L = bin_layout(keys_capacity, ntiles);
+    const BinLayout L = bin_layout(n, keys_capacity, ntiles);
     if (!workspace) { *workspace_bytes = L.total; return GS_OK; }
     if (*workspace_bytes < L.total) return set_error(GS_ERR_WORKSPACE, "workspace %zu < %zu", *workspace_bytes, L.total);
     if (((uintptr_t)workspace & 255) != 0) return set_error(GS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
@@ -440,8 +606,9 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
     uint32_t* fill = (uint32_t*)(ws + L.off_fill);
     uint32_t* start = (uint32_t*)(ws + L.off_start);
     u64* tmp = (u64*)(ws + L.off_tmp);
+    uint32_t* hist = ntiles <= AGG_MAX_TILES ? (uint32_t*)(ws + L.off_hist) : nullptr;
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, st) != cudaSuccess) return set_error(GS_ERR_CUDA, "memset bin state");
-    if ((s = launch_count(cam, rec_dtype, splats, n, count, st)) != GS_OK) return s;
+    if ((s = launch_count(cam, rec_dtype, splats, n, count, hist, st)) != GS_OK) return s;
     unsigned int* err = status_ptr();
     if (!err) return set_error(GS_ERR_CUDA, "status word address");
     k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, keys_capacity, start, tile_ranges, n_keys_out, err);
@@ -453,19 +620,19 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
     if (n == 0 || keys_capacity == 0) return GS_OK;
     if (ntiles <= AGG_MAX_TILES) {
         if ((s = set_agg_smem_attrs()) != GS_OK) return s;
-        const int64_t per = agg_per_cta(n);
+        const int64_t per = agg_per_cta(n, ntiles);
         const unsigned nb = (unsigned)((n + per - 1) / per);
         const size_t sm = 2 * sizeof(uint32_t) * (size_t)ntiles;
         if (rec_dtype == GS_F32)
-            k_tile_scatter_agg<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, fill,
-                                                                   keys_capacity, (u64*)keys_out);
-        else if (rec_dtype == GS_BF16)
-            k_tile_scatter_agg<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, fill,
+            k_tile_scatter_rows<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, hist,
                                                                     keys_capacity, (u64*)keys_out);
+        else if (rec_dtype == GS_BF16)
+            k_tile_scatter_rows<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, hist,
+                                                                     keys_capacity, (u64*)keys_out);
         else
-            k_tile_scatter_agg<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, fill,
-                                                                   keys_capacity, (u64*)keys_out);
-        if ((s = check_launch("k_tile_scatter_agg")) != GS_OK) return s;
+            k_tile_scatter_rows<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, hist,
+                                                                    keys_capacity, (u64*)keys_out);
+        if ((s = check_launch("k_tile_scatter_rows")) != GS_OK) return s;
     } else {
         const unsigned nb = (unsigned)((n + BIN_THREADS - 1) / BIN_THREADS);
         if (rec_dtype == GS_F32)
@@ -488,6 +655,9 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
             if (dev >= 0 && dev < 64) attr_done[dev] = true;
         }
     }
+    k_tile_sort_small<<<(unsigned)((ntiles + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, 0, st>>>(
+        tile_ranges, tile_order, ntiles, (u64*)keys_out, vals_out);
+    if ((s = check_launch("k_tile_sort_small")) != GS_OK) return s;
     k_tile_sort<<<(unsigned)ntiles, TS_THREADS, TS_SMEM_KEYS * sizeof(u64), st>>>(tile_ranges, tile_order,
                                                                                  (u64*)keys_out, vals_out, tmp);
     return check_launch("k_tile_sort");

@@ -47,8 +47,21 @@ struct Grid {
     int W, H;        // full resolution
     int sx, sy;      // strides
     int Ws, Hs;      // sampled image
+    int tw, th;      // tile size in sampled pixels (powers of two)
+    int lw, lh;      // log2 of tw, th
     int TX, TY;      // tiles
 };
+
+// Tile side in sampled pixels for stride s: 16 / p2(s), at least 4, where
+// p2(s) is the smallest power of two >= s.  The tile's full-resolution
+// footprint stays ~16 pixels (the paper's tile), so a sampled pixel's tile
+// list does not grow with the stride.
+__host__ __device__ inline int tile_dim(int s) {
+    int p = 1;
+    while (p < s && p < 16) p <<= 1;
+    const int t = GS_TILE / p;
+    return t < 4 ? 4 : t;
+}
 
 __host__ __device__ inline Grid make_grid(const gs_camera& c) {
     Grid g;
@@ -58,8 +71,12 @@ __host__ __device__ inline Grid make_grid(const gs_camera& c) {
     g.sy = c.sy;
     g.Ws = (c.width + c.sx - 1) / c.sx;
     g.Hs = (c.height + c.sy - 1) / c.sy;
-    g.TX = (g.Ws + GS_TILE - 1) / GS_TILE;
-    g.TY = (g.Hs + GS_TILE - 1) / GS_TILE;
+    g.tw = tile_dim(c.sx);
+    g.th = tile_dim(c.sy);
+    g.lw = g.tw == 16 ? 4 : (g.tw == 8 ? 3 : 2);
+    g.lh = g.th == 16 ? 4 : (g.th == 8 ? 3 : 2);
+    g.TX = (g.Ws + g.tw - 1) / g.tw;
+    g.TY = (g.Hs + g.th - 1) / g.th;
     return g;
 }
 
@@ -79,7 +96,8 @@ __device__ __forceinline__ int pix_floor(float u) {
 // Tile rect [x0,x1) x [y0,y1) of a 2D Gaussian with mean (u, v) and integer
 // radius r: the sampled pixels inside the image whose full-resolution
 // position lies in the box [floor(u)-r, floor(u)+r] x [floor(v)-r, floor(v)+r]
-// (Sec. 2.1, Step 1-2; strides of Sec. 4.2).  Returns the tile count.
+// (Sec. 2.1, Step 1-2; strides of Sec. 4.2), in tiles of tw x th sampled
+// pixels.  Returns the tile count.
 __device__ __forceinline__ int tile_rect(const Grid& g, float u, float v, int r, int& x0, int& x1,
                                          int& y0, int& y1) {
     x0 = x1 = y0 = y1 = 0;
@@ -98,10 +116,10 @@ __device__ __forceinline__ int tile_rect(const Grid& g, float u, float v, int r,
     j0 = clampi(j0, 0, g.Hs);
     j1 = clampi(j1, -1, g.Hs - 1);
     if (i0 > i1 || j0 > j1) return 0;
-    x0 = i0 / GS_TILE;
-    x1 = i1 / GS_TILE + 1;
-    y0 = j0 / GS_TILE;
-    y1 = j1 / GS_TILE + 1;
+    x0 = i0 >> g.lw;  // i0, j0 >= 0 here
+    x1 = (i1 >> g.lw) + 1;
+    y0 = j0 >> g.lh;
+    y1 = (j1 >> g.lh) + 1;
     return (x1 - x0) * (y1 - y0);
 }
 

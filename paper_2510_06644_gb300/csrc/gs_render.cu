@@ -2,7 +2,9 @@
 // (Sec. 4.1, Eq. 6) and A-7 backward compositing (Sec. 2.2, Step 4: Eq. 4,
 // Eq. 5) on sm_103a.
 //
-// One CTA of 256 threads per 16x16 tile, one pixel per thread; CTAs are
+// One CTA per tile, one pixel per thread (256 threads for the 16x16 tiles
+// of a full-resolution image, fewer for the smaller sampled tiles of a
+// downsampled one, at least one warp); CTAs are
 // issued in the heavy-first tile order produced by the binning, so the block
 // scheduler starts the longest lists first (the GPU counterpart of the
 // paper's subtile streaming, Sec. 5.2).  The 8 warps cover 8x4 pixel blocks.
@@ -23,8 +25,8 @@
 
 namespace gs {
 
-#define R_THREADS 256
-#define R_BATCH 256
+#define R_THREADS 256            // largest CTA (16x16 tile)
+#define R_BATCH 256              // entries staged per batch, whatever the CTA size
 #define R_MASKW (R_BATCH / 32)
 
 struct StagedSplat {
@@ -41,20 +43,70 @@ struct PixelMap {
     int wx0, wx1, wy0, wy1;  // full-resolution extent of this warp's 8x4 block
 };
 
-__device__ __forceinline__ PixelMap map_pixel(const Grid& g, int tile) {
+// Threads serving one tile: tw * th, at least one warp.  Warps cover BW x BH
+// pixel blocks (8x4, or 4x8 for 4-wide tiles).
+__host__ __device__ inline int tile_threads(const Grid& g) {
+    const int t = g.tw * g.th;
+    return t < 32 ? 32 : t;
+}
+
+// Every CTA has R_THREADS threads and serves R_THREADS / TT tiles (TT =
+// tile_threads): a full-resolution 16x16 tile takes the whole CTA, the
+// smaller sampled tiles of a downsampled frame take groups of 2 or 1 warps,
+// each group with its own slice of the staging buffer and its own named
+// barrier, so a CTA always holds 8 warps.
+struct Group {
+    int TT;     // threads of the group
+    int gi;     // group index in the CTA
+    int lt;     // thread index in the group
+    int B;      // entries staged per batch
+    int tile;   // tile served, -1 if none
+};
+
+__device__ __forceinline__ Group make_group(const Grid& g, const uint32_t* order) {
+    Group G;
+    G.TT = tile_threads(g);
+    const int gpc = R_THREADS / G.TT;
+    G.gi = threadIdx.x / G.TT;
+    G.lt = threadIdx.x % G.TT;
+    G.B = R_BATCH / gpc;
+    const int t = blockIdx.x * gpc + G.gi;
+    G.tile = t < g.TX * g.TY ? (order ? (int)__ldg(order + t) : t) : -1;
+    return G;
+}
+
+__device__ __forceinline__ void group_sync(const Group& G) {
+    if (G.TT == R_THREADS) __syncthreads();
+    else if (G.TT == 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + G.gi), "r"(G.TT) : "memory");
+}
+
+// Number of threads of the group with `pred` set (also a group barrier).
+__device__ __forceinline__ int group_count(const Group& G, bool pred) {
+    if (G.TT == R_THREADS) return __syncthreads_count(pred);
+    if (G.TT == 32) return __popc(__ballot_sync(0xffffffffu, pred));
+    int r;
+    asm volatile("{ .reg .pred p; setp.ne.u32 p, %3, 0; bar.red.popc.u32 %0, %1, %2, p; }"
+                 : "=r"(r) : "r"(1 + G.gi), "r"(G.TT), "r"((unsigned)pred) : "memory");
+    return r;
+}
+
+__device__ __forceinline__ PixelMap map_pixel(const Grid& g, int tile, int lt) {
     PixelMap m;
     const int tx = tile % g.TX, ty = tile / g.TX;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int bx = (w & 1) * 8, by = (w >> 1) * 4;
-    m.i = tx * GS_TILE + bx + (lane & 7);
-    m.j = ty * GS_TILE + by + (lane >> 3);
-    m.inside = m.i < g.Ws && m.j < g.Hs;
+    const int lane = lt & 31, w = lt >> 5;
+    const int BW = g.tw < 8 ? g.tw : 8, BH = 32 / BW, WX = g.tw / BW;
+    const int bx = (w % WX) * BW, by = (w / WX) * BH;
+    const int lx = lane % BW, ly = lane / BW;
+    m.i = tx * g.tw + bx + lx;
+    m.j = ty * g.th + by + ly;
+    m.inside = by + ly < g.th && m.i < g.Ws && m.j < g.Hs;
     m.px = m.i * g.sx;
     m.py = m.j * g.sy;
-    m.wx0 = (tx * GS_TILE + bx) * g.sx;
-    m.wx1 = (tx * GS_TILE + bx + 7) * g.sx;
-    m.wy0 = (ty * GS_TILE + by) * g.sy;
-    m.wy1 = (ty * GS_TILE + by + 3) * g.sy;
+    m.wx0 = (tx * g.tw + bx) * g.sx;
+    m.wx1 = (tx * g.tw + bx + BW - 1) * g.sx;
+    m.wy0 = (ty * g.th + by) * g.sy;
+    m.wy1 = (ty * g.th + by + BH - 1) * g.sy;
     return m;
 }
 
@@ -97,23 +149,20 @@ __device__ __forceinline__ void stage(const void* splats, uint32_t gid, float al
 }
 
 // Bit e of word q set when staged entry 32q + e (below `limit`) meets the
-// warp's block.
-__device__ __forceinline__ void warp_masks(const StagedSplat* sp, int limit, const PixelMap& m, unsigned* mask) {
+// warp's block; words at or beyond `words` are cleared.
+__device__ __forceinline__ void warp_masks(const StagedSplat* sp, int limit, int words, const PixelMap& m,
+                                           unsigned* mask) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int q = 0; q < R_MASKW; ++q) {
         const int e = q * 32 + lane;
         bool hit = false;
-        if (e < limit) {
+        if (q < words && e < limit) {
             const int4 box = sp[e].box;
             hit = !(box.y < m.wx0 || box.x > m.wx1 || box.w < m.wy0 || box.z > m.wy1);
         }
         mask[q] = __ballot_sync(0xffffffffu, hit);
     }
-}
-
-__device__ __forceinline__ int tile_of(const uint32_t* order) {
-    return order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
 }
 
 template <int DT>
@@ -124,24 +173,28 @@ __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g,
                                                           float* __restrict__ out_rgb, float* __restrict__ out_depth,
                                                           float* __restrict__ out_t, uint32_t* __restrict__ out_last,
                                                           uint32_t* __restrict__ out_nb) {
-    __shared__ StagedSplat sp[R_BATCH];
-    const int tile = tile_of(order);
-    const PixelMap m = map_pixel(g, tile);
+    __shared__ StagedSplat sp_all[R_BATCH];
+    const Group G = make_group(g, order);
+    if (G.tile < 0) return;
+    StagedSplat* sp = sp_all + G.gi * G.B;
+    const int tile = G.tile;
+    const PixelMap m = map_pixel(g, tile, G.lt);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     uint32_t last = 0, nb = 0;
     bool done = !m.inside;
-    for (uint32_t b = start; b < end; b += R_BATCH) {
-        if (__syncthreads_count(done) == R_THREADS) break;
-        const int n_in = (int)min((uint32_t)R_BATCH, end - b);
-        if ((int)threadIdx.x < n_in) stage<DT>(splats, __ldg(vals + b + threadIdx.x), cfg.alpha_min, sp[threadIdx.x]);
-        __syncthreads();
+    const int words = G.B / 32;
+    for (uint32_t b = start; b < end; b += G.B) {
+        if (group_count(G, done) == G.TT) break;
+        const int n_in = (int)min((uint32_t)G.B, end - b);
+        for (int e = G.lt; e < n_in; e += G.TT) stage<DT>(splats, __ldg(vals + b + e), cfg.alpha_min, sp[e]);
+        group_sync(G);
         if (!__all_sync(0xffffffffu, done)) {
             unsigned mask[R_MASKW];
-            warp_masks(sp, n_in, m, mask);
+            warp_masks(sp, n_in, words, m, mask);
 #pragma unroll 1
-            for (int q = 0; q < R_MASKW; ++q) {
+            for (int q = 0; q < words; ++q) {
                 unsigned mq = mask[q];
                 while (mq) {
                     const int e = q * 32 + __ffs(mq) - 1;
@@ -168,7 +221,7 @@ __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g,
                 if (__all_sync(0xffffffffu, done)) break;
             }
         }
-        __syncthreads();
+        group_sync(G);
     }
     if (m.inside) {
         const size_t P = (size_t)g.Ws * g.Hs;
@@ -275,12 +328,18 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
     constexpr int NS = Slots<MODE>::N;
     constexpr int LOG = Slots<MODE>::LOG;
     constexpr int SHIFT = 5 - LOG;  // lanes per slot = 1 << SHIFT
-    __shared__ StagedSplat sp[R_BATCH];
-    __shared__ uint32_t sid[R_BATCH];
-    __shared__ float acc[R_BATCH][NS];
-    __shared__ uint32_t s_max;
-    const int tile = tile_of(order);
-    const PixelMap m = map_pixel(g, tile);
+    __shared__ StagedSplat sp_all[R_BATCH];
+    __shared__ uint32_t sid_all[R_BATCH];
+    __shared__ float acc_all[R_BATCH][NS];
+    __shared__ uint32_t s_max_all[R_THREADS / 32];
+    const Group G = make_group(g, order);
+    if (G.tile < 0) return;
+    StagedSplat* sp = sp_all + G.gi * G.B;
+    uint32_t* sid = sid_all + G.gi * G.B;
+    float(*acc)[NS] = acc_all + G.gi * G.B;
+    uint32_t& s_max = s_max_all[G.gi];
+    const int tile = G.tile;
+    const PixelMap m = map_pixel(g, tile, G.lt);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
     const int lane = threadIdx.x & 31;
@@ -303,28 +362,29 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
     uint32_t wlast = last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
-    if (threadIdx.x == 0) s_max = 0;
-    __syncthreads();
+    if (G.lt == 0) s_max = 0;
+    group_sync(G);
     if (lane == 0) atomicMax(&s_max, wlast);
-    __syncthreads();
+    group_sync(G);
     const uint32_t end_eff = start + s_max;
+    const int words = G.B / 32;
     for (uint32_t hi = end_eff; hi > start;) {
-        const uint32_t lo = hi - start > R_BATCH ? hi - R_BATCH : start;
+        const uint32_t lo = hi - start > (uint32_t)G.B ? hi - G.B : start;
         const int n_in = (int)(hi - lo);
-        if ((int)threadIdx.x < n_in) {
-            const uint32_t gid = __ldg(vals + lo + threadIdx.x);
-            sid[threadIdx.x] = gid;
-            stage<DT>(splats, gid, cfg.alpha_min, sp[threadIdx.x]);
+        for (int e = G.lt; e < n_in; e += G.TT) {
+            const uint32_t gid = __ldg(vals + lo + e);
+            sid[e] = gid;
+            stage<DT>(splats, gid, cfg.alpha_min, sp[e]);
         }
-        for (int q = threadIdx.x; q < R_BATCH * NS; q += R_THREADS) (&acc[0][0])[q] = 0.f;
-        __syncthreads();
+        for (int q = G.lt; q < G.B * NS; q += G.TT) (&acc[0][0])[q] = 0.f;
+        group_sync(G);
         const uint32_t base_pos = lo - start;
         // entries at or beyond the warp's furthest blended position are skipped
         const int wlimit = (int)min((uint32_t)n_in, wlast > base_pos ? wlast - base_pos : 0u);
         unsigned mask[R_MASKW];
-        warp_masks(sp, wlimit, m, mask);
+        warp_masks(sp, wlimit, words, m, mask);
 #pragma unroll 1
-        for (int q = R_MASKW - 1; q >= 0; --q) {
+        for (int q = words - 1; q >= 0; --q) {
             unsigned mq = mask[q];
             while (mq) {
                 const int bit = 31 - __clz(mq);
@@ -341,8 +401,8 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
                     const float4 B = sp[e].b;
                     const float dx = pxc - A.x, dy = pyc - A.y;
                     const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                    const float G = __expf(power);
-                    const float raw = B.y * G;
+                    const float gk = __expf(power);
+                    const float raw = B.y * gk;
                     const float alpha = fminf(cfg.alpha_max, raw);
                     contrib = !(power > 0.f) && !(alpha < cfg.alpha_min);
                     if (contrib) {
@@ -364,7 +424,7 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
                             f[5] = w * gD;
                         }
                         if (!(raw > cfg.alpha_max)) {
-                            if (MODE == GS_MAP) f[5] = G * dLda;
+                            if (MODE == GS_MAP) f[5] = gk * dLda;
                             const float dp = alpha * dLda;
                             f[2] = -0.5f * dx * dx * dp;
                             f[3] = -dx * dy * dp;
@@ -382,13 +442,13 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
                 }
             }
         }
-        __syncthreads();
-        for (int q = threadIdx.x; q < n_in * NS; q += R_THREADS) {
+        group_sync(G);
+        for (int q = G.lt; q < n_in * NS; q += G.TT) {
             const float v = (&acc[0][0])[q];
             const int col = slot_col<MODE>(q % NS);
             if (v != 0.f && col >= 0) atomicAdd(grad2d + (size_t)sid[q / NS] * GS_GRAD2D_STRIDE + col, v);
         }
-        __syncthreads();
+        group_sync(G);
         hi = lo;
     }
 }
@@ -421,7 +481,8 @@ extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, i
     if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
         return set_error(GS_ERR_INVALID_ARG, "an image or range pointer is NULL");
     const Grid g = make_grid(*cam);
-    const unsigned nt = (unsigned)(g.TX * g.TY);
+    const int gpc = R_THREADS / tile_threads(g);
+    const unsigned nt = (unsigned)((g.TX * g.TY + gpc - 1) / gpc);
     cudaStream_t st = (cudaStream_t)stream;
 #define GS_RF(DT) \
     k_render_fwd<DT><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx, \
@@ -454,6 +515,7 @@ extern "C" gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, cons
 
 size_t gs_project_bwd_ws(int64_t n);
 
+
 extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* gsn,
                                    int rec_dtype, const void* splats, const uint32_t* vals,
                                    const uint32_t* tile_ranges, const uint32_t* tile_order, const float* t_final,
@@ -478,7 +540,8 @@ extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, c
     if (n > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_STRIDE * (size_t)n, st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset grad2d");
     const Grid g = make_grid(*cam);
-    const unsigned nt = (unsigned)(g.TX * g.TY);
+    const int gpc = R_THREADS / tile_threads(g);
+    const unsigned nt = (unsigned)((g.TX * g.TY + gpc - 1) / gpc);
 #define GS_RB(DT, MD)                                                                                              \
     k_render_bwd<DT, MD><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, t_final, last_idx, \
                                                    d_rgb, d_depth, grad2d)

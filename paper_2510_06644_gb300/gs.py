@@ -154,6 +154,15 @@ def default_config(**overrides) -> gs_config:
     return c
 
 
+def tile_dim(s):
+    """Tile side in sampled pixels at stride s: 16 / p2(s), at least 4
+    (p2 = smallest power of two >= s), as in include/gs.h."""
+    p = 1
+    while p < s and p < TILE:
+        p *= 2
+    return max(4, TILE // p)
+
+
 def grid(cam):
     """(Ws, Hs, TX, TY) of a camera dict or gs_camera."""
     if isinstance(cam, gs_camera):
@@ -161,7 +170,7 @@ def grid(cam):
     else:
         W, H, sx, sy = int(cam["W"]), int(cam["H"]), int(cam.get("sx", 1)), int(cam.get("sy", 1))
     Ws, Hs = -(-W // sx), -(-H // sy)
-    return Ws, Hs, -(-Ws // TILE), -(-Hs // TILE)
+    return Ws, Hs, -(-Ws // tile_dim(sx)), -(-Hs // tile_dim(sy))
 
 
 def gaussians(g, mask=None) -> gs_gaussians:

@@ -65,14 +65,22 @@ class Rasterizer:
         return self._ws_bwd
 
     # -- stages ------------------------------------------------------------
-    def forward(self, g, cam):
+    def forward(self, g, cam, rebin=True):
         """Projection, binning + sort and forward compositing; returns the
-        image buffers (rgb, depth, t_final, last_idx)."""
+        image buffers (rgb, depth, t_final, last_idx, n_blended).
+
+        rebin=False keeps the tile lists, ranges and order of the last
+        binning (the reuse of tile intersection and sorting across the
+        iterations of a pruning interval, Sec. 4.1 / Obs. 6): the Gaussians
+        are re-projected with the current pose, but each tile composites the
+        Gaussians it held when the lists were built."""
         cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam)
         self.set_grid(cam_s)
         gs.gs_project(self.cfg, cam_s, g, self.rec_dtype, self.splats)
-        gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
-                       keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges, order=self.order)
+        if rebin:
+            gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
+                           keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges,
+                           order=self.order)
         gs.gs_render_fwd(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, self.rec_dtype, out=self.img,
                          order=self.order)
         return self.img
@@ -90,10 +98,10 @@ class Rasterizer:
                          score=self.score if want_score else None, ws=self._bwd_ws(cam_s, g), order=self.order)
         return self.grad2d
 
-    def step(self, g, cam, target_rgb, target_depth, mode=gs.GS_TRACK, grads=None):
+    def step(self, g, cam, target_rgb, target_depth, mode=gs.GS_TRACK, grads=None, rebin=True):
         """One whole iteration: forward, L1 loss (Eq. 6) and backward."""
         cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam)
-        self.forward(g, cam_s)
+        self.forward(g, cam_s, rebin=rebin)
         self.loss_grad(cam_s, target_rgb, target_depth)
         self.backward(g, cam_s, self.dimg["d_rgb"], self.dimg["d_depth"], mode, grads)
         return self.pose

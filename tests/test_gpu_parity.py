@@ -40,7 +40,8 @@ def O():
 
 def gpu_bin(G, cam, rec, n, cap=None):
     cs = G.camera(cam)
-    cap = cap if cap is not None else max(8 * n, 1024)
+    if cap is None:
+        cap = max(int(G.gs_bin_count(cs, rec, n).item()), 1024)
     keys, vals, nk, ranges, order = G.gs_bin_sort(cs, rec, n, cap)
     torch.cuda.synchronize()
     k = int(nk.item())
@@ -118,6 +119,21 @@ def test_bin_sort_bit_exact(G, O, n, W, H, sx, sy, seed, sig):
     assert np.array_equal(vals, ov)
     assert np.array_equal(ranges, orr)
     assert G.gs_status_poll()[0] == G.GS_OK
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 64, 65, 200, 257, 511, 512, 513, 1000, 2049, 4097, 8191, 8192])
+def test_bin_sort_one_bucket_each_network_size(G, O, n):
+    """One 16x16 tile: the bucket sizes straddle every sorting-network size
+    (warp networks of 32..512 keys, CTA networks of 1024..8192 keys)."""
+    cam = S.camera(16, 16, 100.0)
+    s = S.splats(n, 16, 16, seed=9100 + n, sigma_px=(0.6, 40.0), tie_frac=0.2, cull_frac=0.0)
+    s["uv"] = S.rng(9200 + n).uniform(0.0, 16.0, (n, 2)).astype(np.float32)
+    keys, vals, ranges, _, _ = gpu_bin(G, cam, pack_splats(s), n)
+    ok, ov, orr = O.bin_sort(s["uv"], s["depth"], s["radius"], cam)
+    assert keys.shape == ok.shape == (n,)
+    assert np.array_equal(keys, ok)
+    assert np.array_equal(vals, ov)
+    assert np.array_equal(ranges, orr)
 
 
 def test_bin_sort_empty_and_all_culled(G, O):
@@ -405,3 +421,37 @@ def test_downsample_schedule_and_gather(G, O):
         assert np.array_equal(np_of(out), O.gather(full, sx, sy).astype(np.float32))
     sx, sy, out = G.gs_downsample(10, 10, True, 2, torch.from_numpy(full).cuda())
     assert (sx, sy) == (1, 1) and np.array_equal(np_of(out), full)
+
+
+# ---------------------------------------------------------------------------
+# N1: reuse of the tile lists across the iterations of a pruning interval
+# ---------------------------------------------------------------------------
+
+def test_reused_lists_match_oracle_with_the_same_stale_lists(G, O):
+    """Lists built at pose P0, Gaussians re-projected at P1 (Sec. 4.1: tile
+    intersection and sorting reused for the K iterations of an interval):
+    the GPU and the oracle composite P1's splats through P0's lists."""
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    g = S.surface_scene(40000, seed=91)
+    cam0 = S.camera(320, 240, 260.0)
+    cam1 = S.perturbed_pose(cam0, seed=92, trans=0.01, rot_deg=0.5)
+    gd = dev(g)
+    r = Rasterizer(40000, cam0)
+    r.forward(gd, cam0)
+    r.forward(gd, cam1, rebin=False)
+    d_rgb, d_dep = S.image_grads(320, 240, 93)
+    r.backward(gd, cam1, torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=G.GS_MAP)
+    r.check()
+    pr0 = O.project(g, cam0)
+    _, vals0, ranges0 = O.bin_sort(pr0["uv"], pr0["depth"], pr0["radius"], cam0)
+    pr1 = O.project(g, cam1)
+    img = O.render_fwd(pr1, cam1, lists=(vals0, ranges0))
+    good = img["margin"] == 0
+    assert good.mean() > 0.99
+    assert np.abs(np_of(r.img["rgb"]) - img["rgb"]).max(0)[good].max() <= IMG_TOL
+    fresh = O.render_fwd(pr1, cam1)
+    assert np.abs(fresh["rgb"] - img["rgb"]).max() > 0       # the reuse is an approximation
+    ref = O.render_bwd(pr1, cam1, d_rgb, d_dep, lists=(vals0, ranges0))
+    g2 = np_of(r.grad2d)
+    for name, cols in GROUPS.items():
+        assert rel_l2(g2[:, cols], ref[:, cols]) <= GRAD_TOL, name

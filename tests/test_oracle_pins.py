@@ -253,10 +253,13 @@ def test_binning_hand_cases(oracle_lib):
     assert ranges[8].tolist() == [1, 2] and ranges[9].tolist() == [2, 3]
     assert ranges[11].tolist() == [3, 4]
     assert ranges[0].tolist() == [0, 0]
-    # stride 2: sampled columns of G0 are 8..12 -> tile col 0
+    # stride 2: tiles are 8x8 sampled pixels; the sampled columns of G0 are
+    # 8..12 -> tile column 1, rows 1..4 -> tile row 0; TX = ceil(32/8) = 4
     cam2 = dict(cam, sx=2, sy=2)
     k2, v2, r2 = O.bin_sort(uv[:1], depth[:1], radius[:1], cam2)
-    assert [int(k) >> 32 for k in k2] == [0]
+    assert [int(k) >> 32 for k in k2] == [1]
+    assert O.tile_dim(1) == 16 and O.tile_dim(2) == 8 and O.tile_dim(3) == 4 and O.tile_dim(4) == 4
+    assert O.tile_dim(100) == 4
 
 
 def test_sort_invariants_and_stability(oracle_lib):
