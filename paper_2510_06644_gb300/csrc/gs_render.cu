@@ -26,8 +26,11 @@
 namespace gs {
 
 #define R_THREADS 256            // largest CTA (16x16 tile)
-#define R_BATCH 256              // entries staged per batch, whatever the CTA size
+#define R_BATCH 256              // largest batch of entries a tile stages at a time
 #define R_MASKW (R_BATCH / 32)
+#define R_FWD_SMEM (8 * R_BATCH * 64)   // forward staging: up to 8 tiles x 256 x 64 B
+#define R_BWD_SMEM (104 * 1024)         // backward staging budget per CTA
+#define R_STEP 4                 // list entries evaluated side by side in the forward walk
 
 struct StagedSplat {
     float4 a;   // x, y, conic_a, conic_b
@@ -63,13 +66,13 @@ struct Group {
     int tile;   // tile served, -1 if none
 };
 
-__device__ __forceinline__ Group make_group(const Grid& g, const uint32_t* order) {
+__device__ __forceinline__ Group make_group(const Grid& g, const uint32_t* order, int B) {
     Group G;
     G.TT = tile_threads(g);
     const int gpc = R_THREADS / G.TT;
     G.gi = threadIdx.x / G.TT;
     G.lt = threadIdx.x % G.TT;
-    G.B = R_BATCH / gpc;
+    G.B = B;
     const int t = blockIdx.x * gpc + G.gi;
     G.tile = t < g.TX * g.TY ? (order ? (int)__ldg(order + t) : t) : -1;
     return G;
@@ -139,20 +142,46 @@ __device__ __forceinline__ int4 pixel_box(const Splat& v, float alpha_min) {
     return box;
 }
 
-template <int DT>
-__device__ __forceinline__ void stage(const void* splats, uint32_t gid, float alpha_min, StagedSplat& s) {
-    const Splat v = load_splat<DT>(splats, gid);
+__device__ __forceinline__ void fill_staged(const Splat& v, float alpha_min, StagedSplat& s) {
     s.a = make_float4(v.x, v.y, v.ca, v.cb);
     s.b = make_float4(v.cc, v.op, v.depth, 0.f);
     s.c = make_float4(v.r, v.g, v.b, 0.f);
     s.box = pixel_box(v, alpha_min);
 }
 
-// Bit e of word q set when staged entry 32q + e (below `limit`) meets the
-// warp's block; words at or beyond `words` are cleared.
-__device__ __forceinline__ void warp_masks(const StagedSplat* sp, int limit, int words, const PixelMap& m,
-                                           unsigned* mask) {
+// Stages list entries [0, n_in) of `ids` into sp[] (and their ids into sid[]
+// when given) with the group's TT threads.  Each thread gathers KST records
+// before it converts any, so KST dependent id -> record loads are in flight
+// per thread (KST = 4 for the small groups of downsampled frames, which
+// stage several entries per thread; 1 for full-resolution tiles).
+template <int DT, int KST>
+__device__ __forceinline__ void stage_batch(const void* __restrict__ splats, const uint32_t* __restrict__ ids,
+                                            int n_in, int lt, int TT, float alpha_min, StagedSplat* sp,
+                                            uint32_t* sid) {
+    for (int e0 = lt; e0 < n_in; e0 += KST * TT) {
+        uint32_t id[KST];
+#pragma unroll
+        for (int k = 0; k < KST; ++k) id[k] = e0 + k * TT < n_in ? __ldg(ids + e0 + k * TT) : 0u;
+        Splat v[KST];
+#pragma unroll
+        for (int k = 0; k < KST; ++k)
+            if (e0 + k * TT < n_in) v[k] = load_splat<DT>(splats, id[k]);
+#pragma unroll
+        for (int k = 0; k < KST; ++k)
+            if (e0 + k * TT < n_in) {
+                fill_staged(v[k], alpha_min, sp[e0 + k * TT]);
+                if (sid) sid[e0 + k * TT] = id[k];
+            }
+    }
+}
+
+// Overlap masks of the staged entries with the warp's block: bit e of word q
+// is set when entry 32q + e (below `limit`) meets the block.  Lane q returns
+// word q (words at or beyond `words` are zero), so a word is one shuffle away
+// and the masks stay in registers.
+__device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit, int words, const PixelMap& m) {
     const int lane = threadIdx.x & 31;
+    unsigned mine = 0u;
 #pragma unroll
     for (int q = 0; q < R_MASKW; ++q) {
         const int e = q * 32 + lane;
@@ -161,20 +190,47 @@ __device__ __forceinline__ void warp_masks(const StagedSplat* sp, int limit, int
             const int4 box = sp[e].box;
             hit = !(box.y < m.wx0 || box.x > m.wx1 || box.w < m.wy0 || box.z > m.wy1);
         }
-        mask[q] = __ballot_sync(0xffffffffu, hit);
+        const unsigned w = __ballot_sync(0xffffffffu, hit);
+        if (lane == q) mine = w;
     }
+    return mine;
 }
 
-template <int DT>
-__global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g, const void* __restrict__ splats,
+// Exponent of the 2D Gaussian (Eq. 2) at offset (dx, dy) from its mean, with
+// conic (ca, cb, cc).  The operations are spelled out (no contraction left to
+// the compiler) so that every compositing kernel, forward and backward,
+// computes the same value and so takes the same blending decisions.
+__device__ __forceinline__ float gauss_power(float ca, float cb, float cc, float dx, float dy) {
+    const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), xy = __fmul_rn(dx, dy);
+    const float q = __fmaf_rn(cc, yy, __fmul_rn(ca, xx));
+    return __fmaf_rn(-cb, xy, __fmul_rn(-0.5f, q));
+}
+
+// Alpha of a staged Gaussian at the pixel (Eq. 2), or -1 when the pixel is
+// outside its box or the exponent is positive (the fragment is skipped).
+__device__ __forceinline__ float frag_alpha(const StagedSplat& s, const PixelMap& m, float pxc, float pyc,
+                                           float alpha_max) {
+    const int4 box = s.box;
+    const float4 A = s.a;
+    const float cc = s.b.x, op = s.b.y;
+    const float dx = pxc - A.x, dy = pyc - A.y;
+    const float power = gauss_power(A.z, A.w, cc, dx, dy);
+    const float alpha = fminf(alpha_max, op * __expf(power));
+    const bool in = m.px >= box.x && m.px <= box.y && m.py >= box.z && m.py <= box.w && !(power > 0.f);
+    return in ? alpha : -1.f;
+}
+
+template <int DT, int KST>
+__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2) k_render_fwd(gs_config cfg, Grid g, const void* __restrict__ splats,
                                                           const uint32_t* __restrict__ vals,
                                                           const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ order,
                                                           float* __restrict__ out_rgb, float* __restrict__ out_depth,
                                                           float* __restrict__ out_t, uint32_t* __restrict__ out_last,
-                                                          uint32_t* __restrict__ out_nb) {
-    __shared__ StagedSplat sp_all[R_BATCH];
-    const Group G = make_group(g, order);
+                                                          uint32_t* __restrict__ out_nb, int B) {
+    extern __shared__ __align__(16) unsigned char r_smem[];
+    StagedSplat* sp_all = reinterpret_cast<StagedSplat*>(r_smem);
+    const Group G = make_group(g, order, B);
     if (G.tile < 0) return;
     StagedSplat* sp = sp_all + G.gi * G.B;
     const int tile = G.tile;
@@ -188,35 +244,52 @@ __global__ void __launch_bounds__(R_THREADS) k_render_fwd(gs_config cfg, Grid g,
     for (uint32_t b = start; b < end; b += G.B) {
         if (group_count(G, done) == G.TT) break;
         const int n_in = (int)min((uint32_t)G.B, end - b);
-        for (int e = G.lt; e < n_in; e += G.TT) stage<DT>(splats, __ldg(vals + b + e), cfg.alpha_min, sp[e]);
+        stage_batch<DT, KST>(splats, vals + b, n_in, G.lt, G.TT, cfg.alpha_min, sp, nullptr);
         group_sync(G);
         if (!__all_sync(0xffffffffu, done)) {
-            unsigned mask[R_MASKW];
-            warp_masks(sp, n_in, words, m, mask);
+            const unsigned mword = warp_masks(sp, n_in, words, m);
+            const uint32_t base = b - start;
 #pragma unroll 1
             for (int q = 0; q < words; ++q) {
-                unsigned mq = mask[q];
+                unsigned mq = __shfl_sync(0xffffffffu, mword, q);
                 while (mq) {
-                    const int e = q * 32 + __ffs(mq) - 1;
-                    mq &= mq - 1u;
-                    const int4 box = sp[e].box;
-                    if (done || m.px < box.x || m.px > box.y || m.py < box.z || m.py > box.w) continue;
-                    const float4 A = sp[e].a;
-                    const float dx = pxc - A.x, dy = pyc - A.y;
-                    const float4 B = sp[e].b;
-                    const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                    if (power > 0.f) continue;
-                    const float alpha = fminf(cfg.alpha_max, B.y * __expf(power));
-                    if (alpha < cfg.alpha_min) continue;
-                    const float Tn = T * (1.f - alpha);
-                    if (Tn < cfg.t_eps) { done = true; continue; }
-                    const float w = alpha * T;
-                    const float4 Cc = sp[e].c;
-                    C0 += w * Cc.x; C1 += w * Cc.y; C2 += w * Cc.z;
-                    D += w * B.z;
-                    T = Tn;
-                    ++nb;
-                    last = b - start + (uint32_t)e + 1u;
+                    // R_STEP entries per step: their alphas do not depend on
+                    // T, so they are evaluated side by side; the blends then
+                    // run in list order without branches (a skipped fragment
+                    // adds zero weight).  Front to back, a fragment with
+                    // alpha >= alpha_min is blended unless it would take T
+                    // below t_eps, where the pixel stops (Eq. 3).
+                    int eu[R_STEP];
+                    float au[R_STEP];
+#pragma unroll
+                    for (int u = 0; u < R_STEP; ++u) {
+                        eu[u] = mq ? q * 32 + __ffs(mq) - 1 : -1;
+                        mq &= mq - 1u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < R_STEP; ++u)
+                        au[u] = eu[u] >= 0 ? frag_alpha(sp[eu[u]], m, pxc, pyc, cfg.alpha_max) : -1.f;
+#pragma unroll
+                    for (int u = 0; u < R_STEP; ++u) {
+                        const float alpha = au[u];
+                        const bool valid = !done && alpha >= cfg.alpha_min;
+                        const float Tn = T * (1.f - alpha);
+                        const bool stop = valid && Tn < cfg.t_eps;
+                        const bool ok = valid && !stop;
+                        done = done || stop;
+                        const int e = eu[u] >= 0 ? eu[u] : 0;
+                        const float4 Cc = sp[e].c;
+                        const float dep = sp[e].b.z;
+                        const float w = ok ? alpha * T : 0.f;
+                        C0 += w * Cc.x;
+                        C1 += w * Cc.y;
+                        C2 += w * Cc.z;
+                        D += w * dep;
+                        T = ok ? Tn : T;
+                        nb += ok ? 1u : 0u;
+                        last = ok ? base + (uint32_t)e + 1u : last;
+                    }
+                    if (__all_sync(0xffffffffu, done)) break;
                 }
                 if (__all_sync(0xffffffffu, done)) break;
             }
@@ -315,8 +388,34 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
     return x;
 }
 
-template <int DT, int MODE>
-__global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g, const void* __restrict__ splats,
+// Per-fragment quantities of the backward that do not depend on the
+// running state: offsets, Gaussian falloff G, unclamped and clamped alpha,
+// and whether the fragment was blended (inside the box, exponent <= 0,
+// alpha >= alpha_min, before the pixel's last blended position).
+struct FragGeo {
+    float dx, dy, gk, raw, alpha;
+    bool contrib;
+};
+
+__device__ __forceinline__ FragGeo frag_geo(const StagedSplat& s, const PixelMap& m, float pxc, float pyc,
+                                            const gs_config& cfg, bool before_last) {
+    FragGeo f;
+    const int4 box = s.box;
+    const float4 A = s.a;
+    const float cc = s.b.x, op = s.b.y;
+    f.dx = pxc - A.x;
+    f.dy = pyc - A.y;
+    const float power = gauss_power(A.z, A.w, cc, f.dx, f.dy);
+    f.gk = __expf(power);
+    f.raw = op * f.gk;
+    f.alpha = fminf(cfg.alpha_max, f.raw);
+    f.contrib = before_last && m.px >= box.x && m.px <= box.y && m.py >= box.z && m.py <= box.w &&
+                !(power > 0.f) && !(f.alpha < cfg.alpha_min);
+    return f;
+}
+
+template <int DT, int MODE, int KST>
+__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 3 : 2) k_render_bwd(gs_config cfg, Grid g, const void* __restrict__ splats,
                                                           const uint32_t* __restrict__ vals,
                                                           const uint32_t* __restrict__ ranges,
                                                           const uint32_t* __restrict__ order,
@@ -324,15 +423,18 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
                                                           const uint32_t* __restrict__ last_idx,
                                                           const float* __restrict__ d_rgb,
                                                           const float* __restrict__ d_depth,
-                                                          float* __restrict__ grad2d) {
+                                                          float* __restrict__ grad2d, int B) {
     constexpr int NS = Slots<MODE>::N;
     constexpr int LOG = Slots<MODE>::LOG;
     constexpr int SHIFT = 5 - LOG;  // lanes per slot = 1 << SHIFT
-    __shared__ StagedSplat sp_all[R_BATCH];
-    __shared__ uint32_t sid_all[R_BATCH];
-    __shared__ float acc_all[R_BATCH][NS];
+    constexpr int BSTEP = KST == 1 ? 1 : 2;  // entries per backward step
+    extern __shared__ __align__(16) unsigned char r_smem[];
     __shared__ uint32_t s_max_all[R_THREADS / 32];
-    const Group G = make_group(g, order);
+    const int gpc = R_THREADS / tile_threads(g);
+    StagedSplat* sp_all = reinterpret_cast<StagedSplat*>(r_smem);
+    uint32_t* sid_all = reinterpret_cast<uint32_t*>(sp_all + gpc * B);
+    float(*acc_all)[NS] = reinterpret_cast<float(*)[NS]>(sid_all + gpc * B);
+    const Group G = make_group(g, order, B);
     if (G.tile < 0) return;
     StagedSplat* sp = sp_all + G.gi * G.B;
     uint32_t* sid = sid_all + G.gi * G.B;
@@ -371,74 +473,80 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
     for (uint32_t hi = end_eff; hi > start;) {
         const uint32_t lo = hi - start > (uint32_t)G.B ? hi - G.B : start;
         const int n_in = (int)(hi - lo);
-        for (int e = G.lt; e < n_in; e += G.TT) {
-            const uint32_t gid = __ldg(vals + lo + e);
-            sid[e] = gid;
-            stage<DT>(splats, gid, cfg.alpha_min, sp[e]);
-        }
+        stage_batch<DT, KST>(splats, vals + lo, n_in, G.lt, G.TT, cfg.alpha_min, sp, sid);
         for (int q = G.lt; q < G.B * NS; q += G.TT) (&acc[0][0])[q] = 0.f;
         group_sync(G);
         const uint32_t base_pos = lo - start;
         // entries at or beyond the warp's furthest blended position are skipped
         const int wlimit = (int)min((uint32_t)n_in, wlast > base_pos ? wlast - base_pos : 0u);
-        unsigned mask[R_MASKW];
-        warp_masks(sp, wlimit, words, m, mask);
+        const unsigned mword = warp_masks(sp, wlimit, words, m);
+        // back to front over the fragments before `last`; T_k recovered by
+        // division (Eq. 5), A the normalised suffix sums of colour and depth
+        auto back = [&](int e, const FragGeo& fg, float (&f)[NS]) {
+#pragma unroll
+            for (int k = 0; k < NS; ++k) f[k] = 0.f;
+            if (!fg.contrib) return;
+            const float alpha = fg.alpha;
+            T = T / (1.f - alpha);
+            const float w = alpha * T;
+            const float4 Cc = sp[e].c;
+            const float dep = sp[e].b.z;
+            const float dLda = T * ((Cc.x - A0) * gC0 + (Cc.y - A1) * gC1 + (Cc.z - A2) * gC2 + (dep - AD) * gD);
+            A0 = alpha * Cc.x + (1.f - alpha) * A0;
+            A1 = alpha * Cc.y + (1.f - alpha) * A1;
+            A2 = alpha * Cc.z + (1.f - alpha) * A2;
+            AD = alpha * dep + (1.f - alpha) * AD;
+            if (MODE == GS_MAP) {
+                f[6] = w * gD;
+                f[7] = w * gC0;
+                f[8] = w * gC1;
+                f[9] = w * gC2;
+            } else {
+                f[5] = w * gD;
+            }
+            if (!(fg.raw > cfg.alpha_max)) {  // the clamp passes no gradient
+                const float4 Aq = sp[e].a;
+                const float cc = sp[e].b.x;
+                if (MODE == GS_MAP) f[5] = fg.gk * dLda;
+                const float dp = alpha * dLda;
+                f[2] = -0.5f * fg.dx * fg.dx * dp;
+                f[3] = -fg.dx * fg.dy * dp;
+                f[4] = -0.5f * fg.dy * fg.dy * dp;
+                f[0] = (Aq.z * fg.dx + Aq.w * fg.dy) * dp;
+                f[1] = (Aq.w * fg.dx + cc * fg.dy) * dp;
+            }
+        };
+        auto merge = [&](int e, float (&f)[NS]) {
+            const float v = warp_reduce_scatter<NS, LOG>(f);
+            if ((lane & ((1 << SHIFT) - 1)) == 0) {
+                const int sl = lane >> SHIFT;
+                if (slot_col<MODE>(sl) >= 0) atomicAdd(&acc[e][sl], v);
+            }
+        };
 #pragma unroll 1
         for (int q = words - 1; q >= 0; --q) {
-            unsigned mq = mask[q];
+            unsigned mq = __shfl_sync(0xffffffffu, mword, q);
             while (mq) {
-                const int bit = 31 - __clz(mq);
-                const int e = q * 32 + bit;
-                mq &= ~(1u << bit);
-                const int4 box = sp[e].box;
-                bool contrib = (base_pos + (uint32_t)e) < last && m.px >= box.x && m.px <= box.y &&
-                               m.py >= box.z && m.py <= box.w;
-                float f[NS];
+                // BSTEP entries per step, last first: their geometry does
+                // not depend on the running state
+                int eu[BSTEP];
 #pragma unroll
-                for (int s = 0; s < NS; ++s) f[s] = 0.f;
-                if (contrib) {
-                    const float4 A = sp[e].a;
-                    const float4 B = sp[e].b;
-                    const float dx = pxc - A.x, dy = pyc - A.y;
-                    const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
-                    const float gk = __expf(power);
-                    const float raw = B.y * gk;
-                    const float alpha = fminf(cfg.alpha_max, raw);
-                    contrib = !(power > 0.f) && !(alpha < cfg.alpha_min);
-                    if (contrib) {
-                        T = T / (1.f - alpha);
-                        const float w = alpha * T;
-                        const float4 Cc = sp[e].c;
-                        const float dLda = T * ((Cc.x - A0) * gC0 + (Cc.y - A1) * gC1 + (Cc.z - A2) * gC2 +
-                                                (B.z - AD) * gD);
-                        A0 = alpha * Cc.x + (1.f - alpha) * A0;
-                        A1 = alpha * Cc.y + (1.f - alpha) * A1;
-                        A2 = alpha * Cc.z + (1.f - alpha) * A2;
-                        AD = alpha * B.z + (1.f - alpha) * AD;
-                        if (MODE == GS_MAP) {
-                            f[6] = w * gD;
-                            f[7] = w * gC0;
-                            f[8] = w * gC1;
-                            f[9] = w * gC2;
-                        } else {
-                            f[5] = w * gD;
-                        }
-                        if (!(raw > cfg.alpha_max)) {
-                            if (MODE == GS_MAP) f[5] = gk * dLda;
-                            const float dp = alpha * dLda;
-                            f[2] = -0.5f * dx * dx * dp;
-                            f[3] = -dx * dy * dp;
-                            f[4] = -0.5f * dy * dy * dp;
-                            f[0] = (A.z * dx + A.w * dy) * dp;
-                            f[1] = (A.w * dx + B.x * dy) * dp;
-                        }
-                    }
+                for (int u = 0; u < BSTEP; ++u) {
+                    const int bit = mq ? 31 - __clz(mq) : -1;
+                    eu[u] = bit >= 0 ? q * 32 + bit : -1;
+                    if (bit >= 0) mq &= ~(1u << bit);
                 }
-                if (__ballot_sync(0xffffffffu, contrib) == 0u) continue;
-                const float v = warp_reduce_scatter<NS, LOG>(f);
-                if ((lane & ((1 << SHIFT) - 1)) == 0) {
-                    const int s = lane >> SHIFT;
-                    if (slot_col<MODE>(s) >= 0) atomicAdd(&acc[e][s], v);
+                FragGeo gu[BSTEP];
+#pragma unroll
+                for (int u = 0; u < BSTEP; ++u) {
+                    const int e = eu[u] >= 0 ? eu[u] : 0;
+                    gu[u] = frag_geo(sp[e], m, pxc, pyc, cfg, eu[u] >= 0 && base_pos + (uint32_t)e < last);
+                }
+#pragma unroll
+                for (int u = 0; u < BSTEP; ++u) {
+                    float f[NS];
+                    back(eu[u] >= 0 ? eu[u] : 0, gu[u], f);
+                    if (__any_sync(0xffffffffu, gu[u].contrib)) merge(eu[u], f);
                 }
             }
         }
@@ -453,9 +561,356 @@ __global__ void __launch_bounds__(R_THREADS) k_render_bwd(gs_config cfg, Grid g,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Entry-parallel compositing for the small tiles of downsampled frames
+// ---------------------------------------------------------------------------
+// With both strides >= 2 a tile holds at most 8x8 sampled pixels but covers
+// the same full-resolution area, hence the same list length, as a 16x16
+// tile: pixel-parallel warps would walk long lists with few (and far apart)
+// pixels.  Here one CTA of W warps serves a tile (W = 8 for up to 32
+// pixels, else 16); warp w takes PPW = ceil(pixels / W) of its pixels (2 to
+// 4) and lane l takes list entry
+// 32c + l of chunk c.  Front-to-back compositing (Eq. 3) becomes a product
+// scan: the transmittance before a valid entry is the pixel's T times the
+// product of (1 - alpha) over the valid entries of the chunk before it; the
+// pixel stops at the first valid entry that would take T below t_eps.  The
+// backward (Eq. 4, Eq. 5) scans the chunks from the pixel's last blended
+// entry back: T before an entry is T after the chunk divided by the suffix
+// product of (1 - alpha), and the colour behind it is a suffix sum, so
+//     dL/dalpha_k = T_k (c_k . g) - (sum_{j>k} w_j c_j . g + T_N bg . g) / (1 - alpha_k)
+// with g the pixel's image gradient.  Lane l keeps entry l's gradient over
+// the warp's pixels in registers and adds it once per chunk into the tile's
+// shared accumulators.  Entries are staged as four 16-byte arrays (lane l
+// reads element l: conflict-free).
+#define EP_B 256
+
+struct EpStage {
+    float4 a[EP_B];    // x, y, conic_a, conic_b
+    float4 b[EP_B];    // conic_c, opacity, depth, -
+    float4 c[EP_B];    // r, g, b, -
+    int4 box[EP_B];    // pixel box
+};
+
+template <int DT, int W>
+__device__ __forceinline__ void ep_stage(const void* __restrict__ splats, const uint32_t* __restrict__ ids, int n_in,
+                                         float alpha_min, EpStage& S, uint32_t* sid) {
+    for (int e = threadIdx.x; e < n_in; e += W * 32) {
+        const uint32_t id = __ldg(ids + e);
+        const Splat v = load_splat<DT>(splats, id);
+        S.a[e] = make_float4(v.x, v.y, v.ca, v.cb);
+        S.b[e] = make_float4(v.cc, v.op, v.depth, 0.f);
+        S.c[e] = make_float4(v.r, v.g, v.b, 0.f);
+        S.box[e] = pixel_box(v, alpha_min);
+        if (sid) sid[e] = id;
+    }
+}
+
+// Sampled pixel q of the tile: full-resolution coordinates, and whether it
+// lies in the image.
+__device__ __forceinline__ bool ep_pixel(const Grid& g, int tile, int q, int& i, int& j) {
+    const int tx = tile % g.TX, ty = tile / g.TX;
+    i = tx * g.tw + q % g.tw;
+    j = ty * g.th + q / g.tw;
+    return q < g.tw * g.th && i < g.Ws && j < g.Hs;
+}
+
+template <int DT, int W>
+__global__ void __launch_bounds__(W * 32) k_render_fwd_ep(gs_config cfg, Grid g,
+                                                                 const void* __restrict__ splats,
+                                                                 const uint32_t* __restrict__ vals,
+                                                                 const uint32_t* __restrict__ ranges,
+                                                                 const uint32_t* __restrict__ order,
+                                                                 float* __restrict__ out_rgb,
+                                                                 float* __restrict__ out_depth,
+                                                                 float* __restrict__ out_t,
+                                                                 uint32_t* __restrict__ out_last,
+                                                                 uint32_t* __restrict__ out_nb) {
+    __shared__ EpStage S;
+    const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ppw = (g.tw * g.th + W - 1) / W;
+    const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+    // lane j < ppw holds the state of the warp's pixel j
+    int mi, mj;
+    const bool mine = lane < ppw && ep_pixel(g, tile, warp * ppw + lane, mi, mj);
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    uint32_t last = 0, nb = 0;
+    bool done = !mine;
+    for (uint32_t b = start; b < end; b += EP_B) {
+        if (__syncthreads_count(!done) == 0) break;
+        const int n_in = (int)min((uint32_t)EP_B, end - b);
+        ep_stage<DT, W>(splats, vals + b, n_in, cfg.alpha_min, S, nullptr);
+        __syncthreads();
+        for (int j = 0; j < ppw; ++j) {
+            if (__shfl_sync(0xffffffffu, done, j)) continue;
+            int pi, pj;
+            ep_pixel(g, tile, warp * ppw + j, pi, pj);
+            const float pxc = (float)(pi * g.sx) + 0.5f, pyc = (float)(pj * g.sy) + 0.5f;
+            const int px = pi * g.sx, py = pj * g.sy;
+            float Tj = __shfl_sync(0xffffffffu, T, j);
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, pd = 0.f;
+            uint32_t lastj = 0, nbj = 0;
+            bool stopped = false;
+            for (int c = 0; c < n_in && !stopped; c += 32) {
+                const int e = c + lane;
+                float alpha = -1.f;
+                if (e < n_in) {
+                    const int4 box = S.box[e];
+                    const float4 A = S.a[e];
+                    const float2 B = make_float2(S.b[e].x, S.b[e].y);
+                    const float power = gauss_power(A.z, A.w, B.x, pxc - A.x, pyc - A.y);
+                    const float al = fminf(cfg.alpha_max, B.y * __expf(power));
+                    if (px >= box.x && px <= box.y && py >= box.z && py <= box.w && !(power > 0.f)) alpha = al;
+                }
+                const bool valid = alpha >= cfg.alpha_min;
+                if (__ballot_sync(0xffffffffu, valid) == 0u) continue;
+                const float f = valid ? 1.f - alpha : 1.f;
+                float P = f;  // inclusive product over lanes 0..l
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float y = __shfl_up_sync(0xffffffffu, P, o);
+                    if (lane >= o) P *= y;
+                }
+                float Tb = __shfl_up_sync(0xffffffffu, P, 1);  // T before this entry
+                Tb = lane == 0 ? Tj : Tj * Tb;
+                const float Tn = Tb * f;
+                const unsigned stop = __ballot_sync(0xffffffffu, valid && Tn < cfg.t_eps);
+                const int lstar = stop ? __ffs(stop) - 1 : 32;
+                const bool ok = valid && lane < lstar;
+                const float w = ok ? alpha * Tb : 0.f;
+                if (e < n_in) {
+                    const float4 Cc = S.c[e];
+                    p0 += w * Cc.x;
+                    p1 += w * Cc.y;
+                    p2 += w * Cc.z;
+                    pd += w * S.b[e].z;
+                }
+                const unsigned okm = __ballot_sync(0xffffffffu, ok);
+                nbj += __popc(okm);
+                if (okm) lastj = b - start + (uint32_t)(c + 32 - __clz(okm));
+                if (lstar < 32) {
+                    Tj = __shfl_sync(0xffffffffu, Tb, lstar);
+                    stopped = true;
+                } else {
+                    Tj = __shfl_sync(0xffffffffu, Tn, 31);
+                }
+            }
+            p0 = warp_sum(p0);
+            p1 = warp_sum(p1);
+            p2 = warp_sum(p2);
+            pd = warp_sum(pd);
+            if (lane == j) {
+                C0 += p0;
+                C1 += p1;
+                C2 += p2;
+                D += pd;
+                T = Tj;
+                if (lastj) last = lastj;
+                nb += nbj;
+                done = stopped;
+            }
+        }
+        __syncthreads();
+    }
+    if (mine) {
+        const size_t P = (size_t)g.Ws * g.Hs;
+        const size_t pix = (size_t)mj * g.Ws + mi;
+        out_rgb[pix] = C0 + T * cfg.bg[0];
+        out_rgb[P + pix] = C1 + T * cfg.bg[1];
+        out_rgb[2 * P + pix] = C2 + T * cfg.bg[2];
+        out_depth[pix] = D;
+        out_t[pix] = T;
+        out_last[pix] = last;
+        if (out_nb) out_nb[pix] = nb;
+    }
+}
+
+// Fields merged per entry: GS_TRACK du dv dA dB dC dd, GS_MAP du dv dA dB dC
+// dop dd dr dg db; ep_col gives their grad2d columns.
+template <int MODE>
+struct EpFields {
+    static constexpr int N = MODE == GS_MAP ? 10 : 6;
+};
+template <int MODE>
+__device__ __forceinline__ int ep_col(int f) {
+    if (MODE == GS_MAP) return f < 7 ? f : f + 1;
+    return f < 5 ? f : 6;
+}
+
+template <int DT, int MODE, int W>
+__global__ void __launch_bounds__(W * 32) k_render_bwd_ep(gs_config cfg, Grid g,
+                                                                 const void* __restrict__ splats,
+                                                                 const uint32_t* __restrict__ vals,
+                                                                 const uint32_t* __restrict__ ranges,
+                                                                 const uint32_t* __restrict__ order,
+                                                                 const float* __restrict__ t_final,
+                                                                 const uint32_t* __restrict__ last_idx,
+                                                                 const float* __restrict__ d_rgb,
+                                                                 const float* __restrict__ d_depth,
+                                                                 float* __restrict__ grad2d) {
+    constexpr int NF = EpFields<MODE>::N;
+    __shared__ EpStage S;
+    __shared__ uint32_t sid[EP_B];
+    __shared__ float acc[NF][EP_B];
+    __shared__ uint32_t s_max;
+    const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ppw = (g.tw * g.th + W - 1) / W;
+    const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+    int mi, mj;
+    const bool mine = lane < ppw && ep_pixel(g, tile, warp * ppw + lane, mi, mj);
+    // state of pixel `lane`: T after the part already walked, suffix colour
+    // dot product s, last blended position, image gradient
+    float T = 1.f, sdot = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, gd = 0.f;
+    uint32_t last = 0;
+    if (mine) {
+        const size_t P = (size_t)g.Ws * g.Hs;
+        const size_t pix = (size_t)mj * g.Ws + mi;
+        T = t_final[pix];
+        last = min(last_idx[pix], end - start);
+        g0 = d_rgb[pix];
+        g1 = d_rgb[P + pix];
+        g2 = d_rgb[2 * P + pix];
+        gd = d_depth[pix];
+        sdot = T * (cfg.bg[0] * g0 + cfg.bg[1] * g1 + cfg.bg[2] * g2);
+    }
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    uint32_t wl = last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
+    if (lane == 0) atomicMax(&s_max, wl);
+    __syncthreads();
+    const uint32_t tile_last = s_max;
+    // batches from the tile's furthest blended position back to the start
+    for (uint32_t hi = start + tile_last; hi > start;) {
+        const uint32_t lo = hi - start > (uint32_t)EP_B ? hi - EP_B : start;
+        const int n_in = (int)(hi - lo);
+        ep_stage<DT, W>(splats, vals + lo, n_in, cfg.alpha_min, S, sid);
+        for (int q = threadIdx.x; q < NF * EP_B; q += W * 32) (&acc[0][0])[q] = 0.f;
+        __syncthreads();
+        const uint32_t base_pos = lo - start;
+        for (int c = (n_in - 1) & ~31; c >= 0; c -= 32) {
+            const int e = c + lane;
+            const bool has = e < n_in;
+            // geometry of entry e, independent of the pixel's state except the offsets
+            float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Bv = A, Cc = A;
+            int4 box = make_int4(1, 0, 1, 0);
+            if (has) {
+                A = S.a[e];
+                Bv = S.b[e];
+                Cc = S.c[e];
+                box = S.box[e];
+            }
+            float ga[NF];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) ga[k] = 0.f;
+            for (int j = 0; j < ppw; ++j) {
+                const uint32_t lastj = __shfl_sync(0xffffffffu, last, j);
+                if (lastj <= base_pos + (uint32_t)c) continue;  // nothing blended at or after this chunk
+                int pi, pj;
+                ep_pixel(g, tile, warp * ppw + j, pi, pj);
+                const int px = pi * g.sx, py = pj * g.sy;
+                const float dx = (float)px + 0.5f - A.x, dy = (float)py + 0.5f - A.y;
+                const float power = gauss_power(A.z, A.w, Bv.x, dx, dy);
+                const float gk = __expf(power);
+                const float raw = Bv.y * gk;
+                const float alpha = fminf(cfg.alpha_max, raw);
+                const bool valid = has && base_pos + (uint32_t)e < lastj && px >= box.x && px <= box.y &&
+                                   py >= box.z && py <= box.w && !(power > 0.f) && !(alpha < cfg.alpha_min);
+                if (__ballot_sync(0xffffffffu, valid) == 0u) continue;
+                const float Tj = __shfl_sync(0xffffffffu, T, j);
+                const float sj = __shfl_sync(0xffffffffu, sdot, j);
+                const float q0 = __shfl_sync(0xffffffffu, g0, j), q1 = __shfl_sync(0xffffffffu, g1, j);
+                const float q2 = __shfl_sync(0xffffffffu, g2, j), qd = __shfl_sync(0xffffffffu, gd, j);
+                const float f = valid ? 1.f - alpha : 1.f;
+                float Q = f;  // inclusive suffix product over lanes l..31
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float y = __shfl_down_sync(0xffffffffu, Q, o);
+                    if (lane + o < 32) Q *= y;
+                }
+                const float Tb = Tj / Q;  // T before this entry (Eq. 5)
+                const float w = valid ? alpha * Tb : 0.f;
+                const float cg = Cc.x * q0 + Cc.y * q1 + Cc.z * q2 + Bv.z * qd;
+                const float wcg = w * cg;
+                float Ssuf = wcg;  // inclusive suffix sum of w (c . g)
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float y = __shfl_down_sync(0xffffffffu, Ssuf, o);
+                    if (lane + o < 32) Ssuf += y;
+                }
+                const float behind = sj + (Ssuf - wcg);  // colour behind this entry, dotted with g
+                if (valid) {
+                    const float dLda = Tb * cg - behind / f;
+                    if (MODE == GS_MAP) {
+                        ga[6] += w * qd;
+                        ga[7] += w * q0;
+                        ga[8] += w * q1;
+                        ga[9] += w * q2;
+                    } else {
+                        ga[5] += w * qd;
+                    }
+                    if (!(raw > cfg.alpha_max)) {  // the clamp passes no gradient
+                        if (MODE == GS_MAP) ga[5] += gk * dLda;
+                        const float dp = alpha * dLda;
+                        ga[2] += -0.5f * dx * dx * dp;
+                        ga[3] += -dx * dy * dp;
+                        ga[4] += -0.5f * dy * dy * dp;
+                        ga[0] += (A.z * dx + A.w * dy) * dp;
+                        ga[1] += (A.w * dx + Bv.x * dy) * dp;
+                    }
+                }
+                // state before this chunk: T divided by the chunk's product,
+                // the chunk's colour added behind
+                const float Qall = __shfl_sync(0xffffffffu, Q, 0);
+                const float Sall = __shfl_sync(0xffffffffu, Ssuf, 0);
+                if (lane == j) {
+                    T = Tj / Qall;
+                    sdot = sj + Sall;
+                }
+            }
+            if (has) {
+#pragma unroll
+                for (int k = 0; k < NF; ++k)
+                    if (ga[k] != 0.f) atomicAdd(&acc[k][e], ga[k]);
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < NF * n_in; q += W * 32) {
+            const int k = q / n_in, e = q % n_in;
+            const float v = acc[k][e];
+            if (v != 0.f) atomicAdd(grad2d + (size_t)sid[e] * GS_GRAD2D_STRIDE + ep_col<MODE>(k), v);
+        }
+        __syncthreads();
+        hi = lo;
+    }
+}
+
 }  // namespace gs
 
 using namespace gs;
+
+// Entries a tile stages per batch: 256, halved while the CTA's tiles would
+// need more than `budget` bytes of shared memory.
+static int group_batch(int gpc, int bytes_per_entry, int budget) {
+    int B = R_BATCH;
+    while (B > 32 && gpc * B * bytes_per_entry > budget) B >>= 1;
+    return B;
+}
+
+// Raises a kernel's dynamic shared-memory limit once per device and
+// instantiation (not repeated while a graph is being captured).
+static gs_status smem_once(const void* fn, int id, int bytes) {
+    static bool done[64][18] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && done[dev][id]) return GS_OK;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(render kernel %d)", id);
+    if (dev >= 0 && dev < 64) done[dev][id] = true;
+    return GS_OK;
+}
 
 static gs_status render_checks(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
                                int64_t n) {
@@ -481,15 +936,39 @@ extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, i
     if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
         return set_error(GS_ERR_INVALID_ARG, "an image or range pointer is NULL");
     const Grid g = make_grid(*cam);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (g.tw * g.th <= 64) {  // downsampled frame: entry-parallel tiles
+        const unsigned ntl = (unsigned)(g.TX * g.TY);
+#define GS_RFE(DT, W)                                                                                       \
+    k_render_fwd_ep<DT, W><<<ntl, W * 32, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, \
+                                                   t_final, last_idx, n_blended)
+#define GS_RFE_W(DT)                            \
+    if (g.tw * g.th <= 32) { GS_RFE(DT, 8); } \
+    else { GS_RFE(DT, 16); }
+        if (rec_dtype == GS_F32) { GS_RFE_W(GS_F32); }
+        else if (rec_dtype == GS_BF16) { GS_RFE_W(GS_BF16); }
+        else { GS_RFE_W(GS_F16); }
+#undef GS_RFE
+#undef GS_RFE_W
+        return check_launch("k_render_fwd_ep");
+    }
     const int gpc = R_THREADS / tile_threads(g);
     const unsigned nt = (unsigned)((g.TX * g.TY + gpc - 1) / gpc);
-    cudaStream_t st = (cudaStream_t)stream;
-#define GS_RF(DT) \
-    k_render_fwd<DT><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx, \
-                                               n_blended)
-    if (rec_dtype == GS_F32) GS_RF(GS_F32);
-    else if (rec_dtype == GS_BF16) GS_RF(GS_BF16);
-    else GS_RF(GS_F16);
+    const int B = group_batch(gpc, (int)sizeof(StagedSplat), R_FWD_SMEM);
+    const size_t smem = (size_t)gpc * B * sizeof(StagedSplat);
+#define GS_RF(DT, K)                                                                                         \
+    if ((s = smem_once((const void*)k_render_fwd<DT, K>, 2 * DT + (K > 1), R_FWD_SMEM)) != GS_OK) return s; \
+    k_render_fwd<DT, K><<<nt, R_THREADS, smem, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb,     \
+                                                     depth, t_final, last_idx, n_blended, B)
+    if (gpc == 1) {
+        if (rec_dtype == GS_F32) { GS_RF(GS_F32, 1); }
+        else if (rec_dtype == GS_BF16) { GS_RF(GS_BF16, 1); }
+        else { GS_RF(GS_F16, 1); }
+    } else {
+        if (rec_dtype == GS_F32) { GS_RF(GS_F32, 4); }
+        else if (rec_dtype == GS_BF16) { GS_RF(GS_BF16, 4); }
+        else { GS_RF(GS_F16, 4); }
+    }
 #undef GS_RF
     return check_launch("k_render_fwd");
 }
@@ -540,24 +1019,59 @@ extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, c
     if (n > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_STRIDE * (size_t)n, st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset grad2d");
     const Grid g = make_grid(*cam);
+    if (g.tw * g.th <= 64) {  // downsampled frame: entry-parallel tiles
+        const unsigned ntl = (unsigned)(g.TX * g.TY);
+#define GS_RBE(DT, MD, W)                                                                                   \
+    k_render_bwd_ep<DT, MD, W><<<ntl, W * 32, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, t_final, \
+                                                       last_idx, d_rgb, d_depth, grad2d)
+#define GS_RBE_W(DT, MD)                            \
+    if (g.tw * g.th <= 32) { GS_RBE(DT, MD, 8); } \
+    else { GS_RBE(DT, MD, 16); }
+        if (n > 0) {
+            if (mode == GS_MAP) {
+                if (rec_dtype == GS_F32) { GS_RBE_W(GS_F32, GS_MAP); }
+                else if (rec_dtype == GS_BF16) { GS_RBE_W(GS_BF16, GS_MAP); }
+                else { GS_RBE_W(GS_F16, GS_MAP); }
+            } else {
+                if (rec_dtype == GS_F32) { GS_RBE_W(GS_F32, GS_TRACK); }
+                else if (rec_dtype == GS_BF16) { GS_RBE_W(GS_BF16, GS_TRACK); }
+                else { GS_RBE_W(GS_F16, GS_TRACK); }
+            }
+            if ((s = check_launch("k_render_bwd_ep")) != GS_OK) return s;
+        }
+#undef GS_RBE
+#undef GS_RBE_W
+    } else {
     const int gpc = R_THREADS / tile_threads(g);
     const unsigned nt = (unsigned)((g.TX * g.TY + gpc - 1) / gpc);
-#define GS_RB(DT, MD)                                                                                              \
-    k_render_bwd<DT, MD><<<nt, R_THREADS, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, t_final, last_idx, \
-                                                   d_rgb, d_depth, grad2d)
+    const int per_entry = (int)(sizeof(StagedSplat) + sizeof(uint32_t) +
+                                sizeof(float) * (mode == GS_MAP ? Slots<GS_MAP>::N : Slots<GS_TRACK>::N));
+    const int B = group_batch(gpc, per_entry, R_BWD_SMEM);
+    const size_t smem = (size_t)gpc * B * per_entry;
+#define GS_RB(DT, MD, K)                                                                                       \
+    if ((s = smem_once((const void*)k_render_bwd<DT, MD, K>, 6 + 6 * (MD == GS_MAP) + 2 * DT + (K > 1),       \
+                       R_BWD_SMEM)) != GS_OK)                                                                  \
+        return s;                                                                                              \
+    k_render_bwd<DT, MD, K><<<nt, R_THREADS, smem, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order,       \
+                                                         t_final, last_idx, d_rgb, d_depth, grad2d, B)
+#define GS_RB_K(DT, MD)             \
+    if (gpc == 1) { GS_RB(DT, MD, 1); } \
+    else { GS_RB(DT, MD, 4); }
     if (n > 0) {
         if (mode == GS_MAP) {
-            if (rec_dtype == GS_F32) GS_RB(GS_F32, GS_MAP);
-            else if (rec_dtype == GS_BF16) GS_RB(GS_BF16, GS_MAP);
-            else GS_RB(GS_F16, GS_MAP);
+            if (rec_dtype == GS_F32) { GS_RB_K(GS_F32, GS_MAP); }
+            else if (rec_dtype == GS_BF16) { GS_RB_K(GS_BF16, GS_MAP); }
+            else { GS_RB_K(GS_F16, GS_MAP); }
         } else {
-            if (rec_dtype == GS_F32) GS_RB(GS_F32, GS_TRACK);
-            else if (rec_dtype == GS_BF16) GS_RB(GS_BF16, GS_TRACK);
-            else GS_RB(GS_F16, GS_TRACK);
+            if (rec_dtype == GS_F32) { GS_RB_K(GS_F32, GS_TRACK); }
+            else if (rec_dtype == GS_BF16) { GS_RB_K(GS_BF16, GS_TRACK); }
+            else { GS_RB_K(GS_F16, GS_TRACK); }
         }
         if ((s = check_launch("k_render_bwd")) != GS_OK) return s;
     }
 #undef GS_RB
+#undef GS_RB_K
+    }
     if (chain) {
         size_t wb = *workspace_bytes;
         return gs_project_bwd(cfg, cam, gsn, grad2d, grads, pose_grad6, score_terms, workspace, &wb, stream);

@@ -175,8 +175,14 @@ def render_gpu(G, cam, rec, n, cfg=None):
     return {k: np_of(v) for k, v in out.items()}, vals, ranges
 
 
-@pytest.mark.parametrize("n,W,H,seed,sx,sy", [(3000, 96, 72, 11, 1, 1), (30000, 333, 197, 12, 1, 1),
-                                              (20000, 320, 240, 13, 2, 2)])
+@pytest.mark.parametrize("n,W,H,seed,sx,sy", [
+    (3000, 96, 72, 11, 1, 1), (30000, 333, 197, 12, 1, 1),
+    (20000, 320, 240, 13, 2, 2),    # entry-parallel tiles (both strides >= 2)
+    (20000, 333, 197, 14, 4, 4),    # ... 4x4 tiles, ragged
+    (5000, 200, 120, 15, 4, 2),     # ... 4x8 tiles
+    (20000, 333, 197, 16, 3, 3),    # ... odd stride
+    (20000, 320, 240, 17, 1, 2),    # pixel-parallel, two tiles per CTA
+])
 def test_render_fwd_matches_oracle(G, O, n, W, H, seed, sx, sy):
     cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
     s = S.splats(n, W, H, seed=seed)
@@ -196,17 +202,25 @@ def test_render_fwd_matches_oracle(G, O, n, W, H, seed, sx, sy):
     assert np.array_equal(img["n_blended"][good].astype(np.int64), ref["nfrag"][good])
 
 
-def test_stride_render_is_subsampled_full_render_bit_exact(G):
+def test_stride_render_is_subsampled_full_render(G):
+    """A strided render samples the full-resolution image (Sec. 4.2).  The
+    pixel-parallel (stride 1 in one axis) and entry-parallel (both >= 2)
+    kernels sum in different orders, so the samples agree to float32
+    rounding, except where a stopping decision T (1 - alpha) < t_eps flips
+    on that rounding (one fragment at T ~ t_eps: < 2e-4)."""
     g = S.tiny_scene(seed=1234)
     cam = S.tiny_camera()
     cfg = G.default_config()
     rec = G.gs_project(cfg, G.camera(cam), dev(g))
     full, _, _ = render_gpu(G, cam, rec, 2000)
-    for sx, sy in ((2, 2), (4, 2), (4, 4), (3, 1)):
+    for sx, sy in ((2, 2), (4, 2), (4, 4), (3, 1), (1, 2), (3, 3)):
         sub, _, _ = render_gpu(G, dict(cam, sx=sx, sy=sy), rec, 2000)
-        assert np.array_equal(sub["rgb"], full["rgb"][:, ::sy, ::sx])
-        assert np.array_equal(sub["depth"], full["depth"][::sy, ::sx])
-        assert np.array_equal(sub["t_final"], full["t_final"][::sy, ::sx])
+        for k in ("rgb", "depth", "t_final"):
+            ref = full[k][..., ::sy, ::sx]
+            d = np.abs(sub[k] - ref)
+            scale = 1.0 if k != "depth" else max(1.0, float(np.abs(ref).max()))
+            assert d.max() <= 2e-4 * scale, (sx, sy, k, d.max())
+            assert (d > 1e-5 * scale).mean() <= 1e-2, (sx, sy, k)
 
 
 # ---------------------------------------------------------------------------
@@ -216,10 +230,16 @@ def test_stride_render_is_subsampled_full_render_bit_exact(G):
 GROUPS = {"mean2d": [0, 1], "conic": [2, 3, 4], "opacity": [5], "depth": [6], "rgb": [8, 9, 10]}
 
 
-@pytest.mark.parametrize("n,W,H,seed,mode", [(3000, 96, 72, 21, "map"), (30000, 333, 197, 22, "map"),
-                                             (20000, 320, 240, 23, "track")])
-def test_render_bwd_matches_oracle(G, O, n, W, H, seed, mode):
-    cam = S.camera(W, H, 100.0)
+@pytest.mark.parametrize("n,W,H,seed,mode,sx,sy", [
+    (3000, 96, 72, 21, "map", 1, 1), (30000, 333, 197, 22, "map", 1, 1), (20000, 320, 240, 23, "track", 1, 1),
+    (20000, 320, 240, 24, "track", 2, 2),   # entry-parallel tiles
+    (20000, 320, 240, 25, "map", 4, 4),
+    (5000, 200, 120, 26, "track", 4, 2),
+    (20000, 333, 197, 27, "map", 3, 3),
+    (20000, 320, 240, 28, "track", 1, 2),   # pixel-parallel, two tiles per CTA
+])
+def test_render_bwd_matches_oracle(G, O, n, W, H, seed, mode, sx, sy):
+    cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
     s = S.splats(n, W, H, seed=seed)
     rec = pack_splats(s)
     cfg = G.default_config()
@@ -227,7 +247,8 @@ def test_render_bwd_matches_oracle(G, O, n, W, H, seed, mode):
     _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
     order = gpu_bin.order if mode == "map" else None   # both launch orders are exercised
     out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges, order=order)
-    d_rgb, d_dep = S.image_grads(W, H, seed + 100)
+    Ws, Hs, _, _ = O.grid(cam)
+    d_rgb, d_dep = S.image_grads(Ws, Hs, seed + 100)
     gdummy = dev({"means": np.zeros((n, 3), np.float32), "log_scales": np.zeros((n, 3), np.float32),
                   "quats": np.zeros((n, 4), np.float32), "opacity_logit": np.zeros(n, np.float32),
                   "rgb": np.zeros((n, 3), np.float32)})

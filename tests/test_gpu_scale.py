@@ -11,7 +11,8 @@ crop, so its 2D and 3D gradients are the crop's.
 * mapping window: 1,000,000 surface Gaussians, 1200x680, keyframes on a 1 m
   arc, full per-Gaussian gradients, gradient-magnitude pruning at the 10th
   percentile (selection bit-exact on the same float32 score terms), strides
-  (2,2), (4,2), (4,4) equal to the subsampled full render;
+  (2,2), (4,2), (4,4) equal to the subsampled full render (to float32
+  rounding);
 * precision form: 3,000,000 Gaussians, 1920x1080, bf16 and fp16 records.
 """
 import numpy as np
@@ -109,8 +110,14 @@ def test_mapping_window_1M_1200x680(G, O):
         rs = Rasterizer(1_000_000, cs, capacity=r.capacity)
         rs.forward(gd, cs)
         rs.check()
-        assert np.array_equal(np_of(rs.img["rgb"]), full["rgb"][:, ::sy, ::sx])
-        assert np.array_equal(np_of(rs.img["depth"]), full["depth"][::sy, ::sx])
+        # different summation order (entry-parallel tiles); a stopping
+        # decision at T ~ t_eps may flip on rounding (< 2e-4)
+        for k in ("rgb", "depth"):
+            ref = full[k][..., ::sy, ::sx]
+            d = np.abs(np_of(rs.img[k]) - ref)
+            scale = 1.0 if k == "rgb" else max(1.0, float(ref.max()))
+            assert d.max() <= 2e-4 * scale, (sx, sy, k, float(d.max()))
+            assert (d > 1e-5 * scale).mean() <= 1e-2, (sx, sy, k)
 
 
 @pytest.mark.parametrize("name", ["bf16", "fp16"])
