@@ -12,7 +12,7 @@
 //                   key (k_tile_count).
 //   k_tile_scan     one CTA: exclusive scan of the tile counts -> bucket
 //                   starts, tile ranges, key count, capacity check
-//   k_tile_order    one CTA: heavy-first permutation of the tiles
+//   k_tile_order    one CTA: heavy-first permutation of the tiles (stable)
 //   k_tile_scatter  each pair takes a slot of its tile's bucket and writes
 //                   the 64-bit remainder key depth_bits << 32 | id there (a
 //                   CTA's slots start at its row offset and are dealt out
@@ -202,26 +202,47 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
 }
 
 // Heavy-first tile order: tiles grouped by floor(log2(length + 1)), longest
-// group first (the order inside a group comes from atomics; it only affects
-// scheduling, never results).
+// group first, ascending tile index inside a group (a stable counting sort,
+// so the order is a function of the lists alone: the compositing kernels
+// treat the first tiles of the order differently, and their results must
+// not depend on scheduling).
 __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ ranges, int ntiles,
                                                      uint32_t* __restrict__ order) {
     __shared__ uint32_t cnt[33], cur[33];
+    __shared__ uint32_t wcnt[32][33];  // per warp and group, within a 1024-tile chunk
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
     __syncthreads();
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
         const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        atomicAdd(&cnt[__clz(len + 1u)], 1u);  // bucket 0 = longest
+        atomicAdd(&cnt[__clz(len + 1u)], 1u);  // group 0 = longest
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
         for (int b = 0; b < 33; ++b) { cur[b] = run; run += cnt[b]; }
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        order[atomicAdd(&cur[__clz(len + 1u)], 1u)] = (uint32_t)t;
+    for (int base = 0; base < ntiles; base += 1024) {
+        for (int q = threadIdx.x; q < 32 * 33; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+        __syncthreads();
+        const int t = base + (int)threadIdx.x;
+        const int grp = t < ntiles ? __clz(ranges[2 * t + 1] - ranges[2 * t] + 1u) : 33;
+        const unsigned same = __match_any_sync(0xffffffffu, grp);
+        const unsigned rank = __popc(same & ((1u << lane) - 1u));
+        if (grp < 33 && rank == 0) wcnt[warp][grp] = __popc(same);
+        __syncthreads();
+        if (threadIdx.x < 33) {  // exclusive scan over the warps, per group
+            uint32_t run = cur[threadIdx.x];
+            for (int w = 0; w < 32; ++w) {
+                const uint32_t v = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = run;
+                run += v;
+            }
+            cur[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (grp < 33) order[wcnt[warp][grp] + rank] = (uint32_t)t;
+        __syncthreads();
     }
 }
 

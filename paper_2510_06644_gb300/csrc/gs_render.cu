@@ -2,25 +2,33 @@
 // (Sec. 4.1, Eq. 6) and A-7 backward compositing (Sec. 2.2, Step 4: Eq. 4,
 // Eq. 5) on sm_103a.
 //
-// One CTA per tile, one pixel per thread (256 threads for the 16x16 tiles
-// of a full-resolution image, fewer for the smaller sampled tiles of a
-// downsampled one, at least one warp); CTAs are
-// issued in the heavy-first tile order produced by the binning, so the block
-// scheduler starts the longest lists first (the GPU counterpart of the
-// paper's subtile streaming, Sec. 5.2).  The 8 warps cover 8x4 pixel blocks.
-// The tile's sorted list is staged through shared memory in batches of 256
-// records (one 48-byte gather per thread).  Each warp then builds a 256-bit
-// mask of the staged Gaussians whose integer box meets its 8x4 block (8
-// box tests and 8 ballots per lane) and visits only those.
+// Two forms of the compositing, chosen per frame:
 //
-// The backward walks each pixel's blended fragments in reverse from the
-// forward's last position, recovering T_k by division (Eq. 5), and merges the
+// Pixel-parallel (full resolution, or a stride of 1 in one axis): one pixel
+// per thread; a full 16x16 tile takes a CTA of 256 threads, the smaller
+// tiles of a downsampled frame take groups of 64 or 128 threads of such a
+// CTA, each group with its own named barrier and slice of the staging
+// buffer.  Groups are issued in the heavy-first tile order produced by the
+// binning, so the longest lists start first (the GPU counterpart of the
+// paper's subtile streaming, Sec. 5.2).  Warps cover 8x4 pixel blocks.  A
+// tile's sorted list is staged through shared memory in batches of up to
+// 256 records; each warp then builds a bit mask of the staged Gaussians
+// whose pixel box meets its block (one box test and one ballot per 32
+// entries) and visits only those, four at a time in the forward (their
+// alphas are independent; the blends then run in order without branches).
+//
+// Entry-parallel (both strides >= 2): see the section of that name below.
+//
+// The pixel-parallel backward walks each pixel's blended fragments in
+// reverse from the forward's last position, recovering T_k by division (Eq. 5), and merges the
 // per-pixel gradients of each Gaussian across the warp with a reduce-scatter
 // butterfly (each level halves the fields a lane carries: 9 shuffles for 6
 // fields, 16 for 10, instead of 5 per field), after which 8 or 16 lanes add
 // distinct fields into the tile's shared-memory accumulators at once; one
 // global atomic per (Gaussian, tile, field) follows.  This replaces the
 // paper's Gradient Merging Unit (Sec. 5.3).
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -66,14 +74,16 @@ struct Group {
     int tile;   // tile served, -1 if none
 };
 
-__device__ __forceinline__ Group make_group(const Grid& g, const uint32_t* order, int B) {
+// `blk` numbers the CTA among those serving tiles this way; its groups take
+// tile slots blk * gpc + gi of the tile order.
+__device__ __forceinline__ Group make_group(const Grid& g, const uint32_t* order, int B, int blk) {
     Group G;
     G.TT = tile_threads(g);
     const int gpc = R_THREADS / G.TT;
     G.gi = threadIdx.x / G.TT;
     G.lt = threadIdx.x % G.TT;
     G.B = B;
-    const int t = blockIdx.x * gpc + G.gi;
+    const int t = blk * gpc + G.gi;
     G.tile = t < g.TX * g.TY ? (order ? (int)__ldg(order + t) : t) : -1;
     return G;
 }
@@ -220,18 +230,14 @@ __device__ __forceinline__ float frag_alpha(const StagedSplat& s, const PixelMap
     return in ? alpha : -1.f;
 }
 
+// Forward compositing of group G's tile, pixel-parallel (sp_all: the CTA's
+// staging buffer, G.B entries per group).
 template <int DT, int KST>
-__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2) k_render_fwd(gs_config cfg, Grid g, const void* __restrict__ splats,
-                                                          const uint32_t* __restrict__ vals,
-                                                          const uint32_t* __restrict__ ranges,
-                                                          const uint32_t* __restrict__ order,
-                                                          float* __restrict__ out_rgb, float* __restrict__ out_depth,
-                                                          float* __restrict__ out_t, uint32_t* __restrict__ out_last,
-                                                          uint32_t* __restrict__ out_nb, int B) {
-    extern __shared__ __align__(16) unsigned char r_smem[];
-    StagedSplat* sp_all = reinterpret_cast<StagedSplat*>(r_smem);
-    const Group G = make_group(g, order, B);
-    if (G.tile < 0) return;
+__device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
+                                       const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
+                                       float* __restrict__ out_rgb, float* __restrict__ out_depth,
+                                       float* __restrict__ out_t, uint32_t* __restrict__ out_last,
+                                       uint32_t* __restrict__ out_nb, const Group& G, StagedSplat* sp_all) {
     StagedSplat* sp = sp_all + G.gi * G.B;
     const int tile = G.tile;
     const PixelMap m = map_pixel(g, tile, G.lt);
@@ -307,6 +313,19 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2) k_render_fwd(gs_c
         out_last[pix] = last;
         if (out_nb) out_nb[pix] = nb;
     }
+}
+
+template <int DT, int KST>
+__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
+    k_render_fwd(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
+                 const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
+                 float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_t,
+                 uint32_t* __restrict__ out_last, uint32_t* __restrict__ out_nb, int B) {
+    extern __shared__ __align__(16) unsigned char r_smem[];
+    const Group G = make_group(g, order, B, blockIdx.x);
+    if (G.tile < 0) return;
+    fwd_pp<DT, KST>(cfg, g, splats, vals, ranges, out_rgb, out_depth, out_t, out_last, out_nb, G,
+                    reinterpret_cast<StagedSplat*>(r_smem));
 }
 
 // ---------------------------------------------------------------------------
@@ -414,28 +433,24 @@ __device__ __forceinline__ FragGeo frag_geo(const StagedSplat& s, const PixelMap
     return f;
 }
 
+// Backward compositing of group G's tile, pixel-parallel (smem: the CTA's
+// staging, id and accumulator buffers for gpc groups of G.B entries;
+// s_max_all: one word per group).
 template <int DT, int MODE, int KST>
-__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 3 : 2) k_render_bwd(gs_config cfg, Grid g, const void* __restrict__ splats,
-                                                          const uint32_t* __restrict__ vals,
-                                                          const uint32_t* __restrict__ ranges,
-                                                          const uint32_t* __restrict__ order,
-                                                          const float* __restrict__ t_final,
-                                                          const uint32_t* __restrict__ last_idx,
-                                                          const float* __restrict__ d_rgb,
-                                                          const float* __restrict__ d_depth,
-                                                          float* __restrict__ grad2d, int B) {
+__device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
+                                       const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
+                                       const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
+                                       const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
+                                       float* __restrict__ grad2d, const Group& G, unsigned char* smem,
+                                       uint32_t* s_max_all) {
     constexpr int NS = Slots<MODE>::N;
     constexpr int LOG = Slots<MODE>::LOG;
     constexpr int SHIFT = 5 - LOG;  // lanes per slot = 1 << SHIFT
     constexpr int BSTEP = KST == 1 ? 1 : 2;  // entries per backward step
-    extern __shared__ __align__(16) unsigned char r_smem[];
-    __shared__ uint32_t s_max_all[R_THREADS / 32];
-    const int gpc = R_THREADS / tile_threads(g);
-    StagedSplat* sp_all = reinterpret_cast<StagedSplat*>(r_smem);
-    uint32_t* sid_all = reinterpret_cast<uint32_t*>(sp_all + gpc * B);
-    float(*acc_all)[NS] = reinterpret_cast<float(*)[NS]>(sid_all + gpc * B);
-    const Group G = make_group(g, order, B);
-    if (G.tile < 0) return;
+    const int gpc = R_THREADS / G.TT;
+    StagedSplat* sp_all = reinterpret_cast<StagedSplat*>(smem);
+    uint32_t* sid_all = reinterpret_cast<uint32_t*>(sp_all + gpc * G.B);
+    float(*acc_all)[NS] = reinterpret_cast<float(*)[NS]>(sid_all + gpc * G.B);
     StagedSplat* sp = sp_all + G.gi * G.B;
     uint32_t* sid = sid_all + G.gi * G.B;
     float(*acc)[NS] = acc_all + G.gi * G.B;
@@ -561,6 +576,21 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 3 : 2) k_render_bwd(gs_c
     }
 }
 
+template <int DT, int MODE, int KST>
+__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 3 : 2)
+    k_render_bwd(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
+                 const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
+                 const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
+                 const float* __restrict__ d_rgb, const float* __restrict__ d_depth, float* __restrict__ grad2d,
+                 int B) {
+    extern __shared__ __align__(16) unsigned char r_smem[];
+    __shared__ uint32_t s_max_all[R_THREADS / 32];
+    const Group G = make_group(g, order, B, blockIdx.x);
+    if (G.tile < 0) return;
+    bwd_pp<DT, MODE, KST>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, G, r_smem,
+                          s_max_all);
+}
+
 // ---------------------------------------------------------------------------
 // Entry-parallel compositing for the small tiles of downsampled frames
 // ---------------------------------------------------------------------------
@@ -568,20 +598,21 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 3 : 2) k_render_bwd(gs_c
 // the same full-resolution area, hence the same list length, as a 16x16
 // tile: pixel-parallel warps would walk long lists with few (and far apart)
 // pixels.  Here one CTA of W warps serves a tile (W = 8 for up to 32
-// pixels, else 16); warp w takes PPW = ceil(pixels / W) of its pixels (2 to
-// 4) and lane l takes list entry
-// 32c + l of chunk c.  Front-to-back compositing (Eq. 3) becomes a product
-// scan: the transmittance before a valid entry is the pixel's T times the
-// product of (1 - alpha) over the valid entries of the chunk before it; the
-// pixel stops at the first valid entry that would take T below t_eps.  The
-// backward (Eq. 4, Eq. 5) scans the chunks from the pixel's last blended
-// entry back: T before an entry is T after the chunk divided by the suffix
-// product of (1 - alpha), and the colour behind it is a suffix sum, so
+// pixels, else 16) and warp w takes PPW = ceil(pixels / W) of its pixels
+// (2 to 4), one at a time.  For its pixel the warp first compacts the staged
+// entries whose pixel box contains it (a ballot per 32 entries, in list
+// order), then lane l takes the l-th compacted entry.  Front-to-back
+// compositing (Eq. 3) becomes a product scan: the transmittance before a
+// valid entry is the pixel's T times the product of (1 - alpha) over the
+// valid entries before it in the group of 32; the pixel stops at the first
+// valid entry that would take T below t_eps.  The backward (Eq. 4, Eq. 5)
+// compacts from the pixel's last blended entry back: T before an entry is T
+// behind the group divided by the product of (1 - alpha) over it and the
+// entries behind it, and the colour behind it is a prefix sum, so
 //     dL/dalpha_k = T_k (c_k . g) - (sum_{j>k} w_j c_j . g + T_N bg . g) / (1 - alpha_k)
-// with g the pixel's image gradient.  Lane l keeps entry l's gradient over
-// the warp's pixels in registers and adds it once per chunk into the tile's
-// shared accumulators.  Entries are staged as four 16-byte arrays (lane l
-// reads element l: conflict-free).
+// with g the pixel's image gradient; each lane adds its entry's gradient to
+// the tile's shared accumulators.  Entries are staged as four 16-byte arrays
+// (lane l reading element l is conflict-free).
 #define EP_B 256
 
 struct EpStage {
@@ -614,25 +645,23 @@ __device__ __forceinline__ bool ep_pixel(const Grid& g, int tile, int q, int& i,
     return q < g.tw * g.th && i < g.Ws && j < g.Hs;
 }
 
+// Forward compositing of pixels q0 .. q0 + npix - 1 of `tile` by the CTA's W
+// warps, entry-parallel (S: staging; cbuf_all: W compaction buffers).
 template <int DT, int W>
-__global__ void __launch_bounds__(W * 32) k_render_fwd_ep(gs_config cfg, Grid g,
-                                                                 const void* __restrict__ splats,
-                                                                 const uint32_t* __restrict__ vals,
-                                                                 const uint32_t* __restrict__ ranges,
-                                                                 const uint32_t* __restrict__ order,
-                                                                 float* __restrict__ out_rgb,
-                                                                 float* __restrict__ out_depth,
-                                                                 float* __restrict__ out_t,
-                                                                 uint32_t* __restrict__ out_last,
-                                                                 uint32_t* __restrict__ out_nb) {
-    __shared__ EpStage S;
-    const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
+__device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
+                                       const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
+                                       float* __restrict__ out_rgb, float* __restrict__ out_depth,
+                                       float* __restrict__ out_t, uint32_t* __restrict__ out_last,
+                                       uint32_t* __restrict__ out_nb, int tile, int q0, int npix, EpStage& S,
+                                       int (*cbuf_all)[64]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ppw = (g.tw * g.th + W - 1) / W;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int* cbuf = cbuf_all[warp];
+    const int ppw = (npix + W - 1) / W;
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     // lane j < ppw holds the state of the warp's pixel j
     int mi, mj;
-    const bool mine = lane < ppw && ep_pixel(g, tile, warp * ppw + lane, mi, mj);
+    const bool mine = lane < ppw && warp * ppw + lane < npix && ep_pixel(g, tile, q0 + warp * ppw + lane, mi, mj);
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     uint32_t last = 0, nb = 0;
     bool done = !mine;
@@ -644,26 +673,26 @@ __global__ void __launch_bounds__(W * 32) k_render_fwd_ep(gs_config cfg, Grid g,
         for (int j = 0; j < ppw; ++j) {
             if (__shfl_sync(0xffffffffu, done, j)) continue;
             int pi, pj;
-            ep_pixel(g, tile, warp * ppw + j, pi, pj);
-            const float pxc = (float)(pi * g.sx) + 0.5f, pyc = (float)(pj * g.sy) + 0.5f;
+            ep_pixel(g, tile, q0 + warp * ppw + j, pi, pj);
             const int px = pi * g.sx, py = pj * g.sy;
+            const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
             float Tj = __shfl_sync(0xffffffffu, T, j);
             float p0 = 0.f, p1 = 0.f, p2 = 0.f, pd = 0.f;
             uint32_t lastj = 0, nbj = 0;
             bool stopped = false;
-            for (int c = 0; c < n_in && !stopped; c += 32) {
-                const int e = c + lane;
+            // composite the k compacted entries cbuf[0, k), in list order
+            auto composite = [&](int k) {
+                const int e = lane < k ? cbuf[lane] : -1;
                 float alpha = -1.f;
-                if (e < n_in) {
-                    const int4 box = S.box[e];
+                if (e >= 0) {
                     const float4 A = S.a[e];
-                    const float2 B = make_float2(S.b[e].x, S.b[e].y);
-                    const float power = gauss_power(A.z, A.w, B.x, pxc - A.x, pyc - A.y);
-                    const float al = fminf(cfg.alpha_max, B.y * __expf(power));
-                    if (px >= box.x && px <= box.y && py >= box.z && py <= box.w && !(power > 0.f)) alpha = al;
+                    const float4 Bv = S.b[e];
+                    const float power = gauss_power(A.z, A.w, Bv.x, pxc - A.x, pyc - A.y);
+                    const float al = fminf(cfg.alpha_max, Bv.y * __expf(power));
+                    if (!(power > 0.f)) alpha = al;
                 }
                 const bool valid = alpha >= cfg.alpha_min;
-                if (__ballot_sync(0xffffffffu, valid) == 0u) continue;
+                if (__ballot_sync(0xffffffffu, valid) == 0u) return;
                 const float f = valid ? 1.f - alpha : 1.f;
                 float P = f;  // inclusive product over lanes 0..l
 #pragma unroll
@@ -677,8 +706,8 @@ __global__ void __launch_bounds__(W * 32) k_render_fwd_ep(gs_config cfg, Grid g,
                 const unsigned stop = __ballot_sync(0xffffffffu, valid && Tn < cfg.t_eps);
                 const int lstar = stop ? __ffs(stop) - 1 : 32;
                 const bool ok = valid && lane < lstar;
-                const float w = ok ? alpha * Tb : 0.f;
-                if (e < n_in) {
+                if (ok) {
+                    const float w = alpha * Tb;
                     const float4 Cc = S.c[e];
                     p0 += w * Cc.x;
                     p1 += w * Cc.y;
@@ -687,14 +716,39 @@ __global__ void __launch_bounds__(W * 32) k_render_fwd_ep(gs_config cfg, Grid g,
                 }
                 const unsigned okm = __ballot_sync(0xffffffffu, ok);
                 nbj += __popc(okm);
-                if (okm) lastj = b - start + (uint32_t)(c + 32 - __clz(okm));
+                const int ehi = __shfl_sync(0xffffffffu, e, okm ? 31 - __clz(okm) : 0);
+                if (okm) lastj = b - start + (uint32_t)ehi + 1u;
                 if (lstar < 32) {
                     Tj = __shfl_sync(0xffffffffu, Tb, lstar);
                     stopped = true;
                 } else {
                     Tj = __shfl_sync(0xffffffffu, Tn, 31);
                 }
+            };
+            int cnt = 0;
+            for (int c = 0; c < n_in && !stopped; c += 32) {
+                const int e = c + lane;
+                bool in = false;
+                if (e < n_in) {
+                    const int4 box = S.box[e];
+                    in = px >= box.x && px <= box.y && py >= box.z && py <= box.w;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (in) cbuf[cnt + __popc(m & lt_mask)] = e;
+                cnt += __popc(m);
+                __syncwarp();
+                if (cnt >= 32) {
+                    composite(32);
+                    const int rest = cnt - 32;
+                    const int v = lane < rest ? cbuf[32 + lane] : 0;
+                    __syncwarp();
+                    if (lane < rest) cbuf[lane] = v;
+                    __syncwarp();
+                    cnt = rest;
+                }
             }
+            if (!stopped && cnt > 0) composite(cnt);
+            __syncwarp();
             p0 = warp_sum(p0);
             p1 = warp_sum(p1);
             p2 = warp_sum(p2);
@@ -725,6 +779,19 @@ __global__ void __launch_bounds__(W * 32) k_render_fwd_ep(gs_config cfg, Grid g,
     }
 }
 
+template <int DT, int W>
+__global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
+    k_render_fwd_ep(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
+                    const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
+                    float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_t,
+                    uint32_t* __restrict__ out_last, uint32_t* __restrict__ out_nb) {
+    __shared__ EpStage S;
+    __shared__ int cbuf_all[W][64];
+    const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
+    fwd_ep<DT, W>(cfg, g, splats, vals, ranges, out_rgb, out_depth, out_t, out_last, out_nb, tile, 0,
+                  g.tw * g.th, S, cbuf_all);
+}
+
 // Fields merged per entry: GS_TRACK du dv dA dB dC dd, GS_MAP du dv dA dB dC
 // dop dd dr dg db; ep_col gives their grad2d columns.
 template <int MODE>
@@ -737,30 +804,39 @@ __device__ __forceinline__ int ep_col(int f) {
     return f < 5 ? f : 6;
 }
 
+// Shared memory of the entry-parallel backward.
+template <int MODE, int W>
+struct EpBwdSmem {
+    EpStage S;
+    uint32_t sid[EP_B];
+    float acc[EpFields<MODE>::N][EP_B];
+    int cbuf[W][64];
+    uint32_t s_max;
+};
+
+// Backward compositing of pixels q0 .. q0 + npix - 1 of `tile` by the CTA's
+// W warps, entry-parallel.
 template <int DT, int MODE, int W>
-__global__ void __launch_bounds__(W * 32) k_render_bwd_ep(gs_config cfg, Grid g,
-                                                                 const void* __restrict__ splats,
-                                                                 const uint32_t* __restrict__ vals,
-                                                                 const uint32_t* __restrict__ ranges,
-                                                                 const uint32_t* __restrict__ order,
-                                                                 const float* __restrict__ t_final,
-                                                                 const uint32_t* __restrict__ last_idx,
-                                                                 const float* __restrict__ d_rgb,
-                                                                 const float* __restrict__ d_depth,
-                                                                 float* __restrict__ grad2d) {
+__device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
+                                       const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
+                                       const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
+                                       const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
+                                       float* __restrict__ grad2d, int tile, int q0, int npix,
+                                       EpBwdSmem<MODE, W>& M) {
     constexpr int NF = EpFields<MODE>::N;
-    __shared__ EpStage S;
-    __shared__ uint32_t sid[EP_B];
-    __shared__ float acc[NF][EP_B];
-    __shared__ uint32_t s_max;
-    const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
+    EpStage& S = M.S;
+    uint32_t* sid = M.sid;
+    float(&acc)[NF][EP_B] = M.acc;
+    uint32_t& s_max = M.s_max;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ppw = (g.tw * g.th + W - 1) / W;
+    const unsigned gt_mask = lane == 31 ? 0u : ~0u << (lane + 1);
+    int* cbuf = M.cbuf[warp];
+    const int ppw = (npix + W - 1) / W;
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     int mi, mj;
-    const bool mine = lane < ppw && ep_pixel(g, tile, warp * ppw + lane, mi, mj);
-    // state of pixel `lane`: T after the part already walked, suffix colour
-    // dot product s, last blended position, image gradient
+    const bool mine = lane < ppw && warp * ppw + lane < npix && ep_pixel(g, tile, q0 + warp * ppw + lane, mi, mj);
+    // state of pixel `lane`: T after the part already walked, the colour
+    // behind it dotted with g, last blended position, image gradient g
     float T = 1.f, sdot = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, gd = 0.f;
     uint32_t last = 0;
     if (mine) {
@@ -790,90 +866,113 @@ __global__ void __launch_bounds__(W * 32) k_render_bwd_ep(gs_config cfg, Grid g,
         for (int q = threadIdx.x; q < NF * EP_B; q += W * 32) (&acc[0][0])[q] = 0.f;
         __syncthreads();
         const uint32_t base_pos = lo - start;
-        for (int c = (n_in - 1) & ~31; c >= 0; c -= 32) {
-            const int e = c + lane;
-            const bool has = e < n_in;
-            // geometry of entry e, independent of the pixel's state except the offsets
-            float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Bv = A, Cc = A;
-            int4 box = make_int4(1, 0, 1, 0);
-            if (has) {
-                A = S.a[e];
-                Bv = S.b[e];
-                Cc = S.c[e];
-                box = S.box[e];
-            }
-            float ga[NF];
-#pragma unroll
-            for (int k = 0; k < NF; ++k) ga[k] = 0.f;
-            for (int j = 0; j < ppw; ++j) {
-                const uint32_t lastj = __shfl_sync(0xffffffffu, last, j);
-                if (lastj <= base_pos + (uint32_t)c) continue;  // nothing blended at or after this chunk
-                int pi, pj;
-                ep_pixel(g, tile, warp * ppw + j, pi, pj);
-                const int px = pi * g.sx, py = pj * g.sy;
-                const float dx = (float)px + 0.5f - A.x, dy = (float)py + 0.5f - A.y;
-                const float power = gauss_power(A.z, A.w, Bv.x, dx, dy);
-                const float gk = __expf(power);
-                const float raw = Bv.y * gk;
-                const float alpha = fminf(cfg.alpha_max, raw);
-                const bool valid = has && base_pos + (uint32_t)e < lastj && px >= box.x && px <= box.y &&
-                                   py >= box.z && py <= box.w && !(power > 0.f) && !(alpha < cfg.alpha_min);
-                if (__ballot_sync(0xffffffffu, valid) == 0u) continue;
-                const float Tj = __shfl_sync(0xffffffffu, T, j);
-                const float sj = __shfl_sync(0xffffffffu, sdot, j);
-                const float q0 = __shfl_sync(0xffffffffu, g0, j), q1 = __shfl_sync(0xffffffffu, g1, j);
-                const float q2 = __shfl_sync(0xffffffffu, g2, j), qd = __shfl_sync(0xffffffffu, gd, j);
+        for (int j = 0; j < ppw; ++j) {
+            const uint32_t lastj = __shfl_sync(0xffffffffu, last, j);
+            if (lastj <= base_pos) continue;  // nothing blended in this batch
+            const int nj = (int)min((uint32_t)n_in, lastj - base_pos);
+            int pi, pj;
+            ep_pixel(g, tile, q0 + warp * ppw + j, pi, pj);
+            const int px = pi * g.sx, py = pj * g.sy;
+            const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+            float Tj = __shfl_sync(0xffffffffu, T, j);
+            float sj = __shfl_sync(0xffffffffu, sdot, j);
+            const float q0 = __shfl_sync(0xffffffffu, g0, j), q1 = __shfl_sync(0xffffffffu, g1, j);
+            const float q2 = __shfl_sync(0xffffffffu, g2, j), qd = __shfl_sync(0xffffffffu, gd, j);
+            // the k compacted entries cbuf[0, k), last first: lane l's entry
+            // has the entries of lanes < l behind it
+            auto differentiate = [&](int k) {
+                const int e = lane < k ? cbuf[lane] : -1;
+                float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Bv = A, Cc = A;
+                float dx = 0.f, dy = 0.f, gk = 0.f, raw = 0.f, alpha = -1.f;
+                bool valid = false;
+                if (e >= 0) {
+                    A = S.a[e];
+                    Bv = S.b[e];
+                    Cc = S.c[e];
+                    dx = pxc - A.x;
+                    dy = pyc - A.y;
+                    const float power = gauss_power(A.z, A.w, Bv.x, dx, dy);
+                    gk = __expf(power);
+                    raw = Bv.y * gk;
+                    alpha = fminf(cfg.alpha_max, raw);
+                    valid = !(power > 0.f) && !(alpha < cfg.alpha_min);
+                }
+                if (__ballot_sync(0xffffffffu, valid) == 0u) return;
                 const float f = valid ? 1.f - alpha : 1.f;
-                float Q = f;  // inclusive suffix product over lanes l..31
+                float Q = f;  // inclusive product over lanes 0..l (this entry and those behind it)
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const float y = __shfl_down_sync(0xffffffffu, Q, o);
-                    if (lane + o < 32) Q *= y;
+                    const float y = __shfl_up_sync(0xffffffffu, Q, o);
+                    if (lane >= o) Q *= y;
                 }
                 const float Tb = Tj / Q;  // T before this entry (Eq. 5)
                 const float w = valid ? alpha * Tb : 0.f;
                 const float cg = Cc.x * q0 + Cc.y * q1 + Cc.z * q2 + Bv.z * qd;
                 const float wcg = w * cg;
-                float Ssuf = wcg;  // inclusive suffix sum of w (c . g)
+                float Sin = wcg;  // inclusive prefix sum of w (c . g)
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const float y = __shfl_down_sync(0xffffffffu, Ssuf, o);
-                    if (lane + o < 32) Ssuf += y;
+                    const float y = __shfl_up_sync(0xffffffffu, Sin, o);
+                    if (lane >= o) Sin += y;
                 }
-                const float behind = sj + (Ssuf - wcg);  // colour behind this entry, dotted with g
                 if (valid) {
+                    const float behind = sj + (Sin - wcg);
                     const float dLda = Tb * cg - behind / f;
+                    float ga[NF];
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) ga[q] = 0.f;
                     if (MODE == GS_MAP) {
-                        ga[6] += w * qd;
-                        ga[7] += w * q0;
-                        ga[8] += w * q1;
-                        ga[9] += w * q2;
+                        ga[6] = w * qd;
+                        ga[7] = w * q0;
+                        ga[8] = w * q1;
+                        ga[9] = w * q2;
                     } else {
-                        ga[5] += w * qd;
+                        ga[5] = w * qd;
                     }
                     if (!(raw > cfg.alpha_max)) {  // the clamp passes no gradient
-                        if (MODE == GS_MAP) ga[5] += gk * dLda;
+                        if (MODE == GS_MAP) ga[5] = gk * dLda;
                         const float dp = alpha * dLda;
-                        ga[2] += -0.5f * dx * dx * dp;
-                        ga[3] += -dx * dy * dp;
-                        ga[4] += -0.5f * dy * dy * dp;
-                        ga[0] += (A.z * dx + A.w * dy) * dp;
-                        ga[1] += (A.w * dx + Bv.x * dy) * dp;
+                        ga[2] = -0.5f * dx * dx * dp;
+                        ga[3] = -dx * dy * dp;
+                        ga[4] = -0.5f * dy * dy * dp;
+                        ga[0] = (A.z * dx + A.w * dy) * dp;
+                        ga[1] = (A.w * dx + Bv.x * dy) * dp;
                     }
+#pragma unroll
+                    for (int q = 0; q < NF; ++q)
+                        if (ga[q] != 0.f) atomicAdd(&acc[q][e], ga[q]);
                 }
-                // state before this chunk: T divided by the chunk's product,
-                // the chunk's colour added behind
-                const float Qall = __shfl_sync(0xffffffffu, Q, 0);
-                const float Sall = __shfl_sync(0xffffffffu, Ssuf, 0);
-                if (lane == j) {
-                    T = Tj / Qall;
-                    sdot = sj + Sall;
+                // state in front of these entries
+                Tj = __shfl_sync(0xffffffffu, Tj / Q, 31);
+                sj = sj + __shfl_sync(0xffffffffu, Sin, 31);
+            };
+            int cnt = 0;
+            for (int c = (nj - 1) & ~31; c >= 0; c -= 32) {
+                const int e = c + lane;
+                bool in = false;
+                if (e < nj) {
+                    const int4 box = S.box[e];
+                    in = px >= box.x && px <= box.y && py >= box.z && py <= box.w;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (in) cbuf[cnt + __popc(m & gt_mask)] = e;
+                cnt += __popc(m);
+                __syncwarp();
+                if (cnt >= 32) {
+                    differentiate(32);
+                    const int rest = cnt - 32;
+                    const int v = lane < rest ? cbuf[32 + lane] : 0;
+                    __syncwarp();
+                    if (lane < rest) cbuf[lane] = v;
+                    __syncwarp();
+                    cnt = rest;
                 }
             }
-            if (has) {
-#pragma unroll
-                for (int k = 0; k < NF; ++k)
-                    if (ga[k] != 0.f) atomicAdd(&acc[k][e], ga[k]);
+            if (cnt > 0) differentiate(cnt);
+            __syncwarp();
+            if (lane == j) {
+                T = Tj;
+                sdot = sj;
             }
         }
         __syncthreads();
@@ -885,6 +984,19 @@ __global__ void __launch_bounds__(W * 32) k_render_bwd_ep(gs_config cfg, Grid g,
         __syncthreads();
         hi = lo;
     }
+}
+
+template <int DT, int MODE, int W>
+__global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
+    k_render_bwd_ep(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
+                    const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
+                    const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
+                    const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
+                    float* __restrict__ grad2d) {
+    __shared__ EpBwdSmem<MODE, W> M;
+    const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
+    bwd_ep<DT, MODE, W>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, tile, 0,
+                        g.tw * g.th, M);
 }
 
 }  // namespace gs
@@ -912,6 +1024,74 @@ static gs_status smem_once(const void* fn, int id, int bytes) {
     return GS_OK;
 }
 
+// Kernel choice per frame (the results agree to float32 summation order):
+// both strides >= 2 (tiles of at most 64 sampled pixels): entry-parallel,
+// one CTA of 8 or 16 warps per tile; otherwise pixel-parallel groups.
+template <int DT>
+static gs_status launch_fwd(const gs_config& cfg, const Grid& g, const void* splats, const uint32_t* vals,
+                            const uint32_t* ranges, const uint32_t* order, float* rgb, float* depth,
+                            float* t_final, uint32_t* last_idx, uint32_t* n_blended, cudaStream_t st) {
+    const int ntiles = g.TX * g.TY;
+    if (g.tw * g.th <= 64) {
+        if (g.tw * g.th <= 32)
+            k_render_fwd_ep<DT, 8><<<ntiles, 8 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, rgb, depth,
+                                                               t_final, last_idx, n_blended);
+        else
+            k_render_fwd_ep<DT, 16><<<ntiles, 16 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, rgb, depth,
+                                                                 t_final, last_idx, n_blended);
+        return check_launch("k_render_fwd_ep");
+    }
+    const int gpc = R_THREADS / tile_threads(g);
+    const unsigned nt = (unsigned)((ntiles + gpc - 1) / gpc);
+    const int B = group_batch(gpc, (int)sizeof(StagedSplat), R_FWD_SMEM);
+    const size_t smem = (size_t)gpc * B * sizeof(StagedSplat);
+    gs_status s;
+    if (gpc == 1) {
+        if ((s = smem_once((const void*)k_render_fwd<DT, 1>, 2 * DT, R_FWD_SMEM)) != GS_OK) return s;
+        k_render_fwd<DT, 1><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, rgb, depth, t_final,
+                                                         last_idx, n_blended, B);
+    } else {
+        if ((s = smem_once((const void*)k_render_fwd<DT, 4>, 2 * DT + 1, R_FWD_SMEM)) != GS_OK) return s;
+        k_render_fwd<DT, 4><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, rgb, depth, t_final,
+                                                         last_idx, n_blended, B);
+    }
+    return check_launch("k_render_fwd");
+}
+
+template <int DT, int MD>
+static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* splats, const uint32_t* vals,
+                            const uint32_t* ranges, const uint32_t* order, const float* t_final,
+                            const uint32_t* last_idx, const float* d_rgb, const float* d_depth, float* grad2d,
+                            cudaStream_t st) {
+    const int ntiles = g.TX * g.TY;
+    if (g.tw * g.th <= 64) {
+        if (g.tw * g.th <= 32)
+            k_render_bwd_ep<DT, MD, 8><<<ntiles, 8 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, t_final,
+                                                                   last_idx, d_rgb, d_depth, grad2d);
+        else
+            k_render_bwd_ep<DT, MD, 16><<<ntiles, 16 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, t_final,
+                                                                     last_idx, d_rgb, d_depth, grad2d);
+        return check_launch("k_render_bwd_ep");
+    }
+    const int gpc = R_THREADS / tile_threads(g);
+    const unsigned nt = (unsigned)((ntiles + gpc - 1) / gpc);
+    const int per_entry = (int)(sizeof(StagedSplat) + sizeof(uint32_t) + sizeof(float) * Slots<MD>::N);
+    const int B = group_batch(gpc, per_entry, R_BWD_SMEM);
+    const size_t smem = (size_t)gpc * B * per_entry;
+    const int id = 6 + 6 * (MD == GS_MAP) + 2 * DT;
+    gs_status s;
+    if (gpc == 1) {
+        if ((s = smem_once((const void*)k_render_bwd<DT, MD, 1>, id, R_BWD_SMEM)) != GS_OK) return s;
+        k_render_bwd<DT, MD, 1><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, t_final,
+                                                             last_idx, d_rgb, d_depth, grad2d, B);
+    } else {
+        if ((s = smem_once((const void*)k_render_bwd<DT, MD, 4>, id + 1, R_BWD_SMEM)) != GS_OK) return s;
+        k_render_bwd<DT, MD, 4><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, t_final,
+                                                             last_idx, d_rgb, d_depth, grad2d, B);
+    }
+    return check_launch("k_render_bwd");
+}
+
 static gs_status render_checks(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
                                int64_t n) {
     if (!cfg) return set_error(GS_ERR_INVALID_ARG, "config is NULL");
@@ -937,40 +1117,14 @@ extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, i
         return set_error(GS_ERR_INVALID_ARG, "an image or range pointer is NULL");
     const Grid g = make_grid(*cam);
     cudaStream_t st = (cudaStream_t)stream;
-    if (g.tw * g.th <= 64) {  // downsampled frame: entry-parallel tiles
-        const unsigned ntl = (unsigned)(g.TX * g.TY);
-#define GS_RFE(DT, W)                                                                                       \
-    k_render_fwd_ep<DT, W><<<ntl, W * 32, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, \
-                                                   t_final, last_idx, n_blended)
-#define GS_RFE_W(DT)                            \
-    if (g.tw * g.th <= 32) { GS_RFE(DT, 8); } \
-    else { GS_RFE(DT, 16); }
-        if (rec_dtype == GS_F32) { GS_RFE_W(GS_F32); }
-        else if (rec_dtype == GS_BF16) { GS_RFE_W(GS_BF16); }
-        else { GS_RFE_W(GS_F16); }
-#undef GS_RFE
-#undef GS_RFE_W
-        return check_launch("k_render_fwd_ep");
-    }
-    const int gpc = R_THREADS / tile_threads(g);
-    const unsigned nt = (unsigned)((g.TX * g.TY + gpc - 1) / gpc);
-    const int B = group_batch(gpc, (int)sizeof(StagedSplat), R_FWD_SMEM);
-    const size_t smem = (size_t)gpc * B * sizeof(StagedSplat);
-#define GS_RF(DT, K)                                                                                         \
-    if ((s = smem_once((const void*)k_render_fwd<DT, K>, 2 * DT + (K > 1), R_FWD_SMEM)) != GS_OK) return s; \
-    k_render_fwd<DT, K><<<nt, R_THREADS, smem, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb,     \
-                                                     depth, t_final, last_idx, n_blended, B)
-    if (gpc == 1) {
-        if (rec_dtype == GS_F32) { GS_RF(GS_F32, 1); }
-        else if (rec_dtype == GS_BF16) { GS_RF(GS_BF16, 1); }
-        else { GS_RF(GS_F16, 1); }
-    } else {
-        if (rec_dtype == GS_F32) { GS_RF(GS_F32, 4); }
-        else if (rec_dtype == GS_BF16) { GS_RF(GS_BF16, 4); }
-        else { GS_RF(GS_F16, 4); }
-    }
-#undef GS_RF
-    return check_launch("k_render_fwd");
+    if (rec_dtype == GS_F32)
+        return launch_fwd<GS_F32>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx,
+                                  n_blended, st);
+    if (rec_dtype == GS_BF16)
+        return launch_fwd<GS_BF16>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx,
+                                   n_blended, st);
+    return launch_fwd<GS_F16>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx,
+                              n_blended, st);
 }
 
 extern "C" gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, const float* rgb, const float* depth,
@@ -1019,58 +1173,17 @@ extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, c
     if (n > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * GS_GRAD2D_STRIDE * (size_t)n, st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset grad2d");
     const Grid g = make_grid(*cam);
-    if (g.tw * g.th <= 64) {  // downsampled frame: entry-parallel tiles
-        const unsigned ntl = (unsigned)(g.TX * g.TY);
-#define GS_RBE(DT, MD, W)                                                                                   \
-    k_render_bwd_ep<DT, MD, W><<<ntl, W * 32, 0, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order, t_final, \
-                                                       last_idx, d_rgb, d_depth, grad2d)
-#define GS_RBE_W(DT, MD)                            \
-    if (g.tw * g.th <= 32) { GS_RBE(DT, MD, 8); } \
-    else { GS_RBE(DT, MD, 16); }
-        if (n > 0) {
-            if (mode == GS_MAP) {
-                if (rec_dtype == GS_F32) { GS_RBE_W(GS_F32, GS_MAP); }
-                else if (rec_dtype == GS_BF16) { GS_RBE_W(GS_BF16, GS_MAP); }
-                else { GS_RBE_W(GS_F16, GS_MAP); }
-            } else {
-                if (rec_dtype == GS_F32) { GS_RBE_W(GS_F32, GS_TRACK); }
-                else if (rec_dtype == GS_BF16) { GS_RBE_W(GS_BF16, GS_TRACK); }
-                else { GS_RBE_W(GS_F16, GS_TRACK); }
-            }
-            if ((s = check_launch("k_render_bwd_ep")) != GS_OK) return s;
-        }
-#undef GS_RBE
-#undef GS_RBE_W
-    } else {
-    const int gpc = R_THREADS / tile_threads(g);
-    const unsigned nt = (unsigned)((g.TX * g.TY + gpc - 1) / gpc);
-    const int per_entry = (int)(sizeof(StagedSplat) + sizeof(uint32_t) +
-                                sizeof(float) * (mode == GS_MAP ? Slots<GS_MAP>::N : Slots<GS_TRACK>::N));
-    const int B = group_batch(gpc, per_entry, R_BWD_SMEM);
-    const size_t smem = (size_t)gpc * B * per_entry;
-#define GS_RB(DT, MD, K)                                                                                       \
-    if ((s = smem_once((const void*)k_render_bwd<DT, MD, K>, 6 + 6 * (MD == GS_MAP) + 2 * DT + (K > 1),       \
-                       R_BWD_SMEM)) != GS_OK)                                                                  \
-        return s;                                                                                              \
-    k_render_bwd<DT, MD, K><<<nt, R_THREADS, smem, st>>>(*cfg, g, splats, vals, tile_ranges, tile_order,       \
-                                                         t_final, last_idx, d_rgb, d_depth, grad2d, B)
-#define GS_RB_K(DT, MD)             \
-    if (gpc == 1) { GS_RB(DT, MD, 1); } \
-    else { GS_RB(DT, MD, 4); }
     if (n > 0) {
-        if (mode == GS_MAP) {
-            if (rec_dtype == GS_F32) { GS_RB_K(GS_F32, GS_MAP); }
-            else if (rec_dtype == GS_BF16) { GS_RB_K(GS_BF16, GS_MAP); }
-            else { GS_RB_K(GS_F16, GS_MAP); }
-        } else {
-            if (rec_dtype == GS_F32) { GS_RB_K(GS_F32, GS_TRACK); }
-            else if (rec_dtype == GS_BF16) { GS_RB_K(GS_BF16, GS_TRACK); }
-            else { GS_RB_K(GS_F16, GS_TRACK); }
-        }
-        if ((s = check_launch("k_render_bwd")) != GS_OK) return s;
-    }
-#undef GS_RB
-#undef GS_RB_K
+#define GS_LB(DT, MD) \
+    launch_bwd<DT, MD>(*cfg, g, splats, vals, tile_ranges, tile_order, t_final, last_idx, d_rgb, d_depth, grad2d, st)
+        if (mode == GS_MAP)
+            s = rec_dtype == GS_F32 ? GS_LB(GS_F32, GS_MAP) : rec_dtype == GS_BF16 ? GS_LB(GS_BF16, GS_MAP)
+                                                                                   : GS_LB(GS_F16, GS_MAP);
+        else
+            s = rec_dtype == GS_F32 ? GS_LB(GS_F32, GS_TRACK) : rec_dtype == GS_BF16 ? GS_LB(GS_BF16, GS_TRACK)
+                                                                                     : GS_LB(GS_F16, GS_TRACK);
+#undef GS_LB
+        if (s != GS_OK) return s;
     }
     if (chain) {
         size_t wb = *workspace_bytes;

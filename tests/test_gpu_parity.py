@@ -45,12 +45,13 @@ def gpu_bin(G, cam, rec, n, cap=None):
     keys, vals, nk, ranges, order = G.gs_bin_sort(cs, rec, n, cap)
     torch.cuda.synchronize()
     k = int(nk.item())
-    # the tile order is a permutation, longest lists first by log2 group
+    # the tile order: longest lists first by floor(log2(len + 1)) group,
+    # ascending tile index inside a group (a stable sort: exactly this
+    # permutation)
     o = np_of(order).astype(np.int64)
     rr = np_of(ranges).view(np.uint32).astype(np.int64)
-    assert np.array_equal(np.sort(o), np.arange(rr.shape[0]))
-    grp = np.floor(np.log2(rr[o, 1] - rr[o, 0] + 1))
-    assert np.all(np.diff(grp) <= 0)
+    grp = np.floor(np.log2(rr[:, 1] - rr[:, 0] + 1)).astype(np.int64)
+    assert np.array_equal(o, np.lexsort((np.arange(rr.shape[0]), -grp)))
     gpu_bin.order = order
     return np_of(keys[:k]).view(np.uint64), np_of(vals[:k]).view(np.uint32), np_of(ranges).view(np.uint32), vals, ranges
 
