@@ -79,7 +79,7 @@ typedef struct {
  * near_z 0.2, dilation 0.3, alpha_min 1/255, alpha_max 0.99, t_eps 1e-4,
  * bg (0,0,0), lambda_score 0.8 (Sec. 6.1), prune_frac 0.1, prune_cap 0.5
  * (Sec. 6.2 ablation cap), change_thr 0.05 (Sec. 4.1), k0 5 (Sec. 6.1),
- * k_max 64, w_rgb 1, w_depth 0.5 (tracking loss). */
+ * k_max 64, w_rgb 1, w_depth 0.5 (tracking loss), balance 1. */
 typedef struct {
     float near_z;       /* cull when camera-frame z < near_z */
     float dilation;     /* low-pass term added to the 2D covariance diagonal */
@@ -95,6 +95,14 @@ typedef struct {
     int32_t k_max;      /* largest interval */
     float w_rgb;        /* photometric weight of the loss (Eq. 6) */
     float w_depth;      /* geometric weight of the loss (Eq. 6) */
+    int32_t balance;    /* 1: in downsampled frames (both strides >= 2)
+                           gs_render_fwd reads last_idx on entry as the
+                           previous iteration's per-pixel list positions and
+                           pairs heavy with light pixels on the warps of a
+                           tile (the workload scheduling of Sec. 5.2); any
+                           content is valid and only changes scheduling,
+                           never results.  0: no pairing in the forward.
+                           gs_render_bwd always pairs by its last_idx. */
 } gs_config;
 
 /* 3D Gaussians (Sec. 2.1, Eq. 1), structure of arrays, float32:

@@ -69,6 +69,7 @@ extern "C" void gs_default_config(gs_config* c) {
     c->k_max = 64;
     c->w_rgb = 1.0f;
     c->w_depth = 0.5f;
+    c->balance = 1;
 }
 
 extern "C" const char* gs_version(void) { return "gs-gb300 0.1 (sm_103a)"; }

@@ -630,10 +630,19 @@ __device__ __forceinline__ void ep_stage(const void* __restrict__ splats, const 
         const Splat v = load_splat<DT>(splats, id);
         S.a[e] = make_float4(v.x, v.y, v.ca, v.cb);
         S.b[e] = make_float4(v.cc, v.op, v.depth, 0.f);
-        S.c[e] = make_float4(v.r, v.g, v.b, 0.f);
         S.box[e] = pixel_box(v, alpha_min);
+        S.c[e] = make_float4(v.r, v.g, v.b, 0.f);
         if (sid) sid[e] = id;
     }
+}
+
+// Whether staged entry e can blend at full-resolution pixel (px, py): inside
+// its pixel box (a superset of the fragments the alpha test accepts, so
+// compacting by it changes no result).  Testing the alpha ellipse here as
+// well was measured slower: the extra loads cost more than the groups saved.
+__device__ __forceinline__ bool ep_may_blend(const EpStage& S, int e, int px, int py) {
+    const int4 box = S.box[e];
+    return px >= box.x && px <= box.y && py >= box.z && py <= box.w;
 }
 
 // Sampled pixel q of the tile: full-resolution coordinates, and whether it
@@ -645,6 +654,41 @@ __device__ __forceinline__ bool ep_pixel(const Grid& g, int tile, int q, int& i,
     return q < g.tw * g.th && i < g.Ws && j < g.Hs;
 }
 
+// Pixel-to-warp assignment of a tile (the pairing of Sec. 5.2's workload
+// scheduling unit): the tile's npix = W * ppw pixels are ranked by their
+// expected work h (heaviest first, ties by index) and dealt to the W warps
+// in snake order, round r going to warps 0..W-1 for even r and W-1..0 for
+// odd r, so each warp gets a heavy pixel with a light one in every pair of
+// rounds.  h is the pixel's list position of the last blended entry (the
+// backward's input, or the previous iteration's for the forward); pixels
+// outside the image have h = 0.  perm[w * ppw + j] is warp w's j-th pixel.
+// Any h gives a valid permutation; it only changes which warp does what.
+template <int W>
+__device__ __forceinline__ void ep_pair(const Grid& g, int tile, int q0, int npix, const uint32_t* hint,
+                                        uint32_t* s_h, uint8_t* perm) {
+    const int ppw = (npix + W - 1) / W;
+    const int q = (int)threadIdx.x;
+    if (q < npix) {
+        int i, j;
+        uint32_t h = 0;
+        if (hint && ep_pixel(g, tile, q0 + q, i, j)) h = hint[(size_t)j * g.Ws + i];
+        s_h[q] = h;
+    }
+    __syncthreads();
+    if (q < npix) {
+        const uint32_t h = s_h[q];
+        int r = 0;
+        for (int o = 0; o < npix; ++o) {
+            const uint32_t v = s_h[o];
+            r += (v > h || (v == h && o < q)) ? 1 : 0;
+        }
+        const int round = r / W, pos = r % W;
+        const int w = (round & 1) ? W - 1 - pos : pos;
+        perm[w * ppw + round] = (uint8_t)q;
+    }
+    __syncthreads();
+}
+
 // Forward compositing of pixels q0 .. q0 + npix - 1 of `tile` by the CTA's W
 // warps, entry-parallel (S: staging; cbuf_all: W compaction buffers).
 template <int DT, int W>
@@ -653,15 +697,17 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
                                        float* __restrict__ out_rgb, float* __restrict__ out_depth,
                                        float* __restrict__ out_t, uint32_t* __restrict__ out_last,
                                        uint32_t* __restrict__ out_nb, int tile, int q0, int npix, EpStage& S,
-                                       int (*cbuf_all)[64]) {
+                                       int (*cbuf_all)[64], uint32_t* s_h, uint8_t* perm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     int* cbuf = cbuf_all[warp];
     const int ppw = (npix + W - 1) / W;
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+    // out_last still holds the previous iteration's positions (read before any write)
+    ep_pair<W>(g, tile, q0, npix, cfg.balance ? out_last : nullptr, s_h, perm);
     // lane j < ppw holds the state of the warp's pixel j
     int mi, mj;
-    const bool mine = lane < ppw && warp * ppw + lane < npix && ep_pixel(g, tile, q0 + warp * ppw + lane, mi, mj);
+    const bool mine = lane < ppw && warp * ppw + lane < npix && ep_pixel(g, tile, q0 + perm[warp * ppw + lane], mi, mj);
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     uint32_t last = 0, nb = 0;
     bool done = !mine;
@@ -673,7 +719,7 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
         for (int j = 0; j < ppw; ++j) {
             if (__shfl_sync(0xffffffffu, done, j)) continue;
             int pi, pj;
-            ep_pixel(g, tile, q0 + warp * ppw + j, pi, pj);
+            ep_pixel(g, tile, q0 + perm[warp * ppw + j], pi, pj);
             const int px = pi * g.sx, py = pj * g.sy;
             const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
             float Tj = __shfl_sync(0xffffffffu, T, j);
@@ -728,11 +774,7 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
             int cnt = 0;
             for (int c = 0; c < n_in && !stopped; c += 32) {
                 const int e = c + lane;
-                bool in = false;
-                if (e < n_in) {
-                    const int4 box = S.box[e];
-                    in = px >= box.x && px <= box.y && py >= box.z && py <= box.w;
-                }
+                const bool in = e < n_in && ep_may_blend(S, e, px, py);
                 const unsigned m = __ballot_sync(0xffffffffu, in);
                 if (in) cbuf[cnt + __popc(m & lt_mask)] = e;
                 cnt += __popc(m);
@@ -787,9 +829,11 @@ __global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
                     uint32_t* __restrict__ out_last, uint32_t* __restrict__ out_nb) {
     __shared__ EpStage S;
     __shared__ int cbuf_all[W][64];
+    __shared__ uint32_t s_h[64];
+    __shared__ uint8_t perm[64];
     const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
     fwd_ep<DT, W>(cfg, g, splats, vals, ranges, out_rgb, out_depth, out_t, out_last, out_nb, tile, 0,
-                  g.tw * g.th, S, cbuf_all);
+                  g.tw * g.th, S, cbuf_all, s_h, perm);
 }
 
 // Fields merged per entry: GS_TRACK du dv dA dB dC dd, GS_MAP du dv dA dB dC
@@ -811,6 +855,8 @@ struct EpBwdSmem {
     uint32_t sid[EP_B];
     float acc[EpFields<MODE>::N][EP_B];
     int cbuf[W][64];
+    uint32_t s_h[64];
+    uint8_t perm[64];
     uint32_t s_max;
 };
 
@@ -833,8 +879,10 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
     int* cbuf = M.cbuf[warp];
     const int ppw = (npix + W - 1) / W;
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+    uint8_t* perm = M.perm;
+    ep_pair<W>(g, tile, q0, npix, last_idx, M.s_h, perm);
     int mi, mj;
-    const bool mine = lane < ppw && warp * ppw + lane < npix && ep_pixel(g, tile, q0 + warp * ppw + lane, mi, mj);
+    const bool mine = lane < ppw && warp * ppw + lane < npix && ep_pixel(g, tile, q0 + perm[warp * ppw + lane], mi, mj);
     // state of pixel `lane`: T after the part already walked, the colour
     // behind it dotted with g, last blended position, image gradient g
     float T = 1.f, sdot = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, gd = 0.f;
@@ -871,7 +919,7 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
             if (lastj <= base_pos) continue;  // nothing blended in this batch
             const int nj = (int)min((uint32_t)n_in, lastj - base_pos);
             int pi, pj;
-            ep_pixel(g, tile, q0 + warp * ppw + j, pi, pj);
+            ep_pixel(g, tile, q0 + perm[warp * ppw + j], pi, pj);
             const int px = pi * g.sx, py = pj * g.sy;
             const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
             float Tj = __shfl_sync(0xffffffffu, T, j);
@@ -949,11 +997,7 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
             int cnt = 0;
             for (int c = (nj - 1) & ~31; c >= 0; c -= 32) {
                 const int e = c + lane;
-                bool in = false;
-                if (e < nj) {
-                    const int4 box = S.box[e];
-                    in = px >= box.x && px <= box.y && py >= box.z && py <= box.w;
-                }
+                const bool in = e < nj && ep_may_blend(S, e, px, py);
                 const unsigned m = __ballot_sync(0xffffffffu, in);
                 if (in) cbuf[cnt + __popc(m & gt_mask)] = e;
                 cnt += __popc(m);

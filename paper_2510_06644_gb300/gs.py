@@ -44,7 +44,7 @@ class gs_config(C.Structure):
                 ("alpha_max", C.c_float), ("t_eps", C.c_float), ("bg", C.c_float * 3),
                 ("lambda_score", C.c_float), ("prune_frac", C.c_float), ("prune_cap", C.c_float),
                 ("change_thr", C.c_float), ("k0", C.c_int32), ("k_max", C.c_int32),
-                ("w_rgb", C.c_float), ("w_depth", C.c_float)]
+                ("w_rgb", C.c_float), ("w_depth", C.c_float), ("balance", C.c_int32)]
 
 
 class gs_gaussians(C.Structure):

@@ -231,6 +231,50 @@ def test_stride_render_is_subsampled_full_render(G):
 GROUPS = {"mean2d": [0, 1], "conic": [2, 3, 4], "opacity": [5], "depth": [6], "rgb": [8, 9, 10]}
 
 
+@pytest.mark.parametrize("sx,sy", [(2, 2), (4, 4), (4, 2)])
+def test_pixel_pairing_changes_no_result(G, O, sx, sy):
+    """The heavy/light pixel pairing of the entry-parallel tiles (Sec. 5.2)
+    only decides which warp composites which pixel: the forward is bit-exact
+    with pairing off, with the previous iteration's positions, and with
+    arbitrary hint values; the backward (which pairs by its last_idx) matches
+    the oracle."""
+    n, W, H = 20000, 320, 240
+    cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
+    s = S.splats(n, W, H, seed=77 + sx)
+    rec = pack_splats(s)
+    cs = G.camera(cam)
+    _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
+    Ws, Hs, _, _ = O.grid(cam)
+    outs = []
+    for balance, hint in ((0, None), (1, "prev"), (1, "random")):
+        cfg = G.default_config(balance=balance)
+        out = {"rgb": torch.empty((3, Hs, Ws), device="cuda"), "depth": torch.empty((Hs, Ws), device="cuda"),
+               "t_final": torch.empty((Hs, Ws), device="cuda"),
+               "last_idx": torch.zeros((Hs, Ws), dtype=torch.int32, device="cuda"),
+               "n_blended": torch.empty((Hs, Ws), dtype=torch.int32, device="cuda")}
+        if hint == "prev":
+            out["last_idx"].copy_(outs[0]["last_idx"])
+        elif hint == "random":
+            out["last_idx"].copy_(torch.randint(0, 1 << 30, (Hs, Ws), dtype=torch.int32, generator=torch.Generator().manual_seed(5)))
+        G.gs_render_fwd(cfg, cs, rec, n, vals, ranges, out=out, order=gpu_bin.order)
+        torch.cuda.synchronize()
+        outs.append({k: v.clone() for k, v in out.items()})
+    for o in outs[1:]:
+        for k in o:
+            assert torch.equal(o[k], outs[0][k]), k
+    d_rgb, d_dep = S.image_grads(Ws, Hs, 99)
+    gdummy = dev({"means": np.zeros((n, 3), np.float32), "log_scales": np.zeros((n, 3), np.float32),
+                  "quats": np.zeros((n, 4), np.float32), "opacity_logit": np.zeros(n, np.float32),
+                  "rgb": np.zeros((n, 3), np.float32)})
+    g2 = G.gs_render_bwd(G.default_config(), cs, gdummy, rec, vals, ranges, outs[0]["t_final"], outs[0]["last_idx"],
+                         torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=G.GS_MAP,
+                         order=gpu_bin.order)
+    ref = O.render_bwd(s, cam, d_rgb, d_dep)
+    g2 = np_of(g2)
+    for name, cols in GROUPS.items():
+        assert rel_l2(g2[:, cols], ref[:, cols]) <= GRAD_TOL, name
+
+
 @pytest.mark.parametrize("n,W,H,seed,mode,sx,sy", [
     (3000, 96, 72, 21, "map", 1, 1), (30000, 333, 197, 22, "map", 1, 1), (20000, 320, 240, 23, "track", 1, 1),
     (20000, 320, 240, 24, "track", 2, 2),   # entry-parallel tiles
