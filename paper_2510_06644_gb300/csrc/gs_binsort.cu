@@ -19,12 +19,12 @@
 //                   with shared-memory atomics: no global atomics)
 //   k_tile_sort     bucket sort, heavy first: the remainder keys are unique,
 //                   so any correct sort of them gives the same result.
-//                   Buckets of up to 512 keys: one warp each, a bitonic
-//                   network in registers (k_tile_sort_small); up to 8192
-//                   keys: one CTA, 16 keys per thread in registers, stages
-//                   across warps through shared memory; longer buckets sort
-//                   8192-key runs in shared memory and merge them by rank in
-//                   global memory.  The sort writes tile_id << 32 |
+//                   One launch: buckets of up to 512 keys take one warp
+//                   each, a merge sort with the keys in registers; up to
+//                   8192 keys one CTA, each warp merge-sorting 512 before
+//                   the warps merge their runs; longer buckets sort
+//                   8192-key runs in shared memory and merge them by rank
+//                   in global memory.  The sort writes tile_id << 32 |
 //                   depth_bits and the id.
 // The scatter order inside a bucket depends on atomics, the output does not.
 // Everything stays on the device: the key count is never read by the host.
@@ -35,6 +35,7 @@ namespace gs {
 #define BIN_THREADS 256
 #define TS_THREADS 512
 #define TS_SMEM_KEYS 8192
+#define SW_MAX 512               // buckets up to this length sort with one warp
 
 typedef unsigned long long u64;
 
@@ -201,37 +202,43 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
     }
 }
 
-// Heavy-first tile order: tiles grouped by floor(log2(length + 1)), longest
-// group first, ascending tile index inside a group (a stable counting sort,
-// so the order is a function of the lists alone: the compositing kernels
-// treat the first tiles of the order differently, and their results must
-// not depend on scheduling).
+// Heavy-first tile order: tiles grouped by the power of two bounding their
+// length from above, (2^k, 2^(k+1)] (empty tiles last), longest group
+// first, ascending tile index inside a group: a stable counting sort, so the
+// order is a function of the lists alone (the compositing kernels may treat
+// the first tiles of the order differently, and their results must not
+// depend on scheduling).  n_big receives the number of tiles longer than
+// SW_MAX keys, which are exactly the first n_big of the order.
+__device__ __forceinline__ int order_group(uint32_t len) { return len == 0 ? 33 : __clz(len - 1u); }
+
 __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ ranges, int ntiles,
-                                                     uint32_t* __restrict__ order) {
-    __shared__ uint32_t cnt[33], cur[33];
-    __shared__ uint32_t wcnt[32][33];  // per warp and group, within a 1024-tile chunk
+                                                     uint32_t* __restrict__ order, uint32_t* __restrict__ n_big) {
+    __shared__ uint32_t cnt[34], cur[34];
+    __shared__ uint32_t wcnt[32][34];  // per warp and group, within a 1024-tile chunk
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    if (threadIdx.x < 34) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const uint32_t len = ranges[2 * t + 1] - ranges[2 * t];
-        atomicAdd(&cnt[__clz(len + 1u)], 1u);  // group 0 = longest
-    }
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+        atomicAdd(&cnt[order_group(ranges[2 * t + 1] - ranges[2 * t])], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
-        for (int b = 0; b < 33; ++b) { cur[b] = run; run += cnt[b]; }
+        for (int b = 0; b < 34; ++b) {
+            if (b == order_group(SW_MAX + 1)) *n_big = run + cnt[b];
+            cur[b] = run;
+            run += cnt[b];
+        }
     }
     for (int base = 0; base < ntiles; base += 1024) {
-        for (int q = threadIdx.x; q < 32 * 33; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+        for (int q = threadIdx.x; q < 32 * 34; q += blockDim.x) (&wcnt[0][0])[q] = 0;
         __syncthreads();
         const int t = base + (int)threadIdx.x;
-        const int grp = t < ntiles ? __clz(ranges[2 * t + 1] - ranges[2 * t] + 1u) : 33;
+        const int grp = t < ntiles ? order_group(ranges[2 * t + 1] - ranges[2 * t]) : 34;
         const unsigned same = __match_any_sync(0xffffffffu, grp);
         const unsigned rank = __popc(same & ((1u << lane) - 1u));
-        if (grp < 33 && rank == 0) wcnt[warp][grp] = __popc(same);
+        if (grp < 34 && rank == 0) wcnt[warp][grp] = __popc(same);
         __syncthreads();
-        if (threadIdx.x < 33) {  // exclusive scan over the warps, per group
+        if (threadIdx.x < 34) {  // exclusive scan over the warps, per group
             uint32_t run = cur[threadIdx.x];
             for (int w = 0; w < 32; ++w) {
                 const uint32_t v = wcnt[w][threadIdx.x];
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict_
             cur[threadIdx.x] = run;
         }
         __syncthreads();
-        if (grp < 33) order[wcnt[warp][grp] + rank] = (uint32_t)t;
+        if (grp < 34) order[wcnt[warp][grp] + rank] = (uint32_t)t;
         __syncthreads();
     }
 }
@@ -299,152 +306,159 @@ __device__ __forceinline__ int rank_in(const u64* r, int len, u64 x) {
 }
 
 // ---------------------------------------------------------------------------
-// Bitonic networks with the keys in registers.  Position x of the sequence is
-// held by lane x % 32, register (x / 32) % KPT, warp x / (32 KPT) of the
-// sorting group.  A compare-exchange at distance j is a warp shuffle for
-// j < 32, a register swap inside the thread for 32 <= j < 32 KPT, and goes
-// through shared memory for larger j.  Merge step k sorts position x
-// ascending iff (x & k) == 0.
+// Merge sort of a bucket with the keys in registers.  Thread t of the
+// sorting group holds positions [t KPT, (t+1) KPT) (blocked layout).  Each
+// thread first sorts its KPT keys with a register network; then rounds of
+// merges double the sorted run length: each thread finds where its KPT
+// outputs start in the pair of runs (merge path: a binary search on the
+// diagonal) and merges KPT keys serially.  Runs go through shared memory,
+// padded by one key per 16 so that the blocked accesses spread over the
+// banks.  Padding keys are ~0 (above every real key: depth bits < 2^31).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
-__device__ __forceinline__ u64 umax64(u64 a, u64 b) { return a < b ? b : a; }
+__device__ __forceinline__ int pad16(int x) { return x + (x >> 4); }
 
 template <int KPT>
-__device__ __forceinline__ void bit_shfl_stage(u64 (&v)[KPT], int base, int k, int j) {
-    const int lane = threadIdx.x & 31;
-    const bool low = (lane & j) == 0;
+__device__ __forceinline__ void sort_regs(u64 (&v)[KPT]) {
 #pragma unroll
-    for (int r = 0; r < KPT; ++r) {
-        const u64 p = __shfl_xor_sync(0xffffffffu, v[r], j);
-        const bool asc = ((base + lane + 32 * r) & k) == 0;
-        v[r] = (low == asc) ? umin64(v[r], p) : umax64(v[r], p);
-    }
-}
-
-template <int KPT, int JR>
-__device__ __forceinline__ void bit_reg_stage(u64 (&v)[KPT], int base, int k) {
-    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= KPT; k <<= 1)
 #pragma unroll
-    for (int r = 0; r < KPT; ++r) {
-        if (r & JR) continue;
-        const bool asc = ((base + lane + 32 * r) & k) == 0;
-        const u64 lo = umin64(v[r], v[r | JR]), hi = umax64(v[r], v[r | JR]);
-        v[r] = asc ? lo : hi;
-        v[r | JR] = asc ? hi : lo;
-    }
-}
-
-// The stages j = jtop, jtop/2, ..., 1 (jtop < 32 KPT) of merge step k.
-template <int KPT>
-__device__ __forceinline__ void bit_warp_steps(u64 (&v)[KPT], int base, int k, int jtop) {
-    for (int j = jtop; j > 0; j >>= 1) {
-        switch (j >> 5) {
-            case 0: bit_shfl_stage<KPT>(v, base, k, j); break;
-            case 1: if constexpr (KPT > 1) bit_reg_stage<KPT, 1>(v, base, k); break;
-            case 2: if constexpr (KPT > 2) bit_reg_stage<KPT, 2>(v, base, k); break;
-            case 4: if constexpr (KPT > 4) bit_reg_stage<KPT, 4>(v, base, k); break;
-            case 8: if constexpr (KPT > 8) bit_reg_stage<KPT, 8>(v, base, k); break;
-            default: break;
-        }
-    }
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < KPT; ++i) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const u64 lo = v[i] < v[p] ? v[i] : v[p], hi = v[i] < v[p] ? v[p] : v[i];
+                    const bool asc = (i & k) == 0;
+                    v[i] = asc ? lo : hi;
+                    v[p] = asc ? hi : lo;
+                }
+            }
 }
 
 __device__ __forceinline__ void named_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Ascending sort of the W * 32 * KPT keys held by warps 0..W-1; stages that
-// cross warps exchange through s[] (W * 32 * KPT keys) under named barrier 1.
+// Merge rounds from sorted runs of `run` keys up to one run of nthr * KPT
+// keys.  t: the thread's index in the group; buf: the group's buffer
+// (pad16 of nthr * KPT keys); the group synchronises with __syncwarp when
+// it is one warp, else with named barrier 1 over nthr threads.
 template <int KPT>
-__device__ __forceinline__ void bit_sort_group(u64 (&v)[KPT], int W, u64* s) {
-    const int lane = threadIdx.x & 31;
-    const int base = (threadIdx.x >> 5) * 32 * KPT;
-    const int m = W * 32 * KPT;
-    for (int k = 2; k <= m; k <<= 1) {
-        int j = k >> 1;
-        for (; j >= 32 * KPT; j >>= 1) {
+__device__ __forceinline__ void merge_rounds(u64 (&v)[KPT], u64* buf, int t, int nthr, int run) {
+    const int M = nthr * KPT;
+    for (; run < M; run <<= 1) {
 #pragma unroll
-            for (int r = 0; r < KPT; ++r) s[base + lane + 32 * r] = v[r];
-            named_bar(1, W * 32);
-#pragma unroll
-            for (int r = 0; r < KPT; ++r) {
-                const int x = base + lane + 32 * r;
-                const u64 p = s[x ^ j];
-                const bool asc = (x & k) == 0, low = (x & j) == 0;
-                v[r] = (low == asc) ? umin64(v[r], p) : umax64(v[r], p);
-            }
-            named_bar(1, W * 32);
+        for (int k = 0; k < KPT; ++k) buf[pad16(t * KPT + k)] = v[k];
+        if (nthr == 32) __syncwarp(); else named_bar(1, nthr);
+        const int pair0 = (t * KPT) & ~(2 * run - 1);
+        const int diag = t * KPT - pair0;
+        const int a0 = pair0, b0 = pair0 + run;
+        int lo = max(0, diag - run), hi = min(diag, run);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (buf[pad16(a0 + mid)] < buf[pad16(b0 + diag - 1 - mid)]) lo = mid + 1;
+            else hi = mid;
         }
-        bit_warp_steps<KPT>(v, base, k, j);
+        int i = lo, j = diag - lo;
+        u64 x = i < run ? buf[pad16(a0 + i)] : ~0ull;
+        u64 y = j < run ? buf[pad16(b0 + j)] : ~0ull;
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+            const bool ta = x < y;
+            v[k] = ta ? x : y;
+            if (ta) {
+                ++i;
+                x = i < run ? buf[pad16(a0 + i)] : ~0ull;
+            } else {
+                ++j;
+                y = j < run ? buf[pad16(b0 + j)] : ~0ull;
+            }
+        }
+        if (nthr == 32) __syncwarp(); else named_bar(1, nthr);
     }
 }
 
-// Sorts one bucket of at most 32 * KPT keys with the calling warp and
-// writes tile_id << 32 | depth_bits and the ids.
+// Loads a bucket of n <= nthr * KPT keys into the blocked layout (coalesced
+// through buf), padding with ~0.
 template <int KPT>
-__device__ __forceinline__ void warp_sort_bucket(u64* key, uint32_t* val, int n, u64 hi) {
+__device__ __forceinline__ void load_blocked(const u64* key, int n, u64 (&v)[KPT], u64* buf, int t, int nthr) {
+    for (int x = t; x < nthr * KPT; x += nthr) buf[pad16(x)] = x < n ? key[x] : ~0ull;
+    if (nthr == 32) __syncwarp(); else named_bar(1, nthr);
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) v[k] = buf[pad16(t * KPT + k)];
+    if (nthr == 32) __syncwarp(); else named_bar(1, nthr);
+}
+
+// Writes the sorted bucket (coalesced through buf): tile_id << 32 |
+// depth_bits and the id.
+template <int KPT>
+__device__ __forceinline__ void store_sorted(u64* key, uint32_t* val, int n, u64 hi, const u64 (&v)[KPT], u64* buf,
+                                             int t, int nthr) {
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) buf[pad16(t * KPT + k)] = v[k];
+    if (nthr == 32) __syncwarp(); else named_bar(1, nthr);
+    for (int x = t; x < n; x += nthr) {
+        const u64 w = buf[pad16(x)];
+        key[x] = hi | (w >> 32);
+        val[x] = (uint32_t)w;
+    }
+}
+
+template <int KPT>
+__device__ __forceinline__ void warp_sort_bucket(u64* key, uint32_t* val, int n, u64 hi, u64* buf) {
     const int lane = threadIdx.x & 31;
     u64 v[KPT];
-#pragma unroll
-    for (int r = 0; r < KPT; ++r) v[r] = lane + 32 * r < n ? key[lane + 32 * r] : ~0ull;
-    for (int k = 2; k <= 32 * KPT; k <<= 1) bit_warp_steps<KPT>(v, 0, k, k >> 1);
-#pragma unroll
-    for (int r = 0; r < KPT; ++r)
-        if (lane + 32 * r < n) {
-            key[lane + 32 * r] = hi | (v[r] >> 32);
-            val[lane + 32 * r] = (uint32_t)v[r];
-        }
+    load_blocked<KPT>(key, n, v, buf, lane, 32);
+    sort_regs<KPT>(v);
+    merge_rounds<KPT>(v, buf, lane, 32, KPT);
+    store_sorted<KPT>(key, val, n, hi, v, buf, lane, 32);
 }
 
-#define SW_WARPS 8
-#define SW_MAX 512
 
-// Buckets of 1..SW_MAX keys: one warp per bucket, no shared memory.
-__global__ void __launch_bounds__(SW_WARPS * 32) k_tile_sort_small(const uint32_t* __restrict__ ranges,
-                                                                  const uint32_t* __restrict__ order, int ntiles,
-                                                                  u64* __restrict__ keys,
-                                                                  uint32_t* __restrict__ vals) {
-    const int idx = blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
-    if (idx >= ntiles) return;
-    const int t = order ? (int)order[idx] : idx;
-    const uint32_t b = ranges[2 * t], e = ranges[2 * t + 1];
-    const int n = (int)(e - b);
-    if (n <= 0 || n > SW_MAX) return;
-    const u64 hi = (u64)(uint32_t)t << 32;
-    if (n <= 32) warp_sort_bucket<1>(keys + b, vals + b, n, hi);
-    else if (n <= 64) warp_sort_bucket<2>(keys + b, vals + b, n, hi);
-    else if (n <= 128) warp_sort_bucket<4>(keys + b, vals + b, n, hi);
-    else if (n <= 256) warp_sort_bucket<8>(keys + b, vals + b, n, hi);
-    else warp_sort_bucket<16>(keys + b, vals + b, n, hi);
-}
-
+// One launch for all buckets.  CTAs below n_big take the long buckets
+// (first in the order), one each; every later CTA takes 16 short buckets,
+// one per warp (both kinds run at once).
 __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __restrict__ ranges,
-                                                          const uint32_t* __restrict__ order, u64* __restrict__ keys,
-                                                          uint32_t* __restrict__ vals, u64* __restrict__ tmp) {
+                                                          const uint32_t* __restrict__ order,
+                                                          const uint32_t* __restrict__ n_big_p, int ntiles,
+                                                          u64* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                          u64* __restrict__ tmp) {
     extern __shared__ __align__(16) u64 s[];
-    const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+    const int n_big = (int)*n_big_p;
+    if ((int)blockIdx.x >= n_big) {
+        const int warp = threadIdx.x >> 5;
+        const int idx = n_big + ((int)blockIdx.x - n_big) * (TS_THREADS / 32) + warp;
+        if (idx >= ntiles) return;
+        const int t = (int)order[idx];
+        const uint32_t b = ranges[2 * t], e = ranges[2 * t + 1];
+        const int n = (int)(e - b);
+        if (n <= 0 || n > SW_MAX) return;
+        const u64 hi = (u64)(uint32_t)t << 32;
+        u64* buf = s + pad16(warp * SW_MAX);
+        if (n <= 32) warp_sort_bucket<1>(keys + b, vals + b, n, hi, buf);
+        else if (n <= 64) warp_sort_bucket<2>(keys + b, vals + b, n, hi, buf);
+        else if (n <= 128) warp_sort_bucket<4>(keys + b, vals + b, n, hi, buf);
+        else if (n <= 256) warp_sort_bucket<8>(keys + b, vals + b, n, hi, buf);
+        else warp_sort_bucket<16>(keys + b, vals + b, n, hi, buf);
+        return;
+    }
+    const int t = (int)order[blockIdx.x];
     const uint32_t b = ranges[2 * t], e = ranges[2 * t + 1];
     const int n = (int)(e - b);
-    if (n <= SW_MAX) return;  // k_tile_sort_small
     u64* key = keys + b;
     if (n <= TS_SMEM_KEYS) {
-        // m / 512 warps, 16 keys per thread in registers
+        // m / 512 warps, 16 keys per thread in registers: each warp sorts a
+        // run of 512, then the group merges the runs
         int m = 2 * SW_MAX;
         while (m < n) m <<= 1;
         const int W = m / SW_MAX;
         if ((int)(threadIdx.x >> 5) >= W) return;
-        const int x0 = (threadIdx.x >> 5) * SW_MAX + (threadIdx.x & 31);
         u64 v[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = x0 + 32 * r < n ? key[x0 + 32 * r] : ~0ull;
-        bit_sort_group<16>(v, W, s);
-        const u64 hi = (u64)(uint32_t)t << 32;
-#pragma unroll
-        for (int r = 0; r < 16; ++r)
-            if (x0 + 32 * r < n) {
-                key[x0 + 32 * r] = hi | (v[r] >> 32);
-                vals[b + x0 + 32 * r] = (uint32_t)v[r];
-            }
+        load_blocked<16>(key, n, v, s, (int)threadIdx.x, W * 32);
+        sort_regs<16>(v);
+        merge_rounds<16>(v, s + pad16((threadIdx.x >> 5) * SW_MAX), (int)(threadIdx.x & 31), 32, 16);
+        merge_rounds<16>(v, s, (int)threadIdx.x, W * 32, SW_MAX);
+        store_sorted<16>(key, vals + b, n, (u64)(uint32_t)t << 32, v, s, (int)threadIdx.x, W * 32);
         return;
     }
     // long bucket: sorted runs of TS_SMEM_KEYS, then merge by rank
@@ -490,7 +504,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __rest
 // Workspace layout
 // ---------------------------------------------------------------------------
 struct BinLayout {
-    size_t off_count, off_fill, off_start, off_hist, off_tmp, zero_bytes, total;
+    size_t off_count, off_fill, off_start, off_order, off_nbig, off_hist, off_tmp, zero_bytes, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -512,6 +526,8 @@ static BinLayout bin_layout(int64_t n, int64_t cap, int ntiles) {
     L.off_fill = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
     L.zero_bytes = o;
     L.off_start = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
+    L.off_order = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
+    L.off_nbig = o; o = align256(o + sizeof(uint32_t));
     L.off_hist = o;
     if (ntiles <= AGG_MAX_TILES) o = align256(o + sizeof(uint32_t) * (size_t)ntiles * (size_t)rows);
     L.off_tmp = o; o = align256(o + sizeof(u64) * (size_t)(cap > 0 ? cap : 1));
@@ -634,10 +650,11 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
     if (!err) return set_error(GS_ERR_CUDA, "status word address");
     k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, keys_capacity, start, tile_ranges, n_keys_out, err);
     if ((s = check_launch("k_tile_scan")) != GS_OK) return s;
-    if (tile_order) {
-        k_tile_order<<<1, 1024, 0, st>>>(tile_ranges, ntiles, tile_order);
-        if ((s = check_launch("k_tile_order")) != GS_OK) return s;
-    }
+    // the heavy-first order drives the sort; it is returned when asked for
+    uint32_t* order = tile_order ? tile_order : (uint32_t*)(ws + L.off_order);
+    uint32_t* n_big = (uint32_t*)(ws + L.off_nbig);
+    k_tile_order<<<1, 1024, 0, st>>>(tile_ranges, ntiles, order, n_big);
+    if ((s = check_launch("k_tile_order")) != GS_OK) return s;
     if (n == 0 || keys_capacity == 0) return GS_OK;
     if (ntiles <= AGG_MAX_TILES) {
         if ((s = set_agg_smem_attrs()) != GS_OK) return s;
@@ -671,15 +688,12 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
         cudaGetDevice(&dev);
         if (dev < 0 || dev >= 64 || !attr_done[dev]) {
             if (cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(TS_SMEM_KEYS * sizeof(u64))) != cudaSuccess)
+                                     (int)((TS_SMEM_KEYS + TS_SMEM_KEYS / 16) * sizeof(u64))) != cudaSuccess)
                 return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(k_tile_sort)");
             if (dev >= 0 && dev < 64) attr_done[dev] = true;
         }
     }
-    k_tile_sort_small<<<(unsigned)((ntiles + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, 0, st>>>(
-        tile_ranges, tile_order, ntiles, (u64*)keys_out, vals_out);
-    if ((s = check_launch("k_tile_sort_small")) != GS_OK) return s;
-    k_tile_sort<<<(unsigned)ntiles, TS_THREADS, TS_SMEM_KEYS * sizeof(u64), st>>>(tile_ranges, tile_order,
-                                                                                 (u64*)keys_out, vals_out, tmp);
+    k_tile_sort<<<(unsigned)ntiles, TS_THREADS, (TS_SMEM_KEYS + TS_SMEM_KEYS / 16) * sizeof(u64), st>>>(
+        tile_ranges, order, n_big, ntiles, (u64*)keys_out, vals_out, tmp);
     return check_launch("k_tile_sort");
 }
