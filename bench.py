@@ -185,8 +185,7 @@ def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pos
 
     def interval():
         for i in range(K):
-            rast.step(gd, cam_s, trgb, tdep, gs.GS_TRACK, rebin=(i == 0))
-            gs.gs_pose_update(pose, rast.pose, adam, lr_t, lr_r)
+            rast.track_step(gd, cam_s, trgb, tdep, pose, adam, lr_t, lr_r, rebin=(i == 0))
 
     pose.copy_(pose0)
     adam.zero_()
@@ -233,7 +232,7 @@ def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pos
 
 # Algorithmic work per launch of each stage: bytes for
 # the streaming stages, FP32 FLOPs per blended fragment for the compositing.
-FLOP_PER_FRAGMENT = {"render_fwd": 27, "render_bwd": 67}
+FLOP_PER_FRAGMENT = {"render_fwd": 27, "render_fwd_loss": 27, "render_bwd": 67}
 
 
 def roofline(stage_ms, n, n_keys, P, blended, clk):
@@ -267,9 +266,7 @@ def roofline(stage_ms, n, n_keys, P, blended, clk):
     alg = {
         "project": 56 * n + 48 * n,
         "bin_sort": 20 * n + 8 * n_keys * 2 + 12 * n_keys,
-        "loss": 48 * P,
-        "project_bwd_pose": (56 + 48) * n + 8 * n,
-        "pose_update": 100,
+        "project_bwd_pose_step": (56 + 48) * n + 8 * n,
     }[dom]
     ach = alg / t / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
@@ -387,8 +384,7 @@ def run_ours(args):
     lr_t, lr_r = 1e-3, 1e-3
 
     def step():
-        rast.step(gd, cam_s, trgb, tdep, gs.GS_TRACK)
-        gs.gs_pose_update(pose, rast.pose, adam, lr_t, lr_r)
+        rast.track_step(gd, cam_s, trgb, tdep, pose, adam, lr_t, lr_r)
 
     if args.profile:
         for _ in range(args.warmup + args.steps):
@@ -446,7 +442,7 @@ def run_ours(args):
 
     # ---- stage timings (eager, events on the launching stream) ----
     Kst = min(K, 30)
-    names = ["project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd_pose", "pose_update"]
+    names = ["project", "bin_sort", "render_fwd_loss", "render_bwd", "project_bwd_pose_step"]
     acc = {k: 0.0 for k in names}
     cs = cam_s
     for _ in range(Kst):
@@ -458,19 +454,16 @@ def run_ours(args):
         gs.gs_bin_sort(cs, rast.splats, n, rast.capacity, rast.rec_dtype, ws=rast._sort_ws(cs), keys=rast.keys,
                        vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges, order=rast.order)
         evs[2].record()
-        gs.gs_render_fwd(rast.cfg, cs, rast.splats, n, rast.vals, rast.ranges, rast.rec_dtype, out=rast.img,
-                         order=rast.order)
+        gs.gs_render_fwd_loss(rast.cfg, cs, rast.splats, n, rast.vals, rast.ranges, trgb, tdep, rast.rec_dtype,
+                              out=rast.img, dimg=rast.dimg, order=rast.order)
         evs[3].record()
-        rast.loss_grad(cs, trgb, tdep)
-        evs[4].record()
         gs.gs_render_bwd(rast.cfg, cs, gd, rast.splats, rast.vals, rast.ranges, rast.img["t_final"],
                          rast.img["last_idx"], rast.dimg["d_rgb"], rast.dimg["d_depth"], gs.GS_TRACK,
                          rast.rec_dtype, grad2d=rast.grad2d, order=rast.order)
+        evs[4].record()
+        gs.gs_project_bwd_step(rast.cfg, cs, gd, rast.grad2d, rast.pose, gs.pose_step(pose, adam, lr_t, lr_r),
+                               score=rast.score, ws=rast._bwd_ws(cs, gd))
         evs[5].record()
-        gs.gs_project_bwd(rast.cfg, cs, gd, rast.grad2d, pose=rast.pose, score=rast.score, ws=rast._bwd_ws(cs, gd))
-        evs[6].record()
-        gs.gs_pose_update(pose, rast.pose, adam, lr_t, lr_r)
-        evs[7].record()
         torch.cuda.synchronize()
         for i, k in enumerate(names):
             acc[k] += evs[i].elapsed_time(evs[i + 1])
@@ -511,8 +504,10 @@ def run_ours(args):
     e2e = {"value": world * Ke / (te / 1e3), "unit": "iters/s",
            "h2d_bytes_per_step": trgb.numel() * 4 + tdep.numel() * 4, "d2h_bytes_per_step": 7 * 8}
 
-    passes = (32 + max(1, (int(np.ceil(np.log2(max(2, rast._grid[2] * rast._grid[3])))))) + 7) // 8
-    launches_per_step = 1 + (6 + passes) + 1 + 1 + 1 + 1 + 1
+    # kernels of one fused tracking iteration: k_project; k_tile_hist,
+    # k_col_scan, k_tile_scan, k_tile_order, k_tile_scatter_rows, k_tile_sort;
+    # k_render_fwd (+ loss); k_render_bwd; k_project_bwd (+ pose step)
+    launches_per_step = 1 + 6 + 1 + 1 + 1
     line = {
         "metric": METRIC, "value": iters_s, "unit": "iters/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",

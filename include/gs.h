@@ -246,6 +246,21 @@ gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, const float* rg
                      const float* depth, const float* target_rgb, const float* target_depth,
                      float* d_rgb, float* d_depth, double* loss_out, gs_stream stream);
 
+/* Forward compositing and the loss in one launch (a fusion of the tracking
+ * iteration; the paper's Sec. 5 pipeline feeds the loss straight from the
+ * rendering engines): gs_render_fwd's outputs, plus gs_loss_l1's d_rgb and
+ * d_depth computed by the thread that finishes each pixel (identical
+ * values), and loss_out (device double, overwritten: the call zeroes it
+ * first) summed per warp in float32 and across warps in float64 (equal to
+ * gs_loss_l1's to float32 rounding of the partial sums). */
+gs_status gs_render_fwd_loss(const gs_config* cfg, const gs_camera* cam, int rec_dtype,
+                             const void* splats, int64_t n, const uint32_t* vals,
+                             const uint32_t* tile_ranges, const uint32_t* tile_order, float* rgb,
+                             float* depth, float* t_final, uint32_t* last_idx,
+                             uint32_t* n_blended, const float* target_rgb,
+                             const float* target_depth, float* d_rgb, float* d_depth,
+                             double* loss_out, gs_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* A-7 Backward compositing (Sec. 2.2, Step 4; Eq. 4 and Eq. 5)             */
 /* ---------------------------------------------------------------------- */
@@ -376,6 +391,27 @@ gs_status gs_downsample(int64_t frame_idx, int64_t last_kf_idx, int is_keyframe,
  *   Unit (Sec. 5.1) does not fix the optimizer; Adam is this library's. */
 gs_status gs_pose_update(float* pose, const double* pose_grad6, float* adam, float lr_trans,
                          float lr_rot, float beta1, float beta2, float eps, gs_stream stream);
+
+/* The pose step of gs_pose_update, as an argument of gs_project_bwd_step. */
+typedef struct {
+    float* pose;    /* device float[12], updated in place */
+    float* adam;    /* device float[13]: m[6], v[6], step count (starts zeroed) */
+    float lr_trans; /* learning rate of rho */
+    float lr_rot;   /* learning rate of phi */
+    float beta1, beta2, eps;
+} gs_pose_step;
+
+/* gs_project_bwd with the pose step fused into its last block: the block that
+ * completes the compensated float64 pose-gradient reduction (pose_grad6,
+ * required here) applies gs_pose_update's Adam step and SE(3) update with
+ * `step` (same arithmetic, one launch fewer per tracking iteration).  Every
+ * block reads the pose before the last block updates it, so a camera whose
+ * `pose` is step->pose sees the old pose throughout the call.  step NULL:
+ * plain gs_project_bwd.  Workspace as gs_project_bwd. */
+gs_status gs_project_bwd_step(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                              const float* grad2d, gs_grads* grads, double* pose_grad6,
+                              float* score_terms, const gs_pose_step* step, void* workspace,
+                              size_t* workspace_bytes, gs_stream stream);
 
 /* Mapping step: Adam over up to GS_ADAM_MAX_TENSORS float32 arrays in one
  * launch (the map update fed by the backward, Sec. 2.2 Step 5 / Sec. 5.4;

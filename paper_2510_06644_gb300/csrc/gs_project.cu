@@ -158,11 +158,68 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double v) {
     s = t;
 }
 
+// ---------------------------------------------------------------------------
+// Pose step: Adam on xi, then T <- exp(xi^) T
+// ---------------------------------------------------------------------------
+__device__ void pose_adam_exp(float* __restrict__ pose, const double* __restrict__ grad, float* __restrict__ adam,
+                              float lr_t, float lr_r, float b1, float b2, float eps) {
+    const float step = adam[12] + 1.f;
+    adam[12] = step;
+    const float c1 = 1.f - powf(b1, step), c2 = 1.f - powf(b2, step);
+    float xi[6];
+    for (int i = 0; i < 6; ++i) {
+        const float g = (float)grad[i];
+        const float m = b1 * adam[i] + (1.f - b1) * g;
+        const float v = b2 * adam[6 + i] + (1.f - b2) * g * g;
+        adam[i] = m;
+        adam[6 + i] = v;
+        xi[i] = -(i < 3 ? lr_t : lr_r) * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+    // exp of (rho, phi): R_d = Rodrigues(phi), V = I + (1-cos)/th^2 K + (th-sin)/th^3 K^2
+    const float px = xi[3], py = xi[4], pz = xi[5];
+    const float th2 = px * px + py * py + pz * pz, th = sqrtf(th2);
+    float A, B, Cc;
+    if (th < 1e-4f) {
+        A = 1.f - th2 / 6.f;
+        B = 0.5f - th2 / 24.f;
+        Cc = 1.f / 6.f - th2 / 120.f;
+    } else {
+        A = sinf(th) / th;
+        B = (1.f - cosf(th)) / th2;
+        Cc = (th - sinf(th)) / (th2 * th);
+    }
+    const float K[9] = {0.f, -pz, py, pz, 0.f, -px, -py, px, 0.f};
+    float K2[9], Rd[9], V[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+    for (int i = 0; i < 9; ++i) {
+        const float I = (i % 4 == 0) ? 1.f : 0.f;
+        Rd[i] = I + A * K[i] + B * K2[i];
+        V[i] = I + B * K[i] + Cc * K2[i];
+    }
+    float R[9], t[3], Rn[9], tn[3];
+    for (int i = 0; i < 9; ++i) R[i] = pose[i];
+    for (int i = 0; i < 3; ++i) t[i] = pose[9 + i];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Rn[3 * i + j] = Rd[3 * i] * R[j] + Rd[3 * i + 1] * R[3 + j] + Rd[3 * i + 2] * R[6 + j];
+        tn[i] = Rd[3 * i] * t[0] + Rd[3 * i + 1] * t[1] + Rd[3 * i + 2] * t[2] +
+                V[3 * i] * xi[0] + V[3 * i + 1] * xi[1] + V[3 * i + 2] * xi[2];
+    }
+    for (int i = 0; i < 9; ++i) pose[i] = Rn[i];
+    for (int i = 0; i < 3; ++i) pose[9 + i] = tn[i];
+}
+
+__global__ void k_pose_update(float* __restrict__ pose, const double* __restrict__ grad, float* __restrict__ adam,
+                              float lr_t, float lr_r, float b1, float b2, float eps) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    pose_adam_exp(pose, grad, adam, lr_t, lr_r, b1, b2, eps);
+}
+
 // Final combination of the per-block float64 pose partials by the last block
 // to finish (no spin: the block that takes the last ticket sees every other
 // block's partial, published before its ticket).  Warp w < 6 sums component w.
 __device__ void pose_final_last_block(const double* __restrict__ part, int nblk, double* __restrict__ out,
-                                      unsigned int* __restrict__ ticket) {
+                                      unsigned int* __restrict__ ticket, const gs_pose_step& step) {
     __shared__ bool s_last;
     __threadfence();
     if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)nblk - 1u);
@@ -183,6 +240,11 @@ __device__ void pose_final_last_block(const double* __restrict__ part, int nblk,
         if (lane == 0) out[w] = s + c;
     }
     if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
+    if (step.pose) {  // the fused pose step (every block has read the pose by now)
+        __syncthreads();
+        if (threadIdx.x == 0)
+            pose_adam_exp(step.pose, out, step.adam, step.lr_trans, step.lr_rot, step.beta1, step.beta2, step.eps);
+    }
 }
 
 template <bool WANT_GRADS, bool WANT_POSE, bool WANT_SCORE>
@@ -191,7 +253,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_co
                                                             gs_grads grads, float* __restrict__ score,
                                                             double* __restrict__ pose_part,
                                                             double* __restrict__ pose_out,
-                                                            unsigned int* __restrict__ ticket) {
+                                                            unsigned int* __restrict__ ticket, gs_pose_step step) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float pose[6] = {0, 0, 0, 0, 0, 0};
     resolve_pose(cam);
@@ -353,7 +415,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_co
             for (int w = 0; w < PB_THREADS / 32; ++w) s += ws[w][threadIdx.x];
             pose_part[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
         }
-        pose_final_last_block(pose_part, (int)gridDim.x, pose_out, ticket);
+        pose_final_last_block(pose_part, (int)gridDim.x, pose_out, ticket, step);
     }
 }
 
@@ -407,7 +469,24 @@ extern "C" gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, 
                                     const float* grad2d, gs_grads* grads, double* pose_grad6,
                                     float* score_terms, void* workspace, size_t* workspace_bytes,
                                     gs_stream stream) {
+    return gs_project_bwd_step(cfg, cam, g, grad2d, grads, pose_grad6, score_terms, nullptr, workspace,
+                               workspace_bytes, stream);
+}
+
+extern "C" gs_status gs_project_bwd_step(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                                         const float* grad2d, gs_grads* grads, double* pose_grad6,
+                                         float* score_terms, const gs_pose_step* step, void* workspace,
+                                         size_t* workspace_bytes, gs_stream stream) {
     if (!cfg || !workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "config or workspace_bytes is NULL");
+    if (step) {
+        if (!pose_grad6) return set_error(GS_ERR_INVALID_ARG, "a pose step needs pose_grad6");
+        if (!step->pose || !step->adam) return set_error(GS_ERR_INVALID_ARG, "pose step: NULL pose or adam");
+        if (!(step->beta1 >= 0.f && step->beta1 < 1.f) || !(step->beta2 >= 0.f && step->beta2 < 1.f) ||
+            !(step->eps > 0.f))
+            return set_error(GS_ERR_INVALID_ARG, "pose step: bad Adam constants");
+    }
+    const gs_pose_step no_step = {nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const gs_pose_step ps = step ? *step : no_step;
     gs_status s;
     if ((s = check_camera(cam)) != GS_OK) return s;
     if ((s = check_gaussians(g)) != GS_OK) return s;
@@ -422,6 +501,8 @@ extern "C" gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, 
     if (g->n == 0) {
         if (want_pose && cudaMemsetAsync(pose_grad6, 0, 6 * sizeof(double), st) != cudaSuccess)
             return set_error(GS_ERR_CUDA, "memset pose");
+        if (step) return gs_pose_update(ps.pose, pose_grad6, ps.adam, ps.lr_trans, ps.lr_rot, ps.beta1, ps.beta2,
+                                        ps.eps, stream);
         return GS_OK;
     }
     if (!grad2d) return set_error(GS_ERR_INVALID_ARG, "grad2d is NULL");
@@ -432,7 +513,8 @@ extern "C" gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, 
     if (want_pose && cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset ticket");
 #define GS_PB_LAUNCH(A, B, C_) \
-    k_project_bwd<A, B, C_><<<nblk, PB_THREADS, 0, st>>>(*cam, *cfg, *g, grad2d, gg, score_terms, part, pose_grad6, ticket)
+    k_project_bwd<A, B, C_><<<nblk, PB_THREADS, 0, st>>>(*cam, *cfg, *g, grad2d, gg, score_terms, part, pose_grad6, \
+                                                         ticket, ps)
     if (want_grads) {
         if (want_pose) { if (want_score) GS_PB_LAUNCH(true, true, true); else GS_PB_LAUNCH(true, true, false); }
         else { if (want_score) GS_PB_LAUNCH(true, false, true); else GS_PB_LAUNCH(true, false, false); }
@@ -442,58 +524,6 @@ extern "C" gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, 
     }
 #undef GS_PB_LAUNCH
     return check_launch("k_project_bwd");
-}
-
-// ---------------------------------------------------------------------------
-// Pose step: Adam on xi, then T <- exp(xi^) T
-// ---------------------------------------------------------------------------
-__global__ void k_pose_update(float* __restrict__ pose, const double* __restrict__ grad, float* __restrict__ adam,
-                              float lr_t, float lr_r, float b1, float b2, float eps) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const float step = adam[12] + 1.f;
-    adam[12] = step;
-    const float c1 = 1.f - powf(b1, step), c2 = 1.f - powf(b2, step);
-    float xi[6];
-    for (int i = 0; i < 6; ++i) {
-        const float g = (float)grad[i];
-        const float m = b1 * adam[i] + (1.f - b1) * g;
-        const float v = b2 * adam[6 + i] + (1.f - b2) * g * g;
-        adam[i] = m;
-        adam[6 + i] = v;
-        xi[i] = -(i < 3 ? lr_t : lr_r) * (m / c1) / (sqrtf(v / c2) + eps);
-    }
-    // exp of (rho, phi): R_d = Rodrigues(phi), V = I + (1-cos)/th^2 K + (th-sin)/th^3 K^2
-    const float px = xi[3], py = xi[4], pz = xi[5];
-    const float th2 = px * px + py * py + pz * pz, th = sqrtf(th2);
-    float A, B, Cc;
-    if (th < 1e-4f) {
-        A = 1.f - th2 / 6.f;
-        B = 0.5f - th2 / 24.f;
-        Cc = 1.f / 6.f - th2 / 120.f;
-    } else {
-        A = sinf(th) / th;
-        B = (1.f - cosf(th)) / th2;
-        Cc = (th - sinf(th)) / (th2 * th);
-    }
-    const float K[9] = {0.f, -pz, py, pz, 0.f, -px, -py, px, 0.f};
-    float K2[9], Rd[9], V[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
-    for (int i = 0; i < 9; ++i) {
-        const float I = (i % 4 == 0) ? 1.f : 0.f;
-        Rd[i] = I + A * K[i] + B * K2[i];
-        V[i] = I + B * K[i] + Cc * K2[i];
-    }
-    float R[9], t[3], Rn[9], tn[3];
-    for (int i = 0; i < 9; ++i) R[i] = pose[i];
-    for (int i = 0; i < 3; ++i) t[i] = pose[9 + i];
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) Rn[3 * i + j] = Rd[3 * i] * R[j] + Rd[3 * i + 1] * R[3 + j] + Rd[3 * i + 2] * R[6 + j];
-        tn[i] = Rd[3 * i] * t[0] + Rd[3 * i + 1] * t[1] + Rd[3 * i + 2] * t[2] +
-                V[3 * i] * xi[0] + V[3 * i + 1] * xi[1] + V[3 * i + 2] * xi[2];
-    }
-    for (int i = 0; i < 9; ++i) pose[i] = Rn[i];
-    for (int i = 0; i < 3; ++i) pose[9 + i] = tn[i];
 }
 
 extern "C" gs_status gs_pose_update(float* pose, const double* pose_grad6, float* adam, float lr_trans, float lr_rot,

@@ -230,14 +230,71 @@ __device__ __forceinline__ float frag_alpha(const StagedSplat& s, const PixelMap
     return in ? alpha : -1.f;
 }
 
+// Forward outputs (gs_render_fwd) and, when trgb is given, the fused loss
+// (gs_render_fwd_loss).
+struct FwdOut {
+    float* rgb;
+    float* depth;
+    float* t;
+    uint32_t* last;
+    uint32_t* nb;
+    const float* trgb;  // NULL: no loss
+    const float* tdepth;
+    float* d_rgb;
+    float* d_depth;
+    double* loss;
+};
+
+// Writes sampled pixel (i, j)'s results; with the fused loss also its image
+// gradient (the formulas of k_loss_l1 on the same float values) and returns
+// its share of the loss.
+__device__ __forceinline__ float write_pixel(const gs_config& cfg, const Grid& g, const FwdOut& O, int i, int j,
+                                             float C0, float C1, float C2, float D, float T, uint32_t last,
+                                             uint32_t nb) {
+    const size_t P = (size_t)g.Ws * g.Hs;
+    const size_t pix = (size_t)j * g.Ws + i;
+    const float c[3] = {C0 + T * cfg.bg[0], C1 + T * cfg.bg[1], C2 + T * cfg.bg[2]};
+    O.rgb[pix] = c[0];
+    O.rgb[P + pix] = c[1];
+    O.rgb[2 * P + pix] = c[2];
+    O.depth[pix] = D;
+    O.t[pix] = T;
+    O.last[pix] = last;
+    if (O.nb) O.nb[pix] = nb;
+    if (!O.trgb) return 0.f;
+    const float inv3 = 1.f / (3.f * (float)P), inv1 = 1.f / (float)P;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float r = c[k] - O.trgb[k * P + pix];
+        acc += cfg.w_rgb * fabsf(r) * inv3;
+        O.d_rgb[k * P + pix] = cfg.w_rgb * (r > 0.f ? inv3 : (r < 0.f ? -inv3 : 0.f));
+    }
+    const float td = O.tdepth[pix];
+    float gd = 0.f;
+    if (td != 0.f) {
+        const float r = D - td;
+        acc += cfg.w_depth * fabsf(r) * inv1;
+        gd = cfg.w_depth * (r > 0.f ? inv1 : (r < 0.f ? -inv1 : 0.f));
+    }
+    O.d_depth[pix] = gd;
+    return acc;
+}
+
+// Warp sum of the pixels' loss shares, one float64 atomic per warp (all 32
+// lanes call it).
+__device__ __forceinline__ void add_loss(const FwdOut& O, float part) {
+    if (!O.trgb) return;
+    part = warp_sum(part);
+    if ((threadIdx.x & 31) == 0 && part != 0.f) atomicAdd(O.loss, (double)part);
+}
+
 // Forward compositing of group G's tile, pixel-parallel (sp_all: the CTA's
 // staging buffer, G.B entries per group).
 template <int DT, int KST>
 __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
-                                       float* __restrict__ out_rgb, float* __restrict__ out_depth,
-                                       float* __restrict__ out_t, uint32_t* __restrict__ out_last,
-                                       uint32_t* __restrict__ out_nb, const Group& G, StagedSplat* sp_all) {
+                                       const FwdOut& O, const Group& G, StagedSplat* sp_all) {
     StagedSplat* sp = sp_all + G.gi * G.B;
     const int tile = G.tile;
     const PixelMap m = map_pixel(g, tile, G.lt);
@@ -302,30 +359,19 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
         }
         group_sync(G);
     }
-    if (m.inside) {
-        const size_t P = (size_t)g.Ws * g.Hs;
-        const size_t pix = (size_t)m.j * g.Ws + m.i;
-        out_rgb[pix] = C0 + T * cfg.bg[0];
-        out_rgb[P + pix] = C1 + T * cfg.bg[1];
-        out_rgb[2 * P + pix] = C2 + T * cfg.bg[2];
-        out_depth[pix] = D;
-        out_t[pix] = T;
-        out_last[pix] = last;
-        if (out_nb) out_nb[pix] = nb;
-    }
+    float lpart = 0.f;
+    if (m.inside) lpart = write_pixel(cfg, g, O, m.i, m.j, C0, C1, C2, D, T, last, nb);
+    add_loss(O, lpart);
 }
 
 template <int DT, int KST>
 __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
     k_render_fwd(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
-                 const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
-                 float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_t,
-                 uint32_t* __restrict__ out_last, uint32_t* __restrict__ out_nb, int B) {
+                 const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order, FwdOut O, int B) {
     extern __shared__ __align__(16) unsigned char r_smem[];
     const Group G = make_group(g, order, B, blockIdx.x);
     if (G.tile < 0) return;
-    fwd_pp<DT, KST>(cfg, g, splats, vals, ranges, out_rgb, out_depth, out_t, out_last, out_nb, G,
-                    reinterpret_cast<StagedSplat*>(r_smem));
+    fwd_pp<DT, KST>(cfg, g, splats, vals, ranges, O, G, reinterpret_cast<StagedSplat*>(r_smem));
 }
 
 // ---------------------------------------------------------------------------
@@ -502,7 +548,10 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
             for (int k = 0; k < NS; ++k) f[k] = 0.f;
             if (!fg.contrib) return;
             const float alpha = fg.alpha;
-            T = T / (1.f - alpha);
+            // fast division (at most 2 ulp for these operands: 1 - alpha in
+            // [0.01, 1], T in [t_eps, 1]); over the few hundred entries a
+            // pixel recovers the relative drift stays near 1e-5
+            T = __fdividef(T, 1.f - alpha);
             const float w = alpha * T;
             const float4 Cc = sp[e].c;
             const float dep = sp[e].b.z;
@@ -694,9 +743,7 @@ __device__ __forceinline__ void ep_pair(const Grid& g, int tile, int q0, int npi
 template <int DT, int W>
 __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
-                                       float* __restrict__ out_rgb, float* __restrict__ out_depth,
-                                       float* __restrict__ out_t, uint32_t* __restrict__ out_last,
-                                       uint32_t* __restrict__ out_nb, int tile, int q0, int npix, EpStage& S,
+                                       const FwdOut& O, int tile, int q0, int npix, EpStage& S,
                                        int (*cbuf_all)[64], uint32_t* s_h, uint8_t* perm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -704,7 +751,7 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
     const int ppw = (npix + W - 1) / W;
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     // out_last still holds the previous iteration's positions (read before any write)
-    ep_pair<W>(g, tile, q0, npix, cfg.balance ? out_last : nullptr, s_h, perm);
+    ep_pair<W>(g, tile, q0, npix, cfg.balance ? O.last : nullptr, s_h, perm);
     // lane j < ppw holds the state of the warp's pixel j
     int mi, mj;
     const bool mine = lane < ppw && warp * ppw + lane < npix && ep_pixel(g, tile, q0 + perm[warp * ppw + lane], mi, mj);
@@ -808,32 +855,21 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
         }
         __syncthreads();
     }
-    if (mine) {
-        const size_t P = (size_t)g.Ws * g.Hs;
-        const size_t pix = (size_t)mj * g.Ws + mi;
-        out_rgb[pix] = C0 + T * cfg.bg[0];
-        out_rgb[P + pix] = C1 + T * cfg.bg[1];
-        out_rgb[2 * P + pix] = C2 + T * cfg.bg[2];
-        out_depth[pix] = D;
-        out_t[pix] = T;
-        out_last[pix] = last;
-        if (out_nb) out_nb[pix] = nb;
-    }
+    float lpart = 0.f;
+    if (mine) lpart = write_pixel(cfg, g, O, mi, mj, C0, C1, C2, D, T, last, nb);
+    add_loss(O, lpart);
 }
 
 template <int DT, int W>
 __global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
     k_render_fwd_ep(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
-                    const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
-                    float* __restrict__ out_rgb, float* __restrict__ out_depth, float* __restrict__ out_t,
-                    uint32_t* __restrict__ out_last, uint32_t* __restrict__ out_nb) {
+                    const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order, FwdOut O) {
     __shared__ EpStage S;
     __shared__ int cbuf_all[W][64];
     __shared__ uint32_t s_h[64];
     __shared__ uint8_t perm[64];
     const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
-    fwd_ep<DT, W>(cfg, g, splats, vals, ranges, out_rgb, out_depth, out_t, out_last, out_nb, tile, 0,
-                  g.tw * g.th, S, cbuf_all, s_h, perm);
+    fwd_ep<DT, W>(cfg, g, splats, vals, ranges, O, tile, 0, g.tw * g.th, S, cbuf_all, s_h, perm);
 }
 
 // Fields merged per entry: GS_TRACK du dv dA dB dC dd, GS_MAP du dv dA dB dC
@@ -953,7 +989,7 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
                     const float y = __shfl_up_sync(0xffffffffu, Q, o);
                     if (lane >= o) Q *= y;
                 }
-                const float Tb = Tj / Q;  // T before this entry (Eq. 5)
+                const float Tb = __fdividef(Tj, Q);  // T before this entry (Eq. 5)
                 const float w = valid ? alpha * Tb : 0.f;
                 const float cg = Cc.x * q0 + Cc.y * q1 + Cc.z * q2 + Bv.z * qd;
                 const float wcg = w * cg;
@@ -965,7 +1001,7 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
                 }
                 if (valid) {
                     const float behind = sj + (Sin - wcg);
-                    const float dLda = Tb * cg - behind / f;
+                    const float dLda = Tb * cg - __fdividef(behind, f);
                     float ga[NF];
 #pragma unroll
                     for (int q = 0; q < NF; ++q) ga[q] = 0.f;
@@ -991,7 +1027,7 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
                         if (ga[q] != 0.f) atomicAdd(&acc[q][e], ga[q]);
                 }
                 // state in front of these entries
-                Tj = __shfl_sync(0xffffffffu, Tj / Q, 31);
+                Tj = __shfl_sync(0xffffffffu, __fdividef(Tj, Q), 31);
                 sj = sj + __shfl_sync(0xffffffffu, Sin, 31);
             };
             int cnt = 0;
@@ -1073,16 +1109,13 @@ static gs_status smem_once(const void* fn, int id, int bytes) {
 // one CTA of 8 or 16 warps per tile; otherwise pixel-parallel groups.
 template <int DT>
 static gs_status launch_fwd(const gs_config& cfg, const Grid& g, const void* splats, const uint32_t* vals,
-                            const uint32_t* ranges, const uint32_t* order, float* rgb, float* depth,
-                            float* t_final, uint32_t* last_idx, uint32_t* n_blended, cudaStream_t st) {
+                            const uint32_t* ranges, const uint32_t* order, const FwdOut& O, cudaStream_t st) {
     const int ntiles = g.TX * g.TY;
     if (g.tw * g.th <= 64) {
         if (g.tw * g.th <= 32)
-            k_render_fwd_ep<DT, 8><<<ntiles, 8 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, rgb, depth,
-                                                               t_final, last_idx, n_blended);
+            k_render_fwd_ep<DT, 8><<<ntiles, 8 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, O);
         else
-            k_render_fwd_ep<DT, 16><<<ntiles, 16 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, rgb, depth,
-                                                                 t_final, last_idx, n_blended);
+            k_render_fwd_ep<DT, 16><<<ntiles, 16 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, O);
         return check_launch("k_render_fwd_ep");
     }
     const int gpc = R_THREADS / tile_threads(g);
@@ -1092,14 +1125,20 @@ static gs_status launch_fwd(const gs_config& cfg, const Grid& g, const void* spl
     gs_status s;
     if (gpc == 1) {
         if ((s = smem_once((const void*)k_render_fwd<DT, 1>, 2 * DT, R_FWD_SMEM)) != GS_OK) return s;
-        k_render_fwd<DT, 1><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, rgb, depth, t_final,
-                                                         last_idx, n_blended, B);
+        k_render_fwd<DT, 1><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, O, B);
     } else {
         if ((s = smem_once((const void*)k_render_fwd<DT, 4>, 2 * DT + 1, R_FWD_SMEM)) != GS_OK) return s;
-        k_render_fwd<DT, 4><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, rgb, depth, t_final,
-                                                         last_idx, n_blended, B);
+        k_render_fwd<DT, 4><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, O, B);
     }
     return check_launch("k_render_fwd");
+}
+
+static gs_status dispatch_fwd(const gs_config& cfg, const Grid& g, int rec_dtype, const void* splats,
+                              const uint32_t* vals, const uint32_t* ranges, const uint32_t* order, const FwdOut& O,
+                              cudaStream_t st) {
+    if (rec_dtype == GS_F32) return launch_fwd<GS_F32>(cfg, g, splats, vals, ranges, order, O, st);
+    if (rec_dtype == GS_BF16) return launch_fwd<GS_BF16>(cfg, g, splats, vals, ranges, order, O, st);
+    return launch_fwd<GS_F16>(cfg, g, splats, vals, ranges, order, O, st);
 }
 
 template <int DT, int MD>
@@ -1159,16 +1198,27 @@ extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, i
     if ((s = render_checks(cfg, cam, rec_dtype, splats, n)) != GS_OK) return s;
     if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
         return set_error(GS_ERR_INVALID_ARG, "an image or range pointer is NULL");
-    const Grid g = make_grid(*cam);
+    const FwdOut O = {rgb, depth, t_final, last_idx, n_blended, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return dispatch_fwd(*cfg, make_grid(*cam), rec_dtype, splats, vals, tile_ranges, tile_order, O,
+                        (cudaStream_t)stream);
+}
+
+extern "C" gs_status gs_render_fwd_loss(const gs_config* cfg, const gs_camera* cam, int rec_dtype,
+                                        const void* splats, int64_t n, const uint32_t* vals,
+                                        const uint32_t* tile_ranges, const uint32_t* tile_order, float* rgb,
+                                        float* depth, float* t_final, uint32_t* last_idx, uint32_t* n_blended,
+                                        const float* target_rgb, const float* target_depth, float* d_rgb,
+                                        float* d_depth, double* loss_out, gs_stream stream) {
+    gs_status s;
+    if ((s = render_checks(cfg, cam, rec_dtype, splats, n)) != GS_OK) return s;
+    if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
+        return set_error(GS_ERR_INVALID_ARG, "an image or range pointer is NULL");
+    if (!target_rgb || !target_depth || !d_rgb || !d_depth || !loss_out)
+        return set_error(GS_ERR_INVALID_ARG, "a target, gradient or loss pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    if (rec_dtype == GS_F32)
-        return launch_fwd<GS_F32>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx,
-                                  n_blended, st);
-    if (rec_dtype == GS_BF16)
-        return launch_fwd<GS_BF16>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx,
-                                   n_blended, st);
-    return launch_fwd<GS_F16>(*cfg, g, splats, vals, tile_ranges, tile_order, rgb, depth, t_final, last_idx,
-                              n_blended, st);
+    if (cudaMemsetAsync(loss_out, 0, sizeof(double), st) != cudaSuccess) return set_error(GS_ERR_CUDA, "memset loss");
+    const FwdOut O = {rgb, depth, t_final, last_idx, n_blended, target_rgb, target_depth, d_rgb, d_depth, loss_out};
+    return dispatch_fwd(*cfg, make_grid(*cam), rec_dtype, splats, vals, tile_ranges, tile_order, O, st);
 }
 
 extern "C" gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, const float* rgb, const float* depth,

@@ -47,6 +47,11 @@ class gs_config(C.Structure):
                 ("w_rgb", C.c_float), ("w_depth", C.c_float), ("balance", C.c_int32)]
 
 
+class gs_pose_step(C.Structure):
+    _fields_ = [("pose", C.c_void_p), ("adam", C.c_void_p), ("lr_trans", C.c_float), ("lr_rot", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 class gs_gaussians(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logit", C.c_void_p), ("rgb", C.c_void_p), ("mask", C.c_void_p),
@@ -67,10 +72,13 @@ _SIGS = {
     "gs_bin_sort": ([_P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_bin_count": ([_P, C.c_int, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
     "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_render_fwd_loss": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+                           C.c_int),
     "gs_loss_l1": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_render_bwd": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P,
                        _P, _P, _P], C.c_int),
     "gs_project_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_project_bwd_step": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_project_bwd_noalloc": ([_P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_prune": ([_P, _P, C.c_int64, _P, C.c_int, _P, C.c_float, C.c_int64, _P, _P, _P, _P, _P],
                  C.c_int),
@@ -269,6 +277,28 @@ def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None,
     return out
 
 
+def gs_render_fwd_loss(cfg, cam, splats, n, vals, ranges, target_rgb, target_depth, rec_dtype=GS_F32, out=None,
+                       dimg=None, order=None, stream=None):
+    """Forward compositing with the loss fused (gs_render_fwd_loss): returns
+    (out, dimg) like gs_render_fwd and gs_loss_l1."""
+    Ws, Hs, _, _ = grid(cam)
+    dev = splats.device
+    if out is None:
+        out = {"rgb": torch.empty((3, Hs, Ws), device=dev), "depth": torch.empty((Hs, Ws), device=dev),
+               "t_final": torch.empty((Hs, Ws), device=dev),
+               "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=dev),
+               "n_blended": torch.empty((Hs, Ws), dtype=torch.int32, device=dev)}
+    if dimg is None:
+        dimg = {"d_rgb": torch.empty((3, Hs, Ws), device=dev), "d_depth": torch.empty((Hs, Ws), device=dev),
+                "loss": torch.zeros(1, dtype=torch.float64, device=dev)}
+    _check(lib().gs_render_fwd_loss(C.byref(cfg), C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(vals),
+                                    _ptr(ranges), _ptr(order), _ptr(out["rgb"]), _ptr(out["depth"]),
+                                    _ptr(out["t_final"]), _ptr(out["last_idx"]), _ptr(out.get("n_blended")),
+                                    _ptr(target_rgb), _ptr(target_depth), _ptr(dimg["d_rgb"]), _ptr(dimg["d_depth"]),
+                                    _ptr(dimg["loss"]), _stream(stream)), "gs_render_fwd_loss")
+    return out, dimg
+
+
 def gs_loss_l1(cfg, cam, rgb, depth, target_rgb, target_depth, out=None, stream=None):
     if out is None:
         out = {"d_rgb": torch.empty_like(rgb), "d_depth": torch.empty_like(depth),
@@ -320,6 +350,27 @@ def gs_project_bwd(cfg, cam, g, grad2d, grads=None, pose=None, score=None, ws=No
     _check(lib().gs_project_bwd(C.byref(cfg), C.byref(cam), C.byref(gs_g), _ptr(grad2d),
                                 C.byref(gr) if gr is not None else None, _ptr(pose), _ptr(score), _ptr(ws),
                                 C.byref(nb), _stream(stream)), "gs_project_bwd")
+
+
+def pose_step(pose, adam, lr_trans=1e-3, lr_rot=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """gs_pose_step over device tensors pose (float32 [12]) and adam (float32 [13])."""
+    return gs_pose_step(_ptr(pose).value, _ptr(adam).value, float(lr_trans), float(lr_rot), float(beta1),
+                        float(beta2), float(eps))
+
+
+def gs_project_bwd_step(cfg, cam, g, grad2d, pose, step, grads=None, score=None, ws=None, stream=None):
+    """gs_project_bwd with the pose step fused into its last block (pose:
+    float64 [6] output of the reduced pose gradient; step: gs_pose_step)."""
+    need = gs_project_bwd_workspace(cfg, cam, g)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, grad2d.device)
+    gs_g = gaussians(g)
+    gr = grads_struct(grads) if grads is not None else None
+    nb = C.c_size_t(ws.numel())
+    _check(lib().gs_project_bwd_step(C.byref(cfg), C.byref(cam), C.byref(gs_g), _ptr(grad2d),
+                                     C.byref(gr) if gr is not None else None, _ptr(pose), _ptr(score),
+                                     C.byref(step) if step is not None else None, _ptr(ws), C.byref(nb),
+                                     _stream(stream)), "gs_project_bwd_step")
 
 
 def gs_project_bwd_noalloc(cfg, cam, g, grad2d, grads=None, pose=None, score=None, stream=None):

@@ -106,6 +106,32 @@ class Rasterizer:
         self.backward(g, cam_s, self.dimg["d_rgb"], self.dimg["d_depth"], mode, grads)
         return self.pose
 
+    def track_step(self, g, cam, target_rgb, target_depth, pose, pose_adam, lr_trans=1e-3, lr_rot=1e-3,
+                   rebin=True):
+        """One fused tracking iteration: projection, binning + sort, forward
+        compositing with the loss (gs_render_fwd_loss), backward compositing,
+        then backward projection with the pose step fused into its last block
+        (gs_project_bwd_step).  `cam` must carry the device pose (`pose`,
+        float32 [12]) so the next iteration sees the updated pose; pose_adam
+        is the float32 [13] Adam state.  Seven kernel launches (plus memsets)
+        instead of the nine of step() + gs_pose_update."""
+        cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam, pose=pose)
+        self.set_grid(cam_s)
+        gs.gs_project(self.cfg, cam_s, g, self.rec_dtype, self.splats)
+        if rebin:
+            gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
+                           keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges,
+                           order=self.order)
+        gs.gs_render_fwd_loss(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, target_rgb,
+                              target_depth, self.rec_dtype, out=self.img, dimg=self.dimg, order=self.order)
+        gs.gs_render_bwd(self.cfg, cam_s, g, self.splats, self.vals, self.ranges, self.img["t_final"],
+                         self.img["last_idx"], self.dimg["d_rgb"], self.dimg["d_depth"], gs.GS_TRACK,
+                         self.rec_dtype, grad2d=self.grad2d, order=self.order)
+        gs.gs_project_bwd_step(self.cfg, cam_s, g, self.grad2d, self.pose,
+                               gs.pose_step(pose, pose_adam, lr_trans, lr_rot), score=self.score,
+                               ws=self._bwd_ws(cam_s, g))
+        return self.pose
+
     def check(self):
         """Synchronises and raises if a device condition was raised (key
         capacity exceeded, a bounded wait that gave up)."""

@@ -123,8 +123,7 @@ class Session:
         r, (trgb, tdep) = self._rast(sx, sy)
         cam = gs.camera(dict(self.cams[0], sx=sx, sy=sy), pose=self.pose)
         for _ in range(self.spec.iters):
-            r.step(self.g, cam, trgb, tdep, gs.GS_TRACK)
-            gs.gs_pose_update(self.pose, r.pose, self.pose_adam, self.lr_pose, self.lr_pose)
+            r.track_step(self.g, cam, trgb, tdep, self.pose, self.pose_adam, self.lr_pose, self.lr_pose)
         if keyframe:
             r.forward(self.g, cam)
             r.loss_grad(cam, trgb, tdep)

@@ -1,0 +1,121 @@
+"""The fused forms of the tracking iteration against the separate calls:
+forward + loss in one launch (gs_render_fwd_loss) and the backward
+projection with the pose step in its last block (gs_project_bwd_step)."""
+import numpy as np
+import pytest
+import torch
+
+from synth import scenes as S
+from tests.gpu_helpers import dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_06644_gb300 import build
+    build.build()
+    from paper_2510_06644_gb300 import gs
+    return gs
+
+
+def scene_and_cams(seed=40):
+    g = S.surface_scene(40000, seed=seed)
+    true_cam = S.camera(320, 240, 260.0)
+    start = S.perturbed_pose(true_cam, seed=seed + 1, trans=0.02, rot_deg=1.0)
+    return g, true_cam, start
+
+
+@pytest.mark.parametrize("sx,sy,rec", [(1, 1, "f32"), (2, 2, "f32"), (4, 4, "bf16"), (1, 2, "f16")])
+def test_forward_with_fused_loss_equals_separate_calls(G, sx, sy, rec):
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    dt = {"f32": G.GS_F32, "bf16": G.GS_BF16, "f16": G.GS_F16}[rec]
+    g, true_cam, start = scene_and_cams()
+    gd = dev(g)
+    r = Rasterizer(40000, dict(start, sx=sx, sy=sy), rec_dtype=dt, capacity=400000)
+    tgt = Rasterizer(40000, dict(true_cam, sx=sx, sy=sy), rec_dtype=dt, capacity=400000)
+    img_t = tgt.forward(gd, dict(true_cam, sx=sx, sy=sy))
+    trgb, tdep = img_t["rgb"].clone(), img_t["depth"].clone()
+    tdep[::7, ::5] = 0.0  # invalid depths take no depth term
+    cs = G.camera(dict(start, sx=sx, sy=sy))
+    r.forward(gd, cs)
+    sep = {k: v.clone() for k, v in r.img.items()}
+    d = G.gs_loss_l1(r.cfg, cs, r.img["rgb"], r.img["depth"], trgb, tdep)
+    out, dimg = G.gs_render_fwd_loss(r.cfg, cs, r.splats, r.n, r.vals, r.ranges, trgb, tdep, dt, order=r.order)
+    torch.cuda.synchronize()
+    for k in sep:
+        assert torch.equal(out[k], sep[k]), k
+    assert torch.equal(dimg["d_rgb"], d["d_rgb"])
+    assert torch.equal(dimg["d_depth"], d["d_depth"])
+    a, b = float(dimg["loss"].item()), float(d["loss"].item())
+    assert a > 0 and abs(a - b) <= 1e-6 * abs(b)
+    r.check()
+
+
+def test_backward_projection_with_fused_pose_step_equals_separate_calls(G):
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    g, true_cam, start = scene_and_cams(seed=50)
+    gd = dev(g)
+    r = Rasterizer(40000, start, capacity=400000)
+    trgb = r.forward(gd, true_cam)["rgb"].clone()
+    tdep = r.img["depth"].clone()
+    pose = G.pose_tensor(start)
+    cs = G.camera(start, pose=pose)
+    r.forward(gd, cs)
+    r.loss_grad(cs, trgb, tdep)
+    r.backward(gd, cs, r.dimg["d_rgb"], r.dimg["d_depth"], want_pose=False, want_score=False)
+    grad2d = r.grad2d.clone()  # one backward, shared by both routes
+    res = []
+    for fused in (False, True):
+        p = pose.clone()
+        adam = torch.zeros(13, device="cuda")
+        pg = torch.zeros(6, dtype=torch.float64, device="cuda")
+        c = G.camera(start, pose=p)
+        for _ in range(3):
+            if fused:
+                G.gs_project_bwd_step(r.cfg, c, gd, grad2d, pg, G.pose_step(p, adam, 1e-3, 2e-3))
+            else:
+                G.gs_project_bwd(r.cfg, c, gd, grad2d, pose=pg)
+                G.gs_pose_update(p, pg, adam, 1e-3, 2e-3)
+        torch.cuda.synchronize()
+        res.append((p.cpu().numpy(), adam.cpu().numpy(), pg.cpu().numpy()))
+    (pa, aa, ga), (pb, ab, gb) = res
+    assert np.abs(pb - pose.cpu().numpy()).max() > 1e-5  # the pose moved
+    assert np.array_equal(ga, gb)
+    assert np.array_equal(aa, ab)
+    assert np.array_equal(pa, pb)
+    r.check()
+
+
+@pytest.mark.parametrize("sx,sy", [(1, 1), (2, 2)])
+def test_fused_tracking_iterations_follow_the_separate_ones(G, sx, sy):
+    """Ten iterations of Rasterizer.track_step against step() +
+    gs_pose_update: same pose trajectory (to the nondeterministic order of
+    the backward's float atomics)."""
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    g, true_cam, start = scene_and_cams(seed=60)
+    gd = dev(g)
+    tgt = Rasterizer(40000, dict(true_cam, sx=sx, sy=sy), capacity=400000)
+    img = tgt.forward(gd, dict(true_cam, sx=sx, sy=sy))
+    trgb, tdep = img["rgb"].clone(), img["depth"].clone()
+    traj = []
+    for fused in (False, True):
+        r = Rasterizer(40000, dict(start, sx=sx, sy=sy), capacity=400000)
+        pose = G.pose_tensor(start)
+        adam = torch.zeros(13, device="cuda")
+        cs = G.camera(dict(start, sx=sx, sy=sy), pose=pose)
+        poses = []
+        for _ in range(10):
+            if fused:
+                r.track_step(gd, cs, trgb, tdep, pose, adam)
+            else:
+                r.step(gd, cs, trgb, tdep, G.GS_TRACK)
+                G.gs_pose_update(pose, r.pose, adam)
+            poses.append(pose.cpu().numpy().copy())
+        r.check()
+        traj.append(np.array(poses))
+    a, b = traj
+    assert np.abs(a[-1] - a[0]).max() > 1e-4
+    assert np.abs(a - b).max() <= 1e-5, np.abs(a - b).max()
