@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--skip-cpu-baseline", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="only run warmup + steps tracking iterations eagerly (for ncu launch lists), print nothing")
+    p.add_argument("--stride", type=int, nargs=2, default=(1, 1), metavar=("SX", "SY"),
+                   help="with --profile: run the tracking iterations on a downsampled frame (Sec. 4.2 strides)")
     p.add_argument("--serving", action="store_true", help="run only the serving comparison and print its line")
     p.add_argument("--skip-serving", action="store_true")
     p.add_argument("--serving-frames", type=int, default=6)
@@ -382,6 +384,14 @@ def run_ours(args):
     adam = torch.zeros(13, device="cuda")
     cam_s = gs.camera(start_cam, pose=pose)
     lr_t, lr_r = 1e-3, 1e-3
+
+    if args.profile and tuple(args.stride) != (1, 1):
+        sx, sy = args.stride
+        cam_d = dict(start_cam, sx=sx, sy=sy)
+        rast = Rasterizer(n, cam_d, capacity=int(n_keys0 * 1.5) + 4096)
+        cam_s = gs.camera(cam_d, pose=pose)
+        trgb = trgb[:, ::sy, ::sx].contiguous()
+        tdep = tdep[::sy, ::sx].contiguous()
 
     def step():
         rast.track_step(gd, cam_s, trgb, tdep, pose, adam, lr_t, lr_r)
