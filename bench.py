@@ -212,6 +212,13 @@ def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pos
     base_f, base_b = time_pair(rast, gd, cam_s)
     prune = {}
     score = rast.score.clone()
+    # Obs. 3: how concentrated the Eq. 7 scores are (fraction of the Gaussians,
+    # highest scores first, that holds 50 / 90 % of the total)
+    sc = (score[:, 0].double() + 0.8 * score[:, 1].double()).sort(descending=True).values
+    cum = sc.cumsum(0) / sc.sum().clamp_min(1e-300)
+    out["score_concentration"] = {
+        f"frac_for_{p}pct": float((cum < p / 100).sum().item() + 1) / sc.numel() for p in (50, 90)}
+    out["score_concentration"]["frac_nonzero"] = float((sc > 0).sum().item()) / sc.numel()
     for frac in (0.1, 0.3, 0.5):
         mask = torch.zeros(rast.n, dtype=torch.uint8, device="cuda")
         gs.gs_prune(gs.default_config(prune_frac=frac), score, mask, 0, 5)
