@@ -297,8 +297,9 @@ gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gau
  *   dL/drho = sum_k dL/dp_k,
  *   dL/dphi = sum_k p_k x dL/dp_k + (<G_k, [e_i]x S_k - S_k [e_i]x>)_i,
  *   with p_k the camera point, S_k its camera-frame covariance and G_k =
- *   dL/dS_k.  Per-Gaussian terms in float32, per-block sums in float64,
- *   blocks combined with compensated (Neumaier) float64 summation.
+ *   dL/dS_k.  Per-Gaussian terms in float32, warp sums in float32, block
+ *   and cross-block sums as float32 pairs (hi + lo, error-free two-sums:
+ *   about 48 significant bits) in a fixed order, returned as float64.
  * score_terms [n][2] float: (||dL/dmu||_2, ||dL/dSigma||_F) for Eq. 7.
  * Any of the three outputs may be NULL. */
 gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
@@ -402,7 +403,7 @@ typedef struct {
 } gs_pose_step;
 
 /* gs_project_bwd with the pose step fused into its last block: the block that
- * completes the compensated float64 pose-gradient reduction (pose_grad6,
+ * completes the pose-gradient reduction (pose_grad6,
  * required here) applies gs_pose_update's Adam step and SE(3) update with
  * `step` (same arithmetic, one launch fewer per tracking iteration).  Every
  * block reads the pose before the last block updates it, so a camera whose

@@ -149,13 +149,22 @@ __global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, g
 
 #define PB_THREADS 256
 
-// Neumaier's compensated sum of (s, c) pairs held by the lanes of a warp,
-// merged in a fixed butterfly order.
-__device__ __forceinline__ void neumaier_add(double& s, double& c, double v) {
-    const double t = s + v;
-    if (fabs(s) >= fabs(v)) c += (s - t) + v;
-    else c += (v - t) + s;
-    s = t;
+// Pose-gradient sums carry a float32 pair (hi, lo) with hi + lo the value
+// (about 48 significant bits): additions are an error-free two-sum of the
+// high parts (Knuth) plus the low parts, renormalised with a fast two-sum
+// (Dekker).  All in float32 (GB300's float64 rate is 1/64 of it); fixed
+// operation order, so the reduction is deterministic.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bp = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b.hi, bp));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, t);
+    return DF{hi, __fsub_rn(t, __fsub_rn(hi, s))};
 }
 
 // ---------------------------------------------------------------------------
@@ -215,10 +224,11 @@ __global__ void k_pose_update(float* __restrict__ pose, const double* __restrict
     pose_adam_exp(pose, grad, adam, lr_t, lr_r, b1, b2, eps);
 }
 
-// Final combination of the per-block float64 pose partials by the last block
-// to finish (no spin: the block that takes the last ticket sees every other
-// block's partial, published before its ticket).  Warp w < 6 sums component w.
-__device__ void pose_final_last_block(const double* __restrict__ part, int nblk, double* __restrict__ out,
+// Final combination of the per-block pose partials (float32 pairs) by the
+// last block to finish (no spin: the block that takes the last ticket sees
+// every other block's partial, published before its ticket).  Warp w < 6
+// sums component w: lane-strided, then a fixed butterfly.
+__device__ void pose_final_last_block(const float2* __restrict__ part, int nblk, double* __restrict__ out,
                                       unsigned int* __restrict__ ticket, const gs_pose_step& step) {
     __shared__ bool s_last;
     __threadfence();
@@ -228,16 +238,17 @@ __device__ void pose_final_last_block(const double* __restrict__ part, int nblk,
     __threadfence();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (w < 6) {
-        double s = 0.0, c = 0.0;
-        for (int b = lane; b < nblk; b += 32) neumaier_add(s, c, __ldcg(part + (size_t)b * 6 + w));
+        DF s{0.f, 0.f};
+        for (int b = lane; b < nblk; b += 32) {
+            const float2 v = __ldcg(part + (size_t)b * 6 + w);
+            s = df_add(s, DF{v.x, v.y});
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
-            const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
-            c += c2;
-            neumaier_add(s, c, s2);
+            const DF t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+            s = (lane & o) ? df_add(t, s) : df_add(s, t);  // the same operand order on both partners
         }
-        if (lane == 0) out[w] = s + c;
+        if (lane == 0) out[w] = (double)s.hi + (double)s.lo;
     }
     if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
     if (step.pose) {  // the fused pose step (every block has read the pose by now)
@@ -251,7 +262,7 @@ template <bool WANT_GRADS, bool WANT_POSE, bool WANT_SCORE>
 __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_config cfg,
                                                             gs_gaussians g, const float* __restrict__ grad2d,
                                                             gs_grads grads, float* __restrict__ score,
-                                                            double* __restrict__ pose_part,
+                                                            float2* __restrict__ pose_part,
                                                             double* __restrict__ pose_out,
                                                             unsigned int* __restrict__ ticket, gs_pose_step step) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -401,19 +412,19 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_co
         }
     }
     if (WANT_POSE) {
-        // warp sums in float32, then the 8 warp sums of the block in float64
-        __shared__ double ws[PB_THREADS / 32][6];
+        // warp sums in float32, then the 8 warp sums of the block as a pair
+        __shared__ float ws[PB_THREADS / 32][6];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             float v = warp_sum(pose[i]);
-            if (lane == 0) ws[wid][i] = (double)v;
+            if (lane == 0) ws[wid][i] = v;
         }
         __syncthreads();
         if (threadIdx.x < 6) {
-            double s = 0.0;
-            for (int w = 0; w < PB_THREADS / 32; ++w) s += ws[w][threadIdx.x];
-            pose_part[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+            DF s{0.f, 0.f};
+            for (int w = 0; w < PB_THREADS / 32; ++w) s = df_add(s, DF{ws[w][threadIdx.x], 0.f});
+            pose_part[(size_t)blockIdx.x * 6 + threadIdx.x] = make_float2(s.hi, s.lo);
         }
         pose_final_last_block(pose_part, (int)gridDim.x, pose_out, ticket, step);
     }
@@ -508,7 +519,7 @@ extern "C" gs_status gs_project_bwd_step(const gs_config* cfg, const gs_camera* 
     if (!grad2d) return set_error(GS_ERR_INVALID_ARG, "grad2d is NULL");
     gs_grads gg = grads ? *grads : gs_grads{nullptr, nullptr, nullptr, nullptr, nullptr};
     const unsigned nblk = (unsigned)((g->n + PB_THREADS - 1) / PB_THREADS);
-    double* part = (double*)workspace;
+    float2* part = (float2*)workspace;
     unsigned int* ticket = (unsigned int*)((char*)workspace + need - 256);
     if (want_pose && cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset ticket");
