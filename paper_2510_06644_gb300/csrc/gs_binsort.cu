@@ -382,7 +382,11 @@ __device__ __forceinline__ void merge_rounds(u64 (&v)[KPT], u64* buf, int t, int
 // through buf), padding with ~0.
 template <int KPT>
 __device__ __forceinline__ void load_blocked(const u64* key, int n, u64 (&v)[KPT], u64* buf, int t, int nthr) {
-    for (int x = t; x < nthr * KPT; x += nthr) buf[pad16(x)] = x < n ? key[x] : ~0ull;
+    // all KPT global loads are issued before the first shared store
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) v[r] = t + r * nthr < n ? __ldcg(key + t + r * nthr) : ~0ull;
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) buf[pad16(t + r * nthr)] = v[r];
     if (nthr == 32) __syncwarp(); else named_bar(1, nthr);
 #pragma unroll
     for (int k = 0; k < KPT; ++k) v[k] = buf[pad16(t * KPT + k)];
