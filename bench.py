@@ -522,9 +522,9 @@ def run_ours(args):
            "h2d_bytes_per_step": trgb.numel() * 4 + tdep.numel() * 4, "d2h_bytes_per_step": 7 * 8}
 
     # kernels of one fused tracking iteration: k_project; k_tile_hist,
-    # k_col_scan, k_tile_scan, k_tile_order, k_tile_scatter_rows, k_tile_sort;
+    # k_col_scan_tail (+ tile scan + order), k_tile_scatter_rows, k_tile_sort;
     # k_render_fwd (+ loss); k_render_bwd; k_project_bwd (+ pose step)
-    launches_per_step = 1 + 6 + 1 + 1 + 1
+    launches_per_step = 1 + 4 + 1 + 1 + 1
     line = {
         "metric": METRIC, "value": iters_s, "unit": "iters/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",

@@ -13,6 +13,8 @@
 //   k_tile_scan     one CTA: exclusive scan of the tile counts -> bucket
 //                   starts, tile ranges, key count, capacity check
 //   k_tile_order    one CTA: heavy-first permutation of the tiles (stable)
+//                   (with the per-CTA rows, the column scan's last CTA runs
+//                   both: k_col_scan_tail)
 //   k_tile_scatter  each pair takes a slot of its tile's bucket and writes
 //                   the 64-bit remainder key depth_bits << 32 | id there (a
 //                   CTA's slots start at its row offset and are dealt out
@@ -89,8 +91,8 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_hist(gs_camera cam, const 
 // Column scan of the per-CTA rows: CTA b takes 32 tiles; its 32 warps split
 // the rows into 32 consecutive ranges, sum them, scan the 32 partial sums in
 // shared memory and write each row's exclusive prefix in place.
-__global__ void __launch_bounds__(1024) k_col_scan(uint32_t* __restrict__ hist, int nrows, int ntiles,
-                                                   uint32_t* __restrict__ total) {
+__device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int nrows, int ntiles,
+                                              uint32_t* __restrict__ total) {
     __shared__ uint32_t part[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int t = blockIdx.x * 32 + tx;
@@ -119,6 +121,11 @@ __global__ void __launch_bounds__(1024) k_col_scan(uint32_t* __restrict__ hist, 
             *p = run;
             run += v;
         }
+}
+
+__global__ void __launch_bounds__(1024) k_col_scan(uint32_t* __restrict__ hist, int nrows, int ntiles,
+                                                   uint32_t* __restrict__ total) {
+    col_scan_body(hist, nrows, ntiles, total);
 }
 
 template <int DT>
@@ -155,15 +162,15 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rows(gs_camera cam
 
 // Exclusive scan of the tile counts.  start[t] = min(bucket start, cap);
 // ranges (if not NULL) = bucket clipped to the capacity; *n_keys = total.
-__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ count, int ntiles, int64_t cap,
-                                                    uint32_t* __restrict__ start, uint32_t* __restrict__ ranges,
-                                                    int64_t* __restrict__ n_keys, unsigned int* __restrict__ status) {
+__device__ __forceinline__ void tile_scan_body(const uint32_t* __restrict__ count, int ntiles, int64_t cap,
+                                               uint32_t* __restrict__ start, uint32_t* __restrict__ ranges,
+                                               int64_t* __restrict__ n_keys, unsigned int* __restrict__ status) {
     __shared__ u64 s_warp[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     u64 carry = 0;
     for (int base = 0; base < ntiles; base += 1024) {
         const int t = base + threadIdx.x;
-        const u64 v = t < ntiles ? (u64)count[t] : 0ull;
+        const u64 v = t < ntiles ? (u64)__ldcg(count + t) : 0ull;
         u64 x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -202,6 +209,12 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
     }
 }
 
+__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ count, int ntiles, int64_t cap,
+                                                    uint32_t* __restrict__ start, uint32_t* __restrict__ ranges,
+                                                    int64_t* __restrict__ n_keys, unsigned int* __restrict__ status) {
+    tile_scan_body(count, ntiles, cap, start, ranges, n_keys, status);
+}
+
 // Heavy-first tile order: tiles grouped by the power of two bounding their
 // length from above, (2^k, 2^(k+1)] (empty tiles last), longest group
 // first, ascending tile index inside a group: a stable counting sort, so the
@@ -211,15 +224,15 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
 // SW_MAX keys, which are exactly the first n_big of the order.
 __device__ __forceinline__ int order_group(uint32_t len) { return len == 0 ? 33 : __clz(len - 1u); }
 
-__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ ranges, int ntiles,
-                                                     uint32_t* __restrict__ order, uint32_t* __restrict__ n_big) {
+__device__ __forceinline__ void tile_order_body(const uint32_t* __restrict__ ranges, int ntiles,
+                                                uint32_t* __restrict__ order, uint32_t* __restrict__ n_big) {
     __shared__ uint32_t cnt[34], cur[34];
     __shared__ uint32_t wcnt[32][34];  // per warp and group, within a 1024-tile chunk
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 34) cnt[threadIdx.x] = 0;
     __syncthreads();
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-        atomicAdd(&cnt[order_group(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+        atomicAdd(&cnt[order_group(__ldcg(ranges + 2 * t + 1) - __ldcg(ranges + 2 * t))], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict_
         for (int q = threadIdx.x; q < 32 * 34; q += blockDim.x) (&wcnt[0][0])[q] = 0;
         __syncthreads();
         const int t = base + (int)threadIdx.x;
-        const int grp = t < ntiles ? order_group(ranges[2 * t + 1] - ranges[2 * t]) : 34;
+        const int grp = t < ntiles ? order_group(__ldcg(ranges + 2 * t + 1) - __ldcg(ranges + 2 * t)) : 34;
         const unsigned same = __match_any_sync(0xffffffffu, grp);
         const unsigned rank = __popc(same & ((1u << lane) - 1u));
         if (grp < 34 && rank == 0) wcnt[warp][grp] = __popc(same);
@@ -251,6 +264,41 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict_
         if (grp < 34) order[wcnt[warp][grp] + rank] = (uint32_t)t;
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ ranges, int ntiles,
+                                                     uint32_t* __restrict__ order, uint32_t* __restrict__ n_big) {
+    tile_order_body(ranges, ntiles, order, n_big);
+}
+
+// The column scan followed, in the CTA that finishes last (ticket; every
+// other CTA's totals are published before its ticket), by the tile scan and
+// the heavy-first order: one launch instead of three.
+struct ScanTail {
+    unsigned int* ticket;  // zero on entry, zero again on exit
+    int64_t cap;
+    uint32_t* start;
+    uint32_t* ranges;
+    int64_t* n_keys;
+    unsigned int* status;
+    uint32_t* order;
+    uint32_t* n_big;
+};
+
+__global__ void __launch_bounds__(1024) k_col_scan_tail(uint32_t* __restrict__ hist, int nrows, int ntiles,
+                                                        uint32_t* __restrict__ total, ScanTail T) {
+    __shared__ bool s_last;
+    col_scan_body(hist, nrows, ntiles, total);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(T.ticket, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    tile_scan_body(total, ntiles, T.cap, T.start, T.ranges, T.n_keys, T.status);
+    __syncthreads();
+    tile_order_body(T.ranges, ntiles, T.order, T.n_big);
+    if (threadIdx.x == 0) *T.ticket = 0u;
 }
 
 template <int DT>
@@ -508,7 +556,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __rest
 // Workspace layout
 // ---------------------------------------------------------------------------
 struct BinLayout {
-    size_t off_count, off_fill, off_start, off_order, off_nbig, off_hist, off_tmp, zero_bytes, total;
+    size_t off_count, off_fill, off_ticket, off_start, off_order, off_nbig, off_hist, off_tmp, zero_bytes, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -528,6 +576,7 @@ static BinLayout bin_layout(int64_t n, int64_t cap, int ntiles) {
     const int64_t rows = n > 0 ? (n + per - 1) / per : 1;
     L.off_count = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
     L.off_fill = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
+    L.off_ticket = o; o = align256(o + sizeof(unsigned int));
     L.zero_bytes = o;
     L.off_start = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
     L.off_order = o; o = align256(o + sizeof(uint32_t) * (size_t)ntiles);
@@ -576,7 +625,9 @@ static gs_status set_agg_smem_attrs() {
 // Tile counts into `count`: per-CTA rows + column scan (rows kept in `hist`
 // for the scatter) when the grid is small enough, else direct atomics.
 static gs_status launch_count(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
-                              uint32_t* count, uint32_t* hist, cudaStream_t st) {
+                              uint32_t* count, uint32_t* hist, cudaStream_t st, const ScanTail* tail = nullptr,
+                              bool* fused = nullptr) {
+    if (fused) *fused = false;
     if (n == 0) return GS_OK;
     const Grid g = make_grid(*cam);
     const int ntiles = g.TX * g.TY;
@@ -589,6 +640,11 @@ static gs_status launch_count(const gs_camera* cam, int rec_dtype, const void* s
         else k_tile_hist<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, hist);
         gs_status s;
         if ((s = check_launch("k_tile_hist")) != GS_OK) return s;
+        if (tail) {
+            k_col_scan_tail<<<(unsigned)((ntiles + 31) / 32), 1024, 0, st>>>(hist, (int)nb, ntiles, count, *tail);
+            if (fused) *fused = true;
+            return check_launch("k_col_scan_tail");
+        }
         k_col_scan<<<(unsigned)((ntiles + 31) / 32), 1024, 0, st>>>(hist, (int)nb, ntiles, count);
         return check_launch("k_col_scan");
     }
@@ -649,16 +705,21 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
     u64* tmp = (u64*)(ws + L.off_tmp);
     uint32_t* hist = ntiles <= AGG_MAX_TILES ? (uint32_t*)(ws + L.off_hist) : nullptr;
     if (cudaMemsetAsync(ws, 0, L.zero_bytes, st) != cudaSuccess) return set_error(GS_ERR_CUDA, "memset bin state");
-    if ((s = launch_count(cam, rec_dtype, splats, n, count, hist, st)) != GS_OK) return s;
     unsigned int* err = status_ptr();
     if (!err) return set_error(GS_ERR_CUDA, "status word address");
-    k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, keys_capacity, start, tile_ranges, n_keys_out, err);
-    if ((s = check_launch("k_tile_scan")) != GS_OK) return s;
     // the heavy-first order drives the sort; it is returned when asked for
     uint32_t* order = tile_order ? tile_order : (uint32_t*)(ws + L.off_order);
     uint32_t* n_big = (uint32_t*)(ws + L.off_nbig);
-    k_tile_order<<<1, 1024, 0, st>>>(tile_ranges, ntiles, order, n_big);
-    if ((s = check_launch("k_tile_order")) != GS_OK) return s;
+    const ScanTail tail = {(unsigned int*)(ws + L.off_ticket), keys_capacity, start, tile_ranges, n_keys_out, err,
+                           order, n_big};
+    bool fused = false;
+    if ((s = launch_count(cam, rec_dtype, splats, n, count, hist, st, &tail, &fused)) != GS_OK) return s;
+    if (!fused) {
+        k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, keys_capacity, start, tile_ranges, n_keys_out, err);
+        if ((s = check_launch("k_tile_scan")) != GS_OK) return s;
+        k_tile_order<<<1, 1024, 0, st>>>(tile_ranges, ntiles, order, n_big);
+        if ((s = check_launch("k_tile_order")) != GS_OK) return s;
+    }
     if (n == 0 || keys_capacity == 0) return GS_OK;
     if (ntiles <= AGG_MAX_TILES) {
         if ((s = set_agg_smem_attrs()) != GS_OK) return s;

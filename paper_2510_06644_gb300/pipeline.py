@@ -113,8 +113,8 @@ class Rasterizer:
         then backward projection with the pose step fused into its last block
         (gs_project_bwd_step).  `cam` must carry the device pose (`pose`,
         float32 [12]) so the next iteration sees the updated pose; pose_adam
-        is the float32 [13] Adam state.  Seven kernel launches (plus memsets)
-        instead of the nine of step() + gs_pose_update."""
+        is the float32 [13] Adam state.  Eight kernel launches (plus memsets)
+        instead of the ten of step() + gs_pose_update."""
         cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam, pose=pose)
         self.set_grid(cam_s)
         gs.gs_project(self.cfg, cam_s, g, self.rec_dtype, self.splats)
