@@ -76,3 +76,31 @@ def test_workspace_size_queries_need_no_device(built_lib):
     assert big >= 8 * 1_000_000
     with pytest.raises(gs.GsError):
         gs.gs_bin_sort_workspace(cam, gs.GS_F32, 10, 1 << 30)   # capacity limit 2^30
+
+
+def test_fused_entry_points_reject_bad_arguments_on_the_host(built_lib):
+    """The fused forms check their extra arguments before any device work."""
+    from paper_2510_06644_gb300 import gs
+    cfg = gs.default_config()
+    cam = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 10, "fy": 10, "cx": 5, "cy": 5,
+                     "W": 10, "H": 10})
+    g = gs.gs_gaussians()
+    g.n = 10
+    step = gs.gs_pose_step(None, None, 1e-3, 1e-3, 0.9, 0.999, 1e-8)
+    nb = ctypes.c_size_t(1 << 20)
+    # a pose step needs the pose-gradient output
+    rc = gs.lib().gs_project_bwd_step(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), None, None, None,
+                                      None, ctypes.byref(step), None, ctypes.byref(nb), None)
+    assert rc == gs.GS_ERR_INVALID_ARG and b"pose_grad6" in gs.lib().gs_last_error()
+    # ... and a pose and an Adam state
+    pg = ctypes.c_double * 6
+    rc = gs.lib().gs_project_bwd_step(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), None, None,
+                                      ctypes.cast(pg(), ctypes.c_void_p), None, ctypes.byref(step), None,
+                                      ctypes.byref(nb), None)
+    assert rc == gs.GS_ERR_INVALID_ARG and b"pose step" in gs.lib().gs_last_error()
+    # forward + loss: targets, gradients and the loss word are required
+    rc = gs.lib().gs_render_fwd_loss(ctypes.byref(cfg), ctypes.byref(cam), gs.GS_F32, None, 0, None,
+                                     ctypes.c_void_p(16), None, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                     ctypes.c_void_p(16), ctypes.c_void_p(16), None, None, None, None, None,
+                                     None, None)
+    assert rc == gs.GS_ERR_INVALID_ARG and b"target" in gs.lib().gs_last_error()

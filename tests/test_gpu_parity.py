@@ -184,6 +184,8 @@ def render_gpu(G, cam, rec, n, cfg=None):
     (5000, 200, 120, 15, 4, 2),     # ... 4x8 tiles
     (20000, 333, 197, 16, 3, 3),    # ... odd stride
     (20000, 320, 240, 17, 1, 2),    # pixel-parallel, two tiles per CTA
+    (30000, 40, 36, 18, 1, 1),      # lists of 10k-30k entries (many staged batches)
+    (30000, 40, 36, 19, 2, 2),      # ... entry-parallel
 ])
 def test_render_fwd_matches_oracle(G, O, n, W, H, seed, sx, sy):
     cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
@@ -283,6 +285,8 @@ def test_pixel_pairing_changes_no_result(G, O, sx, sy):
     (5000, 200, 120, 26, "track", 4, 2),
     (20000, 333, 197, 27, "map", 3, 3),
     (20000, 320, 240, 28, "track", 1, 2),   # pixel-parallel, two tiles per CTA
+    (30000, 40, 36, 29, "map", 1, 1),       # lists of 10k-30k entries
+    (30000, 40, 36, 30, "track", 2, 2),     # ... entry-parallel
 ])
 def test_render_bwd_matches_oracle(G, O, n, W, H, seed, mode, sx, sy):
     cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
