@@ -662,18 +662,26 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 3 : 2)
 // with g the pixel's image gradient; each lane adds its entry's gradient to
 // the tile's shared accumulators.  Entries are staged as four 16-byte arrays
 // (lane l reading element l is conflict-free).
-#define EP_B 256
+#define EP_B 256     // entries staged per batch (the forward of 64-pixel
+                     // tiles stages 512: fewer CTA barriers per list)
 
-struct EpStage {
-    float4 a[EP_B];    // x, y, conic_a, conic_b
-    float4 b[EP_B];    // conic_c, opacity, depth, -
-    float4 c[EP_B];    // r, g, b, -
-    int4 box[EP_B];    // pixel box
+template <int NB>
+struct EpStageN {
+    float4 a[NB];    // x, y, conic_a, conic_b
+    float4 b[NB];    // conic_c, opacity, depth, -
+    float4 c[NB];    // r, g, b, -
+    int4 box[NB];    // pixel box
+};
+typedef EpStageN<EP_B> EpStage;
+
+template <int W>
+struct EpFwdBatch {
+    static constexpr int N = W == 16 ? 2 * EP_B : EP_B;
 };
 
-template <int DT, int W>
+template <int DT, int W, int NB>
 __device__ __forceinline__ void ep_stage(const void* __restrict__ splats, const uint32_t* __restrict__ ids, int n_in,
-                                         float alpha_min, EpStage& S, uint32_t* sid) {
+                                         float alpha_min, EpStageN<NB>& S, uint32_t* sid) {
     for (int e = threadIdx.x; e < n_in; e += W * 32) {
         const uint32_t id = __ldg(ids + e);
         const Splat v = load_splat<DT>(splats, id);
@@ -689,7 +697,8 @@ __device__ __forceinline__ void ep_stage(const void* __restrict__ splats, const 
 // its pixel box (a superset of the fragments the alpha test accepts, so
 // compacting by it changes no result).  Testing the alpha ellipse here as
 // well was measured slower: the extra loads cost more than the groups saved.
-__device__ __forceinline__ bool ep_may_blend(const EpStage& S, int e, int px, int py) {
+template <int NB>
+__device__ __forceinline__ bool ep_may_blend(const EpStageN<NB>& S, int e, int px, int py) {
     const int4 box = S.box[e];
     return px >= box.x && px <= box.y && py >= box.z && py <= box.w;
 }
@@ -743,7 +752,7 @@ __device__ __forceinline__ void ep_pair(const Grid& g, int tile, int q0, int npi
 template <int DT, int W>
 __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
-                                       const FwdOut& O, int tile, int q0, int npix, EpStage& S,
+                                       const FwdOut& O, int tile, int q0, int npix, EpStageN<EpFwdBatch<W>::N>& S,
                                        int (*cbuf_all)[64], uint32_t* s_h, uint8_t* perm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -758,10 +767,11 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     uint32_t last = 0, nb = 0;
     bool done = !mine;
-    for (uint32_t b = start; b < end; b += EP_B) {
+    constexpr int NB = EpFwdBatch<W>::N;
+    for (uint32_t b = start; b < end; b += NB) {
         if (__syncthreads_count(!done) == 0) break;
-        const int n_in = (int)min((uint32_t)EP_B, end - b);
-        ep_stage<DT, W>(splats, vals + b, n_in, cfg.alpha_min, S, nullptr);
+        const int n_in = (int)min((uint32_t)NB, end - b);
+        ep_stage<DT, W, NB>(splats, vals + b, n_in, cfg.alpha_min, S, nullptr);
         __syncthreads();
         for (int j = 0; j < ppw; ++j) {
             if (__shfl_sync(0xffffffffu, done, j)) continue;
@@ -864,7 +874,7 @@ template <int DT, int W>
 __global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
     k_render_fwd_ep(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
                     const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order, FwdOut O) {
-    __shared__ EpStage S;
+    __shared__ EpStageN<EpFwdBatch<W>::N> S;
     __shared__ int cbuf_all[W][64];
     __shared__ uint32_t s_h[64];
     __shared__ uint8_t perm[64];
@@ -946,7 +956,7 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
     for (uint32_t hi = start + tile_last; hi > start;) {
         const uint32_t lo = hi - start > (uint32_t)EP_B ? hi - EP_B : start;
         const int n_in = (int)(hi - lo);
-        ep_stage<DT, W>(splats, vals + lo, n_in, cfg.alpha_min, S, sid);
+        ep_stage<DT, W, EP_B>(splats, vals + lo, n_in, cfg.alpha_min, S, sid);
         for (int q = threadIdx.x; q < NF * EP_B; q += W * 32) (&acc[0][0])[q] = 0.f;
         __syncthreads();
         const uint32_t base_pos = lo - start;
