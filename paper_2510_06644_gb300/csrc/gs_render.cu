@@ -894,12 +894,13 @@ __device__ __forceinline__ int ep_col(int f) {
     return f < 5 ? f : 6;
 }
 
-// Shared memory of the entry-parallel backward.
-template <int MODE, int W>
+// Shared memory of the entry-parallel backward (batches of NB entries;
+// dynamic: above 48 KB for 16 warps and 512 entries).
+template <int MODE, int W, int NB = EpFwdBatch<W>::N>
 struct EpBwdSmem {
-    EpStage S;
-    uint32_t sid[EP_B];
-    float acc[EpFields<MODE>::N][EP_B];
+    EpStageN<NB> S;
+    uint32_t sid[NB];
+    float acc[EpFields<MODE>::N][NB];
     int cbuf[W][64];
     uint32_t s_h[64];
     uint8_t perm[64];
@@ -916,9 +917,10 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
                                        float* __restrict__ grad2d, int tile, int q0, int npix,
                                        EpBwdSmem<MODE, W>& M) {
     constexpr int NF = EpFields<MODE>::N;
-    EpStage& S = M.S;
+    constexpr int NB = EpFwdBatch<W>::N;
+    EpStageN<NB>& S = M.S;
     uint32_t* sid = M.sid;
-    float(&acc)[NF][EP_B] = M.acc;
+    float(&acc)[NF][NB] = M.acc;
     uint32_t& s_max = M.s_max;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned gt_mask = lane == 31 ? 0u : ~0u << (lane + 1);
@@ -954,10 +956,10 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
     const uint32_t tile_last = s_max;
     // batches from the tile's furthest blended position back to the start
     for (uint32_t hi = start + tile_last; hi > start;) {
-        const uint32_t lo = hi - start > (uint32_t)EP_B ? hi - EP_B : start;
+        const uint32_t lo = hi - start > (uint32_t)NB ? hi - NB : start;
         const int n_in = (int)(hi - lo);
-        ep_stage<DT, W, EP_B>(splats, vals + lo, n_in, cfg.alpha_min, S, sid);
-        for (int q = threadIdx.x; q < NF * EP_B; q += W * 32) (&acc[0][0])[q] = 0.f;
+        ep_stage<DT, W, NB>(splats, vals + lo, n_in, cfg.alpha_min, S, sid);
+        for (int q = threadIdx.x; q < NF * NB; q += W * 32) (&acc[0][0])[q] = 0.f;
         __syncthreads();
         const uint32_t base_pos = lo - start;
         for (int j = 0; j < ppw; ++j) {
@@ -1083,7 +1085,8 @@ __global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
                     const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                     const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
                     float* __restrict__ grad2d) {
-    __shared__ EpBwdSmem<MODE, W> M;
+    extern __shared__ __align__(16) unsigned char r_smem[];
+    EpBwdSmem<MODE, W>& M = *reinterpret_cast<EpBwdSmem<MODE, W>*>(r_smem);
     const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
     bwd_ep<DT, MODE, W>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, tile, 0,
                         g.tw * g.th, M);
@@ -1104,7 +1107,7 @@ static int group_batch(int gpc, int bytes_per_entry, int budget) {
 // Raises a kernel's dynamic shared-memory limit once per device and
 // instantiation (not repeated while a graph is being captured).
 static gs_status smem_once(const void* fn, int id, int bytes) {
-    static bool done[64][18] = {};
+    static bool done[64][40] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && done[dev][id]) return GS_OK;
@@ -1158,12 +1161,19 @@ static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* spl
                             cudaStream_t st) {
     const int ntiles = g.TX * g.TY;
     if (g.tw * g.th <= 64) {
-        if (g.tw * g.th <= 32)
-            k_render_bwd_ep<DT, MD, 8><<<ntiles, 8 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, t_final,
-                                                                   last_idx, d_rgb, d_depth, grad2d);
-        else
-            k_render_bwd_ep<DT, MD, 16><<<ntiles, 16 * 32, 0, st>>>(cfg, g, splats, vals, ranges, order, t_final,
-                                                                     last_idx, d_rgb, d_depth, grad2d);
+        gs_status s;
+        const int id = 18 + 4 * (MD == GS_MAP) + DT;  // + 0 or 8 below: W
+        if (g.tw * g.th <= 32) {
+            const int sm = (int)sizeof(EpBwdSmem<MD, 8>);
+            if ((s = smem_once((const void*)k_render_bwd_ep<DT, MD, 8>, id, sm)) != GS_OK) return s;
+            k_render_bwd_ep<DT, MD, 8><<<ntiles, 8 * 32, sm, st>>>(cfg, g, splats, vals, ranges, order, t_final,
+                                                                    last_idx, d_rgb, d_depth, grad2d);
+        } else {
+            const int sm = (int)sizeof(EpBwdSmem<MD, 16>);
+            if ((s = smem_once((const void*)k_render_bwd_ep<DT, MD, 16>, id + 8, sm)) != GS_OK) return s;
+            k_render_bwd_ep<DT, MD, 16><<<ntiles, 16 * 32, sm, st>>>(cfg, g, splats, vals, ranges, order,
+                                                                      t_final, last_idx, d_rgb, d_depth, grad2d);
+        }
         return check_launch("k_render_bwd_ep");
     }
     const int gpc = R_THREADS / tile_threads(g);
