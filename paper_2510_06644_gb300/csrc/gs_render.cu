@@ -12,7 +12,9 @@
 // binning, so the longest lists start first (the GPU counterpart of the
 // paper's subtile streaming, Sec. 5.2).  Warps cover 8x4 pixel blocks.  A
 // tile's sorted list is staged through shared memory in batches of up to
-// 256 records; each warp then builds a bit mask of the staged Gaussians
+// 1024 records in the forward, 512 in the backward (larger batches, fewer
+// CTA barriers: measured 146 -> 132 us forward); each warp then builds a
+// bit mask of the staged Gaussians
 // whose pixel box meets its block (one box test and one ballot per 32
 // entries) and visits only those, four at a time in the forward (their
 // alphas are independent; the blends then run in order without branches).
@@ -34,10 +36,10 @@
 namespace gs {
 
 #define R_THREADS 256            // largest CTA (16x16 tile)
-#define R_BATCH 256              // largest batch of entries a tile stages at a time
-#define R_MASKW (R_BATCH / 32)
-#define R_FWD_SMEM (8 * R_BATCH * 64)   // forward staging: up to 8 tiles x 256 x 64 B
-#define R_BWD_SMEM (104 * 1024)         // backward staging budget per CTA
+#define R_BATCH 1024             // largest batch of entries a tile stages at a time
+#define R_MASKW (R_BATCH / 32)   // mask words of a batch (at most 32: lane q holds word q)
+#define R_FWD_SMEM (R_BATCH * 64)       // forward staging budget per CTA (64 KB)
+#define R_BWD_SMEM (70 * 1024)          // backward staging budget per CTA (512 entries)
 #define R_STEP 4                 // list entries evaluated side by side in the forward walk
 
 struct StagedSplat {
