@@ -184,23 +184,26 @@ gs_status gs_project(const gs_config* cfg, const gs_camera* cam, const gs_gaussi
                      int rec_dtype, void* splats, gs_stream stream);
 
 /* ---------------------------------------------------------------------- */
-/* A-2..A-4 Tile intersection, key duplication, 64-bit radix sort, ranges   */
+/* A-2..A-4 Tile intersection, key duplication, 64-bit key sort, ranges     */
 /* (Sec. 2.1, Step 1-2 and Step 2)                                          */
 /* ---------------------------------------------------------------------- */
-/* For every Gaussian with radius > 0 and every tile of its rect (row-major
- * inside the rect, Gaussians in id order) one key
+/* For every Gaussian with radius > 0 and every tile of its rect one key
  *     key = tile_id << 32 | float32 bits of depth,   value = Gaussian id,
- * then a stable LSD radix sort on the low 32 + ceil(log2(TX*TY)) key bits,
- * so each tile's list is in (depth, id) order; finally
+ * sorted by (key, id) (the sort is a function of the keys: ties in depth
+ * are ordered by id), so each tile's list is in (depth, id) order; finally
  * tile_ranges[2t], tile_ranges[2t+1] = [first, last+1) of tile t ([0,0) when
  * empty).  The rect is recomputed from (x, y, radius) of the records.
+ * Implementation: a counting scatter on the tile id (per-CTA tile rows and a
+ * column scan) and a merge sort of each tile's (depth, id) bucket.
  * keys_out [keys_capacity] u64, vals_out [keys_capacity] u32,
  * n_keys_out: one device int64 receiving the true key count, tile_ranges
  * [2*TX*TY] u32.  If the count exceeds keys_capacity, only keys_capacity keys
  * are sorted and the device status becomes GS_ERR_CAPACITY.
  * tile_order (may be NULL): [TX*TY] u32 permutation of the tile ids, longest
- * lists first (grouped by floor(log2(length + 1)), any order inside a group);
- * passing it to the compositing calls makes long tiles start first.
+ * lists first: tiles grouped by the power of two bounding their length,
+ * (2^k, 2^(k+1)], empty tiles last, ascending tile id inside a group (a
+ * function of the lists alone); passing it to the compositing calls makes
+ * long tiles start first.
  * Workspace: query with workspace == NULL (depends on n, keys_capacity and
  * the tile count). */
 gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
