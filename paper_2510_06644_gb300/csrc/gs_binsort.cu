@@ -98,9 +98,17 @@ __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int n
     const int t = blockIdx.x * 32 + tx;
     const int per = (nrows + 31) / 32;
     const int r0 = min(nrows, ty * per), r1 = min(nrows, r0 + per);
+    // rows in groups of 8 loads issued back to back (a dependent sum per
+    // load would wait out an L2 round trip per row)
     uint32_t sum = 0;
     if (t < ntiles)
-        for (int r = r0; r < r1; ++r) sum += hist[(size_t)r * ntiles + t];
+        for (int r = r0; r < r1; r += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = r + k < r1 ? __ldcg(hist + (size_t)(r + k) * ntiles + t) : 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sum += v[k];
+        }
     part[ty][tx] = sum;
     __syncthreads();
     if (ty == 0) {
@@ -115,11 +123,16 @@ __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int n
     __syncthreads();
     uint32_t run = part[ty][tx];
     if (t < ntiles)
-        for (int r = r0; r < r1; ++r) {
-            uint32_t* p = hist + (size_t)r * ntiles + t;
-            const uint32_t v = *p;
-            *p = run;
-            run += v;
+        for (int r = r0; r < r1; r += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = r + k < r1 ? __ldcg(hist + (size_t)(r + k) * ntiles + t) : 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (r + k < r1) {
+                    hist[(size_t)(r + k) * ntiles + t] = run;
+                    run += v[k];
+                }
         }
 }
 
