@@ -469,7 +469,7 @@ def run_ours(args):
         gs.gs_project(rast.cfg, cs, gd, rast.rec_dtype, rast.splats)
         evs[1].record()
         gs.gs_bin_sort(cs, rast.splats, n, rast.capacity, rast.rec_dtype, ws=rast._sort_ws(cs), keys=rast.keys,
-                       vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges, order=rast.order)
+                       vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges, order=rast.order, cfg=rast.cfg)
         evs[2].record()
         gs.gs_render_fwd_loss(rast.cfg, cs, rast.splats, n, rast.vals, rast.ranges, trgb, tdep, rast.rec_dtype,
                               out=rast.img, dimg=rast.dimg, order=rast.order)

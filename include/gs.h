@@ -192,7 +192,16 @@ gs_status gs_project(const gs_config* cfg, const gs_camera* cam, const gs_gaussi
  * sorted by (key, id) (the sort is a function of the keys: ties in depth
  * are ordered by id), so each tile's list is in (depth, id) order; finally
  * tile_ranges[2t], tile_ranges[2t+1] = [first, last+1) of tile t ([0,0) when
- * empty).  The rect is recomputed from (x, y, radius) of the records.
+ * empty).  The rect is recomputed from the records: the tiles holding a
+ * sampled in-image pixel of the Gaussian's integer box [floor(x) - r,
+ * floor(x) + r] x [floor(y) - r, floor(y) + r], shrunk to the pixels whose
+ * centre can reach alpha >= cfg->alpha_min: |p + 0.5 - x| <= ex with
+ * ex = sqrt(2 (B + 1e-3) (Q^-1)_xx) 1.002 + 2e-3 (likewise y), Q the conic
+ * and B = 64 ((op / alpha_min)^(1/64) - 1) >= ln(op / alpha_min), all in
+ * float32 with correctly rounded operations (six square roots); a Gaussian
+ * with op < alpha_min gets no tile.  Every fragment the compositing can
+ * blend is in its tile's list; lists hold about 20 % fewer keys than with
+ * the integer box alone.
  * Implementation: a counting scatter on the tile id (per-CTA tile rows and a
  * column scan) and a merge sort of each tile's (depth, id) bucket.
  * keys_out [keys_capacity] u64, vals_out [keys_capacity] u32,
@@ -206,14 +215,14 @@ gs_status gs_project(const gs_config* cfg, const gs_camera* cam, const gs_gaussi
  * long tiles start first.
  * Workspace: query with workspace == NULL (depends on n, keys_capacity and
  * the tile count). */
-gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
+gs_status gs_bin_sort(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
                       int64_t keys_capacity, void* workspace, size_t* workspace_bytes,
                       uint64_t* keys_out, uint32_t* vals_out, int64_t* n_keys_out,
                       uint32_t* tile_ranges, uint32_t* tile_order, gs_stream stream);
 
 /* Key count only (the first two stages of gs_bin_sort), so that a caller can
  * size keys_capacity.  Same workspace as gs_bin_sort. */
-gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
+gs_status gs_bin_count(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
                        void* workspace, size_t* workspace_bytes, int64_t* n_keys_out,
                        gs_stream stream);
 
@@ -356,11 +365,12 @@ gs_status gs_prune(const gs_config* cfg, const float* score_terms, int64_t n,
 /* Change ratio of tile-Gaussian intersections between two binnings of the
  * same n Gaussians on the same tile grid (Sec. 4.1): |A xor B| / max(1, |A|)
  * over the sets of (tile, Gaussian) pairs.  Each Gaussian's tiles form the
- * rect of its record (see gs_project), so |A xor B| = sum_k |rect_a(k)| +
+ * rect of its record (the rect of gs_bin_sort, with cfg->alpha_min), so
+ * |A xor B| = sum_k |rect_a(k)| +
  * |rect_b(k)| - 2 |rect_a(k) & rect_b(k)|.  For the mask-prune rule both
  * binnings should include the masked Gaussians (project with mask = NULL).
  * ratio_out: one device float. */
-gs_status gs_change_ratio(const gs_camera* cam, int rec_dtype, const void* splats_a,
+gs_status gs_change_ratio(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats_a,
                           const void* splats_b, int64_t n, void* workspace,
                           size_t* workspace_bytes, float* ratio_out, gs_stream stream);
 

@@ -97,33 +97,75 @@ static void grid_dims(const or_cam* c, int64_t* Ws, int64_t* Hs, int64_t* TX, in
     *TY = ceil_div(*Hs, tile_dim(c->sy));
 }
 
+/* Half extents of the pixel box where alpha = op exp(-d^T Q d / 2) can reach
+ * alpha_min (Q = conic; fragments below alpha_min are skipped, Sec. 2.1):
+ * |d_x| <= sqrt(2 ln(op / alpha_min) (Q^-1)_xx), (Q^-1)_xx = c / det.  ln is
+ * bounded above by 64 (x^(1/64) - 1) (e^t >= 1 + t), plus 1e-3, and the
+ * extent is widened by 1.002 and 2e-3 px.  This bound decides integers (which
+ * tiles hold the Gaussian), so it is evaluated in float32 with correctly
+ * rounded operations only (products, quotients, six square roots), no
+ * contraction: the same numbers on every IEEE machine.  Returns 0 when no
+ * pixel can reach alpha_min (op < alpha_min); the extents are +inf when the
+ * conic is degenerate. */
+static int alpha_extent_f(float ca, float cb, float cc, float op, float amin, float* ex, float* ey) {
+    if (!(op >= amin)) return 0;
+    *ex = INFINITY;
+    *ey = INFINITY;
+    float det = ca * cc - cb * cb;
+    if (!(det > 0.f)) return 1;
+    float q = op / amin;
+    for (int i = 0; i < 6; ++i) q = sqrtf(q);
+    float L = 64.f * (q - 1.f);
+    float t2 = 2.f * ((L > 0.f ? L : 0.f) + 1e-3f);
+    *ex = sqrtf(t2 * cc / det) * 1.002f + 2e-3f;
+    *ey = sqrtf(t2 * ca / det) * 1.002f + 2e-3f;
+    return 1;
+}
+
 /* Tile rectangle of a 2D Gaussian (Sec. 2.1, Step 1-2).  The Gaussian covers
  * the integer pixel box [floor(u)-r, floor(u)+r] x [floor(v)-r, floor(v)+r]
- * of the full-resolution image; this box contains every pixel whose centre
- * (p+0.5) lies within r of the mean on each axis.  With strides (sx, sy) the
- * sampled pixel i sits at full-resolution column sx*i, so the covered sampled
- * columns are ceil((floor(u)-r)/sx) .. floor((floor(u)+r)/sx), and the tiles
- * are those columns, clipped to the sampled image, divided by the tile side
- * (16 at full resolution, see tile_dim).  Returns
- * the rect [x0,x1) x [y0,y1) in tile units (empty when no sampled pixel of
- * the image lies in the box) and the box in full-resolution pixels. */
-static void tile_rect(const or_cam* c, double u, double v, int64_t r,
-                      int64_t rect[4], int64_t box[4]) {
+ * of the full-resolution image (returned in `box`); this box contains every
+ * pixel whose centre (p+0.5) lies within r of the mean on each axis.  Its
+ * tiles are those holding a sampled pixel of the box that can also reach
+ * alpha_min: |p + 0.5 - u| <= ex (alpha_extent_f, from the float32 values of
+ * u, v, the conic and the opacity).  With strides (sx, sy) the sampled pixel
+ * i sits at full-resolution column sx*i, so the covered sampled columns are
+ * ceil(b0/sx) .. floor(b1/sx) for the shrunk box [b0, b1], clipped to the
+ * sampled image and divided by the tile side (16 at full resolution, see
+ * tile_dim).  Returns the rect [x0,x1) x [y0,y1) in tile units (empty when no
+ * such pixel lies in the image). */
+static void tile_rect(const or_cam* c, double u, double v, int64_t r, const double* conic, double opacity,
+                      double alpha_min, int64_t rect[4], int64_t box[4]) {
     int64_t Ws, Hs, TX, TY;
     grid_dims(c, &Ws, &Hs, &TX, &TY);
     double uc = u < -1e9 ? -1e9 : (u > 1e9 ? 1e9 : u);
     double vc = v < -1e9 ? -1e9 : (v > 1e9 ? 1e9 : v);
     int64_t xi = (int64_t)floor(uc), yi = (int64_t)floor(vc);
     box[0] = xi - r; box[1] = xi + r; box[2] = yi - r; box[3] = yi + r;
-    int64_t i0 = ceil_div(box[0], c->sx), i1 = floor_div(box[1], c->sx);
-    int64_t j0 = ceil_div(box[2], c->sy), j1 = floor_div(box[3], c->sy);
+    rect[0] = rect[1] = rect[2] = rect[3] = 0;
+    float ex, ey;
+    if (!alpha_extent_f((float)conic[0], (float)conic[1], (float)conic[2], (float)opacity, (float)alpha_min,
+                        &ex, &ey))
+        return;
+    int64_t b0 = box[0], b1 = box[1], b2 = box[2], b3 = box[3];
+    const float uf = (float)u, vf = (float)v;
+    if (ex < 1e8f && fabsf(uf) < 1e8f) {
+        int64_t lo = (int64_t)ceilf((uf - ex) - 0.5f), hi = (int64_t)floorf((uf + ex) - 0.5f);
+        if (lo > b0) b0 = lo;
+        if (hi < b1) b1 = hi;
+    }
+    if (ey < 1e8f && fabsf(vf) < 1e8f) {
+        int64_t lo = (int64_t)ceilf((vf - ey) - 0.5f), hi = (int64_t)floorf((vf + ey) - 0.5f);
+        if (lo > b2) b2 = lo;
+        if (hi < b3) b3 = hi;
+    }
+    if (b1 < b0 || b3 < b2) return;
+    int64_t i0 = ceil_div(b0, c->sx), i1 = floor_div(b1, c->sx);
+    int64_t j0 = ceil_div(b2, c->sy), j1 = floor_div(b3, c->sy);
     /* only sampled pixels inside the image count */
     i0 = clamp_i64(i0, 0, Ws); i1 = clamp_i64(i1, -1, Ws - 1);
     j0 = clamp_i64(j0, 0, Hs); j1 = clamp_i64(j1, -1, Hs - 1);
-    if (i0 > i1 || j0 > j1) {
-        rect[0] = rect[1] = rect[2] = rect[3] = 0;
-        return;
-    }
+    if (i0 > i1 || j0 > j1) return;
     rect[0] = i0 / tile_dim(c->sx);
     rect[1] = i1 / tile_dim(c->sx) + 1;
     rect[2] = j0 / tile_dim(c->sy);
@@ -297,7 +339,7 @@ void or_project(int64_t n, const double* means, const double* log_scales, const 
         radius[k] = o.radius;
         r3[k] = o.r3;
         int64_t box[4];
-        tile_rect(cam, o.u, o.v, o.radius, rect + 4 * k, box);
+        tile_rect(cam, o.u, o.v, o.radius, o.conic, o.opacity, cfg->alpha_min, rect + 4 * k, box);
         touched[k] = (rect[4 * k + 1] - rect[4 * k]) * (rect[4 * k + 3] - rect[4 * k + 2]);
     }
 }
@@ -323,13 +365,15 @@ static int cmp_kv(const void* pa, const void* pb) {
     return 0;
 }
 
-/* Number of (tile, Gaussian) pairs: the sum of tiles touched. */
-int64_t or_bin_count(int64_t n, const double* uv, const int64_t* radius, const or_cam* cam) {
+/* Number of (tile, Gaussian) pairs: the sum of tiles touched (tile_rect with
+ * the given conics, opacities and alpha_min). */
+int64_t or_bin_count(int64_t n, const double* uv, const int64_t* radius, const double* conic,
+                     const double* opacity, double alpha_min, const or_cam* cam) {
     int64_t total = 0;
     for (int64_t k = 0; k < n; ++k) {
         if (radius[k] <= 0) continue;
         int64_t rect[4], box[4];
-        tile_rect(cam, uv[2 * k], uv[2 * k + 1], radius[k], rect, box);
+        tile_rect(cam, uv[2 * k], uv[2 * k + 1], radius[k], conic + 3 * k, opacity[k], alpha_min, rect, box);
         total += (rect[1] - rect[0]) * (rect[3] - rect[2]);
     }
     return total;
@@ -342,17 +386,18 @@ int64_t or_bin_count(int64_t n, const double* uv, const int64_t* radius, const o
  * inside a tile keep id order.  ranges[2t], ranges[2t+1] = first and one past
  * the last sorted index of tile t ([0,0) for an empty tile).  Buffers must
  * hold or_bin_count() pairs and 2*TX*TY range words. */
-void or_bin_sort(int64_t n, const double* uv, const double* depth, const int64_t* radius,
-                 const or_cam* cam, uint64_t* keys, uint32_t* vals, uint32_t* ranges) {
+void or_bin_sort(int64_t n, const double* uv, const double* depth, const int64_t* radius, const double* conic,
+                 const double* opacity, double alpha_min, const or_cam* cam, uint64_t* keys, uint32_t* vals,
+                 uint32_t* ranges) {
     int64_t Ws, Hs, TX, TY;
     grid_dims(cam, &Ws, &Hs, &TX, &TY);
-    int64_t total = or_bin_count(n, uv, radius, cam);
+    int64_t total = or_bin_count(n, uv, radius, conic, opacity, alpha_min, cam);
     or_kv* kv = (or_kv*)malloc(sizeof(or_kv) * (size_t)(total > 0 ? total : 1));
     int64_t w = 0;
     for (int64_t k = 0; k < n; ++k) {
         if (radius[k] <= 0) continue;
         int64_t rect[4], box[4];
-        tile_rect(cam, uv[2 * k], uv[2 * k + 1], radius[k], rect, box);
+        tile_rect(cam, uv[2 * k], uv[2 * k + 1], radius[k], conic + 3 * k, opacity[k], alpha_min, rect, box);
         for (int64_t ty = rect[2]; ty < rect[3]; ++ty)
             for (int64_t tx = rect[0]; tx < rect[1]; ++tx) {
                 uint64_t tile = (uint64_t)(ty * TX + tx);

@@ -74,9 +74,9 @@ def _load():
             P = C.c_void_p
             lib.or_project.argtypes = [C.c_int64, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.or_project.restype = None
-            lib.or_bin_count.argtypes = [C.c_int64, P, P, P]
+            lib.or_bin_count.argtypes = [C.c_int64, P, P, P, P, C.c_double, P]
             lib.or_bin_count.restype = C.c_int64
-            lib.or_bin_sort.argtypes = [C.c_int64, P, P, P, P, P, P, P]
+            lib.or_bin_sort.argtypes = [C.c_int64, P, P, P, P, P, C.c_double, P, P, P, P]
             lib.or_bin_sort.restype = None
             lib.or_render_fwd.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
             lib.or_render_fwd.restype = C.c_double
@@ -187,20 +187,26 @@ def project(g, cam, cfg=None):
 # Binning and sort (Sec. 2.1 Steps 1-2 and 2)
 # --------------------------------------------------------------------------
 
-def bin_sort(uv, depth, radius, cam):
-    """Keys (tile<<32 | f32 depth bits), values (ids) and ranges [T,2]."""
+def bin_sort(s, cam, cfg=None):
+    """Keys (tile<<32 | f32 depth bits), values (ids) and ranges [T,2] of the
+    projected splats s (uv, depth, radius, conic, opacity); the tile rects
+    use cfg's alpha_min."""
     lib = _load()
-    uv = _f64(uv)
+    uv = _f64(s["uv"])
     n = uv.shape[0]
-    depth = _f64(depth, (n,))
-    radius = np.ascontiguousarray(np.asarray(radius, dtype=np.int64).reshape(n))
+    depth = _f64(s["depth"], (n,))
+    radius = np.ascontiguousarray(np.asarray(s["radius"], dtype=np.int64).reshape(n))
+    conic = _f64(s["conic"], (n, 3))
+    opacity = _f64(s["opacity"], (n,))
+    amin = float(_cfg(cfg).alpha_min)
     c = _cam(cam)
-    total = lib.or_bin_count(n, _p(uv), _p(radius), C.byref(c))
+    total = lib.or_bin_count(n, _p(uv), _p(radius), _p(conic), _p(opacity), amin, C.byref(c))
     _, _, TX, TY = grid(cam)
     keys = np.zeros(max(total, 1), np.uint64)
     vals = np.zeros(max(total, 1), np.uint32)
     ranges = np.zeros((TX * TY, 2), np.uint32)
-    lib.or_bin_sort(n, _p(uv), _p(depth), _p(radius), C.byref(c), _p(keys), _p(vals), _p(ranges))
+    lib.or_bin_sort(n, _p(uv), _p(depth), _p(radius), _p(conic), _p(opacity), amin, C.byref(c), _p(keys),
+                    _p(vals), _p(ranges))
     return keys[:total], vals[:total], ranges
 
 
@@ -233,7 +239,7 @@ def render_fwd(s, cam, cfg=None, tiled=True, lists=None):
     vals = ranges = None
     if tiled:
         if lists is None:
-            _, vals, ranges = bin_sort(keep["uv"], keep["depth"], keep["radius"], cam)
+            _, vals, ranges = bin_sort(keep, cam, cfg)
         else:
             vals, ranges = lists
         vals = np.ascontiguousarray(vals, dtype=np.uint32)
@@ -274,7 +280,7 @@ def render_bwd(s, cam, d_rgb, d_depth, cfg=None, tiled=True, lists=None):
     vals = ranges = None
     if tiled:
         if lists is None:
-            _, vals, ranges = bin_sort(keep["uv"], keep["depth"], keep["radius"], cam)
+            _, vals, ranges = bin_sort(keep, cam, cfg)
         else:
             vals, ranges = lists
         vals = np.ascontiguousarray(vals, dtype=np.uint32)

@@ -72,7 +72,7 @@ class GsRenderFn(torch.autograd.Function):
         cfg = cfg if cfg is not None else gs.default_config()
         cs = gs.camera(cam_p)
         probe = gs.gs_project(cfg, cs, g, rec_dtype)
-        n_keys = int(gs.gs_bin_count(cs, probe, n, rec_dtype).item())
+        n_keys = int(gs.gs_bin_count(cs, probe, n, rec_dtype, cfg=cfg).item())
         rast = Rasterizer(n, cam_p, cfg, rec_dtype, capacity=max(n_keys, 1), device=means.device)
         img = rast.forward(g, cs)
         rgb, depth = img["rgb"].clone(), img["depth"].clone()

@@ -42,16 +42,14 @@ namespace gs {
 typedef unsigned long long u64;
 
 template <int DT>
-__global__ void __launch_bounds__(BIN_THREADS) k_tile_count(gs_camera cam, const void* __restrict__ splats,
+__global__ void __launch_bounds__(BIN_THREADS) k_tile_count(gs_camera cam, float alpha_min, const void* __restrict__ splats,
                                                             int64_t n, uint32_t* __restrict__ count) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const Grid grid = make_grid(cam);
-    float x, y, d;
-    int r;
-    load_geom<DT>(splats, (uint32_t)k, x, y, d, r);
+    const Geom G = load_geom<DT>(splats, (uint32_t)k);
     int x0, x1, y0, y1;
-    if (tile_rect(grid, x, y, r, x0, x1, y0, y1) == 0) return;
+    if (tile_rect(grid, G, alpha_min, x0, x1, y0, y1) == 0) return;
     for (int ty = y0; ty < y1; ++ty)
         for (int tx = x0; tx < x1; ++tx) atomicAdd(count + ty * grid.TX + tx, 1u);
 }
@@ -67,7 +65,7 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_count(gs_camera cam, const
 #define AGG_MAX_TILES 8192
 
 template <int DT>
-__global__ void __launch_bounds__(BIN_THREADS) k_tile_hist(gs_camera cam, const void* __restrict__ splats, int64_t n,
+__global__ void __launch_bounds__(BIN_THREADS) k_tile_hist(gs_camera cam, float alpha_min, const void* __restrict__ splats, int64_t n,
                                                            int64_t per_cta, int ntiles, uint32_t* __restrict__ hist) {
     extern __shared__ uint32_t h[];
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) h[t] = 0;
@@ -75,11 +73,9 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_hist(gs_camera cam, const 
     const Grid grid = make_grid(cam);
     const int64_t k0 = (int64_t)blockIdx.x * per_cta, k1 = min(n, k0 + per_cta);
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-        float x, y, d;
-        int r;
-        load_geom<DT>(splats, (uint32_t)k, x, y, d, r);
+        const Geom G = load_geom<DT>(splats, (uint32_t)k);
         int x0, x1, y0, y1;
-        if (tile_rect(grid, x, y, r, x0, x1, y0, y1) == 0) continue;
+        if (tile_rect(grid, G, alpha_min, x0, x1, y0, y1) == 0) continue;
         for (int ty = y0; ty < y1; ++ty)
             for (int tx = x0; tx < x1; ++tx) atomicAdd(h + ty * grid.TX + tx, 1u);
     }
@@ -142,7 +138,7 @@ __global__ void __launch_bounds__(1024) k_col_scan(uint32_t* __restrict__ hist, 
 }
 
 template <int DT>
-__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rows(gs_camera cam, const void* __restrict__ splats,
+__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rows(gs_camera cam, float alpha_min, const void* __restrict__ splats,
                                                                    int64_t n, int64_t per_cta, int ntiles,
                                                                    const uint32_t* __restrict__ start,
                                                                    const uint32_t* __restrict__ hist, int64_t cap,
@@ -158,12 +154,10 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rows(gs_camera cam
     const Grid grid = make_grid(cam);
     const int64_t k0 = (int64_t)blockIdx.x * per_cta, k1 = min(n, k0 + per_cta);
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-        float x, y, d;
-        int r;
-        load_geom<DT>(splats, (uint32_t)k, x, y, d, r);
+        const Geom G = load_geom<DT>(splats, (uint32_t)k);
         int x0, x1, y0, y1;
-        if (tile_rect(grid, x, y, r, x0, x1, y0, y1) == 0) continue;
-        const u64 rem = ((u64)__float_as_uint(d) << 32) | (u64)(uint32_t)k;
+        if (tile_rect(grid, G, alpha_min, x0, x1, y0, y1) == 0) continue;
+        const u64 rem = ((u64)__float_as_uint(G.depth) << 32) | (u64)(uint32_t)k;
         for (int ty = y0; ty < y1; ++ty)
             for (int tx = x0; tx < x1; ++tx) {
                 const int t = ty * grid.TX + tx;
@@ -315,19 +309,17 @@ __global__ void __launch_bounds__(1024) k_col_scan_tail(uint32_t* __restrict__ h
 }
 
 template <int DT>
-__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter(gs_camera cam, const void* __restrict__ splats,
+__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter(gs_camera cam, float alpha_min, const void* __restrict__ splats,
                                                               int64_t n, const uint32_t* __restrict__ start,
                                                               uint32_t* __restrict__ fill, int64_t cap,
                                                               u64* __restrict__ keys) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const Grid grid = make_grid(cam);
-    float x, y, d;
-    int r;
-    load_geom<DT>(splats, (uint32_t)k, x, y, d, r);
+    const Geom G = load_geom<DT>(splats, (uint32_t)k);
     int x0, x1, y0, y1;
-    if (tile_rect(grid, x, y, r, x0, x1, y0, y1) == 0) return;
-    const u64 rem = ((u64)__float_as_uint(d) << 32) | (u64)(uint32_t)k;
+    if (tile_rect(grid, G, alpha_min, x0, x1, y0, y1) == 0) return;
+    const u64 rem = ((u64)__float_as_uint(G.depth) << 32) | (u64)(uint32_t)k;
     for (int ty = y0; ty < y1; ++ty)
         for (int tx = x0; tx < x1; ++tx) {
             const int t = ty * grid.TX + tx;
@@ -605,8 +597,9 @@ static BinLayout bin_layout(int64_t n, int64_t cap, int ntiles) {
 
 using namespace gs;
 
-static gs_status bin_common_checks(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
-                                   bool size_query) {
+static gs_status bin_common_checks(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
+                                   int64_t n, bool size_query) {
+    if (!cfg) return set_error(GS_ERR_INVALID_ARG, "config is NULL");
     if (!cam) return set_error(GS_ERR_INVALID_ARG, "camera is NULL");
     if (cam->width <= 0 || cam->height <= 0 || cam->sx < 1 || cam->sy < 1 || cam->width > (1 << 20) ||
         cam->height > (1 << 20))
@@ -637,7 +630,7 @@ static gs_status set_agg_smem_attrs() {
 
 // Tile counts into `count`: per-CTA rows + column scan (rows kept in `hist`
 // for the scatter) when the grid is small enough, else direct atomics.
-static gs_status launch_count(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
+static gs_status launch_count(const gs_camera* cam, float alpha_min, int rec_dtype, const void* splats, int64_t n,
                               uint32_t* count, uint32_t* hist, cudaStream_t st, const ScanTail* tail = nullptr,
                               bool* fused = nullptr) {
     if (fused) *fused = false;
@@ -648,9 +641,9 @@ static gs_status launch_count(const gs_camera* cam, int rec_dtype, const void* s
         const int64_t per = agg_per_cta(n, ntiles);
         const unsigned nb = (unsigned)((n + per - 1) / per);
         const size_t sm = sizeof(uint32_t) * (size_t)ntiles;
-        if (rec_dtype == GS_F32) k_tile_hist<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, hist);
-        else if (rec_dtype == GS_BF16) k_tile_hist<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, hist);
-        else k_tile_hist<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, hist);
+        if (rec_dtype == GS_F32) k_tile_hist<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, hist);
+        else if (rec_dtype == GS_BF16) k_tile_hist<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, hist);
+        else k_tile_hist<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, hist);
         gs_status s;
         if ((s = check_launch("k_tile_hist")) != GS_OK) return s;
         if (tail) {
@@ -662,17 +655,18 @@ static gs_status launch_count(const gs_camera* cam, int rec_dtype, const void* s
         return check_launch("k_col_scan");
     }
     const unsigned nb = (unsigned)((n + BIN_THREADS - 1) / BIN_THREADS);
-    if (rec_dtype == GS_F32) k_tile_count<GS_F32><<<nb, BIN_THREADS, 0, st>>>(*cam, splats, n, count);
-    else if (rec_dtype == GS_BF16) k_tile_count<GS_BF16><<<nb, BIN_THREADS, 0, st>>>(*cam, splats, n, count);
-    else k_tile_count<GS_F16><<<nb, BIN_THREADS, 0, st>>>(*cam, splats, n, count);
+    if (rec_dtype == GS_F32) k_tile_count<GS_F32><<<nb, BIN_THREADS, 0, st>>>(*cam, alpha_min, splats, n, count);
+    else if (rec_dtype == GS_BF16) k_tile_count<GS_BF16><<<nb, BIN_THREADS, 0, st>>>(*cam, alpha_min, splats, n, count);
+    else k_tile_count<GS_F16><<<nb, BIN_THREADS, 0, st>>>(*cam, alpha_min, splats, n, count);
     return check_launch("k_tile_count");
 }
 
-extern "C" gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
+extern "C" gs_status gs_bin_count(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
+                                  int64_t n,
                                   void* workspace, size_t* workspace_bytes, int64_t* n_keys_out,
                                   gs_stream stream) {
     gs_status s;
-    if ((s = bin_common_checks(cam, rec_dtype, splats, n, workspace == nullptr)) != GS_OK) return s;
+    if ((s = bin_common_checks(cfg, cam, rec_dtype, splats, n, workspace == nullptr)) != GS_OK) return s;
     if (!workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "workspace_bytes is NULL");
     const Grid g = make_grid(*cam);
     const int ntiles = g.TX * g.TY;
@@ -686,19 +680,20 @@ extern "C" gs_status gs_bin_count(const gs_camera* cam, int rec_dtype, const voi
     uint32_t* hist = ntiles <= AGG_MAX_TILES ? (uint32_t*)((char*)workspace + L.off_hist) : nullptr;
     if (cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)ntiles, st) != cudaSuccess)
         return set_error(GS_ERR_CUDA, "memset counts");
-    if ((s = launch_count(cam, rec_dtype, splats, n, count, hist, st)) != GS_OK) return s;
+    if ((s = launch_count(cam, cfg->alpha_min, rec_dtype, splats, n, count, hist, st)) != GS_OK) return s;
     unsigned int* err = status_ptr();
     if (!err) return set_error(GS_ERR_CUDA, "status word address");
     k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, (int64_t)1 << 62, nullptr, nullptr, n_keys_out, err);
     return check_launch("k_tile_scan");
 }
 
-extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,
+extern "C" gs_status gs_bin_sort(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
+                                 int64_t n,
                                  int64_t keys_capacity, void* workspace, size_t* workspace_bytes,
                                  uint64_t* keys_out, uint32_t* vals_out, int64_t* n_keys_out,
                                  uint32_t* tile_ranges, uint32_t* tile_order, gs_stream stream) {
     gs_status s;
-    if ((s = bin_common_checks(cam, rec_dtype, splats, n, workspace == nullptr)) != GS_OK) return s;
+    if ((s = bin_common_checks(cfg, cam, rec_dtype, splats, n, workspace == nullptr)) != GS_OK) return s;
     if (!workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "workspace_bytes is NULL");
     if (keys_capacity < 0 || keys_capacity >= ((int64_t)1 << 30))
         return set_error(GS_ERR_INVALID_ARG, "keys_capacity must be in [0, 2^30)");
@@ -726,7 +721,7 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
     const ScanTail tail = {(unsigned int*)(ws + L.off_ticket), keys_capacity, start, tile_ranges, n_keys_out, err,
                            order, n_big};
     bool fused = false;
-    if ((s = launch_count(cam, rec_dtype, splats, n, count, hist, st, &tail, &fused)) != GS_OK) return s;
+    if ((s = launch_count(cam, cfg->alpha_min, rec_dtype, splats, n, count, hist, st, &tail, &fused)) != GS_OK) return s;
     if (!fused) {
         k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, keys_capacity, start, tile_ranges, n_keys_out, err);
         if ((s = check_launch("k_tile_scan")) != GS_OK) return s;
@@ -734,29 +729,30 @@ extern "C" gs_status gs_bin_sort(const gs_camera* cam, int rec_dtype, const void
         if ((s = check_launch("k_tile_order")) != GS_OK) return s;
     }
     if (n == 0 || keys_capacity == 0) return GS_OK;
+    const float alpha_min = cfg->alpha_min;
     if (ntiles <= AGG_MAX_TILES) {
         if ((s = set_agg_smem_attrs()) != GS_OK) return s;
         const int64_t per = agg_per_cta(n, ntiles);
         const unsigned nb = (unsigned)((n + per - 1) / per);
         const size_t sm = 2 * sizeof(uint32_t) * (size_t)ntiles;
         if (rec_dtype == GS_F32)
-            k_tile_scatter_rows<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, hist,
+            k_tile_scatter_rows<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start, hist,
                                                                     keys_capacity, (u64*)keys_out);
         else if (rec_dtype == GS_BF16)
-            k_tile_scatter_rows<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, hist,
+            k_tile_scatter_rows<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start, hist,
                                                                      keys_capacity, (u64*)keys_out);
         else
-            k_tile_scatter_rows<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, splats, n, per, ntiles, start, hist,
+            k_tile_scatter_rows<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start, hist,
                                                                     keys_capacity, (u64*)keys_out);
         if ((s = check_launch("k_tile_scatter_rows")) != GS_OK) return s;
     } else {
         const unsigned nb = (unsigned)((n + BIN_THREADS - 1) / BIN_THREADS);
         if (rec_dtype == GS_F32)
-            k_tile_scatter<GS_F32><<<nb, BIN_THREADS, 0, st>>>(*cam, splats, n, start, fill, keys_capacity, (u64*)keys_out);
+            k_tile_scatter<GS_F32><<<nb, BIN_THREADS, 0, st>>>(*cam, alpha_min, splats, n, start, fill, keys_capacity, (u64*)keys_out);
         else if (rec_dtype == GS_BF16)
-            k_tile_scatter<GS_BF16><<<nb, BIN_THREADS, 0, st>>>(*cam, splats, n, start, fill, keys_capacity, (u64*)keys_out);
+            k_tile_scatter<GS_BF16><<<nb, BIN_THREADS, 0, st>>>(*cam, alpha_min, splats, n, start, fill, keys_capacity, (u64*)keys_out);
         else
-            k_tile_scatter<GS_F16><<<nb, BIN_THREADS, 0, st>>>(*cam, splats, n, start, fill, keys_capacity, (u64*)keys_out);
+            k_tile_scatter<GS_F16><<<nb, BIN_THREADS, 0, st>>>(*cam, alpha_min, splats, n, start, fill, keys_capacity, (u64*)keys_out);
         if ((s = check_launch("k_tile_scatter")) != GS_OK) return s;
     }
     {

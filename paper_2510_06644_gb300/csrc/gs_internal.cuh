@@ -98,14 +98,62 @@ __device__ __forceinline__ int pix_floor(float u) {
 // position lies in the box [floor(u)-r, floor(u)+r] x [floor(v)-r, floor(v)+r]
 // (Sec. 2.1, Step 1-2; strides of Sec. 4.2), in tiles of tw x th sampled
 // pixels.  Returns the tile count.
-__device__ __forceinline__ int tile_rect(const Grid& g, float u, float v, int r, int& x0, int& x1,
+// Geometry a tile rect needs: mean, depth, radius, conic and opacity.
+struct Geom {
+    float x, y, depth;
+    int radius;
+    float ca, cb, cc, op;
+};
+
+// Half extents (ex, ey) of the pixel box where alpha = op exp(-d^T Q d / 2)
+// can reach alpha_min (Q = conic; fragments below alpha_min are skipped,
+// Sec. 2.1): |d_x| <= sqrt(2 ln(op / alpha_min) (Q^-1)_xx).  ln is bounded
+// above by 64 (x^(1/64) - 1) (from e^t >= 1 + t), computed with six
+// correctly rounded square roots and fixed float32 operations, so the FP64
+// oracle evaluates the very same float32 numbers; 1e-3 added to the bound
+// and the factor 1.002 + 2e-3 px cover the rounding of the per-pixel alpha
+// test.  Returns false when no pixel can reach alpha_min (op < alpha_min);
+// (ex, ey) = +inf when the conic is degenerate (no shrinking).
+__device__ __forceinline__ bool alpha_extent(float ca, float cb, float cc, float op, float alpha_min, float& ex,
+                                             float& ey) {
+    if (!(op >= alpha_min)) return false;
+    ex = ey = __int_as_float(0x7f800000);
+    const float det = __fsub_rn(__fmul_rn(ca, cc), __fmul_rn(cb, cb));
+    if (!(det > 0.f)) return true;
+    float q = __fdiv_rn(op, alpha_min);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q = __fsqrt_rn(q);
+    const float L = __fmul_rn(64.f, __fsub_rn(q, 1.f));
+    const float t2 = __fmul_rn(2.f, __fadd_rn(fmaxf(L, 0.f), 1e-3f));
+    ex = __fadd_rn(__fmul_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(t2, cc), det)), 1.002f), 2e-3f);
+    ey = __fadd_rn(__fmul_rn(__fsqrt_rn(__fdiv_rn(__fmul_rn(t2, ca), det)), 1.002f), 2e-3f);
+    return true;
+}
+
+// Tiles of a Gaussian (Sec. 2.1, Step 1-2): those holding a sampled in-image
+// pixel of its integer box [floor(x) - r, floor(x) + r] x [...] shrunk to the
+// pixels whose centre lies within the alpha extent (pixel p when
+// |p + 0.5 - x| <= ex).  Returns the tile count and [x0, x1) x [y0, y1).
+__device__ __forceinline__ int tile_rect(const Grid& g, const Geom& G, float alpha_min, int& x0, int& x1,
                                          int& y0, int& y1) {
     x0 = x1 = y0 = y1 = 0;
+    const int r = G.radius;
     if (r <= 0) return 0;
-    int xi = pix_floor(u), yi = pix_floor(v);
+    float ex, ey;
+    if (!alpha_extent(G.ca, G.cb, G.cc, G.op, alpha_min, ex, ey)) return 0;
+    int xi = pix_floor(G.x), yi = pix_floor(G.y);
     // 64-bit guard against xi +- r overflow is unnecessary: |xi| <= 1e9, r < 2^30
     long long bx0 = (long long)xi - r, bx1 = (long long)xi + r;
     long long by0 = (long long)yi - r, by1 = (long long)yi + r;
+    if (ex < 1e8f && fabsf(G.x) < 1e8f) {
+        bx0 = max(bx0, (long long)ceilf(__fsub_rn(__fsub_rn(G.x, ex), 0.5f)));
+        bx1 = min(bx1, (long long)floorf(__fsub_rn(__fadd_rn(G.x, ex), 0.5f)));
+    }
+    if (ey < 1e8f && fabsf(G.y) < 1e8f) {
+        by0 = max(by0, (long long)ceilf(__fsub_rn(__fsub_rn(G.y, ey), 0.5f)));
+        by1 = min(by1, (long long)floorf(__fsub_rn(__fadd_rn(G.y, ey), 0.5f)));
+    }
+    if (bx1 < bx0 || by1 < by0) return 0;
     if (bx1 < 0 || by1 < 0 || bx0 > (long long)(g.W - 1) || by0 > (long long)(g.H - 1)) return 0;
     int i0 = ceil_div_i((int)max(bx0, -1LL), g.sx);
     int i1 = floor_div((int)min(bx1, (long long)g.W), g.sx);
@@ -164,20 +212,24 @@ __device__ __forceinline__ Splat load_splat(const void* base, uint32_t k) {
     return s;
 }
 
-// Mean, depth and radius only (binning).
+// What the binning reads of a record: mean, depth, radius, conic, opacity.
 template <int DT>
-__device__ __forceinline__ void load_geom(const void* base, uint32_t k, float& x, float& y,
-                                          float& depth, int& radius) {
+__device__ __forceinline__ Geom load_geom(const void* base, uint32_t k) {
+    Geom G;
     if (DT == GS_F32) {
         const float4* p = reinterpret_cast<const float4*>(base) + 3 * (size_t)k;
-        float4 a = __ldg(p), b = __ldg(p + 1);
-        x = a.x; y = a.y; depth = b.z; radius = __float_as_int(b.w);
+        const float4 a = __ldg(p), b = __ldg(p + 1);
+        G.x = a.x; G.y = a.y; G.ca = a.z; G.cb = a.w;
+        G.cc = b.x; G.op = b.y; G.depth = b.z; G.radius = __float_as_int(b.w);
     } else {
         const uint4* p = reinterpret_cast<const uint4*>(base) + 2 * (size_t)k;
-        uint4 a = __ldg(p);
-        x = __uint_as_float(a.x); y = __uint_as_float(a.y);
-        depth = __uint_as_float(a.z); radius = (int)a.w;
+        const uint4 a = __ldg(p), b = __ldg(p + 1);
+        G.x = __uint_as_float(a.x); G.y = __uint_as_float(a.y);
+        G.depth = __uint_as_float(a.z); G.radius = (int)a.w;
+        G.ca = h2f((uint16_t)(b.x & 0xffff), DT); G.cb = h2f((uint16_t)(b.x >> 16), DT);
+        G.cc = h2f((uint16_t)(b.y & 0xffff), DT); G.op = h2f((uint16_t)(b.y >> 16), DT);
     }
+    return G;
 }
 
 // ---------------------------------------------------------------------------

@@ -119,8 +119,15 @@ __global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, g
     float cr = __ldg(g.rgb + 3 * k), cg = __ldg(g.rgb + 3 * k + 1), cb = __ldg(g.rgb + 3 * k + 2);
     int touched = 0;
     if (o.visible) {
+        // the binning's rect, from the values as the record stores them
+        Geom G;
+        G.x = o.u; G.y = o.v; G.depth = o.p[2]; G.radius = o.radius;
+        G.ca = DT == GS_F32 ? o.ca : h2f(f2h(o.ca, DT), DT);
+        G.cb = DT == GS_F32 ? o.cb : h2f(f2h(o.cb, DT), DT);
+        G.cc = DT == GS_F32 ? o.cc : h2f(f2h(o.cc, DT), DT);
+        G.op = DT == GS_F32 ? o.op : h2f(f2h(o.op, DT), DT);
         int x0, x1, y0, y1;
-        touched = tile_rect(grid, o.u, o.v, o.radius, x0, x1, y0, y1);
+        touched = tile_rect(grid, G, cfg.alpha_min, x0, x1, y0, y1);
     } else {
         o.u = o.v = o.ca = o.cb = o.cc = o.op = 0.f;
         o.p[2] = 0.f;

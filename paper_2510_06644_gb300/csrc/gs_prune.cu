@@ -196,18 +196,14 @@ __global__ void __launch_bounds__(PR_THREADS) k_keep_write(const uint8_t* __rest
 
 // |rect_a| + |rect_b| - 2 |rect_a & rect_b| and |rect_a| summed over Gaussians.
 template <int DT>
-__global__ void __launch_bounds__(PR_THREADS) k_change(gs_camera cam, const void* __restrict__ sa,
+__global__ void __launch_bounds__(PR_THREADS) k_change(gs_camera cam, float alpha_min, const void* __restrict__ sa,
                                                        const void* __restrict__ sb, int64_t n, u64* __restrict__ acc) {
     const Grid grid = make_grid(cam);
     u64 sym = 0, na = 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        float x, y, d;
-        int r;
         int ax0, ax1, ay0, ay1, bx0, bx1, by0, by1;
-        load_geom<DT>(sa, (uint32_t)k, x, y, d, r);
-        const int ca = tile_rect(grid, x, y, r, ax0, ax1, ay0, ay1);
-        load_geom<DT>(sb, (uint32_t)k, x, y, d, r);
-        const int cb = tile_rect(grid, x, y, r, bx0, bx1, by0, by1);
+        const int ca = tile_rect(grid, load_geom<DT>(sa, (uint32_t)k), alpha_min, ax0, ax1, ay0, ay1);
+        const int cb = tile_rect(grid, load_geom<DT>(sb, (uint32_t)k), alpha_min, bx0, bx1, by0, by1);
         int inter = 0;
         if (ca > 0 && cb > 0) {
             const int ix = min(ax1, bx1) - max(ax0, bx0), iy = min(ay1, by1) - max(ay0, by0);
@@ -320,10 +316,11 @@ extern "C" gs_status gs_prune(const gs_config* cfg, const float* score_terms, in
     return GS_OK;
 }
 
-extern "C" gs_status gs_change_ratio(const gs_camera* cam, int rec_dtype, const void* splats_a, const void* splats_b,
+extern "C" gs_status gs_change_ratio(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats_a,
+                                     const void* splats_b,
                                      int64_t n, void* workspace, size_t* workspace_bytes, float* ratio_out,
                                      gs_stream stream) {
-    if (!cam || !workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "camera or workspace_bytes NULL");
+    if (!cfg || !cam || !workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "config, camera or workspace_bytes NULL");
     if (cam->width <= 0 || cam->height <= 0 || cam->sx < 1 || cam->sy < 1)
         return set_error(GS_ERR_INVALID_ARG, "bad camera size or stride");
     if (rec_dtype != GS_F32 && rec_dtype != GS_BF16 && rec_dtype != GS_F16)
@@ -341,9 +338,9 @@ extern "C" gs_status gs_change_ratio(const gs_camera* cam, int rec_dtype, const 
         const int sms = num_sms();
         const int64_t want = (n + PR_THREADS - 1) / PR_THREADS;
         const unsigned nb = (unsigned)(want < 4 * sms ? want : 4 * sms);
-        if (rec_dtype == GS_F32) k_change<GS_F32><<<nb, PR_THREADS, 0, st>>>(*cam, splats_a, splats_b, n, acc);
-        else if (rec_dtype == GS_BF16) k_change<GS_BF16><<<nb, PR_THREADS, 0, st>>>(*cam, splats_a, splats_b, n, acc);
-        else k_change<GS_F16><<<nb, PR_THREADS, 0, st>>>(*cam, splats_a, splats_b, n, acc);
+        if (rec_dtype == GS_F32) k_change<GS_F32><<<nb, PR_THREADS, 0, st>>>(*cam, cfg->alpha_min, splats_a, splats_b, n, acc);
+        else if (rec_dtype == GS_BF16) k_change<GS_BF16><<<nb, PR_THREADS, 0, st>>>(*cam, cfg->alpha_min, splats_a, splats_b, n, acc);
+        else k_change<GS_F16><<<nb, PR_THREADS, 0, st>>>(*cam, cfg->alpha_min, splats_a, splats_b, n, acc);
         if ((s = check_launch("k_change")) != GS_OK) return s;
     }
     k_change_final<<<1, 1, 0, st>>>(acc, ratio_out);

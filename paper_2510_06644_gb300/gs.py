@@ -69,8 +69,8 @@ _SIGS = {
     "gs_default_config": ([_P], None),
     "gs_version": ([], C.c_char_p),
     "gs_project": ([_P, _P, _P, C.c_int, _P, _P], C.c_int),
-    "gs_bin_sort": ([_P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "gs_bin_count": ([_P, C.c_int, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
+    "gs_bin_sort": ([_P, _P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_bin_count": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
     "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_render_fwd_loss": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
                            C.c_int),
@@ -82,7 +82,7 @@ _SIGS = {
     "gs_project_bwd_noalloc": ([_P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_prune": ([_P, _P, C.c_int64, _P, C.c_int, _P, C.c_float, C.c_int64, _P, _P, _P, _P, _P],
                  C.c_int),
-    "gs_change_ratio": ([_P, C.c_int, _P, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
+    "gs_change_ratio": ([_P, _P, C.c_int, _P, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
     "gs_compact": ([_P, C.c_int64, C.c_int32, _P, _P, _P], C.c_int),
     "gs_downsample": ([C.c_int64, C.c_int64, C.c_int, C.c_int, _P, _P, _P, C.c_int32, C.c_int32,
                        C.c_int32, _P, _P], C.c_int),
@@ -223,20 +223,34 @@ def gs_project(cfg, cam, g, rec_dtype=GS_F32, splats=None, stream=None):
     return splats
 
 
-def gs_bin_sort_workspace(cam, rec_dtype, n, capacity):
+_DEFAULT_CFG = None
+
+
+def _cfg(cfg):
+    """The given config, or the library's defaults (alpha_min 1/255)."""
+    global _DEFAULT_CFG
+    if cfg is not None:
+        return cfg
+    if _DEFAULT_CFG is None:
+        _DEFAULT_CFG = default_config()
+    return _DEFAULT_CFG
+
+
+def gs_bin_sort_workspace(cam, rec_dtype, n, capacity, cfg=None):
     nb = C.c_size_t(0)
-    _check(lib().gs_bin_sort(C.byref(cam), rec_dtype, None, int(n), int(capacity), None, C.byref(nb),
-                             None, None, None, None, None, None), "gs_bin_sort(size)")
+    _check(lib().gs_bin_sort(C.byref(_cfg(cfg)), C.byref(cam), rec_dtype, None, int(n), int(capacity), None,
+                             C.byref(nb), None, None, None, None, None, None), "gs_bin_sort(size)")
     return nb.value
 
 
 def gs_bin_sort(cam, splats, n, capacity, rec_dtype=GS_F32, ws=None, keys=None, vals=None, n_keys=None,
-                ranges=None, order=None, stream=None):
+                ranges=None, order=None, stream=None, cfg=None):
     """Returns (keys, vals, n_keys, ranges, order); order is the heavy-first
-    tile permutation (allocated unless given)."""
+    tile permutation (allocated unless given).  cfg: its alpha_min shapes the
+    tile rects (the defaults unless given)."""
     dev = splats.device
     _, _, TX, TY = grid(cam)
-    need = gs_bin_sort_workspace(cam, rec_dtype, n, capacity)
+    need = gs_bin_sort_workspace(cam, rec_dtype, n, capacity, cfg)
     if ws is None or ws.numel() < need:
         ws = workspace(need, dev)
     keys = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev) if keys is None else keys
@@ -245,21 +259,22 @@ def gs_bin_sort(cam, splats, n, capacity, rec_dtype=GS_F32, ws=None, keys=None, 
     ranges = torch.empty((TX * TY, 2), dtype=torch.int32, device=dev) if ranges is None else ranges
     order = torch.empty(TX * TY, dtype=torch.int32, device=dev) if order is None else order
     nb = C.c_size_t(ws.numel())
-    _check(lib().gs_bin_sort(C.byref(cam), rec_dtype, _ptr(splats), int(n), int(capacity), _ptr(ws),
+    _check(lib().gs_bin_sort(C.byref(_cfg(cfg)), C.byref(cam), rec_dtype, _ptr(splats), int(n), int(capacity),
+                             _ptr(ws),
                              C.byref(nb), _ptr(keys), _ptr(vals), _ptr(n_keys), _ptr(ranges), _ptr(order),
                              _stream(stream)), "gs_bin_sort")
     return keys, vals, n_keys, ranges, order
 
 
-def gs_bin_count(cam, splats, n, rec_dtype=GS_F32, stream=None):
+def gs_bin_count(cam, splats, n, rec_dtype=GS_F32, stream=None, cfg=None):
     nb = C.c_size_t(0)
-    _check(lib().gs_bin_count(C.byref(cam), rec_dtype, None, int(n), None, C.byref(nb), None, None),
-           "gs_bin_count(size)")
+    _check(lib().gs_bin_count(C.byref(_cfg(cfg)), C.byref(cam), rec_dtype, None, int(n), None, C.byref(nb), None,
+                              None), "gs_bin_count(size)")
     ws = workspace(nb.value, splats.device)
     out = torch.zeros(1, dtype=torch.int64, device=splats.device)
     nb = C.c_size_t(ws.numel())
-    _check(lib().gs_bin_count(C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(ws), C.byref(nb),
-                              _ptr(out), _stream(stream)), "gs_bin_count")
+    _check(lib().gs_bin_count(C.byref(_cfg(cfg)), C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(ws),
+                              C.byref(nb), _ptr(out), _stream(stream)), "gs_bin_count")
     return out
 
 
@@ -401,12 +416,12 @@ def gs_prune(cfg, score, mask, iter_in_interval, K, change_ratio=0.0, max_select
     return k.value
 
 
-def gs_change_ratio(cam, splats_a, splats_b, n, rec_dtype=GS_F32, out=None, stream=None):
+def gs_change_ratio(cam, splats_a, splats_b, n, rec_dtype=GS_F32, out=None, stream=None, cfg=None):
     ws = workspace(256, splats_a.device)
     out = torch.zeros(1, dtype=torch.float32, device=splats_a.device) if out is None else out
     nb = C.c_size_t(ws.numel())
-    _check(lib().gs_change_ratio(C.byref(cam), rec_dtype, _ptr(splats_a), _ptr(splats_b), int(n), _ptr(ws),
-                                 C.byref(nb), _ptr(out), _stream(stream)), "gs_change_ratio")
+    _check(lib().gs_change_ratio(C.byref(_cfg(cfg)), C.byref(cam), rec_dtype, _ptr(splats_a), _ptr(splats_b),
+                                 int(n), _ptr(ws), C.byref(nb), _ptr(out), _stream(stream)), "gs_change_ratio")
     return out
 
 

@@ -53,7 +53,7 @@ class Rasterizer:
         self._ws_sort = None
 
     def _sort_ws(self, cam_s):
-        need = gs.gs_bin_sort_workspace(cam_s, self.rec_dtype, self.n, self.capacity)
+        need = gs.gs_bin_sort_workspace(cam_s, self.rec_dtype, self.n, self.capacity, self.cfg)
         if self._ws_sort is None or self._ws_sort.numel() < need:
             self._ws_sort = gs.workspace(need, self.device)
         return self._ws_sort
@@ -80,7 +80,7 @@ class Rasterizer:
         if rebin:
             gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
                            keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges,
-                           order=self.order)
+                           order=self.order, cfg=self.cfg)
         gs.gs_render_fwd(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, self.rec_dtype, out=self.img,
                          order=self.order)
         return self.img
@@ -121,7 +121,7 @@ class Rasterizer:
         if rebin:
             gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
                            keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges,
-                           order=self.order)
+                           order=self.order, cfg=self.cfg)
         gs.gs_render_fwd_loss(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, target_rgb,
                               target_depth, self.rec_dtype, out=self.img, dimg=self.dimg, order=self.order)
         gs.gs_render_bwd(self.cfg, cam_s, g, self.splats, self.vals, self.ranges, self.img["t_final"],

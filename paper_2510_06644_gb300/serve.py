@@ -82,7 +82,8 @@ class Session:
         self.use_graphs = use_graphs
         # observations: full-resolution RGB-D rendered from the true poses
         self.targets = []
-        n_keys = int(gs.gs_bin_count(gs.camera(c0), gs.gs_project(self.cfg, gs.camera(c0), self.g), spec.n).item())
+        n_keys = int(gs.gs_bin_count(gs.camera(c0), gs.gs_project(self.cfg, gs.camera(c0), self.g), spec.n,
+                                     cfg=self.cfg).item())
         self.capacity = int(n_keys * 1.5) + 4096
         probe = Rasterizer(spec.n, c0, self.cfg, capacity=self.capacity, device=self.device)
         for cam in true_cams:

@@ -58,8 +58,9 @@ def test_argument_errors_are_synchronous(built_lib):
     cam = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 10, "fy": 10, "cx": 5, "cy": 5,
                      "W": 0, "H": 10})
     nb = ctypes.c_size_t(0)
-    rc = gs.lib().gs_bin_sort(ctypes.byref(cam), 0, None, 10, 100, None, ctypes.byref(nb), None, None, None,
-                              None, None, None)
+    cfg = gs.default_config()
+    rc = gs.lib().gs_bin_sort(ctypes.byref(cfg), ctypes.byref(cam), 0, None, 10, 100, None, ctypes.byref(nb), None,
+                              None, None, None, None, None)
     assert rc == gs.GS_ERR_INVALID_ARG
     assert b"camera" in gs.lib().gs_last_error()
 

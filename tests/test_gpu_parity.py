@@ -89,10 +89,17 @@ def test_project_matches_oracle(G, O, case):
     near_int = np.abs(r3 - np.round(r3)) < 1e-4 * np.maximum(1, r3)
     same_r = f["radius"][vis] == pr["radius"][vis]
     assert np.all(same_r | near_int)
-    # tiles touched: exact where radius and floor(u), floor(v) agree
+    # tiles touched: the rect of the record's own float32 fields, exactly (the
+    # oracle's binning of the same fields); and against the oracle's own
+    # projection wherever the integer decisions agree (radius, floor(u),
+    # floor(v); the alpha extent's bounds may round apart on a few)
+    keys, vals, _ = O.bin_sort(f, cam)
+    per_g = np.bincount(vals.astype(np.int64), minlength=f["radius"].shape[0])
+    assert np.array_equal(f["touched"].astype(np.int64), per_g)
     fl_same = np.all(np.floor(f["uv"][vis]) == np.floor(pr["uv"][vis]), axis=1)
     ok = same_r & fl_same
-    assert np.array_equal(f["touched"][vis][ok], pr["touched"][vis][ok])
+    agree = f["touched"][vis][ok] == pr["touched"][vis][ok]
+    assert (~agree).sum() <= max(2, int(2e-3 * ok.sum()))
     assert (~ok).sum() <= max(2, int(1e-3 * vis.sum()))
 
 
@@ -115,7 +122,7 @@ def test_bin_sort_bit_exact(G, O, n, W, H, sx, sy, seed, sig):
     s = S.splats(n, W, H, seed=seed, sigma_px=sig, tie_frac=0.1)
     rec = pack_splats(s)
     keys, vals, ranges, _, _ = gpu_bin(G, cam, rec, n)
-    ok, ov, orr = O.bin_sort(s["uv"], s["depth"], s["radius"], cam)
+    ok, ov, orr = O.bin_sort(s, cam)
     assert keys.shape == ok.shape
     assert np.array_equal(keys, ok)
     assert np.array_equal(vals, ov)
@@ -131,7 +138,7 @@ def test_bin_sort_one_bucket_each_network_size(G, O, n):
     s = S.splats(n, 16, 16, seed=9100 + n, sigma_px=(0.6, 40.0), tie_frac=0.2, cull_frac=0.0)
     s["uv"] = S.rng(9200 + n).uniform(0.0, 16.0, (n, 2)).astype(np.float32)
     keys, vals, ranges, _, _ = gpu_bin(G, cam, pack_splats(s), n)
-    ok, ov, orr = O.bin_sort(s["uv"], s["depth"], s["radius"], cam)
+    ok, ov, orr = O.bin_sort(s, cam)
     assert keys.shape == ok.shape == (n,)
     assert np.array_equal(keys, ok)
     assert np.array_equal(vals, ov)
@@ -472,7 +479,7 @@ def test_change_ratio_matches_pair_sets(G, O):
 
     def pairs(rec):
         f = {k: np_of(v) for k, v in G.splat_fields(rec).items()}
-        keys, vals, _ = O.bin_sort(f["uv"], f["depth"], f["radius"], cam_a)
+        keys, vals, _ = O.bin_sort(f, cam_a)
         return ((keys >> np.uint64(32)) << np.uint64(32)) | vals.astype(np.uint64)
 
     ref = O.change_ratio(pairs(ra), pairs(rb))
@@ -514,7 +521,7 @@ def test_reused_lists_match_oracle_with_the_same_stale_lists(G, O):
     r.backward(gd, cam1, torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=G.GS_MAP)
     r.check()
     pr0 = O.project(g, cam0)
-    _, vals0, ranges0 = O.bin_sort(pr0["uv"], pr0["depth"], pr0["radius"], cam0)
+    _, vals0, ranges0 = O.bin_sort(pr0, cam0)
     pr1 = O.project(g, cam1)
     img = O.render_fwd(pr1, cam1, lists=(vals0, ranges0))
     good = img["margin"] == 0

@@ -69,12 +69,17 @@ def test_records_round_the_float32_fields(G, name):
     tt = torch.bfloat16 if name == "bf16" else torch.float16
     for k in ("conic", "opacity", "rgb"):
         assert torch.equal(f16[k], f32[k].to(tt).float()), k
-    t32 = f32["touched"]
-    assert torch.equal(f16["touched"].long(), torch.clamp(t32.long(), max=65535))
+    # the tile count follows the stored (rounded) conic and opacity
+    t32 = f32["touched"].long()
+    t16 = f16["touched"].long()
+    assert (t16 != torch.clamp(t32, max=65535)).float().mean().item() <= 0.02
 
 
 @pytest.mark.parametrize("name", ["bf16", "fp16"])
-def test_binning_identical_to_float32(G, name):
+def test_binning_of_16bit_records_bit_exact(G, O, name):
+    """The binning reads the 16-bit records' conic and opacity (the tile
+    rects' alpha extent): bit-exact against the oracle on the same rounded
+    values, and within a few percent of the float32 keys."""
     g = S.surface_scene(30000, seed=72)
     cam = S.camera(333, 197, 260.0)
     cfg = G.default_config()
@@ -86,8 +91,12 @@ def test_binning_identical_to_float32(G, name):
         keys, vals, nk, ranges, _ = G.gs_bin_sort(cs, rec, 30000, 400000, dt)
         k = int(nk.item())
         out[dtn] = (np_of(keys[:k]), np_of(vals[:k]), np_of(ranges))
-    for a, b in zip(out["f32"], out[name]):
-        assert np.array_equal(a, b)
+        if dtn == name:
+            f = {kk: np_of(v) for kk, v in G.splat_fields(rec, dt).items()}
+            ok_, ov_, or_ = O.bin_sort(f, cam)
+            assert np.array_equal(out[dtn][0], ok_) and np.array_equal(out[dtn][1], ov_)
+            assert np.array_equal(out[dtn][2], or_)
+    assert abs(len(out[name][0]) - len(out["f32"][0])) <= 0.02 * len(out["f32"][0])
 
 
 @pytest.mark.parametrize("name", ["bf16", "fp16"])

@@ -220,6 +220,40 @@ def test_tiled_equals_brute_force(oracle_lib):
     np.testing.assert_array_equal(ga, gb)
 
 
+def test_alpha_aware_tiles_lose_no_fragment(oracle_lib):
+    """The tile lists leave out a Gaussian only where it cannot reach
+    alpha_min (reading new-2): every (pixel, Gaussian) pair whose float64
+    alpha is at least alpha_min inside the integer box sits in the pixel's
+    tile list, at strides 1 and 2, on faint and anisotropic Gaussians."""
+    O = oracle_lib
+    s = S.splats(1500, 96, 64, seed=31, sigma_px=(0.6, 10.0))
+    # the alpha extent does shrink rects here: about a quarter fewer keys than
+    # with the integer boxes alone (opaque, very wide conics)
+    wide = dict(s, opacity=np.ones(1500), conic=s["conic"] * 1e-6)
+    assert len(O.bin_sort(s, S.camera(96, 64, 80.0))[0]) < 0.85 * len(O.bin_sort(wide, S.camera(96, 64, 80.0))[0])
+    for sx in (1, 2):
+        cam = S.camera(96, 64, 80.0, sx=sx, sy=sx)
+        keys, vals, ranges = O.bin_sort(s, cam)
+        Ws, Hs, TX, TY = O.grid(cam)
+        td = O.tile_dim(sx)
+        lists = [set(vals[b:e].tolist()) for b, e in ranges]
+        a, bq, c = s["conic"][:, 0], s["conic"][:, 1], s["conic"][:, 2]
+        for j in range(Hs):
+            for i in range(Ws):
+                px, py = i * sx, j * sx
+                dx = px + 0.5 - s["uv"][:, 0].astype(np.float64)
+                dy = py + 0.5 - s["uv"][:, 1].astype(np.float64)
+                power = -0.5 * (a * dx * dx + c * dy * dy) - bq * dx * dy
+                alpha = np.minimum(0.99, s["opacity"] * np.exp(np.minimum(power, 0)))
+                xi = np.floor(s["uv"][:, 0]).astype(np.int64)
+                yi = np.floor(s["uv"][:, 1]).astype(np.int64)
+                r = s["radius"]
+                inbox = (r > 0) & (np.abs(px - xi) <= r) & (np.abs(py - yi) <= r)
+                need = np.nonzero(inbox & (power <= 0) & (alpha >= 1 / 255))[0]
+                have = lists[(j // td) * TX + i // td]
+                assert set(need.tolist()) <= have, (sx, i, j)
+
+
 def test_tiled_equals_brute_force_on_stage_splats(oracle_lib):
     O = oracle_lib
     s = S.splats(400, 70, 50, seed=3)
@@ -240,7 +274,14 @@ def test_binning_hand_cases(oracle_lib):
     uv = np.array([[20.5, 5.2], [16.0, 40.0], [-3.5, 10.0], [63.9, 47.9]])
     depth = np.array([2.0, 1.5, 3.0, 2.5])
     radius = np.array([4, 1, 2, 1])
-    keys, vals, ranges = O.bin_sort(uv, depth, radius, cam)
+    # nearly opaque isotropic Gaussians with sigma = r / 3: alpha >= 1/255
+    # reaches 3.4 sigma > r, so the integer boxes decide these rects
+    sig2 = (radius / 3.0) ** 2
+    conic = np.stack([1.0 / sig2, np.zeros(4), 1.0 / sig2], 1)
+    opac = np.full(4, 0.99)
+    spl = lambda sl: {"uv": uv[sl], "depth": depth[sl], "radius": radius[sl], "conic": conic[sl],
+                      "opacity": opac[sl]}
+    keys, vals, ranges = O.bin_sort(spl(slice(None)), cam)
     bits = lambda d: int(np.array(d, np.float32).view(np.uint32))
     # G0: box x [16,24] -> tile col 1, y [1,9] -> row 0 -> tile 1
     # G1: box x [15,17] -> cols 0,1; y [39,41] -> row 2 -> tiles 8, 9
@@ -256,8 +297,20 @@ def test_binning_hand_cases(oracle_lib):
     # stride 2: tiles are 8x8 sampled pixels; the sampled columns of G0 are
     # 8..12 -> tile column 1, rows 1..4 -> tile row 0; TX = ceil(32/8) = 4
     cam2 = dict(cam, sx=2, sy=2)
-    k2, v2, r2 = O.bin_sort(uv[:1], depth[:1], radius[:1], cam2)
+    k2, v2, r2 = O.bin_sort(spl(slice(0, 1)), cam2)
     assert [int(k) >> 32 for k in k2] == [1]
+    # a faint Gaussian: r = 9 (sigma 3) at (31.0, 24.0), opacity 0.02.  Its
+    # integer box x [22, 40], y [15, 33] spans tile columns 1-2 and rows 0-2,
+    # but alpha reaches 1/255 only within |d| <= ex = sqrt(2 (B + 1e-3) 9)
+    # 1.002 + 2e-3 = 5.4645 (B = 64 (5.1^(1/64) - 1) = 1.6501 >= ln 5.1 =
+    # 1.6292): pixels x 26..35, y 19..28 -> row 1 only: tiles 5 and 6
+    faint = {"uv": np.array([[31.0, 24.0]]), "depth": np.array([4.0]), "radius": np.array([9]),
+             "conic": np.array([[1 / 9.0, 0.0, 1 / 9.0]]), "opacity": np.array([0.02])}
+    k3, _, _ = O.bin_sort(faint, cam)
+    assert [int(k) >> 32 for k in k3] == [5, 6]
+    # below alpha_min it touches no tile at all
+    k4, _, _ = O.bin_sort(dict(faint, opacity=np.array([0.003])), cam)
+    assert len(k4) == 0
     assert O.tile_dim(1) == 16 and O.tile_dim(2) == 8 and O.tile_dim(3) == 4 and O.tile_dim(4) == 4
     assert O.tile_dim(100) == 4
 
@@ -266,20 +319,38 @@ def test_sort_invariants_and_stability(oracle_lib):
     O = oracle_lib
     cam = S.camera(200, 120, 100.0)
     s = S.splats(3000, 200, 120, seed=5, tie_frac=0.2)
-    keys, vals, ranges = O.bin_sort(s["uv"], s["depth"], s["radius"], cam)
+    keys, vals, ranges = O.bin_sort(s, cam)
     # permutation of the expected multiset and non-decreasing keys
     assert np.all(np.diff(keys.astype(np.float64)) >= 0) or np.all(keys[1:] >= keys[:-1])
     _, _, TX, TY = O.grid(cam)
+    # brute-force rect: tiles with a pixel p in the integer box whose centre
+    # also lies within the alpha extent, |p + 0.5 - u| <= ex, the extent
+    # evaluated in numpy float32 from its definition (reading new-2)
+    f32 = np.float32
+    amin = f32(1.0) / f32(255.0)
     pr_rect = []
     total = 0
     for k in range(3000):
         r = int(s["radius"][k])
-        if r <= 0:
+        ca, cb, cc = (f32(v) for v in s["conic"][k])
+        op = f32(s["opacity"][k])
+        if r <= 0 or not op >= amin:
             pr_rect.append(None)
             continue
-        xi, yi = math.floor(s["uv"][k, 0]), math.floor(s["uv"][k, 1])
-        tx = [t for t in range(TX) if any(abs(p - xi) <= r for p in range(16 * t, min(16 * t + 16, 200)))]
-        ty = [t for t in range(TY) if any(abs(p - yi) <= r for p in range(16 * t, min(16 * t + 16, 120)))]
+        det = f32(ca * cc) - f32(cb * cb)
+        q = f32(op / amin)
+        for _ in range(6):
+            q = np.sqrt(q)
+        B = f32(f32(64.0) * f32(q - f32(1.0)))
+        t2 = f32(f32(2.0) * f32(max(B, f32(0.0)) + f32(1e-3)))
+        ex = f32(f32(np.sqrt(f32(f32(t2 * cc) / det)) * f32(1.002)) + f32(2e-3))
+        ey = f32(f32(np.sqrt(f32(f32(t2 * ca) / det)) * f32(1.002)) + f32(2e-3))
+        u, v = f32(s["uv"][k, 0]), f32(s["uv"][k, 1])
+        xi, yi = math.floor(u), math.floor(v)
+        okx = lambda p: abs(p - xi) <= r and abs(f32(f32(p) + f32(0.5)) - u) <= ex
+        oky = lambda p: abs(p - yi) <= r and abs(f32(f32(p) + f32(0.5)) - v) <= ey
+        tx = [t for t in range(TX) if any(okx(p) for p in range(16 * t, min(16 * t + 16, 200)))]
+        ty = [t for t in range(TY) if any(oky(p) for p in range(16 * t, min(16 * t + 16, 120)))]
         pr_rect.append((tx, ty))
         total += len(tx) * len(ty)
     assert len(keys) == total
