@@ -156,6 +156,43 @@ def test_bin_sort_empty_and_all_culled(G, O):
     assert keys.size == 0 and np.all(ranges == 0)
 
 
+@pytest.mark.parametrize("sx,sy", [(1, 1), (2, 2), (4, 4)])
+def test_empty_and_culled_scenes_render_background(G, sx, sy):
+    """No Gaussian (n = 0), all culled, or all below alpha_min: the image is
+    the background with T = 1, no blended fragment, zero 2D gradients; the
+    fused loss sees the same image."""
+    cam = S.camera(64, 48, 50.0, sx=sx, sy=sy)
+    cs = G.camera(cam)
+    bg = (0.25, 0.5, 0.75)
+    cfg = G.default_config(bg=bg)
+    Ws, Hs, _, _ = G.grid(cam)
+    s = S.splats(100, 64, 48, seed=9)
+    culled = dict(s, radius=np.zeros_like(s["radius"]))
+    faint = dict(s, opacity=np.full_like(s["opacity"], 0.002))
+    for name, rec, n in (("empty", torch.zeros((0, 12), device="cuda"), 0), ("culled", pack_splats(culled), 100),
+                         ("faint", pack_splats(faint), 100)):
+        _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
+        out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges, order=gpu_bin.order)
+        for c in range(3):
+            assert torch.all(out["rgb"][c] == bg[c]), name
+        assert torch.all(out["t_final"] == 1) and torch.all(out["depth"] == 0), name
+        assert torch.all(out["last_idx"] == 0) and torch.all(out["n_blended"] == 0), name
+        trgb = torch.full((3, Hs, Ws), 0.5, device="cuda")
+        tdep = torch.full((Hs, Ws), 2.0, device="cuda")
+        out2, dimg = G.gs_render_fwd_loss(cfg, cs, rec, n, vals, ranges, trgb, tdep, order=gpu_bin.order)
+        assert torch.equal(out2["rgb"], out["rgb"]), name
+        ref = (0.25 + 0.0 + 0.25) / 3 + 0.5 * 2.0   # mean |C - C*| over 3 channels + w_depth |0 - 2|
+        assert abs(float(dimg["loss"].item()) - ref) <= 1e-6, (name, float(dimg["loss"].item()))
+        if n > 0:
+            gdummy = dev({"means": np.zeros((n, 3), np.float32), "log_scales": np.zeros((n, 3), np.float32),
+                          "quats": np.zeros((n, 4), np.float32), "opacity_logit": np.zeros(n, np.float32),
+                          "rgb": np.zeros((n, 3), np.float32)})
+            g2 = G.gs_render_bwd(cfg, cs, gdummy, rec, vals, ranges, out["t_final"], out["last_idx"],
+                                 dimg["d_rgb"], dimg["d_depth"], mode=G.GS_MAP, order=gpu_bin.order)
+            assert torch.all(g2 == 0), name
+    assert G.gs_status_poll()[0] == G.GS_OK
+
+
 def test_bin_sort_capacity_overflow_is_reported(G):
     cam = S.camera(256, 256, 100.0)
     s = S.splats(4000, 256, 256, seed=10, sigma_px=(4, 20))
