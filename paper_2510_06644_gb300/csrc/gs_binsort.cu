@@ -89,10 +89,12 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_hist(gs_camera cam, float 
 // shared memory and write each row's exclusive prefix in place.
 __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int nrows, int ntiles,
                                               uint32_t* __restrict__ total) {
-    __shared__ uint32_t part[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int t = blockIdx.x * 32 + tx;
-    const int per = (nrows + 31) / 32;
+    // CTA: CS_TILES tiles x (1024 / CS_TILES) row groups of consecutive rows
+    constexpr int CS_TILES = 8, CS_GROUPS = 1024 / CS_TILES;
+    __shared__ uint32_t part[CS_GROUPS][CS_TILES + 1];
+    const int tx = threadIdx.x % CS_TILES, ty = threadIdx.x / CS_TILES;
+    const int t = blockIdx.x * CS_TILES + tx;
+    const int per = (nrows + CS_GROUPS - 1) / CS_GROUPS;
     const int r0 = min(nrows, ty * per), r1 = min(nrows, r0 + per);
     // rows in groups of 8 loads issued back to back (a dependent sum per
     // load would wait out an L2 round trip per row)
@@ -107,14 +109,30 @@ __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int n
         }
     part[ty][tx] = sum;
     __syncthreads();
-    if (ty == 0) {
-        uint32_t run = 0;
-        for (int k = 0; k < 32; ++k) {
-            const uint32_t v = part[k][tx];
-            part[k][tx] = run;
-            run += v;
+    // warp w < CS_TILES scans column w's CS_GROUPS partial sums (4 per lane)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < CS_TILES) {
+        uint32_t v[CS_GROUPS / 32];
+        uint32_t loc = 0;
+#pragma unroll
+        for (int k = 0; k < CS_GROUPS / 32; ++k) {
+            v[k] = part[lane * (CS_GROUPS / 32) + k][w];
+            loc += v[k];
         }
-        if (t < ntiles) total[t] = run;
+        uint32_t incl = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t run = incl - loc;
+#pragma unroll
+        for (int k = 0; k < CS_GROUPS / 32; ++k) {
+            part[lane * (CS_GROUPS / 32) + k][w] = run;
+            run += v[k];
+        }
+        const int tc = blockIdx.x * CS_TILES + w;
+        if (lane == 31 && tc < ntiles) total[tc] = incl;
     }
     __syncthreads();
     uint32_t run = part[ty][tx];
@@ -647,11 +665,11 @@ static gs_status launch_count(const gs_camera* cam, float alpha_min, int rec_dty
         gs_status s;
         if ((s = check_launch("k_tile_hist")) != GS_OK) return s;
         if (tail) {
-            k_col_scan_tail<<<(unsigned)((ntiles + 31) / 32), 1024, 0, st>>>(hist, (int)nb, ntiles, count, *tail);
+            k_col_scan_tail<<<(unsigned)((ntiles + 7) / 8), 1024, 0, st>>>(hist, (int)nb, ntiles, count, *tail);
             if (fused) *fused = true;
             return check_launch("k_col_scan_tail");
         }
-        k_col_scan<<<(unsigned)((ntiles + 31) / 32), 1024, 0, st>>>(hist, (int)nb, ntiles, count);
+        k_col_scan<<<(unsigned)((ntiles + 7) / 8), 1024, 0, st>>>(hist, (int)nb, ntiles, count);
         return check_launch("k_col_scan");
     }
     const unsigned nb = (unsigned)((n + BIN_THREADS - 1) / BIN_THREADS);
