@@ -255,6 +255,7 @@ def roofline(stage_ms, n, n_keys, P, blended, clk):
     dom = max(stage_ms, key=stage_ms.get)
     t = stage_ms[dom] * 1e-3
     traffic = None
+    issue = None
     try:
         import hashlib
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
@@ -262,6 +263,7 @@ def roofline(stage_ms, n, n_keys, P, blended, clk):
         src = os.path.join(ROOT, "paper_2510_06644_gb300", "csrc", ent["source"]) if ent else None
         if ent and hashlib.sha256(open(src, "rb").read()).hexdigest() == ent["source_sha256"]:
             traffic = ent["dram_bytes_per_launch"]
+            issue = ent.get("issue_active_pct")
     except Exception:
         traffic = None
     if dom in FLOP_PER_FRAGMENT:
@@ -270,9 +272,12 @@ def roofline(stage_ms, n, n_keys, P, blended, clk):
         peak = 152 * 128 * 2 * max_mhz * 1e6 / 1e12
         flops = FLOP_PER_FRAGMENT[dom] * blended
         ach = flops / t / 1e12
+        # issue_active_pct: ncu's smsp__issue_active of the same source (the
+        # share of issue slots the kernel uses: its practical ceiling)
         return {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                "algorithmic_flops": flops, "blended_fragments": blended, "avg_ms": stage_ms[dom]}
+                "algorithmic_flops": flops, "blended_fragments": blended, "avg_ms": stage_ms[dom],
+                "issue_active_pct": issue}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     alg = {
         "project": 56 * n + 48 * n,
