@@ -58,6 +58,25 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(t_ms, world, device="cuda"):
+    """Longest timed-region duration (ms) over the ranks: the job is done
+    when its slowest replica is.  One all-reduce on the host's process
+    group, outside every timed region."""
+    if world <= 1:
+        return float(t_ms)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_rate(units_per_rank, world, t_max_ms):
+    """Whole-job throughput: the units all replicas processed over the
+    slowest replica's time."""
+    return world * units_per_rank / (t_max_ms / 1e3)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -456,12 +475,8 @@ def run_ours(args):
     clk = clocks.stop()
     rast.check()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = t_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    iters_s = world * K / (t_max / 1e3)
+    t_max = max_over_ranks(t_ms, world)
+    iters_s = replica_rate(K, world, t_max)
     final_pose = pose.cpu().numpy()
 
     # ---- stage timings (eager, events on the launching stream) ----
@@ -524,8 +539,8 @@ def run_ours(args):
         out_h[6:].copy_(rast.dimg["loss"], non_blocking=True)
         ev2[i][1].record()
     torch.cuda.synchronize()
-    te = sum(a.elapsed_time(b) for a, b in ev2)
-    e2e = {"value": world * Ke / (te / 1e3), "unit": "iters/s",
+    te = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), world)
+    e2e = {"value": replica_rate(Ke, world, te), "unit": "iters/s",
            "h2d_bytes_per_step": trgb.numel() * 4 + tdep.numel() * 4, "d2h_bytes_per_step": 7 * 8}
 
     # kernels of one fused tracking iteration: k_project; k_tile_hist,
