@@ -51,6 +51,13 @@ def parse():
     return p.parse_args()
 
 
+def _pct(xs, q):
+    """q-th percentile (nearest rank) of a list."""
+    import math
+    ys = sorted(xs)
+    return ys[max(1, math.ceil(q / 100 * len(ys))) - 1]
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -155,7 +162,31 @@ def oracle_iteration(scene, true_img, cam, band_rows):
     return t3 - t0, (t1 - t0) + (t3 - t2) + per_pixel * (H / band_rows)
 
 
-def cpu_baseline(budget_s=20.0):
+def _oracle_replica(args):
+    """One single-threaded oracle replica (a spawned process): `iters` full
+    640x480/200k tracking iterations; returns their total seconds."""
+    iters, true_img = args
+    from synth import scenes as S
+    scene, _, start_cam = S.tracking_workload(N_G, W_IMG, H_IMG)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        oracle_iteration(scene, true_img, start_cam, H_IMG)
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(budget_s=20.0, replica_iters=2):
+    """The FP64 oracle as it stands (single-threaded C) on the host cores:
+    one core (median of up to 5 full iterations), then every core running an
+    independent replica (processes started with spawn), aggregate
+    iterations / the slowest replica's time."""
+    import multiprocessing as mp
     from oracle import oracle as O
     from synth import scenes as S
     O.build()
@@ -163,15 +194,22 @@ def cpu_baseline(budget_s=20.0):
     _, true_img = O.forward(scene, true_cam)
     times = []
     t_start = time.perf_counter()
-    while time.perf_counter() - t_start < budget_s and len(times) < 5:
+    while time.perf_counter() - t_start < budget_s / 2 and len(times) < 5:
         _, full = oracle_iteration(scene, true_img, start_cam, H_IMG)
         times.append(full)
     t = statistics.median(times)
-    return {"value": 1.0 / t, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} full 640x480/200k tracking iterations of the single-threaded FP64 C oracle "
-                      f"(projection, binning+sort, forward, L1 loss, backward, backward projection + pose); "
-                      f"median {t:.2f} s/iter",
-            "mpix_per_s": W_IMG * H_IMG / t / 1e6}
+    one = {"value": 1.0 / t, "unit": "iters/s", "cores": 1, "mpix_per_s": W_IMG * H_IMG / t / 1e6,
+           "sample": f"{len(times)} full iterations, median {t:.2f} s/iter"}
+    cores = host_cores()
+    slim = {"rgb": true_img["rgb"], "depth": true_img["depth"]}
+    with mp.get_context("spawn").Pool(cores) as pool:
+        wall = pool.map(_oracle_replica, [(replica_iters, slim)] * cores, chunksize=1)
+    v = cores * replica_iters / max(wall)
+    return {"value": v, "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} single-threaded FP64 C oracle replicas (spawned processes), {replica_iters} full "
+                      f"640x480/200k tracking iterations each (projection, binning+sort, forward, L1 loss, "
+                      f"backward, backward projection + pose); slowest replica {max(wall):.2f} s",
+            "mpix_per_s": W_IMG * H_IMG * v / 1e6, "one_core": one}
 
 
 def _graph_ms(fn, reps, flush):
@@ -265,6 +303,72 @@ def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pos
 FLOP_PER_FRAGMENT = {"render_fwd": 27, "render_fwd_loss": 27, "render_bwd": 67}
 
 
+def stage_bytes(n, n_keys, P):
+    """Algorithmic HBM bytes per launch of each stage (n Gaussians, n_keys
+    tile-Gaussian keys, P pixels): projection 56 read + 48 written per
+    Gaussian; binning 40 per Gaussian (two reads of the 20-byte geometry) and
+    28 per key (key written, then sorted: 8 read, 12 written); forward 48 per
+    staged key (its record) and 56 per pixel (24 written, 16 target read, 16
+    gradient written); backward 52 per staged key plus 24 of reductions per
+    (Gaussian, tile), 40 per pixel; backward projection 56 + 48 read, 8
+    written per Gaussian."""
+    return {"project": 104 * n, "bin_sort": 40 * n + 28 * n_keys, "render_fwd_loss": 48 * n_keys + 56 * P,
+            "render_bwd": 76 * n_keys + 40 * P, "project_bwd_pose_step": 112 * n}
+
+
+def hbm_fractions(stage_ms, n, n_keys, P, iter_ms):
+    """Each stage's and the whole iteration's algorithmic bytes per second
+    against the measured HBM copy bandwidth."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    b = stage_bytes(n, n_keys, P)
+    st = {k: {"bytes": b[k], "ms": stage_ms[k], "gbs": b[k] / (stage_ms[k] * 1e-3) / 1e9,
+              "frac": b[k] / (stage_ms[k] * 1e-3) / 1e9 / peak} for k in stage_ms}
+    tot = sum(b.values())
+    return {"peak_gbs": peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "stages": st,
+            "iteration": {"bytes": tot, "ms": iter_ms, "gbs": tot / (iter_ms * 1e-3) / 1e9,
+                          "frac": tot / (iter_ms * 1e-3) / 1e9 / peak}}
+
+
+def red_probe(gs, reps=10):
+    """Measured global float32 reduction throughput (G adds/s) of
+    gs_probe_red_f32: distinct addresses and 64 contended ones."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    nthr = sms * 8 * 256
+    res = {"threads": nthr}
+    for name, n_dst, per in (("distinct_gops", nthr, 64), ("contended64_gops", 64, 4)):
+        dst = torch.zeros(n_dst, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            gs.gs_probe_red_f32(dst, nthr, per)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            gs.gs_probe_red_f32(dst, nthr, per)
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = nthr * per / (a.elapsed_time(b) / reps * 1e-3) / 1e9
+    return res
+
+
+def committed_counters(stage):
+    """ncu counters of `stage`'s kernel from the committed capture
+    (profiles/traffic.json), or {} once its source has changed since."""
+    try:
+        import hashlib
+        ent = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(stage)
+        src = os.path.join(ROOT, "paper_2510_06644_gb300", "csrc", ent["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() == ent["source_sha256"]:
+            return ent
+    except Exception:
+        pass
+    return {}
+
+
 def roofline(stage_ms, n, n_keys, P, blended, clk):
     peaks = {}
     try:
@@ -273,18 +377,9 @@ def roofline(stage_ms, n, n_keys, P, blended, clk):
         pass
     dom = max(stage_ms, key=stage_ms.get)
     t = stage_ms[dom] * 1e-3
-    traffic = None
-    issue = None
-    try:
-        import hashlib
-        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ent = tr.get(dom)
-        src = os.path.join(ROOT, "paper_2510_06644_gb300", "csrc", ent["source"]) if ent else None
-        if ent and hashlib.sha256(open(src, "rb").read()).hexdigest() == ent["source_sha256"]:
-            traffic = ent["dram_bytes_per_launch"]
-            issue = ent.get("issue_active_pct")
-    except Exception:
-        traffic = None
+    ent = committed_counters(dom)
+    traffic = ent.get("dram_bytes_per_launch")
+    issue = ent.get("issue_active_pct")
     if dom in FLOP_PER_FRAGMENT:
         # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 (FMA)
         max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -298,11 +393,7 @@ def roofline(stage_ms, n, n_keys, P, blended, clk):
                 "algorithmic_flops": flops, "blended_fragments": blended, "avg_ms": stage_ms[dom],
                 "issue_active_pct": issue}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    alg = {
-        "project": 56 * n + 48 * n,
-        "bin_sort": 20 * n + 8 * n_keys * 2 + 12 * n_keys,
-        "project_bwd_pose_step": (56 + 48) * n + 8 * n,
-    }[dom]
+    alg = stage_bytes(n, n_keys, P)[dom]
     ach = alg / t / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
             "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
@@ -474,7 +565,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     rast.check()
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = sum(step_ms)
     t_max = max_over_ranks(t_ms, world)
     iters_s = replica_rate(K, world, t_max)
     final_pose = pose.cpu().numpy()
@@ -515,6 +607,16 @@ def run_ours(args):
     # ---- roofline of the dominant kernel ----
     blended = int(rast.img["n_blended"].long().sum().item())
     roof = roofline(stage_ms, n, n_keys, P, blended, clk)
+    hbm = hbm_fractions(stage_ms, n, n_keys, P, t_max / K)
+
+    # ---- the backward's global reductions against the probe's measured rate
+    # (tracking: at most six per (Gaussian, tile) after the block merge) ----
+    probe = red_probe(gs)
+    reds = 6 * n_keys
+    red_ach = reds / (stage_ms["render_bwd"] * 1e-3) / 1e9
+    atomics = {"kernel": "render_bwd", "red_per_launch_max": reds, "achieved_gops": red_ach, **probe,
+               "frac": red_ach / probe["distinct_gops"],
+               "l2_atomic_unit_active_pct": committed_counters("render_bwd").get("l2_atomic_active_pct")}
 
     # ---- variants: list reuse (N1) and the speedup breakdown (N4) ----
     variants = measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pose, pose0, adam, flush,
@@ -557,8 +659,11 @@ def run_ours(args):
                    "cuda_graph": graph is not None,
                    "l2": "flushed before every timed step (256 MB write, outside the step's events)",
                    "parallelism": f"replicas x{world}", "stage_ms": stage_ms,
+                   "step_ms_p50": statistics.median(step_ms), "step_ms_p99": _pct(step_ms, 99),
                    "pose_moved": float(np.abs(final_pose - pose0.cpu().numpy()).max())},
         "roofline": roof,
+        "hbm": hbm,
+        "atomics": atomics,
         "variants": variants,
         "e2e": e2e,
         "gpu_launches": launches_per_step * K,

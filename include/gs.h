@@ -450,6 +450,18 @@ gs_status gs_adam(int n_tensors, float* const* params, const float* const* grads
 gs_status gs_status_poll(gs_stream stream, int blocking, int* state);
 gs_status gs_status_reset(gs_stream stream);
 
+/* ---------------------------------------------------------------------- */
+/* Measurement probe (not a step of the method)                             */
+/* ---------------------------------------------------------------------- */
+/* Global float32 reduction throughput, the operation that merges the
+ * per-(Gaussian, tile) gradients into per-Gaussian arrays in the backward
+ * (Sec. 2.2 Step 4): thread t of n_threads adds 1.0f to dst[t % n_dst]
+ * per_thread times with red.global.add.f32 (n_dst >= n_threads: distinct
+ * addresses; small n_dst: contended).  dst: device float[n_dst], owned by the
+ * caller, accumulated into (not cleared).  Enqueued on `stream`; the caller
+ * times it.  GS_ERR_INVALID_ARG for a NULL dst or a non-positive count. */
+gs_status gs_probe_red_f32(float* dst, int64_t n_dst, int64_t n_threads, int32_t per_thread, gs_stream stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char* gs_last_error(void);
 

@@ -89,6 +89,7 @@ _SIGS = {
     "gs_pose_update": ([_P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, _P], C.c_int),
     "gs_adam": ([C.c_int, _P, _P, _P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float, _P, _P], C.c_int),
     "gs_status_poll": ([_P, C.c_int, _P], C.c_int),
+    "gs_probe_red_f32": ([_P, C.c_int64, C.c_int64, C.c_int32, _P], C.c_int),
     "gs_status_reset": ([_P], C.c_int),
     "gs_last_error": ([], C.c_char_p),
 }
@@ -483,6 +484,15 @@ def gs_adam(params, grads, ms, vs, state, lr=1e-3, beta1=0.9, beta2=0.999, eps=1
     cnt = (C.c_int64 * k)(*[int(t.numel()) for t in params])
     _check(lib().gs_adam(k, P_, G_, M_, V_, cnt, float(lr), float(beta1), float(beta2), float(eps), _ptr(state),
                          _stream(stream)), "gs_adam")
+
+
+def gs_probe_red_f32(dst, n_threads, per_thread, stream=None):
+    """Reduction-throughput probe: thread t of n_threads adds 1.0 to
+    dst[t % dst.numel()] per_thread times (float32 device tensor dst)."""
+    if dst.dtype != torch.float32:
+        raise ValueError("float32 dst expected")
+    _check(lib().gs_probe_red_f32(_ptr(dst), int(dst.numel()), int(n_threads), int(per_thread), _stream(stream)),
+           "gs_probe_red_f32")
 
 
 def gs_status_poll(blocking=True, stream=None):

@@ -105,3 +105,12 @@ def test_fused_entry_points_reject_bad_arguments_on_the_host(built_lib):
                                      ctypes.c_void_p(16), ctypes.c_void_p(16), None, None, None, None, None,
                                      None, None)
     assert rc == gs.GS_ERR_INVALID_ARG and b"target" in gs.lib().gs_last_error()
+
+
+def test_reduction_probe_rejects_bad_arguments_on_the_host(built_lib):
+    from paper_2510_06644_gb300 import gs
+    L = gs.lib()
+    assert L.gs_probe_red_f32(None, 16, 16, 1, None) == gs.GS_ERR_INVALID_ARG
+    fake = ctypes.c_void_p(16)  # never dereferenced: the counts are checked first
+    for n_dst, n_thr, per in ((0, 16, 1), (16, 0, 1), (16, 16, 0), (16, -5, 1)):
+        assert L.gs_probe_red_f32(fake, n_dst, n_thr, per, None) == gs.GS_ERR_INVALID_ARG
