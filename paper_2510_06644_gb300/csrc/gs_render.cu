@@ -38,13 +38,13 @@ namespace gs {
 #define R_THREADS 256            // largest CTA (16x16 tile)
 #define R_BATCH 1024             // largest batch of entries a tile stages at a time
 #define R_MASKW (R_BATCH / 32)   // mask words of a batch (at most 32: lane q holds word q)
-#define R_FWD_SMEM (R_BATCH * 64)       // forward staging budget per CTA (64 KB)
+#define R_FWD_SMEM (48 * 1024)          // forward staging budget per CTA (768 entries: 4 CTAs per SM)
 #define R_BWD_SMEM (70 * 1024)          // backward staging budget per CTA (512 entries)
 #define R_STEP 4                 // list entries evaluated side by side in the forward walk
 
 struct StagedSplat {
     float4 a;   // x, y, conic_a, conic_b
-    float4 b;   // conic_c, opacity, depth, unused
+    float4 b;   // conic_c, opacity, depth, log2(opacity)
     float4 c;   // r, g, b, unused
     int4 box;   // full-resolution integer box x0, x1, y0, y1
 };
@@ -125,6 +125,48 @@ __device__ __forceinline__ PixelMap map_pixel(const Grid& g, int tile, int lt) {
     return m;
 }
 
+// The 2D Gaussian at offset d = (dx, dy) from its mean (Eq. 2): with the
+// conic Q = [[ca, cb], [cb, cc]], (a, b) = Q d and q = d^T Q d = dx a + dy b,
+// the exponent is -q/2 and the backward's mean gradient is (a, b) times
+// dL/dexponent.  The operations are spelled out (no contraction left to the
+// compiler) so that every compositing kernel, forward and backward, computes
+// the same value and so takes the same blending decisions; q < 0 (a positive
+// exponent, from rounding) skips the fragment.
+struct Quad {
+    float a, b, q;
+};
+
+__device__ __forceinline__ Quad quad_form(float ca, float cb, float cc, float dx, float dy) {
+    Quad r;
+    r.a = __fmaf_rn(cb, dy, __fmul_rn(ca, dx));
+    r.b = __fmaf_rn(cc, dy, __fmul_rn(cb, dx));
+    r.q = __fmaf_rn(dx, r.a, __fmul_rn(dy, r.b));
+    return r;
+}
+
+// 2^x with the SFU's ex2 instruction.
+__device__ __forceinline__ float exp2_sfu(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// log2 of a staged opacity (the same instruction for every kernel that
+// stages an entry, so all of them see the same value).
+__device__ __forceinline__ float log2_opacity(float op) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(op));
+    return y;
+}
+
+// -log2(e) / 2: op e^(-q/2) = 2^(log2(op) - q log2(e) / 2).
+#define R_NEG_HALF_LOG2E (-0.721347520444481703680f)
+
+// Unclamped alpha op e^(-q/2) of a fragment, one FMA and one ex2.
+__device__ __forceinline__ float raw_alpha(float q, float log2_op) {
+    return exp2_sfu(__fmaf_rn(q, R_NEG_HALF_LOG2E, log2_op));
+}
+
 // Pixel box of a staged Gaussian: its integer 3-sigma box (the definition of
 // which pixels see it), shrunk to the pixels whose centre lies in the
 // axis-aligned bounding box of the ellipse where alpha can reach alpha_min,
@@ -156,7 +198,7 @@ __device__ __forceinline__ int4 pixel_box(const Splat& v, float alpha_min) {
 
 __device__ __forceinline__ void fill_staged(const Splat& v, float alpha_min, StagedSplat& s) {
     s.a = make_float4(v.x, v.y, v.ca, v.cb);
-    s.b = make_float4(v.cc, v.op, v.depth, 0.f);
+    s.b = make_float4(v.cc, v.op, v.depth, log2_opacity(v.op));
     s.c = make_float4(v.r, v.g, v.b, 0.f);
     s.box = pixel_box(v, alpha_min);
 }
@@ -208,27 +250,16 @@ __device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit,
     return mine;
 }
 
-// Exponent of the 2D Gaussian (Eq. 2) at offset (dx, dy) from its mean, with
-// conic (ca, cb, cc).  The operations are spelled out (no contraction left to
-// the compiler) so that every compositing kernel, forward and backward,
-// computes the same value and so takes the same blending decisions.
-__device__ __forceinline__ float gauss_power(float ca, float cb, float cc, float dx, float dy) {
-    const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), xy = __fmul_rn(dx, dy);
-    const float q = __fmaf_rn(cc, yy, __fmul_rn(ca, xx));
-    return __fmaf_rn(-cb, xy, __fmul_rn(-0.5f, q));
-}
-
 // Alpha of a staged Gaussian at the pixel (Eq. 2), or -1 when the pixel is
 // outside its box or the exponent is positive (the fragment is skipped).
 __device__ __forceinline__ float frag_alpha(const StagedSplat& s, const PixelMap& m, float pxc, float pyc,
                                            float alpha_max) {
     const int4 box = s.box;
     const float4 A = s.a;
-    const float cc = s.b.x, op = s.b.y;
-    const float dx = pxc - A.x, dy = pyc - A.y;
-    const float power = gauss_power(A.z, A.w, cc, dx, dy);
-    const float alpha = fminf(alpha_max, op * __expf(power));
-    const bool in = m.px >= box.x && m.px <= box.y && m.py >= box.z && m.py <= box.w && !(power > 0.f);
+    const float cc = s.b.x, lop = s.b.w;
+    const Quad Qd = quad_form(A.z, A.w, cc, pxc - A.x, pyc - A.y);
+    const float alpha = fminf(alpha_max, raw_alpha(Qd.q, lop));
+    const bool in = m.px >= box.x && m.px <= box.y && m.py >= box.z && m.py <= box.w && !(Qd.q < 0.f);
     return in ? alpha : -1.f;
 }
 
@@ -460,7 +491,7 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
 // and whether the fragment was blended (inside the box, exponent <= 0,
 // alpha >= alpha_min, before the pixel's last blended position).
 struct FragGeo {
-    float dx, dy, gk, raw, alpha;
+    float dx, dy, a, b, q, raw, alpha;  // offset, Q d, d^T Q d, alphas
     bool contrib;
 };
 
@@ -469,15 +500,17 @@ __device__ __forceinline__ FragGeo frag_geo(const StagedSplat& s, const PixelMap
     FragGeo f;
     const int4 box = s.box;
     const float4 A = s.a;
-    const float cc = s.b.x, op = s.b.y;
+    const float cc = s.b.x, lop = s.b.w;
     f.dx = pxc - A.x;
     f.dy = pyc - A.y;
-    const float power = gauss_power(A.z, A.w, cc, f.dx, f.dy);
-    f.gk = __expf(power);
-    f.raw = op * f.gk;
+    const Quad Qd = quad_form(A.z, A.w, cc, f.dx, f.dy);
+    f.a = Qd.a;
+    f.b = Qd.b;
+    f.q = Qd.q;
+    f.raw = raw_alpha(Qd.q, lop);
     f.alpha = fminf(cfg.alpha_max, f.raw);
     f.contrib = before_last && m.px >= box.x && m.px <= box.y && m.py >= box.z && m.py <= box.w &&
-                !(power > 0.f) && !(f.alpha < cfg.alpha_min);
+                !(Qd.q < 0.f) && !(f.alpha < cfg.alpha_min);
     return f;
 }
 
@@ -571,15 +604,14 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
                 f[5] = w * gD;
             }
             if (!(fg.raw > cfg.alpha_max)) {  // the clamp passes no gradient
-                const float4 Aq = sp[e].a;
-                const float cc = sp[e].b.x;
-                if (MODE == GS_MAP) f[5] = fg.gk * dLda;
-                const float dp = alpha * dLda;
+                // dalpha/dopacity = e^(-q/2) (mapping only)
+                if (MODE == GS_MAP) f[5] = exp2_sfu(__fmul_rn(fg.q, R_NEG_HALF_LOG2E)) * dLda;
+                const float dp = alpha * dLda;  // dL/d(exponent)
                 f[2] = -0.5f * fg.dx * fg.dx * dp;
                 f[3] = -fg.dx * fg.dy * dp;
                 f[4] = -0.5f * fg.dy * fg.dy * dp;
-                f[0] = (Aq.z * fg.dx + Aq.w * fg.dy) * dp;
-                f[1] = (Aq.w * fg.dx + cc * fg.dy) * dp;
+                f[0] = fg.a * dp;
+                f[1] = fg.b * dp;
             }
         };
         auto merge = [&](int e, float (&f)[NS]) {
@@ -688,7 +720,7 @@ __device__ __forceinline__ void ep_stage(const void* __restrict__ splats, const 
         const uint32_t id = __ldg(ids + e);
         const Splat v = load_splat<DT>(splats, id);
         S.a[e] = make_float4(v.x, v.y, v.ca, v.cb);
-        S.b[e] = make_float4(v.cc, v.op, v.depth, 0.f);
+        S.b[e] = make_float4(v.cc, v.op, v.depth, log2_opacity(v.op));
         S.box[e] = pixel_box(v, alpha_min);
         S.c[e] = make_float4(v.r, v.g, v.b, 0.f);
         if (sid) sid[e] = id;
@@ -792,9 +824,9 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
                 if (e >= 0) {
                     const float4 A = S.a[e];
                     const float4 Bv = S.b[e];
-                    const float power = gauss_power(A.z, A.w, Bv.x, pxc - A.x, pyc - A.y);
-                    const float al = fminf(cfg.alpha_max, Bv.y * __expf(power));
-                    if (!(power > 0.f)) alpha = al;
+                    const Quad Qd = quad_form(A.z, A.w, Bv.x, pxc - A.x, pyc - A.y);
+                    const float al = fminf(cfg.alpha_max, raw_alpha(Qd.q, Bv.w));
+                    if (!(Qd.q < 0.f)) alpha = al;
                 }
                 const bool valid = alpha >= cfg.alpha_min;
                 if (__ballot_sync(0xffffffffu, valid) == 0u) return;
@@ -980,20 +1012,20 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
             // has the entries of lanes < l behind it
             auto differentiate = [&](int k) {
                 const int e = lane < k ? cbuf[lane] : -1;
-                float4 A = make_float4(0.f, 0.f, 0.f, 0.f), Bv = A, Cc = A;
-                float dx = 0.f, dy = 0.f, gk = 0.f, raw = 0.f, alpha = -1.f;
+                float4 Bv = make_float4(0.f, 0.f, 0.f, 0.f), Cc = Bv;
+                float dx = 0.f, dy = 0.f, raw = 0.f, alpha = -1.f;
+                Quad Qd = {0.f, 0.f, 0.f};
                 bool valid = false;
                 if (e >= 0) {
-                    A = S.a[e];
+                    const float4 A = S.a[e];
                     Bv = S.b[e];
                     Cc = S.c[e];
                     dx = pxc - A.x;
                     dy = pyc - A.y;
-                    const float power = gauss_power(A.z, A.w, Bv.x, dx, dy);
-                    gk = __expf(power);
-                    raw = Bv.y * gk;
+                    Qd = quad_form(A.z, A.w, Bv.x, dx, dy);
+                    raw = raw_alpha(Qd.q, Bv.w);
                     alpha = fminf(cfg.alpha_max, raw);
-                    valid = !(power > 0.f) && !(alpha < cfg.alpha_min);
+                    valid = !(Qd.q < 0.f) && !(alpha < cfg.alpha_min);
                 }
                 if (__ballot_sync(0xffffffffu, valid) == 0u) return;
                 const float f = valid ? 1.f - alpha : 1.f;
@@ -1028,13 +1060,13 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
                         ga[5] = w * qd;
                     }
                     if (!(raw > cfg.alpha_max)) {  // the clamp passes no gradient
-                        if (MODE == GS_MAP) ga[5] = gk * dLda;
+                        if (MODE == GS_MAP) ga[5] = exp2_sfu(__fmul_rn(Qd.q, R_NEG_HALF_LOG2E)) * dLda;
                         const float dp = alpha * dLda;
                         ga[2] = -0.5f * dx * dx * dp;
                         ga[3] = -dx * dy * dp;
                         ga[4] = -0.5f * dy * dy * dp;
-                        ga[0] = (A.z * dx + A.w * dy) * dp;
-                        ga[1] = (A.w * dx + Bv.x * dy) * dp;
+                        ga[0] = Qd.a * dp;
+                        ga[1] = Qd.b * dp;
                     }
 #pragma unroll
                     for (int q = 0; q < NF; ++q)
@@ -1098,12 +1130,19 @@ __global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
 
 using namespace gs;
 
-// Entries a tile stages per batch: 256, halved while the CTA's tiles would
-// need more than `budget` bytes of shared memory.
+// Entries a tile stages per batch: R_BATCH, halved while the CTA's tiles
+// would need more than `budget` bytes of shared memory.
 static int group_batch(int gpc, int bytes_per_entry, int budget) {
     int B = R_BATCH;
     while (B > 32 && gpc * B * bytes_per_entry > budget) B >>= 1;
     return B;
+}
+
+// The forward's batch: the most entries (a multiple of 32, at most R_BATCH)
+// whose records fit the forward budget for the CTA's gpc tiles.
+static int fwd_batch(int gpc) {
+    const int B = R_FWD_SMEM / (gpc * (int)sizeof(StagedSplat)) / 32 * 32;
+    return B < 32 ? 32 : (B > R_BATCH ? R_BATCH : B);
 }
 
 // Raises a kernel's dynamic shared-memory limit once per device and
@@ -1135,7 +1174,7 @@ static gs_status launch_fwd(const gs_config& cfg, const Grid& g, const void* spl
     }
     const int gpc = R_THREADS / tile_threads(g);
     const unsigned nt = (unsigned)((ntiles + gpc - 1) / gpc);
-    const int B = group_batch(gpc, (int)sizeof(StagedSplat), R_FWD_SMEM);
+    const int B = fwd_batch(gpc);
     const size_t smem = (size_t)gpc * B * sizeof(StagedSplat);
     gs_status s;
     if (gpc == 1) {
