@@ -585,12 +585,13 @@ def run_ours(args):
         gs.gs_bin_sort(cs, rast.splats, n, rast.capacity, rast.rec_dtype, ws=rast._sort_ws(cs), keys=rast.keys,
                        vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges, order=rast.order, cfg=rast.cfg)
         evs[2].record()
+        bm = rast._masks(cs)
         gs.gs_render_fwd_loss(rast.cfg, cs, rast.splats, n, rast.vals, rast.ranges, trgb, tdep, rast.rec_dtype,
-                              out=rast.img, dimg=rast.dimg, order=rast.order)
+                              out=rast.img, dimg=rast.dimg, order=rast.order, masks=bm)
         evs[3].record()
         gs.gs_render_bwd(rast.cfg, cs, gd, rast.splats, rast.vals, rast.ranges, rast.img["t_final"],
                          rast.img["last_idx"], rast.dimg["d_rgb"], rast.dimg["d_depth"], gs.GS_TRACK,
-                         rast.rec_dtype, grad2d=rast.grad2d, order=rast.order)
+                         rast.rec_dtype, grad2d=rast.grad2d, order=rast.order, masks=bm)
         evs[4].record()
         gs.gs_project_bwd_step(rast.cfg, cs, gd, rast.grad2d, rast.pose, gs.pose_step(pose, adam, lr_t, lr_r),
                                score=rast.score, ws=rast._bwd_ws(cs, gd))

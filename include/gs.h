@@ -240,12 +240,21 @@ gs_status gs_bin_count(const gs_config* cfg, const gs_camera* cam, int rec_dtype
  * [Hs][Ws] (list position + 1 of the last blended fragment, relative to the
  * tile's first entry; 0 if none), n_blended [Hs][Ws] (may be NULL: number of
  * fragments blended into the pixel).  vals, tile_ranges and tile_order (may be
- * NULL: tiles in id order) come from gs_bin_sort with the same camera. */
+ * NULL: tiles in id order) come from gs_bin_sort with the same camera.
+ * blend_masks (may be NULL): device uint32 array of gs_blend_mask_words
+ * words that receives, for frames rendered pixel-parallel (a stride of 1),
+ * which list entries each warp of each tile blended; gs_render_bwd given the
+ * same array skips the entries no pixel of a warp blended (the same result,
+ * fewer visits).  Frames with both strides >= 2 leave it untouched. */
 gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype,
                         const void* splats, int64_t n, const uint32_t* vals,
                         const uint32_t* tile_ranges, const uint32_t* tile_order, float* rgb,
                         float* depth, float* t_final, uint32_t* last_idx, uint32_t* n_blended,
-                        gs_stream stream);
+                        uint32_t* blend_masks, gs_stream stream);
+
+/* Words of a blend-mask array for `cam`'s tile grid and lists of up to
+ * key_capacity entries (host arithmetic; 0 for an invalid camera). */
+size_t gs_blend_mask_words(const gs_camera* cam, int64_t key_capacity);
 
 /* ---------------------------------------------------------------------- */
 /* A-6 Loss (Sec. 4.1, Eq. 6)                                               */
@@ -269,7 +278,7 @@ gs_status gs_render_fwd_loss(const gs_config* cfg, const gs_camera* cam, int rec
                              const void* splats, int64_t n, const uint32_t* vals,
                              const uint32_t* tile_ranges, const uint32_t* tile_order, float* rgb,
                              float* depth, float* t_final, uint32_t* last_idx,
-                             uint32_t* n_blended, const float* target_rgb,
+                             uint32_t* n_blended, uint32_t* blend_masks, const float* target_rgb,
                              const float* target_depth, float* d_rgb, float* d_depth,
                              double* loss_out, gs_stream stream);
 
@@ -288,12 +297,13 @@ gs_status gs_render_fwd_loss(const gs_config* cfg, const gs_camera* cam, int rec
  * grad2d [n][12] float (GS_GRAD2D_STRIDE layout): zeroed by this call.
  * mode GS_TRACK skips dL/dopacity and dL/drgb (not needed for the pose).
  * If grads, pose_grad6 or score_terms is non-NULL, gs_project_bwd runs as
- * well on the same stream (same workspace). */
+ * well on the same stream (same workspace).  blend_masks (may be NULL) must
+ * come from the forward call that produced t_final and last_idx. */
 gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
                         int rec_dtype, const void* splats, const uint32_t* vals,
                         const uint32_t* tile_ranges, const uint32_t* tile_order,
-                        const float* t_final,
-                        const uint32_t* last_idx, const float* d_rgb, const float* d_depth,
+                        const float* t_final, const uint32_t* last_idx,
+                        const uint32_t* blend_masks, const float* d_rgb, const float* d_depth,
                         int mode, float* grad2d, gs_grads* grads, double* pose_grad6,
                         float* score_terms, void* workspace, size_t* workspace_bytes,
                         gs_stream stream);

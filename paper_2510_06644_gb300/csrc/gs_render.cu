@@ -200,7 +200,12 @@ __device__ __forceinline__ void fill_staged(const Splat& v, float alpha_min, Sta
     s.a = make_float4(v.x, v.y, v.ca, v.cb);
     s.b = make_float4(v.cc, v.op, v.depth, log2_opacity(v.op));
     s.c = make_float4(v.r, v.g, v.b, 0.f);
-    s.box = pixel_box(v, alpha_min);
+    // the box as (x0, x1 - x0, y0, y1 - y0), clamped far outside any image;
+    // an empty box never matches
+    const int4 bx = pixel_box(v, alpha_min);
+    const int lo = -(1 << 28), hi = 1 << 28;
+    const int x0 = max(bx.x, lo), x1 = min(bx.y, hi), y0 = max(bx.z, lo), y1 = min(bx.w, hi);
+    s.box = x1 < x0 || y1 < y0 ? make_int4(hi, 0, hi, 0) : make_int4(x0, x1 - x0, y0, y1 - y0);
 }
 
 // Stages list entries [0, n_in) of `ids` into sp[] (and their ids into sid[]
@@ -242,7 +247,7 @@ __device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit,
         bool hit = false;
         if (q < words && e < limit) {
             const int4 box = sp[e].box;
-            hit = !(box.y < m.wx0 || box.x > m.wx1 || box.w < m.wy0 || box.z > m.wy1);
+            hit = !(box.x + box.y < m.wx0 || box.x > m.wx1 || box.z + box.w < m.wy0 || box.z > m.wy1);
         }
         const unsigned w = __ballot_sync(0xffffffffu, hit);
         if (lane == q) mine = w;
@@ -259,7 +264,8 @@ __device__ __forceinline__ float frag_alpha(const StagedSplat& s, const PixelMap
     const float cc = s.b.x, lop = s.b.w;
     const Quad Qd = quad_form(A.z, A.w, cc, pxc - A.x, pyc - A.y);
     const float alpha = fminf(alpha_max, raw_alpha(Qd.q, lop));
-    const bool in = m.px >= box.x && m.px <= box.y && m.py >= box.z && m.py <= box.w && !(Qd.q < 0.f);
+    const bool in = (unsigned)(m.px - box.x) <= (unsigned)box.y && (unsigned)(m.py - box.z) <= (unsigned)box.w &&
+                    !(Qd.q < 0.f);
     return in ? alpha : -1.f;
 }
 
@@ -276,7 +282,17 @@ struct FwdOut {
     float* d_rgb;
     float* d_depth;
     double* loss;
+    uint32_t* bmask;    // NULL: no blend masks
 };
+
+// Blend masks: for each tile, each of its warps (at most 8) and each run of
+// 32 list entries, the entries one of the warp's pixels blended in the
+// forward (bit e of word q: entry 32 q + e of the tile's list).  Tile t with
+// list [s, s + len) owns 8 ceil(len / 32) words from word 8 (floor(s / 32) +
+// t) on, warp w's ceil(len / 32) words consecutive; tiles never overlap.
+__host__ __device__ inline size_t blend_mask_base(int tile, uint32_t start) {
+    return (size_t)8 * ((size_t)(start >> 5) + (size_t)tile);
+}
 
 // Writes sampled pixel (i, j)'s results; with the fused loss also its image
 // gradient (the formulas of k_loss_l1 on the same float values) and returns
@@ -337,17 +353,26 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
     uint32_t last = 0, nb = 0;
     bool done = !m.inside;
     const int words = G.B / 32;
+    const int lane = threadIdx.x & 31;
+    // the warp's blend-mask words (word w at O.bmask[bm_off + w])
+    const uint32_t bm_off = (uint32_t)blend_mask_base(tile, start) + (uint32_t)(G.lt >> 5) * ((end - start + 31) >> 5);
     for (uint32_t b = start; b < end; b += G.B) {
-        if (group_count(G, done) == G.TT) break;
+        // from the second batch on: a barrier (the previous batch's records
+        // are no longer read) that also ends the tile once every pixel stopped
+        if (b != start && group_count(G, done) == G.TT) break;
         const int n_in = (int)min((uint32_t)G.B, end - b);
         stage_batch<DT, KST>(splats, vals + b, n_in, G.lt, G.TT, cfg.alpha_min, sp, nullptr);
         group_sync(G);
+        // lane q clears word q of the batch, then stores it once processed
+        const uint32_t bm_w = bm_off + ((b - start) >> 5);
+        if (O.bmask && lane < ((n_in + 31) >> 5)) O.bmask[bm_w + lane] = 0u;
         if (!__all_sync(0xffffffffu, done)) {
             const unsigned mword = warp_masks(sp, n_in, words, m);
             const uint32_t base = b - start;
 #pragma unroll 1
             for (int q = 0; q < words; ++q) {
                 unsigned mq = __shfl_sync(0xffffffffu, mword, q);
+                unsigned bq = 0u;  // entries of word q this pixel blended
                 while (mq) {
                     // R_STEP entries per step: their alphas do not depend on
                     // T, so they are evaluated side by side; the blends then
@@ -384,13 +409,17 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
                         T = ok ? Tn : T;
                         nb += ok ? 1u : 0u;
                         last = ok ? base + (uint32_t)e + 1u : last;
+                        bq |= ok ? 1u << (e & 31) : 0u;
                     }
                     if (__all_sync(0xffffffffu, done)) break;
+                }
+                if (O.bmask) {  // (words past the batch's entries stay clear)
+                    bq = __reduce_or_sync(0xffffffffu, bq);
+                    if (lane == q && bq != 0u) O.bmask[bm_w + q] = bq;
                 }
                 if (__all_sync(0xffffffffu, done)) break;
             }
         }
-        group_sync(G);
     }
     float lpart = 0.f;
     if (m.inside) lpart = write_pixel(cfg, g, O, m.i, m.j, C0, C1, C2, D, T, last, nb);
@@ -491,7 +520,7 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
 // and whether the fragment was blended (inside the box, exponent <= 0,
 // alpha >= alpha_min, before the pixel's last blended position).
 struct FragGeo {
-    float dx, dy, a, b, q, raw, alpha;  // offset, Q d, d^T Q d, alphas
+    float dx, dy, a, b, q, raw, alpha, dep;  // offset, Q d, d^T Q d, alphas, depth
     bool contrib;
 };
 
@@ -500,7 +529,9 @@ __device__ __forceinline__ FragGeo frag_geo(const StagedSplat& s, const PixelMap
     FragGeo f;
     const int4 box = s.box;
     const float4 A = s.a;
-    const float cc = s.b.x, lop = s.b.w;
+    const float4 Bv = s.b;
+    const float cc = Bv.x, lop = Bv.w;
+    f.dep = Bv.z;
     f.dx = pxc - A.x;
     f.dy = pyc - A.y;
     const Quad Qd = quad_form(A.z, A.w, cc, f.dx, f.dy);
@@ -509,21 +540,22 @@ __device__ __forceinline__ FragGeo frag_geo(const StagedSplat& s, const PixelMap
     f.q = Qd.q;
     f.raw = raw_alpha(Qd.q, lop);
     f.alpha = fminf(cfg.alpha_max, f.raw);
-    f.contrib = before_last && m.px >= box.x && m.px <= box.y && m.py >= box.z && m.py <= box.w &&
+    f.contrib = before_last && (unsigned)(m.px - box.x) <= (unsigned)box.y &&
+                (unsigned)(m.py - box.z) <= (unsigned)box.w &&
                 !(Qd.q < 0.f) && !(f.alpha < cfg.alpha_min);
     return f;
 }
 
 // Backward compositing of group G's tile, pixel-parallel (smem: the CTA's
 // staging, id and accumulator buffers for gpc groups of G.B entries;
-// s_max_all: one word per group).
+// s_max_all: one word per warp).
 template <int DT, int MODE, int KST>
 __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
                                        const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                                        const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
-                                       float* __restrict__ grad2d, const Group& G, unsigned char* smem,
-                                       uint32_t* s_max_all) {
+                                       float* __restrict__ grad2d, const uint32_t* __restrict__ bmask,
+                                       const Group& G, unsigned char* smem, uint32_t* s_max_all) {
     constexpr int NS = Slots<MODE>::N;
     constexpr int LOG = Slots<MODE>::LOG;
     constexpr int SHIFT = 5 - LOG;  // lanes per slot = 1 << SHIFT
@@ -535,7 +567,7 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
     StagedSplat* sp = sp_all + G.gi * G.B;
     uint32_t* sid = sid_all + G.gi * G.B;
     float(*acc)[NS] = acc_all + G.gi * G.B;
-    uint32_t& s_max = s_max_all[G.gi];
+    uint32_t* s_wl = s_max_all + G.gi * (G.TT >> 5);  // the group's per-warp maxima
     const int tile = G.tile;
     const PixelMap m = map_pixel(g, tile, G.lt);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
@@ -560,22 +592,34 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
     uint32_t wlast = last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
-    if (G.lt == 0) s_max = 0;
+    if (lane == 0) s_wl[G.lt >> 5] = wlast;
     group_sync(G);
-    if (lane == 0) atomicMax(&s_max, wlast);
-    group_sync(G);
-    const uint32_t end_eff = start + s_max;
+    uint32_t s_max = 0;
+    for (int w = 0; w < (G.TT >> 5); ++w) s_max = max(s_max, s_wl[w]);
     const int words = G.B / 32;
-    for (uint32_t hi = end_eff; hi > start;) {
-        const uint32_t lo = hi - start > (uint32_t)G.B ? hi - G.B : start;
+    const uint32_t* bm_in =
+        bmask ? bmask + blend_mask_base(tile, start) + (size_t)(G.lt >> 5) * ((end - start + 31) >> 5) : nullptr;
+    // batches [start + k B, start + (k + 1) B) from the last one holding a
+    // blended entry back to the first (whole mask words for every batch)
+    for (int k = (int)((s_max + G.B - 1) / G.B) - 1; k >= 0; --k) {
+        const uint32_t base_pos = (uint32_t)k * G.B;
+        const uint32_t lo = start + base_pos, hi = start + min(s_max, base_pos + G.B);
         const int n_in = (int)(hi - lo);
         stage_batch<DT, KST>(splats, vals + lo, n_in, G.lt, G.TT, cfg.alpha_min, sp, sid);
         for (int q = G.lt; q < G.B * NS; q += G.TT) (&acc[0][0])[q] = 0.f;
         group_sync(G);
-        const uint32_t base_pos = lo - start;
-        // entries at or beyond the warp's furthest blended position are skipped
+        // entries at or beyond the warp's furthest blended position are
+        // skipped; with the forward's blend masks, so is every entry none of
+        // the warp's pixels blended
         const int wlimit = (int)min((uint32_t)n_in, wlast > base_pos ? wlast - base_pos : 0u);
-        const unsigned mword = warp_masks(sp, wlimit, words, m);
+        unsigned mword;
+        if (bm_in) {
+            const int q = lane;
+            mword = q * 32 < wlimit ? __ldg(bm_in + (base_pos >> 5) + q) : 0u;
+            if (q * 32 < wlimit && wlimit - q * 32 < 32) mword &= (1u << (wlimit - q * 32)) - 1u;
+        } else {
+            mword = warp_masks(sp, wlimit, words, m);
+        }
         // back to front over the fragments before `last`; T_k recovered by
         // division (Eq. 5), A the normalised suffix sums of colour and depth
         auto back = [&](int e, const FragGeo& fg, float (&f)[NS]) {
@@ -589,12 +633,13 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
             T = __fdividef(T, 1.f - alpha);
             const float w = alpha * T;
             const float4 Cc = sp[e].c;
-            const float dep = sp[e].b.z;
-            const float dLda = T * ((Cc.x - A0) * gC0 + (Cc.y - A1) * gC1 + (Cc.z - A2) * gC2 + (dep - AD) * gD);
-            A0 = alpha * Cc.x + (1.f - alpha) * A0;
-            A1 = alpha * Cc.y + (1.f - alpha) * A1;
-            A2 = alpha * Cc.z + (1.f - alpha) * A2;
-            AD = alpha * dep + (1.f - alpha) * AD;
+            const float d0 = Cc.x - A0, d1 = Cc.y - A1, d2 = Cc.z - A2, dD = fg.dep - AD;
+            const float dLda = T * (d0 * gC0 + d1 * gC1 + d2 * gC2 + dD * gD);
+            // suffix sums behind the next entry: alpha c + (1 - alpha) A
+            A0 = __fmaf_rn(alpha, d0, A0);
+            A1 = __fmaf_rn(alpha, d1, A1);
+            A2 = __fmaf_rn(alpha, d2, A2);
+            AD = __fmaf_rn(alpha, dD, AD);
             if (MODE == GS_MAP) {
                 f[6] = w * gD;
                 f[7] = w * gC0;
@@ -607,9 +652,10 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
                 // dalpha/dopacity = e^(-q/2) (mapping only)
                 if (MODE == GS_MAP) f[5] = exp2_sfu(__fmul_rn(fg.q, R_NEG_HALF_LOG2E)) * dLda;
                 const float dp = alpha * dLda;  // dL/d(exponent)
-                f[2] = -0.5f * fg.dx * fg.dx * dp;
-                f[3] = -fg.dx * fg.dy * dp;
-                f[4] = -0.5f * fg.dy * fg.dy * dp;
+                const float hx = -0.5f * dp * fg.dx, hy = -0.5f * dp * fg.dy;
+                f[2] = hx * fg.dx;
+                f[3] = (hx + hx) * fg.dy;
+                f[4] = hy * fg.dy;
                 f[0] = fg.a * dp;
                 f[1] = fg.b * dp;
             }
@@ -654,8 +700,7 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
             const int col = slot_col<MODE>(q % NS);
             if (v != 0.f && col >= 0) atomicAdd(grad2d + (size_t)sid[q / NS] * GS_GRAD2D_STRIDE + col, v);
         }
-        group_sync(G);
-        hi = lo;
+        if (k > 0) group_sync(G);  // the next batch reuses the buffers
     }
 }
 
@@ -665,13 +710,13 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 3 : 2)
                  const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
                  const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                  const float* __restrict__ d_rgb, const float* __restrict__ d_depth, float* __restrict__ grad2d,
-                 int B) {
+                 const uint32_t* __restrict__ bmask, int B) {
     extern __shared__ __align__(16) unsigned char r_smem[];
     __shared__ uint32_t s_max_all[R_THREADS / 32];
     const Group G = make_group(g, order, B, blockIdx.x);
     if (G.tile < 0) return;
-    bwd_pp<DT, MODE, KST>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, G, r_smem,
-                          s_max_all);
+    bwd_pp<DT, MODE, KST>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, bmask, G,
+                          r_smem, s_max_all);
 }
 
 // ---------------------------------------------------------------------------
@@ -1199,7 +1244,7 @@ template <int DT, int MD>
 static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* splats, const uint32_t* vals,
                             const uint32_t* ranges, const uint32_t* order, const float* t_final,
                             const uint32_t* last_idx, const float* d_rgb, const float* d_depth, float* grad2d,
-                            cudaStream_t st) {
+                            const uint32_t* bmask, cudaStream_t st) {
     const int ntiles = g.TX * g.TY;
     if (g.tw * g.th <= 64) {
         gs_status s;
@@ -1227,11 +1272,11 @@ static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* spl
     if (gpc == 1) {
         if ((s = smem_once((const void*)k_render_bwd<DT, MD, 1>, id, R_BWD_SMEM)) != GS_OK) return s;
         k_render_bwd<DT, MD, 1><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, t_final,
-                                                             last_idx, d_rgb, d_depth, grad2d, B);
+                                                             last_idx, d_rgb, d_depth, grad2d, bmask, B);
     } else {
         if ((s = smem_once((const void*)k_render_bwd<DT, MD, 4>, id + 1, R_BWD_SMEM)) != GS_OK) return s;
         k_render_bwd<DT, MD, 4><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, t_final,
-                                                             last_idx, d_rgb, d_depth, grad2d, B);
+                                                             last_idx, d_rgb, d_depth, grad2d, bmask, B);
     }
     return check_launch("k_render_bwd");
 }
@@ -1254,12 +1299,14 @@ static gs_status render_checks(const gs_config* cfg, const gs_camera* cam, int r
 extern "C" gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats,
                                    int64_t n, const uint32_t* vals, const uint32_t* tile_ranges,
                                    const uint32_t* tile_order, float* rgb, float* depth, float* t_final,
-                                   uint32_t* last_idx, uint32_t* n_blended, gs_stream stream) {
+                                   uint32_t* last_idx, uint32_t* n_blended, uint32_t* blend_masks,
+                                   gs_stream stream) {
     gs_status s;
     if ((s = render_checks(cfg, cam, rec_dtype, splats, n)) != GS_OK) return s;
     if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
         return set_error(GS_ERR_INVALID_ARG, "an image or range pointer is NULL");
-    const FwdOut O = {rgb, depth, t_final, last_idx, n_blended, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const FwdOut O = {rgb, depth, t_final, last_idx, n_blended, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      blend_masks};
     return dispatch_fwd(*cfg, make_grid(*cam), rec_dtype, splats, vals, tile_ranges, tile_order, O,
                         (cudaStream_t)stream);
 }
@@ -1268,8 +1315,8 @@ extern "C" gs_status gs_render_fwd_loss(const gs_config* cfg, const gs_camera* c
                                         const void* splats, int64_t n, const uint32_t* vals,
                                         const uint32_t* tile_ranges, const uint32_t* tile_order, float* rgb,
                                         float* depth, float* t_final, uint32_t* last_idx, uint32_t* n_blended,
-                                        const float* target_rgb, const float* target_depth, float* d_rgb,
-                                        float* d_depth, double* loss_out, gs_stream stream) {
+                                        uint32_t* blend_masks, const float* target_rgb, const float* target_depth,
+                                        float* d_rgb, float* d_depth, double* loss_out, gs_stream stream) {
     gs_status s;
     if ((s = render_checks(cfg, cam, rec_dtype, splats, n)) != GS_OK) return s;
     if (!tile_ranges || !rgb || !depth || !t_final || !last_idx)
@@ -1278,8 +1325,15 @@ extern "C" gs_status gs_render_fwd_loss(const gs_config* cfg, const gs_camera* c
         return set_error(GS_ERR_INVALID_ARG, "a target, gradient or loss pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(loss_out, 0, sizeof(double), st) != cudaSuccess) return set_error(GS_ERR_CUDA, "memset loss");
-    const FwdOut O = {rgb, depth, t_final, last_idx, n_blended, target_rgb, target_depth, d_rgb, d_depth, loss_out};
+    const FwdOut O = {rgb, depth, t_final, last_idx, n_blended, target_rgb, target_depth, d_rgb, d_depth, loss_out,
+                      blend_masks};
     return dispatch_fwd(*cfg, make_grid(*cam), rec_dtype, splats, vals, tile_ranges, tile_order, O, st);
+}
+
+extern "C" size_t gs_blend_mask_words(const gs_camera* cam, int64_t key_capacity) {
+    if (!cam || cam->width <= 0 || cam->height <= 0 || cam->sx < 1 || cam->sy < 1 || key_capacity < 0) return 0;
+    const Grid g = make_grid(*cam);
+    return blend_mask_base(g.TX * g.TY, 0) + (size_t)8 * ((size_t)(key_capacity >> 5) + 1);
 }
 
 extern "C" gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, const float* rgb, const float* depth,
@@ -1307,7 +1361,8 @@ size_t gs_project_bwd_ws(int64_t n);
 extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* gsn,
                                    int rec_dtype, const void* splats, const uint32_t* vals,
                                    const uint32_t* tile_ranges, const uint32_t* tile_order, const float* t_final,
-                                   const uint32_t* last_idx, const float* d_rgb, const float* d_depth, int mode,
+                                   const uint32_t* last_idx, const uint32_t* blend_masks, const float* d_rgb,
+                                   const float* d_depth, int mode,
                                    float* grad2d, gs_grads* grads, double* pose_grad6, float* score_terms,
                                    void* workspace, size_t* workspace_bytes, gs_stream stream) {
     if (!gsn) return set_error(GS_ERR_INVALID_ARG, "gaussians is NULL");
@@ -1330,7 +1385,8 @@ extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, c
     const Grid g = make_grid(*cam);
     if (n > 0) {
 #define GS_LB(DT, MD) \
-    launch_bwd<DT, MD>(*cfg, g, splats, vals, tile_ranges, tile_order, t_final, last_idx, d_rgb, d_depth, grad2d, st)
+    launch_bwd<DT, MD>(*cfg, g, splats, vals, tile_ranges, tile_order, t_final, last_idx, d_rgb, d_depth, grad2d, \
+                       blend_masks, st)
         if (mode == GS_MAP)
             s = rec_dtype == GS_F32 ? GS_LB(GS_F32, GS_MAP) : rec_dtype == GS_BF16 ? GS_LB(GS_BF16, GS_MAP)
                                                                                    : GS_LB(GS_F16, GS_MAP);

@@ -71,11 +71,12 @@ _SIGS = {
     "gs_project": ([_P, _P, _P, C.c_int, _P, _P], C.c_int),
     "gs_bin_sort": ([_P, _P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_bin_count": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
-    "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "gs_render_fwd_loss": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
-                           C.c_int),
+    "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gs_blend_mask_words": ([_P, C.c_int64], C.c_size_t),
+    "gs_render_fwd_loss": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                            _P], C.c_int),
     "gs_loss_l1": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "gs_render_bwd": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P,
+    "gs_render_bwd": ([_P, _P, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P,
                        _P, _P, _P], C.c_int),
     "gs_project_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_project_bwd_step": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
@@ -279,7 +280,15 @@ def gs_bin_count(cam, splats, n, rec_dtype=GS_F32, stream=None, cfg=None):
     return out
 
 
-def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None, order=None, stream=None):
+def gs_blend_mask_words(cam, key_capacity):
+    """Words of a blend-mask array for the camera's grid and key capacity."""
+    return int(lib().gs_blend_mask_words(C.byref(cam), int(key_capacity)))
+
+
+def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None, order=None, masks=None,
+                  stream=None):
+    """masks: optional int32 device tensor of gs_blend_mask_words words that
+    receives the blend masks gs_render_bwd can reuse."""
     Ws, Hs, _, _ = grid(cam)
     dev = splats.device
     if out is None:
@@ -289,12 +298,13 @@ def gs_render_fwd(cfg, cam, splats, n, vals, ranges, rec_dtype=GS_F32, out=None,
                "n_blended": torch.empty((Hs, Ws), dtype=torch.int32, device=dev)}
     _check(lib().gs_render_fwd(C.byref(cfg), C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(vals),
                                _ptr(ranges), _ptr(order), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["t_final"]),
-                               _ptr(out["last_idx"]), _ptr(out.get("n_blended")), _stream(stream)), "gs_render_fwd")
+                               _ptr(out["last_idx"]), _ptr(out.get("n_blended")), _ptr(masks), _stream(stream)),
+           "gs_render_fwd")
     return out
 
 
 def gs_render_fwd_loss(cfg, cam, splats, n, vals, ranges, target_rgb, target_depth, rec_dtype=GS_F32, out=None,
-                       dimg=None, order=None, stream=None):
+                       dimg=None, order=None, masks=None, stream=None):
     """Forward compositing with the loss fused (gs_render_fwd_loss): returns
     (out, dimg) like gs_render_fwd and gs_loss_l1."""
     Ws, Hs, _, _ = grid(cam)
@@ -310,7 +320,7 @@ def gs_render_fwd_loss(cfg, cam, splats, n, vals, ranges, target_rgb, target_dep
     _check(lib().gs_render_fwd_loss(C.byref(cfg), C.byref(cam), rec_dtype, _ptr(splats), int(n), _ptr(vals),
                                     _ptr(ranges), _ptr(order), _ptr(out["rgb"]), _ptr(out["depth"]),
                                     _ptr(out["t_final"]), _ptr(out["last_idx"]), _ptr(out.get("n_blended")),
-                                    _ptr(target_rgb), _ptr(target_depth), _ptr(dimg["d_rgb"]), _ptr(dimg["d_depth"]),
+                                    _ptr(masks), _ptr(target_rgb), _ptr(target_depth), _ptr(dimg["d_rgb"]), _ptr(dimg["d_depth"]),
                                     _ptr(dimg["loss"]), _stream(stream)), "gs_render_fwd_loss")
     return out, dimg
 
@@ -335,9 +345,10 @@ def gs_project_bwd_workspace(cfg, cam, g):
 
 def gs_render_bwd(cfg, cam, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, mode=GS_MAP,
                   rec_dtype=GS_F32, grad2d=None, grads=None, pose=None, score=None, ws=None, order=None,
-                  stream=None):
+                  masks=None, stream=None):
     """grads: dict of output tensors (or None); pose: float64 [6] tensor or
-    None; score: float32 [n,2] tensor or None."""
+    None; score: float32 [n,2] tensor or None; masks: the blend masks of the
+    forward that produced t_final and last_idx (or None)."""
     n = int(g["means"].shape[0])
     dev = splats.device
     grad2d = torch.empty((n, GRAD2D_STRIDE), device=dev) if grad2d is None else grad2d
@@ -349,7 +360,8 @@ def gs_render_bwd(cfg, cam, g, splats, vals, ranges, t_final, last_idx, d_rgb, d
         ws = workspace(need, dev)
     nb = C.c_size_t(ws.numel())
     _check(lib().gs_render_bwd(C.byref(cfg), C.byref(cam), C.byref(gs_g), rec_dtype, _ptr(splats), _ptr(vals),
-                               _ptr(ranges), _ptr(order), _ptr(t_final), _ptr(last_idx), _ptr(d_rgb), _ptr(d_depth),
+                               _ptr(ranges), _ptr(order), _ptr(t_final), _ptr(last_idx), _ptr(masks), _ptr(d_rgb),
+                               _ptr(d_depth),
                                mode,
                                _ptr(grad2d), C.byref(gr) if gr is not None else None, _ptr(pose),
                                _ptr(score), _ptr(ws), C.byref(nb), _stream(stream)), "gs_render_bwd")

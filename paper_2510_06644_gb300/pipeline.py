@@ -34,6 +34,10 @@ class Rasterizer:
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
         self._ws_sort = None
         self._ws_bwd = None
+        # the forward records which entries each warp blended and the
+        # backward visits only those (same results, fewer visits)
+        self.use_blend_masks = True
+        self._bm = None
 
     def set_grid(self, cam):
         """(Re)allocates the image buffers for the camera's sampled grid."""
@@ -58,6 +62,14 @@ class Rasterizer:
             self._ws_sort = gs.workspace(need, self.device)
         return self._ws_sort
 
+    def _masks(self, cam_s):
+        if not self.use_blend_masks:
+            return None
+        need = gs.gs_blend_mask_words(cam_s, self.capacity)
+        if self._bm is None or self._bm.numel() < need:
+            self._bm = torch.empty(max(need, 1), dtype=torch.int32, device=self.device)
+        return self._bm
+
     def _bwd_ws(self, cam_s, g):
         need = gs.gs_project_bwd_workspace(self.cfg, cam_s, g)
         if self._ws_bwd is None or self._ws_bwd.numel() < need:
@@ -81,8 +93,9 @@ class Rasterizer:
             gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
                            keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges,
                            order=self.order, cfg=self.cfg)
+        self._bm_used = self._masks(cam_s)
         gs.gs_render_fwd(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, self.rec_dtype, out=self.img,
-                         order=self.order)
+                         order=self.order, masks=self._bm_used)
         return self.img
 
     def loss_grad(self, cam, target_rgb, target_depth):
@@ -95,7 +108,8 @@ class Rasterizer:
         gs.gs_render_bwd(self.cfg, cam_s, g, self.splats, self.vals, self.ranges, self.img["t_final"],
                          self.img["last_idx"], d_rgb, d_depth, mode, self.rec_dtype, grad2d=self.grad2d,
                          grads=grads, pose=self.pose if want_pose else None,
-                         score=self.score if want_score else None, ws=self._bwd_ws(cam_s, g), order=self.order)
+                         score=self.score if want_score else None, ws=self._bwd_ws(cam_s, g), order=self.order,
+                         masks=getattr(self, "_bm_used", None))
         return self.grad2d
 
     def step(self, g, cam, target_rgb, target_depth, mode=gs.GS_TRACK, grads=None, rebin=True):
@@ -122,11 +136,13 @@ class Rasterizer:
             gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
                            keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges,
                            order=self.order, cfg=self.cfg)
+        self._bm_used = self._masks(cam_s)
         gs.gs_render_fwd_loss(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, target_rgb,
-                              target_depth, self.rec_dtype, out=self.img, dimg=self.dimg, order=self.order)
+                              target_depth, self.rec_dtype, out=self.img, dimg=self.dimg, order=self.order,
+                              masks=self._bm_used)
         gs.gs_render_bwd(self.cfg, cam_s, g, self.splats, self.vals, self.ranges, self.img["t_final"],
                          self.img["last_idx"], self.dimg["d_rgb"], self.dimg["d_depth"], gs.GS_TRACK,
-                         self.rec_dtype, grad2d=self.grad2d, order=self.order)
+                         self.rec_dtype, grad2d=self.grad2d, order=self.order, masks=self._bm_used)
         gs.gs_project_bwd_step(self.cfg, cam_s, g, self.grad2d, self.pose,
                                gs.pose_step(pose, pose_adam, lr_trans, lr_rot), score=self.score,
                                ws=self._bwd_ws(cam_s, g))

@@ -103,7 +103,7 @@ def test_fused_entry_points_reject_bad_arguments_on_the_host(built_lib):
     rc = gs.lib().gs_render_fwd_loss(ctypes.byref(cfg), ctypes.byref(cam), gs.GS_F32, None, 0, None,
                                      ctypes.c_void_p(16), None, ctypes.c_void_p(16), ctypes.c_void_p(16),
                                      ctypes.c_void_p(16), ctypes.c_void_p(16), None, None, None, None, None,
-                                     None, None)
+                                     None, None, None)
     assert rc == gs.GS_ERR_INVALID_ARG and b"target" in gs.lib().gs_last_error()
 
 
@@ -114,3 +114,17 @@ def test_reduction_probe_rejects_bad_arguments_on_the_host(built_lib):
     fake = ctypes.c_void_p(16)  # never dereferenced: the counts are checked first
     for n_dst, n_thr, per in ((0, 16, 1), (16, 0, 1), (16, 16, 0), (16, -5, 1)):
         assert L.gs_probe_red_f32(fake, n_dst, n_thr, per, None) == gs.GS_ERR_INVALID_ARG
+
+
+def test_blend_mask_words_host_arithmetic(built_lib):
+    """8 words per 32 keys of capacity plus 8 per tile (and one spare run):
+    enough for every tile's per-warp runs of 32 list entries."""
+    from paper_2510_06644_gb300 import gs
+    cam = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 500, "fy": 500, "cx": 320,
+                     "cy": 240, "W": 640, "H": 480})
+    T = 40 * 30
+    for cap in (0, 31, 32, 491244, 10 ** 7):
+        assert gs.gs_blend_mask_words(cam, cap) == 8 * T + 8 * (cap // 32 + 1)
+    bad = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 1, "fy": 1, "cx": 0, "cy": 0,
+                     "W": 0, "H": 10})
+    assert gs.gs_blend_mask_words(bad, 100) == 0

@@ -340,24 +340,35 @@ def test_render_bwd_matches_oracle(G, O, n, W, H, seed, mode, sx, sy):
     cs = G.camera(cam)
     _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
     order = gpu_bin.order if mode == "map" else None   # both launch orders are exercised
-    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges, order=order)
+    bm = torch.zeros(max(G.gs_blend_mask_words(cs, int(vals.numel())), 1), dtype=torch.int32, device="cuda")
+    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges, order=order, masks=bm)
     Ws, Hs, _, _ = O.grid(cam)
     d_rgb, d_dep = S.image_grads(Ws, Hs, seed + 100)
     gdummy = dev({"means": np.zeros((n, 3), np.float32), "log_scales": np.zeros((n, 3), np.float32),
                   "quats": np.zeros((n, 4), np.float32), "opacity_logit": np.zeros(n, np.float32),
                   "rgb": np.zeros((n, 3), np.float32)})
     md = G.GS_MAP if mode == "map" else G.GS_TRACK
-    g2 = G.gs_render_bwd(cfg, cs, gdummy, rec, vals, ranges, out["t_final"], out["last_idx"],
-                         torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=md, order=order)
-    torch.cuda.synchronize()
-    g2 = np_of(g2)
     ref = O.render_bwd(s, cam, d_rgb, d_dep)
+    got = []
+    # the backward's visits from the pixel boxes, then only those the
+    # forward's blend masks keep
+    for masks in (None, bm):
+        g2 = G.gs_render_bwd(cfg, cs, gdummy, rec, vals, ranges, out["t_final"], out["last_idx"],
+                             torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=md, order=order,
+                             masks=masks)
+        torch.cuda.synchronize()
+        g2 = np_of(g2).copy()
+        for name, cols in GROUPS.items():
+            if mode == "track" and name in ("opacity", "rgb"):
+                assert np.all(g2[:, cols] == 0)
+                continue
+            e = rel_l2(g2[:, cols], ref[:, cols])
+            assert e <= GRAD_TOL, (name, masks is None, e)
+        got.append(g2)
+    # the masks drop only visits no pixel contributes to: the same sums up to
+    # the order of the float32 additions
     for name, cols in GROUPS.items():
-        if mode == "track" and name in ("opacity", "rgb"):
-            assert np.all(g2[:, cols] == 0)
-            continue
-        e = rel_l2(g2[:, cols], ref[:, cols])
-        assert e <= GRAD_TOL, (name, e)
+        assert rel_l2(got[1][:, cols], got[0][:, cols]) <= 1e-5, name
 
 
 # ---------------------------------------------------------------------------
