@@ -294,6 +294,13 @@ __host__ __device__ inline size_t blend_mask_base(int tile, uint32_t start) {
     return (size_t)8 * ((size_t)(start >> 5) + (size_t)tile);
 }
 
+// Entry-parallel tiles (at most 64 sampled pixels) keep one run per pixel
+// instead of one per warp: pixel q of tile t at word 64 (floor(s / 32) + t)
+// + q ceil(len / 32).
+__host__ __device__ inline size_t blend_mask_base_ep(int tile, uint32_t start) {
+    return (size_t)64 * ((size_t)(start >> 5) + (size_t)tile);
+}
+
 // Writes sampled pixel (i, j)'s results; with the fused loss also its image
 // gradient (the formulas of k_loss_l1 on the same float values) and returns
 // its share of the loss.
@@ -407,12 +414,13 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
                         C2 += w * Cc.z;
                         D += w * dep;
                         T = ok ? Tn : T;
-                        nb += ok ? 1u : 0u;
-                        last = ok ? base + (uint32_t)e + 1u : last;
                         bq |= ok ? 1u << (e & 31) : 0u;
                     }
                     if (__all_sync(0xffffffffu, done)) break;
                 }
+                // the count and the last position follow from the word's blended bits
+                nb += __popc(bq);
+                if (bq != 0u) last = base + (uint32_t)(q * 32 + 32 - __clz(bq));
                 if (O.bmask) {  // (words past the batch's entries stay clear)
                     bq = __reduce_or_sync(0xffffffffu, bq);
                     if (lane == q && bq != 0u) O.bmask[bm_w + q] = bq;
@@ -832,7 +840,8 @@ template <int DT, int W>
 __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
                                        const FwdOut& O, int tile, int q0, int npix, EpStageN<EpFwdBatch<W>::N>& S,
-                                       int (*cbuf_all)[64], uint32_t* s_h, uint8_t* perm) {
+                                       int (*cbuf_all)[64], uint32_t* s_h, uint8_t* perm,
+                                       uint32_t (*bm_all)[EpFwdBatch<W>::N / 32]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     int* cbuf = cbuf_all[warp];
@@ -847,6 +856,9 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
     uint32_t last = 0, nb = 0;
     bool done = !mine;
     constexpr int NB = EpFwdBatch<W>::N;
+    uint32_t* bmw = bm_all[warp];  // the pixel's blend mask over the batch
+    const uint32_t nw = (end - start + 31) >> 5;
+    const size_t bm_tile = blend_mask_base_ep(tile, start);
     for (uint32_t b = start; b < end; b += NB) {
         if (__syncthreads_count(!done) == 0) break;
         const int n_in = (int)min((uint32_t)NB, end - b);
@@ -862,6 +874,10 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
             float p0 = 0.f, p1 = 0.f, p2 = 0.f, pd = 0.f;
             uint32_t lastj = 0, nbj = 0;
             bool stopped = false;
+            if (O.bmask) {
+                if (lane < NB / 32) bmw[lane] = 0u;
+                __syncwarp();
+            }
             // composite the k compacted entries cbuf[0, k), in list order
             auto composite = [&](int k) {
                 const int e = lane < k ? cbuf[lane] : -1;
@@ -898,6 +914,7 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
                 }
                 const unsigned okm = __ballot_sync(0xffffffffu, ok);
                 nbj += __popc(okm);
+                if (O.bmask && ok) atomicOr(&bmw[e >> 5], 1u << (e & 31));
                 const int ehi = __shfl_sync(0xffffffffu, e, okm ? 31 - __clz(okm) : 0);
                 if (okm) lastj = b - start + (uint32_t)ehi + 1u;
                 if (lstar < 32) {
@@ -927,6 +944,8 @@ __device__ __forceinline__ void fwd_ep(const gs_config& cfg, const Grid& g, cons
             }
             if (!stopped && cnt > 0) composite(cnt);
             __syncwarp();
+            if (O.bmask && lane < ((n_in + 31) >> 5))
+                O.bmask[bm_tile + (size_t)(q0 + perm[warp * ppw + j]) * nw + ((b - start) >> 5) + lane] = bmw[lane];
             p0 = warp_sum(p0);
             p1 = warp_sum(p1);
             p2 = warp_sum(p2);
@@ -957,8 +976,9 @@ __global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
     __shared__ int cbuf_all[W][64];
     __shared__ uint32_t s_h[64];
     __shared__ uint8_t perm[64];
+    __shared__ uint32_t bm_all[W][EpFwdBatch<W>::N / 32];
     const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
-    fwd_ep<DT, W>(cfg, g, splats, vals, ranges, O, tile, 0, g.tw * g.th, S, cbuf_all, s_h, perm);
+    fwd_ep<DT, W>(cfg, g, splats, vals, ranges, O, tile, 0, g.tw * g.th, S, cbuf_all, s_h, perm, bm_all);
 }
 
 // Fields merged per entry: GS_TRACK du dv dA dB dC dd, GS_MAP du dv dA dB dC
@@ -993,8 +1013,8 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
                                        const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                                        const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
-                                       float* __restrict__ grad2d, int tile, int q0, int npix,
-                                       EpBwdSmem<MODE, W>& M) {
+                                       float* __restrict__ grad2d, const uint32_t* __restrict__ bmask, int tile,
+                                       int q0, int npix, EpBwdSmem<MODE, W>& M) {
     constexpr int NF = EpFields<MODE>::N;
     constexpr int NB = EpFwdBatch<W>::N;
     EpStageN<NB>& S = M.S;
@@ -1033,9 +1053,12 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
     if (lane == 0) atomicMax(&s_max, wl);
     __syncthreads();
     const uint32_t tile_last = s_max;
-    // batches from the tile's furthest blended position back to the start
-    for (uint32_t hi = start + tile_last; hi > start;) {
-        const uint32_t lo = hi - start > (uint32_t)NB ? hi - NB : start;
+    const uint32_t nw = (end - start + 31) >> 5;
+    const uint32_t* bm_tile = bmask ? bmask + blend_mask_base_ep(tile, start) : nullptr;
+    // batches [start + k NB, start + (k + 1) NB) from the last one holding a
+    // blended entry back to the first
+    for (int kb = (int)((tile_last + NB - 1) / NB) - 1; kb >= 0; --kb) {
+        const uint32_t lo = start + (uint32_t)kb * NB, hi = start + min(tile_last, (uint32_t)(kb + 1) * NB);
         const int n_in = (int)(hi - lo);
         ep_stage<DT, W, NB>(splats, vals + lo, n_in, cfg.alpha_min, S, sid);
         for (int q = threadIdx.x; q < NF * NB; q += W * 32) (&acc[0][0])[q] = 0.f;
@@ -1045,14 +1068,19 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
             const uint32_t lastj = __shfl_sync(0xffffffffu, last, j);
             if (lastj <= base_pos) continue;  // nothing blended in this batch
             const int nj = (int)min((uint32_t)n_in, lastj - base_pos);
+            const int qj = q0 + perm[warp * ppw + j];  // the pixel's index in the tile
             int pi, pj;
-            ep_pixel(g, tile, q0 + perm[warp * ppw + j], pi, pj);
+            ep_pixel(g, tile, qj, pi, pj);
             const int px = pi * g.sx, py = pj * g.sy;
             const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+            // the pixel's blend mask from the forward (entries it blended),
+            // else its pixel box, selects the entries to compact
+            const uint32_t* bmj = bm_tile ? bm_tile + (size_t)qj * nw + (base_pos >> 5) : nullptr;
             float Tj = __shfl_sync(0xffffffffu, T, j);
             float sj = __shfl_sync(0xffffffffu, sdot, j);
-            const float q0 = __shfl_sync(0xffffffffu, g0, j), q1 = __shfl_sync(0xffffffffu, g1, j);
-            const float q2 = __shfl_sync(0xffffffffu, g2, j), qd = __shfl_sync(0xffffffffu, gd, j);
+            // the pixel's image gradient
+            const float h0 = __shfl_sync(0xffffffffu, g0, j), h1 = __shfl_sync(0xffffffffu, g1, j);
+            const float h2 = __shfl_sync(0xffffffffu, g2, j), hd = __shfl_sync(0xffffffffu, gd, j);
             // the k compacted entries cbuf[0, k), last first: lane l's entry
             // has the entries of lanes < l behind it
             auto differentiate = [&](int k) {
@@ -1082,7 +1110,7 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
                 }
                 const float Tb = __fdividef(Tj, Q);  // T before this entry (Eq. 5)
                 const float w = valid ? alpha * Tb : 0.f;
-                const float cg = Cc.x * q0 + Cc.y * q1 + Cc.z * q2 + Bv.z * qd;
+                const float cg = Cc.x * h0 + Cc.y * h1 + Cc.z * h2 + Bv.z * hd;
                 const float wcg = w * cg;
                 float Sin = wcg;  // inclusive prefix sum of w (c . g)
 #pragma unroll
@@ -1097,12 +1125,12 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
 #pragma unroll
                     for (int q = 0; q < NF; ++q) ga[q] = 0.f;
                     if (MODE == GS_MAP) {
-                        ga[6] = w * qd;
-                        ga[7] = w * q0;
-                        ga[8] = w * q1;
-                        ga[9] = w * q2;
+                        ga[6] = w * hd;
+                        ga[7] = w * h0;
+                        ga[8] = w * h1;
+                        ga[9] = w * h2;
                     } else {
-                        ga[5] = w * qd;
+                        ga[5] = w * hd;
                     }
                     if (!(raw > cfg.alpha_max)) {  // the clamp passes no gradient
                         if (MODE == GS_MAP) ga[5] = exp2_sfu(__fmul_rn(Qd.q, R_NEG_HALF_LOG2E)) * dLda;
@@ -1124,7 +1152,7 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
             int cnt = 0;
             for (int c = (nj - 1) & ~31; c >= 0; c -= 32) {
                 const int e = c + lane;
-                const bool in = e < nj && ep_may_blend(S, e, px, py);
+                const bool in = e < nj && (bmj ? ((__ldg(bmj + (c >> 5)) >> lane) & 1u) != 0u : ep_may_blend(S, e, px, py));
                 const unsigned m = __ballot_sync(0xffffffffu, in);
                 if (in) cbuf[cnt + __popc(m & gt_mask)] = e;
                 cnt += __popc(m);
@@ -1153,7 +1181,6 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
             if (v != 0.f) atomicAdd(grad2d + (size_t)sid[e] * GS_GRAD2D_STRIDE + ep_col<MODE>(k), v);
         }
         __syncthreads();
-        hi = lo;
     }
 }
 
@@ -1163,11 +1190,11 @@ __global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
                     const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
                     const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                     const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
-                    float* __restrict__ grad2d) {
+                    float* __restrict__ grad2d, const uint32_t* __restrict__ bmask) {
     extern __shared__ __align__(16) unsigned char r_smem[];
     EpBwdSmem<MODE, W>& M = *reinterpret_cast<EpBwdSmem<MODE, W>*>(r_smem);
     const int tile = order ? (int)__ldg(order + blockIdx.x) : (int)blockIdx.x;
-    bwd_ep<DT, MODE, W>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, tile, 0,
+    bwd_ep<DT, MODE, W>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, bmask, tile, 0,
                         g.tw * g.th, M);
 }
 
@@ -1253,12 +1280,13 @@ static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* spl
             const int sm = (int)sizeof(EpBwdSmem<MD, 8>);
             if ((s = smem_once((const void*)k_render_bwd_ep<DT, MD, 8>, id, sm)) != GS_OK) return s;
             k_render_bwd_ep<DT, MD, 8><<<ntiles, 8 * 32, sm, st>>>(cfg, g, splats, vals, ranges, order, t_final,
-                                                                    last_idx, d_rgb, d_depth, grad2d);
+                                                                    last_idx, d_rgb, d_depth, grad2d, bmask);
         } else {
             const int sm = (int)sizeof(EpBwdSmem<MD, 16>);
             if ((s = smem_once((const void*)k_render_bwd_ep<DT, MD, 16>, id + 8, sm)) != GS_OK) return s;
             k_render_bwd_ep<DT, MD, 16><<<ntiles, 16 * 32, sm, st>>>(cfg, g, splats, vals, ranges, order,
-                                                                      t_final, last_idx, d_rgb, d_depth, grad2d);
+                                                                      t_final, last_idx, d_rgb, d_depth, grad2d,
+                                                                      bmask);
         }
         return check_launch("k_render_bwd_ep");
     }
@@ -1333,6 +1361,8 @@ extern "C" gs_status gs_render_fwd_loss(const gs_config* cfg, const gs_camera* c
 extern "C" size_t gs_blend_mask_words(const gs_camera* cam, int64_t key_capacity) {
     if (!cam || cam->width <= 0 || cam->height <= 0 || cam->sx < 1 || cam->sy < 1 || key_capacity < 0) return 0;
     const Grid g = make_grid(*cam);
+    if (g.tw * g.th <= 64)  // entry-parallel tiles: a run per pixel
+        return blend_mask_base_ep(g.TX * g.TY, 0) + (size_t)64 * ((size_t)(key_capacity >> 5) + 1);
     return blend_mask_base(g.TX * g.TY, 0) + (size_t)8 * ((size_t)(key_capacity >> 5) + 1);
 }
 
