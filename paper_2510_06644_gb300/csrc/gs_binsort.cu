@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __rest
     u64* dst = tmp + b;
     for (int run = TS_SMEM_KEYS; run < n; run <<= 1) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int pair = (i / (2 * run)) * (2 * run);
+            const int pair = i & ~(2 * run - 1);  // run: a power of two
             const int a0 = pair, a1 = min(pair + run, n), b1 = min(pair + 2 * run, n);
             const u64 x = __ldcg(src + i);
             int out;

@@ -69,18 +69,21 @@ __host__ __device__ inline Grid make_grid(const gs_camera& c) {
     g.H = c.height;
     g.sx = c.sx;
     g.sy = c.sy;
-    g.Ws = (c.width + c.sx - 1) / c.sx;
-    g.Hs = (c.height + c.sy - 1) / c.sy;
+    // (integer division is a long instruction sequence on the GPU: stride 1
+    // and the power-of-two tile sides take the direct forms)
+    g.Ws = c.sx == 1 ? c.width : (c.width + c.sx - 1) / c.sx;
+    g.Hs = c.sy == 1 ? c.height : (c.height + c.sy - 1) / c.sy;
     g.tw = tile_dim(c.sx);
     g.th = tile_dim(c.sy);
     g.lw = g.tw == 16 ? 4 : (g.tw == 8 ? 3 : 2);
     g.lh = g.th == 16 ? 4 : (g.th == 8 ? 3 : 2);
-    g.TX = (g.Ws + g.tw - 1) / g.tw;
-    g.TY = (g.Hs + g.th - 1) / g.th;
+    g.TX = (g.Ws + g.tw - 1) >> g.lw;
+    g.TY = (g.Hs + g.th - 1) >> g.lh;
     return g;
 }
 
 __host__ __device__ inline int floor_div(int a, int b) {
+    if (b == 1) return a;
     int q = a / b;
     return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }

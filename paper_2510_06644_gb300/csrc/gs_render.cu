@@ -213,7 +213,13 @@ __device__ __forceinline__ void fill_staged(const Splat& v, float alpha_min, Sta
 // before it converts any, so KST dependent id -> record loads are in flight
 // per thread (KST = 4 for the small groups of downsampled frames, which
 // stage several entries per thread; 1 for full-resolution tiles).
-template <int DT, int KST>
+// Forward layout of a staged batch: slot 33 q of each run of 32 entries is
+// a dummy that never blends (an empty box), entry e sits at slot il_slot(e):
+// a step slot with no entry left in its word reads the word's dummy instead
+// of testing for one.
+__device__ __forceinline__ int il_slot(int e) { return (e >> 5) * 33 + (e & 31) + 1; }
+
+template <int DT, int KST, bool IL = false>
 __device__ __forceinline__ void stage_batch(const void* __restrict__ splats, const uint32_t* __restrict__ ids,
                                             int n_in, int lt, int TT, float alpha_min, StagedSplat* sp,
                                             uint32_t* sid) {
@@ -228,7 +234,7 @@ __device__ __forceinline__ void stage_batch(const void* __restrict__ splats, con
 #pragma unroll
         for (int k = 0; k < KST; ++k)
             if (e0 + k * TT < n_in) {
-                fill_staged(v[k], alpha_min, sp[e0 + k * TT]);
+                fill_staged(v[k], alpha_min, sp[IL ? il_slot(e0 + k * TT) : e0 + k * TT]);
                 if (sid) sid[e0 + k * TT] = id[k];
             }
     }
@@ -238,6 +244,7 @@ __device__ __forceinline__ void stage_batch(const void* __restrict__ splats, con
 // is set when entry 32q + e (below `limit`) meets the block.  Lane q returns
 // word q (words at or beyond `words` are zero), so a word is one shuffle away
 // and the masks stay in registers.
+template <bool IL = false>
 __device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit, int words, const PixelMap& m) {
     const int lane = threadIdx.x & 31;
     unsigned mine = 0u;
@@ -246,7 +253,7 @@ __device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit,
         const int e = q * 32 + lane;
         bool hit = false;
         if (q < words && e < limit) {
-            const int4 box = sp[e].box;
+            const int4 box = sp[IL ? il_slot(e) : e].box;
             hit = !(box.x + box.y < m.wx0 || box.x > m.wx1 || box.z + box.w < m.wy0 || box.z > m.wy1);
         }
         const unsigned w = __ballot_sync(0xffffffffu, hit);
@@ -346,16 +353,22 @@ __device__ __forceinline__ void add_loss(const FwdOut& O, float part) {
 }
 
 // Forward compositing of group G's tile, pixel-parallel (sp_all: the CTA's
-// staging buffer, G.B entries per group).
+// staging buffer, G.B entries plus one dummy per 32 per group).
 template <int DT, int KST>
 __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
                                        const FwdOut& O, const Group& G, StagedSplat* sp_all) {
-    StagedSplat* sp = sp_all + G.gi * G.B;
+    StagedSplat* sp = sp_all + G.gi * (G.B / 32 * 33);
     const int tile = G.tile;
     const PixelMap m = map_pixel(g, tile, G.lt);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
+    for (int q = G.lt; q < G.B / 32; q += G.TT) {  // the dummies
+        sp[q * 33].a = make_float4(0.f, 0.f, 0.f, 0.f);
+        sp[q * 33].b = make_float4(0.f, 0.f, 0.f, 0.f);
+        sp[q * 33].c = make_float4(0.f, 0.f, 0.f, 0.f);
+        sp[q * 33].box = make_int4(1 << 28, 0, 1 << 28, 0);
+    }
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     uint32_t last = 0, nb = 0;
     bool done = !m.inside;
@@ -368,13 +381,13 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
         // are no longer read) that also ends the tile once every pixel stopped
         if (b != start && group_count(G, done) == G.TT) break;
         const int n_in = (int)min((uint32_t)G.B, end - b);
-        stage_batch<DT, KST>(splats, vals + b, n_in, G.lt, G.TT, cfg.alpha_min, sp, nullptr);
+        stage_batch<DT, KST, true>(splats, vals + b, n_in, G.lt, G.TT, cfg.alpha_min, sp, nullptr);
         group_sync(G);
         // lane q clears word q of the batch, then stores it once processed
         const uint32_t bm_w = bm_off + ((b - start) >> 5);
         if (O.bmask && lane < ((n_in + 31) >> 5)) O.bmask[bm_w + lane] = 0u;
         if (!__all_sync(0xffffffffu, done)) {
-            const unsigned mword = warp_masks(sp, n_in, words, m);
+            const unsigned mword = warp_masks<true>(sp, n_in, words, m);
             const uint32_t base = b - start;
 #pragma unroll 1
             for (int q = 0; q < words; ++q) {
@@ -387,16 +400,16 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
                     // adds zero weight).  Front to back, a fragment with
                     // alpha >= alpha_min is blended unless it would take T
                     // below t_eps, where the pixel stops (Eq. 3).
+                    // slot of the next entry, or the word's dummy once none is left
                     int eu[R_STEP];
                     float au[R_STEP];
 #pragma unroll
                     for (int u = 0; u < R_STEP; ++u) {
-                        eu[u] = mq ? q * 32 + __ffs(mq) - 1 : -1;
+                        eu[u] = q * 33 + __ffs(mq);
                         mq &= mq - 1u;
                     }
 #pragma unroll
-                    for (int u = 0; u < R_STEP; ++u)
-                        au[u] = eu[u] >= 0 ? frag_alpha(sp[eu[u]], m, pxc, pyc, cfg.alpha_max) : -1.f;
+                    for (int u = 0; u < R_STEP; ++u) au[u] = frag_alpha(sp[eu[u]], m, pxc, pyc, cfg.alpha_max);
 #pragma unroll
                     for (int u = 0; u < R_STEP; ++u) {
                         const float alpha = au[u];
@@ -405,7 +418,7 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
                         const bool stop = valid && Tn < cfg.t_eps;
                         const bool ok = valid && !stop;
                         done = done || stop;
-                        const int e = eu[u] >= 0 ? eu[u] : 0;
+                        const int e = eu[u];
                         const float4 Cc = sp[e].c;
                         const float dep = sp[e].b.z;
                         const float w = ok ? alpha * T : 0.f;
@@ -414,7 +427,7 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
                         C2 += w * Cc.z;
                         D += w * dep;
                         T = ok ? Tn : T;
-                        bq |= ok ? 1u << (e & 31) : 0u;
+                        bq |= ok ? 1u << ((e - q * 33 - 1) & 31) : 0u;
                     }
                     if (__all_sync(0xffffffffu, done)) break;
                 }
@@ -1175,10 +1188,13 @@ __device__ __forceinline__ void bwd_ep(const gs_config& cfg, const Grid& g, cons
             }
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < NF * n_in; q += W * 32) {
-            const int k = q / n_in, e = q % n_in;
-            const float v = acc[k][e];
-            if (v != 0.f) atomicAdd(grad2d + (size_t)sid[e] * GS_GRAD2D_STRIDE + ep_col<MODE>(k), v);
+        for (int e = threadIdx.x; e < n_in; e += W * 32) {
+            float* dst = grad2d + (size_t)sid[e] * GS_GRAD2D_STRIDE;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                const float v = acc[k][e];
+                if (v != 0.f) atomicAdd(dst + ep_col<MODE>(k), v);
+            }
         }
         __syncthreads();
     }
@@ -1247,13 +1263,13 @@ static gs_status launch_fwd(const gs_config& cfg, const Grid& g, const void* spl
     const int gpc = R_THREADS / tile_threads(g);
     const unsigned nt = (unsigned)((ntiles + gpc - 1) / gpc);
     const int B = fwd_batch(gpc);
-    const size_t smem = (size_t)gpc * B * sizeof(StagedSplat);
+    const size_t smem = (size_t)gpc * (B / 32 * 33) * sizeof(StagedSplat);  // + a dummy per 32
     gs_status s;
     if (gpc == 1) {
-        if ((s = smem_once((const void*)k_render_fwd<DT, 1>, 2 * DT, R_FWD_SMEM)) != GS_OK) return s;
+        if ((s = smem_once((const void*)k_render_fwd<DT, 1>, 2 * DT, R_FWD_SMEM / 32 * 33)) != GS_OK) return s;
         k_render_fwd<DT, 1><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, O, B);
     } else {
-        if ((s = smem_once((const void*)k_render_fwd<DT, 4>, 2 * DT + 1, R_FWD_SMEM)) != GS_OK) return s;
+        if ((s = smem_once((const void*)k_render_fwd<DT, 4>, 2 * DT + 1, R_FWD_SMEM / 32 * 33)) != GS_OK) return s;
         k_render_fwd<DT, 4><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, O, B);
     }
     return check_launch("k_render_fwd");
