@@ -4,10 +4,11 @@
 L1 RGB + 0.5 L1 depth against a target rendered from the true pose, the
 camera starting 2 cm / 1 deg away.
 
-One step = one tracking iteration: projection, binning + 64-bit radix sort +
-tile ranges, forward compositing, L1 loss and its image gradient, backward
-compositing, backward projection with the compensated pose-gradient
-reduction and Eq. 7 score terms, and an Adam pose step on the device.
+One step = one tracking iteration: projection fused with the binning's
+tile counts, the (tile | depth) key sort and tile ranges, forward
+compositing with the L1 loss and its image gradient, backward compositing,
+backward projection with the compensated pose-gradient reduction and Eq. 7
+score terms, and an Adam pose step on the device.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
 oracle on the same workload instead (a bounded sample per step).
@@ -305,14 +306,14 @@ FLOP_PER_FRAGMENT = {"render_fwd": 27, "render_fwd_loss": 27, "render_bwd": 67}
 
 def stage_bytes(n, n_keys, P):
     """Algorithmic HBM bytes per launch of each stage (n Gaussians, n_keys
-    tile-Gaussian keys, P pixels): projection 56 read + 48 written per
-    Gaussian; binning 40 per Gaussian (two reads of the 20-byte geometry) and
-    28 per key (key written, then sorted: 8 read, 12 written); forward 48 per
-    staged key (its record) and 56 per pixel (24 written, 16 target read, 16
-    gradient written); backward 52 per staged key plus 24 of reductions per
-    (Gaussian, tile), 40 per pixel; backward projection 56 + 48 read, 8
-    written per Gaussian."""
-    return {"project": 104 * n, "bin_sort": 40 * n + 28 * n_keys, "render_fwd_loss": 48 * n_keys + 56 * P,
+    tile-Gaussian keys, P pixels): projection + binning 56 read + 48 written
+    per Gaussian (the record), 8 written and 8 read (its tile rect), 4 read
+    (its depth), and 28 per key (key written, then sorted: 8 read, 12
+    written); forward 48 per staged key (its record) and 56 per pixel (24
+    written, 16 target read, 16 gradient written); backward 52 per staged
+    key plus 24 of reductions per (Gaussian, tile), 40 per pixel; backward
+    projection 56 + 48 read, 8 written per Gaussian."""
+    return {"project_bin_sort": 124 * n + 28 * n_keys, "render_fwd_loss": 48 * n_keys + 56 * P,
             "render_bwd": 76 * n_keys + 40 * P, "project_bwd_pose_step": 112 * n}
 
 
@@ -573,29 +574,27 @@ def run_ours(args):
 
     # ---- stage timings (eager, events on the launching stream) ----
     Kst = min(K, 30)
-    names = ["project", "bin_sort", "render_fwd_loss", "render_bwd", "project_bwd_pose_step"]
+    names = ["project_bin_sort", "render_fwd_loss", "render_bwd", "project_bwd_pose_step"]
     acc = {k: 0.0 for k in names}
     cs = cam_s
     for _ in range(Kst):
         flush.zero_()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        pb_ws, bm = rast._pb_ws(cs, gd), rast._masks(cs)
         evs[0].record()
-        gs.gs_project(rast.cfg, cs, gd, rast.rec_dtype, rast.splats)
+        gs.gs_project_bin_sort(rast.cfg, cs, gd, rast.splats, rast.capacity, rast.rec_dtype, ws=pb_ws, keys=rast.keys,
+                               vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges, order=rast.order)
         evs[1].record()
-        gs.gs_bin_sort(cs, rast.splats, n, rast.capacity, rast.rec_dtype, ws=rast._sort_ws(cs), keys=rast.keys,
-                       vals=rast.vals, n_keys=rast.n_keys, ranges=rast.ranges, order=rast.order, cfg=rast.cfg)
-        evs[2].record()
-        bm = rast._masks(cs)
         gs.gs_render_fwd_loss(rast.cfg, cs, rast.splats, n, rast.vals, rast.ranges, trgb, tdep, rast.rec_dtype,
                               out=rast.img, dimg=rast.dimg, order=rast.order, masks=bm)
-        evs[3].record()
+        evs[2].record()
         gs.gs_render_bwd(rast.cfg, cs, gd, rast.splats, rast.vals, rast.ranges, rast.img["t_final"],
                          rast.img["last_idx"], rast.dimg["d_rgb"], rast.dimg["d_depth"], gs.GS_TRACK,
                          rast.rec_dtype, grad2d=rast.grad2d, order=rast.order, masks=bm)
-        evs[4].record()
+        evs[3].record()
         gs.gs_project_bwd_step(rast.cfg, cs, gd, rast.grad2d, rast.pose, gs.pose_step(pose, adam, lr_t, lr_r),
                                score=rast.score, ws=rast._bwd_ws(cs, gd))
-        evs[5].record()
+        evs[4].record()
         torch.cuda.synchronize()
         for i, k in enumerate(names):
             acc[k] += evs[i].elapsed_time(evs[i + 1])
@@ -646,10 +645,11 @@ def run_ours(args):
     e2e = {"value": replica_rate(Ke, world, te), "unit": "iters/s",
            "h2d_bytes_per_step": trgb.numel() * 4 + tdep.numel() * 4, "d2h_bytes_per_step": 7 * 8}
 
-    # kernels of one fused tracking iteration: k_project; k_tile_hist,
-    # k_col_scan_tail (+ tile scan + order), k_tile_scatter_rows, k_tile_sort;
-    # k_render_fwd (+ loss); k_render_bwd; k_project_bwd (+ pose step)
-    launches_per_step = 1 + 4 + 1 + 1 + 1
+    # kernels of one fused tracking iteration: k_project_hist (projection +
+    # per-CTA tile counts), k_col_scan_tail (+ tile scan + order),
+    # k_tile_scatter_rects, k_tile_sort; k_render_fwd (+ loss);
+    # k_render_bwd; k_project_bwd (+ pose step)
+    launches_per_step = 4 + 1 + 1 + 1
     line = {
         "metric": METRIC, "value": iters_s, "unit": "iters/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",

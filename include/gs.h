@@ -226,6 +226,19 @@ gs_status gs_bin_count(const gs_config* cfg, const gs_camera* cam, int rec_dtype
                        void* workspace, size_t* workspace_bytes, int64_t* n_keys_out,
                        gs_stream stream);
 
+/* Projection and binning in one call (a fusion of the tracking iteration):
+ * gs_project followed by gs_bin_sort, with the binning's first pass (per-CTA
+ * tile counts) done by the projection kernel and the scatter reusing the
+ * tile rects it computed.  Outputs identical to the two calls (records in
+ * `splats`, keys, values, n_keys, ranges, order).  Workspace: NULL asks for
+ * its size (gs_bin_sort's plus 8 bytes per Gaussian), 256-byte aligned.
+ * Grids of more than 8192 tiles run the two calls. */
+gs_status gs_project_bin_sort(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                              int rec_dtype, void* splats, int64_t keys_capacity, void* workspace,
+                              size_t* workspace_bytes, uint64_t* keys_out, uint32_t* vals_out,
+                              int64_t* n_keys_out, uint32_t* tile_ranges, uint32_t* tile_order,
+                              gs_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* A-5 Forward compositing (Sec. 2.1, Step 3; Eq. 2 and Eq. 3)              */
 /* ---------------------------------------------------------------------- */

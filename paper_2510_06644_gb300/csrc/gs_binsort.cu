@@ -326,6 +326,40 @@ __global__ void __launch_bounds__(1024) k_col_scan_tail(uint32_t* __restrict__ h
     if (threadIdx.x == 0) *T.ticket = 0u;
 }
 
+// k_tile_scatter_rows with the rects the fused projection kept (no
+// geometry re-read, no tile-rect arithmetic): only the depth is loaded.
+template <int DT>
+__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rects(int TX, const void* __restrict__ splats, int64_t n,
+                                                                    int64_t per_cta, int ntiles,
+                                                                    const uint32_t* __restrict__ start,
+                                                                    const uint32_t* __restrict__ hist,
+                                                                    const uint2* __restrict__ rects, int64_t cap,
+                                                                    u64* __restrict__ keys) {
+    extern __shared__ uint32_t h[];
+    uint32_t* base = h + ntiles;
+    const uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        h[t] = 0;
+        base[t] = start[t] + row[t];
+    }
+    __syncthreads();
+    const int64_t k0 = (int64_t)blockIdx.x * per_cta, k1 = min(n, k0 + per_cta);
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const uint2 r = __ldg(rects + k);
+        const int x0 = (int)(r.x & 0xffffu), x1 = (int)(r.x >> 16), y0 = (int)(r.y & 0xffffu), y1 = (int)(r.y >> 16);
+        if (x1 <= x0) continue;
+        const float depth = DT == GS_F32 ? __ldg(reinterpret_cast<const float*>(splats) + 12 * (size_t)k + 6)
+                                         : __ldg(reinterpret_cast<const float*>(splats) + 8 * (size_t)k + 2);
+        const u64 rem = ((u64)__float_as_uint(depth) << 32) | (u64)(uint32_t)k;
+        for (int ty = y0; ty < y1; ++ty)
+            for (int tx = x0; tx < x1; ++tx) {
+                const int t = ty * TX + tx;
+                const u64 pos = (u64)base[t] + atomicAdd(h + t, 1u);
+                if ((int64_t)pos < cap) keys[pos] = rem;
+            }
+    }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter(gs_camera cam, float alpha_min, const void* __restrict__ splats,
                                                               int64_t n, const uint32_t* __restrict__ start,
@@ -640,10 +674,32 @@ static gs_status set_agg_smem_attrs() {
     const int bytes = (int)(2 * AGG_MAX_TILES * sizeof(uint32_t));
     bool ok = cudaFuncSetAttribute(k_tile_scatter_rows<GS_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
               cudaFuncSetAttribute(k_tile_scatter_rows<GS_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
-              cudaFuncSetAttribute(k_tile_scatter_rows<GS_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+              cudaFuncSetAttribute(k_tile_scatter_rows<GS_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+              cudaFuncSetAttribute(k_tile_scatter_rects<GS_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+              cudaFuncSetAttribute(k_tile_scatter_rects<GS_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+              cudaFuncSetAttribute(k_tile_scatter_rects<GS_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
     if (!ok) return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(k_tile_scatter_rows)");
     if (dev >= 0 && dev < 64) done[dev] = true;
     return GS_OK;
+}
+
+// The bucket sort of the scattered keys, heavy tiles first.
+static gs_status launch_tile_sort(int ntiles, const uint32_t* tile_ranges, const uint32_t* order,
+                                  const uint32_t* n_big, uint64_t* keys_out, uint32_t* vals_out, u64* tmp,
+                                  cudaStream_t st) {
+    // once per device (not repeated while a graph is being captured)
+    static bool attr_done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        if (cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((TS_SMEM_KEYS + TS_SMEM_KEYS / 16) * sizeof(u64))) != cudaSuccess)
+            return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(k_tile_sort)");
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    k_tile_sort<<<(unsigned)ntiles, TS_THREADS, (TS_SMEM_KEYS + TS_SMEM_KEYS / 16) * sizeof(u64), st>>>(
+        tile_ranges, order, n_big, ntiles, (u64*)keys_out, vals_out, tmp);
+    return check_launch("k_tile_sort");
 }
 
 // Tile counts into `count`: per-CTA rows + column scan (rows kept in `hist`
@@ -773,19 +829,72 @@ extern "C" gs_status gs_bin_sort(const gs_config* cfg, const gs_camera* cam, int
             k_tile_scatter<GS_F16><<<nb, BIN_THREADS, 0, st>>>(*cam, alpha_min, splats, n, start, fill, keys_capacity, (u64*)keys_out);
         if ((s = check_launch("k_tile_scatter")) != GS_OK) return s;
     }
-    {
-        // once per device (not repeated while a graph is being captured)
-        static bool attr_done[64] = {false};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-            if (cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((TS_SMEM_KEYS + TS_SMEM_KEYS / 16) * sizeof(u64))) != cudaSuccess)
-                return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(k_tile_sort)");
-            if (dev >= 0 && dev < 64) attr_done[dev] = true;
-        }
+    return launch_tile_sort(ntiles, tile_ranges, order, n_big, keys_out, vals_out, tmp, st);
+}
+
+// Projection and binning in one call: gs_project, then gs_bin_sort with
+// the first binning pass (per-CTA tile rows) done by the projection kernel
+// itself and the scatter reading the rects it kept.  Same outputs as the two
+// calls.  Workspace: gs_bin_sort's plus 8 bytes per Gaussian.
+extern "C" gs_status gs_project_bin_sort(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                                         int rec_dtype, void* splats, int64_t keys_capacity, void* workspace,
+                                         size_t* workspace_bytes, uint64_t* keys_out, uint32_t* vals_out,
+                                         int64_t* n_keys_out, uint32_t* tile_ranges, uint32_t* tile_order,
+                                         gs_stream stream) {
+    gs_status s;
+    if ((s = project_checks(cfg, cam, g, rec_dtype)) != GS_OK) return s;
+    const int64_t n = g->n;
+    if ((s = bin_common_checks(cfg, cam, rec_dtype, splats, n, workspace == nullptr)) != GS_OK) return s;
+    if (!workspace_bytes) return set_error(GS_ERR_INVALID_ARG, "workspace_bytes is NULL");
+    if (keys_capacity < 0 || keys_capacity >= ((int64_t)1 << 30))
+        return set_error(GS_ERR_INVALID_ARG, "keys_capacity must be in [0, 2^30)");
+    const Grid grid = make_grid(*cam);
+    const int ntiles = grid.TX * grid.TY;
+    const BinLayout L = bin_layout(n, keys_capacity, ntiles);
+    const size_t off_rects = L.total, total = align256(L.total + sizeof(uint2) * (size_t)(n > 0 ? n : 1));
+    if (!workspace) { *workspace_bytes = total; return GS_OK; }
+    if (*workspace_bytes < total) return set_error(GS_ERR_WORKSPACE, "workspace %zu < %zu", *workspace_bytes, total);
+    if (((uintptr_t)workspace & 255) != 0) return set_error(GS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    if (!n_keys_out || !tile_ranges || (keys_capacity > 0 && (!keys_out || !vals_out)))
+        return set_error(GS_ERR_INVALID_ARG, "an output pointer is NULL");
+    if (ntiles > AGG_MAX_TILES || n == 0) {  // no per-CTA rows: the two calls
+        if ((s = gs_project(cfg, cam, g, rec_dtype, splats, stream)) != GS_OK) return s;
+        size_t wb = *workspace_bytes;
+        return gs_bin_sort(cfg, cam, rec_dtype, splats, n, keys_capacity, workspace, &wb, keys_out, vals_out,
+                           n_keys_out, tile_ranges, tile_order, stream);
     }
-    k_tile_sort<<<(unsigned)ntiles, TS_THREADS, (TS_SMEM_KEYS + TS_SMEM_KEYS / 16) * sizeof(u64), st>>>(
-        tile_ranges, order, n_big, ntiles, (u64*)keys_out, vals_out, tmp);
-    return check_launch("k_tile_sort");
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    uint32_t* count = (uint32_t*)(ws + L.off_count);
+    uint32_t* start = (uint32_t*)(ws + L.off_start);
+    u64* tmp = (u64*)(ws + L.off_tmp);
+    uint32_t* hist = (uint32_t*)(ws + L.off_hist);
+    void* rects = ws + off_rects;
+    if (cudaMemsetAsync(ws, 0, L.zero_bytes, st) != cudaSuccess) return set_error(GS_ERR_CUDA, "memset bin state");
+    unsigned int* err = status_ptr();
+    if (!err) return set_error(GS_ERR_CUDA, "status word address");
+    uint32_t* order = tile_order ? tile_order : (uint32_t*)(ws + L.off_order);
+    uint32_t* n_big = (uint32_t*)(ws + L.off_nbig);
+    const ScanTail tail = {(unsigned int*)(ws + L.off_ticket), keys_capacity, start, tile_ranges, n_keys_out, err,
+                           order, n_big};
+    const int64_t per = agg_per_cta(n, ntiles);
+    const unsigned nb = (unsigned)((n + per - 1) / per);
+    if ((s = launch_project_hist(cfg, cam, g, rec_dtype, splats, per, nb, ntiles, hist, rects, st)) != GS_OK) return s;
+    k_col_scan_tail<<<(unsigned)((ntiles + 7) / 8), 1024, 0, st>>>(hist, (int)nb, ntiles, count, tail);
+    if ((s = check_launch("k_col_scan_tail")) != GS_OK) return s;
+    if (keys_capacity == 0) return GS_OK;
+    if ((s = set_agg_smem_attrs()) != GS_OK) return s;
+    const size_t sm = 2 * sizeof(uint32_t) * (size_t)ntiles;
+    const uint2* r = (const uint2*)rects;
+    if (rec_dtype == GS_F32)
+        k_tile_scatter_rects<GS_F32><<<nb, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
+                                                                 keys_capacity, (u64*)keys_out);
+    else if (rec_dtype == GS_BF16)
+        k_tile_scatter_rects<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
+                                                                  keys_capacity, (u64*)keys_out);
+    else
+        k_tile_scatter_rects<GS_F16><<<nb, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
+                                                                 keys_capacity, (u64*)keys_out);
+    if ((s = check_launch("k_tile_scatter_rects")) != GS_OK) return s;
+    return launch_tile_sort(ntiles, tile_ranges, order, n_big, keys_out, vals_out, tmp, st);
 }

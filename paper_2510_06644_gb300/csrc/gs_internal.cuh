@@ -18,6 +18,12 @@ namespace gs {
 // Host-side error plumbing (defined in gs_api.cu)
 // ---------------------------------------------------------------------------
 gs_status set_error(gs_status code, const char* fmt, ...);
+// gs_project's argument checks (gs_project.cu).
+gs_status project_checks(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g, int rec_dtype);
+// Projection fused with the binning's per-CTA tile rows (gs_project.cu).
+gs_status launch_project_hist(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g, int rec_dtype,
+                              void* splats, int64_t per, unsigned nb, int ntiles, uint32_t* hist, void* rects,
+                              cudaStream_t st);
 gs_status check_launch(const char* what);
 int num_sms();
 

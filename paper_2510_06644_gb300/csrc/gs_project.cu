@@ -101,13 +101,13 @@ __device__ __forceinline__ void project_core(const gs_camera& cam, const gs_conf
     o.visible = true;
 }
 
+// Projects Gaussian k and writes its 2D record; returns its tile count and
+// rect [x0, x1) x [y0, y1) (the binning's, from the values as the record
+// stores them).  `cam` has its pose resolved.
 template <int DT>
-__global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, gs_gaussians g,
-                                                 void* out) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.n) return;
-    resolve_pose(cam);
-    const Grid grid = make_grid(cam);
+__device__ __forceinline__ int project_write(const gs_camera& cam, const gs_config& cfg, const gs_gaussians& g,
+                                             const Grid& grid, int64_t k, void* out, int& x0, int& x1, int& y0,
+                                             int& y1) {
     float mu[3], ls[3], q[4];
     for (int i = 0; i < 3; ++i) { mu[i] = __ldg(g.means + 3 * k + i); ls[i] = __ldg(g.log_scales + 3 * k + i); }
     for (int i = 0; i < 4; ++i) q[i] = __ldg(g.quats + 4 * k + i);
@@ -118,15 +118,14 @@ __global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, g
     else { o.visible = false; o.radius = 0; }
     float cr = __ldg(g.rgb + 3 * k), cg = __ldg(g.rgb + 3 * k + 1), cb = __ldg(g.rgb + 3 * k + 2);
     int touched = 0;
+    x0 = x1 = y0 = y1 = 0;
     if (o.visible) {
-        // the binning's rect, from the values as the record stores them
         Geom G;
         G.x = o.u; G.y = o.v; G.depth = o.p[2]; G.radius = o.radius;
         G.ca = DT == GS_F32 ? o.ca : h2f(f2h(o.ca, DT), DT);
         G.cb = DT == GS_F32 ? o.cb : h2f(f2h(o.cb, DT), DT);
         G.cc = DT == GS_F32 ? o.cc : h2f(f2h(o.cc, DT), DT);
         G.op = DT == GS_F32 ? o.op : h2f(f2h(o.op, DT), DT);
-        int x0, x1, y0, y1;
         touched = tile_rect(grid, G, cfg.alpha_min, x0, x1, y0, y1);
     } else {
         o.u = o.v = o.ca = o.cb = o.cc = o.op = 0.f;
@@ -148,6 +147,45 @@ __global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, g
                             (uint32_t)f2h(cr, DT) | ((uint32_t)f2h(cg, DT) << 16),
                             (uint32_t)f2h(cb, DT) | (t16 << 16));
     }
+    return touched;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, gs_gaussians g,
+                                                 void* out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    resolve_pose(cam);
+    const Grid grid = make_grid(cam);
+    int x0, x1, y0, y1;
+    project_write<DT>(cam, cfg, g, grid, k, out, x0, x1, y0, y1);
+}
+
+// Projection fused with the binning's first pass: CTA c projects Gaussians
+// [c per, (c + 1) per), counts their tiles in a shared row that becomes row
+// c of `hist` (the per-CTA tile rows of the binning), and keeps each rect
+// (x0 | x1 << 16, y0 | y1 << 16; zero: no tile) for the scatter.
+template <int DT>
+__global__ void __launch_bounds__(256) k_project_hist(gs_camera cam, gs_config cfg, gs_gaussians g, void* out,
+                                                      int64_t per, int ntiles, uint32_t* __restrict__ hist,
+                                                      uint2* __restrict__ rects) {
+    extern __shared__ uint32_t h_row[];
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) h_row[t] = 0;
+    __syncthreads();
+    resolve_pose(cam);
+    const Grid grid = make_grid(cam);
+    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(g.n, k0 + per);
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        int x0, x1, y0, y1;
+        const int touched = project_write<DT>(cam, cfg, g, grid, k, out, x0, x1, y0, y1);
+        rects[k] = touched ? make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16))
+                           : make_uint2(0u, 0u);
+        for (int ty = y0; ty < y1; ++ty)
+            for (int tx = x0; tx < x1; ++tx) atomicAdd(h_row + ty * grid.TX + tx, 1u);
+    }
+    __syncthreads();
+    uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = h_row[t];
 }
 
 // ---------------------------------------------------------------------------
@@ -437,6 +475,19 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_co
     }
 }
 
+// Launches k_project_hist (nb CTAs of `per` Gaussians; ntiles words of
+// dynamic shared memory).
+gs_status launch_project_hist(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g, int rec_dtype,
+                              void* splats, int64_t per, unsigned nb, int ntiles, uint32_t* hist, void* rects,
+                              cudaStream_t st) {
+    const size_t sm = sizeof(uint32_t) * (size_t)ntiles;
+    uint2* r = (uint2*)rects;
+    if (rec_dtype == GS_F32) k_project_hist<GS_F32><<<nb, 256, sm, st>>>(*cam, *cfg, *g, splats, per, ntiles, hist, r);
+    else if (rec_dtype == GS_BF16) k_project_hist<GS_BF16><<<nb, 256, sm, st>>>(*cam, *cfg, *g, splats, per, ntiles, hist, r);
+    else k_project_hist<GS_F16><<<nb, 256, sm, st>>>(*cam, *cfg, *g, splats, per, ntiles, hist, r);
+    return check_launch("k_project_hist");
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -459,6 +510,19 @@ static gs_status check_gaussians(const gs_gaussians* g) {
         return set_error(GS_ERR_INVALID_ARG, "a Gaussian parameter array is NULL");
     return GS_OK;
 }
+
+namespace gs {
+// gs_project's argument checks (the record pointer aside).
+gs_status project_checks(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g, int rec_dtype) {
+    if (!cfg) return set_error(GS_ERR_INVALID_ARG, "config is NULL");
+    gs_status s;
+    if ((s = check_camera(cam)) != GS_OK) return s;
+    if ((s = check_gaussians(g)) != GS_OK) return s;
+    if (rec_dtype != GS_F32 && rec_dtype != GS_BF16 && rec_dtype != GS_F16)
+        return set_error(GS_ERR_INVALID_ARG, "bad record dtype %d", rec_dtype);
+    return GS_OK;
+}
+}  // namespace gs
 
 extern "C" gs_status gs_project(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
                                 int rec_dtype, void* splats, gs_stream stream) {

@@ -39,7 +39,7 @@ namespace gs {
 #define R_BATCH 1024             // largest batch of entries a tile stages at a time
 #define R_MASKW (R_BATCH / 32)   // mask words of a batch (at most 32: lane q holds word q)
 #define R_FWD_SMEM (48 * 1024)          // forward staging budget per CTA (768 entries: 4 CTAs per SM)
-#define R_BWD_SMEM (70 * 1024)          // backward staging budget per CTA (512 entries)
+#define R_BWD_SMEM (70 * 1024)          // backward staging budget per CTA (512 entries: 51 KB, 4 CTAs per SM)
 #define R_STEP 4                 // list entries evaluated side by side in the forward walk
 
 struct StagedSplat {
@@ -726,7 +726,7 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
 }
 
 template <int DT, int MODE, int KST>
-__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 3 : 2)
+__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
     k_render_bwd(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
                  const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
                  const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,

@@ -71,6 +71,7 @@ _SIGS = {
     "gs_project": ([_P, _P, _P, C.c_int, _P, _P], C.c_int),
     "gs_bin_sort": ([_P, _P, C.c_int, _P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_bin_count": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P], C.c_int),
+    "gs_project_bin_sort": ([_P, _P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_render_fwd": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_blend_mask_words": ([_P, C.c_int64], C.c_size_t),
     "gs_render_fwd_loss": ([_P, _P, C.c_int, _P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
@@ -265,6 +266,36 @@ def gs_bin_sort(cam, splats, n, capacity, rec_dtype=GS_F32, ws=None, keys=None, 
                              _ptr(ws),
                              C.byref(nb), _ptr(keys), _ptr(vals), _ptr(n_keys), _ptr(ranges), _ptr(order),
                              _stream(stream)), "gs_bin_sort")
+    return keys, vals, n_keys, ranges, order
+
+
+def gs_project_bin_sort_workspace(cfg, cam, g, rec_dtype, capacity):
+    nb = C.c_size_t(0)
+    gs_g = gaussians(g)
+    _check(lib().gs_project_bin_sort(C.byref(cfg), C.byref(cam), C.byref(gs_g), rec_dtype, None, int(capacity), None,
+                                     C.byref(nb), None, None, None, None, None, None), "gs_project_bin_sort(size)")
+    return nb.value
+
+
+def gs_project_bin_sort(cfg, cam, g, splats, capacity, rec_dtype=GS_F32, ws=None, keys=None, vals=None, n_keys=None,
+                        ranges=None, order=None, stream=None):
+    """gs_project into `splats`, then gs_bin_sort, in one fused call:
+    returns (keys, vals, n_keys, ranges, order)."""
+    dev = splats.device
+    _, _, TX, TY = grid(cam)
+    need = gs_project_bin_sort_workspace(cfg, cam, g, rec_dtype, capacity)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    keys = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev) if keys is None else keys
+    vals = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev) if vals is None else vals
+    n_keys = torch.zeros(1, dtype=torch.int64, device=dev) if n_keys is None else n_keys
+    ranges = torch.empty((TX * TY, 2), dtype=torch.int32, device=dev) if ranges is None else ranges
+    order = torch.empty(TX * TY, dtype=torch.int32, device=dev) if order is None else order
+    gs_g = gaussians(g)
+    nb = C.c_size_t(ws.numel())
+    _check(lib().gs_project_bin_sort(C.byref(cfg), C.byref(cam), C.byref(gs_g), rec_dtype, _ptr(splats), int(capacity),
+                                     _ptr(ws), C.byref(nb), _ptr(keys), _ptr(vals), _ptr(n_keys), _ptr(ranges),
+                                     _ptr(order), _stream(stream)), "gs_project_bin_sort")
     return keys, vals, n_keys, ranges, order
 
 

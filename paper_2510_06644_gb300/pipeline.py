@@ -55,12 +55,28 @@ class Rasterizer:
         self.dimg = {"d_rgb": torch.empty((3, Hs, Ws), device=d), "d_depth": torch.empty((Hs, Ws), device=d),
                      "loss": torch.zeros(1, dtype=torch.float64, device=d)}
         self._ws_sort = None
+        self._ws_pb = None
 
     def _sort_ws(self, cam_s):
         need = gs.gs_bin_sort_workspace(cam_s, self.rec_dtype, self.n, self.capacity, self.cfg)
         if self._ws_sort is None or self._ws_sort.numel() < need:
             self._ws_sort = gs.workspace(need, self.device)
         return self._ws_sort
+
+    def _pb_ws(self, cam_s, g):
+        need = gs.gs_project_bin_sort_workspace(self.cfg, cam_s, g, self.rec_dtype, self.capacity)
+        if getattr(self, "_ws_pb", None) is None or self._ws_pb.numel() < need:
+            self._ws_pb = gs.workspace(need, self.device)
+        return self._ws_pb
+
+    def _project_bin(self, g, cam_s, rebin):
+        """Projection, and with rebin the binning + sort fused into it."""
+        if rebin:
+            gs.gs_project_bin_sort(self.cfg, cam_s, g, self.splats, self.capacity, self.rec_dtype,
+                                   ws=self._pb_ws(cam_s, g), keys=self.keys, vals=self.vals, n_keys=self.n_keys,
+                                   ranges=self.ranges, order=self.order)
+        else:
+            gs.gs_project(self.cfg, cam_s, g, self.rec_dtype, self.splats)
 
     def _masks(self, cam_s):
         if not self.use_blend_masks:
@@ -88,11 +104,7 @@ class Rasterizer:
         Gaussians it held when the lists were built."""
         cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam)
         self.set_grid(cam_s)
-        gs.gs_project(self.cfg, cam_s, g, self.rec_dtype, self.splats)
-        if rebin:
-            gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
-                           keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges,
-                           order=self.order, cfg=self.cfg)
+        self._project_bin(g, cam_s, rebin)
         self._bm_used = self._masks(cam_s)
         gs.gs_render_fwd(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, self.rec_dtype, out=self.img,
                          order=self.order, masks=self._bm_used)
@@ -127,15 +139,11 @@ class Rasterizer:
         then backward projection with the pose step fused into its last block
         (gs_project_bwd_step).  `cam` must carry the device pose (`pose`,
         float32 [12]) so the next iteration sees the updated pose; pose_adam
-        is the float32 [13] Adam state.  Eight kernel launches (plus memsets)
-        instead of the ten of step() + gs_pose_update."""
+        is the float32 [13] Adam state.  Seven kernel launches (plus memsets):
+        the projection also counts the binning's tiles (gs_project_bin_sort)."""
         cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam, pose=pose)
         self.set_grid(cam_s)
-        gs.gs_project(self.cfg, cam_s, g, self.rec_dtype, self.splats)
-        if rebin:
-            gs.gs_bin_sort(cam_s, self.splats, self.n, self.capacity, self.rec_dtype, ws=self._sort_ws(cam_s),
-                           keys=self.keys, vals=self.vals, n_keys=self.n_keys, ranges=self.ranges,
-                           order=self.order, cfg=self.cfg)
+        self._project_bin(g, cam_s, rebin)
         self._bm_used = self._masks(cam_s)
         gs.gs_render_fwd_loss(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, target_rgb,
                               target_depth, self.rec_dtype, out=self.img, dimg=self.dimg, order=self.order,

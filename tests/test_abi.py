@@ -133,3 +133,22 @@ def test_blend_mask_words_host_arithmetic(built_lib):
     bad = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 1, "fy": 1, "cx": 0, "cy": 0,
                      "W": 0, "H": 10})
     assert gs.gs_blend_mask_words(bad, 100) == 0
+
+
+def test_fused_projection_binning_checks_arguments_on_the_host(built_lib):
+    from paper_2510_06644_gb300 import gs
+    cfg = gs.default_config()
+    cam = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 100, "fy": 100, "cx": 48,
+                     "cy": 36, "W": 96, "H": 72})
+    nb = ctypes.c_size_t(0)
+    L = gs.lib()
+    assert L.gs_project_bin_sort(ctypes.byref(cfg), ctypes.byref(cam), None, gs.GS_F32, None, 100, None,
+                                 ctypes.byref(nb), None, None, None, None, None, None) == gs.GS_ERR_INVALID_ARG
+    g = gs.gs_gaussians()
+    g.n = 0
+    assert L.gs_project_bin_sort(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), 7, None, 100, None,
+                                 ctypes.byref(nb), None, None, None, None, None, None) == gs.GS_ERR_INVALID_ARG
+    # a size query with no Gaussians needs no device
+    assert L.gs_project_bin_sort(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), gs.GS_F32, None, 100,
+                                 None, ctypes.byref(nb), None, None, None, None, None, None) == gs.GS_OK
+    assert nb.value > 0

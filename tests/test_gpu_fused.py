@@ -119,3 +119,41 @@ def test_fused_tracking_iterations_follow_the_separate_ones(G, sx, sy):
     a, b = traj
     assert np.abs(a[-1] - a[0]).max() > 1e-4
     assert np.abs(a - b).max() <= 1e-5, np.abs(a - b).max()
+
+
+@pytest.mark.parametrize("n,W,H,sx,sy,dt,mask_frac", [
+    (40000, 320, 240, 1, 1, 0, 0.0),
+    (40000, 320, 240, 2, 2, 1, 0.1),
+    (40000, 320, 240, 4, 2, 2, 0.0),
+    (30000, 333, 197, 1, 2, 0, 0.3),
+    (0, 320, 240, 1, 1, 0, 0.0),            # no Gaussians
+    (20000, 2048, 1080, 1, 1, 0, 0.0),      # more than 8192 tiles: the two calls
+    (600000, 1920, 1080, 1, 1, 0, 0.0),     # more than 256 Gaussians per tile row
+])
+def test_project_bin_sort_equals_the_two_calls(G, n, W, H, sx, sy, dt, mask_frac):
+    """gs_project_bin_sort (projection counting the binning's tiles, scatter
+    from the kept rects) gives the records, keys, values, ranges and order of
+    gs_project followed by gs_bin_sort, bit for bit."""
+    g = S.surface_scene(max(n, 1), seed=70 + n % 7)
+    if n == 0:
+        g = {k: v[:0] for k, v in g.items()}
+    if mask_frac > 0:
+        g["mask"] = (np.random.default_rng(5).random(n) < mask_frac).astype(np.uint8)
+    gd = dev(g)
+    cam = S.camera(W, H, 0.8 * W, sx=sx, sy=sy)
+    cfg = G.default_config()
+    cs = G.camera(cam)
+    words = G.SPLAT_WORDS[dt]
+    rtype = torch.float32 if dt == G.GS_F32 else torch.int32
+    rec_a = torch.empty((max(n, 1), words), dtype=rtype, device="cuda")
+    rec_b = torch.empty_like(rec_a)
+    G.gs_project(cfg, cs, gd, dt, rec_a)
+    cap = max(int(G.gs_bin_count(cs, rec_a, n, dt).item()), 1024) if n > 0 else 1024
+    ka, va, na, ra, oa = G.gs_bin_sort(cs, rec_a, n, cap, dt, cfg=cfg)
+    kb, vb, nb, rb, ob = G.gs_project_bin_sort(cfg, cs, gd, rec_b, cap, dt)
+    torch.cuda.synchronize()
+    assert int(na.item()) == int(nb.item())
+    k = int(na.item())
+    assert torch.equal(rec_a[:n], rec_b[:n])
+    assert torch.equal(ka[:k], kb[:k]) and torch.equal(va[:k], vb[:k])
+    assert torch.equal(ra, rb) and torch.equal(oa, ob)
