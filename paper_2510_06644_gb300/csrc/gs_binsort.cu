@@ -155,12 +155,23 @@ __global__ void __launch_bounds__(1024) k_col_scan(uint32_t* __restrict__ hist, 
     col_scan_body(hist, nrows, ntiles, total);
 }
 
+// Heavy-first tile order (defined below with the tile scan).
+__device__ __forceinline__ void tile_order_body(const uint32_t* __restrict__ ranges, int ntiles,
+                                                uint32_t* __restrict__ order, uint32_t* __restrict__ n_big);
+
 template <int DT>
 __global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rows(gs_camera cam, float alpha_min, const void* __restrict__ splats,
                                                                    int64_t n, int64_t per_cta, int ntiles,
                                                                    const uint32_t* __restrict__ start,
                                                                    const uint32_t* __restrict__ hist, int64_t cap,
-                                                                   u64* __restrict__ keys) {
+                                                                   u64* __restrict__ keys,
+                                                                   const uint32_t* __restrict__ ranges,
+                                                                   uint32_t* __restrict__ order,
+                                                                   uint32_t* __restrict__ n_big) {
+    if (blockIdx.x == gridDim.x - 1) {  // the heavy-first order, beside the scatter
+        tile_order_body(ranges, ntiles, order, n_big);
+        return;
+    }
     extern __shared__ uint32_t h[];
     uint32_t* base = h + ntiles;
     const uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
@@ -267,7 +278,8 @@ __device__ __forceinline__ void tile_order_body(const uint32_t* __restrict__ ran
             run += cnt[b];
         }
     }
-    for (int base = 0; base < ntiles; base += 1024) {
+    const int nw = (int)(blockDim.x >> 5);
+    for (int base = 0; base < ntiles; base += (int)blockDim.x) {
         for (int q = threadIdx.x; q < 32 * 34; q += blockDim.x) (&wcnt[0][0])[q] = 0;
         __syncthreads();
         const int t = base + (int)threadIdx.x;
@@ -278,7 +290,7 @@ __device__ __forceinline__ void tile_order_body(const uint32_t* __restrict__ ran
         __syncthreads();
         if (threadIdx.x < 34) {  // exclusive scan over the warps, per group
             uint32_t run = cur[threadIdx.x];
-            for (int w = 0; w < 32; ++w) {
+            for (int w = 0; w < nw; ++w) {
                 const uint32_t v = wcnt[w][threadIdx.x];
                 wcnt[w][threadIdx.x] = run;
                 run += v;
@@ -322,7 +334,7 @@ __global__ void __launch_bounds__(1024) k_col_scan_tail(uint32_t* __restrict__ h
     __threadfence();
     tile_scan_body(total, ntiles, T.cap, T.start, T.ranges, T.n_keys, T.status);
     __syncthreads();
-    tile_order_body(T.ranges, ntiles, T.order, T.n_big);
+    if (T.order) tile_order_body(T.ranges, ntiles, T.order, T.n_big);  // else the scatter's extra CTA
     if (threadIdx.x == 0) *T.ticket = 0u;
 }
 
@@ -334,7 +346,14 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rects(int TX, cons
                                                                     const uint32_t* __restrict__ start,
                                                                     const uint32_t* __restrict__ hist,
                                                                     const uint2* __restrict__ rects, int64_t cap,
-                                                                    u64* __restrict__ keys) {
+                                                                    u64* __restrict__ keys,
+                                                                    const uint32_t* __restrict__ ranges,
+                                                                    uint32_t* __restrict__ order,
+                                                                    uint32_t* __restrict__ n_big) {
+    if (blockIdx.x == gridDim.x - 1) {  // the heavy-first order, beside the scatter
+        tile_order_body(ranges, ntiles, order, n_big);
+        return;
+    }
     extern __shared__ uint32_t h[];
     uint32_t* base = h + ntiles;
     const uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
@@ -792,8 +811,11 @@ extern "C" gs_status gs_bin_sort(const gs_config* cfg, const gs_camera* cam, int
     // the heavy-first order drives the sort; it is returned when asked for
     uint32_t* order = tile_order ? tile_order : (uint32_t*)(ws + L.off_order);
     uint32_t* n_big = (uint32_t*)(ws + L.off_nbig);
+    // with per-CTA rows and keys to scatter, the scatter's extra CTA computes
+    // the order; otherwise the column scan's last CTA does
+    const bool order_beside = ntiles <= AGG_MAX_TILES && n > 0 && keys_capacity > 0;
     const ScanTail tail = {(unsigned int*)(ws + L.off_ticket), keys_capacity, start, tile_ranges, n_keys_out, err,
-                           order, n_big};
+                           order_beside ? nullptr : order, n_big};
     bool fused = false;
     if ((s = launch_count(cam, cfg->alpha_min, rec_dtype, splats, n, count, hist, st, &tail, &fused)) != GS_OK) return s;
     if (!fused) {
@@ -810,14 +832,17 @@ extern "C" gs_status gs_bin_sort(const gs_config* cfg, const gs_camera* cam, int
         const unsigned nb = (unsigned)((n + per - 1) / per);
         const size_t sm = 2 * sizeof(uint32_t) * (size_t)ntiles;
         if (rec_dtype == GS_F32)
-            k_tile_scatter_rows<GS_F32><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start, hist,
-                                                                    keys_capacity, (u64*)keys_out);
+            k_tile_scatter_rows<GS_F32><<<nb + 1, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start,
+                                                                        hist, keys_capacity, (u64*)keys_out,
+                                                                        tile_ranges, order, n_big);
         else if (rec_dtype == GS_BF16)
-            k_tile_scatter_rows<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start, hist,
-                                                                     keys_capacity, (u64*)keys_out);
+            k_tile_scatter_rows<GS_BF16><<<nb + 1, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start,
+                                                                         hist, keys_capacity, (u64*)keys_out,
+                                                                         tile_ranges, order, n_big);
         else
-            k_tile_scatter_rows<GS_F16><<<nb, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start, hist,
-                                                                    keys_capacity, (u64*)keys_out);
+            k_tile_scatter_rows<GS_F16><<<nb + 1, BIN_THREADS, sm, st>>>(*cam, alpha_min, splats, n, per, ntiles, start,
+                                                                        hist, keys_capacity, (u64*)keys_out,
+                                                                        tile_ranges, order, n_big);
         if ((s = check_launch("k_tile_scatter_rows")) != GS_OK) return s;
     } else {
         const unsigned nb = (unsigned)((n + BIN_THREADS - 1) / BIN_THREADS);
@@ -875,8 +900,9 @@ extern "C" gs_status gs_project_bin_sort(const gs_config* cfg, const gs_camera* 
     if (!err) return set_error(GS_ERR_CUDA, "status word address");
     uint32_t* order = tile_order ? tile_order : (uint32_t*)(ws + L.off_order);
     uint32_t* n_big = (uint32_t*)(ws + L.off_nbig);
+    // the order is computed beside the scatter unless there is none
     const ScanTail tail = {(unsigned int*)(ws + L.off_ticket), keys_capacity, start, tile_ranges, n_keys_out, err,
-                           order, n_big};
+                           keys_capacity == 0 ? order : nullptr, n_big};
     const int64_t per = agg_per_cta(n, ntiles);
     const unsigned nb = (unsigned)((n + per - 1) / per);
     if ((s = launch_project_hist(cfg, cam, g, rec_dtype, splats, per, nb, ntiles, hist, rects, st)) != GS_OK) return s;
@@ -887,14 +913,17 @@ extern "C" gs_status gs_project_bin_sort(const gs_config* cfg, const gs_camera* 
     const size_t sm = 2 * sizeof(uint32_t) * (size_t)ntiles;
     const uint2* r = (const uint2*)rects;
     if (rec_dtype == GS_F32)
-        k_tile_scatter_rects<GS_F32><<<nb, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
-                                                                 keys_capacity, (u64*)keys_out);
+        k_tile_scatter_rects<GS_F32><<<nb + 1, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
+                                                                     keys_capacity, (u64*)keys_out, tile_ranges,
+                                                                     order, n_big);
     else if (rec_dtype == GS_BF16)
-        k_tile_scatter_rects<GS_BF16><<<nb, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
-                                                                  keys_capacity, (u64*)keys_out);
+        k_tile_scatter_rects<GS_BF16><<<nb + 1, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
+                                                                      keys_capacity, (u64*)keys_out, tile_ranges,
+                                                                      order, n_big);
     else
-        k_tile_scatter_rects<GS_F16><<<nb, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
-                                                                 keys_capacity, (u64*)keys_out);
+        k_tile_scatter_rects<GS_F16><<<nb + 1, BIN_THREADS, sm, st>>>(grid.TX, splats, n, per, ntiles, start, hist, r,
+                                                                     keys_capacity, (u64*)keys_out, tile_ranges,
+                                                                     order, n_big);
     if ((s = check_launch("k_tile_scatter_rects")) != GS_OK) return s;
     return launch_tile_sort(ntiles, tile_ranges, order, n_big, keys_out, vals_out, tmp, st);
 }

@@ -16,7 +16,7 @@
 // CTA barriers: measured 146 -> 132 us forward); each warp then builds a
 // bit mask of the staged Gaussians
 // whose pixel box meets its block (one box test and one ballot per 32
-// entries) and visits only those, four at a time in the forward (their
+// entries) and visits only those, three at a time in the forward (their
 // alphas are independent; the blends then run in order without branches).
 //
 // Entry-parallel (both strides >= 2): see the section of that name below.
@@ -40,7 +40,7 @@ namespace gs {
 #define R_MASKW (R_BATCH / 32)   // mask words of a batch (at most 32: lane q holds word q)
 #define R_FWD_SMEM (48 * 1024)          // forward staging budget per CTA (768 entries: 4 CTAs per SM)
 #define R_BWD_SMEM (70 * 1024)          // backward staging budget per CTA (512 entries: 51 KB, 4 CTAs per SM)
-#define R_STEP 4                 // list entries evaluated side by side in the forward walk
+#define R_STEP 3                 // list entries evaluated side by side in the forward walk
 
 struct StagedSplat {
     float4 a;   // x, y, conic_a, conic_b
