@@ -11,24 +11,30 @@
 // buffer.  Groups are issued in the heavy-first tile order produced by the
 // binning, so the longest lists start first (the GPU counterpart of the
 // paper's subtile streaming, Sec. 5.2).  Warps cover 8x4 pixel blocks.  A
-// tile's sorted list is staged through shared memory in batches of up to
-// 1024 records in the forward, 512 in the backward (larger batches, fewer
-// CTA barriers: measured 146 -> 132 us forward); each warp then builds a
-// bit mask of the staged Gaussians
-// whose pixel box meets its block (one box test and one ballot per 32
-// entries) and visits only those, three at a time in the forward (their
-// alphas are independent; the blends then run in order without branches).
+// tile's sorted list is staged through shared memory in batches of 768
+// records in the forward (4 CTAs per SM; one dummy slot per 32 records) and
+// 512 in the backward; each warp then builds a bit mask of the staged
+// Gaussians whose pixel box meets its block (one box test and one ballot per
+// 32 entries) and visits only those, three at a time in the forward (their
+// alphas are independent; the blends then run in order without branches; a
+// slot past the word's last entry reads the word's dummy).  The alpha of a
+// fragment is one FMA and one ex2: op e^(-q/2) = 2^(log2 op - q log2(e)/2),
+// with q = d.(Q d) and log2 op staged per entry.  The forward also records,
+// per warp and run of 32 list entries, the entries it blended (the blend
+// masks).
 //
 // Entry-parallel (both strides >= 2): see the section of that name below.
 //
-// The pixel-parallel backward walks each pixel's blended fragments in
-// reverse from the forward's last position, recovering T_k by division (Eq. 5), and merges the
-// per-pixel gradients of each Gaussian across the warp with a reduce-scatter
-// butterfly (each level halves the fields a lane carries: 9 shuffles for 6
-// fields, 16 for 10, instead of 5 per field), after which 8 or 16 lanes add
-// distinct fields into the tile's shared-memory accumulators at once; one
-// global atomic per (Gaussian, tile, field) follows.  This replaces the
-// paper's Gradient Merging Unit (Sec. 5.3).
+// The pixel-parallel backward visits, per warp, the entries the forward's
+// blend masks name (else those whose pixel box meets the block), walks each
+// pixel's blended fragments in reverse from the forward's last position,
+// recovering T_k by division (Eq. 5), and merges the per-pixel gradients of
+// each Gaussian across the warp with a reduce-scatter butterfly (each level
+// halves the fields a lane carries: 9 shuffles for 6 fields, 16 for 10,
+// instead of 5 per field), after which 8 or 16 lanes add distinct fields
+// into the tile's shared-memory accumulators at once; one global atomic per
+// (Gaussian, tile, field) follows.  This replaces the paper's Gradient
+// Merging Unit (Sec. 5.3).
 #include <algorithm>
 
 #include "gs_internal.cuh"
