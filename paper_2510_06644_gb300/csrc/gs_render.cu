@@ -731,8 +731,10 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
     }
 }
 
+// 4 CTAs per SM for the pose-only backward (64 registers); 3 when mapping,
+// whose 16-slot merge would spill at 64 (measured 363 vs 342 us at 1200x680).
 template <int DT, int MODE, int KST>
-__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
+__global__ void __launch_bounds__(R_THREADS, KST == 1 ? (MODE == GS_TRACK ? 4 : 3) : 2)
     k_render_bwd(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
                  const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
                  const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
