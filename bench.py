@@ -46,6 +46,9 @@ def parse():
                    help="only run warmup + steps tracking iterations eagerly (for ncu launch lists), print nothing")
     p.add_argument("--stride", type=int, nargs=2, default=(1, 1), metavar=("SX", "SY"),
                    help="with --profile: run the tracking iterations on a downsampled frame (Sec. 4.2 strides)")
+    p.add_argument("--profile-mapping", action="store_true",
+                   help="only run warmup + steps mapping iterations (GS_MAP: forward, loss, backward with all "
+                        "per-Gaussian gradients) on the 1200x680 / 1M mapping window, for ncu captures")
     p.add_argument("--serving", action="store_true", help="run only the serving comparison and print its line")
     p.add_argument("--skip-serving", action="store_true")
     p.add_argument("--serving-frames", type=int, default=6)
@@ -712,9 +715,39 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def profile_mapping(args):
+    """Eager mapping iterations on the first keyframe of the mapping window
+    (1M surface Gaussians, 1200x680, a target rendered from the next
+    keyframe): nothing is printed; for ncu launch lists and captures."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_06644_gb300 import gs
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    from synth import scenes as S
+    g = S.surface_scene(1_000_000, seed=3000)
+    cams = S.arc_keyframes(8, 1200, 680, 600.0, seed=3001)
+    gd = {k: torch.from_numpy(v).cuda() for k, v in g.items()}
+    n = 1_000_000
+    cap = 0
+    for c in cams[:2]:
+        probe = gs.gs_project(gs.default_config(), gs.camera(c), gd)
+        cap = max(cap, int(int(gs.gs_bin_count(gs.camera(c), probe, n).item()) * 1.3) + 4096)
+    r = Rasterizer(n, cams[0], capacity=cap)
+    img = r.forward(gd, cams[1])
+    trgb, tdep = img["rgb"].clone(), img["depth"].clone()
+    grads = {k: torch.empty_like(gd[k]) for k in ("means", "log_scales", "quats", "opacity_logit", "rgb")}
+    cs = gs.camera(cams[0])
+    for _ in range(args.warmup + args.steps):
+        r.step(gd, cs, trgb, tdep, mode=gs.GS_MAP, grads=grads)
+    r.check()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_mapping:
+        profile_mapping(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.serving:
         import torch
