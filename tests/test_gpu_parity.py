@@ -371,6 +371,57 @@ def test_render_bwd_matches_oracle(G, O, n, W, H, seed, mode, sx, sy):
         assert rel_l2(got[1][:, cols], got[0][:, cols]) <= 1e-5, name
 
 
+@pytest.mark.parametrize("n,W,H,seed,mode,sx,sy", [
+    (300, 96, 72, 41, "map", 1, 1),         # pixel-parallel
+    (2500, 320, 240, 42, "track", 1, 1),
+    (2500, 320, 240, 43, "map", 2, 2),      # entry-parallel tiles
+    (2500, 333, 197, 44, "track", 4, 4),
+])
+def test_render_with_background_matches_oracle(G, O, n, W, H, seed, mode, sx, sy):
+    """A non-black background (Eq. 3: the background is seen through the
+    final transmittance) behind real Gaussians: the image is C + T_final bg,
+    and every alpha gradient carries -T_final (bg . dL/dC) / (1 - alpha_k)."""
+    bg = (0.25, 0.5, 0.75)
+    cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
+    s = S.splats(n, W, H, seed=seed)
+    rec = pack_splats(s)
+    cfg = G.default_config(bg=bg)
+    cs = G.camera(cam)
+    _, _, _, vals, ranges = gpu_bin(G, cam, rec, n)
+    bm = torch.zeros(max(G.gs_blend_mask_words(cs, int(vals.numel())), 1), dtype=torch.int32, device="cuda")
+    out = G.gs_render_fwd(cfg, cs, rec, n, vals, ranges, order=gpu_bin.order, masks=bm)
+    torch.cuda.synchronize()
+    ocfg = {"bg": bg}
+    ref = O.render_fwd(s, cam, cfg=ocfg)
+    good = ref["margin"] == 0
+    assert good.mean() > 0.97
+    diff = np.abs(np_of(out["rgb"]) - ref["rgb"]).max(0)
+    assert diff[good].max() <= IMG_TOL, diff[good].max()
+    # sparse scenes: the background shows through a tenth of the frame or more
+    assert (ref["T"] > 0.5).mean() > 0.1
+    Ws, Hs, _, _ = O.grid(cam)
+    d_rgb, d_dep = S.image_grads(Ws, Hs, seed + 100)
+    gdummy = dev({"means": np.zeros((n, 3), np.float32), "log_scales": np.zeros((n, 3), np.float32),
+                  "quats": np.zeros((n, 4), np.float32), "opacity_logit": np.zeros(n, np.float32),
+                  "rgb": np.zeros((n, 3), np.float32)})
+    md = G.GS_MAP if mode == "map" else G.GS_TRACK
+    gref = O.render_bwd(s, cam, d_rgb, d_dep, cfg=ocfg)
+    gblack = O.render_bwd(s, cam, d_rgb, d_dep)
+    for masks in (None, bm):
+        g2 = G.gs_render_bwd(cfg, cs, gdummy, rec, vals, ranges, out["t_final"], out["last_idx"],
+                             torch.from_numpy(d_rgb).cuda(), torch.from_numpy(d_dep).cuda(), mode=md,
+                             order=gpu_bin.order, masks=masks)
+        torch.cuda.synchronize()
+        g2 = np_of(g2)
+        for name, cols in GROUPS.items():
+            if mode == "track" and name in ("opacity", "rgb"):
+                continue
+            e = rel_l2(g2[:, cols], gref[:, cols])
+            assert e <= GRAD_TOL, (name, masks is None, e)
+    # the background term is not negligible at this tolerance
+    assert rel_l2(gblack[:, [0, 1, 2, 3, 4]], gref[:, [0, 1, 2, 3, 4]]) > 10 * GRAD_TOL
+
+
 # ---------------------------------------------------------------------------
 # A-8 backward projection + pose
 # ---------------------------------------------------------------------------

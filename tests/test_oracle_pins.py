@@ -125,6 +125,12 @@ def test_single_isotropic_gradients_closed_form(oracle_lib):
     np.testing.assert_allclose(gb["log_scales"][0, 1], dlsx, rtol=1e-9)
     assert abs(gb["means"][0, 0]) < 1e-12 and abs(gb["means"][0, 1]) < 1e-12
     assert abs(gb["log_scales"][0, 2]) < 1e-12
+    # Eq. 7 score terms: dL/dmu = (0, 0, dL/dz); Sigma = s^2 I only reaches the
+    # 2D covariance through its x-y block ((f/z)^2 times it on the axis), the
+    # mirror symmetry of the image zeroes the x-y entry, and Sigma_xx = s_x^2
+    # gives dL/dls_x = 2 s^2 dL/dSigma_xx: ||dL/dSigma||_F = sqrt(2) |dls_x| / (2 s^2)
+    np.testing.assert_allclose(gb["score_terms"][0, 0], abs(dz), rtol=1e-9)
+    np.testing.assert_allclose(gb["score_terms"][0, 1], math.sqrt(2) * abs(dlsx) / (2 * s * s), rtol=1e-9)
 
 
 # ---------------------------------------------------------------------------
@@ -189,20 +195,24 @@ def test_termination_tests_the_transmittance_after_the_fragment(oracle_lib):
 # Compositing invariants
 # ---------------------------------------------------------------------------
 
-def test_transmittance_partition_of_unity(oracle_lib):
-    """With every colour 1 and black background, C = sum_k T_k a_k, so
-    C + T_final = 1 per pixel; with every depth z0, D = z0 (1 - T_final)."""
+@pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.25, 0.5, 0.75)])
+def test_transmittance_partition_of_unity(oracle_lib, bg):
+    """With every colour 1, C = sum_k T_k a_k + T_final bg and the weights
+    T_k a_k sum to 1 - T_final, so C + T_final (1 - bg) = 1 per pixel and
+    channel (Eq. 3 with the background behind the last fragment); with every
+    depth z0, D = z0 (1 - T_final) (no background depth)."""
     O = oracle_lib
     g = S.tiny_scene(seed=7, n=600)
     cam = S.tiny_camera()
     pr = O.project(g, cam)
     pr["rgb"] = np.ones_like(pr["rgb"])
     pr["depth"] = np.full_like(pr["depth"], 3.25)
-    img = O.render_fwd(pr, cam)
+    img = O.render_fwd(pr, cam, cfg={"bg": bg})
     for ch in range(3):
-        np.testing.assert_allclose(img["rgb"][ch] + img["T"], 1.0, atol=1e-12)
+        np.testing.assert_allclose(img["rgb"][ch] + img["T"] * (1.0 - bg[ch]), 1.0, atol=1e-12)
     np.testing.assert_allclose(img["depth"], 3.25 * (1 - img["T"]), atol=1e-12)
     assert img["nfrag"].max() > 5
+    assert img["T"].min() < 0.5 and img["T"].max() == 1.0
 
 
 def test_tiled_equals_brute_force(oracle_lib):
@@ -444,21 +454,29 @@ def small_fd_scene(seed):
     return gs
 
 
-def fd_loss(O, gs, cam, w, wd):
-    pr, img = O.forward(gs, cam)
+def fd_loss(O, gs, cam, w, wd, cfg=None):
+    pr, img = O.forward(gs, cam, cfg)
     return float((w * img["rgb"]).sum() + (wd * img["depth"]).sum()), img["sig"], tuple(pr["radius"])
 
 
-def test_gradients_match_central_differences(oracle_lib):
+BGS = [(0.0, 0.0, 0.0), (0.25, 0.5, 0.75)]
+
+
+@pytest.mark.parametrize("bg", BGS)
+def test_gradients_match_central_differences(oracle_lib, bg):
+    """Every parameter kind against central differences of the forward; with
+    a non-black background the alpha gradients also carry the background seen
+    through the transmittance, -T_final bg / (1 - a_k) (Eq. 3 differentiated)."""
     O = oracle_lib
     W, H = 40, 30
     gs = small_fd_scene(21)
     R = S.axis_angle_matrix([0.2, -0.5, 1.0], 0.05)
     cam = S.camera(W, H, 36.0, R=R, t=[0.01, -0.02, 0.05])
+    cfg = {"bg": bg}
     g = S.rng(22)
     w = g.normal(0, 1, (3, H, W))
     wd = g.normal(0, 1, (H, W))
-    _, _, an = O.forward_backward(gs, cam, w, wd)
+    _, _, an = O.forward_backward(gs, cam, w, wd, cfg)
     h = 1e-5
     checked = 0
     for key, width in (("means", 3), ("log_scales", 3), ("quats", 4), ("opacity_logit", 1),
@@ -473,9 +491,9 @@ def test_gradients_match_central_differences(oracle_lib):
                 else:
                     gp[key][k, j] += h
                     gm[key][k, j] -= h
-                Lp, sp, rp = fd_loss(O, gp, cam, w, wd)
-                Lm, sm, rm = fd_loss(O, gm, cam, w, wd)
-                L0, s0, r0 = fd_loss(O, gs, cam, w, wd)
+                Lp, sp, rp = fd_loss(O, gp, cam, w, wd, cfg)
+                Lm, sm, rm = fd_loss(O, gm, cam, w, wd, cfg)
+                L0, s0, r0 = fd_loss(O, gs, cam, w, wd, cfg)
                 if not (sp == s0 == sm and rp == r0 == rm):
                     continue  # the stencil crosses a predicate; not differentiable here
                 fd = (Lp - Lm) / (2 * h)
@@ -500,24 +518,113 @@ def pose_perturb(cam, xi):
     return c
 
 
-def test_pose_gradient_matches_central_differences(oracle_lib):
+@pytest.mark.parametrize("bg", BGS)
+def test_pose_gradient_matches_central_differences(oracle_lib, bg):
     O = oracle_lib
     W, H = 40, 30
     gs = small_fd_scene(31)
     cam = S.camera(W, H, 36.0, R=S.axis_angle_matrix([1, 0.3, 0.1], 0.04), t=[0.02, 0.01, -0.03])
+    cfg = {"bg": bg}
     g = S.rng(32)
     w = g.normal(0, 1, (3, H, W))
     wd = g.normal(0, 1, (H, W))
-    _, _, an = O.forward_backward(gs, cam, w, wd)
+    _, _, an = O.forward_backward(gs, cam, w, wd, cfg)
     h = 1e-6
     for i in range(6):
         e = np.zeros(6)
         e[i] = h
-        Lp, sp, rp = fd_loss(O, gs, pose_perturb(cam, e), w, wd)
-        Lm, sm, rm = fd_loss(O, gs, pose_perturb(cam, -e), w, wd)
+        Lp, sp, rp = fd_loss(O, gs, pose_perturb(cam, e), w, wd, cfg)
+        Lm, sm, rm = fd_loss(O, gs, pose_perturb(cam, -e), w, wd, cfg)
         assert sp == sm and rp == rm
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - an["pose"][i]) <= 1e-5 * max(1.0, abs(fd)), (i, fd, an["pose"][i])
+
+
+def sigma_to_params(Sig):
+    """Log-scales and a (w, x, y, z) unit quaternion whose
+    R(q) diag(exp(2 ls)) R(q)^T is the symmetric positive definite Sig (its
+    eigendecomposition, with the eigenvector basis made a proper rotation)."""
+    from scipy.spatial.transform import Rotation
+    lam, V = np.linalg.eigh(Sig)
+    if np.linalg.det(V) < 0:
+        V[:, 2] = -V[:, 2]
+    x, y, z, w = Rotation.from_matrix(V).as_quat()
+    return 0.5 * np.log(lam), np.array([w, x, y, z])
+
+
+def test_score_terms_match_differences_in_mean_and_covariance(oracle_lib):
+    """Both terms of the Eq. 7 score against central differences of the
+    forward alone (reading c12: the 3D mean's 2-norm and the Frobenius norm,
+    over all nine entries, of the 3D covariance's gradient).  The covariance
+    is moved directly: Sigma + h E for the six symmetric directions
+    E = e_i e_i^T and e_i e_j^T + e_j e_i^T, each turned back into log-scales
+    and a quaternion by an eigendecomposition, so dL/dh = <dL/dSigma, E>
+    needs neither the projection's chain rule nor its parameterisation.  The
+    camera-frame gradient dL/dSigma_c = R dL/dSigma R^T is checked entrywise."""
+    from scipy.spatial.transform import Rotation
+    O = oracle_lib
+    W, H = 40, 30
+    gs = small_fd_scene(21)
+    R = S.axis_angle_matrix([0.2, -0.5, 1.0], 0.05)
+    cam = S.camera(W, H, 36.0, R=R, t=[0.01, -0.02, 0.05])
+    g = S.rng(23)
+    w = g.normal(0, 1, (3, H, W))
+    wd = g.normal(0, 1, (H, W))
+    _, _, an = O.forward_backward(gs, cam, w, wd)
+    n = gs["means"].shape[0]
+    checked = 0
+    offdiag = 0.0
+    for k in range(n):
+        qk = gs["quats"][k] / np.linalg.norm(gs["quats"][k])
+        Rq = Rotation.from_quat([qk[1], qk[2], qk[3], qk[0]]).as_matrix()
+        Sig = Rq @ np.diag(np.exp(2 * gs["log_scales"][k])) @ Rq.T
+        h = 1e-5 * np.trace(Sig) / 3
+        Gfd = np.zeros((3, 3))
+        ok = True
+        for i in range(3):
+            for j in range(i, 3):
+                E = np.zeros((3, 3))
+                E[i, j] += 1.0
+                E[j, i] += 1.0 if i != j else 0.0
+                Ls = []
+                for sgn in (1.0, -1.0):
+                    ls, q = sigma_to_params(Sig + sgn * h * E)
+                    gg = {kk: np.array(v, dtype=np.float64, copy=True) for kk, v in gs.items()}
+                    gg["log_scales"][k] = ls
+                    gg["quats"][k] = q
+                    Ls.append(fd_loss(O, gg, cam, w, wd))
+                L0 = fd_loss(O, gs, cam, w, wd)
+                if not (Ls[0][1:] == L0[1:] == Ls[1][1:]):
+                    ok = False   # the stencil crosses a predicate
+                    break
+                d = (Ls[0][0] - Ls[1][0]) / (2 * h)
+                Gfd[i, j] = Gfd[j, i] = d if i == j else 0.5 * d
+            if not ok:
+                break
+        gmu = np.zeros(3)
+        hm = 1e-6
+        for i in range(3):
+            Ls = []
+            for sgn in (1.0, -1.0):
+                gg = {kk: np.array(v, dtype=np.float64, copy=True) for kk, v in gs.items()}
+                gg["means"][k, i] += sgn * hm
+                Ls.append(fd_loss(O, gg, cam, w, wd))
+            if not (Ls[0][1:] == Ls[1][1:]):
+                ok = False
+            gmu[i] = (Ls[0][0] - Ls[1][0]) / (2 * hm)
+        if not ok:
+            continue
+        fro = np.linalg.norm(Gfd)
+        st = an["score_terms"][k]
+        assert abs(st[1] - fro) <= 1e-5 * max(1.0, fro), (k, st[1], fro)
+        assert abs(st[0] - np.linalg.norm(gmu)) <= 1e-5 * max(1.0, np.linalg.norm(gmu)), (k, st[0], gmu)
+        Gc = np.asarray(cam["R"]) @ Gfd @ np.asarray(cam["R"]).T
+        np.testing.assert_allclose(an["Sc"][k].reshape(3, 3), Gc, rtol=0, atol=1e-5 * max(1.0, fro))
+        offdiag = max(offdiag, np.abs(Gfd - np.diag(np.diag(Gfd))).max() / max(fro, 1e-30))
+        checked += fro > 0
+    assert checked >= 8
+    # the off-diagonal entries carry weight: a norm over the diagonal alone is far off
+    assert offdiag > 0.1
 
 
 def test_pose_gradient_zero_at_target_and_descent_when_perturbed(oracle_lib):
