@@ -502,44 +502,82 @@ __global__ void __launch_bounds__(256) k_loss_l1(gs_config cfg, int64_t P, const
 // ---------------------------------------------------------------------------
 // Backward compositing
 // ---------------------------------------------------------------------------
-// Slots merged per fragment: GS_TRACK 8 (du, dv, dA, dB, dC, dd, -, -),
-// GS_MAP 16 (du, dv, dA, dB, dC, dop, dd, dr, dg, db, -...).
+// Fields merged per fragment, in the order the backward forms them:
+//   GS_TRACK  a h, b h, u dx, u dy, v dy, w gD                      (6)
+//   GS_MAP    a h, b h, u dx, u dy, v dy, G T (dL/dalpha T^-1), w gD,
+//             w gR, w gG, w gB                                      (10)
+// with h = -dL/d(exponent) / 2 = -alpha dL/dalpha / 2, (u, v) = h (dx, dy),
+// (a, b) = Q d and w = T alpha.  The gradients follow by exact power-of-two
+// scalings applied once per entry when a batch is written out:
+// dL/dmean = -2 (a h, b h) (since dL/dmean = Q d dL/d(exponent)),
+// dL/dconic = (u dx, 2 u dy, v dy) (the exponent is -(A dx^2 + 2 B dx dy +
+// C dy^2) / 2).
 template <int MODE>
-struct Slots {
-    static constexpr int N = MODE == GS_MAP ? 16 : 8;
-    static constexpr int LOG = MODE == GS_MAP ? 4 : 3;
+struct Fields {
+    static constexpr int N = MODE == GS_MAP ? 10 : 6;
 };
 
-// grad2d column of a slot (-1 = padding).
+// grad2d column of a merged field, and its scale.
 template <int MODE>
-__device__ __forceinline__ int slot_col(int s) {
-    if (MODE == GS_MAP) return s < 7 ? s : (s < 10 ? s + 1 : -1);  // du dv dA dB dC dop dd | dr dg db
-    return s < 5 ? s : (s == 5 ? 6 : -1);                             // du dv dA dB dC | dd
+__device__ __forceinline__ int field_col(int f) {
+    if (MODE == GS_MAP) return f < 7 ? f : f + 1;  // du dv dA dB dC dop dd | dr dg db
+    return f < 5 ? f : 6;                          // du dv dA dB dC | dd
 }
+__device__ __forceinline__ float field_scale(int f) { return f < 2 ? -2.f : (f == 3 ? 2.f : 1.f); }
 
-// Reduce-scatter of N values across the warp.  On return lane l holds the
-// warp total of slot (l >> (5 - LOG)) when (l & ((1 << (5 - LOG)) - 1)) == 0.
-template <int N, int LOG>
-__device__ __forceinline__ float warp_reduce_scatter(float (&v)[N]) {
-    const int lane = threadIdx.x & 31;
+// Warp sum of NF fields, scattered over the lanes: at each butterfly level
+// (lane offsets 16, 8, ..., 1) the C values a lane still carries are paired,
+// the lower lanes keeping the first C/2 and the upper lanes the second C/2
+// (a lane sends the half it gives up and adds what its partner sends), and
+// an odd one out is summed whole; once one value is left, the remaining
+// levels add it up.  NF = 6 takes 8 shuffles, NF = 10 takes 12 (instead of
+// 5 per field).  The fields end up summed over all 32 lanes, field f on the
+// lanes whose merge_ids<NF> is f.
+template <int C, int OFF>
+struct MergeLevel {
+    template <typename T, int NF, bool SHFL>
+    static __device__ __forceinline__ void run(T (&v)[NF], int lane) {
+        if constexpr (OFF > 0) {
+            if constexpr (C > 1) {
+                constexpr int H = C / 2;
+                const bool up = (lane & OFF) != 0;
 #pragma unroll
-    for (int lvl = 0; lvl < LOG; ++lvl) {
-        const int off = 16 >> lvl;
-        const int half = N >> (lvl + 1);
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < N / 2; ++i) {
-            if (i < half) {
-                const float send = up ? v[i] : v[i + half];
-                const float keep = up ? v[i + half] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                for (int i = 0; i < H; ++i) {
+                    const T send = up ? v[i] : v[i + H];
+                    const T keep = up ? v[i + H] : v[i];
+                    if constexpr (SHFL) v[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+                    else v[i] = keep;
+                }
+                if constexpr ((C & 1) != 0) {
+                    if constexpr (SHFL) v[H] = v[C - 1] + __shfl_xor_sync(0xffffffffu, v[C - 1], OFF);
+                    else v[H] = v[C - 1];
+                }
+                MergeLevel<H + (C & 1), OFF / 2>::template run<T, NF, SHFL>(v, lane);
+            } else {
+                if constexpr (SHFL) v[0] += __shfl_xor_sync(0xffffffffu, v[0], OFF);
+                MergeLevel<1, OFF / 2>::template run<T, NF, SHFL>(v, lane);
             }
         }
     }
-    float x = v[0];
+};
+
+template <int NF>
+__device__ __forceinline__ float warp_merge(float (&v)[NF]) {
+    MergeLevel<NF, 16>::template run<float, NF, true>(v, threadIdx.x & 31);
+    return v[0];
+}
+
+// The field this lane adds after warp_merge<NF>, or -1: the same pairing on
+// field numbers; of the lanes left holding the same field, the lowest adds.
+template <int NF>
+__device__ __forceinline__ int merge_owner() {
+    const int lane = threadIdx.x & 31;
+    int id[NF];
 #pragma unroll
-    for (int off = 16 >> LOG; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    return x;
+    for (int i = 0; i < NF; ++i) id[i] = i;
+    MergeLevel<NF, 16>::template run<int, NF, false>(id, lane);
+    const unsigned same = __match_any_sync(0xffffffffu, id[0]);
+    return lane == __ffs(same) - 1 ? id[0] : -1;
 }
 
 // Per-fragment quantities of the backward that do not depend on the
@@ -583,23 +621,24 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
                                        const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
                                        float* __restrict__ grad2d, const uint32_t* __restrict__ bmask,
                                        const Group& G, unsigned char* smem, uint32_t* s_max_all) {
-    constexpr int NS = Slots<MODE>::N;
-    constexpr int LOG = Slots<MODE>::LOG;
-    constexpr int SHIFT = 5 - LOG;  // lanes per slot = 1 << SHIFT
-    constexpr int BSTEP = KST == 1 ? 1 : 2;  // entries per backward step
+    constexpr int NF = Fields<MODE>::N;
+    constexpr int BSTEP = 2;  // entries per backward step, merged together
     const int gpc = R_THREADS / G.TT;
     StagedSplat* sp_all = reinterpret_cast<StagedSplat*>(smem);
     uint32_t* sid_all = reinterpret_cast<uint32_t*>(sp_all + gpc * G.B);
-    float(*acc_all)[NS] = reinterpret_cast<float(*)[NS]>(sid_all + gpc * G.B);
+    float(*acc_all)[NF] = reinterpret_cast<float(*)[NF]>(sid_all + gpc * G.B);
     StagedSplat* sp = sp_all + G.gi * G.B;
     uint32_t* sid = sid_all + G.gi * G.B;
-    float(*acc)[NS] = acc_all + G.gi * G.B;
+    float(*acc)[NF] = acc_all + G.gi * G.B;
     uint32_t* s_wl = s_max_all + G.gi * (G.TT >> 5);  // the group's per-warp maxima
     const int tile = G.tile;
     const PixelMap m = map_pixel(g, tile, G.lt);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
     const int lane = threadIdx.x & 31;
+    // the merged field this lane adds (entry owner / NF of a step, field
+    // owner % NF), or -1
+    const int owner = merge_owner<BSTEP * NF>();
     float T = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f;
     uint32_t last = 0;
     if (m.inside) {
@@ -614,8 +653,11 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
     }
     // a last_idx beyond the tile's list (inconsistent inputs) is clamped
     last = min(last, end - start);
-    // normalised suffix sums (background enters with weight T_final)
-    float A0 = cfg.bg[0], A1 = cfg.bg[1], A2 = cfg.bg[2], AD = 0.f;
+    // the normalised suffix sums A (colour and depth behind the current
+    // entry divided by the transmittance in front of it; the background
+    // enters with weight T_final) only ever appear dotted with the pixel's
+    // image gradient: s = A . g
+    float sg = cfg.bg[0] * gC0 + cfg.bg[1] * gC1 + cfg.bg[2] * gC2;
     uint32_t wlast = last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
@@ -633,7 +675,7 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
         const uint32_t lo = start + base_pos, hi = start + min(s_max, base_pos + G.B);
         const int n_in = (int)(hi - lo);
         stage_batch<DT, KST>(splats, vals + lo, n_in, G.lt, G.TT, cfg.alpha_min, sp, sid);
-        for (int q = G.lt; q < G.B * NS; q += G.TT) (&acc[0][0])[q] = 0.f;
+        for (int q = G.lt; q < G.B * NF; q += G.TT) (&acc[0][0])[q] = 0.f;
         group_sync(G);
         // entries at or beyond the warp's furthest blended position are
         // skipped; with the forward's blend masks, so is every entry none of
@@ -648,10 +690,14 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
             mword = warp_masks(sp, wlimit, words, m);
         }
         // back to front over the fragments before `last`; T_k recovered by
-        // division (Eq. 5), A the normalised suffix sums of colour and depth
-        auto back = [&](int e, const FragGeo& fg, float (&f)[NS]) {
+        // division (Eq. 5).  With w = T_k alpha_k and c_k . g (colour and
+        // depth dotted with the image gradient),
+        //   dL/dalpha_k = T_k (c_k . g - s_k),  s_k = A_k . g,
+        //   s_{k-1} = s_k + alpha_k (c_k . g - s_k),
+        // and alpha dL/dalpha = w (c . g - s) is the exponent's gradient.
+        auto back = [&](int e, const FragGeo& fg, float* f) {
 #pragma unroll
-            for (int k = 0; k < NS; ++k) f[k] = 0.f;
+            for (int q = 0; q < NF; ++q) f[q] = 0.f;
             if (!fg.contrib) return;
             const float alpha = fg.alpha;
             // fast division (at most 2 ulp for these operands: 1 - alpha in
@@ -660,13 +706,9 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
             T = __fdividef(T, 1.f - alpha);
             const float w = alpha * T;
             const float4 Cc = sp[e].c;
-            const float d0 = Cc.x - A0, d1 = Cc.y - A1, d2 = Cc.z - A2, dD = fg.dep - AD;
-            const float dLda = T * (d0 * gC0 + d1 * gC1 + d2 * gC2 + dD * gD);
-            // suffix sums behind the next entry: alpha c + (1 - alpha) A
-            A0 = __fmaf_rn(alpha, d0, A0);
-            A1 = __fmaf_rn(alpha, d1, A1);
-            A2 = __fmaf_rn(alpha, d2, A2);
-            AD = __fmaf_rn(alpha, dD, AD);
+            const float cg = __fmaf_rn(fg.dep, gD, __fmaf_rn(Cc.z, gC2, __fmaf_rn(Cc.y, gC1, Cc.x * gC0)));
+            const float dif = cg - sg;
+            sg = __fmaf_rn(alpha, dif, sg);
             if (MODE == GS_MAP) {
                 f[6] = w * gD;
                 f[7] = w * gC0;
@@ -677,21 +719,14 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
             }
             if (!(fg.raw > cfg.alpha_max)) {  // the clamp passes no gradient
                 // dalpha/dopacity = e^(-q/2) (mapping only)
-                if (MODE == GS_MAP) f[5] = exp2_sfu(__fmul_rn(fg.q, R_NEG_HALF_LOG2E)) * dLda;
-                const float dp = alpha * dLda;  // dL/d(exponent)
-                const float hx = -0.5f * dp * fg.dx, hy = -0.5f * dp * fg.dy;
-                f[2] = hx * fg.dx;
-                f[3] = (hx + hx) * fg.dy;
-                f[4] = hy * fg.dy;
-                f[0] = fg.a * dp;
-                f[1] = fg.b * dp;
-            }
-        };
-        auto merge = [&](int e, float (&f)[NS]) {
-            const float v = warp_reduce_scatter<NS, LOG>(f);
-            if ((lane & ((1 << SHIFT) - 1)) == 0) {
-                const int sl = lane >> SHIFT;
-                if (slot_col<MODE>(sl) >= 0) atomicAdd(&acc[e][sl], v);
+                if (MODE == GS_MAP) f[5] = exp2_sfu(__fmul_rn(fg.q, R_NEG_HALF_LOG2E)) * (T * dif);
+                const float h = (-0.5f * w) * dif;  // -dL/d(exponent) / 2
+                const float u = h * fg.dx, v = h * fg.dy;
+                f[0] = fg.a * h;
+                f[1] = fg.b * h;
+                f[2] = u * fg.dx;
+                f[3] = u * fg.dy;
+                f[4] = v * fg.dy;
             }
         };
 #pragma unroll 1
@@ -713,19 +748,32 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
                     const int e = eu[u] >= 0 ? eu[u] : 0;
                     gu[u] = frag_geo(sp[e], m, pxc, pyc, cfg, eu[u] >= 0 && base_pos + (uint32_t)e < last);
                 }
+                float f[BSTEP * NF];
 #pragma unroll
-                for (int u = 0; u < BSTEP; ++u) {
-                    float f[NS];
-                    back(eu[u] >= 0 ? eu[u] : 0, gu[u], f);
-                    if (__any_sync(0xffffffffu, gu[u].contrib)) merge(eu[u], f);
+                for (int u = 0; u < BSTEP; ++u) back(eu[u] >= 0 ? eu[u] : 0, gu[u], f + u * NF);
+                // the step's fields merged at once (with the blend masks
+                // every visited entry has a contributing pixel in the warp)
+                bool any = false;
+#pragma unroll
+                for (int u = 0; u < BSTEP; ++u) any = any || gu[u].contrib;
+                if (bm_in || __any_sync(0xffffffffu, any)) {
+                    const float v = warp_merge<BSTEP * NF>(f);
+                    if (owner >= 0) {
+                        const int u = owner / NF;
+                        int e = eu[0];
+#pragma unroll
+                        for (int x = 1; x < BSTEP; ++x) e = u == x ? eu[x] : e;
+                        if (e >= 0) atomicAdd(&acc[e][owner - u * NF], v);
+                    }
                 }
             }
         }
         group_sync(G);
-        for (int q = G.lt; q < n_in * NS; q += G.TT) {
+        for (int q = G.lt; q < n_in * NF; q += G.TT) {
             const float v = (&acc[0][0])[q];
-            const int col = slot_col<MODE>(q % NS);
-            if (v != 0.f && col >= 0) atomicAdd(grad2d + (size_t)sid[q / NS] * GS_GRAD2D_STRIDE + col, v);
+            const int f = q % NF;
+            if (v != 0.f) atomicAdd(grad2d + (size_t)sid[q / NF] * GS_GRAD2D_STRIDE + field_col<MODE>(f),
+                                    v * field_scale(f));
         }
         if (k > 0) group_sync(G);  // the next batch reuses the buffers
     }
@@ -1316,7 +1364,7 @@ static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* spl
     }
     const int gpc = R_THREADS / tile_threads(g);
     const unsigned nt = (unsigned)((ntiles + gpc - 1) / gpc);
-    const int per_entry = (int)(sizeof(StagedSplat) + sizeof(uint32_t) + sizeof(float) * Slots<MD>::N);
+    const int per_entry = (int)(sizeof(StagedSplat) + sizeof(uint32_t) + sizeof(float) * Fields<MD>::N);
     const int B = group_batch(gpc, per_entry, R_BWD_SMEM);
     const size_t smem = (size_t)gpc * B * per_entry;
     const int id = 6 + 6 * (MD == GS_MAP) + 2 * DT;
