@@ -89,51 +89,79 @@ def replica_rate(units_per_rank, world, t_max_ms):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling (every 100 ms) of SM clocks, power and throttle
+    reasons over the whole GPU part of the run (warm-up, timed steps, stage
+    timing, probes, variants, end-to-end steps and serving), so the summary
+    has samples even when the timed steps take milliseconds; the samples
+    that fall inside the timed region are counted apart."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.timed = []  # (start, end) wall-clock seconds of timed regions
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
+    def mark_timed(self, t0, t1):
+        self.timed.append((t0, t1))
+
+    @staticmethod
+    def parse(lines, timed=()):
+        """Summary of nvidia-smi CSV lines (the query above): median SM clock
+        over all samples and over the timed regions' samples, the maximum
+        clock, and every throttle reason seen active."""
+        import datetime
+        sm, mx, sm_t, pw, reasons = [], [], [], [], set()
+        for line in lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                c, m = float(f[2]), float(f[3])
+            except ValueError:
+                continue
+            sm.append(c)
+            mx.append(m)
+            try:
+                pw.append(float(f[4]))
+            except ValueError:
+                pass
+            if any(a - 0.1 <= ts <= b + 0.1 for a, b in timed):
+                sm_t.append(c)
+            for nm, v in zip(Clocks.NAMES, f[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_timed": len(sm_t),
+                "sm_mhz_timed": statistics.median(sm_t) if sm_t else None,
+                "power_w_max": max(pw) if pw else None, "window": "whole GPU run, 100 ms sampling"}
+
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+        with open(self.path) as fh:
+            out = self.parse(fh.readlines(), self.timed)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return out
 
 
 # --------------------------------------------------------------------------
@@ -300,10 +328,16 @@ def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pos
     return out
 
 
-# Algorithmic work per launch of each stage: bytes for the streaming stages,
-# FP32 FLOPs per blended fragment for the compositing (forward: exponent 6,
-# exp 2, alpha 3, tests 2, blend 14; backward: those 13, T recovery 1,
-# dL/dalpha 9, suffix update 8, the six fields 15, their merge 21).
+# Algorithmic work of the compositing kernels (FP32 FLOPs).  The model
+# charges every evaluated fragment F -- each list entry a pixel walks up to
+# its last blended one (F = sum of last_idx) -- 15 FLOP + 1 exp in the
+# forward (offset, quadratic form, alpha, tests) and 45 FLOP + 1 exp in the
+# backward (those, the T recovery, dL/dalpha, suffix update and gradient
+# fields).  The per-blended view counts the arithmetic written out for a
+# fragment that blends: forward 27 (exponent 6, exp 2, alpha 3, tests 2,
+# blend 14), backward 67 (those 13, T recovery 1, dL/dalpha 9, suffix update
+# 8, the six fields 15, their merge 21).
+FLOP_PER_EVALUATED = {"render_fwd_loss": 15, "render_bwd": 45}
 FLOP_PER_FRAGMENT = {"render_fwd": 27, "render_fwd_loss": 27, "render_bwd": 67}
 
 
@@ -373,7 +407,35 @@ def committed_counters(stage):
     return {}
 
 
-def roofline(stage_ms, n, n_keys, P, blended, clk):
+def fma_probe(gs, reps=10, iters=4096):
+    """Measured FP32 FMA throughput (TFLOP/s) of gs_probe_fma_f32: 2048
+    threads per SM, 8 independent FMA chains each; best of `reps` launches."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    nthr = sms * 2048
+    out = torch.empty(nthr, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        gs.gs_probe_fma_f32(out, iters)
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        gs.gs_probe_fma_f32(out, iters)
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    ok = bool(torch.all(out == float(28 + 8 * iters)).item())
+    flops = nthr * iters * 16
+    return {"tflops": flops / (best * 1e-3) / 1e12, "threads": nthr, "iters": iters, "ms": best, "exact": ok,
+            "nominal_tflops": sms * 128 * 2 * 2.07e9 / 1e12}
+
+
+def roofline(stage_ms, n, n_keys, P, blended, walked, fma):
+    """The dominant kernel against its bound.  The compositing kernels are
+    bound by FP32 arithmetic issue, not HBM: achieved = FLOP per evaluated
+    fragment x evaluated fragments (sum of last_idx) / the kernel's CUDA-event
+    time, against the FMA throughput measured in this run; the per-blended
+    view and the forward's fraction beside it."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -383,19 +445,26 @@ def roofline(stage_ms, n, n_keys, P, blended, clk):
     t = stage_ms[dom] * 1e-3
     ent = committed_counters(dom)
     traffic = ent.get("dram_bytes_per_launch")
-    issue = ent.get("issue_active_pct")
-    if dom in FLOP_PER_FRAGMENT:
-        # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 (FMA)
-        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = 152 * 128 * 2 * max_mhz * 1e6 / 1e12
-        flops = FLOP_PER_FRAGMENT[dom] * blended
-        ach = flops / t / 1e12
-        # issue_active_pct: ncu's smsp__issue_active of the same source (the
-        # share of issue slots the kernel uses: its practical ceiling)
-        return {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                "algorithmic_flops": flops, "blended_fragments": blended, "avg_ms": stage_ms[dom],
-                "issue_active_pct": issue}
+    if dom in FLOP_PER_EVALUATED:
+        peak = fma["tflops"]
+
+        def view(stage, per, units):
+            ach = per * units / (stage_ms[stage] * 1e-3) / 1e12
+            return {"achieved": ach, "frac": ach / peak, "flop_per_unit": per, "units": units,
+                    "avg_ms": stage_ms[stage]}
+
+        ev = view(dom, FLOP_PER_EVALUATED[dom], walked)
+        other = "render_fwd_loss" if dom == "render_bwd" else "render_bwd"
+        return {"bound": "alu", "kernel": dom, "achieved": ev["achieved"], "peak": peak, "unit": "TFLOP/s",
+                "frac": ev["frac"], "traffic": traffic,
+                "peak_source": "measured in this run: gs_probe_fma_f32 (8 independent FMA chains per thread, "
+                               "2048 threads per SM, best of 10)",
+                "work": f"{FLOP_PER_EVALUATED[dom]} FLOP + 1 exp per evaluated fragment (sum of last_idx)",
+                "evaluated_fragments": walked, "algorithmic_flops": FLOP_PER_EVALUATED[dom] * walked,
+                "avg_ms": stage_ms[dom], "exp_per_s": walked / t,
+                "per_blended": view(dom, FLOP_PER_FRAGMENT[dom], blended),
+                other: view(other, FLOP_PER_EVALUATED[other], walked),
+                "fma_probe": fma, "issue_active_pct": ent.get("issue_active_pct")}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     alg = stage_bytes(n, n_keys, P)[dom]
     ach = alg / t / 1e9
@@ -442,6 +511,10 @@ def serving_bench(frames=6, sessions=16):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands (single-threaded C) on
+    one host core, each step one full tracking iteration of the benchmark
+    workload (projection, binning + sort, forward, L1 loss, backward,
+    backward projection + pose gradient of 200k Gaussians at 640x480)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -450,26 +523,25 @@ def run_reference(args):
     O.build()
     scene, true_cam, start_cam = S.tracking_workload(N_G, W_IMG, H_IMG)
     _, true_img = O.forward(scene, true_cam)
-    band = 48  # rows per step: keeps a 100-step run within a few minutes
     for _ in range(args.warmup):
-        oracle_iteration(scene, true_img, start_cam, band)
-    ext = []
+        oracle_iteration(scene, true_img, start_cam, H_IMG)
+    per = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, full = oracle_iteration(scene, true_img, start_cam, band)
-        ext.append(full)
+        t1 = time.perf_counter()
+        oracle_iteration(scene, true_img, start_cam, H_IMG)
+        per.append(time.perf_counter() - t1)
     wall = time.perf_counter() - t0
-    t = sum(ext) / len(ext)
-    v = 1.0 / t
+    v = args.steps / wall
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mpix_per_s": W_IMG * H_IMG * v / 1e6,
-                       "sample": f"each step: full projection and backward projection of 200k Gaussians, "
-                                 f"binning/forward/loss/backward on a {band}-row band, per-pixel time scaled "
-                                 f"by {H_IMG}/{band}; wall {wall:.1f} s"},
+                       "step_s_p50": statistics.median(per), "step_s_max": max(per),
+                       "sample": f"each step one full 640x480 / 200k tracking iteration of the FP64 oracle "
+                                 f"(no extrapolation); wall {wall:.1f} s for {args.steps} steps"},
             "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{band}-row band per step, extrapolated to 640x480"},
+                             "sample": f"{args.steps} full iterations on one core"},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -496,6 +568,9 @@ def run_ours(args):
     from paper_2510_06644_gb300.pipeline import Rasterizer
     from synth import scenes as S
 
+    clocks = Clocks(local)
+    if not args.profile:
+        clocks.start()
     scene, true_cam, start_cam = S.tracking_workload(N_G, W_IMG, H_IMG)
     gd = {k: torch.from_numpy(v).cuda() for k, v in scene.items()}
     n = N_G
@@ -556,18 +631,17 @@ def run_ours(args):
     pose.copy_(pose0)
     adam.zero_()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    clocks = Clocks(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    t_wall0 = time.time()
     for i in range(K):
         flush.zero_()
         ev[i][0].record()
         run()
         ev[i][1].record()
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clocks.mark_timed(t_wall0, time.time())
     rast.check()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = sum(step_ms)
@@ -609,7 +683,8 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel ----
     blended = int(rast.img["n_blended"].long().sum().item())
-    roof = roofline(stage_ms, n, n_keys, P, blended, clk)
+    fma = fma_probe(gs)
+    roof = roofline(stage_ms, n, n_keys, P, blended, walked, fma)
     hbm = hbm_fractions(stage_ms, n, n_keys, P, t_max / K)
 
     # ---- the backward's global reductions against the probe's measured rate
@@ -703,10 +778,11 @@ def run_ours(args):
         "variants": variants,
         "e2e": e2e,
         "gpu_launches": launches_per_step * K,
-        "clocks": clk,
     }
     if not args.skip_serving:
         line["serving"] = serving_bench(args.serving_frames)
+    torch.cuda.synchronize()
+    line["clocks"] = clocks.stop()
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -485,6 +485,15 @@ gs_status gs_status_reset(gs_stream stream);
  * times it.  GS_ERR_INVALID_ARG for a NULL dst or a non-positive count. */
 gs_status gs_probe_red_f32(float* dst, int64_t n_dst, int64_t n_threads, int32_t per_thread, gs_stream stream);
 
+/* FP32 fused multiply-add throughput, the peak the compositing kernels'
+ * per-fragment arithmetic (Sec. 2.1 Eq. 2-3, Sec. 2.2 Eq. 4-5) is measured
+ * against: each of n_threads threads runs 8 independent chains of `iters`
+ * FMAs (16 FLOP per iteration) and writes out[t] = 28 + 8 iters (exact for
+ * iters < 2^21).  out: device float[n_threads], owned by the caller.
+ * Enqueued on `stream`; the caller times it.  GS_ERR_INVALID_ARG for a NULL
+ * out or a non-positive count. */
+gs_status gs_probe_fma_f32(float* out, int64_t n_threads, int32_t iters, gs_stream stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char* gs_last_error(void);
 

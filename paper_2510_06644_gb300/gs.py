@@ -92,6 +92,7 @@ _SIGS = {
     "gs_adam": ([C.c_int, _P, _P, _P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float, _P, _P], C.c_int),
     "gs_status_poll": ([_P, C.c_int, _P], C.c_int),
     "gs_probe_red_f32": ([_P, C.c_int64, C.c_int64, C.c_int32, _P], C.c_int),
+    "gs_probe_fma_f32": ([_P, C.c_int64, C.c_int32, _P], C.c_int),
     "gs_status_reset": ([_P], C.c_int),
     "gs_last_error": ([], C.c_char_p),
 }
@@ -536,6 +537,12 @@ def gs_probe_red_f32(dst, n_threads, per_thread, stream=None):
         raise ValueError("float32 dst expected")
     _check(lib().gs_probe_red_f32(_ptr(dst), int(dst.numel()), int(n_threads), int(per_thread), _stream(stream)),
            "gs_probe_red_f32")
+
+
+def gs_probe_fma_f32(out, iters, stream=None):
+    """FMA-throughput probe: each of out.numel() threads runs 8 chains of
+    `iters` FMAs (16 FLOP per iteration) and writes 28 + 8 iters."""
+    _check(lib().gs_probe_fma_f32(_ptr(out), int(out.numel()), int(iters), _stream(stream)), "gs_probe_fma_f32")
 
 
 def gs_status_poll(blocking=True, stream=None):

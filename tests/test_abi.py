@@ -114,6 +114,9 @@ def test_reduction_probe_rejects_bad_arguments_on_the_host(built_lib):
     fake = ctypes.c_void_p(16)  # never dereferenced: the counts are checked first
     for n_dst, n_thr, per in ((0, 16, 1), (16, 0, 1), (16, 16, 0), (16, -5, 1)):
         assert L.gs_probe_red_f32(fake, n_dst, n_thr, per, None) == gs.GS_ERR_INVALID_ARG
+    assert L.gs_probe_fma_f32(None, 16, 1, None) == gs.GS_ERR_INVALID_ARG
+    for n_thr, iters in ((0, 1), (16, 0), (-3, 4)):
+        assert L.gs_probe_fma_f32(fake, n_thr, iters, None) == gs.GS_ERR_INVALID_ARG
 
 
 def test_blend_mask_words_host_arithmetic(built_lib):

@@ -46,11 +46,33 @@ def test_hbm_fractions_add_up():
 
 def test_alu_roofline_of_the_dominant_compositing_kernel():
     stage_ms = {"project_bin_sort": 0.07, "render_fwd_loss": 0.09, "render_bwd": 0.15, "project_bwd_pose_step": 0.02}
-    r = bench.roofline(stage_ms, 200_000, 491_000, 640 * 480, blended=12_570_000, clk=None)
+    fma = {"tflops": 78.0}
+    walked, blended = 54_000_000, 12_570_000
+    r = bench.roofline(stage_ms, 200_000, 491_000, 640 * 480, blended, walked, fma)
     assert r["bound"] == "alu" and r["kernel"] == "render_bwd" and r["unit"] == "TFLOP/s"
-    flops = bench.FLOP_PER_FRAGMENT["render_bwd"] * 12_570_000
-    assert r["algorithmic_flops"] == flops
-    assert r["achieved"] == pytest.approx(flops / 0.15e-3 / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    # 152 SMs x 128 lanes x 2 FLOPs x the maximum SM clock
-    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2070.0e6 / 1e12, rel=1e-6)
+    # 45 FLOP per evaluated fragment (sum of last_idx) against the measured FMA peak
+    assert r["algorithmic_flops"] == 45 * walked
+    assert r["achieved"] == pytest.approx(45 * walked / 0.15e-3 / 1e12)
+    assert r["peak"] == 78.0
+    assert r["frac"] == pytest.approx(r["achieved"] / 78.0)
+    # the per-blended view and the forward beside it
+    assert r["per_blended"]["achieved"] == pytest.approx(67 * blended / 0.15e-3 / 1e12)
+    assert r["render_fwd_loss"]["achieved"] == pytest.approx(15 * walked / 0.09e-3 / 1e12)
+    assert r["render_fwd_loss"]["frac"] == pytest.approx(r["render_fwd_loss"]["achieved"] / 78.0)
+
+
+def test_clock_summary_counts_the_timed_samples():
+    import datetime
+    t0 = datetime.datetime(2026, 1, 1, 12, 0, 0).timestamp()
+
+    def row(dt, mhz, pcap="Not Active"):
+        ts = datetime.datetime.fromtimestamp(t0 + dt).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 500.5, 0x0, Not Active, Not Active, Not Active, {pcap}"
+
+    lines = [row(0.0, 1900), row(0.1, 2070), row(0.2, 2070, "Active"), row(0.3, 2000), "garbage line"]
+    c = bench.Clocks.parse(lines, timed=[(t0 + 0.15, t0 + 0.25)])
+    assert c["samples"] == 4 and c["sm_max_mhz"] == 2070.0
+    assert c["sm_mhz"] == pytest.approx(2035.0)
+    assert c["reasons"] == ["sw_power_cap"]
+    # the timed region (widened by one sampling interval) holds the samples at 0.1, 0.2 and 0.3 s
+    assert c["samples_timed"] == 3 and c["sm_mhz_timed"] == 2070.0

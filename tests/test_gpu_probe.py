@@ -1,5 +1,7 @@
-"""The reduction-throughput probe does exactly the adds it states (its
-timing is the denominator of the backward's atomic-throughput fraction)."""
+"""The measurement probes do exactly the work they state: the reduction
+probe's adds (its timing is the denominator of the backward's
+atomic-throughput fraction) and the FMA probe's chains (the denominator of
+the compositing kernels' ALU fraction)."""
 import pytest
 import torch
 
@@ -25,3 +27,11 @@ def test_probe_adds_exactly(G, n_dst, n_threads, per):
     idx = torch.arange(n_threads) % n_dst
     want.index_add_(0, idx, torch.full((n_threads,), float(per), dtype=torch.float64))
     assert torch.equal(dst.cpu().double(), want)
+
+
+@pytest.mark.parametrize("n_threads,iters", [(1, 1), (300, 7), (4096, 1000)])
+def test_fma_probe_runs_every_chain(G, n_threads, iters):
+    out = torch.full((n_threads,), -1.0, dtype=torch.float32, device="cuda")
+    G.gs_probe_fma_f32(out, iters)
+    torch.cuda.synchronize()
+    assert torch.all(out.cpu() == float(28 + 8 * iters))
