@@ -450,6 +450,67 @@ gs_status gs_project_bwd_step(const gs_config* cfg, const gs_camera* cam, const 
                               float* score_terms, const gs_pose_step* step, void* workspace,
                               size_t* workspace_bytes, gs_stream stream);
 
+/* ---------------------------------------------------------------------- */
+/* Multi-session waves (serving form)                                       */
+/* ---------------------------------------------------------------------- */
+/* One session's fused tracking iteration inside a wave: everything
+ * gs_project_bin_sort + gs_render_fwd_loss + gs_render_bwd(GS_TRACK) +
+ * gs_project_bwd_step take for that session, with the same meaning and
+ * layouts.  All pointers are device memory owned by the caller and must stay
+ * valid until the wave's work on `stream` has completed.  The paper runs
+ * many frames through one rasterizer (its frame-level programming interface,
+ * Sec. 5.5); a wave is that interface for many concurrent sessions. */
+typedef struct {
+    gs_camera cam;            /* the session's camera; cam.pose is read on the device */
+    gs_gaussians g;           /* the session's map; g.n >= 1 */
+    float* splats;            /* float32 records [g.n][12] (GS_F32 layout) */
+    int64_t keys_capacity;    /* in [1, 2^30) */
+    void* bin_workspace;      /* gs_project_bin_sort's workspace (256-byte aligned) */
+    size_t bin_workspace_bytes;
+    uint64_t* keys;           /* [keys_capacity] */
+    uint32_t* vals;           /* [keys_capacity] */
+    int64_t* n_keys;          /* device int64 */
+    uint32_t* tile_ranges;    /* [T][2] */
+    uint32_t* tile_order;     /* [T] */
+    float* rgb;               /* [3][Hs][Ws] */
+    float* depth;             /* [Hs][Ws] */
+    float* t_final;           /* [Hs][Ws] */
+    uint32_t* last_idx;       /* [Hs][Ws] */
+    uint32_t* n_blended;      /* [Hs][Ws] or NULL */
+    uint32_t* blend_masks;    /* gs_blend_mask_words(cam, keys_capacity) words, or NULL */
+    const float* target_rgb;  /* [3][Hs][Ws] */
+    const float* target_depth;/* [Hs][Ws] (0 = no depth measurement) */
+    float* d_rgb;             /* [3][Hs][Ws] */
+    float* d_depth;           /* [Hs][Ws] */
+    double* loss;             /* device double */
+    float* grad2d;            /* [g.n][12], 16-byte aligned */
+    double* pose_grad6;       /* device double[6] */
+    float* score_terms;       /* [g.n][2] or NULL */
+    void* bwd_workspace;      /* gs_project_bwd's workspace */
+    size_t bwd_workspace_bytes;
+    gs_pose_step step;        /* the pose step applied after the reduction */
+} gs_track_job;
+
+/* Largest number of sessions in one wave. */
+#define GS_WAVE_MAX 32
+
+/* One tracking iteration of every job (Sec. 2.1 Steps 1-3, Sec. 2.2 Steps
+ * 4-5, Sec. 4.1 Eq. 6), each with the results of its own fused iteration,
+ * in launches whose grids span all jobs: projection with the binning's tile
+ * counts, the column scan with the tile scan and order, the key scatter, the
+ * bucket sort, the forward compositing with the loss, the backward
+ * compositing and the backward projection with the pose step -- one launch
+ * each (the compositing ones once per kernel form present: full-resolution
+ * tiles, strided tiles of up to 32 or 64 sampled pixels).  Each CTA finds its
+ * job and its block inside the job from the wave's descriptor table, which
+ * travels in the launch's parameter space (no device allocation, no copy).
+ * jobs: host array of n_jobs (1..GS_WAVE_MAX) descriptors; the jobs' buffers
+ * must not overlap.  Limits: float32 records, at most 8192 tiles per job.
+ * Errors: GS_ERR_INVALID_ARG / GS_ERR_WORKSPACE (naming the job) before
+ * anything is enqueued; key-capacity overflow sets the device status word as
+ * in gs_bin_sort. */
+gs_status gs_track_wave(const gs_config* cfg, const gs_track_job* jobs, int32_t n_jobs, gs_stream stream);
+
 /* Mapping step: Adam over up to GS_ADAM_MAX_TENSORS float32 arrays in one
  * launch (the map update fed by the backward, Sec. 2.2 Step 5 / Sec. 5.4;
  * the optimizer itself is not fixed by the paper).  params[t], grads[t],

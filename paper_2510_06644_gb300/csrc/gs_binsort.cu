@@ -30,6 +30,8 @@
 //                   depth_bits and the id.
 // The scatter order inside a bucket depends on atomics, the output does not.
 // Everything stays on the device: the key count is never read by the host.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -88,12 +90,12 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_hist(gs_camera cam, float 
 // the rows into 32 consecutive ranges, sum them, scan the 32 partial sums in
 // shared memory and write each row's exclusive prefix in place.
 __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int nrows, int ntiles,
-                                              uint32_t* __restrict__ total) {
+                                              uint32_t* __restrict__ total, int blk) {
     // CTA: CS_TILES tiles x (1024 / CS_TILES) row groups of consecutive rows
     constexpr int CS_TILES = 8, CS_GROUPS = 1024 / CS_TILES;
     __shared__ uint32_t part[CS_GROUPS][CS_TILES + 1];
     const int tx = threadIdx.x % CS_TILES, ty = threadIdx.x / CS_TILES;
-    const int t = blockIdx.x * CS_TILES + tx;
+    const int t = blk * CS_TILES + tx;
     const int per = (nrows + CS_GROUPS - 1) / CS_GROUPS;
     const int r0 = min(nrows, ty * per), r1 = min(nrows, r0 + per);
     // rows in groups of 8 loads issued back to back (a dependent sum per
@@ -131,7 +133,7 @@ __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int n
             part[lane * (CS_GROUPS / 32) + k][w] = run;
             run += v[k];
         }
-        const int tc = blockIdx.x * CS_TILES + w;
+        const int tc = blk * CS_TILES + w;
         if (lane == 31 && tc < ntiles) total[tc] = incl;
     }
     __syncthreads();
@@ -152,7 +154,7 @@ __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int n
 
 __global__ void __launch_bounds__(1024) k_col_scan(uint32_t* __restrict__ hist, int nrows, int ntiles,
                                                    uint32_t* __restrict__ total) {
-    col_scan_body(hist, nrows, ntiles, total);
+    col_scan_body(hist, nrows, ntiles, total, (int)blockIdx.x);
 }
 
 // Heavy-first tile order (defined below with the tile scan).
@@ -322,13 +324,14 @@ struct ScanTail {
     uint32_t* n_big;
 };
 
-__global__ void __launch_bounds__(1024) k_col_scan_tail(uint32_t* __restrict__ hist, int nrows, int ntiles,
-                                                        uint32_t* __restrict__ total, ScanTail T) {
+__device__ __forceinline__ void col_scan_tail_body(uint32_t* __restrict__ hist, int nrows, int ntiles,
+                                                   uint32_t* __restrict__ total, const ScanTail& T, int blk,
+                                                   int nblk) {
     __shared__ bool s_last;
-    col_scan_body(hist, nrows, ntiles, total);
+    col_scan_body(hist, nrows, ntiles, total, blk);
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(T.ticket, 1u) == gridDim.x - 1u;
+    if (threadIdx.x == 0) s_last = atomicAdd(T.ticket, 1u) == (unsigned)nblk - 1u;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -338,31 +341,34 @@ __global__ void __launch_bounds__(1024) k_col_scan_tail(uint32_t* __restrict__ h
     if (threadIdx.x == 0) *T.ticket = 0u;
 }
 
+__global__ void __launch_bounds__(1024) k_col_scan_tail(uint32_t* __restrict__ hist, int nrows, int ntiles,
+                                                        uint32_t* __restrict__ total, ScanTail T) {
+    col_scan_tail_body(hist, nrows, ntiles, total, T, (int)blockIdx.x, (int)gridDim.x);
+}
+
 // k_tile_scatter_rows with the rects the fused projection kept (no
 // geometry re-read, no tile-rect arithmetic): only the depth is loaded.
 template <int DT>
-__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rects(int TX, const void* __restrict__ splats, int64_t n,
-                                                                    int64_t per_cta, int ntiles,
-                                                                    const uint32_t* __restrict__ start,
-                                                                    const uint32_t* __restrict__ hist,
-                                                                    const uint2* __restrict__ rects, int64_t cap,
-                                                                    u64* __restrict__ keys,
-                                                                    const uint32_t* __restrict__ ranges,
-                                                                    uint32_t* __restrict__ order,
-                                                                    uint32_t* __restrict__ n_big) {
-    if (blockIdx.x == gridDim.x - 1) {  // the heavy-first order, beside the scatter
+__device__ __forceinline__ void scatter_rects_body(int TX, const void* __restrict__ splats, int64_t n,
+                                                   int64_t per_cta, int ntiles, const uint32_t* __restrict__ start,
+                                                   const uint32_t* __restrict__ hist,
+                                                   const uint2* __restrict__ rects, int64_t cap,
+                                                   u64* __restrict__ keys, const uint32_t* __restrict__ ranges,
+                                                   uint32_t* __restrict__ order, uint32_t* __restrict__ n_big,
+                                                   int blk, int nblk) {
+    if (blk == nblk - 1) {  // the heavy-first order, beside the scatter
         tile_order_body(ranges, ntiles, order, n_big);
         return;
     }
     extern __shared__ uint32_t h[];
     uint32_t* base = h + ntiles;
-    const uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
+    const uint32_t* row = hist + (size_t)blk * ntiles;
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
         h[t] = 0;
         base[t] = start[t] + row[t];
     }
     __syncthreads();
-    const int64_t k0 = (int64_t)blockIdx.x * per_cta, k1 = min(n, k0 + per_cta);
+    const int64_t k0 = (int64_t)blk * per_cta, k1 = min(n, k0 + per_cta);
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         const uint2 r = __ldg(rects + k);
         const int x0 = (int)(r.x & 0xffffu), x1 = (int)(r.x >> 16), y0 = (int)(r.y & 0xffffu), y1 = (int)(r.y >> 16);
@@ -377,6 +383,20 @@ __global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rects(int TX, cons
                 if ((int64_t)pos < cap) keys[pos] = rem;
             }
     }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(BIN_THREADS) k_tile_scatter_rects(int TX, const void* __restrict__ splats, int64_t n,
+                                                                    int64_t per_cta, int ntiles,
+                                                                    const uint32_t* __restrict__ start,
+                                                                    const uint32_t* __restrict__ hist,
+                                                                    const uint2* __restrict__ rects, int64_t cap,
+                                                                    u64* __restrict__ keys,
+                                                                    const uint32_t* __restrict__ ranges,
+                                                                    uint32_t* __restrict__ order,
+                                                                    uint32_t* __restrict__ n_big) {
+    scatter_rects_body<DT>(TX, splats, n, per_cta, ntiles, start, hist, rects, cap, keys, ranges, order, n_big,
+                           (int)blockIdx.x, (int)gridDim.x);
 }
 
 template <int DT>
@@ -546,16 +566,15 @@ __device__ __forceinline__ void warp_sort_bucket(u64* key, uint32_t* val, int n,
 // One launch for all buckets.  CTAs below n_big take the long buckets
 // (first in the order), one each; every later CTA takes 16 short buckets,
 // one per warp (both kinds run at once).
-__global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __restrict__ ranges,
-                                                          const uint32_t* __restrict__ order,
-                                                          const uint32_t* __restrict__ n_big_p, int ntiles,
-                                                          u64* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                          u64* __restrict__ tmp) {
+__device__ __forceinline__ void tile_sort_body(const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
+                                               const uint32_t* __restrict__ n_big_p, int ntiles,
+                                               u64* __restrict__ keys, uint32_t* __restrict__ vals,
+                                               u64* __restrict__ tmp, int blk) {
     extern __shared__ __align__(16) u64 s[];
     const int n_big = (int)*n_big_p;
-    if ((int)blockIdx.x >= n_big) {
+    if (blk >= n_big) {
         const int warp = threadIdx.x >> 5;
-        const int idx = n_big + ((int)blockIdx.x - n_big) * (TS_THREADS / 32) + warp;
+        const int idx = n_big + (blk - n_big) * (TS_THREADS / 32) + warp;
         if (idx >= ntiles) return;
         const int t = (int)order[idx];
         const uint32_t b = ranges[2 * t], e = ranges[2 * t + 1];
@@ -570,7 +589,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __rest
         else warp_sort_bucket<16>(keys + b, vals + b, n, hi, buf);
         return;
     }
-    const int t = (int)order[blockIdx.x];
+    const int t = (int)order[blk];
     const uint32_t b = ranges[2 * t], e = ranges[2 * t + 1];
     const int n = (int)(e - b);
     u64* key = keys + b;
@@ -626,6 +645,71 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __rest
     __syncthreads();
     if (src == key)
         for (int i = threadIdx.x; i < n; i += blockDim.x) key[i] = hi | (key[i] >> 32);
+}
+
+__global__ void __launch_bounds__(TS_THREADS) k_tile_sort(const uint32_t* __restrict__ ranges,
+                                                          const uint32_t* __restrict__ order,
+                                                          const uint32_t* __restrict__ n_big_p, int ntiles,
+                                                          u64* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                          u64* __restrict__ tmp) {
+    tile_sort_body(ranges, order, n_big_p, ntiles, keys, vals, tmp, (int)blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Multi-session waves: column scan (+ tile scan and order), scatter and sort
+// over every job of a wave (gs_track_wave)
+// ---------------------------------------------------------------------------
+struct WaveScanJob {
+    uint32_t* hist;
+    int nrows, ntiles;
+    uint32_t* total;
+    ScanTail tail;
+};
+
+__global__ void __launch_bounds__(1024) k_wave_col_scan_tail(const __grid_constant__ Wave<WaveScanJob> W) {
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveScanJob& J = W.job[j];
+    col_scan_tail_body(J.hist, J.nrows, J.ntiles, J.total, J.tail, (int)blockIdx.x - W.start[j],
+                       W.start[j + 1] - W.start[j]);
+}
+
+struct WaveScatterJob {
+    int TX;
+    const void* splats;
+    int64_t n, per;
+    int ntiles;
+    const uint32_t* start;
+    const uint32_t* hist;
+    const uint2* rects;
+    int64_t cap;
+    u64* keys;
+    const uint32_t* ranges;
+    uint32_t* order;
+    uint32_t* n_big;
+};
+
+__global__ void __launch_bounds__(BIN_THREADS) k_wave_scatter_rects(const __grid_constant__ Wave<WaveScatterJob> W) {
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveScatterJob& J = W.job[j];
+    scatter_rects_body<GS_F32>(J.TX, J.splats, J.n, J.per, J.ntiles, J.start, J.hist, J.rects, J.cap, J.keys,
+                               J.ranges, J.order, J.n_big, (int)blockIdx.x - W.start[j],
+                               W.start[j + 1] - W.start[j]);
+}
+
+struct WaveSortJob {
+    const uint32_t* ranges;
+    const uint32_t* order;
+    const uint32_t* n_big;
+    int ntiles;
+    u64* keys;
+    uint32_t* vals;
+    u64* tmp;
+};
+
+__global__ void __launch_bounds__(TS_THREADS) k_wave_tile_sort(const __grid_constant__ Wave<WaveSortJob> W) {
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveSortJob& J = W.job[j];
+    tile_sort_body(J.ranges, J.order, J.n_big, J.ntiles, J.keys, J.vals, J.tmp, (int)blockIdx.x - W.start[j]);
 }
 
 // ---------------------------------------------------------------------------
@@ -927,3 +1011,110 @@ extern "C" gs_status gs_project_bin_sort(const gs_config* cfg, const gs_camera* 
     if ((s = check_launch("k_tile_scatter_rects")) != GS_OK) return s;
     return launch_tile_sort(ntiles, tile_ranges, order, n_big, keys_out, vals_out, tmp, st);
 }
+
+// ---------------------------------------------------------------------------
+// Wave launchers (gs_track_wave)
+// ---------------------------------------------------------------------------
+namespace gs {
+
+// The job's binning state inside its gs_project_bin_sort workspace (the same
+// layout as the single-session call), after checking the workspace size.
+gs_status wave_bin_layout(const gs_track_job& j, WaveBin* out) {
+    const Grid grid = make_grid(j.cam);
+    const int ntiles = grid.TX * grid.TY;
+    const int64_t n = j.g.n;
+    if (ntiles > AGG_MAX_TILES) return set_error(GS_ERR_INVALID_ARG, "more than %d tiles", AGG_MAX_TILES);
+    const BinLayout L = bin_layout(n, j.keys_capacity, ntiles);
+    const size_t total = align256(L.total + sizeof(uint2) * (size_t)n);
+    if (!j.bin_workspace || j.bin_workspace_bytes < total)
+        return set_error(GS_ERR_WORKSPACE, "bin workspace %zu < %zu bytes", j.bin_workspace_bytes, total);
+    if (((uintptr_t)j.bin_workspace & 255) != 0) return set_error(GS_ERR_INVALID_ARG, "bin workspace not 256-byte aligned");
+    char* ws = (char*)j.bin_workspace;
+    out->per = agg_per_cta(n, ntiles);
+    out->nb = (unsigned)((n + out->per - 1) / out->per);
+    out->ntiles = ntiles;
+    out->count = (uint32_t*)(ws + L.off_count);
+    out->start = (uint32_t*)(ws + L.off_start);
+    out->hist = (uint32_t*)(ws + L.off_hist);
+    out->ticket = (unsigned int*)(ws + L.off_ticket);
+    out->n_big = (uint32_t*)(ws + L.off_nbig);
+    out->tmp = ws + L.off_tmp;
+    out->rects = ws + L.total;
+    return GS_OK;
+}
+
+gs_status wave_bin_sort(const gs_track_job* jobs, const WaveBin* bins, int n, cudaStream_t st) {
+    unsigned int* err = status_ptr();
+    if (!err) return set_error(GS_ERR_CUDA, "status word address");
+    gs_status s;
+    {
+        Wave<WaveScanJob> W;
+        W.n = n;
+        int blocks = 0;
+        for (int j = 0; j < n; ++j) {
+            const gs_track_job& t = jobs[j];
+            const WaveBin& b = bins[j];
+            W.start[j] = blocks;
+            blocks += (b.ntiles + 7) / 8;
+            const ScanTail tail = {b.ticket, t.keys_capacity, b.start, t.tile_ranges, t.n_keys, err, nullptr, b.n_big};
+            W.job[j] = WaveScanJob{b.hist, (int)b.nb, b.ntiles, b.count, tail};
+        }
+        W.start[n] = blocks;
+        k_wave_col_scan_tail<<<(unsigned)blocks, 1024, 0, st>>>(W);
+        if ((s = check_launch("k_wave_col_scan_tail")) != GS_OK) return s;
+    }
+    {
+        static bool attr_done[64] = {false};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+            if (cudaFuncSetAttribute(k_wave_scatter_rects, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(2 * AGG_MAX_TILES * sizeof(uint32_t))) != cudaSuccess)
+                return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(k_wave_scatter_rects)");
+            if (dev >= 0 && dev < 64) attr_done[dev] = true;
+        }
+        Wave<WaveScatterJob> W;
+        W.n = n;
+        int blocks = 0, smax = 1;
+        for (int j = 0; j < n; ++j) {
+            const gs_track_job& t = jobs[j];
+            const WaveBin& b = bins[j];
+            W.start[j] = blocks;
+            blocks += (int)b.nb + 1;  // + the CTA that computes the heavy-first order
+            smax = std::max(smax, b.ntiles);
+            W.job[j] = WaveScatterJob{make_grid(t.cam).TX, t.splats, t.g.n, b.per, b.ntiles, b.start, b.hist,
+                                      (const uint2*)b.rects, t.keys_capacity, (u64*)t.keys, t.tile_ranges,
+                                      t.tile_order, b.n_big};
+        }
+        W.start[n] = blocks;
+        k_wave_scatter_rects<<<(unsigned)blocks, BIN_THREADS, 2 * sizeof(uint32_t) * (size_t)smax, st>>>(W);
+        if ((s = check_launch("k_wave_scatter_rects")) != GS_OK) return s;
+    }
+    {
+        static bool attr_done[64] = {false};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const int sm = (int)((TS_SMEM_KEYS + TS_SMEM_KEYS / 16) * sizeof(u64));
+        if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+            if (cudaFuncSetAttribute(k_wave_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+                return set_error(GS_ERR_CUDA, "cudaFuncSetAttribute(k_wave_tile_sort)");
+            if (dev >= 0 && dev < 64) attr_done[dev] = true;
+        }
+        Wave<WaveSortJob> W;
+        W.n = n;
+        int blocks = 0;
+        for (int j = 0; j < n; ++j) {
+            const gs_track_job& t = jobs[j];
+            const WaveBin& b = bins[j];
+            W.start[j] = blocks;
+            blocks += b.ntiles;
+            W.job[j] = WaveSortJob{t.tile_ranges, t.tile_order, b.n_big, b.ntiles, (u64*)t.keys, t.vals, (u64*)b.tmp};
+        }
+        W.start[n] = blocks;
+        k_wave_tile_sort<<<(unsigned)blocks, TS_THREADS, (size_t)sm, st>>>(W);
+        if ((s = check_launch("k_wave_tile_sort")) != GS_OK) return s;
+    }
+    return GS_OK;
+}
+
+}  // namespace gs

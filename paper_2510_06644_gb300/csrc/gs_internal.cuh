@@ -242,6 +242,52 @@ __device__ __forceinline__ Geom load_geom(const void* base, uint32_t k) {
 }
 
 // ---------------------------------------------------------------------------
+// Multi-session waves (gs_track_wave)
+// ---------------------------------------------------------------------------
+// A wave launch's descriptor table: job j owns blocks [start[j], start[j+1])
+// of the grid.  It is passed by value as a __grid_constant__ kernel
+// parameter (constant bank), so every CTA reads it without a copy.
+template <typename J>
+struct Wave {
+    int n;
+    int start[GS_WAVE_MAX + 1];
+    J job[GS_WAVE_MAX];
+};
+
+// Job of block b: the largest j with start[j] <= b (binary search).
+__device__ __forceinline__ int wave_find(const int* start, int n, int b) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Where a job's binning state lives in its gs_project_bin_sort workspace.
+struct WaveBin {
+    int64_t per;          // Gaussians per projection / scatter CTA
+    unsigned nb;          // projection CTAs (rows of hist)
+    int ntiles;
+    uint32_t* count;      // tile totals
+    uint32_t* start;      // bucket starts
+    uint32_t* hist;       // per-CTA tile rows
+    unsigned int* ticket; // the column scan's ticket
+    uint32_t* n_big;
+    void* tmp;            // sort scratch
+    void* rects;          // kept tile rects
+};
+gs_status wave_bin_layout(const gs_track_job& j, WaveBin* out);
+unsigned int* wave_bwd_ticket(const gs_track_job& j);
+// The stages of a wave, in launch order.
+gs_status wave_project_hist(const gs_config& cfg, const gs_track_job* jobs, const WaveBin* bins, int n,
+                            cudaStream_t st);
+gs_status wave_bin_sort(const gs_track_job* jobs, const WaveBin* bins, int n, cudaStream_t st);
+gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cudaStream_t st);
+gs_status wave_project_bwd(const gs_config& cfg, const gs_track_job* jobs, int n, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
 // Reductions
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float warp_sum(float v) {

@@ -8,6 +8,8 @@
 // HBM-bound at large n.
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -166,15 +168,15 @@ __global__ void __launch_bounds__(256) k_project(gs_camera cam, gs_config cfg, g
 // c of `hist` (the per-CTA tile rows of the binning), and keeps each rect
 // (x0 | x1 << 16, y0 | y1 << 16; zero: no tile) for the scatter.
 template <int DT>
-__global__ void __launch_bounds__(256) k_project_hist(gs_camera cam, gs_config cfg, gs_gaussians g, void* out,
-                                                      int64_t per, int ntiles, uint32_t* __restrict__ hist,
-                                                      uint2* __restrict__ rects) {
+__device__ __forceinline__ void project_hist_body(gs_camera cam, const gs_config& cfg, const gs_gaussians& g,
+                                                  void* out, int64_t per, int ntiles, uint32_t* __restrict__ hist,
+                                                  uint2* __restrict__ rects, int blk) {
     extern __shared__ uint32_t h_row[];
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) h_row[t] = 0;
     __syncthreads();
     resolve_pose(cam);
     const Grid grid = make_grid(cam);
-    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(g.n, k0 + per);
+    const int64_t k0 = (int64_t)blk * per, k1 = min(g.n, k0 + per);
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         int x0, x1, y0, y1;
         const int touched = project_write<DT>(cam, cfg, g, grid, k, out, x0, x1, y0, y1);
@@ -184,8 +186,15 @@ __global__ void __launch_bounds__(256) k_project_hist(gs_camera cam, gs_config c
             for (int tx = x0; tx < x1; ++tx) atomicAdd(h_row + ty * grid.TX + tx, 1u);
     }
     __syncthreads();
-    uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
+    uint32_t* row = hist + (size_t)blk * ntiles;
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = h_row[t];
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_project_hist(gs_camera cam, gs_config cfg, gs_gaussians g, void* out,
+                                                      int64_t per, int ntiles, uint32_t* __restrict__ hist,
+                                                      uint2* __restrict__ rects) {
+    project_hist_body<DT>(cam, cfg, g, out, per, ntiles, hist, rects, (int)blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -304,13 +313,12 @@ __device__ void pose_final_last_block(const float2* __restrict__ part, int nblk,
 }
 
 template <bool WANT_GRADS, bool WANT_POSE, bool WANT_SCORE>
-__global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_config cfg,
-                                                            gs_gaussians g, const float* __restrict__ grad2d,
-                                                            gs_grads grads, float* __restrict__ score,
-                                                            float2* __restrict__ pose_part,
-                                                            double* __restrict__ pose_out,
-                                                            unsigned int* __restrict__ ticket, gs_pose_step step) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void project_bwd_body(gs_camera cam, const gs_config& cfg, const gs_gaussians& g,
+                                                 const float* __restrict__ grad2d, const gs_grads& grads,
+                                                 float* __restrict__ score, float2* __restrict__ pose_part,
+                                                 double* __restrict__ pose_out, unsigned int* __restrict__ ticket,
+                                                 const gs_pose_step& step, int blk, int nblk) {
+    const int64_t k = (int64_t)blk * blockDim.x + threadIdx.x;
     float pose[6] = {0, 0, 0, 0, 0, 0};
     resolve_pose(cam);
     if (k < g.n) {
@@ -469,10 +477,80 @@ __global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_co
         if (threadIdx.x < 6) {
             DF s{0.f, 0.f};
             for (int w = 0; w < PB_THREADS / 32; ++w) s = df_add(s, DF{ws[w][threadIdx.x], 0.f});
-            pose_part[(size_t)blockIdx.x * 6 + threadIdx.x] = make_float2(s.hi, s.lo);
+            pose_part[(size_t)blk * 6 + threadIdx.x] = make_float2(s.hi, s.lo);
         }
-        pose_final_last_block(pose_part, (int)gridDim.x, pose_out, ticket, step);
+        pose_final_last_block(pose_part, nblk, pose_out, ticket, step);
     }
+}
+
+template <bool WANT_GRADS, bool WANT_POSE, bool WANT_SCORE>
+__global__ void __launch_bounds__(PB_THREADS) k_project_bwd(gs_camera cam, gs_config cfg,
+                                                            gs_gaussians g, const float* __restrict__ grad2d,
+                                                            gs_grads grads, float* __restrict__ score,
+                                                            float2* __restrict__ pose_part,
+                                                            double* __restrict__ pose_out,
+                                                            unsigned int* __restrict__ ticket, gs_pose_step step) {
+    project_bwd_body<WANT_GRADS, WANT_POSE, WANT_SCORE>(cam, cfg, g, grad2d, grads, score, pose_part, pose_out,
+                                                        ticket, step, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Multi-session waves: the projection with the binning's tile rows, and the
+// backward projection with the pose step, over every job of a wave
+// ---------------------------------------------------------------------------
+struct WaveProjJob {
+    gs_camera cam;
+    gs_gaussians g;
+    float* splats;
+    int64_t per;
+    int ntiles;
+    uint32_t* hist;
+    uint2* rects;
+    // zeroed here for the later stages of the wave: the column scan's ticket,
+    // the backward projection's ticket, the loss and the 2D gradients
+    unsigned int* bin_ticket;
+    unsigned int* bwd_ticket;
+    double* loss;
+    float* grad2d;
+};
+
+__global__ void __launch_bounds__(256) k_wave_project_hist(const gs_config cfg,
+                                                           const __grid_constant__ Wave<WaveProjJob> W) {
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveProjJob& J = W.job[j];
+    const int blk = (int)blockIdx.x - W.start[j];
+    if (blk == 0 && threadIdx.x == 0) {
+        *J.bin_ticket = 0u;
+        *J.bwd_ticket = 0u;
+        *J.loss = 0.0;
+    }
+    // this CTA's Gaussians' 2D gradient rows (the backward accumulates into them)
+    const int64_t k0 = (int64_t)blk * J.per, k1 = min(J.g.n, k0 + J.per);
+    float4* g4 = reinterpret_cast<float4*>(J.grad2d);
+    for (int64_t q = 3 * k0 + threadIdx.x; q < 3 * k1; q += blockDim.x) g4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    project_hist_body<GS_F32>(J.cam, cfg, J.g, J.splats, J.per, J.ntiles, J.hist, J.rects, blk);
+}
+
+struct WavePbJob {
+    gs_camera cam;
+    gs_gaussians g;
+    const float* grad2d;
+    float* score;
+    float2* part;
+    double* pose_out;
+    unsigned int* ticket;
+    gs_pose_step step;
+};
+
+template <bool WANT_SCORE>
+__global__ void __launch_bounds__(PB_THREADS) k_wave_project_bwd(const gs_config cfg,
+                                                                 const __grid_constant__ Wave<WavePbJob> W) {
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WavePbJob& J = W.job[j];
+    const gs_grads none = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    project_bwd_body<false, true, WANT_SCORE>(J.cam, cfg, J.g, J.grad2d, none, J.score, J.part, J.pose_out,
+                                              J.ticket, J.step, (int)blockIdx.x - W.start[j],
+                                              W.start[j + 1] - W.start[j]);
 }
 
 // Launches k_project_hist (nb CTAs of `per` Gaussians; ntiles words of
@@ -658,3 +736,56 @@ extern "C" gs_status gs_project_bwd_noalloc(const gs_config* cfg, const gs_camer
     size_t have = (size_t)GS_NOALLOC_SCRATCH_BYTES;
     return gs_project_bwd(cfg, cam, g, grad2d, grads, pose_grad6, score_terms, scratch, &have, stream);
 }
+
+// ---------------------------------------------------------------------------
+// Wave launchers (gs_track_wave)
+// ---------------------------------------------------------------------------
+namespace gs {
+
+unsigned int* wave_bwd_ticket(const gs_track_job& j) {
+    const size_t need = gs_project_bwd_ws(j.g.n);
+    return (unsigned int*)((char*)j.bwd_workspace + need - 256);
+}
+
+gs_status wave_project_hist(const gs_config& cfg, const gs_track_job* jobs, const WaveBin* bins, int n,
+                            cudaStream_t st) {
+    Wave<WaveProjJob> W;  // the launch's parameter block (copied at launch)
+    W.n = n;
+    int blocks = 0, smax = 1;
+    for (int j = 0; j < n; ++j) {
+        const gs_track_job& t = jobs[j];
+        const WaveBin& b = bins[j];
+        W.start[j] = blocks;
+        blocks += (int)b.nb;
+        smax = std::max(smax, b.ntiles);
+        W.job[j] = WaveProjJob{t.cam, t.g, t.splats, b.per, b.ntiles, b.hist, (uint2*)b.rects, b.ticket,
+                               wave_bwd_ticket(t), t.loss, t.grad2d};
+    }
+    W.start[n] = blocks;
+    k_wave_project_hist<<<(unsigned)blocks, 256, sizeof(uint32_t) * (size_t)smax, st>>>(cfg, W);
+    return check_launch("k_wave_project_hist");
+}
+
+gs_status wave_project_bwd(const gs_config& cfg, const gs_track_job* jobs, int n, cudaStream_t st) {
+    Wave<WavePbJob> W;
+    W.n = n;
+    int blocks = 0;
+    bool score = false;
+    for (int j = 0; j < n; ++j) score = score || jobs[j].score_terms;
+    for (int j = 0; j < n; ++j) {
+        const gs_track_job& t = jobs[j];
+        W.start[j] = blocks;
+        blocks += (int)((t.g.n + PB_THREADS - 1) / PB_THREADS);
+        W.job[j] = WavePbJob{t.cam, t.g, t.grad2d, t.score_terms, (float2*)t.bwd_workspace, t.pose_grad6,
+                             wave_bwd_ticket(t), t.step};
+    }
+    W.start[n] = blocks;
+    if (score) {  // (gs_track_wave checked that every job has one)
+        k_wave_project_bwd<true><<<(unsigned)blocks, PB_THREADS, 0, st>>>(cfg, W);
+    } else {
+        k_wave_project_bwd<false><<<(unsigned)blocks, PB_THREADS, 0, st>>>(cfg, W);
+    }
+    return check_launch("k_wave_project_bwd");
+}
+
+}  // namespace gs

@@ -1270,6 +1270,88 @@ __global__ void __launch_bounds__(W * 32, W == 8 ? 4 : 2)
                         g.tw * g.th, M);
 }
 
+// ---------------------------------------------------------------------------
+// Multi-session waves: forward compositing with the loss and backward
+// compositing (GS_TRACK) over every job of a wave, one launch per kernel form
+// ---------------------------------------------------------------------------
+struct WaveFwdJob {
+    Grid g;
+    const void* splats;
+    const uint32_t* vals;
+    const uint32_t* ranges;
+    const uint32_t* order;
+    FwdOut O;
+    int B;
+};
+
+template <int KST>
+__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
+    k_wave_render_fwd(const gs_config cfg, const __grid_constant__ Wave<WaveFwdJob> W) {
+    extern __shared__ __align__(16) unsigned char r_smem[];
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveFwdJob& J = W.job[j];
+    const Group G = make_group(J.g, J.order, J.B, (int)blockIdx.x - W.start[j]);
+    if (G.tile < 0) return;
+    fwd_pp<GS_F32, KST>(cfg, J.g, J.splats, J.vals, J.ranges, J.O, G, reinterpret_cast<StagedSplat*>(r_smem));
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 2)
+    k_wave_render_fwd_ep(const gs_config cfg, const __grid_constant__ Wave<WaveFwdJob> W) {
+    __shared__ EpStageN<EpFwdBatch<NW>::N> S;
+    __shared__ int cbuf_all[NW][64];
+    __shared__ uint32_t s_h[64];
+    __shared__ uint8_t perm[64];
+    __shared__ uint32_t bm_all[NW][EpFwdBatch<NW>::N / 32];
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveFwdJob& J = W.job[j];
+    const int blk = (int)blockIdx.x - W.start[j];
+    const int tile = J.order ? (int)__ldg(J.order + blk) : blk;
+    fwd_ep<GS_F32, NW>(cfg, J.g, J.splats, J.vals, J.ranges, J.O, tile, 0, J.g.tw * J.g.th, S, cbuf_all, s_h, perm,
+                       bm_all);
+}
+
+struct WaveBwdJob {
+    Grid g;
+    const void* splats;
+    const uint32_t* vals;
+    const uint32_t* ranges;
+    const uint32_t* order;
+    const float* t_final;
+    const uint32_t* last_idx;
+    const float* d_rgb;
+    const float* d_depth;
+    float* grad2d;
+    const uint32_t* bmask;
+    int B;
+};
+
+template <int KST>
+__global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
+    k_wave_render_bwd(const gs_config cfg, const __grid_constant__ Wave<WaveBwdJob> W) {
+    extern __shared__ __align__(16) unsigned char r_smem[];
+    __shared__ uint32_t s_max_all[R_THREADS / 32];
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveBwdJob& J = W.job[j];
+    const Group G = make_group(J.g, J.order, J.B, (int)blockIdx.x - W.start[j]);
+    if (G.tile < 0) return;
+    bwd_pp<GS_F32, GS_TRACK, KST>(cfg, J.g, J.splats, J.vals, J.ranges, J.t_final, J.last_idx, J.d_rgb, J.d_depth,
+                                  J.grad2d, J.bmask, G, r_smem, s_max_all);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 2)
+    k_wave_render_bwd_ep(const gs_config cfg, const __grid_constant__ Wave<WaveBwdJob> W) {
+    extern __shared__ __align__(16) unsigned char r_smem[];
+    EpBwdSmem<GS_TRACK, NW>& M = *reinterpret_cast<EpBwdSmem<GS_TRACK, NW>*>(r_smem);
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveBwdJob& J = W.job[j];
+    const int blk = (int)blockIdx.x - W.start[j];
+    const int tile = J.order ? (int)__ldg(J.order + blk) : blk;
+    bwd_ep<GS_F32, GS_TRACK, NW>(cfg, J.g, J.splats, J.vals, J.ranges, J.t_final, J.last_idx, J.d_rgb, J.d_depth,
+                                 J.grad2d, J.bmask, tile, 0, J.g.tw * J.g.th, M);
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -1292,7 +1374,7 @@ static int fwd_batch(int gpc) {
 // Raises a kernel's dynamic shared-memory limit once per device and
 // instantiation (not repeated while a graph is being captured).
 static gs_status smem_once(const void* fn, int id, int bytes) {
-    static bool done[64][40] = {};
+    static bool done[64][48] = {};  // ids: fwd 0-5, bwd 6-17, entry-parallel bwd 18-33, waves 40-45
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && done[dev][id]) return GS_OK;
@@ -1504,3 +1586,100 @@ extern "C" gs_status gs_render_bwd(const gs_config* cfg, const gs_camera* cam, c
     }
     return GS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Wave launcher (gs_track_wave): the compositing of every job, grouped by
+// kernel form (0: full tiles, one per CTA; 1: smaller pixel-parallel tiles,
+// several per CTA; 2, 3: entry-parallel tiles of up to 32 or 64 pixels)
+// ---------------------------------------------------------------------------
+namespace gs {
+
+static int render_form(const Grid& g) {
+    if (g.tw * g.th <= 64) return g.tw * g.th <= 32 ? 2 : 3;
+    return R_THREADS / tile_threads(g) == 1 ? 0 : 1;
+}
+
+gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cudaStream_t st) {
+    gs_status s;
+    int present = 0;
+    for (int j = 0; j < n; ++j) present |= 1 << render_form(make_grid(jobs[j].cam));
+    // forward compositing with the fused loss
+    for (int form = 0; form < 4; ++form) {
+        if (!(present & (1 << form))) continue;
+        Wave<WaveFwdJob> W;
+        W.n = 0;
+        int blocks = 0;
+        size_t smem = 0;
+        for (int j = 0; j < n; ++j) {
+            const gs_track_job& t = jobs[j];
+            const Grid g = make_grid(t.cam);
+            if (render_form(g) != form) continue;
+            const int ntiles = g.TX * g.TY;
+            const int gpc = form < 2 ? R_THREADS / tile_threads(g) : 1;
+            const int B = form < 2 ? fwd_batch(gpc) : 0;
+            const FwdOut O = {t.rgb, t.depth, t.t_final, t.last_idx, t.n_blended, t.target_rgb, t.target_depth,
+                              t.d_rgb, t.d_depth, t.loss, t.blend_masks};
+            W.start[W.n] = blocks;
+            W.job[W.n] = WaveFwdJob{g, t.splats, t.vals, t.tile_ranges, t.tile_order, O, B};
+            ++W.n;
+            blocks += (ntiles + gpc - 1) / gpc;
+            if (form < 2) smem = std::max(smem, (size_t)gpc * (B / 32 * 33) * sizeof(StagedSplat));
+        }
+        W.start[W.n] = blocks;
+        if (form == 0) {
+            if ((s = smem_once((const void*)k_wave_render_fwd<1>, 40, R_FWD_SMEM / 32 * 33)) != GS_OK) return s;
+            k_wave_render_fwd<1><<<(unsigned)blocks, R_THREADS, smem, st>>>(cfg, W);
+        } else if (form == 1) {
+            if ((s = smem_once((const void*)k_wave_render_fwd<4>, 41, R_FWD_SMEM / 32 * 33)) != GS_OK) return s;
+            k_wave_render_fwd<4><<<(unsigned)blocks, R_THREADS, smem, st>>>(cfg, W);
+        } else if (form == 2) {
+            k_wave_render_fwd_ep<8><<<(unsigned)blocks, 8 * 32, 0, st>>>(cfg, W);
+        } else {
+            k_wave_render_fwd_ep<16><<<(unsigned)blocks, 16 * 32, 0, st>>>(cfg, W);
+        }
+        if ((s = check_launch("k_wave_render_fwd")) != GS_OK) return s;
+    }
+    // backward compositing, pose-only fields
+    for (int form = 0; form < 4; ++form) {
+        if (!(present & (1 << form))) continue;
+        Wave<WaveBwdJob> W;
+        W.n = 0;
+        int blocks = 0;
+        size_t smem = 0;
+        const int per_entry = (int)(sizeof(StagedSplat) + sizeof(uint32_t) + sizeof(float) * Fields<GS_TRACK>::N);
+        for (int j = 0; j < n; ++j) {
+            const gs_track_job& t = jobs[j];
+            const Grid g = make_grid(t.cam);
+            if (render_form(g) != form) continue;
+            const int ntiles = g.TX * g.TY;
+            const int gpc = form < 2 ? R_THREADS / tile_threads(g) : 1;
+            const int B = form < 2 ? group_batch(gpc, per_entry, R_BWD_SMEM) : 0;
+            W.start[W.n] = blocks;
+            W.job[W.n] = WaveBwdJob{g, t.splats, t.vals, t.tile_ranges, t.tile_order, t.t_final, t.last_idx, t.d_rgb,
+                                    t.d_depth, t.grad2d, t.blend_masks, B};
+            ++W.n;
+            blocks += (ntiles + gpc - 1) / gpc;
+            if (form < 2) smem = std::max(smem, (size_t)gpc * B * per_entry);
+        }
+        W.start[W.n] = blocks;
+        if (form == 0) {
+            if ((s = smem_once((const void*)k_wave_render_bwd<1>, 42, R_BWD_SMEM)) != GS_OK) return s;
+            k_wave_render_bwd<1><<<(unsigned)blocks, R_THREADS, smem, st>>>(cfg, W);
+        } else if (form == 1) {
+            if ((s = smem_once((const void*)k_wave_render_bwd<4>, 43, R_BWD_SMEM)) != GS_OK) return s;
+            k_wave_render_bwd<4><<<(unsigned)blocks, R_THREADS, smem, st>>>(cfg, W);
+        } else if (form == 2) {
+            const int sm = (int)sizeof(EpBwdSmem<GS_TRACK, 8>);
+            if ((s = smem_once((const void*)k_wave_render_bwd_ep<8>, 44, sm)) != GS_OK) return s;
+            k_wave_render_bwd_ep<8><<<(unsigned)blocks, 8 * 32, sm, st>>>(cfg, W);
+        } else {
+            const int sm = (int)sizeof(EpBwdSmem<GS_TRACK, 16>);
+            if ((s = smem_once((const void*)k_wave_render_bwd_ep<16>, 45, sm)) != GS_OK) return s;
+            k_wave_render_bwd_ep<16><<<(unsigned)blocks, 16 * 32, sm, st>>>(cfg, W);
+        }
+        if ((s = check_launch("k_wave_render_bwd")) != GS_OK) return s;
+    }
+    return GS_OK;
+}
+
+}  // namespace gs

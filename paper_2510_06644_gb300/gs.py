@@ -63,6 +63,22 @@ class gs_grads(C.Structure):
                 ("opacity_logit", C.c_void_p), ("rgb", C.c_void_p)]
 
 
+class gs_track_job(C.Structure):
+    """One session's tracking iteration inside a wave (gs_track_wave)."""
+    _fields_ = [("cam", gs_camera), ("g", gs_gaussians), ("splats", C.c_void_p), ("keys_capacity", C.c_int64),
+                ("bin_workspace", C.c_void_p), ("bin_workspace_bytes", C.c_size_t), ("keys", C.c_void_p),
+                ("vals", C.c_void_p), ("n_keys", C.c_void_p), ("tile_ranges", C.c_void_p),
+                ("tile_order", C.c_void_p), ("rgb", C.c_void_p), ("depth", C.c_void_p), ("t_final", C.c_void_p),
+                ("last_idx", C.c_void_p), ("n_blended", C.c_void_p), ("blend_masks", C.c_void_p),
+                ("target_rgb", C.c_void_p), ("target_depth", C.c_void_p), ("d_rgb", C.c_void_p),
+                ("d_depth", C.c_void_p), ("loss", C.c_void_p), ("grad2d", C.c_void_p), ("pose_grad6", C.c_void_p),
+                ("score_terms", C.c_void_p), ("bwd_workspace", C.c_void_p), ("bwd_workspace_bytes", C.c_size_t),
+                ("step", gs_pose_step)]
+
+
+GS_WAVE_MAX = 32
+
+
 _lib = None
 _P = C.c_void_p
 _SIGS = {
@@ -93,6 +109,7 @@ _SIGS = {
     "gs_status_poll": ([_P, C.c_int, _P], C.c_int),
     "gs_probe_red_f32": ([_P, C.c_int64, C.c_int64, C.c_int32, _P], C.c_int),
     "gs_probe_fma_f32": ([_P, C.c_int64, C.c_int32, _P], C.c_int),
+    "gs_track_wave": ([_P, _P, C.c_int32, _P], C.c_int),
     "gs_status_reset": ([_P], C.c_int),
     "gs_last_error": ([], C.c_char_p),
 }
@@ -431,6 +448,19 @@ def gs_project_bwd_step(cfg, cam, g, grad2d, pose, step, grads=None, score=None,
                                      C.byref(gr) if gr is not None else None, _ptr(pose), _ptr(score),
                                      C.byref(step) if step is not None else None, _ptr(ws), C.byref(nb),
                                      _stream(stream)), "gs_project_bwd_step")
+
+
+def gs_track_wave(cfg, jobs, stream=None):
+    """One tracking iteration of every session in `jobs` (a ctypes array of
+    gs_track_job, or a list of them) in launches whose grids span all of
+    them."""
+    if not isinstance(jobs, C.Array):
+        arr = (gs_track_job * len(jobs))()
+        for i, j in enumerate(jobs):
+            arr[i] = j
+        jobs = arr
+    _check(lib().gs_track_wave(C.byref(_cfg(cfg)), C.cast(jobs, C.c_void_p), len(jobs), _stream(stream)),
+           "gs_track_wave")
 
 
 def gs_project_bwd_noalloc(cfg, cam, g, grad2d, grads=None, pose=None, score=None, stream=None):

@@ -156,6 +156,41 @@ class Rasterizer:
                                ws=self._bwd_ws(cam_s, g))
         return self.pose
 
+    def track_job(self, g, cam, target_rgb, target_depth, pose, pose_adam, lr_trans=1e-3, lr_rot=1e-3,
+                  want_score=True):
+        """The descriptor of one track_step of this rasterizer for a wave
+        (gs.gs_track_wave): the same buffers, workspaces and pose step.  The
+        descriptor holds raw device pointers: g, the targets and this
+        rasterizer must outlive every wave that uses it."""
+        if self.rec_dtype != gs.GS_F32:
+            raise ValueError("waves take float32 records")
+        cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam, pose=pose)
+        self.set_grid(cam_s)
+        j = gs.gs_track_job()
+        j.cam = cam_s
+        j.g = gs.gaussians(g)
+        j.splats = gs._ptr(self.splats).value
+        j.keys_capacity = self.capacity
+        pb = self._pb_ws(cam_s, g)
+        j.bin_workspace, j.bin_workspace_bytes = gs._ptr(pb).value, pb.numel()
+        j.keys, j.vals, j.n_keys = gs._ptr(self.keys).value, gs._ptr(self.vals).value, gs._ptr(self.n_keys).value
+        j.tile_ranges, j.tile_order = gs._ptr(self.ranges).value, gs._ptr(self.order).value
+        for k in ("rgb", "depth", "t_final", "last_idx", "n_blended"):
+            setattr(j, k, gs._ptr(self.img[k]).value)
+        bm = self._masks(cam_s)
+        self._bm_used = bm
+        j.blend_masks = gs._ptr(bm).value if bm is not None else None
+        j.target_rgb, j.target_depth = gs._ptr(target_rgb).value, gs._ptr(target_depth).value
+        j.d_rgb, j.d_depth = gs._ptr(self.dimg["d_rgb"]).value, gs._ptr(self.dimg["d_depth"]).value
+        j.loss = gs._ptr(self.dimg["loss"]).value
+        j.grad2d = gs._ptr(self.grad2d).value
+        j.pose_grad6 = gs._ptr(self.pose).value
+        j.score_terms = gs._ptr(self.score).value if want_score else None
+        bw = self._bwd_ws(cam_s, g)
+        j.bwd_workspace, j.bwd_workspace_bytes = gs._ptr(bw).value, bw.numel()
+        j.step = gs.pose_step(pose, pose_adam, lr_trans, lr_rot)
+        return j
+
     def check(self):
         """Synchronises and raises if a device condition was raised (key
         capacity exceeded, a bounded wait that gave up)."""

@@ -155,3 +155,25 @@ def test_fused_projection_binning_checks_arguments_on_the_host(built_lib):
     assert L.gs_project_bin_sort(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), gs.GS_F32, None, 100,
                                  None, ctypes.byref(nb), None, None, None, None, None, None) == gs.GS_OK
     assert nb.value > 0
+
+
+def test_track_wave_rejects_bad_arguments_on_the_host(built_lib):
+    """gs_track_wave checks every job before it enqueues anything: the
+    count of jobs, then each descriptor (the message names the job)."""
+    from paper_2510_06644_gb300 import gs
+    L = gs.lib()
+    cfg = gs.default_config()
+    jobs = (gs.gs_track_job * 2)()
+    assert L.gs_track_wave(ctypes.byref(cfg), None, 1, None) == gs.GS_ERR_INVALID_ARG
+    assert L.gs_track_wave(ctypes.byref(cfg), ctypes.cast(jobs, ctypes.c_void_p), 0, None) == gs.GS_ERR_INVALID_ARG
+    assert L.gs_track_wave(ctypes.byref(cfg), ctypes.cast(jobs, ctypes.c_void_p), gs.GS_WAVE_MAX + 1,
+                           None) == gs.GS_ERR_INVALID_ARG
+    # a camera but no map
+    for j in jobs:
+        j.cam = gs.camera({"R": [[1, 0, 0], [0, 1, 0], [0, 0, 1]], "t": [0, 0, 0], "fx": 80.0, "fy": 80.0,
+                           "cx": 48.0, "cy": 36.0, "W": 96, "H": 72})
+    rc = L.gs_track_wave(ctypes.byref(cfg), ctypes.cast(jobs, ctypes.c_void_p), 2, None)
+    assert rc == gs.GS_ERR_INVALID_ARG and b"job 0" in L.gs_last_error()
+    jobs[0].cam.width = 0
+    rc = L.gs_track_wave(ctypes.byref(cfg), ctypes.cast(jobs, ctypes.c_void_p), 2, None)
+    assert rc == gs.GS_ERR_INVALID_ARG and b"job 0: bad camera" in L.gs_last_error()
