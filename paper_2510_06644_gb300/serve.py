@@ -17,6 +17,11 @@ footprint), each admitted session gets its own stream, and whenever a
 session has an arrived frame and no frame in flight the frame program is
 launched on its stream, so frames of different sessions overlap on the GPU;
 finished sessions release their slot and memory, which admits the next.
+Server(mode="wave") batches inside the kernels: every tracking iteration of
+every session with a frame in progress runs in one wave (gs_track_wave), a
+set of launches whose grids span all those sessions; a session joins the
+wave when its next frame has arrived and leaves it after the frame's 40th
+iteration (its keyframe mapping iteration follows on the same stream).
 Server(mode="plain") is the per-session sequential loop: one stream, frames
 in arrival order, each frame run to completion before the next.
 
@@ -96,6 +101,7 @@ class Session:
         self.programs = {}  # (sx, sy, keyframe) -> CUDA graph
         self.frames_done = 0
         self.poses = []
+        self.pose_log = torch.empty((spec.n_frames, 12), device=self.device)  # final pose of each frame
 
     # -- footprint ---------------------------------------------------------
     @staticmethod
@@ -180,6 +186,50 @@ class Session:
             ev.record(stream)
         return ev
 
+    # -- waves -------------------------------------------------------------
+    def wave_job(self, sx, sy):
+        """The gs_track_job of one tracking iteration at stride (sx, sy)
+        (cached: it points at this session's device buffers)."""
+        if not hasattr(self, "_jobs"):
+            self._jobs = {}
+        key = (sx, sy)
+        if key not in self._jobs:
+            r, (trgb, tdep) = self._rast(sx, sy)
+            cam = gs.camera(dict(self.cams[0], sx=sx, sy=sy), pose=self.pose)
+            self._jobs[key] = r.track_job(self.g, cam, trgb, tdep, self.pose, self.pose_adam, self.lr_pose,
+                                          self.lr_pose)
+        return self._jobs[key]
+
+    def start_frame(self, fr, stream):
+        """Gathers frame fr's observation at its stride (Sec. 4.2) on
+        `stream`; returns (keyframe, sx, sy)."""
+        kf, sx, sy = stride_of(fr, self.spec.kf_every)
+        trgb_full, tdep_full = self.targets[fr]
+        _, (trgb, tdep) = self._rast(sx, sy)
+        k = (fr // self.spec.kf_every) * self.spec.kf_every
+        gs.gs_downsample(fr, k, kf, 2, trgb_full, out=trgb, stream=stream)
+        gs.gs_downsample(fr, k, kf, 2, tdep_full, out=tdep, stream=stream)
+        return kf, sx, sy
+
+    def finish_frame(self, fr, keyframe, stream):
+        """The keyframe's mapping iteration (if any) on `stream`, then a copy
+        of the frame's final pose (later waves may move the pose before the
+        host looks); returns the frame's completion event."""
+        with torch.cuda.stream(stream):
+            if keyframe:
+                r, (trgb, tdep) = self._rast(1, 1)
+                cam = gs.camera(dict(self.cams[0], sx=1, sy=1), pose=self.pose)
+                r.forward(self.g, cam)
+                r.loss_grad(cam, trgb, tdep)
+                r.backward(self.g, cam, r.dimg["d_rgb"], r.dimg["d_depth"], gs.GS_MAP, grads=self.grads,
+                           want_pose=False, want_score=True)
+                gs.gs_adam([self.g[k] for k in PARAMS], [self.grads[k] for k in PARAMS],
+                           [self.m[k] for k in PARAMS], [self.v[k] for k in PARAMS], self.map_state, lr=self.lr_map)
+            self.pose_log[fr].copy_(self.pose)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return ev
+
     # -- state snapshots (checkpoint / resume) ------------------------------
     def snapshot(self):
         st = {"pose": self.pose.clone(), "pose_adam": self.pose_adam.clone(), "map_state": self.map_state.clone()}
@@ -248,17 +298,21 @@ class Admission:
 
 
 class Server:
-    def __init__(self, sessions, arrivals, mode="batched", slots=16, budget_bytes=150 << 30, device="cuda"):
+    def __init__(self, sessions, arrivals, mode="batched", slots=16, budget_bytes=150 << 30, device="cuda",
+                 groups=4):
         """sessions: prepared Session objects; arrivals[sid] = frame arrival
-        times (seconds from the start)."""
+        times (seconds from the start); groups: wave groups (mode "wave")."""
         self.sessions = {s.spec.sid: s for s in sessions}
         self.arrivals = arrivals
         self.mode = mode
-        self.adm = Admission(budget_bytes, slots if mode == "batched" else 1)
+        self.groups = groups
+        self.adm = Admission(budget_bytes, slots if mode in ("batched", "wave") else 1)
         self.device = torch.device(device)
         self.latency = []   # (sid, frame, seconds)
 
     def run(self):
+        if self.mode == "wave":
+            return self.run_waves()
         order = sorted(self.sessions, key=lambda sid: self.arrivals[sid][0])
         waiting = list(order)
         done_frames = {sid: 0 for sid in self.sessions}
@@ -311,6 +365,87 @@ class Server:
                     progressed = True
                     if done_frames[sid] == self.sessions[sid].spec.n_frames:
                         self.adm.release(sid)
+            if not progressed:
+                time.sleep(20e-6)
+        self.makespan = time.perf_counter() - t0
+        return self.stats()
+
+    def run_waves(self, depth=3):
+        """Continuous batching inside the kernels: each wave is one tracking
+        iteration of every session of a group with a frame in progress (one
+        gs_track_wave call); sessions join at frame boundaries as their frames
+        arrive and slots and memory free up.  Sessions are dealt to
+        `self.groups` groups (the lightest group by map size at admission),
+        each with its own stream, so one group's stage boundaries overlap
+        with another's work.  At most `depth` waves per group are queued
+        ahead of the GPU, so a frame that arrives joins within a few waves."""
+        order = sorted(self.sessions, key=lambda sid: self.arrivals[sid][0])
+        waiting = list(order)
+        done_frames = {sid: 0 for sid in self.sessions}
+        started = {sid: 0 for sid in self.sessions}
+        progress = {}      # sid -> [frame, iteration, keyframe, sx, sy]
+        pending = []       # (sid, frame, completion event)
+        ng = max(1, int(self.groups))
+        queued = [[] for _ in range(ng)]   # events of each group's waves in flight
+        streams = [torch.cuda.Stream(device=self.device) for _ in range(ng)]
+        group = {}         # sid -> group
+        load = [0] * ng
+        weight = {sid: s.spec.n for sid, s in self.sessions.items()}
+        t0 = time.perf_counter()
+        total = sum(s.spec.n_frames for s in self.sessions.values())
+        completed = 0
+        while completed < total:
+            now = time.perf_counter() - t0
+            while waiting:
+                sid = waiting[0]
+                if self.arrivals[sid][0] > now:
+                    break
+                if not self.adm.try_admit(sid, Session.footprint_bytes(self.sessions[sid].spec)):
+                    break
+                waiting.pop(0)
+                gi = min(range(ng), key=lambda q: load[q])
+                group[sid] = gi
+                load[gi] += weight[sid]
+            # sessions whose next frame has arrived join their group's wave
+            for sid in self.adm.active:
+                s = self.sessions[sid]
+                fr = started[sid]
+                if sid not in progress and fr < s.spec.n_frames and self.arrivals[sid][fr] <= now:
+                    kf, sx, sy = s.start_frame(fr, streams[group[sid]])
+                    progress[sid] = [fr, 0, kf, sx, sy]
+                    started[sid] += 1
+            # completions
+            progressed = False
+            for item in list(pending):
+                sid, fr, ev = item
+                if ev.query():
+                    self.latency.append((sid, fr, time.perf_counter() - t0 - self.arrivals[sid][fr]))
+                    self.sessions[sid].poses.append(self.sessions[sid].pose_log[fr].cpu().numpy().copy())
+                    pending.remove(item)
+                    done_frames[sid] += 1
+                    completed += 1
+                    progressed = True
+                    if done_frames[sid] == self.sessions[sid].spec.n_frames:
+                        self.adm.release(sid)
+                        load[group.pop(sid)] -= weight[sid]
+            for gi in range(ng):
+                queued[gi] = [e for e in queued[gi] if not e.query()]
+                sids = sorted((q for q in progress if group[q] == gi), key=lambda q: -weight[q])
+                if not sids or len(queued[gi]) >= depth:
+                    continue
+                st_ = streams[gi]
+                jobs = [self.sessions[q].wave_job(progress[q][3], progress[q][4]) for q in sids]
+                gs.gs_track_wave(self.sessions[sids[0]].cfg, jobs, stream=st_)
+                ev = torch.cuda.Event()
+                ev.record(st_)
+                queued[gi].append(ev)
+                for q in sids:
+                    st = progress[q]
+                    st[1] += 1
+                    if st[1] == self.sessions[q].spec.iters:
+                        pending.append((q, st[0], self.sessions[q].finish_frame(st[0], st[2], st_)))
+                        del progress[q]
+                progressed = True
             if not progressed:
                 time.sleep(20e-6)
         self.makespan = time.perf_counter() - t0

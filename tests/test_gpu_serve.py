@@ -1,7 +1,9 @@
-"""Serving form on the GPU: continuous batching of several SLAM sessions.
-Each session's result is the same alone and in the mix (within the
-nondeterminism of float atomics in the backward), every frame is served, and
-a snapshot restores a session's state for an identical continuation."""
+"""Serving form on the GPU: continuous batching of several SLAM sessions,
+by streams (mode "batched") and inside the kernels (mode "wave": launches
+whose grids span every session).  Each session's result is the same alone
+and in the mix (within the nondeterminism of float atomics in the
+backward), every frame is served, and a snapshot restores a session's state
+for an identical continuation."""
 import numpy as np
 import pytest
 import torch
@@ -35,13 +37,14 @@ def build_sessions(SV, specs, use_graphs=True):
     return out
 
 
-def test_result_same_alone_and_in_the_mix(SV):
+@pytest.mark.parametrize("mode", ["batched", "wave"])
+def test_result_same_alone_and_in_the_mix(SV, mode):
     specs = small_specs(SV)
     arr = SV.poisson_arrivals(specs, seed=3)
     alone = build_sessions(SV, specs[:1])
-    SV.Server(alone, {0: arr[0]}, mode="batched", slots=4).run()
+    SV.Server(alone, {0: arr[0]}, mode="plain").run()
     mix = build_sessions(SV, specs)
-    st = SV.Server(mix, arr, mode="batched", slots=4).run()
+    st = SV.Server(mix, arr, mode=mode, slots=4).run()
     assert st["frames"] == sum(s.n_frames for s in specs)
     a = np.array(alone[0].poses)
     b = np.array(mix[0].poses)
@@ -94,3 +97,26 @@ def test_snapshot_restore_continues_identically(SV):
         s.launch_frame(fr, stream).synchronize()
     second = s.pose.cpu().numpy().copy()
     assert np.abs(first - second).max() <= 1e-5
+
+
+def test_waves_serve_every_frame_with_sessions_joining_and_leaving(SV):
+    """Sessions of different sizes, resolutions and frame counts arrive at
+    different times: every frame is served once, in order per session, and
+    the slots and memory are all released at the end."""
+    specs = SV.make_session_specs(4, seed=910, n_frames=5, n_range=(5_000, 40_000),
+                                  resolutions=((160, 120), (320, 240), (200, 120)), iters=6, fps=60.0)
+    specs[1].n_frames = 3
+    arr = SV.poisson_arrivals(specs, seed=6)
+    arr[2] = [t + 0.05 for t in arr[2]]   # joins late
+    sess = build_sessions(SV, specs, use_graphs=False)
+    srv = SV.Server(sess, arr, mode="wave", slots=3)
+    st = srv.run()
+    assert st["frames"] == sum(s.n_frames for s in specs)
+    per = {}
+    for sid, fr, lat in srv.latency:
+        per.setdefault(sid, []).append(fr)
+        assert lat >= 0
+    assert all(v == list(range(specs[sid].n_frames)) for sid, v in per.items())
+    assert srv.adm.used == 0 and not srv.adm.active
+    for s in sess:
+        assert np.all(np.isfinite(np.array(s.poses)))
