@@ -270,6 +270,7 @@ def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pos
     the first (Sec. 4.1 / Obs. 6).  N4: forward and backward time with the
     lowest-score 10/30/50 % of the Gaussians masked (Eq. 7 scores of the
     current backward) and at the Sec. 4.2 strides."""
+    import numpy as np
     import torch
     out = {}
     K = 5
@@ -282,6 +283,46 @@ def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pos
     adam.zero_()
     ms = _graph_ms(interval, 20, flush) / K
     out["list_reuse_k5"] = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms}
+
+    # N1 as a policy: 100 tracking iterations from the 2 cm / 1 deg start,
+    # fresh binning every iteration against the re-binning policy (bin when an
+    # interval ends; intervals from the change ratio).  Eager launches for
+    # both (the policy reads one ratio per interval on the host); pose error
+    # against the true (identity) pose after the run.
+    from paper_2510_06644_gb300.pipeline import ListReuse
+
+    def pose_err(p):
+        R = p[:9].reshape(3, 3)
+        return {"t_m": float(np.linalg.norm(p[9:])),
+                "r_deg": float(np.degrees(np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1))))}
+
+    iters = 100
+    res = {"iters": iters, "start": pose_err(pose0.cpu().numpy())}
+    for name in ("fresh", "policy"):
+        r = Rasterizer(rast.n, start_cam, capacity=rast.capacity)
+        pose.copy_(pose0)
+        adam.zero_()
+        lr = ListReuse(r, gd) if name == "policy" else None
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(iters):
+            if lr is not None:
+                lr.step(cam_s, trgb, tdep, pose, adam, lr_t, lr_r)
+            else:
+                r.track_step(gd, cam_s, trgb, tdep, pose, adam, lr_t, lr_r)
+        b.record()
+        torch.cuda.synchronize()
+        r.check()
+        ms = a.elapsed_time(b) / iters
+        res[name] = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "pose_error": pose_err(pose.cpu().numpy())}
+        if lr is not None:
+            res[name]["binnings"] = len(lr.intervals) + (1 if lr.i > 0 else 0)
+            res[name]["intervals"] = [[k, round(x, 4)] for k, x in lr.intervals]
+    res["speedup"] = res["fresh"]["ms_per_iter"] / res["policy"]["ms_per_iter"]
+    out["rebin_policy"] = res
+    pose.copy_(pose0)
+    adam.zero_()
 
     def fwd(r, g, cam):
         return lambda: r.forward(g, cam)

@@ -385,6 +385,14 @@ gs_status gs_prune(const gs_config* cfg, const float* score_terms, int64_t n,
                    int64_t* n_kept_out, void* workspace, size_t* workspace_bytes,
                    gs_stream stream);
 
+/* Length of the next pruning interval (Sec. 4.1): after an interval of K
+ * iterations whose tile-Gaussian intersections changed by change_ratio,
+ * max(1, floor(K / 2)) if change_ratio > cfg->change_thr, else
+ * min(2 K, cfg->k_max) (the current K playing the paper's K0).  Host, pure;
+ * the rule gs_prune applies at the removal iteration.  Returns 1 for a NULL
+ * cfg or K < 1. */
+int32_t gs_next_interval(const gs_config* cfg, int32_t K, float change_ratio);
+
 /* Change ratio of tile-Gaussian intersections between two binnings of the
  * same n Gaussians on the same tile grid (Sec. 4.1): |A xor B| / max(1, |A|)
  * over the sets of (tile, Gaussian) pairs.  Each Gaussian's tiles form the

@@ -256,6 +256,14 @@ static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 using namespace gs;
 
+extern "C" int32_t gs_next_interval(const gs_config* cfg, int32_t K, float change_ratio) {
+    if (!cfg || K < 1) return 1;
+    int32_t nk = change_ratio > cfg->change_thr ? K / 2 : 2 * K;
+    if (nk < 1) nk = 1;
+    if (nk > cfg->k_max) nk = cfg->k_max;
+    return nk;
+}
+
 extern "C" gs_status gs_prune(const gs_config* cfg, const float* score_terms, int64_t n, uint8_t* mask_inout,
                               int iter_in_interval, int* k_inout, float change_ratio, int64_t max_select,
                               uint32_t* compact_map_out, int64_t* n_kept_out, void* workspace,
@@ -306,11 +314,7 @@ extern "C" gs_status gs_prune(const gs_config* cfg, const float* score_terms, in
             k_keep_write<<<(unsigned)nchunk, PR_THREADS, 0, st>>>(mask_inout, n, part, compact_map_out);
             if ((s = check_launch("k_keep_write")) != GS_OK) return s;
         }
-        const int K = *k_inout;
-        int nk = change_ratio > cfg->change_thr ? K / 2 : 2 * K;
-        if (nk < 1) nk = 1;
-        if (nk > cfg->k_max) nk = cfg->k_max;
-        *k_inout = nk;
+        *k_inout = gs_next_interval(cfg, *k_inout, change_ratio);
         return GS_OK;
     }
     return GS_OK;

@@ -110,6 +110,7 @@ _SIGS = {
     "gs_probe_red_f32": ([_P, C.c_int64, C.c_int64, C.c_int32, _P], C.c_int),
     "gs_probe_fma_f32": ([_P, C.c_int64, C.c_int32, _P], C.c_int),
     "gs_track_wave": ([_P, _P, C.c_int32, _P], C.c_int),
+    "gs_next_interval": ([_P, C.c_int32, C.c_float], C.c_int32),
     "gs_status_reset": ([_P], C.c_int),
     "gs_last_error": ([], C.c_char_p),
 }
@@ -489,6 +490,11 @@ def gs_prune(cfg, score, mask, iter_in_interval, K, change_ratio=0.0, max_select
                           float(change_ratio), max_select, _ptr(compact_map), _ptr(n_kept), _ptr(ws),
                           C.byref(nb), _stream(stream)), "gs_prune")
     return k.value
+
+
+def gs_next_interval(cfg, K, change_ratio):
+    """Next pruning interval after K iterations with the given change ratio."""
+    return int(lib().gs_next_interval(C.byref(_cfg(cfg)), int(K), float(change_ratio)))
 
 
 def gs_change_ratio(cam, splats_a, splats_b, n, rec_dtype=GS_F32, out=None, stream=None, cfg=None):

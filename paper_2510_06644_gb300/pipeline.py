@@ -198,3 +198,45 @@ class Rasterizer:
         if code != gs.GS_OK:
             raise gs.GsError(code, f"device status {code} (n_keys={int(self.n_keys.item())}, "
                                    f"capacity={self.capacity})")
+
+
+class ListReuse:
+    """Tracking with the tile lists reused across a pruning interval (Sec.
+    4.1, Obs. 6: the tile-Gaussian intersections barely change from one
+    iteration to the next).  The first iteration of an interval bins and
+    sorts; the other K - 1 re-project the Gaussians with the current pose and
+    composite them through the lists of that binning.  When the interval
+    ends, the change ratio of the intersections between the records the
+    lists were built from and the records at the current pose decides the
+    next interval, gs_next_interval: halved above cfg.change_thr, doubled
+    (up to cfg.k_max) below it, starting from cfg.k0.  One host read of the
+    ratio per interval."""
+
+    def __init__(self, rast, g):
+        self.r = rast
+        self.g = g
+        self.K = int(rast.cfg.k0)
+        self.i = 0
+        self.binned = torch.empty_like(rast.splats)  # records the current lists were built from
+        self.now = torch.empty_like(rast.splats)
+        self.ratio = torch.zeros(1, dtype=torch.float32, device=rast.device)
+        self.intervals = []  # (K, change ratio) of every completed interval
+
+    def step(self, cam, target_rgb, target_depth, pose, pose_adam, lr_trans=1e-3, lr_rot=1e-3):
+        """One tracking iteration (Rasterizer.track_step); returns whether it
+        re-binned."""
+        rebin = self.i == 0
+        self.r.track_step(self.g, cam, target_rgb, target_depth, pose, pose_adam, lr_trans, lr_rot, rebin=rebin)
+        if rebin:
+            self.binned.copy_(self.r.splats)
+        self.i += 1
+        if self.i == self.K:
+            cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam, pose=pose)
+            gs.gs_project(self.r.cfg, cam_s, self.g, self.r.rec_dtype, self.now)
+            gs.gs_change_ratio(cam_s, self.binned, self.now, self.r.n, self.r.rec_dtype, out=self.ratio,
+                               cfg=self.r.cfg)
+            r = float(self.ratio.item())
+            self.intervals.append((self.K, r))
+            self.K = gs.gs_next_interval(self.r.cfg, self.K, r)
+            self.i = 0
+        return rebin

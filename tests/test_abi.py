@@ -177,3 +177,20 @@ def test_track_wave_rejects_bad_arguments_on_the_host(built_lib):
     jobs[0].cam.width = 0
     rc = L.gs_track_wave(ctypes.byref(cfg), ctypes.cast(jobs, ctypes.c_void_p), 2, None)
     assert rc == gs.GS_ERR_INVALID_ARG and b"job 0: bad camera" in L.gs_last_error()
+
+
+def test_next_interval_follows_the_oracle_rule(built_lib):
+    """gs_next_interval (the rule gs_prune applies when an interval ends)
+    against the oracle's statement of Sec. 4.1 on scripted change ratios:
+    halved above the threshold, doubled below it, capped, never below 1."""
+    from oracle import oracle as O
+    O.build()
+    from paper_2510_06644_gb300 import gs
+    cfg = gs.default_config()
+    K = int(cfg.k0)
+    for r in (0.0, 0.01, 0.2, 0.05, 0.051, 0.3, 0.3, 0.3, 0.3, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0):
+        got = gs.gs_next_interval(cfg, K, r)
+        assert got == O.next_interval(K, r, K0=int(cfg.k0), thr=float(cfg.change_thr), k_max=int(cfg.k_max)), (K, r)
+        K = got
+    assert K == 32   # ... 64 at the cap, then one halving
+    assert gs.gs_next_interval(cfg, 0, 0.0) == 1

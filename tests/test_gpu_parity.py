@@ -632,3 +632,52 @@ def test_reused_lists_match_oracle_with_the_same_stale_lists(G, O):
     g2 = np_of(r.grad2d)
     for name, cols in GROUPS.items():
         assert rel_l2(g2[:, cols], ref[:, cols]) <= GRAD_TOL, name
+
+
+def test_list_reuse_policy_rebins_when_intervals_end(G):
+    """The re-binning policy (Sec. 4.1 / Obs. 6): bins on the first
+    iteration of each interval only, the intervals follow gs_next_interval
+    of the change ratios measured at their ends, and the ratio is the change
+    of tile-Gaussian intersections between the binned and the current
+    records.  Tracking with reused lists converges like tracking with fresh
+    lists (same target, same start)."""
+    from paper_2510_06644_gb300.pipeline import ListReuse, Rasterizer
+    g = S.surface_scene(40000, seed=94)
+    true_cam = S.camera(320, 240, 260.0)
+    start = S.perturbed_pose(true_cam, seed=95, trans=0.02, rot_deg=1.0)
+    gd = dev(g)
+    r0 = Rasterizer(40000, start)
+    img = r0.forward(gd, true_cam)
+    trgb, tdep = img["rgb"].clone(), img["depth"].clone()
+    iters = 60
+    finals = {}
+    for policy in (False, True):
+        r = Rasterizer(40000, start)
+        pose = G.pose_tensor(start)
+        adam = torch.zeros(13, device="cuda")
+        cs = G.camera(start, pose=pose)
+        if policy:
+            lr = ListReuse(r, gd)
+            flags = [lr.step(cs, trgb, tdep, pose, adam) for _ in range(iters)]
+        else:
+            for _ in range(iters):
+                r.track_step(gd, cs, trgb, tdep, pose, adam)
+        r.check()
+        finals[policy] = pose.cpu().numpy().copy()
+    starts = [i for i, f in enumerate(flags) if f]
+    Ks = [k for k, _ in lr.intervals]
+    assert starts[:len(Ks)] == list(np.cumsum([0] + Ks[:-1]))
+    assert len(starts) == len(Ks) + (1 if sum(Ks) < iters else 0)
+    for (k, ratio), k_next in zip(lr.intervals, Ks[1:]):
+        assert 0.0 <= ratio <= 2.0
+        assert k_next == G.gs_next_interval(None, k, ratio)
+    assert len(starts) < iters // 2          # most iterations reuse the lists
+    # both move toward the true (identity) pose from 2 cm / 1 deg away, to
+    # about the same place
+    def err(p):
+        R = p[:9].reshape(3, 3)
+        ang = float(np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1)))
+        return np.linalg.norm(p[9:]) + ang   # metres + radians (1 deg ~ 1.7 cm)
+    e0 = err(G.pose_tensor(start).cpu().numpy())
+    assert err(finals[False]) < e0 and err(finals[True]) < e0
+    assert abs(err(finals[True]) - err(finals[False])) < 0.5 * e0
