@@ -296,4 +296,68 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Warp sum of NF values, scattered over the lanes: at each butterfly level
+// (lane offsets 16, 8, ..., 1) the C values a lane still carries are paired,
+// the lower lanes keeping the first C/2 and the upper lanes the second C/2
+// (a lane sends the half it gives up and combines it with what its partner
+// sends), and an odd one out is combined whole; once one value is left, the
+// remaining levels combine it with the partner's.  NF = 6 takes 8 exchanges,
+// NF = 10 takes 12, NF = 12 takes 13 (instead of 5 per value).  Value f ends
+// up summed over all 32 lanes on the lanes whose merge_owner<NF> is f.
+// Op::swap(x, off) exchanges x with the lane `off` away; Op::join(mine,
+// theirs, up) combines the value a lane keeps with the one its partner sent
+// (up: this lane is the upper partner), in an operand order that makes both
+// partners of a level compute the same bits.
+struct MergeFloat {
+    static __device__ __forceinline__ float swap(float x, int off) { return __shfl_xor_sync(0xffffffffu, x, off); }
+    static __device__ __forceinline__ float join(float mine, float theirs, bool) { return mine + theirs; }
+};
+struct MergeIds {  // the pairing alone, on value numbers
+    static __device__ __forceinline__ int swap(int x, int) { return x; }
+    static __device__ __forceinline__ int join(int mine, int, bool) { return mine; }
+};
+
+template <int C, int OFF>
+struct MergeLevel {
+    template <typename T, int NF, typename Op>
+    static __device__ __forceinline__ void run(T (&v)[NF], int lane) {
+        if constexpr (OFF > 0) {
+            const bool up = (lane & OFF) != 0;
+            if constexpr (C > 1) {
+                constexpr int H = C / 2;
+#pragma unroll
+                for (int i = 0; i < H; ++i) {
+                    const T send = up ? v[i] : v[i + H];
+                    const T keep = up ? v[i + H] : v[i];
+                    v[i] = Op::join(keep, Op::swap(send, OFF), up);
+                }
+                if constexpr ((C & 1) != 0) v[H] = Op::join(v[C - 1], Op::swap(v[C - 1], OFF), up);
+                MergeLevel<H + (C & 1), OFF / 2>::template run<T, NF, Op>(v, lane);
+            } else {
+                v[0] = Op::join(v[0], Op::swap(v[0], OFF), up);
+                MergeLevel<1, OFF / 2>::template run<T, NF, Op>(v, lane);
+            }
+        }
+    }
+};
+
+template <int NF, typename T = float, typename Op = MergeFloat>
+__device__ __forceinline__ T warp_merge(T (&v)[NF]) {
+    MergeLevel<NF, 16>::template run<T, NF, Op>(v, threadIdx.x & 31);
+    return v[0];
+}
+
+// The value this lane holds after warp_merge<NF>, or -1: the same pairing on
+// value numbers; of the lanes left holding the same value, the lowest owns it.
+template <int NF>
+__device__ __forceinline__ int merge_owner() {
+    const int lane = threadIdx.x & 31;
+    int id[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) id[i] = i;
+    MergeLevel<NF, 16>::template run<int, NF, MergeIds>(id, lane);
+    const unsigned same = __match_any_sync(0xffffffffu, id[0]);
+    return lane == __ffs(same) - 1 ? id[0] : -1;
+}
+
 }  // namespace gs

@@ -203,11 +203,15 @@ __global__ void __launch_bounds__(256) k_project_hist(gs_camera cam, gs_config c
 
 #define PB_THREADS 256
 
-// Pose-gradient sums carry a float32 pair (hi, lo) with hi + lo the value
-// (about 48 significant bits): additions are an error-free two-sum of the
-// high parts (Knuth) plus the low parts, renormalised with a fast two-sum
-// (Dekker).  All in float32 (GB300's float64 rate is 1/64 of it); fixed
-// operation order, so the reduction is deterministic.
+// The pose gradient is a sum over every Gaussian of terms of both signs
+// (the Merging Tree of Sec. 5.1 reduces it in hardware).  Inside a block the
+// sums carry a float32 pair (hi, lo) with hi + lo the value (about 48
+// significant bits): additions are an error-free two-sum of the high parts
+// (Knuth) plus the low parts, renormalised with a fast two-sum (Dekker), in
+// float32 because GB300's float64 rate is a small fraction of it; the last
+// block sums the blocks' pairs the same way and merges the 32 lane sums in
+// compensated float64 (Neumaier).
+// Fixed operation order throughout, so the reduction is deterministic.
 struct DF {
     float hi, lo;
 };
@@ -220,6 +224,16 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     const float hi = __fadd_rn(s, t);
     return DF{hi, __fsub_rn(t, __fsub_rn(hi, s))};
 }
+
+// Pairs exchanged and added in warp_merge.
+struct MergeDF {
+    static __device__ __forceinline__ DF swap(DF x, int off) {
+        return DF{__shfl_xor_sync(0xffffffffu, x.hi, off), __shfl_xor_sync(0xffffffffu, x.lo, off)};
+    }
+    static __device__ __forceinline__ DF join(DF mine, DF theirs, bool up) {
+        return up ? df_add(theirs, mine) : df_add(mine, theirs);  // the lower lane's value first
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Pose step: Adam on xi, then T <- exp(xi^) T
@@ -278,10 +292,34 @@ __global__ void k_pose_update(float* __restrict__ pose, const double* __restrict
     pose_adam_exp(pose, grad, adam, lr_t, lr_r, b1, b2, eps);
 }
 
+// Compensated float64 sum (Neumaier): s + c is the running value, c the
+// accumulated rounding errors of the additions into s.
+struct CD {
+    double s, c;
+};
+
+__device__ __forceinline__ CD cd_add(CD a, double x) {
+    const double t = a.s + x;
+    const double e = fabs(a.s) >= fabs(x) ? (a.s - t) + x : (x - t) + a.s;
+    return CD{t, a.c + e};
+}
+
+// Two compensated sums combined: the error of adding the two main parts
+// (an error-free two-sum) joins both compensation terms.
+__device__ __forceinline__ CD cd_merge(CD a, CD b) {
+    const double t = a.s + b.s;
+    const double bp = t - a.s;
+    const double e = (a.s - (t - bp)) + (b.s - bp);
+    return CD{t, (a.c + b.c) + e};
+}
+
 // Final combination of the per-block pose partials (float32 pairs) by the
 // last block to finish (no spin: the block that takes the last ticket sees
-// every other block's partial, published before its ticket).  Warp w < 6
-// sums component w: lane-strided, then a fixed butterfly.
+// every other block's partial, published before its ticket): warp w < 6 sums
+// component w, each lane its strided share of the blocks as a float32 pair
+// (float64 would make this block the kernel's tail: GB300 runs float64 at a
+// small fraction of the float32 rate), then the 32 lane sums meet in a fixed
+// butterfly of compensated float64 merges.
 __device__ void pose_final_last_block(const float2* __restrict__ part, int nblk, double* __restrict__ out,
                                       unsigned int* __restrict__ ticket, const gs_pose_step& step) {
     __shared__ bool s_last;
@@ -292,17 +330,18 @@ __device__ void pose_final_last_block(const float2* __restrict__ part, int nblk,
     __threadfence();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (w < 6) {
-        DF s{0.f, 0.f};
+        DF d{0.f, 0.f};
         for (int b = lane; b < nblk; b += 32) {
             const float2 v = __ldcg(part + (size_t)b * 6 + w);
-            s = df_add(s, DF{v.x, v.y});
+            d = df_add(d, DF{v.x, v.y});
         }
+        CD s = cd_add(CD{(double)d.hi, 0.0}, (double)d.lo);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const DF t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
-            s = (lane & o) ? df_add(t, s) : df_add(s, t);  // the same operand order on both partners
+            const CD t{__shfl_xor_sync(0xffffffffu, s.s, o), __shfl_xor_sync(0xffffffffu, s.c, o)};
+            s = (lane & o) ? cd_merge(t, s) : cd_merge(s, t);  // the same operand order on both partners
         }
-        if (lane == 0) out[w] = (double)s.hi + (double)s.lo;
+        if (lane == 0) out[w] = s.s + s.c;
     }
     if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
     if (step.pose) {  // the fused pose step (every block has read the pose by now)
@@ -465,18 +504,23 @@ __device__ __forceinline__ void project_bwd_body(gs_camera cam, const gs_config&
         }
     }
     if (WANT_POSE) {
-        // warp sums in float32, then the 8 warp sums of the block as a pair
-        __shared__ float ws[PB_THREADS / 32][6];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        // warp sums as float32 pairs (error-free two-sums, a reduce-scatter
+        // of the six components), then the block's 8 warp pairs in order
+        __shared__ float2 ws[PB_THREADS / 32][6];
+        const int wid = threadIdx.x >> 5;
+        DF v[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            float v = warp_sum(pose[i]);
-            if (lane == 0) ws[wid][i] = v;
-        }
+        for (int i = 0; i < 6; ++i) v[i] = DF{pose[i], 0.f};
+        const DF tot = warp_merge<6, DF, MergeDF>(v);  // 8 pair exchanges for the six components
+        const int owner = merge_owner<6>();
+        if (owner >= 0) ws[wid][owner] = make_float2(tot.hi, tot.lo);
         __syncthreads();
         if (threadIdx.x < 6) {
             DF s{0.f, 0.f};
-            for (int w = 0; w < PB_THREADS / 32; ++w) s = df_add(s, DF{ws[w][threadIdx.x], 0.f});
+            for (int w = 0; w < PB_THREADS / 32; ++w) {
+                const float2 v = ws[w][threadIdx.x];
+                s = df_add(s, DF{v.x, v.y});
+            }
             pose_part[(size_t)blk * 6 + threadIdx.x] = make_float2(s.hi, s.lo);
         }
         pose_final_last_block(pose_part, nblk, pose_out, ticket, step);

@@ -525,61 +525,6 @@ __device__ __forceinline__ int field_col(int f) {
 }
 __device__ __forceinline__ float field_scale(int f) { return f < 2 ? -2.f : (f == 3 ? 2.f : 1.f); }
 
-// Warp sum of NF fields, scattered over the lanes: at each butterfly level
-// (lane offsets 16, 8, ..., 1) the C values a lane still carries are paired,
-// the lower lanes keeping the first C/2 and the upper lanes the second C/2
-// (a lane sends the half it gives up and adds what its partner sends), and
-// an odd one out is summed whole; once one value is left, the remaining
-// levels add it up.  NF = 6 takes 8 shuffles, NF = 10 takes 12 (instead of
-// 5 per field).  The fields end up summed over all 32 lanes, field f on the
-// lanes whose merge_ids<NF> is f.
-template <int C, int OFF>
-struct MergeLevel {
-    template <typename T, int NF, bool SHFL>
-    static __device__ __forceinline__ void run(T (&v)[NF], int lane) {
-        if constexpr (OFF > 0) {
-            if constexpr (C > 1) {
-                constexpr int H = C / 2;
-                const bool up = (lane & OFF) != 0;
-#pragma unroll
-                for (int i = 0; i < H; ++i) {
-                    const T send = up ? v[i] : v[i + H];
-                    const T keep = up ? v[i + H] : v[i];
-                    if constexpr (SHFL) v[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
-                    else v[i] = keep;
-                }
-                if constexpr ((C & 1) != 0) {
-                    if constexpr (SHFL) v[H] = v[C - 1] + __shfl_xor_sync(0xffffffffu, v[C - 1], OFF);
-                    else v[H] = v[C - 1];
-                }
-                MergeLevel<H + (C & 1), OFF / 2>::template run<T, NF, SHFL>(v, lane);
-            } else {
-                if constexpr (SHFL) v[0] += __shfl_xor_sync(0xffffffffu, v[0], OFF);
-                MergeLevel<1, OFF / 2>::template run<T, NF, SHFL>(v, lane);
-            }
-        }
-    }
-};
-
-template <int NF>
-__device__ __forceinline__ float warp_merge(float (&v)[NF]) {
-    MergeLevel<NF, 16>::template run<float, NF, true>(v, threadIdx.x & 31);
-    return v[0];
-}
-
-// The field this lane adds after warp_merge<NF>, or -1: the same pairing on
-// field numbers; of the lanes left holding the same field, the lowest adds.
-template <int NF>
-__device__ __forceinline__ int merge_owner() {
-    const int lane = threadIdx.x & 31;
-    int id[NF];
-#pragma unroll
-    for (int i = 0; i < NF; ++i) id[i] = i;
-    MergeLevel<NF, 16>::template run<int, NF, false>(id, lane);
-    const unsigned same = __match_any_sync(0xffffffffu, id[0]);
-    return lane == __ffs(same) - 1 ? id[0] : -1;
-}
-
 // Per-fragment quantities of the backward that do not depend on the
 // running state: offsets, Gaussian falloff G, unclamped and clamped alpha,
 // and whether the fragment was blended (inside the box, exponent <= 0,

@@ -166,3 +166,19 @@ def test_precision_form_3M_1920x1080(G, O, name):
     assert (dq > 1e-4).mean() <= 1e-3 and dq.max() <= 4 * u
     for k, v in gq.items():
         assert v <= 1e-3, (k, v)
+    # the pose gradient of a tracking loss (L1 of Eq. 6 against the crop
+    # rendered from the true pose) rather than of random image gradients,
+    # whose signs cancel far more: the 16-bit storage moves it by well under
+    # 1e-2 (the random-gradient figure above is ~30u)
+    tgt = O.render_fwd(oracle_crop(O, O.project(g, S.camera(1920, 1080, 1000.0)), cam, x0, y0, w, h)[0], ccam)
+    _, lr_, ld_ = O.loss_l1(img["rgb"], img["depth"], tgt["rgb"], tgt["depth"])
+    t_rgb = np.zeros((3, 1080, 1920), np.float32)
+    t_dep = np.zeros((1080, 1920), np.float32)
+    t_rgb[:, y0:y0 + h, x0:x0 + w] = lr_
+    t_dep[y0:y0 + h, x0:x0 + w] = ld_
+    r.backward(gd, cam, torch.from_numpy(t_rgb).cuda(), torch.from_numpy(t_dep).cuda(), mode=G.GS_TRACK)
+    r.check()
+    ref_t = O.project_bwd(g, cam, O.render_bwd(sp, ccam, lr_, ld_))["pose"]
+    e_t = rel_l2(np_of(r.pose), ref_t)
+    print(f"[{name} 3M tracking-loss pose] {e_t:.2e}")
+    assert e_t <= 1e-2, e_t
