@@ -51,6 +51,7 @@ def parse():
                         "per-Gaussian gradients) on the 1200x680 / 1M mapping window, for ncu captures")
     p.add_argument("--serving", action="store_true", help="run only the serving comparison and print its line")
     p.add_argument("--skip-serving", action="store_true")
+    p.add_argument("--skip-mapping", action="store_true")
     p.add_argument("--serving-frames", type=int, default=30)
     return p.parse_args()
 
@@ -561,6 +562,97 @@ def serving_bench(frames=30, sessions=16, light_scale=10.0):
             "resolutions": [f"{s.W}x{s.H}" for s in specs], "setup_s": setup, **out}
 
 
+def mapping_bench(iters=16, warm=8):
+    """Mapping window (1200x680, 1M surface Gaussians, 8 keyframes on a 1 m
+    arc): each mapping iteration renders one keyframe of the window (in turn)
+    from a map whose means and colours were perturbed, takes the L1 loss
+    against the keyframe rendered from the true map, and runs the backward to
+    every per-Gaussian gradient with the map's Adam step fused into the
+    backward projection (gs_project_bwd_adam).  Timed: full resolution,
+    strides 2x2 and 4x4 (Sec. 4.2), full resolution with the lowest-score
+    10 % of the Gaussians masked (Eq. 7 scores of the iterations before), and
+    full resolution with the Adam step as its own launch (gs_adam) after the
+    backward projection."""
+    import numpy as np
+    import torch
+    from paper_2510_06644_gb300 import gs
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    from synth import scenes as S
+    n = 1_000_000
+    g_true = S.surface_scene(n, seed=3000)
+    cams = S.arc_keyframes(8, 1200, 680, 600.0, seed=3001)
+    rng = S.rng(3003)
+    g0 = dict(g_true)
+    g0["means"] = (g_true["means"] + rng.normal(0, 0.002, g_true["means"].shape)).astype(np.float32)
+    g0["rgb"] = np.clip(g_true["rgb"] + rng.normal(0, 0.05, g_true["rgb"].shape), 0, 1).astype(np.float32)
+    gt = {k: torch.from_numpy(v).cuda() for k, v in g_true.items()}
+    cap = 0
+    for c in cams:
+        probe = gs.gs_project(gs.default_config(), gs.camera(c), gt)
+        cap = max(cap, int(int(gs.gs_bin_count(gs.camera(c), probe, n).item()) * 1.3) + 4096)
+    r_t = Rasterizer(n, cams[0], capacity=cap)
+    targets = []
+    for c in cams:
+        img = r_t.forward(gt, c)
+        targets.append((img["rgb"].clone(), img["depth"].clone()))
+    r_t.check()
+    del r_t, gt
+    keys = gs.PARAM_KEYS
+    out = {"workload": "1200x680, 1M surface Gaussians (means +- 2 mm, colours +- 0.05 perturbed), 8 arc keyframes",
+           "iters_timed": iters}
+
+    def run(sx, sy, mask=None, fused=True):
+        g = {k: torch.from_numpy(v).cuda() for k, v in g0.items()}
+        if mask is not None:
+            g["mask"] = mask
+        ms = {k: torch.zeros_like(g[k]) for k in keys}
+        vs = {k: torch.zeros_like(g[k]) for k in keys}
+        st = torch.zeros(2, device="cuda")
+        cs = [gs.camera(dict(c, sx=sx, sy=sy)) for c in cams]
+        tg = [(t[0][:, ::sy, ::sx].contiguous(), t[1][::sy, ::sx].contiguous()) for t in targets]
+        r = Rasterizer(n, dict(cams[0], sx=sx, sy=sy), capacity=cap)
+        grads = {k: torch.empty_like(g[k]) for k in keys} if not fused else None
+
+        def one(i):
+            j = i % len(cams)
+            if fused:
+                r.map_step(g, cs[j], tg[j][0], tg[j][1], ms, vs, st, lr=1e-4)
+            else:
+                r.forward(g, cs[j])
+                r.loss_grad(cs[j], tg[j][0], tg[j][1])
+                r.backward(g, cs[j], r.dimg["d_rgb"], r.dimg["d_depth"], gs.GS_MAP, grads=grads, want_pose=False,
+                           want_score=True)
+                gs.gs_adam([g[k] for k in keys], [grads[k] for k in keys], [ms[k] for k in keys],
+                           [vs[k] for k in keys], st, lr=1e-4)
+
+        for i in range(warm):
+            one(i)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for i in range(iters):
+            one(warm + i)
+        b.record()
+        torch.cuda.synchronize()
+        r.check()
+        ms_it = a.elapsed_time(b) / iters
+        loss = float(r.dimg["loss"].item())
+        return {"ms_per_iter": ms_it, "iters_per_s": 1e3 / ms_it, "last_loss": loss}, r
+
+    out["stride_1x1"], r_full = run(1, 1)
+    out["stride_2x2"], _ = run(2, 2)
+    out["stride_4x4"], _ = run(4, 4)
+    # the lowest-score 10 % masked (Eq. 7 scores of the last full-resolution iteration)
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    gs.gs_prune(gs.default_config(prune_frac=0.1), r_full.score, mask, 0, 5)
+    out["pruned_10pct"], _ = run(1, 1, mask=mask)
+    out["pruned_10pct"]["masked"] = int(mask.sum().item())
+    out["separate_adam"], _ = run(1, 1, fused=False)
+    for k in ("stride_2x2", "stride_4x4", "pruned_10pct", "separate_adam"):
+        out[k]["speedup_vs_1x1"] = out["stride_1x1"]["ms_per_iter"] / out[k]["ms_per_iter"]
+    return out
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle as it stands (single-threaded C) on
     one host core, each step one full tracking iteration of the benchmark
@@ -830,6 +922,8 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches_per_step * K,
     }
+    if not args.skip_mapping:
+        line["mapping"] = mapping_bench()
     if not args.skip_serving:
         line["serving"] = serving_bench(args.serving_frames)
     torch.cuda.synchronize()

@@ -531,6 +531,30 @@ gs_status gs_adam(int n_tensors, float* const* params, const float* const* grads
                   float* const* v, const int64_t* counts, float lr, float beta1, float beta2,
                   float eps, float* state, gs_stream stream);
 
+/* The map's Adam step of a mapping iteration, for gs_project_bwd_adam:
+ * moments of the five parameter arrays in gs_gaussians order (means,
+ * log_scales, quats, opacity_logit, rgb; each the size of its parameter
+ * array, starting zeroed) and the step state of gs_adam. */
+typedef struct {
+    float* m[5];
+    float* v[5];
+    float lr, beta1, beta2, eps;
+    float* state;   /* device float[2]: step count, then a ticket word (starts zeroed) */
+} gs_map_adam;
+
+/* gs_project_bwd (Sec. 2.2 Step 5, mapping) with gs_adam's step fused into
+ * it: each Gaussian's gradients are formed and applied to its parameters in
+ * the same thread, with gs_adam's arithmetic (the same bits), and the step
+ * count advances once.  g's five parameter arrays are updated in place (the
+ * const of gs_gaussians aside); grads (optional, any member NULL) still
+ * receive the gradients, score_terms (optional) the Eq. 7 terms.  No
+ * workspace; no pose gradient (tracking uses gs_project_bwd_step).  The
+ * paper's Preprocessing Engines feed the map update from the same pass
+ * (Sec. 5.4). */
+gs_status gs_project_bwd_adam(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                              const float* grad2d, const gs_map_adam* adam, gs_grads* grads, float* score_terms,
+                              gs_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* Status (the frame-level status query of Sec. 5.5, as a device word)      */
 /* ---------------------------------------------------------------------- */

@@ -242,6 +242,20 @@ __device__ __forceinline__ Geom load_geom(const void* base, uint32_t k) {
 }
 
 // ---------------------------------------------------------------------------
+// Adam (the map update of a mapping iteration; the paper fixes no optimizer)
+// ---------------------------------------------------------------------------
+// One element: m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+// p <- p - lr (m / c1) / (sqrt(v / c2) + eps), c1 = 1 - b1^t, c2 = 1 - b2^t.
+// Every operation rounded on its own (no contraction), so gs_adam and the
+// Adam step fused into the backward projection give the same bits.
+__device__ __forceinline__ void adam_elem(float& p, float& m, float& v, float g, float lr, float b1, float b2,
+                                          float c1, float c2, float eps) {
+    m = __fadd_rn(__fmul_rn(b1, m), __fmul_rn(__fsub_rn(1.f, b1), g));
+    v = __fadd_rn(__fmul_rn(b2, v), __fmul_rn(__fmul_rn(__fsub_rn(1.f, b2), g), g));
+    p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, __fdiv_rn(m, c1)), __fadd_rn(__fsqrt_rn(__fdiv_rn(v, c2)), eps)));
+}
+
+// ---------------------------------------------------------------------------
 // Multi-session waves (gs_track_wave)
 // ---------------------------------------------------------------------------
 // A wave launch's descriptor table: job j owns blocks [start[j], start[j+1])

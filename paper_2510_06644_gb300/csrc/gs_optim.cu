@@ -25,12 +25,11 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs a, int64_t total, float l
         int t = 0;
         while (t < a.nt - 1 && q >= a.end[t]) ++t;
         const int64_t i = q - (t > 0 ? a.end[t - 1] : 0);
-        const float gr = a.g[t][i];
-        const float m = b1 * a.m[t][i] + (1.f - b1) * gr;
-        const float v = b2 * a.v[t][i] + (1.f - b2) * gr * gr;
+        float p = a.p[t][i], m = a.m[t][i], v = a.v[t][i];
+        adam_elem(p, m, v, a.g[t][i], lr, b1, b2, c1, c2, eps);
+        a.p[t][i] = p;
         a.m[t][i] = m;
         a.v[t][i] = v;
-        a.p[t][i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
     }
     __shared__ bool last;
     __syncthreads();

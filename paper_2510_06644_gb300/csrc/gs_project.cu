@@ -351,12 +351,24 @@ __device__ void pose_final_last_block(const float2* __restrict__ part, int nblk,
     }
 }
 
-template <bool WANT_GRADS, bool WANT_POSE, bool WANT_SCORE>
+// The map's Adam step fused into the backward projection (mapping): each
+// thread updates its Gaussian's parameters and moments from the gradients it
+// just formed.  p[t] are the parameter arrays of the map (means, log_scales,
+// quats, opacity_logit, rgb), m[t] and v[t] their moments.
+struct AdamMap {
+    float* p[5];
+    float* m[5];
+    float* v[5];
+    float lr, b1, b2, eps, c1, c2;
+};
+
+template <bool WANT_GRADS, bool WANT_POSE, bool WANT_SCORE, bool ADAM = false>
 __device__ __forceinline__ void project_bwd_body(gs_camera cam, const gs_config& cfg, const gs_gaussians& g,
                                                  const float* __restrict__ grad2d, const gs_grads& grads,
                                                  float* __restrict__ score, float2* __restrict__ pose_part,
                                                  double* __restrict__ pose_out, unsigned int* __restrict__ ticket,
-                                                 const gs_pose_step& step, int blk, int nblk) {
+                                                 const gs_pose_step& step, int blk, int nblk,
+                                                 const AdamMap* adam = nullptr) {
     const int64_t k = (int64_t)blk * blockDim.x + threadIdx.x;
     float pose[6] = {0, 0, 0, 0, 0, 0};
     resolve_pose(cam);
@@ -490,6 +502,22 @@ __device__ __forceinline__ void project_bwd_body(gs_camera cam, const gs_config&
         } else if (!masked && WANT_GRADS) {
             // rgb gradient is independent of visibility only through grad2d,
             // which is zero for culled Gaussians; keep zeros.
+        }
+        if (ADAM) {
+            const AdamMap& A = *adam;
+            float* const gv[5] = {gmu, gls, gq, &gol, grgb};
+            const int width[5] = {3, 3, 4, 1, 3};
+#pragma unroll
+            for (int t = 0; t < 5; ++t)
+#pragma unroll
+                for (int i = 0; i < width[t]; ++i) {
+                    const size_t e = (size_t)width[t] * k + i;
+                    float pp = A.p[t][e], mm = A.m[t][e], vv = A.v[t][e];
+                    adam_elem(pp, mm, vv, gv[t][i], A.lr, A.b1, A.b2, A.c1, A.c2, A.eps);
+                    A.p[t][e] = pp;
+                    A.m[t][e] = mm;
+                    A.v[t][e] = vv;
+                }
         }
         if (WANT_GRADS) {
             if (grads.means) for (int i = 0; i < 3; ++i) grads.means[3 * k + i] = gmu[i];
@@ -779,6 +807,74 @@ extern "C" gs_status gs_project_bwd_noalloc(const gs_config* cfg, const gs_camer
     if ((s = noalloc_scratch(&scratch)) != GS_OK) return s;
     size_t have = (size_t)GS_NOALLOC_SCRATCH_BYTES;
     return gs_project_bwd(cfg, cam, g, grad2d, grads, pose_grad6, score_terms, scratch, &have, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Backward projection with the map's Adam step (mapping iteration)
+// ---------------------------------------------------------------------------
+namespace gs {
+template <bool WANT_SCORE>
+__global__ void __launch_bounds__(PB_THREADS) k_project_bwd_adam(gs_camera cam, gs_config cfg, gs_gaussians g,
+                                                                 const float* __restrict__ grad2d, gs_grads grads,
+                                                                 float* __restrict__ score, AdamMap A,
+                                                                 float* __restrict__ state) {
+    // the step count: read by every block, advanced by the last (as gs_adam)
+    const float step = __ldcg(state) + 1.f;
+    A.c1 = 1.f - powf(A.b1, step);
+    A.c2 = 1.f - powf(A.b2, step);
+    const gs_pose_step none = {nullptr, nullptr, 0.f, 0.f, 0.f, 0.f, 0.f};
+    project_bwd_body<true, false, WANT_SCORE, true>(cam, cfg, g, grad2d, grads, score, nullptr, nullptr, nullptr,
+                                                    none, (int)blockIdx.x, (int)gridDim.x, &A);
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(reinterpret_cast<unsigned int*>(state + 1), 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        state[0] = step;
+        *reinterpret_cast<unsigned int*>(state + 1) = 0u;
+    }
+}
+}  // namespace gs
+
+extern "C" gs_status gs_project_bwd_adam(const gs_config* cfg, const gs_camera* cam, const gs_gaussians* g,
+                                         const float* grad2d, const gs_map_adam* adam, gs_grads* grads,
+                                         float* score_terms, gs_stream stream) {
+    if (!cfg || !adam) return set_error(GS_ERR_INVALID_ARG, "config or adam is NULL");
+    gs_status s;
+    if ((s = check_camera(cam)) != GS_OK) return s;
+    if ((s = check_gaussians(g)) != GS_OK) return s;
+    if (!(adam->beta1 >= 0.f && adam->beta1 < 1.f) || !(adam->beta2 >= 0.f && adam->beta2 < 1.f) ||
+        !(adam->eps > 0.f))
+        return set_error(GS_ERR_INVALID_ARG, "bad Adam constants");
+    if (!adam->state) return set_error(GS_ERR_INVALID_ARG, "Adam state is NULL");
+    for (int t = 0; t < 5; ++t)
+        if (g->n > 0 && (!adam->m[t] || !adam->v[t])) return set_error(GS_ERR_INVALID_ARG, "moment array %d is NULL", t);
+    if (g->n == 0) return GS_OK;
+    if (!grad2d) return set_error(GS_ERR_INVALID_ARG, "grad2d is NULL");
+    AdamMap A;
+    float* const P[5] = {(float*)g->means, (float*)g->log_scales, (float*)g->quats, (float*)g->opacity_logit,
+                         (float*)g->rgb};
+    for (int t = 0; t < 5; ++t) {
+        A.p[t] = P[t];
+        A.m[t] = adam->m[t];
+        A.v[t] = adam->v[t];
+    }
+    A.lr = adam->lr;
+    A.b1 = adam->beta1;
+    A.b2 = adam->beta2;
+    A.eps = adam->eps;
+    A.c1 = A.c2 = 1.f;
+    const gs_grads gg = grads ? *grads : gs_grads{nullptr, nullptr, nullptr, nullptr, nullptr};
+    const unsigned nblk = (unsigned)((g->n + PB_THREADS - 1) / PB_THREADS);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (score_terms)
+        k_project_bwd_adam<true><<<nblk, PB_THREADS, 0, st>>>(*cam, *cfg, *g, grad2d, gg, score_terms, A, adam->state);
+    else
+        k_project_bwd_adam<false><<<nblk, PB_THREADS, 0, st>>>(*cam, *cfg, *g, grad2d, gg, nullptr, A, adam->state);
+    return check_launch("k_project_bwd_adam");
 }
 
 // ---------------------------------------------------------------------------

@@ -79,6 +79,11 @@ class gs_track_job(C.Structure):
 GS_WAVE_MAX = 32
 
 
+class gs_map_adam(C.Structure):
+    _fields_ = [("m", C.c_void_p * 5), ("v", C.c_void_p * 5), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("state", C.c_void_p)]
+
+
 _lib = None
 _P = C.c_void_p
 _SIGS = {
@@ -111,6 +116,7 @@ _SIGS = {
     "gs_probe_fma_f32": ([_P, C.c_int64, C.c_int32, _P], C.c_int),
     "gs_track_wave": ([_P, _P, C.c_int32, _P], C.c_int),
     "gs_next_interval": ([_P, C.c_int32, C.c_float], C.c_int32),
+    "gs_project_bwd_adam": ([_P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gs_status_reset": ([_P], C.c_int),
     "gs_last_error": ([], C.c_char_p),
 }
@@ -462,6 +468,27 @@ def gs_track_wave(cfg, jobs, stream=None):
         jobs = arr
     _check(lib().gs_track_wave(C.byref(_cfg(cfg)), C.cast(jobs, C.c_void_p), len(jobs), _stream(stream)),
            "gs_track_wave")
+
+
+PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logit", "rgb")
+
+
+def gs_project_bwd_adam(cfg, cam, g, grad2d, ms, vs, state, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15,
+                        grads=None, score=None, stream=None):
+    """Backward projection of a mapping iteration with the map's Adam step
+    fused in: g's parameter tensors are updated in place; ms / vs: dicts of
+    moment tensors keyed like g; state: float32 [2] (as gs_adam)."""
+    a = gs_map_adam()
+    for i, k in enumerate(PARAM_KEYS):
+        a.m[i] = _ptr(ms[k]).value
+        a.v[i] = _ptr(vs[k]).value
+    a.lr, a.beta1, a.beta2, a.eps = float(lr), float(beta1), float(beta2), float(eps)
+    a.state = _ptr(state).value
+    gs_g = gaussians(g)
+    gr = grads_struct(grads) if grads is not None else None
+    _check(lib().gs_project_bwd_adam(C.byref(_cfg(cfg)), C.byref(cam), C.byref(gs_g), _ptr(grad2d), C.byref(a),
+                                     C.byref(gr) if gr is not None else None, _ptr(score), _stream(stream)),
+           "gs_project_bwd_adam")
 
 
 def gs_project_bwd_noalloc(cfg, cam, g, grad2d, grads=None, pose=None, score=None, stream=None):

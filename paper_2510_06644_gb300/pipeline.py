@@ -156,6 +156,23 @@ class Rasterizer:
                                ws=self._bwd_ws(cam_s, g))
         return self.pose
 
+    def map_step(self, g, cam, target_rgb, target_depth, ms, vs, adam_state, lr=1e-4, rebin=True):
+        """One mapping iteration: forward, L1 loss (Eq. 6), backward to the
+        2D gradients (GS_MAP), then the backward projection with the map's
+        Adam step fused in (gs_project_bwd_adam): g is updated in place, the
+        Eq. 7 score terms land in self.score."""
+        cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam)
+        self.set_grid(cam_s)
+        self._project_bin(g, cam_s, rebin)
+        self._bm_used = self._masks(cam_s)
+        gs.gs_render_fwd_loss(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, target_rgb,
+                              target_depth, self.rec_dtype, out=self.img, dimg=self.dimg, order=self.order,
+                              masks=self._bm_used)
+        gs.gs_render_bwd(self.cfg, cam_s, g, self.splats, self.vals, self.ranges, self.img["t_final"],
+                         self.img["last_idx"], self.dimg["d_rgb"], self.dimg["d_depth"], gs.GS_MAP,
+                         self.rec_dtype, grad2d=self.grad2d, order=self.order, masks=self._bm_used)
+        gs.gs_project_bwd_adam(self.cfg, cam_s, g, self.grad2d, ms, vs, adam_state, lr=lr, score=self.score)
+
     def track_job(self, g, cam, target_rgb, target_depth, pose, pose_adam, lr_trans=1e-3, lr_rot=1e-3,
                   want_score=True):
         """The descriptor of one track_step of this rasterizer for a wave

@@ -194,3 +194,24 @@ def test_next_interval_follows_the_oracle_rule(built_lib):
         K = got
     assert K == 32   # ... 64 at the cap, then one halving
     assert gs.gs_next_interval(cfg, 0, 0.0) == 1
+
+
+def test_fused_adam_rejects_bad_arguments_on_the_host(built_lib):
+    from paper_2510_06644_gb300 import gs
+    L = gs.lib()
+    cfg = gs.default_config()
+    cam = gs.camera({"R": [[1, 0, 0], [0, 1, 0], [0, 0, 1]], "t": [0, 0, 0], "fx": 80.0, "fy": 80.0,
+                     "cx": 48.0, "cy": 36.0, "W": 96, "H": 72})
+    g = gs.gs_gaussians()
+    a = gs.gs_map_adam()
+    a.lr, a.beta1, a.beta2, a.eps = 1e-3, 0.9, 0.999, 1e-15
+    assert L.gs_project_bwd_adam(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), None, None, None, None,
+                                 None) == gs.GS_ERR_INVALID_ARG
+    # no state word
+    assert L.gs_project_bwd_adam(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), None, ctypes.byref(a), None,
+                                 None, None) == gs.GS_ERR_INVALID_ARG
+    a.state = 16
+    a.beta1 = 1.0
+    assert L.gs_project_bwd_adam(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), None, ctypes.byref(a), None,
+                                 None, None) == gs.GS_ERR_INVALID_ARG
+    assert b"Adam" in L.gs_last_error()

@@ -157,3 +157,55 @@ def test_project_bin_sort_equals_the_two_calls(G, n, W, H, sx, sy, dt, mask_frac
     assert torch.equal(rec_a[:n], rec_b[:n])
     assert torch.equal(ka[:k], kb[:k]) and torch.equal(va[:k], vb[:k])
     assert torch.equal(ra, rb) and torch.equal(oa, ob)
+
+
+def test_backward_projection_with_fused_adam_equals_separate_calls(G):
+    """A mapping iteration's map update fused into the backward projection
+    (gs_project_bwd_adam) against gs_project_bwd followed by gs_adam:
+    parameters, moments, step count, gradients and score terms bit for bit,
+    over three steps (the second and third project the updated map), with a
+    masked Gaussian and Gaussians behind the camera in the map."""
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    g, true_cam, start = scene_and_cams(seed=47)
+    g["means"][:50, 2] = -1.0                      # behind the camera: zero gradients, still stepped
+    mask = np.zeros(40000, np.uint8)
+    mask[60:70] = 1
+    gd = dev(g)
+    r = Rasterizer(40000, start, capacity=400000)
+    tgt = Rasterizer(40000, true_cam, capacity=400000)
+    img_t = tgt.forward(gd, true_cam)
+    trgb, tdep = img_t["rgb"].clone(), img_t["depth"].clone()
+    r.forward(gd, start)
+    r.loss_grad(start, trgb, tdep)
+    r.backward(gd, start, r.dimg["d_rgb"], r.dimg["d_depth"], G.GS_MAP, want_pose=False, want_score=False)
+    grad2d = r.grad2d.clone()
+    keys = G.PARAM_KEYS
+    cs = G.camera(start)
+    cfg = G.default_config()
+    sides = []
+    for fused in (False, True):
+        p = {k: gd[k].clone() for k in keys}
+        p["mask"] = torch.from_numpy(mask).cuda()
+        ms = {k: torch.zeros_like(gd[k]) for k in keys}
+        vs = {k: torch.zeros_like(gd[k]) for k in keys}
+        state = torch.zeros(2, device="cuda")
+        grads = {k: torch.empty_like(gd[k]) for k in keys}
+        score = torch.empty((40000, 2), device="cuda")
+        for _ in range(3):
+            if fused:
+                G.gs_project_bwd_adam(cfg, cs, p, grad2d, ms, vs, state, lr=1e-3, grads=grads, score=score)
+            else:
+                G.gs_project_bwd(cfg, cs, p, grad2d, grads=grads, score=score)
+                G.gs_adam([p[k] for k in keys], [grads[k] for k in keys], [ms[k] for k in keys],
+                          [vs[k] for k in keys], state, lr=1e-3)
+        torch.cuda.synchronize()
+        sides.append((p, ms, vs, state, grads, score))
+    a, b = sides
+    for k in keys:
+        assert torch.equal(a[0][k], b[0][k]), ("param", k)
+        assert torch.equal(a[1][k], b[1][k]), ("m", k)
+        assert torch.equal(a[2][k], b[2][k]), ("v", k)
+        assert torch.equal(a[4][k], b[4][k]), ("grad", k)
+    assert torch.equal(a[3], b[3]) and float(a[3][0]) == 3.0
+    assert torch.equal(a[5], b[5])
+    assert not torch.equal(a[0]["means"], gd["means"])   # the map moved
