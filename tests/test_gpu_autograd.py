@@ -152,3 +152,84 @@ def test_pose_central_differences(A, O):
         a = float(delta.grad[i])
         assert abs(fd - a) <= 2e-2 * max(abs(a), 1.0), (i, fd, a)
     assert pose_checked >= 4
+
+
+def test_two_views_before_one_backward(A):
+    """Two renders of the same map (the same pooled buffer shape) before one
+    backward: each keeps its own intermediates, so the gradient of the sum
+    is the sum of the two single-view gradients."""
+    g = S.surface_scene(30000, seed=14)
+    c1 = S.camera(200, 150, 160.0)
+    c2 = S.perturbed_pose(c1, seed=15, trans=0.03, rot_deg=2.0)
+    w1, wd1 = weights(200, 150, 16)
+    w2, wd2 = weights(200, 150, 17)
+    single = []
+    for cam, w, wd in ((c1, w1, wd1), (c2, w2, wd2)):
+        p = leaf_params(g)
+        delta = torch.zeros(6, device="cuda", requires_grad=True)
+        run(A, p, delta, cam, w, wd).backward()
+        single.append({k: np_of(p[k].grad) for k in KEYS})
+    p = leaf_params(g)
+    delta = torch.zeros(6, device="cuda", requires_grad=True)
+    (run(A, p, delta, c1, w1, wd1) + run(A, p, delta, c2, w2, wd2)).backward()
+    for k in KEYS:
+        assert rel_l2(np_of(p[k].grad), single[0][k] + single[1][k]) <= 1e-5, k
+
+
+def test_capacity_overflow_is_raised_then_grown(A):
+    """A pooled rasterizer sized by a sparse view overflows on a dense one of
+    the same grid: the backward raises, the capacity grows, and the render
+    that follows is complete."""
+    g = S.surface_scene(30000, seed=18)
+    away = S.camera(200, 150, 160.0, R=S.axis_angle_matrix([0, 1, 0], 2.5))   # turned away: no keys
+    near = S.camera(200, 150, 160.0)
+    w, wd = weights(200, 150, 19)
+    A._POOL.free.clear()                                       # (earlier tests pooled this shape)
+    p = leaf_params(g)
+    delta = torch.zeros(6, device="cuda", requires_grad=True)
+    run(A, p, delta, away, w, wd).backward()                   # sizes the pooled buffers
+    with pytest.raises(RuntimeError, match="exceeded the capacity"):
+        run(A, leaf_params(g), delta, near, w, wd).backward()
+    p = leaf_params(g)
+    run(A, p, delta, near, w, wd).backward()
+    fresh = leaf_params(g)
+    A._POOL.free.clear()
+    run(A, fresh, delta, near, w, wd).backward()
+    for k in KEYS:
+        assert rel_l2(np_of(p[k].grad), np_of(fresh[k].grad)) <= 1e-5, k
+
+
+def test_autograd_3M_1920x1080_bf16(A, O):
+    """The precision workload through gs_render: 3M Gaussians at 1920x1080
+    with bf16 records, loss weights on a 256x256 crop; gradients within the
+    64u bound of the precision form against the FP64 oracle on the crop, and
+    recompute (memory budget 0) equal to store."""
+    import torch as T
+    from tests.test_gpu_scale import oracle_crop
+    g = S.surface_scene(3_000_000, seed=4000)
+    cam = S.perturbed_pose(S.camera(1920, 1080, 1000.0), seed=4001, trans=0.02, rot_deg=1.0)
+    x0, y0, w, h = 832, 412, 256, 256
+    rng = S.rng(4005)
+    W = np.zeros((3, 1080, 1920), np.float32)
+    Wd = np.zeros((1080, 1920), np.float32)
+    W[:, y0:y0 + h, x0:x0 + w] = rng.normal(0, 1, (3, h, w)) / (w * h)
+    Wd[y0:y0 + h, x0:x0 + w] = rng.normal(0, 1, (h, w)) / (w * h)
+    from paper_2510_06644_gb300 import gs
+    out = []
+    for budget in (None, 0):
+        p = leaf_params(g)
+        delta = T.zeros(6, device="cuda", requires_grad=True)
+        run(A, p, delta, cam, W, Wd, rec_dtype=gs.GS_BF16, memory_budget=budget).backward()
+        out.append({**{k: np_of(p[k].grad) for k in KEYS}, "pose": np_of(delta.grad)})
+    for k in out[0]:
+        assert rel_l2(out[1][k], out[0][k]) <= 1e-5, k
+    pr = O.project(g, cam)
+    sp, ccam = oracle_crop(O, pr, cam, x0, y0, w, h)
+    g2 = O.render_bwd(sp, ccam, W[:, y0:y0 + h, x0:x0 + w], Wd[y0:y0 + h, x0:x0 + w])
+    ref = O.project_bwd(g, cam, g2)
+    u = 2.0 ** -8
+    errs = {k: rel_l2(out[0][k], ref[k]) for k in KEYS}
+    errs["pose"] = rel_l2(out[0]["pose"], ref["pose"])
+    print("\n[autograd bf16 3M 1920x1080 crop] " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    for k, v in errs.items():
+        assert v <= 64 * u, (k, v)
