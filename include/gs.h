@@ -348,11 +348,14 @@ gs_status gs_project_bwd(const gs_config* cfg, const gs_camera* cam, const gs_ga
  * framework that owns every allocation and offers the library no allocator).
  * Same arguments and results as gs_project_bwd, minus the workspace: the
  * scratch (per-block pose partials and a ticket) lives in a static device
- * array of GS_NOALLOC_SCRATCH_BYTES (~769 KB) that every device which loads
+ * array of GS_NOALLOC_SCRATCH_BYTES (768 KiB: 786,688 bytes) that every device which loads
  * the library holds until the process exits.  n is limited to
  * GS_NOALLOC_MAX_GAUSSIANS; a larger n returns GS_ERR_INVALID_ARG.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
+ * device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process: after cudaDeviceReset the
+ * entry point must not be called again, and it serves the device's primary
+ * context only.  All
  * calls share the one array: calls that overlap on the GPU (different
  * streams, or different host threads, without ordering) race and must be
  * serialised by the caller.  No cudaMalloc, cudaFree or allocating library

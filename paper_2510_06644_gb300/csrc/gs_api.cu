@@ -1,6 +1,7 @@
 // Host-side plumbing of the C ABI: thread-local error messages, the device
 // status word, defaults and version.
 #include <stdarg.h>
+#include <atomic>
 #include <stdio.h>
 
 #include "gs_internal.cuh"
@@ -12,15 +13,18 @@ __device__ unsigned int g_status = 0u;
 // Cached per device, so that no runtime query happens while a stream is
 // being captured into a CUDA graph after the first call on a device.
 unsigned int* status_ptr() {
-    static unsigned int* cache[64] = {nullptr};
+    // threads that race on an entry store the same address
+    static std::atomic<unsigned int*> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!cache[dev]) {
+    unsigned int* q = cache[dev].load(std::memory_order_relaxed);
+    if (!q) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-        cache[dev] = (unsigned int*)p;
+        q = (unsigned int*)p;
+        cache[dev].store(q, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return q;
 }
 
 static thread_local char t_msg[512] = "";

@@ -9,6 +9,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "gs_internal.cuh"
 
@@ -775,19 +776,27 @@ extern "C" gs_status gs_pose_update(float* pose, const double* pose_grad6, float
 // host code this name is only a stand-in: the kernel gets the device address
 // looked up below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GS_NOALLOC_SCRATCH_BYTES];
+// the size: one float2 pose partial per component (6) and block of PB_THREADS
+// Gaussians, plus the ticket word, rounded to 256 bytes
+static_assert(PB_THREADS == 256 && 6 * sizeof(float2) == 48,
+              "GS_NOALLOC_SCRATCH_BYTES assumes 256 Gaussians and 48 bytes of pose partials per block");
 
 static gs_status noalloc_scratch(void** out) {
-    static void* cache[64] = {nullptr};
+    // One entry per device, written by a host thread's first call.  Threads
+    // that race on an entry store the same address (relaxed atomics keep
+    // that race defined).  cudaDeviceReset invalidates the entry: the
+    // address is not looked up again until the process restarts.
+    static std::atomic<void*> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
         return set_error(GS_ERR_CUDA, "no current device");
-    if (!cache[dev]) {
-        void* p = nullptr;
+    void* p = cache[dev].load(std::memory_order_relaxed);
+    if (!p) {
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return set_error(GS_ERR_CUDA, "scratch address: %s", cudaGetErrorString(e));
-        cache[dev] = p;
+        cache[dev].store(p, std::memory_order_relaxed);
     }
-    *out = cache[dev];
+    *out = p;
     return GS_OK;
 }
 

@@ -85,3 +85,44 @@ def test_noalloc_rejects_more_than_its_maximum():
                                          ctypes.c_void_p(dummy.data_ptr()), None, None, None, None)
     assert rc == gs.GS_ERR_INVALID_ARG
     assert b"GS_NOALLOC_MAX_GAUSSIANS" in gs.lib().gs_last_error()
+
+
+@pytest.mark.parametrize("subset", ["pose", "grads+score", "score"])
+def test_noalloc_output_subsets_through_the_binding(subset):
+    """Each subset of outputs takes its own kernel form (and only the pose
+    uses the scratch's ticket): through the Python binding, every subset
+    gives what gs_project_bwd gives for it, on two calls in a row."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_06644_gb300 import build
+    build.build()
+    from paper_2510_06644_gb300 import gs
+
+    n = 30000
+    g = S.surface_scene(n, seed=4300)
+    cam = S.perturbed_pose(S.camera(320, 240, 260.0), seed=6, trans=0.03, rot_deg=1.0)
+    gd = {k: torch.from_numpy(v).cuda() for k, v in g.items()}
+    g2 = torch.from_numpy((S.rng(8).normal(0, 1e-3, (n, 12))).astype(np.float32)).cuda()
+    cfg = gs.default_config()
+    cs = gs.camera(cam)
+    keys = ("means", "log_scales", "quats", "opacity_logit", "rgb")
+
+    def outputs():
+        return ({k: torch.full_like(gd[k], float("nan")) for k in keys} if "grads" in subset else None,
+                torch.full((6,), float("nan"), dtype=torch.float64, device="cuda") if "pose" in subset else None,
+                torch.full((n, 2), float("nan"), device="cuda") if "score" in subset else None)
+
+    rg, rp, rs = outputs()
+    gs.gs_project_bwd(cfg, cs, gd, g2, grads=rg, pose=rp, score=rs)
+    for call in range(2):
+        og, op, os_ = outputs()
+        gs.gs_project_bwd_noalloc(cfg, cs, gd, g2, grads=og, pose=op, score=os_)
+        torch.cuda.synchronize()
+        for a, b in ((og, rg), (op, rp), (os_, rs)):
+            if a is None:
+                continue
+            if isinstance(a, dict):
+                for k in keys:
+                    assert rel(a[k], b[k]) <= TOL, (call, subset, k)
+            else:
+                assert rel(a, b) <= TOL, (call, subset)
