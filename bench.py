@@ -293,9 +293,12 @@ def measure_variants(gs, Rasterizer, rast, gd, cam_s, start_cam, trgb, tdep, pos
     from paper_2510_06644_gb300.pipeline import ListReuse
 
     def pose_err(p):
-        R = p[:9].reshape(3, 3)
-        return {"t_m": float(np.linalg.norm(p[9:])),
-                "r_deg": float(np.degrees(np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1))))}
+        R = p[:9].reshape(3, 3).astype(np.float64)
+        # the rotation angle from both its sine (the skew part) and cosine:
+        # accurate for small angles, unlike the arc cosine of the trace
+        s = 0.5 * np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]])
+        ang = np.arctan2(np.linalg.norm(s), (np.trace(R) - 1) / 2)
+        return {"t_m": float(np.linalg.norm(p[9:])), "r_deg": float(np.degrees(ang))}
 
     iters = 100
     res = {"iters": iters, "start": pose_err(pose0.cpu().numpy())}
