@@ -641,37 +641,37 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
         //   s_{k-1} = s_k + alpha_k (c_k . g - s_k),
         // and alpha dL/dalpha = w (c . g - s) is the exponent's gradient.
         auto back = [&](int e, const FragGeo& fg, float* f) {
-#pragma unroll
-            for (int q = 0; q < NF; ++q) f[q] = 0.f;
-            if (!fg.contrib) return;
+            // branch-free: every lane evaluates the recursion (all values are
+            // finite: 1 - alpha >= 1 - alpha_max); a lane whose pixel did not
+            // blend the entry keeps its state and contributes zeros
             const float alpha = fg.alpha;
             // fast division (at most 2 ulp for these operands: 1 - alpha in
             // [0.01, 1], T in [t_eps, 1]); over the few hundred entries a
             // pixel recovers the relative drift stays near 1e-5
-            T = __fdividef(T, 1.f - alpha);
-            const float w = alpha * T;
+            T = fg.contrib ? __fdividef(T, 1.f - alpha) : T;
+            const float w = fg.contrib ? alpha * T : 0.f;
             const float4 Cc = sp[e].c;
             const float cg = __fmaf_rn(fg.dep, gD, __fmaf_rn(Cc.z, gC2, __fmaf_rn(Cc.y, gC1, Cc.x * gC0)));
             const float dif = cg - sg;
-            sg = __fmaf_rn(alpha, dif, sg);
+            sg = fg.contrib ? __fmaf_rn(alpha, dif, sg) : sg;
+            // the clamp passes no gradient to opacity or shape
+            const bool clamped = fg.raw > cfg.alpha_max;
+            const float h = clamped ? 0.f : (-0.5f * w) * dif;  // -dL/d(exponent) / 2
+            const float u = h * fg.dx, v = h * fg.dy;
+            f[0] = fg.a * h;
+            f[1] = fg.b * h;
+            f[2] = u * fg.dx;
+            f[3] = u * fg.dy;
+            f[4] = v * fg.dy;
             if (MODE == GS_MAP) {
+                // dalpha/dopacity = e^(-q/2)
+                f[5] = (fg.contrib && !clamped) ? exp2_sfu(__fmul_rn(fg.q, R_NEG_HALF_LOG2E)) * (T * dif) : 0.f;
                 f[6] = w * gD;
                 f[7] = w * gC0;
                 f[8] = w * gC1;
                 f[9] = w * gC2;
             } else {
                 f[5] = w * gD;
-            }
-            if (!(fg.raw > cfg.alpha_max)) {  // the clamp passes no gradient
-                // dalpha/dopacity = e^(-q/2) (mapping only)
-                if (MODE == GS_MAP) f[5] = exp2_sfu(__fmul_rn(fg.q, R_NEG_HALF_LOG2E)) * (T * dif);
-                const float h = (-0.5f * w) * dif;  // -dL/d(exponent) / 2
-                const float u = h * fg.dx, v = h * fg.dy;
-                f[0] = fg.a * h;
-                f[1] = fg.b * h;
-                f[2] = u * fg.dx;
-                f[3] = u * fg.dy;
-                f[4] = v * fg.dy;
             }
         };
 #pragma unroll 1
