@@ -50,6 +50,8 @@ def parse():
                    help="only run warmup + steps mapping iterations (GS_MAP: forward, loss, backward with all "
                         "per-Gaussian gradients) on the 1200x680 / 1M mapping window, for ncu captures")
     p.add_argument("--serving", action="store_true", help="run only the serving comparison and print its line")
+    p.add_argument("--profile-wave", action="store_true",
+                   help="eager waves of the 16 serving sessions for ncu (nothing printed)")
     p.add_argument("--skip-serving", action="store_true")
     p.add_argument("--skip-mapping", action="store_true")
     p.add_argument("--serving-frames", type=int, default=30)
@@ -967,10 +969,42 @@ def profile_mapping(args):
     r.check()
 
 
+def profile_wave(args):
+    """Eager waves of the 16 serving sessions (each at the stride of a
+    different frame of the keyframe schedule, so every compositing form
+    runs): warm-up + steps waves of gs_track_wave over all sessions; nothing
+    is printed; for ncu launch lists of the wave kernels."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_06644_gb300 import gs
+    from paper_2510_06644_gb300 import serve as SV
+    specs = SV.make_session_specs(16, n_frames=5)
+    sess = []
+    for sp in specs:
+        scene, cams = SV.session_inputs(sp)
+        s = SV.Session(sp, scene, cams, use_graphs=False)
+        s.prepare()
+        sess.append(s)
+    stream = torch.cuda.current_stream()
+    jobs = []
+    for i, s in enumerate(sorted(sess, key=lambda x: -x.spec.n)):
+        _, sx, sy = s.start_frame(i % 5, stream)
+        jobs.append(s.wave_job(sx, sy))
+    arr = (gs.gs_track_job * len(jobs))(*jobs)
+    for _ in range(args.warmup + args.steps):
+        gs.gs_track_wave(sess[0].cfg, arr)
+    torch.cuda.synchronize()
+    code, _ = gs.gs_status_poll(blocking=True)
+    assert code == gs.GS_OK, code
+
+
 def main():
     args = parse()
     if args.profile_mapping:
         profile_mapping(args)
+    elif args.profile_wave:
+        profile_wave(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.serving:
