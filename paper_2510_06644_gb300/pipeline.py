@@ -133,16 +133,22 @@ class Rasterizer:
         return self.pose
 
     def track_step(self, g, cam, target_rgb, target_depth, pose, pose_adam, lr_trans=1e-3, lr_rot=1e-3,
-                   rebin=True):
+                   rebin=True, wave=True):
         """One fused tracking iteration: projection, binning + sort, forward
         compositing with the loss (gs_render_fwd_loss), backward compositing,
         then backward projection with the pose step fused into its last block
         (gs_project_bwd_step).  `cam` must carry the device pose (`pose`,
         float32 [12]) so the next iteration sees the updated pose; pose_adam
-        is the float32 [13] Adam state.  Seven kernel launches (plus memsets):
-        the projection also counts the binning's tiles (gs_project_bin_sort)."""
+        is the float32 [13] Adam state.  Seven kernel launches: with float32
+        records, fresh binning and at most 8192 tiles the iteration runs as a
+        wave of one session (gs_track_wave, no memsets) unless wave=False;
+        otherwise through the separate calls (the projection also counts the
+        binning's tiles, gs_project_bin_sort)."""
         cam_s = cam if isinstance(cam, gs.gs_camera) else gs.camera(cam, pose=pose)
         self.set_grid(cam_s)
+        _, _, TX, TY = self._grid
+        if wave and rebin and self.rec_dtype == gs.GS_F32 and self.n > 0 and TX * TY <= 8192:
+            return self.track_step_wave(g, cam_s, target_rgb, target_depth, pose, pose_adam, lr_trans, lr_rot)
         self._project_bin(g, cam_s, rebin)
         self._bm_used = self._masks(cam_s)
         gs.gs_render_fwd_loss(self.cfg, cam_s, self.splats, self.n, self.vals, self.ranges, target_rgb,
@@ -207,6 +213,22 @@ class Rasterizer:
         j.bwd_workspace, j.bwd_workspace_bytes = gs._ptr(bw).value, bw.numel()
         j.step = gs.pose_step(pose, pose_adam, lr_trans, lr_rot)
         return j
+
+    def track_step_wave(self, g, cam, target_rgb, target_depth, pose, pose_adam, lr_trans=1e-3, lr_rot=1e-3):
+        """track_step as a wave of one session (gs_track_wave): the same
+        iteration in 7 launches, the zeroing the separate calls do with
+        memsets (loss, tickets, 2D gradients) folded into the projection
+        launch.  The descriptor is rebuilt when a buffer or the camera
+        changes."""
+        key = (g["means"].data_ptr(), target_rgb.data_ptr(), target_depth.data_ptr(), pose.data_ptr(),
+               pose_adam.data_ptr(), float(lr_trans), float(lr_rot),
+               bytes(cam) if isinstance(cam, gs.gs_camera) else repr(cam), self.capacity)
+        if getattr(self, "_wave_key", None) != key:
+            self._wave_job = (gs.gs_track_job * 1)(self.track_job(g, cam, target_rgb, target_depth, pose, pose_adam,
+                                                                 lr_trans, lr_rot))
+            self._wave_key = key
+        gs.gs_track_wave(self.cfg, self._wave_job)
+        return self.pose
 
     def check(self):
         """Synchronises and raises if a device condition was raised (key

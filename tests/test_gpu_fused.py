@@ -91,9 +91,10 @@ def test_backward_projection_with_fused_pose_step_equals_separate_calls(G):
 
 @pytest.mark.parametrize("sx,sy", [(1, 1), (2, 2)])
 def test_fused_tracking_iterations_follow_the_separate_ones(G, sx, sy):
-    """Ten iterations of Rasterizer.track_step against step() +
-    gs_pose_update: same pose trajectory (to the nondeterministic order of
-    the backward's float atomics)."""
+    """Ten iterations of Rasterizer.track_step (as a wave of one session, and
+    through the separate fused calls) against step() + gs_pose_update: same
+    pose trajectory (to the nondeterministic order of the backward's float
+    atomics)."""
     from paper_2510_06644_gb300.pipeline import Rasterizer
     g, true_cam, start = scene_and_cams(seed=60)
     gd = dev(g)
@@ -101,7 +102,7 @@ def test_fused_tracking_iterations_follow_the_separate_ones(G, sx, sy):
     img = tgt.forward(gd, dict(true_cam, sx=sx, sy=sy))
     trgb, tdep = img["rgb"].clone(), img["depth"].clone()
     traj = []
-    for fused in (False, True):
+    for fused in (False, True, "calls"):
         r = Rasterizer(40000, dict(start, sx=sx, sy=sy), capacity=400000)
         pose = G.pose_tensor(start)
         adam = torch.zeros(13, device="cuda")
@@ -109,16 +110,17 @@ def test_fused_tracking_iterations_follow_the_separate_ones(G, sx, sy):
         poses = []
         for _ in range(10):
             if fused:
-                r.track_step(gd, cs, trgb, tdep, pose, adam)
+                r.track_step(gd, cs, trgb, tdep, pose, adam, wave=fused is True)
             else:
                 r.step(gd, cs, trgb, tdep, G.GS_TRACK)
                 G.gs_pose_update(pose, r.pose, adam)
             poses.append(pose.cpu().numpy().copy())
         r.check()
         traj.append(np.array(poses))
-    a, b = traj
+    a, b, c = traj
     assert np.abs(a[-1] - a[0]).max() > 1e-4
     assert np.abs(a - b).max() <= 1e-5, np.abs(a - b).max()
+    assert np.abs(a - c).max() <= 1e-5, np.abs(a - c).max()
 
 
 @pytest.mark.parametrize("n,W,H,sx,sy,dt,mask_frac", [

@@ -68,7 +68,7 @@ def test_wave_equals_each_session_alone(G):
     ref = []
     for s in sess:
         r, pose, adam, cs = fresh(G, s)
-        r.track_step(s["g"], cs, s["trgb"], s["tdep"], pose, adam)
+        r.track_step(s["g"], cs, s["trgb"], s["tdep"], pose, adam, wave=False)   # the separate calls
         torch.cuda.synchronize()
         r.check()
         ref.append((outputs(r), pose.clone()))
@@ -105,7 +105,7 @@ def test_waves_track_like_the_plain_loop(G):
     for s in sess:
         r, pose, adam, cs = fresh(G, s)
         for _ in range(iters):
-            r.track_step(s["g"], cs, s["trgb"], s["tdep"], pose, adam)
+            r.track_step(s["g"], cs, s["trgb"], s["tdep"], pose, adam, wave=False)
         ref.append(pose.clone())
     state = [fresh(G, s) for s in sess]
     jobs = [r.track_job(s["g"], cs, s["trgb"], s["tdep"], pose, adam) for s, (r, pose, adam, cs) in zip(sess, state)]
