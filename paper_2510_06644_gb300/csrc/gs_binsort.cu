@@ -23,8 +23,9 @@
 //                   so any correct sort of them gives the same result.
 //                   One launch: buckets of up to 512 keys take one warp
 //                   each, a merge sort with the keys in registers; up to
-//                   8192 keys one CTA, each warp merge-sorting 512 before
-//                   the warps merge their runs; longer buckets sort
+//                   4096 keys one CTA, each warp merge-sorting 256 (8 per
+//                   lane) before the warps merge their runs, up to 8192 the
+//                   same with 512 per warp; longer buckets sort
 //                   8192-key runs in shared memory and merge them by rank
 //                   in global memory.  The sort writes tile_id << 32 |
 //                   depth_bits and the id.
@@ -593,6 +594,22 @@ __device__ __forceinline__ void tile_sort_body(const uint32_t* __restrict__ rang
     const uint32_t b = ranges[2 * t], e = ranges[2 * t + 1];
     const int n = (int)(e - b);
     u64* key = keys + b;
+    if (n <= 4096) {
+        // m / 256 warps, 8 keys per thread in registers: each warp sorts a
+        // run of 256, then the group merges the runs (half the serial merge
+        // steps per round of 16 keys per thread)
+        int m = 1024;
+        while (m < n) m <<= 1;
+        const int W = m / 256;
+        if ((int)(threadIdx.x >> 5) >= W) return;
+        u64 v[8];
+        load_blocked<8>(key, n, v, s, (int)threadIdx.x, W * 32);
+        sort_regs<8>(v);
+        merge_rounds<8>(v, s + pad16((threadIdx.x >> 5) * 256), (int)(threadIdx.x & 31), 32, 8);
+        merge_rounds<8>(v, s, (int)threadIdx.x, W * 32, 256);
+        store_sorted<8>(key, vals + b, n, (u64)(uint32_t)t << 32, v, s, (int)threadIdx.x, W * 32);
+        return;
+    }
     if (n <= TS_SMEM_KEYS) {
         // m / 512 warps, 16 keys per thread in registers: each warp sorts a
         // run of 512, then the group merges the runs
