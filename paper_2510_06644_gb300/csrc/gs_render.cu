@@ -183,17 +183,21 @@ __device__ __forceinline__ float raw_alpha(float q, float log2_op) {
 // test, so the image and gradients are unchanged; the compositing loops just
 // visit fewer entries.  A Gaussian whose opacity is clearly below alpha_min
 // gets an empty box.  Forward and backward use the same box.
-__device__ __forceinline__ int4 pixel_box(const Splat& v, float alpha_min) {
+// t2 receives the widened threshold 2 (ln(opacity / alpha_min) + 1e-4), or
+// -1 when the box is the 3-sigma box alone (no usable ellipse).
+__device__ __forceinline__ int4 pixel_box(const Splat& v, float alpha_min, float& t2) {
     const int xi = pix_floor(v.x), yi = pix_floor(v.y), r = v.radius;
     int4 box = make_int4(xi - r, xi + r, yi - r, yi + r);
+    t2 = -1.f;
     const float det = v.ca * v.cc - v.cb * v.cb;
     if (!(det > 0.f) || !(v.op > 0.f) || !(alpha_min > 0.f)) return box;
     const float thr = logf(v.op / alpha_min);
     if (thr < -1e-4f) return make_int4(1, 0, 1, 0);  // empty: opacity < alpha_min
-    const float t2 = 2.f * (fmaxf(thr, 0.f) + 1e-4f);
-    const float ex = sqrtf(t2 * v.cc / det) * 1.001f + 1e-3f;
-    const float ey = sqrtf(t2 * v.ca / det) * 1.001f + 1e-3f;
+    const float t = 2.f * (fmaxf(thr, 0.f) + 1e-4f);
+    const float ex = sqrtf(t * v.cc / det) * 1.001f + 1e-3f;
+    const float ey = sqrtf(t * v.ca / det) * 1.001f + 1e-3f;
     if (!(ex < 1e8f) || !(ey < 1e8f)) return box;
+    t2 = t;
     // pixel p qualifies when |p + 0.5 - x| <= ex
     box.x = max(box.x, (int)ceilf(v.x - ex - 0.5f));
     box.y = min(box.y, (int)floorf(v.x + ex - 0.5f));
@@ -202,16 +206,101 @@ __device__ __forceinline__ int4 pixel_box(const Splat& v, float alpha_min) {
     return box;
 }
 
-__device__ __forceinline__ void fill_staged(const Splat& v, float alpha_min, StagedSplat& s) {
+// The warp blocks of a group's tile in full-resolution pixels: warp w's
+// block (strip w / wx, column w % wx) spans columns x0 + (w % wx) sxb ..
+// + bw and rows y0 + (w / wx) syb .. + bh (the extents map_pixel gives).
+struct TileBlocks {
+    int x0, y0, bw, bh, sxb, syb, wx, ns;
+};
+
+// (KST == 1: a full-resolution 16x16 tile of 8 warps, compile-time extents)
+template <int KST>
+__device__ __forceinline__ TileBlocks tile_blocks(const Grid& g, int tile, int TT) {
+    const int tx = tile % g.TX, ty = tile / g.TX;
+    TileBlocks b;
+    if (KST == 1) {
+        b.x0 = tx * 16;
+        b.y0 = ty * 16;
+        b.bw = 7;
+        b.bh = 3;
+        b.sxb = 8;
+        b.syb = 4;
+        b.wx = 2;
+        b.ns = 4;
+        return b;
+    }
+    const int BW = g.tw < 8 ? g.tw : 8, BH = 32 / BW, WX = g.tw / BW;
+    b.x0 = tx * g.tw * g.sx;
+    b.y0 = ty * g.th * g.sy;
+    b.bw = (BW - 1) * g.sx;
+    b.bh = (BH - 1) * g.sy;
+    b.sxb = BW * g.sx;
+    b.syb = BH * g.sy;
+    b.wx = WX;
+    b.ns = (TT >> 5) / WX;
+    return b;
+}
+
+// Warp blocks of the tile in which a Gaussian can be blended: bit w when
+// some pixel of warp w's block lies in the Gaussian's box (bx, staged form)
+// and in the region d^T Q d <= t (t = t2 widened by 1 %; t2 < 0: the box
+// alone decides).  Per strip of blocks (a band of rows) the ellipse's x
+// extent over the band follows from its chord [(-cb dy -+ sqrt(t ca - det
+// dy^2)) / ca] at the band's rows closest to the rightmost point (dy = -cb
+// ex / cc) and the leftmost point (dy = cb ex / cc): the chord's right end
+// is concave in dy and its left end convex.  The extent is widened by 1e-2
+// ex + 0.05 px, well beyond the float32 rounding of the fragment test, so
+// the bits never drop a fragment the compositing loop would blend.
+__device__ __forceinline__ unsigned block_bits(const Splat& v, const int4& bx, float t2, const TileBlocks& tb) {
+    const bool ell = t2 > 0.f;
+    const float det = v.ca * v.cc - v.cb * v.cb;
+    float tA = 0.f, ey = 0.f, yr = 0.f, ia = 0.f, sl = 0.f;
+    if (ell) {
+        const float t = t2 * 1.01f;
+        const float ex = sqrtf(t * v.cc / det);
+        tA = t * v.ca;
+        ey = sqrtf(tA / det);
+        yr = -v.cb * ex / v.cc;
+        ia = 1.f / v.ca;
+        sl = 1e-2f * ex + 0.05f;
+    }
+    unsigned bits = 0u;
+#pragma unroll 1
+    for (int s = 0; s < tb.ns; ++s) {
+        const int ry = tb.y0 + s * tb.syb;
+        const int r0 = max(ry, bx.z), r1 = min(ry + tb.bh, bx.z + bx.w);
+        if (r0 > r1) continue;
+        int c0 = bx.x, c1 = bx.x + bx.y;
+        if (ell) {
+            const float ylo = fminf(fmaxf((float)r0 + 0.5f - v.y, -ey), ey);
+            const float yhi = fminf(fmaxf((float)r1 + 0.5f - v.y, -ey), ey);
+            const float dr = fminf(fmaxf(yr, ylo), yhi), dl = fminf(fmaxf(-yr, ylo), yhi);
+            const float xr = (sqrtf(fmaxf(tA - det * dr * dr, 0.f)) - v.cb * dr) * ia;
+            const float xl = (-sqrtf(fmaxf(tA - det * dl * dl, 0.f)) - v.cb * dl) * ia;
+            c0 = max(c0, (int)ceilf(v.x + xl - sl - 0.5f));
+            c1 = min(c1, (int)floorf(v.x + xr + sl - 0.5f));
+        }
+        for (int c = 0; c < tb.wx; ++c) {
+            const int x = tb.x0 + c * tb.sxb;
+            if (c0 <= x + tb.bw && c1 >= x) bits |= 1u << (s * tb.wx + c);
+        }
+    }
+    return bits;
+}
+
+// Stages a Gaussian; with tb (the forward) c.w holds its block bits.
+__device__ __forceinline__ void fill_staged(const Splat& v, float alpha_min, StagedSplat& s,
+                                            const TileBlocks* tb = nullptr) {
     s.a = make_float4(v.x, v.y, v.ca, v.cb);
     s.b = make_float4(v.cc, v.op, v.depth, log2_opacity(v.op));
-    s.c = make_float4(v.r, v.g, v.b, 0.f);
     // the box as (x0, x1 - x0, y0, y1 - y0), clamped far outside any image;
     // an empty box never matches
-    const int4 bx = pixel_box(v, alpha_min);
+    float t2;
+    const int4 bx = pixel_box(v, alpha_min, t2);
     const int lo = -(1 << 28), hi = 1 << 28;
     const int x0 = max(bx.x, lo), x1 = min(bx.y, hi), y0 = max(bx.z, lo), y1 = min(bx.w, hi);
     s.box = x1 < x0 || y1 < y0 ? make_int4(hi, 0, hi, 0) : make_int4(x0, x1 - x0, y0, y1 - y0);
+    s.c = make_float4(v.r, v.g, v.b, tb ? __uint_as_float(block_bits(v, s.box, t2, *tb)) : 0.f);
 }
 
 // Stages list entries [0, n_in) of `ids` into sp[] (and their ids into sid[]
@@ -228,7 +317,7 @@ __device__ __forceinline__ int il_slot(int e) { return (e >> 5) * 33 + (e & 31) 
 template <int DT, int KST, bool IL = false>
 __device__ __forceinline__ void stage_batch(const void* __restrict__ splats, const uint32_t* __restrict__ ids,
                                             int n_in, int lt, int TT, float alpha_min, StagedSplat* sp,
-                                            uint32_t* sid) {
+                                            uint32_t* sid, const TileBlocks* tb = nullptr) {
     for (int e0 = lt; e0 < n_in; e0 += KST * TT) {
         uint32_t id[KST];
 #pragma unroll
@@ -240,7 +329,7 @@ __device__ __forceinline__ void stage_batch(const void* __restrict__ splats, con
 #pragma unroll
         for (int k = 0; k < KST; ++k)
             if (e0 + k * TT < n_in) {
-                fill_staged(v[k], alpha_min, sp[IL ? il_slot(e0 + k * TT) : e0 + k * TT]);
+                fill_staged(v[k], alpha_min, sp[IL ? il_slot(e0 + k * TT) : e0 + k * TT], tb);
                 if (sid) sid[e0 + k * TT] = id[k];
             }
     }
@@ -250,7 +339,6 @@ __device__ __forceinline__ void stage_batch(const void* __restrict__ splats, con
 // is set when entry 32q + e (below `limit`) meets the block.  Lane q returns
 // word q (words at or beyond `words` are zero), so a word is one shuffle away
 // and the masks stay in registers.
-template <bool IL = false>
 __device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit, int words, const PixelMap& m) {
     const int lane = threadIdx.x & 31;
     unsigned mine = 0u;
@@ -259,9 +347,24 @@ __device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit,
         const int e = q * 32 + lane;
         bool hit = false;
         if (q < words && e < limit) {
-            const int4 box = sp[IL ? il_slot(e) : e].box;
+            const int4 box = sp[e].box;
             hit = !(box.x + box.y < m.wx0 || box.x > m.wx1 || box.z + box.w < m.wy0 || box.z > m.wy1);
         }
+        const unsigned w = __ballot_sync(0xffffffffu, hit);
+        if (lane == q) mine = w;
+    }
+    return mine;
+}
+
+// The same masks from the block bits of a forward batch (warp wg of its
+// group): entries whose alpha region misses the block are left out too.
+__device__ __forceinline__ unsigned warp_masks_bits(const StagedSplat* sp, int limit, int words, int wg) {
+    const int lane = threadIdx.x & 31;
+    unsigned mine = 0u;
+#pragma unroll
+    for (int q = 0; q < R_MASKW; ++q) {
+        const int e = q * 32 + lane;
+        const bool hit = q < words && e < limit && ((__float_as_uint(sp[il_slot(e)].c.w) >> wg) & 1u);
         const unsigned w = __ballot_sync(0xffffffffu, hit);
         if (lane == q) mine = w;
     }
@@ -367,6 +470,7 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
     StagedSplat* sp = sp_all + G.gi * (G.B / 32 * 33);
     const int tile = G.tile;
     const PixelMap m = map_pixel(g, tile, G.lt);
+    const TileBlocks tb = tile_blocks<KST>(g, tile, G.TT);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
     for (int q = G.lt; q < G.B / 32; q += G.TT) {  // the dummies
@@ -387,13 +491,13 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
         // are no longer read) that also ends the tile once every pixel stopped
         if (b != start && group_count(G, done) == G.TT) break;
         const int n_in = (int)min((uint32_t)G.B, end - b);
-        stage_batch<DT, KST, true>(splats, vals + b, n_in, G.lt, G.TT, cfg.alpha_min, sp, nullptr);
+        stage_batch<DT, KST, true>(splats, vals + b, n_in, G.lt, G.TT, cfg.alpha_min, sp, nullptr, &tb);
         group_sync(G);
         // lane q clears word q of the batch, then stores it once processed
         const uint32_t bm_w = bm_off + ((b - start) >> 5);
         if (O.bmask && lane < ((n_in + 31) >> 5)) O.bmask[bm_w + lane] = 0u;
         if (!__all_sync(0xffffffffu, done)) {
-            const unsigned mword = warp_masks<true>(sp, n_in, words, m);
+            const unsigned mword = warp_masks_bits(sp, n_in, words, G.lt >> 5);
             const uint32_t base = b - start;
 #pragma unroll 1
             for (int q = 0; q < words; ++q) {
@@ -788,7 +892,8 @@ __device__ __forceinline__ void ep_stage(const void* __restrict__ splats, const 
         const Splat v = load_splat<DT>(splats, id);
         S.a[e] = make_float4(v.x, v.y, v.ca, v.cb);
         S.b[e] = make_float4(v.cc, v.op, v.depth, log2_opacity(v.op));
-        S.box[e] = pixel_box(v, alpha_min);
+        float t2;
+        S.box[e] = pixel_box(v, alpha_min, t2);
         S.c[e] = make_float4(v.r, v.g, v.b, 0.f);
         if (sid) sid[e] = id;
     }

@@ -179,10 +179,11 @@ def arc_keyframes(n_kf=8, W=1200, H=680, f=600.0, seed=3000, arc=1.0, centre=(0.
 # --------------------------------------------------------------------------
 
 def splats(n, W, H, seed, tie_frac=0.05, cull_frac=0.03, sigma_px=(0.6, 12.0), depth=(0.5, 10.0),
-           opaque_frac=0.1):
+           opaque_frac=0.1, aniso=(0.25, 1.0)):
     """Projected 2D Gaussians drawn directly (for stage-isolated binning and
     compositing tests): 2D means uniform over the image plus a 20 px margin,
-    random anisotropic 2D covariances given by their inverse (the conic),
+    random anisotropic 2D covariances given by their inverse (the conic;
+    minor / major sigma U(aniso)),
     radius ceil(3 sigma_max) as an input, opacity U(0.05, 0.99) with
     `opaque_frac` at 0.995 (so the alpha clamp is exercised), RGB U[0,1],
     depth U(depth) with `tie_frac` copying another Gaussian's depth exactly
@@ -191,7 +192,7 @@ def splats(n, W, H, seed, tie_frac=0.05, cull_frac=0.03, sigma_px=(0.6, 12.0), d
     u = g.uniform(-20, W + 20, n)
     v = g.uniform(-20, H + 20, n)
     s1 = np.exp(g.uniform(math.log(sigma_px[0]), math.log(sigma_px[1]), n))
-    s2 = s1 * g.uniform(0.25, 1.0, n)
+    s2 = s1 * g.uniform(aniso[0], aniso[1], n)
     th = g.uniform(0, math.pi, n)
     c, s = np.cos(th), np.sin(th)
     i1, i2 = 1.0 / s1 ** 2, 1.0 / s2 ** 2

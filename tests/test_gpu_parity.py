@@ -250,6 +250,26 @@ def test_render_fwd_matches_oracle(G, O, n, W, H, seed, sx, sy):
     assert np.array_equal(img["n_blended"][good].astype(np.int64), ref["nfrag"][good])
 
 
+@pytest.mark.parametrize("W,H,seed,sx,sy", [(333, 197, 21, 1, 1), (320, 240, 22, 1, 2), (333, 197, 23, 2, 1)])
+def test_render_fwd_needles_match_oracle(G, O, W, H, seed, sx, sy):
+    """Thin rotated Gaussians (minor / major sigma 0.03-0.1, major sigma up
+    to 40 px) stress the pixel-parallel forward's per-warp block bits, which
+    skip an entry for a warp block its alpha >= alpha_min ellipse misses: no
+    fragment may be lost (blend counts and last positions exact)."""
+    n = 20000
+    cam = S.camera(W, H, 100.0, sx=sx, sy=sy)
+    s = S.splats(n, W, H, seed=seed, sigma_px=(1.5, 40.0), aniso=(0.03, 0.1))
+    rec = pack_splats(s)
+    img, _, _ = render_gpu(G, cam, rec, n)
+    ref = O.render_fwd(s, cam)
+    good = ref["margin"] == 0
+    assert good.mean() > 0.95
+    assert np.array_equal(img["last_idx"][good].astype(np.int64), ref["last"][good])
+    assert np.array_equal(img["n_blended"][good].astype(np.int64), ref["nfrag"][good])
+    d = np.abs(img["rgb"] - ref["rgb"]).max(0)
+    assert d[good].max() <= IMG_TOL
+
+
 def test_stride_render_is_subsampled_full_render(G):
     """A strided render samples the full-resolution image (Sec. 4.2).  The
     pixel-parallel (stride 1 in one axis) and entry-parallel (both >= 2)
