@@ -255,10 +255,10 @@ gs_status gs_project_bin_sort(const gs_config* cfg, const gs_camera* cam, const 
  * fragments blended into the pixel).  vals, tile_ranges and tile_order (may be
  * NULL: tiles in id order) come from gs_bin_sort with the same camera.
  * blend_masks (may be NULL): device uint32 array of gs_blend_mask_words
- * words that receives, for frames rendered pixel-parallel (a stride of 1),
- * which list entries each warp of each tile blended; gs_render_bwd given the
- * same array skips the entries no pixel of a warp blended (the same result,
- * fewer visits).  Frames with both strides >= 2 leave it untouched. */
+ * words that receives, per pixel and run of 32 list entries, which entries
+ * the forward blended into the pixel; gs_render_bwd given the same array
+ * visits only those (the same result, fewer visits) and takes the forward's
+ * decisions from it instead of re-deriving them. */
 gs_status gs_render_fwd(const gs_config* cfg, const gs_camera* cam, int rec_dtype,
                         const void* splats, int64_t n, const uint32_t* vals,
                         const uint32_t* tile_ranges, const uint32_t* tile_order, float* rgb,
@@ -305,8 +305,10 @@ gs_status gs_render_fwd_loss(const gs_config* cfg, const gs_camera* cam, int rec
  * (Eq. 3 differentiated; the printed Eq. 4 omits T_k and the normalisation);
  * then through alpha = opacity exp(power) to opacity, conic and 2D mean
  * unless alpha was clamped.  Per-fragment gradients are summed per Gaussian
- * inside each warp, then per tile in shared memory, then added to grad2d
- * with one global atomic per (Gaussian, tile, field).
+ * inside each warp; with blend_masks (pixel-parallel frames) each warp's
+ * sums go to grad2d with one global atomic per (Gaussian, warp, field),
+ * otherwise they are summed per tile in shared memory first (one atomic per
+ * (Gaussian, tile, field)).
  * grad2d [n][12] float (GS_GRAD2D_STRIDE layout): zeroed by this call.
  * mode GS_TRACK skips dL/dopacity and dL/drgb (not needed for the pose).
  * If grads, pose_grad6 or score_terms is non-NULL, gs_project_bwd runs as

@@ -401,13 +401,15 @@ struct FwdOut {
     uint32_t* bmask;    // NULL: no blend masks
 };
 
-// Blend masks: for each tile, each of its warps (at most 8) and each run of
-// 32 list entries, the entries one of the warp's pixels blended in the
-// forward (bit e of word q: entry 32 q + e of the tile's list).  Tile t with
-// list [s, s + len) owns 8 ceil(len / 32) words from word 8 (floor(s / 32) +
-// t) on, warp w's ceil(len / 32) words consecutive; tiles never overlap.
+// Blend masks: for each pixel of a tile and each run of 32 list entries,
+// the entries the forward blended into that pixel (bit e of run r: entry
+// 32 r + e of the tile's list).  A pixel-parallel tile (TT <= 256 threads,
+// pixel = thread lt of the group) with list [s, s + len) keeps run r of
+// pixel lt at word 256 (floor(s / 32) + t) + r TT + lt: run-major, so a
+// warp's 32 pixels read one 128-byte line; the TT ceil(len / 32) words of a
+// tile end before the next tile's first word.
 __host__ __device__ inline size_t blend_mask_base(int tile, uint32_t start) {
-    return (size_t)8 * ((size_t)(start >> 5) + (size_t)tile);
+    return (size_t)256 * ((size_t)(start >> 5) + (size_t)tile);
 }
 
 // Entry-parallel tiles (at most 64 sampled pixels) keep one run per pixel
@@ -483,9 +485,8 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
     uint32_t last = 0, nb = 0;
     bool done = !m.inside;
     const int words = G.B / 32;
-    const int lane = threadIdx.x & 31;
-    // the warp's blend-mask words (word w at O.bmask[bm_off + w])
-    const uint32_t bm_off = (uint32_t)blend_mask_base(tile, start) + (uint32_t)(G.lt >> 5) * ((end - start + 31) >> 5);
+    // this pixel's blend-mask words (run r at bm_pix[r TT])
+    uint32_t* bm_pix = O.bmask ? O.bmask + blend_mask_base(tile, start) + G.lt : nullptr;
     for (uint32_t b = start; b < end; b += G.B) {
         // from the second batch on: a barrier (the previous batch's records
         // are no longer read) that also ends the tile once every pixel stopped
@@ -493,14 +494,12 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
         const int n_in = (int)min((uint32_t)G.B, end - b);
         stage_batch<DT, KST, true>(splats, vals + b, n_in, G.lt, G.TT, cfg.alpha_min, sp, nullptr, &tb);
         group_sync(G);
-        // lane q clears word q of the batch, then stores it once processed
-        const uint32_t bm_w = bm_off + ((b - start) >> 5);
-        if (O.bmask && lane < ((n_in + 31) >> 5)) O.bmask[bm_w + lane] = 0u;
         if (!__all_sync(0xffffffffu, done)) {
             const unsigned mword = warp_masks_bits(sp, n_in, words, G.lt >> 5);
             const uint32_t base = b - start;
+            const int wq = (n_in + 31) >> 5;
 #pragma unroll 1
-            for (int q = 0; q < words; ++q) {
+            for (int q = 0; q < wq; ++q) {
                 unsigned mq = __shfl_sync(0xffffffffu, mword, q);
                 unsigned bq = 0u;  // entries of word q this pixel blended
                 while (mq) {
@@ -544,10 +543,9 @@ __device__ __forceinline__ void fwd_pp(const gs_config& cfg, const Grid& g, cons
                 // the count and the last position follow from the word's blended bits
                 nb += __popc(bq);
                 if (bq != 0u) last = base + (uint32_t)(q * 32 + 32 - __clz(bq));
-                if (O.bmask) {  // (words past the batch's entries stay clear)
-                    bq = __reduce_or_sync(0xffffffffu, bq);
-                    if (lane == q && bq != 0u) O.bmask[bm_w + q] = bq;
-                }
+                // every run up to the one where the warp stops is written (a
+                // run past every pixel's last position is never read)
+                if (bm_pix) bm_pix[(size_t)((base >> 5) + q) * G.TT] = bq;
                 if (__all_sync(0xffffffffu, done)) break;
             }
         }
@@ -631,45 +629,129 @@ __device__ __forceinline__ float field_scale(int f) { return f < 2 ? -2.f : (f =
 
 // Per-fragment quantities of the backward that do not depend on the
 // running state: offsets, Gaussian falloff G, unclamped and clamped alpha,
-// and whether the fragment was blended (inside the box, exponent <= 0,
-// alpha >= alpha_min, before the pixel's last blended position).
+// and whether the fragment was blended.
 struct FragGeo {
     float dx, dy, a, b, q, raw, alpha, dep;  // offset, Q d, d^T Q d, alphas, depth
     bool contrib;
 };
 
-__device__ __forceinline__ FragGeo frag_geo(const StagedSplat& s, const PixelMap& m, float pxc, float pyc,
-                                            const gs_config& cfg, bool before_last) {
+// The geometry of a staged entry at the pixel, with the forward's arithmetic
+// (so the same alpha); `blended` says whether the forward blended it.
+__device__ __forceinline__ FragGeo frag_geo_at(const StagedSplat& s, float pxc, float pyc, const gs_config& cfg,
+                                               bool blended) {
     FragGeo f;
-    const int4 box = s.box;
     const float4 A = s.a;
     const float4 Bv = s.b;
-    const float cc = Bv.x, lop = Bv.w;
     f.dep = Bv.z;
     f.dx = pxc - A.x;
     f.dy = pyc - A.y;
-    const Quad Qd = quad_form(A.z, A.w, cc, f.dx, f.dy);
+    const Quad Qd = quad_form(A.z, A.w, Bv.x, f.dx, f.dy);
     f.a = Qd.a;
     f.b = Qd.b;
     f.q = Qd.q;
-    f.raw = raw_alpha(Qd.q, lop);
+    f.raw = raw_alpha(Qd.q, Bv.w);
     f.alpha = fminf(cfg.alpha_max, f.raw);
-    f.contrib = before_last && (unsigned)(m.px - box.x) <= (unsigned)box.y &&
-                (unsigned)(m.py - box.z) <= (unsigned)box.w &&
-                !(Qd.q < 0.f) && !(f.alpha < cfg.alpha_min);
+    f.contrib = blended;
     return f;
 }
 
-// Backward compositing of group G's tile, pixel-parallel (smem: the CTA's
-// staging, id and accumulator buffers for gpc groups of G.B entries;
-// s_max_all: one word per warp).
+// Without blend masks the decision is re-derived: inside the box, exponent
+// <= 0, alpha >= alpha_min, before the pixel's last blended position.
+__device__ __forceinline__ FragGeo frag_geo(const StagedSplat& s, const PixelMap& m, float pxc, float pyc,
+                                            const gs_config& cfg, bool before_last) {
+    FragGeo f = frag_geo_at(s, pxc, pyc, cfg, false);
+    const int4 box = s.box;
+    f.contrib = before_last && (unsigned)(m.px - box.x) <= (unsigned)box.y &&
+                (unsigned)(m.py - box.z) <= (unsigned)box.w && !(f.q < 0.f) && !(f.alpha < cfg.alpha_min);
+    return f;
+}
+
+// A pixel's running state in the backward walk: the transmittance in front
+// of the current entry, s = A . g (the normalised suffix sum A of colour and
+// depth behind it -- the background entering with weight T_final -- dotted
+// with the image gradient g) and g itself.
+struct BackState {
+    float T, sg, gC0, gC1, gC2, gD;
+};
+
+// Loads a pixel's backward inputs (t_final, image gradients); pixels outside
+// the image keep T = 1 and zero gradients.  Returns its last_idx (0 outside).
+__device__ __forceinline__ uint32_t back_start(const gs_config& cfg, const Grid& g, const PixelMap& m,
+                                               const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
+                                               const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
+                                               BackState& S) {
+    S.T = 1.f;
+    S.gC0 = S.gC1 = S.gC2 = S.gD = 0.f;
+    uint32_t last = 0;
+    if (m.inside) {
+        const size_t P = (size_t)g.Ws * g.Hs;
+        const size_t pix = (size_t)m.j * g.Ws + m.i;
+        S.T = t_final[pix];
+        last = last_idx[pix];
+        S.gC0 = d_rgb[pix];
+        S.gC1 = d_rgb[P + pix];
+        S.gC2 = d_rgb[2 * P + pix];
+        S.gD = d_depth[pix];
+    }
+    S.sg = cfg.bg[0] * S.gC0 + cfg.bg[1] * S.gC1 + cfg.bg[2] * S.gC2;
+    return last;
+}
+
+// One fragment, back to front: T_k recovered by division (Eq. 5).  With
+// w = T_k alpha_k and c_k . g (colour and depth dotted with the image
+// gradient),
+//   dL/dalpha_k = T_k (c_k . g - s_k),  s_k = A_k . g,
+//   s_{k-1} = s_k + alpha_k (c_k . g - s_k),
+// and alpha dL/dalpha = w (c . g - s) is the exponent's gradient.  Writes the
+// fragment's merged fields f[0, Fields<MODE>::N).  Branch-free: every lane
+// evaluates the recursion (all values are finite: 1 - alpha >= 1 -
+// alpha_max); a lane whose pixel did not blend the entry keeps its state and
+// contributes zeros.
+template <int MODE>
+__device__ __forceinline__ void back_frag(BackState& S, const FragGeo& fg, const float4& Cc, const gs_config& cfg,
+                                          float* f) {
+    const float alpha = fg.alpha;
+    // fast division (at most 2 ulp for these operands: 1 - alpha in
+    // [0.01, 1], T in [t_eps, 1]); over the few hundred entries a pixel
+    // recovers the relative drift stays near 1e-5
+    S.T = fg.contrib ? __fdividef(S.T, 1.f - alpha) : S.T;
+    const float w = fg.contrib ? alpha * S.T : 0.f;
+    const float cg = __fmaf_rn(fg.dep, S.gD, __fmaf_rn(Cc.z, S.gC2, __fmaf_rn(Cc.y, S.gC1, Cc.x * S.gC0)));
+    const float dif = cg - S.sg;
+    S.sg = fg.contrib ? __fmaf_rn(alpha, dif, S.sg) : S.sg;
+    // the clamp passes no gradient to opacity or shape
+    const bool clamped = fg.raw > cfg.alpha_max;
+    const float h = clamped ? 0.f : (-0.5f * w) * dif;  // -dL/d(exponent) / 2
+    const float u = h * fg.dx, v = h * fg.dy;
+    f[0] = fg.a * h;
+    f[1] = fg.b * h;
+    f[2] = u * fg.dx;
+    f[3] = u * fg.dy;
+    f[4] = v * fg.dy;
+    if (MODE == GS_MAP) {
+        // dalpha/dopacity = e^(-q/2)
+        f[5] = (fg.contrib && !clamped) ? exp2_sfu(__fmul_rn(fg.q, R_NEG_HALF_LOG2E)) * (S.T * dif) : 0.f;
+        f[6] = w * S.gD;
+        f[7] = w * S.gC0;
+        f[8] = w * S.gC1;
+        f[9] = w * S.gC2;
+    } else {
+        f[5] = w * S.gD;
+    }
+}
+
+// Backward compositing of group G's tile, pixel-parallel, without blend
+// masks (smem: the CTA's staging, id and accumulator buffers for gpc groups
+// of G.B entries; s_max_all: one word per warp).  Each warp visits the
+// staged entries whose pixel box meets its block, up to the furthest last
+// position of its pixels.
 template <int DT, int MODE, int KST>
 __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
                                        const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                                        const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
-                                       float* __restrict__ grad2d, const uint32_t* __restrict__ bmask,
-                                       const Group& G, unsigned char* smem, uint32_t* s_max_all) {
+                                       float* __restrict__ grad2d, const Group& G, unsigned char* smem,
+                                       uint32_t* s_max_all) {
     constexpr int NF = Fields<MODE>::N;
     constexpr int BSTEP = 2;  // entries per backward step, merged together
     const int gpc = R_THREADS / G.TT;
@@ -688,25 +770,10 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
     // the merged field this lane adds (entry owner / NF of a step, field
     // owner % NF), or -1
     const int owner = merge_owner<BSTEP * NF>();
-    float T = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f;
-    uint32_t last = 0;
-    if (m.inside) {
-        const size_t P = (size_t)g.Ws * g.Hs;
-        const size_t pix = (size_t)m.j * g.Ws + m.i;
-        T = t_final[pix];
-        last = last_idx[pix];
-        gC0 = d_rgb[pix];
-        gC1 = d_rgb[P + pix];
-        gC2 = d_rgb[2 * P + pix];
-        gD = d_depth[pix];
-    }
+    BackState S;
+    uint32_t last = back_start(cfg, g, m, t_final, last_idx, d_rgb, d_depth, S);
     // a last_idx beyond the tile's list (inconsistent inputs) is clamped
     last = min(last, end - start);
-    // the normalised suffix sums A (colour and depth behind the current
-    // entry divided by the transmittance in front of it; the background
-    // enters with weight T_final) only ever appear dotted with the pixel's
-    // image gradient: s = A . g
-    float sg = cfg.bg[0] * gC0 + cfg.bg[1] * gC1 + cfg.bg[2] * gC2;
     uint32_t wlast = last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
@@ -715,8 +782,6 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
     uint32_t s_max = 0;
     for (int w = 0; w < (G.TT >> 5); ++w) s_max = max(s_max, s_wl[w]);
     const int words = G.B / 32;
-    const uint32_t* bm_in =
-        bmask ? bmask + blend_mask_base(tile, start) + (size_t)(G.lt >> 5) * ((end - start + 31) >> 5) : nullptr;
     // batches [start + k B, start + (k + 1) B) from the last one holding a
     // blended entry back to the first (whole mask words for every batch)
     for (int k = (int)((s_max + G.B - 1) / G.B) - 1; k >= 0; --k) {
@@ -726,58 +791,9 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
         stage_batch<DT, KST>(splats, vals + lo, n_in, G.lt, G.TT, cfg.alpha_min, sp, sid);
         for (int q = G.lt; q < G.B * NF; q += G.TT) (&acc[0][0])[q] = 0.f;
         group_sync(G);
-        // entries at or beyond the warp's furthest blended position are
-        // skipped; with the forward's blend masks, so is every entry none of
-        // the warp's pixels blended
+        // entries at or beyond the warp's furthest blended position are skipped
         const int wlimit = (int)min((uint32_t)n_in, wlast > base_pos ? wlast - base_pos : 0u);
-        unsigned mword;
-        if (bm_in) {
-            const int q = lane;
-            mword = q * 32 < wlimit ? __ldg(bm_in + (base_pos >> 5) + q) : 0u;
-            if (q * 32 < wlimit && wlimit - q * 32 < 32) mword &= (1u << (wlimit - q * 32)) - 1u;
-        } else {
-            mword = warp_masks(sp, wlimit, words, m);
-        }
-        // back to front over the fragments before `last`; T_k recovered by
-        // division (Eq. 5).  With w = T_k alpha_k and c_k . g (colour and
-        // depth dotted with the image gradient),
-        //   dL/dalpha_k = T_k (c_k . g - s_k),  s_k = A_k . g,
-        //   s_{k-1} = s_k + alpha_k (c_k . g - s_k),
-        // and alpha dL/dalpha = w (c . g - s) is the exponent's gradient.
-        auto back = [&](int e, const FragGeo& fg, float* f) {
-            // branch-free: every lane evaluates the recursion (all values are
-            // finite: 1 - alpha >= 1 - alpha_max); a lane whose pixel did not
-            // blend the entry keeps its state and contributes zeros
-            const float alpha = fg.alpha;
-            // fast division (at most 2 ulp for these operands: 1 - alpha in
-            // [0.01, 1], T in [t_eps, 1]); over the few hundred entries a
-            // pixel recovers the relative drift stays near 1e-5
-            T = fg.contrib ? __fdividef(T, 1.f - alpha) : T;
-            const float w = fg.contrib ? alpha * T : 0.f;
-            const float4 Cc = sp[e].c;
-            const float cg = __fmaf_rn(fg.dep, gD, __fmaf_rn(Cc.z, gC2, __fmaf_rn(Cc.y, gC1, Cc.x * gC0)));
-            const float dif = cg - sg;
-            sg = fg.contrib ? __fmaf_rn(alpha, dif, sg) : sg;
-            // the clamp passes no gradient to opacity or shape
-            const bool clamped = fg.raw > cfg.alpha_max;
-            const float h = clamped ? 0.f : (-0.5f * w) * dif;  // -dL/d(exponent) / 2
-            const float u = h * fg.dx, v = h * fg.dy;
-            f[0] = fg.a * h;
-            f[1] = fg.b * h;
-            f[2] = u * fg.dx;
-            f[3] = u * fg.dy;
-            f[4] = v * fg.dy;
-            if (MODE == GS_MAP) {
-                // dalpha/dopacity = e^(-q/2)
-                f[5] = (fg.contrib && !clamped) ? exp2_sfu(__fmul_rn(fg.q, R_NEG_HALF_LOG2E)) * (T * dif) : 0.f;
-                f[6] = w * gD;
-                f[7] = w * gC0;
-                f[8] = w * gC1;
-                f[9] = w * gC2;
-            } else {
-                f[5] = w * gD;
-            }
-        };
+        const unsigned mword = warp_masks(sp, wlimit, words, m);
 #pragma unroll 1
         for (int q = words - 1; q >= 0; --q) {
             unsigned mq = __shfl_sync(0xffffffffu, mword, q);
@@ -799,13 +815,12 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
                 }
                 float f[BSTEP * NF];
 #pragma unroll
-                for (int u = 0; u < BSTEP; ++u) back(eu[u] >= 0 ? eu[u] : 0, gu[u], f + u * NF);
-                // the step's fields merged at once (with the blend masks
-                // every visited entry has a contributing pixel in the warp)
+                for (int u = 0; u < BSTEP; ++u) back_frag<MODE>(S, gu[u], sp[eu[u] >= 0 ? eu[u] : 0].c, cfg, f + u * NF);
+                // the step's fields merged at once
                 bool any = false;
 #pragma unroll
                 for (int u = 0; u < BSTEP; ++u) any = any || gu[u].contrib;
-                if (bm_in || __any_sync(0xffffffffu, any)) {
+                if (__any_sync(0xffffffffu, any)) {
                     const float v = warp_merge<BSTEP * NF>(f);
                     if (owner >= 0) {
                         const int u = owner / NF;
@@ -836,13 +851,117 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? (MODE == GS_TRACK ? 4 : 
                  const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
                  const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                  const float* __restrict__ d_rgb, const float* __restrict__ d_depth, float* __restrict__ grad2d,
-                 const uint32_t* __restrict__ bmask, int B) {
+                 int B) {
     extern __shared__ __align__(16) unsigned char r_smem[];
     __shared__ uint32_t s_max_all[R_THREADS / 32];
     const Group G = make_group(g, order, B, blockIdx.x);
     if (G.tile < 0) return;
-    bwd_pp<DT, MODE, KST>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, bmask, G,
-                          r_smem, s_max_all);
+    bwd_pp<DT, MODE, KST>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, G, r_smem,
+                          s_max_all);
+}
+
+// Backward compositing of one warp's block of a pixel-parallel tile from the
+// forward's per-pixel blend masks (warp w of the tile's TT / 32).  The warp
+// walks its runs of 32 list entries from the last one holding an entry one
+// of its pixels blended back to the first.  Per run it stages only those
+// entries, one lane each (the record alone: no box, which the masks make
+// unnecessary), the last first, then evaluates them back to front, BSTEP at
+// a time; a lane's fragment counts when its own mask bit says the forward
+// blended it, so both passes take identical decisions by construction, and
+// the alpha it recomputes is the forward's (same staged values, same
+// arithmetic).  The merged fields go straight to grad2d, one atomic per
+// (entry, field, warp): the warps of a tile share nothing and run as
+// one-warp CTAs that the hardware schedules as they free up, heavy tiles
+// first.
+template <int DT, int MODE>
+__device__ __forceinline__ void bwd_pw(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
+                                       const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
+                                       const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
+                                       const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
+                                       float* __restrict__ grad2d, const uint32_t* __restrict__ bmask, int tile,
+                                       int w, StagedSplat* sp, uint32_t* sid) {
+    constexpr int NF = Fields<MODE>::N;
+    constexpr int BSTEP = 2;
+    const int TT = tile_threads(g);
+    const int lane = threadIdx.x & 31;
+    const int lt = w * 32 + lane;
+    const PixelMap m = map_pixel(g, tile, lt);
+    const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
+    BackState S;
+    uint32_t last = back_start(cfg, g, m, t_final, last_idx, d_rgb, d_depth, S);
+    last = min(last, end - start);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+    if (last == 0u) return;  // (warp-uniform) no pixel of the block blended anything
+    const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
+    const int owner = merge_owner<BSTEP * NF>();
+    const uint32_t* bm = bmask + blend_mask_base(tile, start) + lt;
+#pragma unroll 1
+    for (int r = (int)((last + 31u) >> 5) - 1; r >= 0; --r) {
+        // (bits past the list's end are ignored: masks from another forward
+        // cannot send a load outside the tile's list)
+        const uint32_t len_r = min(32u, (end - start) - (uint32_t)r * 32u);
+        const uint32_t mine = __ldg(bm + (size_t)r * TT) & (len_r == 32u ? ~0u : (1u << len_r) - 1u);
+        const unsigned mw = __reduce_or_sync(0xffffffffu, mine);
+        if (mw == 0u) continue;
+        // stage the run's blended entries: entry 32 r + lane into slot (its
+        // rank from the top among the run's set bits)
+        if ((mw >> lane) & 1u) {
+            const int slot = __popc(mw & ~((2u << lane) - 1u));
+            const uint32_t id = __ldg(vals + start + (uint32_t)r * 32u + (uint32_t)lane);
+            const Splat v = load_splat<DT>(splats, id);
+            sp[slot].a = make_float4(v.x, v.y, v.ca, v.cb);
+            sp[slot].b = make_float4(v.cc, v.op, v.depth, log2_opacity(v.op));
+            sp[slot].c = make_float4(v.r, v.g, v.b, 0.f);
+            sid[slot] = id;
+        }
+        __syncwarp();
+        unsigned mq = mw;
+        for (int k = 0; mq; k += BSTEP) {
+            int bu[BSTEP];  // bit of slot k + u, or -1
+#pragma unroll
+            for (int u = 0; u < BSTEP; ++u) {
+                bu[u] = mq ? 31 - __clz(mq) : -1;
+                if (bu[u] >= 0) mq &= ~(1u << bu[u]);
+            }
+            FragGeo gu[BSTEP];
+#pragma unroll
+            for (int u = 0; u < BSTEP; ++u)
+                gu[u] = frag_geo_at(sp[bu[u] >= 0 ? k + u : k], pxc, pyc, cfg,
+                                    bu[u] >= 0 && ((mine >> (bu[u] & 31)) & 1u));
+            float f[BSTEP * NF];
+#pragma unroll
+            for (int u = 0; u < BSTEP; ++u) back_frag<MODE>(S, gu[u], sp[bu[u] >= 0 ? k + u : k].c, cfg, f + u * NF);
+            const float v = warp_merge<BSTEP * NF>(f);
+            if (owner >= 0) {
+                const int u = owner / NF, fl = owner - u * NF;
+                bool valid = bu[0] >= 0;
+#pragma unroll
+                for (int x = 1; x < BSTEP; ++x) valid = u == x ? bu[x] >= 0 : valid;
+                if (valid && v != 0.f)
+                    atomicAdd(grad2d + (size_t)sid[k + u] * GS_GRAD2D_STRIDE + field_col<MODE>(fl), v * field_scale(fl));
+            }
+        }
+        __syncwarp();  // the next run reuses the slots
+    }
+}
+
+// One-warp CTAs: 32 per SM at 64 registers for the pose-only fields; 24 when
+// mapping (the 20-value merge).
+template <int DT, int MODE>
+__global__ void __launch_bounds__(32, MODE == GS_TRACK ? 32 : 24)
+    k_render_bwd_pw(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
+                    const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
+                    const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
+                    const float* __restrict__ d_rgb, const float* __restrict__ d_depth, float* __restrict__ grad2d,
+                    const uint32_t* __restrict__ bmask) {
+    __shared__ __align__(16) StagedSplat sp[32];
+    __shared__ uint32_t sid[32];
+    const int wpt = tile_threads(g) >> 5;
+    const int t = (int)blockIdx.x / wpt, w = (int)blockIdx.x % wpt;
+    const int tile = order ? (int)__ldg(order + t) : t;
+    bwd_pw<DT, MODE>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, bmask, tile, w, sp,
+                     sid);
 }
 
 // ---------------------------------------------------------------------------
@@ -1386,7 +1505,22 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
     const Group G = make_group(J.g, J.order, J.B, (int)blockIdx.x - W.start[j]);
     if (G.tile < 0) return;
     bwd_pp<GS_F32, GS_TRACK, KST>(cfg, J.g, J.splats, J.vals, J.ranges, J.t_final, J.last_idx, J.d_rgb, J.d_depth,
-                                  J.grad2d, J.bmask, G, r_smem, s_max_all);
+                                  J.grad2d, G, r_smem, s_max_all);
+}
+
+// Pixel-parallel jobs with blend masks: one-warp CTAs over (job, tile, warp).
+__global__ void __launch_bounds__(32, 32) k_wave_render_bwd_pw(const gs_config cfg,
+                                                                const __grid_constant__ Wave<WaveBwdJob> W) {
+    __shared__ __align__(16) StagedSplat sp[32];
+    __shared__ uint32_t sid[32];
+    const int j = wave_find(W.start, W.n, (int)blockIdx.x);
+    const WaveBwdJob& J = W.job[j];
+    const int blk = (int)blockIdx.x - W.start[j];
+    const int wpt = tile_threads(J.g) >> 5;
+    const int t = blk / wpt, w = blk % wpt;
+    const int tile = J.order ? (int)__ldg(J.order + t) : t;
+    bwd_pw<GS_F32, GS_TRACK>(cfg, J.g, J.splats, J.vals, J.ranges, J.t_final, J.last_idx, J.d_rgb, J.d_depth,
+                             J.grad2d, J.bmask, tile, w, sp, sid);
 }
 
 template <int NW>
@@ -1494,6 +1628,12 @@ static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* spl
         }
         return check_launch("k_render_bwd_ep");
     }
+    if (bmask) {
+        const unsigned nw = (unsigned)ntiles * (unsigned)(tile_threads(g) >> 5);
+        k_render_bwd_pw<DT, MD><<<nw, 32, 0, st>>>(cfg, g, splats, vals, ranges, order, t_final, last_idx, d_rgb,
+                                                    d_depth, grad2d, bmask);
+        return check_launch("k_render_bwd_pw");
+    }
     const int gpc = R_THREADS / tile_threads(g);
     const unsigned nt = (unsigned)((ntiles + gpc - 1) / gpc);
     const int per_entry = (int)(sizeof(StagedSplat) + sizeof(uint32_t) + sizeof(float) * Fields<MD>::N);
@@ -1504,11 +1644,11 @@ static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* spl
     if (gpc == 1) {
         if ((s = smem_once((const void*)k_render_bwd<DT, MD, 1>, id, R_BWD_SMEM)) != GS_OK) return s;
         k_render_bwd<DT, MD, 1><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, t_final,
-                                                             last_idx, d_rgb, d_depth, grad2d, bmask, B);
+                                                             last_idx, d_rgb, d_depth, grad2d, B);
     } else {
         if ((s = smem_once((const void*)k_render_bwd<DT, MD, 4>, id + 1, R_BWD_SMEM)) != GS_OK) return s;
         k_render_bwd<DT, MD, 4><<<nt, R_THREADS, smem, st>>>(cfg, g, splats, vals, ranges, order, t_final,
-                                                             last_idx, d_rgb, d_depth, grad2d, bmask, B);
+                                                             last_idx, d_rgb, d_depth, grad2d, B);
     }
     return check_launch("k_render_bwd");
 }
@@ -1567,7 +1707,7 @@ extern "C" size_t gs_blend_mask_words(const gs_camera* cam, int64_t key_capacity
     const Grid g = make_grid(*cam);
     if (g.tw * g.th <= 64)  // entry-parallel tiles: a run per pixel
         return blend_mask_base_ep(g.TX * g.TY, 0) + (size_t)64 * ((size_t)(key_capacity >> 5) + 1);
-    return blend_mask_base(g.TX * g.TY, 0) + (size_t)8 * ((size_t)(key_capacity >> 5) + 1);
+    return blend_mask_base(g.TX * g.TY, 0) + (size_t)256 * ((size_t)(key_capacity >> 5) + 1);
 }
 
 extern "C" gs_status gs_loss_l1(const gs_config* cfg, const gs_camera* cam, const float* rgb, const float* depth,
@@ -1689,9 +1829,15 @@ gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cud
         }
         if ((s = check_launch("k_wave_render_fwd")) != GS_OK) return s;
     }
-    // backward compositing, pose-only fields
-    for (int form = 0; form < 4; ++form) {
-        if (!(present & (1 << form))) continue;
+    // backward compositing, pose-only fields; pixel-parallel jobs with blend
+    // masks (kind 4) go to the one-warp kernel
+    int kinds = 0;
+    for (int j = 0; j < n; ++j) {
+        const int form = render_form(make_grid(jobs[j].cam));
+        kinds |= 1 << (form < 2 && jobs[j].blend_masks ? 4 : form);
+    }
+    for (int kind = 0; kind < 5; ++kind) {
+        if (!(kinds & (1 << kind))) continue;
         Wave<WaveBwdJob> W;
         W.n = 0;
         int blocks = 0;
@@ -1700,32 +1846,35 @@ gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cud
         for (int j = 0; j < n; ++j) {
             const gs_track_job& t = jobs[j];
             const Grid g = make_grid(t.cam);
-            if (render_form(g) != form) continue;
+            const int form = render_form(g);
+            if ((form < 2 && t.blend_masks ? 4 : form) != kind) continue;
             const int ntiles = g.TX * g.TY;
-            const int gpc = form < 2 ? R_THREADS / tile_threads(g) : 1;
-            const int B = form < 2 ? group_batch(gpc, per_entry, R_BWD_SMEM) : 0;
+            const int gpc = kind < 2 ? R_THREADS / tile_threads(g) : 1;
+            const int B = kind < 2 ? group_batch(gpc, per_entry, R_BWD_SMEM) : 0;
             W.start[W.n] = blocks;
             W.job[W.n] = WaveBwdJob{g, t.splats, t.vals, t.tile_ranges, t.tile_order, t.t_final, t.last_idx, t.d_rgb,
                                     t.d_depth, t.grad2d, t.blend_masks, B};
             ++W.n;
-            blocks += (ntiles + gpc - 1) / gpc;
-            if (form < 2) smem = std::max(smem, (size_t)gpc * B * per_entry);
+            blocks += kind == 4 ? ntiles * (tile_threads(g) >> 5) : (ntiles + gpc - 1) / gpc;
+            if (kind < 2) smem = std::max(smem, (size_t)gpc * B * per_entry);
         }
         W.start[W.n] = blocks;
-        if (form == 0) {
+        if (kind == 0) {
             if ((s = smem_once((const void*)k_wave_render_bwd<1>, 42, R_BWD_SMEM)) != GS_OK) return s;
             k_wave_render_bwd<1><<<(unsigned)blocks, R_THREADS, smem, st>>>(cfg, W);
-        } else if (form == 1) {
+        } else if (kind == 1) {
             if ((s = smem_once((const void*)k_wave_render_bwd<4>, 43, R_BWD_SMEM)) != GS_OK) return s;
             k_wave_render_bwd<4><<<(unsigned)blocks, R_THREADS, smem, st>>>(cfg, W);
-        } else if (form == 2) {
+        } else if (kind == 2) {
             const int sm = (int)sizeof(EpBwdSmem<GS_TRACK, 8>);
             if ((s = smem_once((const void*)k_wave_render_bwd_ep<8>, 44, sm)) != GS_OK) return s;
             k_wave_render_bwd_ep<8><<<(unsigned)blocks, 8 * 32, sm, st>>>(cfg, W);
-        } else {
+        } else if (kind == 3) {
             const int sm = (int)sizeof(EpBwdSmem<GS_TRACK, 16>);
             if ((s = smem_once((const void*)k_wave_render_bwd_ep<16>, 45, sm)) != GS_OK) return s;
             k_wave_render_bwd_ep<16><<<(unsigned)blocks, 16 * 32, sm, st>>>(cfg, W);
+        } else {
+            k_wave_render_bwd_pw<<<(unsigned)blocks, 32, 0, st>>>(cfg, W);
         }
         if ((s = check_launch("k_wave_render_bwd")) != GS_OK) return s;
     }

@@ -108,10 +108,12 @@ class Session:
     def footprint_bytes(spec: SessionSpec, keys_per_gaussian=4.0):
         """Device bytes of a session: map + Adam (3 x 56 B/G), gradients
         (56 B/G), four rasterizer instances (records, 2D gradients, scores,
-        keys, sort scratch) and the frames' RGB-D targets."""
+        keys, sort scratch, blend masks: a word per pixel and run of 32 list
+        entries, 32 B per key of capacity plus 1 KB per tile) and the frames'
+        RGB-D targets."""
         n, P = spec.n, spec.W * spec.H
         cap = int(keys_per_gaussian * n * 1.5) + 4096
-        per_rast = n * (48 + 48 + 8) + cap * (8 + 4 + 8) + P * 40
+        per_rast = n * (48 + 48 + 8) + cap * (8 + 4 + 8 + 32) + P * 44
         return n * 56 * 4 + 4 * per_rast + spec.n_frames * P * 16
 
     # -- frame programs ----------------------------------------------------

@@ -120,15 +120,15 @@ def test_reduction_probe_rejects_bad_arguments_on_the_host(built_lib):
 
 
 def test_blend_mask_words_host_arithmetic(built_lib):
-    """8 words per 32 keys of capacity plus 8 per tile (and one spare run):
-    enough for every tile's per-warp runs of 32 list entries (64, one run
-    per pixel, for entry-parallel frames)."""
+    """256 words per 32 keys of capacity plus 256 per tile (and one spare
+    run): enough for every pixel's runs of 32 list entries in tiles of up to
+    256 pixels (64 per tile and run for entry-parallel frames)."""
     from paper_2510_06644_gb300 import gs
     cam = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 500, "fy": 500, "cx": 320,
                      "cy": 240, "W": 640, "H": 480})
     T = 40 * 30
     for cap in (0, 31, 32, 491244, 10 ** 7):
-        assert gs.gs_blend_mask_words(cam, cap) == 8 * T + 8 * (cap // 32 + 1)
+        assert gs.gs_blend_mask_words(cam, cap) == 256 * T + 256 * (cap // 32 + 1)
     # entry-parallel frames (both strides >= 2) keep a run per pixel: 64 per tile
     cam2 = gs.camera({"R": [1, 0, 0, 0, 1, 0, 0, 0, 1], "t": [0, 0, 0], "fx": 500, "fy": 500, "cx": 320,
                       "cy": 240, "W": 640, "H": 480, "sx": 2, "sy": 2})
