@@ -357,6 +357,7 @@ struct MergeLevel {
 
 template <int NF, typename T = float, typename Op = MergeFloat>
 __device__ __forceinline__ T warp_merge(T (&v)[NF]) {
+    static_assert(NF >= 1 && NF <= 32, "at most one merged value per lane");
     MergeLevel<NF, 16>::template run<T, NF, Op>(v, threadIdx.x & 31);
     return v[0];
 }

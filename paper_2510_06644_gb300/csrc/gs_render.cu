@@ -754,6 +754,7 @@ __device__ __forceinline__ void bwd_pp(const gs_config& cfg, const Grid& g, cons
                                        uint32_t* s_max_all) {
     constexpr int NF = Fields<MODE>::N;
     constexpr int BSTEP = 2;  // entries per backward step, merged together
+    static_assert(BSTEP * NF <= 32, "one lane per merged value");
     const int gpc = R_THREADS / G.TT;
     StagedSplat* sp_all = reinterpret_cast<StagedSplat*>(smem);
     uint32_t* sid_all = reinterpret_cast<uint32_t*>(sp_all + gpc * G.B);
@@ -881,7 +882,11 @@ __device__ __forceinline__ void bwd_pw(const gs_config& cfg, const Grid& g, cons
                                        float* __restrict__ grad2d, const uint32_t* __restrict__ bmask, int tile,
                                        int w, StagedSplat* sp, uint32_t* sid) {
     constexpr int NF = Fields<MODE>::N;
-    constexpr int BSTEP = 2;
+    // entries per step, merged together (three pose-only entries are 18
+    // merged values, measured 99.0 us against 103.1 with two, 101.0 with
+    // four; the merge gives each value its own lane, so at most 32)
+    constexpr int BSTEP = MODE == GS_TRACK ? 3 : 2;
+    static_assert(BSTEP * NF <= 32, "one lane per merged value");
     const int TT = tile_threads(g);
     const int lane = threadIdx.x & 31;
     const int lt = w * 32 + lane;
