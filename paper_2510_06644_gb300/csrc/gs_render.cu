@@ -861,34 +861,138 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? (MODE == GS_TRACK ? 4 : 
                           s_max_all);
 }
 
+// Two float32 values in one 64-bit register for the packed f32x2
+// instructions (add, sub, mul, fma with round-to-nearest: one instruction for
+// both halves, each half rounded exactly as the scalar operation).
+typedef unsigned long long x2f;
+
+__device__ __forceinline__ x2f x2_pack(float lo, float hi) {
+    x2f r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void x2_unpack(x2f v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ x2f x2_sub(x2f a, x2f b) {
+    x2f r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ x2f x2_mul(x2f a, x2f b) {
+    x2f r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ x2f x2_fma(x2f a, x2f b, x2f c) {  // a b + c
+    x2f r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// One warp's staged run for the masked backward: the blended entries'
+// fields, one array per field (slot k: the run's k-th blended entry from the
+// top), so that slots k and k + 1 load as one packed pair.
+struct __align__(16) RunStage {
+    float x[32], y[32], ca[32], cb[32], cc[32], lop[32], dep[32], cr[32], cg[32], cl[32];
+    uint32_t id[32];
+};
+
+__device__ __forceinline__ x2f x2_ld(const float* p) { return *reinterpret_cast<const x2f*>(p); }
+
+// Two consecutive fragments of a warp's run, back to front (slot k + 1 is
+// the earlier entry of the list, so slot k goes first): the geometry and the
+// gradient products of both in packed pairs, with the forward's arithmetic
+// in every half (the same alpha); the transmittance and suffix recursions
+// (Eq. 5) run fragment by fragment as in back_frag.  c0, c1: whether the
+// forward blended them.  Writes each fragment's merged fields to f0, f1.
+template <int MODE>
+__device__ __forceinline__ void back_pair(BackState& S, const RunStage& R, int k, bool c0, bool c1, x2f PXC, x2f PYC,
+                                          const gs_config& cfg, float* f0, float* f1) {
+    const x2f DX = x2_sub(PXC, x2_ld(R.x + k)), DY = x2_sub(PYC, x2_ld(R.y + k));
+    const x2f CA = x2_ld(R.ca + k), CB = x2_ld(R.cb + k), CC = x2_ld(R.cc + k);
+    const x2f A = x2_fma(CB, DY, x2_mul(CA, DX));  // Q d, as quad_form
+    const x2f B = x2_fma(CC, DY, x2_mul(CB, DX));
+    const x2f Q = x2_fma(DX, A, x2_mul(DY, B));
+    float e0, e1;
+    x2_unpack(x2_fma(Q, x2_pack(R_NEG_HALF_LOG2E, R_NEG_HALF_LOG2E), x2_ld(R.lop + k)), e0, e1);
+    const float raw0 = exp2_sfu(e0), raw1 = exp2_sfu(e1);
+    const float al0 = fminf(cfg.alpha_max, raw0), al1 = fminf(cfg.alpha_max, raw1);
+    float d0, d1, r0, r1, g0, g1, b0, b1;
+    x2_unpack(x2_ld(R.dep + k), d0, d1);
+    x2_unpack(x2_ld(R.cr + k), r0, r1);
+    x2_unpack(x2_ld(R.cg + k), g0, g1);
+    x2_unpack(x2_ld(R.cl + k), b0, b1);
+    const float cg0 = __fmaf_rn(d0, S.gD, __fmaf_rn(b0, S.gC2, __fmaf_rn(g0, S.gC1, r0 * S.gC0)));
+    const float cg1 = __fmaf_rn(d1, S.gD, __fmaf_rn(b1, S.gC2, __fmaf_rn(g1, S.gC1, r1 * S.gC0)));
+    S.T = c0 ? __fdividef(S.T, 1.f - al0) : S.T;
+    const float T0 = S.T;
+    const float w0 = c0 ? al0 * S.T : 0.f;
+    const float dif0 = cg0 - S.sg;
+    S.sg = c0 ? __fmaf_rn(al0, dif0, S.sg) : S.sg;
+    S.T = c1 ? __fdividef(S.T, 1.f - al1) : S.T;
+    const float T1 = S.T;
+    const float w1 = c1 ? al1 * S.T : 0.f;
+    const float dif1 = cg1 - S.sg;
+    S.sg = c1 ? __fmaf_rn(al1, dif1, S.sg) : S.sg;
+    // the clamp passes no gradient to opacity or shape
+    const bool cl0 = raw0 > cfg.alpha_max, cl1 = raw1 > cfg.alpha_max;
+    const x2f H = x2_mul(x2_pack(cl0 ? 0.f : -0.5f * w0, cl1 ? 0.f : -0.5f * w1), x2_pack(dif0, dif1));
+    const x2f U = x2_mul(H, DX), V = x2_mul(H, DY);
+    x2_unpack(x2_mul(A, H), f0[0], f1[0]);
+    x2_unpack(x2_mul(B, H), f0[1], f1[1]);
+    x2_unpack(x2_mul(U, DX), f0[2], f1[2]);
+    x2_unpack(x2_mul(U, DY), f0[3], f1[3]);
+    x2_unpack(x2_mul(V, DY), f0[4], f1[4]);
+    if (MODE == GS_MAP) {
+        float q0, q1;
+        x2_unpack(Q, q0, q1);
+        f0[5] = (c0 && !cl0) ? exp2_sfu(__fmul_rn(q0, R_NEG_HALF_LOG2E)) * (T0 * dif0) : 0.f;
+        f1[5] = (c1 && !cl1) ? exp2_sfu(__fmul_rn(q1, R_NEG_HALF_LOG2E)) * (T1 * dif1) : 0.f;
+        f0[6] = w0 * S.gD;
+        f0[7] = w0 * S.gC0;
+        f0[8] = w0 * S.gC1;
+        f0[9] = w0 * S.gC2;
+        f1[6] = w1 * S.gD;
+        f1[7] = w1 * S.gC0;
+        f1[8] = w1 * S.gC1;
+        f1[9] = w1 * S.gC2;
+    } else {
+        f0[5] = w0 * S.gD;
+        f1[5] = w1 * S.gD;
+    }
+}
+
 // Backward compositing of one warp's block of a pixel-parallel tile from the
 // forward's per-pixel blend masks (warp w of the tile's TT / 32).  The warp
 // walks its runs of 32 list entries from the last one holding an entry one
 // of its pixels blended back to the first.  Per run it stages only those
 // entries, one lane each (the record alone: no box, which the masks make
-// unnecessary), the last first, then evaluates them back to front, BSTEP at
-// a time; a lane's fragment counts when its own mask bit says the forward
-// blended it, so both passes take identical decisions by construction, and
-// the alpha it recomputes is the forward's (same staged values, same
-// arithmetic).  The merged fields go straight to grad2d, one atomic per
-// (entry, field, warp): the warps of a tile share nothing and run as
-// one-warp CTAs that the hardware schedules as they free up, heavy tiles
+// unnecessary), the last first, then evaluates them back to front, 2 NP at
+// a time in packed pairs; a lane's fragment counts when its own mask bit
+// says the forward blended it, so both passes take identical decisions by
+// construction, and the alpha it recomputes is the forward's (same staged
+// values, same arithmetic).  The merged fields go straight to grad2d, one
+// atomic per (entry, field, warp): the warps of a tile share nothing and run
+// as one-warp CTAs that the hardware schedules as they free up, heavy tiles
 // first.
-template <int DT, int MODE>
+template <int DT, int MODE, int NP>
 __device__ __forceinline__ void bwd_pw(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
                                        const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                                        const float* __restrict__ d_rgb, const float* __restrict__ d_depth,
                                        float* __restrict__ grad2d, const uint32_t* __restrict__ bmask, int tile,
-                                       int w, StagedSplat* sp, uint32_t* sid) {
+                                       int w, RunStage& R) {
     constexpr int NF = Fields<MODE>::N;
-    // entries per step, merged together (three pose-only entries are 18
-    // merged values, measured 99.0 us against 103.1 with two, 101.0 with
-    // four; the merge gives each value its own lane, so at most 32)
-    constexpr int BSTEP = MODE == GS_TRACK ? 3 : 2;
+    constexpr int BSTEP = 2 * NP;  // entries per step, merged together
     static_assert(BSTEP * NF <= 32, "one lane per merged value");
     const int TT = tile_threads(g);
     const int lane = threadIdx.x & 31;
+    // slots past a run's entries are read by the last step's unused halves:
+    // they must hold finite values (zeros, or an earlier run's records)
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(RunStage) / 4 / 32); ++q) (&R.x[0])[q * 32 + lane] = 0.f;
+    __syncwarp();
     const int lt = w * 32 + lane;
     const PixelMap m = map_pixel(g, tile, lt);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
@@ -899,60 +1003,87 @@ __device__ __forceinline__ void bwd_pw(const gs_config& cfg, const Grid& g, cons
     for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
     if (last == 0u) return;  // (warp-uniform) no pixel of the block blended anything
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
+    const x2f PXC = x2_pack(pxc, pxc), PYC = x2_pack(pyc, pyc);
     const int owner = merge_owner<BSTEP * NF>();
     const uint32_t* bm = bmask + blend_mask_base(tile, start) + lt;
+    const int r_top = (int)((last + 31u) >> 5) - 1;
+    // a run's list ids and mask word are loaded one run ahead (runs below
+    // the top one are full: their 32 positions lie inside the list)
+    uint32_t id_nx = r_top * 32 + lane < (int)(end - start)
+                         ? __ldg(vals + start + (uint32_t)r_top * 32u + (uint32_t)lane)
+                         : 0u;
+    uint32_t bm_nx = __ldg(bm + (size_t)r_top * TT);
 #pragma unroll 1
-    for (int r = (int)((last + 31u) >> 5) - 1; r >= 0; --r) {
+    for (int r = r_top; r >= 0; --r) {
         // (bits past the list's end are ignored: masks from another forward
         // cannot send a load outside the tile's list)
         const uint32_t len_r = min(32u, (end - start) - (uint32_t)r * 32u);
-        const uint32_t mine = __ldg(bm + (size_t)r * TT) & (len_r == 32u ? ~0u : (1u << len_r) - 1u);
+        const uint32_t mine = bm_nx & (len_r == 32u ? ~0u : (1u << len_r) - 1u);
+        const uint32_t id = id_nx;
+        if (r > 0) {
+            id_nx = __ldg(vals + start + (uint32_t)(r - 1) * 32u + (uint32_t)lane);
+            bm_nx = __ldg(bm + (size_t)(r - 1) * TT);
+        }
         const unsigned mw = __reduce_or_sync(0xffffffffu, mine);
         if (mw == 0u) continue;
         // stage the run's blended entries: entry 32 r + lane into slot (its
         // rank from the top among the run's set bits)
         if ((mw >> lane) & 1u) {
             const int slot = __popc(mw & ~((2u << lane) - 1u));
-            const uint32_t id = __ldg(vals + start + (uint32_t)r * 32u + (uint32_t)lane);
             const Splat v = load_splat<DT>(splats, id);
-            sp[slot].a = make_float4(v.x, v.y, v.ca, v.cb);
-            sp[slot].b = make_float4(v.cc, v.op, v.depth, log2_opacity(v.op));
-            sp[slot].c = make_float4(v.r, v.g, v.b, 0.f);
-            sid[slot] = id;
+            R.x[slot] = v.x;
+            R.y[slot] = v.y;
+            R.ca[slot] = v.ca;
+            R.cb[slot] = v.cb;
+            R.cc[slot] = v.cc;
+            R.lop[slot] = log2_opacity(v.op);
+            R.dep[slot] = v.depth;
+            R.cr[slot] = v.r;
+            R.cg[slot] = v.g;
+            R.cl[slot] = v.b;
+            R.id[slot] = id;
         }
         __syncwarp();
         unsigned mq = mw;
         for (int k = 0; mq; k += BSTEP) {
-            int bu[BSTEP];  // bit of slot k + u, or -1
+            bool cu[BSTEP], has[BSTEP];  // slot k + u: blended here, holds an entry
 #pragma unroll
             for (int u = 0; u < BSTEP; ++u) {
-                bu[u] = mq ? 31 - __clz(mq) : -1;
-                if (bu[u] >= 0) mq &= ~(1u << bu[u]);
+                const int bit = mq ? 31 - __clz(mq) : -1;
+                has[u] = bit >= 0;
+                cu[u] = has[u] && ((mine >> (bit & 31)) & 1u);
+                if (has[u]) mq &= ~(1u << bit);
             }
-            FragGeo gu[BSTEP];
-#pragma unroll
-            for (int u = 0; u < BSTEP; ++u)
-                gu[u] = frag_geo_at(sp[bu[u] >= 0 ? k + u : k], pxc, pyc, cfg,
-                                    bu[u] >= 0 && ((mine >> (bu[u] & 31)) & 1u));
             float f[BSTEP * NF];
 #pragma unroll
-            for (int u = 0; u < BSTEP; ++u) back_frag<MODE>(S, gu[u], sp[bu[u] >= 0 ? k + u : k].c, cfg, f + u * NF);
+            for (int p = 0; p < NP; ++p)
+                back_pair<MODE>(S, R, k + 2 * p, cu[2 * p], cu[2 * p + 1], PXC, PYC, cfg, f + 2 * p * NF,
+                                f + (2 * p + 1) * NF);
             const float v = warp_merge<BSTEP * NF>(f);
             if (owner >= 0) {
                 const int u = owner / NF, fl = owner - u * NF;
-                bool valid = bu[0] >= 0;
+                bool valid = has[0];
 #pragma unroll
-                for (int x = 1; x < BSTEP; ++x) valid = u == x ? bu[x] >= 0 : valid;
+                for (int x = 1; x < BSTEP; ++x) valid = u == x ? has[x] : valid;
                 if (valid && v != 0.f)
-                    atomicAdd(grad2d + (size_t)sid[k + u] * GS_GRAD2D_STRIDE + field_col<MODE>(fl), v * field_scale(fl));
+                    atomicAdd(grad2d + (size_t)R.id[k + u] * GS_GRAD2D_STRIDE + field_col<MODE>(fl),
+                              v * field_scale(fl));
             }
         }
         __syncwarp();  // the next run reuses the slots
     }
 }
 
+// Pairs per step of the masked backward: two for the pose-only fields (24
+// merged values; 98.0-98.7 us against 99.0 with one pair, and 99.0 for three
+// unpacked entries), one when mapping (20).
+template <int MODE>
+struct PwPairs {
+    static constexpr int N = MODE == GS_TRACK ? 2 : 1;
+};
+
 // One-warp CTAs: 32 per SM at 64 registers for the pose-only fields; 24 when
-// mapping (the 20-value merge).
+// mapping.
 template <int DT, int MODE>
 __global__ void __launch_bounds__(32, MODE == GS_TRACK ? 32 : 24)
     k_render_bwd_pw(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
@@ -960,13 +1091,12 @@ __global__ void __launch_bounds__(32, MODE == GS_TRACK ? 32 : 24)
                     const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
                     const float* __restrict__ d_rgb, const float* __restrict__ d_depth, float* __restrict__ grad2d,
                     const uint32_t* __restrict__ bmask) {
-    __shared__ __align__(16) StagedSplat sp[32];
-    __shared__ uint32_t sid[32];
+    __shared__ RunStage R;
     const int wpt = tile_threads(g) >> 5;
     const int t = (int)blockIdx.x / wpt, w = (int)blockIdx.x % wpt;
     const int tile = order ? (int)__ldg(order + t) : t;
-    bwd_pw<DT, MODE>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d, bmask, tile, w, sp,
-                     sid);
+    bwd_pw<DT, MODE, PwPairs<MODE>::N>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d,
+                                       bmask, tile, w, R);
 }
 
 // ---------------------------------------------------------------------------
@@ -1516,16 +1646,15 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
 // Pixel-parallel jobs with blend masks: one-warp CTAs over (job, tile, warp).
 __global__ void __launch_bounds__(32, 32) k_wave_render_bwd_pw(const gs_config cfg,
                                                                 const __grid_constant__ Wave<WaveBwdJob> W) {
-    __shared__ __align__(16) StagedSplat sp[32];
-    __shared__ uint32_t sid[32];
+    __shared__ RunStage R;
     const int j = wave_find(W.start, W.n, (int)blockIdx.x);
     const WaveBwdJob& J = W.job[j];
     const int blk = (int)blockIdx.x - W.start[j];
     const int wpt = tile_threads(J.g) >> 5;
     const int t = blk / wpt, w = blk % wpt;
     const int tile = J.order ? (int)__ldg(J.order + t) : t;
-    bwd_pw<GS_F32, GS_TRACK>(cfg, J.g, J.splats, J.vals, J.ranges, J.t_final, J.last_idx, J.d_rgb, J.d_depth,
-                             J.grad2d, J.bmask, tile, w, sp, sid);
+    bwd_pw<GS_F32, GS_TRACK, PwPairs<GS_TRACK>::N>(cfg, J.g, J.splats, J.vals, J.ranges, J.t_final, J.last_idx,
+                                                    J.d_rgb, J.d_depth, J.grad2d, J.bmask, tile, w, R);
 }
 
 template <int NW>
