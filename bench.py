@@ -454,6 +454,48 @@ def committed_counters(stage):
     return {}
 
 
+def mask_visits(bm, ranges, last_idx, TX, TY):
+    """(warp, entry) pairs the masked backward visits on a full-resolution
+    frame: per 8x4 warp block of each 16x16 tile, the entries blended into
+    one of its pixels (the OR of the pixels' blend-mask words), counted from
+    the per-pixel words of the runs up to the block's last blended entry
+    (word of run r of pixel lt in tile t: 256 (start / 32 + t) + 256 r + lt,
+    lt = 32 w + lane with warp w covering rows 4 (w / 2), columns 8 (w % 2)).
+    Device tensors in, an int out."""
+    import torch
+    dev = bm.device
+    T = TX * TY
+    H, W = last_idx.shape
+    lp = torch.zeros((TY * 16, TX * 16), dtype=torch.int64, device=dev)
+    lp[:H, :W] = last_idx.long()
+    # [TY, 4 block rows, 4 rows, TX, 2 block cols, 8 cols] -> per (tile, warp) the block's last
+    wl = lp.view(TY, 4, 4, TX, 2, 8).amax(dim=(2, 5)).permute(0, 2, 1, 3).reshape(T, 8)
+    start = ranges[:, 0].long()
+    ln = (ranges[:, 1] - ranges[:, 0]).long()
+    nr = (wl + 31) // 32                                   # runs read per (tile, warp)
+    R = int(nr.max().item()) if T else 0
+    if R == 0:
+        return 0
+    r = torch.arange(R, device=dev)
+    lane = torch.arange(32, device=dev)
+    base = 256 * (start // 32 + torch.arange(T, device=dev))  # [T]
+    w = torch.arange(8, device=dev)
+    idx = base[:, None, None, None] + 256 * r[None, None, :, None] + 32 * w[None, :, None, None] + lane
+    ok = (r[None, None, :] < nr[:, :, None])               # [T, 8, R]
+    words = torch.where(ok[..., None], bm.long()[idx.clamp(max=bm.numel() - 1)] & 0xFFFFFFFF, 0)
+    while words.shape[-1] > 1:                             # OR over the warp's 32 lanes
+        h = words.shape[-1] // 2
+        words = words[..., :h] | words[..., h:]
+    x = words[..., 0]
+    # bits past the list's end are not entries
+    rem = (ln[:, None, None] - 32 * r[None, None, :]).clamp(min=0, max=32)
+    x = x & ((1 << rem) - 1)
+    x = x - ((x >> 1) & 0x55555555)
+    x = (x & 0x33333333) + ((x >> 2) & 0x33333333)
+    x = (x + (x >> 4)) & 0x0F0F0F0F
+    return int(((x * 0x01010101) & 0xFFFFFFFF).__rshift__(24).sum().item())
+
+
 def fma_probe(gs, reps=10, iters=4096):
     """Measured FP32 FMA throughput (TFLOP/s) of gs_probe_fma_f32: 2048
     threads per SM, 8 independent FMA chains each; best of `reps` launches."""
@@ -836,11 +878,14 @@ def run_ours(args):
     hbm = hbm_fractions(stage_ms, n, n_keys, P, t_max / K)
 
     # ---- the backward's global reductions against the probe's measured rate
-    # (tracking: at most six per (Gaussian, tile) after the block merge) ----
+    # (tracking with blend masks: at most six per (warp, entry) visit) ----
     probe = red_probe(gs)
-    reds = 6 * n_keys
+    _, _, TXg, TYg = gs.grid(start_cam)
+    visits = mask_visits(bm, rast.ranges, rast.img["last_idx"], TXg, TYg)
+    reds = 6 * visits
     red_ach = reds / (stage_ms["render_bwd"] * 1e-3) / 1e9
-    atomics = {"kernel": "render_bwd", "red_per_launch_max": reds, "achieved_gops": red_ach, **probe,
+    atomics = {"kernel": "render_bwd", "warp_entry_visits": visits, "red_per_launch_max": reds,
+               "achieved_gops": red_ach, **probe,
                "frac": red_ach / probe["distinct_gops"],
                "l2_atomic_unit_active_pct": committed_counters("render_bwd").get("l2_atomic_active_pct")}
 

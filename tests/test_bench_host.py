@@ -76,3 +76,48 @@ def test_clock_summary_counts_the_timed_samples():
     assert c["reasons"] == ["sw_power_cap"]
     # the timed region (widened by one sampling interval) holds the samples at 0.1, 0.2 and 0.3 s
     assert c["samples_timed"] == 3 and c["sm_mhz_timed"] == 2070.0
+
+
+def test_mask_visits_counts_warp_entry_pairs():
+    """The bench's count of the masked backward's (warp, entry) visits
+    against a plain loop over tiles, warps and entries on random per-pixel
+    blend-mask words (garbage past each warp's last run and past each list's
+    end must not count)."""
+    import numpy as np
+    import torch
+    import bench
+    rng = np.random.default_rng(5)
+    TX, TY, H, W = 3, 2, 29, 45          # ragged: the last tile row/column is partial
+    T = TX * TY
+    lens = rng.integers(0, 90, T)
+    starts = np.concatenate([[0], np.cumsum(lens)[:-1]]) + 7
+    ranges = np.stack([starts, starts + lens], 1).astype(np.int32)
+    nwords = 256 * (int(starts.max()) // 32 + T) + 256 * 8 + 256
+    bm = rng.integers(0, 2 ** 32, nwords, dtype=np.uint64).astype(np.uint32).view(np.int32)
+    last = np.zeros((H, W), np.int64)
+    for t in range(T):
+        tx, ty = t % TX, t // TX
+        for py in range(16):
+            for px in range(16):
+                y, x = ty * 16 + py, tx * 16 + px
+                if y < H and x < W:
+                    last[y, x] = rng.integers(0, lens[t] + 1)
+    want = 0
+    for t in range(T):
+        tx, ty = t % TX, t // TX
+        for w in range(8):
+            wl = 0
+            for lane in range(32):
+                y = ty * 16 + (w // 2) * 4 + lane // 8
+                x = tx * 16 + (w % 2) * 8 + lane % 8
+                if y < H and x < W:
+                    wl = max(wl, int(last[y, x]))
+            for e in range(wl if wl % 32 == 0 else (wl // 32 + 1) * 32):
+                if e >= lens[t]:
+                    continue
+                r, b = divmod(e, 32)
+                base = 256 * (int(starts[t]) // 32 + t) + 256 * r + 32 * w
+                if any((int(bm.view(np.uint32)[base + lane]) >> b) & 1 for lane in range(32)):
+                    want += 1
+    got = bench.mask_visits(torch.from_numpy(bm), torch.from_numpy(ranges), torch.from_numpy(last), TX, TY)
+    assert got == want
