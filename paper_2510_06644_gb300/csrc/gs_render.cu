@@ -131,6 +131,15 @@ __device__ __forceinline__ PixelMap map_pixel(const Grid& g, int tile, int lt) {
     return m;
 }
 
+// Sampled pixel q of the tile: full-resolution coordinates, and whether it
+// lies in the image.
+__device__ __forceinline__ bool ep_pixel(const Grid& g, int tile, int q, int& i, int& j) {
+    const int tx = tile % g.TX, ty = tile / g.TX;
+    i = tx * g.tw + q % g.tw;
+    j = ty * g.th + q / g.tw;
+    return q < g.tw * g.th && i < g.Ws && j < g.Hs;
+}
+
 // The 2D Gaussian at offset d = (dx, dy) from its mean (Eq. 2): with the
 // conic Q = [[ca, cb], [cb, cc]], (a, b) = Q d and q = d^T Q d = dx a + dy b,
 // the exponent is -q/2 and the backward's mean gradient is (a, b) times
@@ -963,8 +972,14 @@ __device__ __forceinline__ void back_pair(BackState& S, const RunStage& R, int k
     }
 }
 
-// Backward compositing of one warp's block of a pixel-parallel tile from the
-// forward's per-pixel blend masks (warp w of the tile's TT / 32).  The warp
+// Backward compositing of one warp's block of a tile from the forward's
+// per-pixel blend masks (warp w of the tile's).  Pixel-parallel tiles (EP
+// false): the warp's 8x4 block, the masks in the run-major layout.
+// Entry-parallel tiles of strided frames (EP true): the tile's sampled
+// pixels 32 w .. 32 w + 31 in row-major order, the masks in the
+// entry-parallel forward's pixel-major layout, whose words past a pixel's
+// stopping batch were never written: each lane keeps only the bits before
+// its own last blended position.  The warp
 // walks its runs of 32 list entries from the last one holding an entry one
 // of its pixels blended back to the first.  Per run it stages only those
 // entries, one lane each (the record alone: no box, which the masks make
@@ -976,7 +991,7 @@ __device__ __forceinline__ void back_pair(BackState& S, const RunStage& R, int k
 // atomic per (entry, field, warp): the warps of a tile share nothing and run
 // as one-warp CTAs that the hardware schedules as they free up, heavy tiles
 // first.
-template <int DT, int MODE, int NP>
+template <int DT, int MODE, int NP, bool EP>
 __device__ __forceinline__ void bwd_pw(const gs_config& cfg, const Grid& g, const void* __restrict__ splats,
                                        const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
                                        const float* __restrict__ t_final, const uint32_t* __restrict__ last_idx,
@@ -986,7 +1001,6 @@ __device__ __forceinline__ void bwd_pw(const gs_config& cfg, const Grid& g, cons
     constexpr int NF = Fields<MODE>::N;
     constexpr int BSTEP = 2 * NP;  // entries per step, merged together
     static_assert(BSTEP * NF <= 32, "one lane per merged value");
-    const int TT = tile_threads(g);
     const int lane = threadIdx.x & 31;
     // slots past a run's entries are read by the last step's unused halves:
     // they must hold finite values (zeros, or an earlier run's records)
@@ -994,35 +1008,49 @@ __device__ __forceinline__ void bwd_pw(const gs_config& cfg, const Grid& g, cons
     for (int q = 0; q < (int)(sizeof(RunStage) / 4 / 32); ++q) (&R.x[0])[q * 32 + lane] = 0.f;
     __syncwarp();
     const int lt = w * 32 + lane;
-    const PixelMap m = map_pixel(g, tile, lt);
+    PixelMap m;
+    if (EP) {
+        int i, j;
+        m.inside = ep_pixel(g, tile, lt, i, j);
+        m.i = i;
+        m.j = j;
+        m.px = i * g.sx;
+        m.py = j * g.sy;
+    } else {
+        m = map_pixel(g, tile, lt);
+    }
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
     BackState S;
-    uint32_t last = back_start(cfg, g, m, t_final, last_idx, d_rgb, d_depth, S);
-    last = min(last, end - start);
+    const uint32_t own = min(back_start(cfg, g, m, t_final, last_idx, d_rgb, d_depth, S), end - start);
+    uint32_t last = own;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
     if (last == 0u) return;  // (warp-uniform) no pixel of the block blended anything
     const float pxc = (float)m.px + 0.5f, pyc = (float)m.py + 0.5f;
     const x2f PXC = x2_pack(pxc, pxc), PYC = x2_pack(pyc, pyc);
     const int owner = merge_owner<BSTEP * NF>();
-    const uint32_t* bm = bmask + blend_mask_base(tile, start) + lt;
+    // this pixel's word of run r at bm[r rs]
+    const uint32_t* bm = EP ? bmask + blend_mask_base_ep(tile, start) + (size_t)lt * ((end - start + 31) >> 5)
+                            : bmask + blend_mask_base(tile, start) + lt;
+    const size_t rs = EP ? 1 : (size_t)tile_threads(g);
     const int r_top = (int)((last + 31u) >> 5) - 1;
     // a run's list ids and mask word are loaded one run ahead (runs below
     // the top one are full: their 32 positions lie inside the list)
     uint32_t id_nx = r_top * 32 + lane < (int)(end - start)
                          ? __ldg(vals + start + (uint32_t)r_top * 32u + (uint32_t)lane)
                          : 0u;
-    uint32_t bm_nx = __ldg(bm + (size_t)r_top * TT);
+    uint32_t bm_nx = __ldg(bm + (size_t)r_top * rs);
 #pragma unroll 1
     for (int r = r_top; r >= 0; --r) {
-        // (bits past the list's end are ignored: masks from another forward
-        // cannot send a load outside the tile's list)
-        const uint32_t len_r = min(32u, (end - start) - (uint32_t)r * 32u);
-        const uint32_t mine = bm_nx & (len_r == 32u ? ~0u : (1u << len_r) - 1u);
+        // only bits before the pixel's own last blended position count
+        // (this also keeps masks from another forward from sending a load
+        // outside the tile's list)
+        const uint32_t lim = own > (uint32_t)r * 32u ? min(32u, own - (uint32_t)r * 32u) : 0u;
+        const uint32_t mine = bm_nx & (lim == 32u ? ~0u : (1u << lim) - 1u);
         const uint32_t id = id_nx;
         if (r > 0) {
             id_nx = __ldg(vals + start + (uint32_t)(r - 1) * 32u + (uint32_t)lane);
-            bm_nx = __ldg(bm + (size_t)(r - 1) * TT);
+            bm_nx = __ldg(bm + (size_t)(r - 1) * rs);
         }
         const unsigned mw = __reduce_or_sync(0xffffffffu, mine);
         if (mw == 0u) continue;
@@ -1084,7 +1112,12 @@ struct PwPairs {
 
 // One-warp CTAs: 32 per SM at 64 registers for the pose-only fields; 24 when
 // mapping.
-template <int DT, int MODE>
+// Warps per tile of the masked backward.
+__host__ __device__ inline int pw_warps(const Grid& g, bool ep) {
+    return ep ? (g.tw * g.th + 31) >> 5 : tile_threads(g) >> 5;
+}
+
+template <int DT, int MODE, bool EP>
 __global__ void __launch_bounds__(32, MODE == GS_TRACK ? 32 : 24)
     k_render_bwd_pw(gs_config cfg, Grid g, const void* __restrict__ splats, const uint32_t* __restrict__ vals,
                     const uint32_t* __restrict__ ranges, const uint32_t* __restrict__ order,
@@ -1092,11 +1125,11 @@ __global__ void __launch_bounds__(32, MODE == GS_TRACK ? 32 : 24)
                     const float* __restrict__ d_rgb, const float* __restrict__ d_depth, float* __restrict__ grad2d,
                     const uint32_t* __restrict__ bmask) {
     __shared__ RunStage R;
-    const int wpt = tile_threads(g) >> 5;
+    const int wpt = pw_warps(g, EP);
     const int t = (int)blockIdx.x / wpt, w = (int)blockIdx.x % wpt;
     const int tile = order ? (int)__ldg(order + t) : t;
-    bwd_pw<DT, MODE, PwPairs<MODE>::N>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth, grad2d,
-                                       bmask, tile, w, R);
+    bwd_pw<DT, MODE, PwPairs<MODE>::N, EP>(cfg, g, splats, vals, ranges, t_final, last_idx, d_rgb, d_depth,
+                                           grad2d, bmask, tile, w, R);
 }
 
 // ---------------------------------------------------------------------------
@@ -1163,14 +1196,6 @@ __device__ __forceinline__ bool ep_may_blend(const EpStageN<NB>& S, int e, int p
     return px >= box.x && px <= box.y && py >= box.z && py <= box.w;
 }
 
-// Sampled pixel q of the tile: full-resolution coordinates, and whether it
-// lies in the image.
-__device__ __forceinline__ bool ep_pixel(const Grid& g, int tile, int q, int& i, int& j) {
-    const int tx = tile % g.TX, ty = tile / g.TX;
-    i = tx * g.tw + q % g.tw;
-    j = ty * g.th + q / g.tw;
-    return q < g.tw * g.th && i < g.Ws && j < g.Hs;
-}
 
 // Pixel-to-warp assignment of a tile (the pairing of Sec. 5.2's workload
 // scheduling unit): the tile's npix = W * ppw pixels are ranked by their
@@ -1643,18 +1668,19 @@ __global__ void __launch_bounds__(R_THREADS, KST == 1 ? 4 : 2)
                                   J.grad2d, G, r_smem, s_max_all);
 }
 
-// Pixel-parallel jobs with blend masks: one-warp CTAs over (job, tile, warp).
+// Jobs with blend masks: one-warp CTAs over (job, tile, warp).
+template <bool EP>
 __global__ void __launch_bounds__(32, 32) k_wave_render_bwd_pw(const gs_config cfg,
                                                                 const __grid_constant__ Wave<WaveBwdJob> W) {
     __shared__ RunStage R;
     const int j = wave_find(W.start, W.n, (int)blockIdx.x);
     const WaveBwdJob& J = W.job[j];
     const int blk = (int)blockIdx.x - W.start[j];
-    const int wpt = tile_threads(J.g) >> 5;
+    const int wpt = pw_warps(J.g, EP);
     const int t = blk / wpt, w = blk % wpt;
     const int tile = J.order ? (int)__ldg(J.order + t) : t;
-    bwd_pw<GS_F32, GS_TRACK, PwPairs<GS_TRACK>::N>(cfg, J.g, J.splats, J.vals, J.ranges, J.t_final, J.last_idx,
-                                                    J.d_rgb, J.d_depth, J.grad2d, J.bmask, tile, w, R);
+    bwd_pw<GS_F32, GS_TRACK, PwPairs<GS_TRACK>::N, EP>(cfg, J.g, J.splats, J.vals, J.ranges, J.t_final, J.last_idx,
+                                                        J.d_rgb, J.d_depth, J.grad2d, J.bmask, tile, w, R);
 }
 
 template <int NW>
@@ -1745,7 +1771,22 @@ static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* spl
                             const uint32_t* last_idx, const float* d_rgb, const float* d_depth, float* grad2d,
                             const uint32_t* bmask, cudaStream_t st) {
     const int ntiles = g.TX * g.TY;
-    if (g.tw * g.th <= 64) {
+    const bool ep = g.tw * g.th <= 64;
+    // with masks: one-warp CTAs for pixel-parallel tiles and for the 64-pixel
+    // tiles of strided frames (stride 2: 64 -> 90 us in the entry-parallel
+    // kernel; the 16- and 32-pixel tiles of larger strides half-fill or
+    // spread a warp and stay entry-parallel: 38 against 60 us at 4x4)
+    if (bmask && (!ep || g.tw * g.th == 64)) {
+        const unsigned nw = (unsigned)ntiles * (unsigned)pw_warps(g, ep);
+        if (ep)
+            k_render_bwd_pw<DT, MD, true><<<nw, 32, 0, st>>>(cfg, g, splats, vals, ranges, order, t_final, last_idx,
+                                                              d_rgb, d_depth, grad2d, bmask);
+        else
+            k_render_bwd_pw<DT, MD, false><<<nw, 32, 0, st>>>(cfg, g, splats, vals, ranges, order, t_final, last_idx,
+                                                               d_rgb, d_depth, grad2d, bmask);
+        return check_launch("k_render_bwd_pw");
+    }
+    if (ep) {
         gs_status s;
         const int id = 18 + 4 * (MD == GS_MAP) + DT;  // + 0 or 8 below: W
         if (g.tw * g.th <= 32) {
@@ -1761,12 +1802,6 @@ static gs_status launch_bwd(const gs_config& cfg, const Grid& g, const void* spl
                                                                       bmask);
         }
         return check_launch("k_render_bwd_ep");
-    }
-    if (bmask) {
-        const unsigned nw = (unsigned)ntiles * (unsigned)(tile_threads(g) >> 5);
-        k_render_bwd_pw<DT, MD><<<nw, 32, 0, st>>>(cfg, g, splats, vals, ranges, order, t_final, last_idx, d_rgb,
-                                                    d_depth, grad2d, bmask);
-        return check_launch("k_render_bwd_pw");
     }
     const int gpc = R_THREADS / tile_threads(g);
     const unsigned nt = (unsigned)((ntiles + gpc - 1) / gpc);
@@ -1925,9 +1960,9 @@ static int render_form(const Grid& g) {
 
 gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cudaStream_t st) {
     gs_status s;
+    // forward compositing with the fused loss
     int present = 0;
     for (int j = 0; j < n; ++j) present |= 1 << render_form(make_grid(jobs[j].cam));
-    // forward compositing with the fused loss
     for (int form = 0; form < 4; ++form) {
         if (!(present & (1 << form))) continue;
         Wave<WaveFwdJob> W;
@@ -1963,14 +1998,17 @@ gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cud
         }
         if ((s = check_launch("k_wave_render_fwd")) != GS_OK) return s;
     }
-    // backward compositing, pose-only fields; pixel-parallel jobs with blend
-    // masks (kind 4) go to the one-warp kernel
+    // backward compositing, pose-only fields; jobs with blend masks go to the
+    // one-warp kernel as in launch_bwd (kind 4: pixel-parallel tiles, 5:
+    // 64-pixel entry-parallel tiles)
+    auto bwd_kind = [](const gs_track_job& t) {
+        const int form = render_form(make_grid(t.cam));
+        if (!t.blend_masks) return form;
+        return form < 2 ? 4 : (form == 3 ? 5 : form);
+    };
     int kinds = 0;
-    for (int j = 0; j < n; ++j) {
-        const int form = render_form(make_grid(jobs[j].cam));
-        kinds |= 1 << (form < 2 && jobs[j].blend_masks ? 4 : form);
-    }
-    for (int kind = 0; kind < 5; ++kind) {
+    for (int j = 0; j < n; ++j) kinds |= 1 << bwd_kind(jobs[j]);
+    for (int kind = 0; kind < 6; ++kind) {
         if (!(kinds & (1 << kind))) continue;
         Wave<WaveBwdJob> W;
         W.n = 0;
@@ -1980,8 +2018,7 @@ gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cud
         for (int j = 0; j < n; ++j) {
             const gs_track_job& t = jobs[j];
             const Grid g = make_grid(t.cam);
-            const int form = render_form(g);
-            if ((form < 2 && t.blend_masks ? 4 : form) != kind) continue;
+            if (bwd_kind(t) != kind) continue;
             const int ntiles = g.TX * g.TY;
             const int gpc = kind < 2 ? R_THREADS / tile_threads(g) : 1;
             const int B = kind < 2 ? group_batch(gpc, per_entry, R_BWD_SMEM) : 0;
@@ -1989,7 +2026,7 @@ gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cud
             W.job[W.n] = WaveBwdJob{g, t.splats, t.vals, t.tile_ranges, t.tile_order, t.t_final, t.last_idx, t.d_rgb,
                                     t.d_depth, t.grad2d, t.blend_masks, B};
             ++W.n;
-            blocks += kind == 4 ? ntiles * (tile_threads(g) >> 5) : (ntiles + gpc - 1) / gpc;
+            blocks += kind >= 4 ? ntiles * pw_warps(g, kind == 5) : (ntiles + gpc - 1) / gpc;
             if (kind < 2) smem = std::max(smem, (size_t)gpc * B * per_entry);
         }
         W.start[W.n] = blocks;
@@ -2008,7 +2045,10 @@ gs_status wave_render(const gs_config& cfg, const gs_track_job* jobs, int n, cud
             if ((s = smem_once((const void*)k_wave_render_bwd_ep<16>, 45, sm)) != GS_OK) return s;
             k_wave_render_bwd_ep<16><<<(unsigned)blocks, 16 * 32, sm, st>>>(cfg, W);
         } else {
-            k_wave_render_bwd_pw<<<(unsigned)blocks, 32, 0, st>>>(cfg, W);
+            if (kind == 4)
+                k_wave_render_bwd_pw<false><<<(unsigned)blocks, 32, 0, st>>>(cfg, W);
+            else
+                k_wave_render_bwd_pw<true><<<(unsigned)blocks, 32, 0, st>>>(cfg, W);
         }
         if ((s = check_launch("k_wave_render_bwd")) != GS_OK) return s;
     }
