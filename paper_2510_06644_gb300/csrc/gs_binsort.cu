@@ -738,12 +738,15 @@ struct BinLayout {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Gaussians per CTA of the aggregated passes: one per thread, or more when
-// the per-CTA rows would pass 2^24 entries (64 MB).
+// Gaussians per CTA of the aggregated passes: two per thread (half the
+// rows of one per thread for the column scan, and 782 -> 391 CTAs fit one
+// wave: projection + binning + sort 63.6-64.6 -> 61.6-62.5 us on the
+// tracking frame; four per thread 72.8-74.8), or more when the per-CTA rows
+// would pass 2^24 entries (64 MB).
 static int64_t agg_per_cta(int64_t n, int ntiles) {
     const int64_t lim = (int64_t)1 << 24;
     const int64_t want = (n * (int64_t)ntiles + lim - 1) / lim;
-    return want > BIN_THREADS ? want : BIN_THREADS;
+    return want > 2 * BIN_THREADS ? want : 2 * BIN_THREADS;
 }
 
 static BinLayout bin_layout(int64_t n, int64_t cap, int ntiles) {
