@@ -203,6 +203,10 @@ __global__ void __launch_bounds__(256) k_project_hist(gs_camera cam, gs_config c
 // ---------------------------------------------------------------------------
 
 #define PB_THREADS 256
+#define PB_PER 2          // Gaussians per thread of the backward projection
+
+// Blocks of the backward projection for n Gaussians.
+static inline int64_t pb_blocks(int64_t n) { return (n + PB_PER * PB_THREADS - 1) / (PB_PER * PB_THREADS); }
 
 // The pose gradient is a sum over every Gaussian of terms of both signs
 // (the Merging Tree of Sec. 5.1 reduces it in hardware).  Inside a block the
@@ -370,166 +374,177 @@ __device__ __forceinline__ void project_bwd_body(gs_camera cam, const gs_config&
                                                  double* __restrict__ pose_out, unsigned int* __restrict__ ticket,
                                                  const gs_pose_step& step, int blk, int nblk,
                                                  const AdamMap* adam = nullptr) {
-    const int64_t k = (int64_t)blk * blockDim.x + threadIdx.x;
-    float pose[6] = {0, 0, 0, 0, 0, 0};
+    // the thread's pose terms, summed as float32 pairs over its Gaussians
+    DF pacc[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pacc[i] = DF{0.f, 0.f};
     resolve_pose(cam);
-    if (k < g.n) {
-        float mu[3], ls[3], q[4];
-        for (int i = 0; i < 3; ++i) { mu[i] = __ldg(g.means + 3 * k + i); ls[i] = __ldg(g.log_scales + 3 * k + i); }
-        for (int i = 0; i < 4; ++i) q[i] = __ldg(g.quats + 4 * k + i);
-        const float ol = __ldg(g.opacity_logit + k);
-        const bool masked = g.mask && __ldg(g.mask + k);
-        Proj o;
-        o.visible = false;
-        if (!masked) project_core(cam, cfg, mu, ls, q, ol, o);
-        float gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gol = 0.f, grgb[3] = {0, 0, 0};
-        float t_mu = 0.f, t_sig = 0.f;
-        const float4* g4 = reinterpret_cast<const float4*>(grad2d) + 3 * k;
-        if (o.visible) {
-            const float4 ga = __ldg(g4), gb = __ldg(g4 + 1), gc = __ldg(g4 + 2);
-            const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, gop = gb.y, gd = gb.z;
-            grgb[0] = gc.x; grgb[1] = gc.y; grgb[2] = gc.z;
-            const float x = o.p[0], y = o.p[1], z = o.p[2];
-            const float fx = cam.fx, fy = cam.fy;
-            // conic Q = S2^{-1}: G2 = -Q Gq Q with Gq = [[gA, gB/2], [gB/2, gC]]
-            const float Q00 = o.ca, Q01 = o.cb, Q11 = o.cc;
-            const float hB = 0.5f * gB;
-            const float M00 = Q00 * gA + Q01 * hB, M01 = Q00 * hB + Q01 * gC;
-            const float M10 = Q01 * gA + Q11 * hB, M11 = Q01 * hB + Q11 * gC;
-            const float G00 = -(M00 * Q00 + M01 * Q01);
-            const float G01 = -(M00 * Q01 + M01 * Q11);
-            const float G11 = -(M10 * Q01 + M11 * Q11);
-            // dL/dSc = J^T G2 J (J rows: (J00, 0, J02), (0, J11, J12))
-            const float J00 = o.J00, J02 = o.J02, J11 = o.J11, J12 = o.J12;
-            float Gc[9];
-            {
-                // columns of J: c0 = (J00, 0), c1 = (0, J11), c2 = (J02, J12)
-                const float c0x = J00, c1y = J11, c2x = J02, c2y = J12;
-                // G2 c_j
-                const float g0x = G00 * c0x;
-                const float g1x = G01 * c1y, g1y = G11 * c1y;
-                const float g2x = G00 * c2x + G01 * c2y, g2y = G01 * c2x + G11 * c2y;
-                Gc[0] = c0x * g0x;
-                Gc[1] = c0x * g1x;
-                Gc[2] = c0x * g2x;
-                Gc[4] = c1y * g1y;
-                Gc[5] = c1y * g2y;
-                Gc[8] = c2x * g2x + c2y * g2y;
-                Gc[3] = Gc[1]; Gc[6] = Gc[2]; Gc[7] = Gc[5];
-            }
-            // dL/dJ = 2 G2 J Sc ; only entries (0,0), (0,2), (1,1), (1,2) matter
-            const float* S = o.Sc;
-            // J Sc rows
-            const float JS0x = J00 * S[0] + J02 * S[6], JS0y = J00 * S[1] + J02 * S[7], JS0z = J00 * S[2] + J02 * S[8];
-            const float JS1x = J11 * S[3] + J12 * S[6], JS1y = J11 * S[4] + J12 * S[7], JS1z = J11 * S[5] + J12 * S[8];
-            const float GJ00 = 2.f * (G00 * JS0x + G01 * JS1x);
-            const float GJ02 = 2.f * (G00 * JS0z + G01 * JS1z);
-            const float GJ11 = 2.f * (G01 * JS0y + G11 * JS1y);
-            const float GJ12 = 2.f * (G01 * JS0z + G11 * JS1z);
-            const float zi = 1.f / z, zi2 = zi * zi, zi3 = zi2 * zi;
-            float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
-            gp2 += GJ00 * (-fx * zi2) + GJ11 * (-fy * zi2);
-            if (o.clx) gp2 += GJ02 * (fx * o.lx * zi2);
-            else { gp0 += GJ02 * (-fx * zi2); gp2 += GJ02 * (2.f * fx * x * zi3); }
-            if (o.cly) gp2 += GJ12 * (fy * o.ly * zi2);
-            else { gp1 += GJ12 * (-fy * zi2); gp2 += GJ12 * (2.f * fy * y * zi3); }
-            gp0 += gu * fx * zi;
-            gp1 += gv * fy * zi;
-            gp2 += -(gu * fx * x + gv * fy * y) * zi2 + gd;
-            const float* R = cam.R;
-            gmu[0] = R[0] * gp0 + R[3] * gp1 + R[6] * gp2;
-            gmu[1] = R[1] * gp0 + R[4] * gp1 + R[7] * gp2;
-            gmu[2] = R[2] * gp0 + R[5] * gp1 + R[8] * gp2;
-            // GS = R^T Gc R
-            float tmp[9], GS[9];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j)
-                    tmp[3 * i + j] = R[i] * Gc[j] + R[3 + i] * Gc[3 + j] + R[6 + i] * Gc[6 + j];
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j)
-                    GS[3 * i + j] = tmp[3 * i] * R[j] + tmp[3 * i + 1] * R[3 + j] + tmp[3 * i + 2] * R[6 + j];
-            if (WANT_SCORE) {
-                t_mu = sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]);
-                float fr = 0.f;
-                for (int i = 0; i < 9; ++i) fr += GS[i] * GS[i];
-                t_sig = sqrtf(fr);
-            }
-            if (WANT_GRADS) {
-                // Sigma = M M^T: dL/dM = 2 GS M
-                float GM[9];
+#pragma unroll 1
+    for (int rep = 0; rep < PB_PER; ++rep) {
+        const int64_t k = ((int64_t)blk * PB_PER + rep) * blockDim.x + threadIdx.x;
+        float pose[6] = {0, 0, 0, 0, 0, 0};
+        if (k < g.n) {
+            float mu[3], ls[3], q[4];
+            for (int i = 0; i < 3; ++i) { mu[i] = __ldg(g.means + 3 * k + i); ls[i] = __ldg(g.log_scales + 3 * k + i); }
+            for (int i = 0; i < 4; ++i) q[i] = __ldg(g.quats + 4 * k + i);
+            const float ol = __ldg(g.opacity_logit + k);
+            const bool masked = g.mask && __ldg(g.mask + k);
+            Proj o;
+            o.visible = false;
+            if (!masked) project_core(cam, cfg, mu, ls, q, ol, o);
+            float gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gol = 0.f, grgb[3] = {0, 0, 0};
+            float t_mu = 0.f, t_sig = 0.f;
+            const float4* g4 = reinterpret_cast<const float4*>(grad2d) + 3 * k;
+            if (o.visible) {
+                const float4 ga = __ldg(g4), gb = __ldg(g4 + 1), gc = __ldg(g4 + 2);
+                const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, gop = gb.y, gd = gb.z;
+                grgb[0] = gc.x; grgb[1] = gc.y; grgb[2] = gc.z;
+                const float x = o.p[0], y = o.p[1], z = o.p[2];
+                const float fx = cam.fx, fy = cam.fy;
+                // conic Q = S2^{-1}: G2 = -Q Gq Q with Gq = [[gA, gB/2], [gB/2, gC]]
+                const float Q00 = o.ca, Q01 = o.cb, Q11 = o.cc;
+                const float hB = 0.5f * gB;
+                const float M00 = Q00 * gA + Q01 * hB, M01 = Q00 * hB + Q01 * gC;
+                const float M10 = Q01 * gA + Q11 * hB, M11 = Q01 * hB + Q11 * gC;
+                const float G00 = -(M00 * Q00 + M01 * Q01);
+                const float G01 = -(M00 * Q01 + M01 * Q11);
+                const float G11 = -(M10 * Q01 + M11 * Q11);
+                // dL/dSc = J^T G2 J (J rows: (J00, 0, J02), (0, J11, J12))
+                const float J00 = o.J00, J02 = o.J02, J11 = o.J11, J12 = o.J12;
+                float Gc[9];
+                {
+                    // columns of J: c0 = (J00, 0), c1 = (0, J11), c2 = (J02, J12)
+                    const float c0x = J00, c1y = J11, c2x = J02, c2y = J12;
+                    // G2 c_j
+                    const float g0x = G00 * c0x;
+                    const float g1x = G01 * c1y, g1y = G11 * c1y;
+                    const float g2x = G00 * c2x + G01 * c2y, g2y = G01 * c2x + G11 * c2y;
+                    Gc[0] = c0x * g0x;
+                    Gc[1] = c0x * g1x;
+                    Gc[2] = c0x * g2x;
+                    Gc[4] = c1y * g1y;
+                    Gc[5] = c1y * g2y;
+                    Gc[8] = c2x * g2x + c2y * g2y;
+                    Gc[3] = Gc[1]; Gc[6] = Gc[2]; Gc[7] = Gc[5];
+                }
+                // dL/dJ = 2 G2 J Sc ; only entries (0,0), (0,2), (1,1), (1,2) matter
+                const float* S = o.Sc;
+                // J Sc rows
+                const float JS0x = J00 * S[0] + J02 * S[6], JS0y = J00 * S[1] + J02 * S[7], JS0z = J00 * S[2] + J02 * S[8];
+                const float JS1x = J11 * S[3] + J12 * S[6], JS1y = J11 * S[4] + J12 * S[7], JS1z = J11 * S[5] + J12 * S[8];
+                const float GJ00 = 2.f * (G00 * JS0x + G01 * JS1x);
+                const float GJ02 = 2.f * (G00 * JS0z + G01 * JS1z);
+                const float GJ11 = 2.f * (G01 * JS0y + G11 * JS1y);
+                const float GJ12 = 2.f * (G01 * JS0z + G11 * JS1z);
+                const float zi = 1.f / z, zi2 = zi * zi, zi3 = zi2 * zi;
+                float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f;
+                gp2 += GJ00 * (-fx * zi2) + GJ11 * (-fy * zi2);
+                if (o.clx) gp2 += GJ02 * (fx * o.lx * zi2);
+                else { gp0 += GJ02 * (-fx * zi2); gp2 += GJ02 * (2.f * fx * x * zi3); }
+                if (o.cly) gp2 += GJ12 * (fy * o.ly * zi2);
+                else { gp1 += GJ12 * (-fy * zi2); gp2 += GJ12 * (2.f * fy * y * zi3); }
+                gp0 += gu * fx * zi;
+                gp1 += gv * fy * zi;
+                gp2 += -(gu * fx * x + gv * fy * y) * zi2 + gd;
+                const float* R = cam.R;
+                gmu[0] = R[0] * gp0 + R[3] * gp1 + R[6] * gp2;
+                gmu[1] = R[1] * gp0 + R[4] * gp1 + R[7] * gp2;
+                gmu[2] = R[2] * gp0 + R[5] * gp1 + R[8] * gp2;
+                // GS = R^T Gc R
+                float tmp[9], GS[9];
                 for (int i = 0; i < 3; ++i)
                     for (int j = 0; j < 3; ++j)
-                        GM[3 * i + j] = 2.f * (GS[3 * i] * o.M[j] + GS[3 * i + 1] * o.M[3 + j] + GS[3 * i + 2] * o.M[6 + j]);
-                float GR[9];
-                for (int j = 0; j < 3; ++j) {
-                    gls[j] = GM[j] * o.M[j] + GM[3 + j] * o.M[3 + j] + GM[6 + j] * o.M[6 + j];
-                    for (int i = 0; i < 3; ++i) GR[3 * i + j] = GM[3 * i + j] * o.scale[j];
+                        tmp[3 * i + j] = R[i] * Gc[j] + R[3 + i] * Gc[3 + j] + R[6 + i] * Gc[6 + j];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        GS[3 * i + j] = tmp[3 * i] * R[j] + tmp[3 * i + 1] * R[3 + j] + tmp[3 * i + 2] * R[6 + j];
+                if (WANT_SCORE) {
+                    t_mu = sqrtf(gmu[0] * gmu[0] + gmu[1] * gmu[1] + gmu[2] * gmu[2]);
+                    float fr = 0.f;
+                    for (int i = 0; i < 9; ++i) fr += GS[i] * GS[i];
+                    t_sig = sqrtf(fr);
                 }
-                const float w = o.qn[0], qx = o.qn[1], qy = o.qn[2], qz = o.qn[3];
-                float gqn[4];
-                gqn[0] = 2.f * (-qz * GR[1] + qy * GR[2] + qz * GR[3] - qx * GR[5] - qy * GR[6] + qx * GR[7]);
-                gqn[1] = 2.f * (qy * GR[1] + qz * GR[2] + qy * GR[3] - 2.f * qx * GR[4] - w * GR[5] + qz * GR[6] + w * GR[7] - 2.f * qx * GR[8]);
-                gqn[2] = 2.f * (-2.f * qy * GR[0] + qx * GR[1] + w * GR[2] + qx * GR[3] + qz * GR[5] - w * GR[6] + qz * GR[7] - 2.f * qy * GR[8]);
-                gqn[3] = 2.f * (-2.f * qz * GR[0] - w * GR[1] + qx * GR[2] + w * GR[3] - 2.f * qz * GR[4] + qy * GR[5] + qx * GR[6] + qy * GR[7]);
-                const float dq = o.qn[0] * gqn[0] + o.qn[1] * gqn[1] + o.qn[2] * gqn[2] + o.qn[3] * gqn[3];
-                for (int i = 0; i < 4; ++i) gq[i] = (gqn[i] - o.qn[i] * dq) * o.qinv;
-                gol = gop * o.op * (1.f - o.op);
-            }
-            if (WANT_POSE) {
-                pose[0] = gp0; pose[1] = gp1; pose[2] = gp2;
-                // p x gp
-                pose[3] = y * gp2 - z * gp1;
-                pose[4] = z * gp0 - x * gp2;
-                pose[5] = x * gp1 - y * gp0;
-                // <Gc, [e_i]x S - S [e_i]x> for the symmetric Gc and S
-                // [e_x]x S - S [e_x]x etc. written out entrywise
-                const float* Sm = o.Sc;
-                // D = E S - S E;  sum_ij Gc_ij D_ij
-                for (int e = 0; e < 3; ++e) {
-                    float E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-                    if (e == 0) { E[5] = -1.f; E[7] = 1.f; }
-                    if (e == 1) { E[2] = 1.f; E[6] = -1.f; }
-                    if (e == 2) { E[1] = -1.f; E[3] = 1.f; }
-                    float s = 0.f;
+                if (WANT_GRADS) {
+                    // Sigma = M M^T: dL/dM = 2 GS M
+                    float GM[9];
                     for (int i = 0; i < 3; ++i)
-                        for (int j = 0; j < 3; ++j) {
-                            float es = E[3 * i] * Sm[j] + E[3 * i + 1] * Sm[3 + j] + E[3 * i + 2] * Sm[6 + j];
-                            float se = Sm[3 * i] * E[j] + Sm[3 * i + 1] * E[3 + j] + Sm[3 * i + 2] * E[6 + j];
-                            s += Gc[3 * i + j] * (es - se);
-                        }
-                    pose[3 + e] += s;
+                        for (int j = 0; j < 3; ++j)
+                            GM[3 * i + j] = 2.f * (GS[3 * i] * o.M[j] + GS[3 * i + 1] * o.M[3 + j] + GS[3 * i + 2] * o.M[6 + j]);
+                    float GR[9];
+                    for (int j = 0; j < 3; ++j) {
+                        gls[j] = GM[j] * o.M[j] + GM[3 + j] * o.M[3 + j] + GM[6 + j] * o.M[6 + j];
+                        for (int i = 0; i < 3; ++i) GR[3 * i + j] = GM[3 * i + j] * o.scale[j];
+                    }
+                    const float w = o.qn[0], qx = o.qn[1], qy = o.qn[2], qz = o.qn[3];
+                    float gqn[4];
+                    gqn[0] = 2.f * (-qz * GR[1] + qy * GR[2] + qz * GR[3] - qx * GR[5] - qy * GR[6] + qx * GR[7]);
+                    gqn[1] = 2.f * (qy * GR[1] + qz * GR[2] + qy * GR[3] - 2.f * qx * GR[4] - w * GR[5] + qz * GR[6] + w * GR[7] - 2.f * qx * GR[8]);
+                    gqn[2] = 2.f * (-2.f * qy * GR[0] + qx * GR[1] + w * GR[2] + qx * GR[3] + qz * GR[5] - w * GR[6] + qz * GR[7] - 2.f * qy * GR[8]);
+                    gqn[3] = 2.f * (-2.f * qz * GR[0] - w * GR[1] + qx * GR[2] + w * GR[3] - 2.f * qz * GR[4] + qy * GR[5] + qx * GR[6] + qy * GR[7]);
+                    const float dq = o.qn[0] * gqn[0] + o.qn[1] * gqn[1] + o.qn[2] * gqn[2] + o.qn[3] * gqn[3];
+                    for (int i = 0; i < 4; ++i) gq[i] = (gqn[i] - o.qn[i] * dq) * o.qinv;
+                    gol = gop * o.op * (1.f - o.op);
                 }
+                if (WANT_POSE) {
+                    pose[0] = gp0; pose[1] = gp1; pose[2] = gp2;
+                    // p x gp
+                    pose[3] = y * gp2 - z * gp1;
+                    pose[4] = z * gp0 - x * gp2;
+                    pose[5] = x * gp1 - y * gp0;
+                    // <Gc, [e_i]x S - S [e_i]x> for the symmetric Gc and S
+                    // [e_x]x S - S [e_x]x etc. written out entrywise
+                    const float* Sm = o.Sc;
+                    // D = E S - S E;  sum_ij Gc_ij D_ij
+                    for (int e = 0; e < 3; ++e) {
+                        float E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                        if (e == 0) { E[5] = -1.f; E[7] = 1.f; }
+                        if (e == 1) { E[2] = 1.f; E[6] = -1.f; }
+                        if (e == 2) { E[1] = -1.f; E[3] = 1.f; }
+                        float s = 0.f;
+                        for (int i = 0; i < 3; ++i)
+                            for (int j = 0; j < 3; ++j) {
+                                float es = E[3 * i] * Sm[j] + E[3 * i + 1] * Sm[3 + j] + E[3 * i + 2] * Sm[6 + j];
+                                float se = Sm[3 * i] * E[j] + Sm[3 * i + 1] * E[3 + j] + Sm[3 * i + 2] * E[6 + j];
+                                s += Gc[3 * i + j] * (es - se);
+                            }
+                        pose[3 + e] += s;
+                    }
+                }
+            } else if (!masked && WANT_GRADS) {
+                // rgb gradient is independent of visibility only through grad2d,
+                // which is zero for culled Gaussians; keep zeros.
             }
-        } else if (!masked && WANT_GRADS) {
-            // rgb gradient is independent of visibility only through grad2d,
-            // which is zero for culled Gaussians; keep zeros.
+            if (ADAM) {
+                const AdamMap& A = *adam;
+                float* const gv[5] = {gmu, gls, gq, &gol, grgb};
+                const int width[5] = {3, 3, 4, 1, 3};
+    #pragma unroll
+                for (int t = 0; t < 5; ++t)
+    #pragma unroll
+                    for (int i = 0; i < width[t]; ++i) {
+                        const size_t e = (size_t)width[t] * k + i;
+                        float pp = A.p[t][e], mm = A.m[t][e], vv = A.v[t][e];
+                        adam_elem(pp, mm, vv, gv[t][i], A.lr, A.b1, A.b2, A.c1, A.c2, A.eps);
+                        A.p[t][e] = pp;
+                        A.m[t][e] = mm;
+                        A.v[t][e] = vv;
+                    }
+            }
+            if (WANT_GRADS) {
+                if (grads.means) for (int i = 0; i < 3; ++i) grads.means[3 * k + i] = gmu[i];
+                if (grads.log_scales) for (int i = 0; i < 3; ++i) grads.log_scales[3 * k + i] = gls[i];
+                if (grads.quats) for (int i = 0; i < 4; ++i) grads.quats[4 * k + i] = gq[i];
+                if (grads.opacity_logit) grads.opacity_logit[k] = gol;
+                if (grads.rgb) for (int i = 0; i < 3; ++i) grads.rgb[3 * k + i] = o.visible ? grgb[i] : 0.f;
+            }
+            if (WANT_SCORE) {
+                score[2 * k] = t_mu;
+                score[2 * k + 1] = t_sig;
+            }
         }
-        if (ADAM) {
-            const AdamMap& A = *adam;
-            float* const gv[5] = {gmu, gls, gq, &gol, grgb};
-            const int width[5] = {3, 3, 4, 1, 3};
-#pragma unroll
-            for (int t = 0; t < 5; ++t)
-#pragma unroll
-                for (int i = 0; i < width[t]; ++i) {
-                    const size_t e = (size_t)width[t] * k + i;
-                    float pp = A.p[t][e], mm = A.m[t][e], vv = A.v[t][e];
-                    adam_elem(pp, mm, vv, gv[t][i], A.lr, A.b1, A.b2, A.c1, A.c2, A.eps);
-                    A.p[t][e] = pp;
-                    A.m[t][e] = mm;
-                    A.v[t][e] = vv;
-                }
-        }
-        if (WANT_GRADS) {
-            if (grads.means) for (int i = 0; i < 3; ++i) grads.means[3 * k + i] = gmu[i];
-            if (grads.log_scales) for (int i = 0; i < 3; ++i) grads.log_scales[3 * k + i] = gls[i];
-            if (grads.quats) for (int i = 0; i < 4; ++i) grads.quats[4 * k + i] = gq[i];
-            if (grads.opacity_logit) grads.opacity_logit[k] = gol;
-            if (grads.rgb) for (int i = 0; i < 3; ++i) grads.rgb[3 * k + i] = o.visible ? grgb[i] : 0.f;
-        }
-        if (WANT_SCORE) {
-            score[2 * k] = t_mu;
-            score[2 * k + 1] = t_sig;
+        if (WANT_POSE) {
+    #pragma unroll
+            for (int i = 0; i < 6; ++i) pacc[i] = df_add(pacc[i], DF{pose[i], 0.f});
         }
     }
     if (WANT_POSE) {
@@ -539,7 +554,7 @@ __device__ __forceinline__ void project_bwd_body(gs_camera cam, const gs_config&
         const int wid = threadIdx.x >> 5;
         DF v[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) v[i] = DF{pose[i], 0.f};
+        for (int i = 0; i < 6; ++i) v[i] = pacc[i];
         const DF tot = warp_merge<6, DF, MergeDF>(v);  // 8 pair exchanges for the six components
         const int owner = merge_owner<6>();
         if (owner >= 0) ws[wid][owner] = make_float2(tot.hi, tot.lo);
@@ -694,7 +709,7 @@ extern "C" gs_status gs_project(const gs_config* cfg, const gs_camera* cam, cons
 }
 
 size_t gs_project_bwd_ws(int64_t n) {
-    const size_t nblk = (size_t)((n + PB_THREADS - 1) / PB_THREADS);
+    const size_t nblk = (size_t)pb_blocks(n);
     return ((nblk * 6 * sizeof(double)) + 255 + 256) & ~(size_t)255;  // partials + ticket
 }
 
@@ -740,7 +755,7 @@ extern "C" gs_status gs_project_bwd_step(const gs_config* cfg, const gs_camera* 
     }
     if (!grad2d) return set_error(GS_ERR_INVALID_ARG, "grad2d is NULL");
     gs_grads gg = grads ? *grads : gs_grads{nullptr, nullptr, nullptr, nullptr, nullptr};
-    const unsigned nblk = (unsigned)((g->n + PB_THREADS - 1) / PB_THREADS);
+    const unsigned nblk = (unsigned)pb_blocks(g->n);
     float2* part = (float2*)workspace;
     unsigned int* ticket = (unsigned int*)((char*)workspace + need - 256);
     if (want_pose && cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st) != cudaSuccess)
@@ -777,9 +792,10 @@ extern "C" gs_status gs_pose_update(float* pose, const double* pose_grad6, float
 // looked up below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GS_NOALLOC_SCRATCH_BYTES];
 // the size: one float2 pose partial per component (6) and block of PB_THREADS
-// Gaussians, plus the ticket word, rounded to 256 bytes
-static_assert(PB_THREADS == 256 && 6 * sizeof(float2) == 48,
-              "GS_NOALLOC_SCRATCH_BYTES assumes 256 Gaussians and 48 bytes of pose partials per block");
+// Gaussians, plus the ticket word, rounded to 256 bytes (an upper bound: a
+// block takes PB_PER x PB_THREADS Gaussians)
+static_assert(PB_THREADS == 256 && PB_PER >= 1 && 6 * sizeof(float2) == 48,
+              "GS_NOALLOC_SCRATCH_BYTES assumes at least 256 Gaussians and 48 bytes of pose partials per block");
 
 static gs_status noalloc_scratch(void** out) {
     // One entry per device, written by a host thread's first call.  Threads
@@ -877,7 +893,7 @@ extern "C" gs_status gs_project_bwd_adam(const gs_config* cfg, const gs_camera* 
     A.eps = adam->eps;
     A.c1 = A.c2 = 1.f;
     const gs_grads gg = grads ? *grads : gs_grads{nullptr, nullptr, nullptr, nullptr, nullptr};
-    const unsigned nblk = (unsigned)((g->n + PB_THREADS - 1) / PB_THREADS);
+    const unsigned nblk = (unsigned)pb_blocks(g->n);
     cudaStream_t st = (cudaStream_t)stream;
     if (score_terms)
         k_project_bwd_adam<true><<<nblk, PB_THREADS, 0, st>>>(*cam, *cfg, *g, grad2d, gg, score_terms, A, adam->state);
@@ -924,7 +940,7 @@ gs_status wave_project_bwd(const gs_config& cfg, const gs_track_job* jobs, int n
     for (int j = 0; j < n; ++j) {
         const gs_track_job& t = jobs[j];
         W.start[j] = blocks;
-        blocks += (int)((t.g.n + PB_THREADS - 1) / PB_THREADS);
+        blocks += (int)pb_blocks(t.g.n);
         W.job[j] = WavePbJob{t.cam, t.g, t.grad2d, t.score_terms, (float2*)t.bwd_workspace, t.pose_grad6,
                              wave_bwd_ticket(t), t.step};
     }
