@@ -347,15 +347,18 @@ __device__ __forceinline__ void stage_batch(const void* __restrict__ splats, con
 // Overlap masks of the staged entries with the warp's block: bit e of word q
 // is set when entry 32q + e (below `limit`) meets the block.  Lane q returns
 // word q (words at or beyond `words` are zero), so a word is one shuffle away
-// and the masks stay in registers.
+// and the masks stay in registers.  Only the words that hold entries are
+// built (a loop to the batch's last word rather than over all R_MASKW:
+// tracking step 236.6 -> 231.5 us).
 __device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit, int words, const PixelMap& m) {
     const int lane = threadIdx.x & 31;
     unsigned mine = 0u;
-#pragma unroll
-    for (int q = 0; q < R_MASKW; ++q) {
+    const int nq = min(words, (limit + 31) >> 5);  // the words holding entries
+#pragma unroll 4
+    for (int q = 0; q < nq; ++q) {
         const int e = q * 32 + lane;
         bool hit = false;
-        if (q < words && e < limit) {
+        if (e < limit) {
             const int4 box = sp[e].box;
             hit = !(box.x + box.y < m.wx0 || box.x > m.wx1 || box.z + box.w < m.wy0 || box.z > m.wy1);
         }
@@ -370,10 +373,11 @@ __device__ __forceinline__ unsigned warp_masks(const StagedSplat* sp, int limit,
 __device__ __forceinline__ unsigned warp_masks_bits(const StagedSplat* sp, int limit, int words, int wg) {
     const int lane = threadIdx.x & 31;
     unsigned mine = 0u;
-#pragma unroll
-    for (int q = 0; q < R_MASKW; ++q) {
+    const int nq = min(words, (limit + 31) >> 5);  // the words holding entries
+#pragma unroll 4
+    for (int q = 0; q < nq; ++q) {
         const int e = q * 32 + lane;
-        const bool hit = q < words && e < limit && ((__float_as_uint(sp[il_slot(e)].c.w) >> wg) & 1u);
+        const bool hit = e < limit && ((__float_as_uint(sp[il_slot(e)].c.w) >> wg) & 1u);
         const unsigned w = __ballot_sync(0xffffffffu, hit);
         if (lane == q) mine = w;
     }
