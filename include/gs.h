@@ -209,10 +209,10 @@ gs_status gs_project(const gs_config* cfg, const gs_camera* cam, const gs_gaussi
  * [2*TX*TY] u32.  If the count exceeds keys_capacity, only keys_capacity keys
  * are sorted and the device status becomes GS_ERR_CAPACITY.
  * tile_order (may be NULL): [TX*TY] u32 permutation of the tile ids, longest
- * lists first: tiles grouped by the power of two bounding their length,
- * (2^k, 2^(k+1)], empty tiles last, ascending tile id inside a group (a
- * function of the lists alone); passing it to the compositing calls makes
- * long tiles start first.
+ * lists first: tiles grouped by quarter octaves of their length (x = length
+ * - 1 in [2^m + q 2^(m-2), 2^m + (q + 1) 2^(m-2)), q = 0..3), then lengths 1
+ * and 0, ascending tile id inside a group (a function of the lists alone);
+ * passing it to the compositing calls makes long tiles start first.
  * Workspace: query with workspace == NULL (depends on n, keys_capacity and
  * the tile count). */
 gs_status gs_bin_sort(const gs_config* cfg, const gs_camera* cam, int rec_dtype, const void* splats, int64_t n,

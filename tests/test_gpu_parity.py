@@ -45,14 +45,19 @@ def gpu_bin(G, cam, rec, n, cap=None):
     keys, vals, nk, ranges, order = G.gs_bin_sort(cs, rec, n, cap)
     torch.cuda.synchronize()
     k = int(nk.item())
-    # the tile order: longest lists first by the group (2^k, 2^(k+1)] of
-    # their length (empty lists last), ascending tile index inside a group
-    # (a stable sort: exactly this permutation)
+    # the tile order: longest lists first by quarter octaves of their length
+    # (x = length - 1 in [2^m + q 2^(m-2), 2^m + (q + 1) 2^(m-2)); lengths 1
+    # and 0 last), ascending tile index inside a group (a stable sort:
+    # exactly this permutation)
     o = np_of(order).astype(np.int64)
     rr = np_of(ranges).view(np.uint32).astype(np.int64)
     ln = rr[:, 1] - rr[:, 0]
-    grp = np.where(ln == 0, -2, np.where(ln == 1, -1, np.floor(np.log2(np.maximum(ln - 1, 1))))).astype(np.int64)
-    assert np.array_equal(o, np.lexsort((np.arange(rr.shape[0]), -grp)))
+    x = np.maximum(ln - 1, 1)
+    m = np.array([int(v).bit_length() - 1 for v in x])
+    q = np.where(m >= 2, (x >> np.maximum(m - 2, 0)) & 3, (x << np.maximum(2 - m, 0)) & 3)
+    heavy = m * 4 + q                   # larger: longer
+    heavy = np.where(ln == 1, -1, np.where(ln == 0, -2, heavy))
+    assert np.array_equal(o, np.lexsort((np.arange(rr.shape[0]), -heavy)))
     gpu_bin.order = order
     return np_of(keys[:k]).view(np.uint64), np_of(vals[:k]).view(np.uint32), np_of(ranges).view(np.uint32), vals, ranges
 
