@@ -10,30 +10,30 @@
 // CTA, each group with its own named barrier and slice of the staging
 // buffer.  Groups are issued in the heavy-first tile order produced by the
 // binning, so the longest lists start first (the GPU counterpart of the
-// paper's subtile streaming, Sec. 5.2).  Warps cover 8x4 pixel blocks.  A
-// tile's sorted list is staged through shared memory in batches of 768
-// records in the forward (4 CTAs per SM; one dummy slot per 32 records) and
-// 512 in the backward; each warp then builds a bit mask of the staged
-// Gaussians whose pixel box meets its block (one box test and one ballot per
-// 32 entries) and visits only those, three at a time in the forward (their
-// alphas are independent; the blends then run in order without branches; a
-// slot past the word's last entry reads the word's dummy).  The alpha of a
+// paper's subtile streaming, Sec. 5.2).  Warps cover 8x4 pixel blocks.  The
+// forward stages a tile's sorted list through shared memory in batches of
+// 768 records (4 CTAs per SM; one dummy slot per 32 records); the thread
+// that stages an entry also marks the warp blocks its alpha >= alpha_min
+// ellipse meets (block bits), each warp builds from those bits a mask of the
+// entries it may blend and visits only them, three at a time (their alphas
+// are independent; the blends then run in order without branches; a slot
+// past the word's last entry reads the word's dummy).  The alpha of a
 // fragment is one FMA and one ex2: op e^(-q/2) = 2^(log2 op - q log2(e)/2),
 // with q = d.(Q d) and log2 op staged per entry.  The forward also records,
-// per warp and run of 32 list entries, the entries it blended (the blend
+// per pixel and run of 32 list entries, the entries it blended (the blend
 // masks).
 //
 // Entry-parallel (both strides >= 2): see the section of that name below.
 //
-// The pixel-parallel backward visits, per warp, the entries the forward's
-// blend masks name (else those whose pixel box meets the block), walks each
-// pixel's blended fragments in reverse from the forward's last position,
-// recovering T_k by division (Eq. 5), and merges the per-pixel gradients of
-// each Gaussian across the warp with a reduce-scatter butterfly (each level
-// halves the fields a lane carries: 9 shuffles for 6 fields, 16 for 10,
-// instead of 5 per field), after which 8 or 16 lanes add distinct fields
-// into the tile's shared-memory accumulators at once; one global atomic per
-// (Gaussian, tile, field) follows.  This replaces the paper's Gradient
+// The backward, given the blend masks, runs every 8x4 warp block as its own
+// one-warp CTA: it visits the entries one of its pixels blended, takes each
+// lane's decision from the lane's own mask bit, walks the fragments in
+// reverse recovering T_k by division (Eq. 5), and merges the per-pixel
+// gradients of each Gaussian across the warp with a reduce-scatter
+// butterfly (each level halves the fields a lane carries) before one global
+// atomic per (Gaussian, warp, field).  Without masks a CTA per tile stages
+// the list, visits the entries whose pixel box meets each warp's block and
+// sums the warps in shared memory first.  This replaces the paper's Gradient
 // Merging Unit (Sec. 5.3).
 #include <algorithm>
 
@@ -983,9 +983,9 @@ __device__ __forceinline__ void back_pair(BackState& S, const RunStage& R, int k
 // pixels 32 w .. 32 w + 31 in row-major order, the masks in the
 // entry-parallel forward's pixel-major layout, whose words past a pixel's
 // stopping batch were never written: each lane keeps only the bits before
-// its own last blended position.  The warp
-// walks its runs of 32 list entries from the last one holding an entry one
-// of its pixels blended back to the first.  Per run it stages only those
+// its own last blended position.  The warp walks its runs of 32 list
+// entries from the last one holding an entry one of its pixels blended back
+// to the first.  Per run it stages only those
 // entries, one lane each (the record alone: no box, which the masks make
 // unnecessary), the last first, then evaluates them back to front, 2 NP at
 // a time in packed pairs; a lane's fragment counts when its own mask bit
