@@ -936,8 +936,7 @@ def run_ours(args):
                 bufs[1 - b][1].copy_(tdep_h, non_blocking=True)
                 ready[i + 1].record(copy_stream)
         runs[b]()
-        out_h[:6].copy_(rast.pose, non_blocking=True)
-        out_h[6:].copy_(rast.dimg["loss"], non_blocking=True)
+        out_h.copy_(rast.result, non_blocking=True)  # pose gradient and loss, one copy
         if i + 1 < Ke:
             main.wait_event(ready[i + 1])
         ev2[i][1].record()

@@ -29,7 +29,10 @@ class Rasterizer:
         self.vals = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
         self.n_keys = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.grad2d = torch.empty((self.n, gs.GRAD2D_STRIDE), device=self.device)
-        self.pose = torch.zeros(6, dtype=torch.float64, device=self.device)
+        # the pose gradient (6 doubles) and the loss side by side, so that a
+        # step's result reads back in one copy (`result`)
+        self.result = torch.zeros(7, dtype=torch.float64, device=self.device)
+        self.pose = self.result[:6]
         self.score = torch.empty((self.n, 2), device=self.device)
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
         self._ws_sort = None
@@ -53,7 +56,7 @@ class Rasterizer:
                     "last_idx": torch.empty((Hs, Ws), dtype=torch.int32, device=d),
                     "n_blended": torch.empty((Hs, Ws), dtype=torch.int32, device=d)}
         self.dimg = {"d_rgb": torch.empty((3, Hs, Ws), device=d), "d_depth": torch.empty((Hs, Ws), device=d),
-                     "loss": torch.zeros(1, dtype=torch.float64, device=d)}
+                     "loss": self.result[6:7]}
         self._ws_sort = None
         self._ws_pb = None
 
