@@ -20,6 +20,10 @@ class Rasterizer:
         self.cfg = cfg if cfg is not None else gs.default_config()
         self.rec_dtype = rec_dtype
         self.device = torch.device(device)
+        # the pose gradient (6 doubles) and the loss side by side, so that a
+        # step's result reads back in one copy (`result`)
+        self.result = torch.zeros(7, dtype=torch.float64, device=self.device)
+        self.pose = self.result[:6]
         self.set_grid(cam)
         words = gs.SPLAT_WORDS[rec_dtype]
         dt = torch.float32 if rec_dtype == gs.GS_F32 else torch.int32
@@ -29,10 +33,6 @@ class Rasterizer:
         self.vals = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
         self.n_keys = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.grad2d = torch.empty((self.n, gs.GRAD2D_STRIDE), device=self.device)
-        # the pose gradient (6 doubles) and the loss side by side, so that a
-        # step's result reads back in one copy (`result`)
-        self.result = torch.zeros(7, dtype=torch.float64, device=self.device)
-        self.pose = self.result[:6]
         self.score = torch.empty((self.n, 2), device=self.device)
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
         self._ws_sort = None

@@ -47,3 +47,18 @@ def test_footprint_grows_with_map_and_resolution():
     assert a < b and a < c
     # 16 of the largest sessions fit the 150 GB budget of the serving workload
     assert 16 * Session.footprint_bytes(SessionSpec(0, 1_500_000, 1200, 680, 984.0, 10, 1)) < 150 << 30
+
+
+def test_rasterizer_result_buffer_holds_pose_gradient_and_loss():
+    """The rasterizer's pose gradient and loss are views of one 7-double
+    buffer (read back in one copy), also after the grid changes."""
+    import torch
+    from paper_2510_06644_gb300.pipeline import Rasterizer
+    from synth import scenes as S
+    cam = S.camera(96, 72, 100.0)
+    r = Rasterizer(100, cam, device="cpu")
+    for c in (cam, dict(cam, sx=2, sy=2)):
+        r.set_grid(c)
+        assert r.pose.data_ptr() == r.result.data_ptr() and r.pose.numel() == 6
+        assert r.dimg["loss"].data_ptr() == r.result.data_ptr() + 6 * 8 and r.dimg["loss"].numel() == 1
+        assert r.result.dtype == torch.float64
