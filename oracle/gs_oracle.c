@@ -444,6 +444,29 @@ typedef struct {
     double T;         /* transmittance before this fragment */
 } or_frag;
 
+/* Integer box test of reading new-1: is pixel (px, py) inside
+ * [floor(u) - r, floor(u) + r] x [floor(v) - r, floor(v) + r]?  The floors
+ * are integer decisions that a float32 mean can take the other way when u or
+ * v lies within its rounding of an integer, so *amb is set when flooring
+ * u -+ d and v -+ d (d = 1e-5 max(1, |u|), likewise for v) does not decide
+ * the inclusion the same way in all four combinations. */
+static int in_box(double u, double v, int64_t r, int64_t px, int64_t py, int* amb) {
+    u = u < -1e9 ? -1e9 : (u > 1e9 ? 1e9 : u);
+    v = v < -1e9 ? -1e9 : (v > 1e9 ? 1e9 : v);
+    const double du = 1e-5 * fmax(1.0, fabs(u)), dv = 1e-5 * fmax(1.0, fabs(v));
+    const int64_t xs[2] = {(int64_t)floor(u - du), (int64_t)floor(u + du)};
+    const int64_t ys[2] = {(int64_t)floor(v - dv), (int64_t)floor(v + dv)};
+    const int64_t xi = (int64_t)floor(u), yi = (int64_t)floor(v);
+    const int in = !(px < xi - r || px > xi + r || py < yi - r || py > yi + r);
+    *amb = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const int ib = !(px < xs[a] - r || px > xs[a] + r || py < ys[b] - r || py > ys[b] + r);
+            if (ib != in) *amb = 1;
+        }
+    return in;
+}
+
 /* Per-pixel compositing of an ordered candidate list (Eq. 2, Eq. 3).
  * Readings: the pixel centre is (px + 0.5, py + 0.5) in full-resolution
  * pixels; a candidate outside the Gaussian's integer box is not a fragment
@@ -452,6 +475,9 @@ typedef struct {
  * skipped; if T (1 - alpha) < t_eps the ray stops before this fragment is
  * blended (early termination, Eq. 3 note); colour and depth blend with the
  * same weights T alpha; the background enters with weight T_final.
+ * A candidate whose box inclusion is float-decided (in_box's *amb) marks
+ * the pixel marginal if it would blend there (power <= 0, alpha within the
+ * margin of alpha_min or above); the float64 floors decide the fragment.
  * Writes the composited fragments to frags (if not NULL) and returns their
  * count.  *last_pos = list position + 1 of the last composited fragment.
  * margin accumulates whether any predicate was within a relative 1e-4 of its
@@ -470,12 +496,15 @@ static int64_t composite_pixel(const or_splats* s, const or_cfg* cfg, int64_t px
         int64_t r = s->radius[k];
         if (r <= 0) continue;
         double u = s->uv[2 * k], v = s->uv[2 * k + 1];
-        int64_t xi = (int64_t)floor(u < -1e9 ? -1e9 : (u > 1e9 ? 1e9 : u));
-        int64_t yi = (int64_t)floor(v < -1e9 ? -1e9 : (v > 1e9 ? 1e9 : v));
-        if (px < xi - r || px > xi + r || py < yi - r || py > yi + r) continue;
+        int amb;
+        const int in = in_box(u, v, r, px, py, &amb);
+        if (!in && !amb) continue;
         double dx = pxc - u, dy = pyc - v;
         double A = s->conic[3 * k], B = s->conic[3 * k + 1], Cc = s->conic[3 * k + 2];
         double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+        if (amb && power <= 0 && s->opacity[k] * exp(power) >= (1.0 - rel) * cfg->alpha_min)
+            *margin = 1;
+        if (!in) continue;
         if (fabs(power) < 1e-6) *margin = 1;
         if (power > 0) continue;
         double G = exp(power);
@@ -525,17 +554,16 @@ static int cmp_dk(const void* pa, const void* pb) {
 }
 
 /* Candidate list of a pixel by brute force: every Gaussian with radius > 0
- * whose integer box contains the pixel, ordered by (float32 depth bits, id). */
+ * whose integer box contains the pixel (or may, in float32: in_box's *amb),
+ * ordered by (float32 depth bits, id). */
 static int64_t brute_candidates(const or_splats* s, int64_t px, int64_t py, int64_t* cand,
                                 or_dk* scratch) {
     int64_t m = 0;
     for (int64_t k = 0; k < s->n; ++k) {
         int64_t r = s->radius[k];
         if (r <= 0) continue;
-        double u = s->uv[2 * k], v = s->uv[2 * k + 1];
-        int64_t xi = (int64_t)floor(u < -1e9 ? -1e9 : (u > 1e9 ? 1e9 : u));
-        int64_t yi = (int64_t)floor(v < -1e9 ? -1e9 : (v > 1e9 ? 1e9 : v));
-        if (px < xi - r || px > xi + r || py < yi - r || py > yi + r) continue;
+        int amb;
+        if (!in_box(s->uv[2 * k], s->uv[2 * k + 1], r, px, py, &amb) && !amb) continue;
         scratch[m].dbits = f32_bits(s->depth[k]);
         scratch[m].k = k;
         ++m;

@@ -230,6 +230,35 @@ def test_tiled_equals_brute_force(oracle_lib):
     np.testing.assert_array_equal(ga, gb)
 
 
+@pytest.mark.parametrize("tiled", [True, False])
+def test_box_edge_decided_by_floor_is_marginal(oracle_lib, tiled):
+    """The integer box of reading new-1 floors the mean; with v 1e-7 below
+    40 the float64 floor gives rows 33..45 (r = 6) and a float32 mean (40.0)
+    rows 34..46.  Exactly the two edge rows, inside the box's columns, are
+    marked marginal; the float64 floor decides what blends (row 33 blends,
+    row 46 does not).  A mean far from an integer marks nothing."""
+    O = oracle_lib
+    cam = S.camera(64, 64, 60.0)
+    sig2 = 16.0
+
+    def one(v):
+        return {"uv": np.array([[32.5, v]]), "conic": np.array([[1 / sig2, 0.0, 1 / sig2]]),
+                "opacity": np.array([0.9]), "rgb": np.array([[0.2, 0.5, 0.8]]),
+                "depth": np.array([3.0]), "radius": np.array([6])}
+
+    img = O.render_fwd(one(40.0 - 1e-7), cam, tiled=tiled)
+    want = np.zeros((64, 64), np.uint8)
+    want[[33, 46], 26:39] = 1
+    np.testing.assert_array_equal(img["margin"], want)
+    assert np.all(img["nfrag"][33, 26:39] == 1) and np.all(img["nfrag"][46, 26:39] == 0)
+    # the blended pixels follow Eq. 2 with the float64 box
+    a = 0.9 * np.exp(-((np.arange(26, 39) + 0.5 - 32.5) ** 2 + (33.5 - 40.0 + 1e-7) ** 2) / (2 * sig2))
+    np.testing.assert_allclose(img["rgb"][1, 33, 26:39], 0.5 * a, rtol=1e-12)
+    ctrl = O.render_fwd(one(40.3), cam, tiled=tiled)
+    assert ctrl["margin"].sum() == 0
+    assert ctrl["nfrag"].sum() == 13 * 13
+
+
 def test_alpha_aware_tiles_lose_no_fragment(oracle_lib):
     """The tile lists leave out a Gaussian only where it cannot reach
     alpha_min (reading new-2): every (pixel, Gaussian) pair whose float64
