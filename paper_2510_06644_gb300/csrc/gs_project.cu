@@ -214,8 +214,8 @@ static inline int64_t pb_blocks(int64_t n, int per) { return (n + per * PB_THREA
 // significant bits): additions are an error-free two-sum of the high parts
 // (Knuth) plus the low parts, renormalised with a fast two-sum (Dekker), in
 // float32 because GB300's float64 rate is a small fraction of it; the last
-// block sums the blocks' pairs the same way and merges the 32 lane sums in
-// compensated float64 (Neumaier).
+// block sums the blocks' pairs the same way, merges its 32 lane sums in a
+// butterfly of pair additions and returns hi + lo as a float64.
 // Fixed operation order throughout, so the reduction is deterministic.
 struct DF {
     float hi, lo;
@@ -243,20 +243,18 @@ struct MergeDF {
 // ---------------------------------------------------------------------------
 // Pose step: Adam on xi, then T <- exp(xi^) T
 // ---------------------------------------------------------------------------
-__device__ void pose_adam_exp(float* __restrict__ pose, const double* __restrict__ grad, float* __restrict__ adam,
-                              float lr_t, float lr_r, float b1, float b2, float eps) {
-    const float step = adam[12] + 1.f;
-    adam[12] = step;
+// Adam on component i of xi: its moments (m, v) are updated in place; returns
+// the step xi_i (rho: lr_t, phi: lr_r).
+__device__ __forceinline__ float pose_adam_component(int i, float g, float& m, float& v, float step, float lr_t,
+                                                     float lr_r, float b1, float b2, float eps) {
     const float c1 = 1.f - powf(b1, step), c2 = 1.f - powf(b2, step);
-    float xi[6];
-    for (int i = 0; i < 6; ++i) {
-        const float g = (float)grad[i];
-        const float m = b1 * adam[i] + (1.f - b1) * g;
-        const float v = b2 * adam[6 + i] + (1.f - b2) * g * g;
-        adam[i] = m;
-        adam[6 + i] = v;
-        xi[i] = -(i < 3 ? lr_t : lr_r) * (m / c1) / (sqrtf(v / c2) + eps);
-    }
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    return -(i < 3 ? lr_t : lr_r) * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+// T <- exp(xi^) T for a pose (R row-major, t); pose_in may be pose_out.
+__device__ __forceinline__ void pose_exp_apply(const float* xi, const float* pose_in, float* pose_out) {
     // exp of (rho, phi): R_d = Rodrigues(phi), V = I + (1-cos)/th^2 K + (th-sin)/th^3 K^2
     const float px = xi[3], py = xi[4], pz = xi[5];
     const float th2 = px * px + py * py + pz * pz, th = sqrtf(th2);
@@ -280,79 +278,101 @@ __device__ void pose_adam_exp(float* __restrict__ pose, const double* __restrict
         V[i] = I + B * K[i] + Cc * K2[i];
     }
     float R[9], t[3], Rn[9], tn[3];
-    for (int i = 0; i < 9; ++i) R[i] = pose[i];
-    for (int i = 0; i < 3; ++i) t[i] = pose[9 + i];
+    for (int i = 0; i < 9; ++i) R[i] = pose_in[i];
+    for (int i = 0; i < 3; ++i) t[i] = pose_in[9 + i];
     for (int i = 0; i < 3; ++i) {
         for (int j = 0; j < 3; ++j) Rn[3 * i + j] = Rd[3 * i] * R[j] + Rd[3 * i + 1] * R[3 + j] + Rd[3 * i + 2] * R[6 + j];
         tn[i] = Rd[3 * i] * t[0] + Rd[3 * i + 1] * t[1] + Rd[3 * i + 2] * t[2] +
                 V[3 * i] * xi[0] + V[3 * i + 1] * xi[1] + V[3 * i + 2] * xi[2];
     }
-    for (int i = 0; i < 9; ++i) pose[i] = Rn[i];
-    for (int i = 0; i < 3; ++i) pose[9 + i] = tn[i];
+    for (int i = 0; i < 9; ++i) pose_out[i] = Rn[i];
+    for (int i = 0; i < 3; ++i) pose_out[9 + i] = tn[i];
+}
+
+// The pose step by one block (every thread calls it, at least 6 of them):
+// thread i < 6 takes component i of the Adam step, thread 0 the exp map.
+// g6 = dL/dxi; the moments and step count are read from adam_in and written
+// to adam_out, the pose read from pose_in and written to pose_out (in and out
+// may be the same memory).  Not inlined, so that the separate pose update and
+// the one fused into the backward projection run the same code.
+__device__ __noinline__ void pose_step_block(const double* g6, const float* adam_in, float* adam_out,
+                                             const float* pose_in, float* pose_out, float lr_t, float lr_r,
+                                             float b1, float b2, float eps) {
+    __shared__ float s_xi[6];
+    const int i = threadIdx.x;
+    const float step = adam_in[12] + 1.f;
+    if (i < 6) {
+        float m = adam_in[i], v = adam_in[6 + i];
+        s_xi[i] = pose_adam_component(i, (float)g6[i], m, v, step, lr_t, lr_r, b1, b2, eps);
+        adam_out[i] = m;
+        adam_out[6 + i] = v;
+    }
+    __syncthreads();
+    if (i == 0) {
+        adam_out[12] = step;
+        pose_exp_apply(s_xi, pose_in, pose_out);
+    }
 }
 
 __global__ void k_pose_update(float* __restrict__ pose, const double* __restrict__ grad, float* __restrict__ adam,
                               float lr_t, float lr_r, float b1, float b2, float eps) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    pose_adam_exp(pose, grad, adam, lr_t, lr_r, b1, b2, eps);
-}
-
-// Compensated float64 sum (Neumaier): s + c is the running value, c the
-// accumulated rounding errors of the additions into s.
-struct CD {
-    double s, c;
-};
-
-__device__ __forceinline__ CD cd_add(CD a, double x) {
-    const double t = a.s + x;
-    const double e = fabs(a.s) >= fabs(x) ? (a.s - t) + x : (x - t) + a.s;
-    return CD{t, a.c + e};
-}
-
-// Two compensated sums combined: the error of adding the two main parts
-// (an error-free two-sum) joins both compensation terms.
-__device__ __forceinline__ CD cd_merge(CD a, CD b) {
-    const double t = a.s + b.s;
-    const double bp = t - a.s;
-    const double e = (a.s - (t - bp)) + (b.s - bp);
-    return CD{t, (a.c + b.c) + e};
+    pose_step_block(grad, adam, adam, pose, pose, lr_t, lr_r, b1, b2, eps);
 }
 
 // Final combination of the per-block pose partials (float32 pairs) by the
 // last block to finish (no spin: the block that takes the last ticket sees
-// every other block's partial, published before its ticket): warp w < 6 sums
-// component w, each lane its strided share of the blocks as a float32 pair
-// (float64 would make this block the kernel's tail: GB300 runs float64 at a
-// small fraction of the float32 rate), then the 32 lane sums meet in a fixed
-// butterfly of compensated float64 merges.
+// every other block's partial, published before its ticket).  Warp w < 6 sums
+// component w, each lane its strided share of the blocks (16 loads in flight
+// before the dependent additions), then the 32 lane sums meet in a fixed
+// butterfly of pair additions; warp 7 meanwhile reads the pose step's inputs.
+// float64 appears only in the result: on GB300 a float64 butterfly took
+// 2.7 us of this block's tail, the pairs a small fraction of it.
 __device__ void pose_final_last_block(const float2* __restrict__ part, int nblk, double* __restrict__ out,
                                       unsigned int* __restrict__ ticket, const gs_pose_step& step) {
+    static_assert(PB_THREADS >= 256, "the last block uses warps 0-5 and 7");
     __shared__ bool s_last;
+    __shared__ float s_pose[12], s_adam[13];
+    __shared__ double s_g[6];
     __threadfence();
+    __syncwarp();  // lanes 0-5 of warp 0 wrote the partials: their fences precede the ticket
     if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)nblk - 1u);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (step.pose && w == 7) {
+        if (lane < 12) s_pose[lane] = step.pose[lane];
+        else if (lane < 25) s_adam[lane - 12] = step.adam[lane - 12];
+    }
     if (w < 6) {
         DF d{0.f, 0.f};
-        for (int b = lane; b < nblk; b += 32) {
-            const float2 v = __ldcg(part + (size_t)b * 6 + w);
-            d = df_add(d, DF{v.x, v.y});
+        for (int b0 = lane; b0 < nblk; b0 += 16 * 32) {
+            float2 v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int b = b0 + 32 * j;
+                v[j] = b < nblk ? __ldcg(part + (size_t)b * 6 + w) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (b0 + 32 * j < nblk) d = df_add(d, DF{v[j].x, v[j].y});
         }
-        CD s = cd_add(CD{(double)d.hi, 0.0}, (double)d.lo);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const CD t{__shfl_xor_sync(0xffffffffu, s.s, o), __shfl_xor_sync(0xffffffffu, s.c, o)};
-            s = (lane & o) ? cd_merge(t, s) : cd_merge(s, t);  // the same operand order on both partners
+            const DF t{__shfl_xor_sync(0xffffffffu, d.hi, o), __shfl_xor_sync(0xffffffffu, d.lo, o)};
+            d = (lane & o) ? df_add(t, d) : df_add(d, t);  // the same operand order on both partners
         }
-        if (lane == 0) out[w] = s.s + s.c;
+        if (lane == 0) {
+            const double g = (double)d.hi + (double)d.lo;
+            out[w] = g;
+            s_g[w] = g;
+        }
     }
     if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
     if (step.pose) {  // the fused pose step (every block has read the pose by now)
         __syncthreads();
-        if (threadIdx.x == 0)
-            pose_adam_exp(step.pose, out, step.adam, step.lr_trans, step.lr_rot, step.beta1, step.beta2, step.eps);
+        pose_step_block(s_g, s_adam, step.adam, s_pose, step.pose, step.lr_trans, step.lr_rot, step.beta1,
+                        step.beta2, step.eps);
     }
 }
 
@@ -393,14 +413,21 @@ __device__ __forceinline__ void project_bwd_body(gs_camera cam, const gs_config&
             for (int i = 0; i < 4; ++i) q[i] = __ldg(g.quats + 4 * k + i);
             const float ol = __ldg(g.opacity_logit + k);
             const bool masked = g.mask && __ldg(g.mask + k);
+            // With the pose reduced (a latency-bound launch of one wave) the
+            // 2D gradient is read with the parameters, so the two loads'
+            // latencies overlap instead of following the projection (grad2d
+            // holds n rows; the values count only for a visible Gaussian).
+            // Otherwise it is read after it, keeping fewer values live.
+            const float4* g4 = reinterpret_cast<const float4*>(grad2d) + 3 * k;
+            float4 ga, gb, gc;
+            if (WANT_POSE) { ga = __ldg(g4); gb = __ldg(g4 + 1); gc = __ldg(g4 + 2); }
             Proj o;
             o.visible = false;
             if (!masked) project_core(cam, cfg, mu, ls, q, ol, o);
             float gmu[3] = {0, 0, 0}, gls[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gol = 0.f, grgb[3] = {0, 0, 0};
             float t_mu = 0.f, t_sig = 0.f;
-            const float4* g4 = reinterpret_cast<const float4*>(grad2d) + 3 * k;
             if (o.visible) {
-                const float4 ga = __ldg(g4), gb = __ldg(g4 + 1), gc = __ldg(g4 + 2);
+                if (!WANT_POSE) { ga = __ldg(g4); gb = __ldg(g4 + 1); gc = __ldg(g4 + 2); }
                 const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, gop = gb.y, gd = gb.z;
                 grgb[0] = gc.x; grgb[1] = gc.y; grgb[2] = gc.z;
                 const float x = o.p[0], y = o.p[1], z = o.p[2];
@@ -495,24 +522,16 @@ __device__ __forceinline__ void project_bwd_body(gs_camera cam, const gs_config&
                     pose[3] = y * gp2 - z * gp1;
                     pose[4] = z * gp0 - x * gp2;
                     pose[5] = x * gp1 - y * gp0;
-                    // <Gc, [e_i]x S - S [e_i]x> for the symmetric Gc and S
-                    // [e_x]x S - S [e_x]x etc. written out entrywise
+                    // <Gc, [e_i]x S - S [e_i]x>: for the symmetric Gc and S it
+                    // is tr([e_i]x (W - W^T)) with W = S Gc, i.e.
+                    // 2 (W_jk - W_kj) for (i, j, k) a cyclic order of (0, 1, 2)
                     const float* Sm = o.Sc;
-                    // D = E S - S E;  sum_ij Gc_ij D_ij
-                    for (int e = 0; e < 3; ++e) {
-                        float E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-                        if (e == 0) { E[5] = -1.f; E[7] = 1.f; }
-                        if (e == 1) { E[2] = 1.f; E[6] = -1.f; }
-                        if (e == 2) { E[1] = -1.f; E[3] = 1.f; }
-                        float s = 0.f;
-                        for (int i = 0; i < 3; ++i)
-                            for (int j = 0; j < 3; ++j) {
-                                float es = E[3 * i] * Sm[j] + E[3 * i + 1] * Sm[3 + j] + E[3 * i + 2] * Sm[6 + j];
-                                float se = Sm[3 * i] * E[j] + Sm[3 * i + 1] * E[3 + j] + Sm[3 * i + 2] * E[6 + j];
-                                s += Gc[3 * i + j] * (es - se);
-                            }
-                        pose[3 + e] += s;
-                    }
+                    auto Wij = [&](int i, int j) {
+                        return Sm[3 * i] * Gc[j] + Sm[3 * i + 1] * Gc[3 + j] + Sm[3 * i + 2] * Gc[6 + j];
+                    };
+                    pose[3] += 2.f * (Wij(1, 2) - Wij(2, 1));
+                    pose[4] += 2.f * (Wij(2, 0) - Wij(0, 2));
+                    pose[5] += 2.f * (Wij(0, 1) - Wij(1, 0));
                 }
             } else if (!masked && WANT_GRADS) {
                 // rgb gradient is independent of visibility only through grad2d,
