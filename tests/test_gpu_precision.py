@@ -1,8 +1,8 @@
 """Precision form (16-bit record storage): conic, opacity and colour stored as
 bf16 or fp16, means, depths and radii in float32, all compositing and
 accumulation in float32; the pose-gradient sum over all Gaussians is carried
-as float32 pairs (error-free two-sums) inside each block and summed across
-blocks in compensated float64.  Each output's error against the FP64 oracle is measured and printed
+as float32 pairs (error-free two-sums) inside each block and across blocks,
+and returned as float64.  Each output's error against the FP64 oracle is measured and printed
 (`pytest -s`), and bounded by a figure derived from the storage precision:
 
   u = unit roundoff of the storage type (bf16 2^-8, fp16 2^-11).  Colour and
