@@ -100,8 +100,10 @@ __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int n
     const int per = (nrows + CS_GROUPS - 1) / CS_GROUPS;
     const int r0 = min(nrows, ty * per), r1 = min(nrows, r0 + per);
     // rows in groups of 8 loads issued back to back (a dependent sum per
-    // load would wait out an L2 round trip per row)
-    uint32_t sum = 0;
+    // load would wait out an L2 round trip per row); the first group stays
+    // in registers for the prefix pass (the only group when a thread has at
+    // most 8 rows: up to 1024 rows)
+    uint32_t sum = 0, v0[8];
     if (t < ntiles)
         for (int r = r0; r < r1; r += 8) {
             uint32_t v[8];
@@ -109,6 +111,10 @@ __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int n
             for (int k = 0; k < 8; ++k) v[k] = r + k < r1 ? __ldcg(hist + (size_t)(r + k) * ntiles + t) : 0u;
 #pragma unroll
             for (int k = 0; k < 8; ++k) sum += v[k];
+            if (r == r0) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v0[k] = v[k];
+            }
         }
     part[ty][tx] = sum;
     __syncthreads();
@@ -143,7 +149,8 @@ __device__ __forceinline__ void col_scan_body(uint32_t* __restrict__ hist, int n
         for (int r = r0; r < r1; r += 8) {
             uint32_t v[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = r + k < r1 ? __ldcg(hist + (size_t)(r + k) * ntiles + t) : 0u;
+            for (int k = 0; k < 8; ++k)
+                v[k] = r == r0 ? v0[k] : (r + k < r1 ? __ldcg(hist + (size_t)(r + k) * ntiles + t) : 0u);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 if (r + k < r1) {
@@ -207,9 +214,12 @@ __device__ __forceinline__ void tile_scan_body(const uint32_t* __restrict__ coun
     __shared__ u64 s_warp[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     u64 carry = 0;
+    // each chunk's counts are loaded while the previous chunk is scanned
+    u64 v_nx = (int)threadIdx.x < ntiles ? (u64)__ldcg(count + threadIdx.x) : 0ull;
     for (int base = 0; base < ntiles; base += 1024) {
         const int t = base + threadIdx.x;
-        const u64 v = t < ntiles ? (u64)__ldcg(count + t) : 0ull;
+        const u64 v = v_nx;
+        v_nx = t + 1024 < ntiles ? (u64)__ldcg(count + t + 1024) : 0ull;
         u64 x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
