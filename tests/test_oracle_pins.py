@@ -230,33 +230,143 @@ def test_tiled_equals_brute_force(oracle_lib):
     np.testing.assert_array_equal(ga, gb)
 
 
+def one_splat(u, v, op, sig2, radius, depth=3.0):
+    """One isotropic 2D Gaussian as projected splats (conic 1 / sig2)."""
+    return {"uv": np.array([[u, v]], np.float64), "conic": np.array([[1 / sig2, 0.0, 1 / sig2]]),
+            "opacity": np.array([op]), "rgb": np.array([[0.2, 0.5, 0.8]]), "depth": np.array([depth]),
+            "radius": np.array([radius])}
+
+
 @pytest.mark.parametrize("tiled", [True, False])
-def test_box_edge_decided_by_floor_is_marginal(oracle_lib, tiled):
-    """The integer box of reading new-1 floors the mean; with v 1e-7 below
-    40 the float64 floor gives rows 33..45 (r = 6) and a float32 mean (40.0)
-    rows 34..46.  Exactly the two edge rows, inside the box's columns, are
-    marked marginal; the float64 floor decides what blends (row 33 blends,
-    row 46 does not).  A mean far from an integer marks nothing."""
+@pytest.mark.parametrize("u,v,axis,edges", [
+    (32.5, 40.0 - 1e-7, "y", (33, 46)),   # floor 39 in float64, 40 in float32
+    (32.5, 40.0 + 1e-7, "y", (33, 46)),   # floor 40, 39 a rounding away
+    (32.0 + 1e-7, 40.3, "x", (25, 38)),   # floor 32, 31 a rounding away
+    (32.0 - 1e-7, 40.3, "x", (25, 38)),   # floor 31, 32 in float32
+])
+def test_box_edge_decided_by_floor_is_marginal(oracle_lib, tiled, u, v, axis, edges):
+    """The integer box of reading new-1 floors the mean (r = 6).  A mean
+    within a rounding of an integer puts the box's two edge lines (rows or
+    columns) on either side of the decision: exactly those pixels, inside the
+    other axis's extent, are marked marginal; the float64 floor decides what
+    blends.  A mean far from an integer marks nothing, nor does an ambiguous
+    edge where the Gaussian does not reach alpha_min."""
     O = oracle_lib
     cam = S.camera(64, 64, 60.0)
-    sig2 = 16.0
-
-    def one(v):
-        return {"uv": np.array([[32.5, v]]), "conic": np.array([[1 / sig2, 0.0, 1 / sig2]]),
-                "opacity": np.array([0.9]), "rgb": np.array([[0.2, 0.5, 0.8]]),
-                "depth": np.array([3.0]), "radius": np.array([6])}
-
-    img = O.render_fwd(one(40.0 - 1e-7), cam, tiled=tiled)
+    img = O.render_fwd(one_splat(u, v, 0.9, 16.0, 6), cam, tiled=tiled)
+    xi, yi = math.floor(u), math.floor(v)
     want = np.zeros((64, 64), np.uint8)
-    want[[33, 46], 26:39] = 1
+    if axis == "y":
+        want[list(edges), xi - 6:xi + 7] = 1
+        inside = [e for e in edges if yi - 6 <= e <= yi + 6]
+        outside = [e for e in edges if e not in inside]
+        assert len(inside) == 1 and np.all(img["nfrag"][inside[0], xi - 6:xi + 7] == 1)
+        assert np.all(img["nfrag"][outside[0], :] == 0)
+    else:
+        want[yi - 6:yi + 7, list(edges)] = 1
+        inside = [e for e in edges if xi - 6 <= e <= xi + 6]
+        outside = [e for e in edges if e not in inside]
+        assert len(inside) == 1 and np.all(img["nfrag"][yi - 6:yi + 7, inside[0]] == 1)
+        assert np.all(img["nfrag"][:, outside[0]] == 0)
     np.testing.assert_array_equal(img["margin"], want)
-    assert np.all(img["nfrag"][33, 26:39] == 1) and np.all(img["nfrag"][46, 26:39] == 0)
     # the blended pixels follow Eq. 2 with the float64 box
-    a = 0.9 * np.exp(-((np.arange(26, 39) + 0.5 - 32.5) ** 2 + (33.5 - 40.0 + 1e-7) ** 2) / (2 * sig2))
-    np.testing.assert_allclose(img["rgb"][1, 33, 26:39], 0.5 * a, rtol=1e-12)
-    ctrl = O.render_fwd(one(40.3), cam, tiled=tiled)
-    assert ctrl["margin"].sum() == 0
-    assert ctrl["nfrag"].sum() == 13 * 13
+    a = 0.9 * np.exp(-((np.arange(xi - 6, xi + 7) + 0.5 - u) ** 2 + (yi + 0.5 - v) ** 2) / 32.0)
+    np.testing.assert_allclose(img["rgb"][1, yi, xi - 6:xi + 7], 0.5 * a, rtol=1e-12)
+    ctrl = O.render_fwd(one_splat(32.5, 40.3, 0.9, 16.0, 6), cam, tiled=tiled)
+    assert ctrl["margin"].sum() == 0 and ctrl["nfrag"].sum() == 13 * 13
+    # sigma 2: alpha at the edge rows <= 0.5 exp(-6.5^2 / 8) < 1/255
+    faint = O.render_fwd(one_splat(u, v, 0.5, 4.0, 6), cam, tiled=tiled)
+    assert faint["margin"].sum() == 0
+
+
+def test_margin_windows(oracle_lib):
+    """The oracle marks a pixel marginal where float32 and float64 may take a
+    predicate apart: alpha within a relative 1e-4 of alpha_min or alpha_max,
+    the exponent within 1e-6 of 0, the transmittance after a fragment within
+    a relative 1e-4 of t_eps.  Each case places exactly known pixels inside
+    the window (sigma^2 = 16, radius 8, so alpha_min is never approached
+    elsewhere) and checks that only they are marked."""
+    O = oracle_lib
+    cam = S.camera(64, 64, 60.0)
+    amin, amax = 1 / 255, 0.99
+    def run(sp):
+        return O.render_fwd(sp, cam)["margin"]
+    def only(*pix):
+        m = np.zeros((64, 64), np.uint8)
+        for x, y in pix:
+            m[y, x] = 1
+        return m
+    # alpha_min: pixel offsets (3.2, 0.2) and (0.2, 3.2) from (32.3, 32.3)
+    op = amin * (1 + 5e-5) / math.exp(-(3.2 ** 2 + 0.2 ** 2) / 32)
+    np.testing.assert_array_equal(run(one_splat(32.3, 32.3, op, 16.0, 8)), only((35, 32), (32, 35)))
+    # alpha_max: the pixel at offset (0.2, 0.2)
+    op = amax * (1 - 5e-5) / math.exp(-0.08 / 32)
+    np.testing.assert_array_equal(run(one_splat(32.3, 32.3, op, 16.0, 8)), only((32, 32)))
+    # exponent 0: the mean on the centre of pixel (32, 32)
+    np.testing.assert_array_equal(run(one_splat(32.5, 32.5, 0.5, 16.0, 8)), only((32, 32)))
+    # t_eps: three fronts of alpha a at (32, 32) leave (1 - a)^3 = 1e-4 (1 + 5e-5)
+    a = 1 - (1e-4 * (1 + 5e-5)) ** (1 / 3)
+    op = a / math.exp(-0.08 / 32)
+    three = [one_splat(32.3, 32.3, op, 16.0, 8, depth=d) for d in (2.0, 3.0, 4.0)]
+    sp = {k: np.concatenate([t[k] for t in three]) for k in three[0]}
+    np.testing.assert_array_equal(run(sp), only((32, 32)))
+
+
+def test_ewa_jacobian_clamp_closed_form(oracle_lib):
+    """An isotropic Gaussian (scale s) at camera point (x, 0, z), R = I: the
+    EWA Jacobian is [[f/z, 0, -f t/z], [0, f/z, 0]] with t = x/z clamped to
+    1.3 (W/2)/f (reading c5: inside J only), so Sigma2 = s^2 J J^T + 0.3 I =
+    diag(s^2 f^2 (1 + t^2)/z^2 + 0.3, s^2 f^2/z^2 + 0.3) and the mean
+    projects unclamped to f x/z + W/2.  Likewise on the y axis, with the
+    clamp line 1.3 (H/2)/f."""
+    O = oracle_lib
+    W, H, f, z, s = 64, 48, 80.0, 4.0, 0.05
+    limx, limy = 1.3 * (W / 2) / f, 1.3 * (H / 2) / f   # 0.52, 0.39
+    cam = S.camera(W, H, f)
+    q = s * s * f * f / (z * z)
+    for xz in (0.3, 0.8):
+        pr = O.project(one_gaussian(xz * z, 0.0, z, math.log(s), 2.0, [0.5, 0.5, 0.5]), cam)
+        t = min(xz, limx)
+        np.testing.assert_allclose(pr["conic"][0], [1 / (q * (1 + t * t) + 0.3), 0.0, 1 / (q + 0.3)],
+                                   rtol=1e-12, atol=1e-15)
+        assert math.isclose(pr["uv"][0, 0], f * xz + W / 2, rel_tol=1e-14)
+    for yz in (0.3, 0.8):
+        pr = O.project(one_gaussian(0.0, yz * z, z, math.log(s), 2.0, [0.5, 0.5, 0.5]), cam)
+        t = min(yz, limy)
+        np.testing.assert_allclose(pr["conic"][0], [1 / (q + 0.3), 0.0, 1 / (q * (1 + t * t) + 0.3)],
+                                   rtol=1e-12, atol=1e-15)
+        assert math.isclose(pr["uv"][0, 1], f * yz + H / 2, rel_tol=1e-14)
+
+
+def test_project_rects_match_the_lists(oracle_lib):
+    """or_project's tile rect and count per Gaussian are those of the binning
+    (the same alpha-aware rect, reading new-2): counted from the sorted
+    lists, Gaussian k appears touched[k] times, and its listed tiles span
+    exactly rect[k] = (x0, x1, y0, y1); a Gaussian with no tile (culled, as
+    the one behind the near plane, off-screen, or below alpha_min) has an
+    all-zero rect."""
+    O = oracle_lib
+    g = concat(S.tiny_scene(seed=1200, n=600), one_gaussian(0.0, 0.0, 0.1, -3.0, 0.0, [1, 1, 1]))
+    cam = S.tiny_camera()
+    pr = O.project(g, cam)
+    _, vals, ranges = O.bin_sort(pr, cam)
+    n = len(pr["radius"])
+    assert pr["radius"][-1] == 0
+    cnt = np.bincount(vals.astype(np.int64), minlength=n)
+    np.testing.assert_array_equal(cnt, pr["touched"])
+    _, _, TX, TY = O.grid(cam)
+    lo = np.full((n, 2), 1 << 30)
+    hi = np.full((n, 2), -1)
+    for t in range(TX * TY):
+        b, e = ranges[t]
+        ids = vals[b:e].astype(np.int64)
+        np.minimum.at(lo, ids, [t % TX, t // TX])
+        np.maximum.at(hi, ids, [t % TX, t // TX])
+    listed = cnt > 0
+    assert listed.sum() > 100
+    np.testing.assert_array_equal(pr["rect"][listed], np.stack([lo[listed, 0], hi[listed, 0] + 1,
+                                                                lo[listed, 1], hi[listed, 1] + 1], 1))
+    assert not pr["rect"][~listed].any() and not pr["touched"][~listed].any()
 
 
 def test_alpha_aware_tiles_lose_no_fragment(oracle_lib):
@@ -525,13 +635,25 @@ def small_fd_scene(seed):
     g = S.rng(seed)
     n = 14
     means = np.stack([g.uniform(-0.6, 0.6, n), g.uniform(-0.45, 0.45, n), g.uniform(1.5, 3.0, n)], 1)
-    # one Gaussian beyond the Jacobian clamp line whose footprint still reaches the image
-    means[0] = [0.75 * 2.6, 0.1, 2.6]   # x/z = 0.75 > 1.3 * (W/2)/fx = 0.72
+    # one Gaussian beyond each Jacobian clamp line whose footprint still
+    # reaches the 40x30 image at f = 36 (clamp lines x/z = 1.3 * 20/36 = 0.72,
+    # y/z = 1.3 * 15/36 = 0.54)
+    means[0] = [0.8 * 2.6, 0.1, 2.6]
+    means[1] = [0.1, 0.65 * 2.6, 2.6]
     gs = {"means": means, "log_scales": g.normal(-2.2, 0.25, (n, 3)),
           "quats": S.random_unit_quats(g, n) * g.uniform(0.7, 1.4, (n, 1)),
           "opacity_logit": g.normal(0.5, 1.0, n), "rgb": g.uniform(0, 1, (n, 3))}
     gs["log_scales"][0] = [-0.7, -0.7, -0.7]
+    gs["log_scales"][1] = [-0.7, -0.7, -0.7]
     return gs
+
+
+def assert_beyond_clamp_lines(gs, cam):
+    """Gaussians 0 and 1 of small_fd_scene lie beyond the x and the y clamp
+    line in this camera's frame."""
+    p = gs["means"][:2] @ np.asarray(cam["R"]).T + np.asarray(cam["t"])
+    assert p[0, 0] / p[0, 2] > 1.3 * (cam["W"] / 2) / cam["fx"]
+    assert p[1, 1] / p[1, 2] > 1.3 * (cam["H"] / 2) / cam["fy"]
 
 
 def fd_loss(O, gs, cam, w, wd, cfg=None):
@@ -552,6 +674,7 @@ def test_gradients_match_central_differences(oracle_lib, bg):
     gs = small_fd_scene(21)
     R = S.axis_angle_matrix([0.2, -0.5, 1.0], 0.05)
     cam = S.camera(W, H, 36.0, R=R, t=[0.01, -0.02, 0.05])
+    assert_beyond_clamp_lines(gs, cam)
     cfg = {"bg": bg}
     g = S.rng(22)
     w = g.normal(0, 1, (3, H, W))
@@ -581,8 +704,8 @@ def test_gradients_match_central_differences(oracle_lib, bg):
                 assert abs(fd - a) <= 2e-5 * max(1.0, abs(a)), (key, k, j, fd, a)
                 checked += 1
     assert checked > 150
-    # clamped-Jacobian Gaussian 0 was exercised
-    assert abs(an["means"][0]).sum() > 0
+    # the clamped-Jacobian Gaussians 0 (x) and 1 (y) were exercised
+    assert abs(an["means"][0]).sum() > 0 and abs(an["means"][1]).sum() > 0
 
 
 def pose_perturb(cam, xi):
@@ -604,6 +727,7 @@ def test_pose_gradient_matches_central_differences(oracle_lib, bg):
     W, H = 40, 30
     gs = small_fd_scene(31)
     cam = S.camera(W, H, 36.0, R=S.axis_angle_matrix([1, 0.3, 0.1], 0.04), t=[0.02, 0.01, -0.03])
+    assert_beyond_clamp_lines(gs, cam)
     cfg = {"bg": bg}
     g = S.rng(32)
     w = g.normal(0, 1, (3, H, W))
@@ -746,6 +870,14 @@ def test_loss_hand_values(oracle_lib):
     np.testing.assert_array_equal(np.sign(dr).ravel(), [1, 0, -1, 1, 1, -1])
     np.testing.assert_allclose(np.abs(dr[dr != 0]), 0.9 / 6)
     np.testing.assert_allclose(dd, [[0.1 / 2, 0.0]])
+    # a negative depth residual, an invalid target and a zero residual: the
+    # gradient is sign(r) w / P with P every sampled pixel, sign(0) = 0
+    z = np.zeros((3, 1, 3))
+    L2, dr2, dd2 = O.loss_l1(z, np.array([[1.0, 2.0, 0.5]]), z, np.array([[1.5, 0.0, 0.5]]), w_rgb=0.9,
+                             w_depth=0.1)
+    assert math.isclose(L2, 0.1 * 0.5 / 3, rel_tol=1e-14)
+    assert not dr2.any()
+    np.testing.assert_allclose(dd2, [[-0.1 / 3, 0.0, 0.0]], rtol=1e-14)
 
 
 # ---------------------------------------------------------------------------
@@ -768,6 +900,15 @@ def test_prune_select_hand_case(oracle_lib):
     # cap on the number selected
     m3, c3 = O.prune_select(t_mu, t_sig, np.zeros(7, np.uint8), frac=0.5, max_select=1)
     assert c3 == 1 and m3.tolist() == [0, 0, 0, 0, 1, 0, 0]
+    # the weight multiplies the covariance term: at lambda = 0.5, (0, 5)
+    # scores 2.5, below (3, 0); and both terms add: (9, 6) scores 13.8, above
+    # (5, 0) (all scores non-negative, so their bit patterns order them)
+    m5, _ = O.prune_select(np.array([0, 3], np.float32), np.array([5, 0], np.float32), np.zeros(2, np.uint8),
+                           lam=0.5, frac=0.5)
+    assert m5.tolist() == [1, 0]
+    m6, _ = O.prune_select(np.array([5, 9], np.float32), np.array([0, 6], np.float32), np.zeros(2, np.uint8),
+                           lam=0.8, frac=0.5)
+    assert m6.tolist() == [1, 0]
     # all equal: ids decide
     m4, c4 = O.prune_select(np.ones(10, np.float32), np.ones(10, np.float32), np.zeros(10, np.uint8),
                             frac=0.3)
@@ -789,6 +930,9 @@ def test_interval_schedule(oracle_lib):
     # the paper's literal constants: K0/2 or 2 K0
     assert O.next_interval(7, 0.10, K0=5, literal=True) == 2
     assert O.next_interval(7, 0.01, K0=5, literal=True) == 10
+    # a ratio equal to the threshold does not exceed it: the interval grows
+    assert O.next_interval(8, thr, thr=thr) == 16
+    assert O.next_interval(7, thr, K0=5, thr=thr, literal=True) == 10
 
 
 def test_change_ratio_hand_case(oracle_lib):
@@ -815,6 +959,10 @@ def test_downsample_schedule_table(oracle_lib):
     assert O.downsample_schedule(k, k, True) == (1, 1)
     with pytest.raises(ValueError):
         O.downsample_schedule(12, 10, False, m=3)
+    # a non-keyframe comes after its keyframe
+    for n in (k, k - 1):
+        with pytest.raises(ValueError):
+            O.downsample_schedule(n, k, False)
 
 
 @pytest.mark.parametrize("sx,sy", [(2, 2), (4, 2), (4, 4), (3, 1)])
