@@ -447,24 +447,45 @@ typedef struct {
 /* Integer box test of reading new-1: is pixel (px, py) inside
  * [floor(u) - r, floor(u) + r] x [floor(v) - r, floor(v) + r]?  The floors
  * are integer decisions that a float32 mean can take the other way when u or
- * v lies within its rounding of an integer, so *amb is set when flooring
- * u -+ d and v -+ d (d = 1e-5 max(1, |u|), likewise for v) does not decide
- * the inclusion the same way in all four combinations. */
-static int in_box(double u, double v, int64_t r, int64_t px, int64_t py, int* amb) {
-    u = u < -1e9 ? -1e9 : (u > 1e9 ? 1e9 : u);
-    v = v < -1e9 ? -1e9 : (v > 1e9 ? 1e9 : v);
-    const double du = 1e-5 * fmax(1.0, fabs(u)), dv = 1e-5 * fmax(1.0, fabs(v));
-    const int64_t xs[2] = {(int64_t)floor(u - du), (int64_t)floor(u + du)};
-    const int64_t ys[2] = {(int64_t)floor(v - dv), (int64_t)floor(v + dv)};
+ * v lies within its rounding of an integer: box_window gives that window,
+ * d = 1e-5 max(1, |u|) (likewise for v), and box_float_decided says whether
+ * flooring u -+ d or v -+ d moves a floor.  For such a Gaussian in_box sets
+ * *amb when the four combinations of those floors do not decide the pixel's
+ * inclusion the same way (decided = 0: *amb = 0). */
+static double box_window(double u) { return 1e-5 * fmax(1.0, fabs(u)); }
+
+static double clamp_coord(double u) { return u < -1e9 ? -1e9 : (u > 1e9 ? 1e9 : u); }
+
+static int box_float_decided(double u, double v) {
+    u = clamp_coord(u);
+    v = clamp_coord(v);
+    const double du = box_window(u), dv = box_window(v);
+    return floor(u - du) != floor(u + du) || floor(v - dv) != floor(v + dv);
+}
+
+static int in_box(double u, double v, int64_t r, int64_t px, int64_t py, int decided, int* amb) {
+    u = clamp_coord(u);
+    v = clamp_coord(v);
     const int64_t xi = (int64_t)floor(u), yi = (int64_t)floor(v);
     const int in = !(px < xi - r || px > xi + r || py < yi - r || py > yi + r);
     *amb = 0;
+    if (!decided) return in;
+    const double du = box_window(u), dv = box_window(v);
+    const int64_t xs[2] = {(int64_t)floor(u - du), (int64_t)floor(u + du)};
+    const int64_t ys[2] = {(int64_t)floor(v - dv), (int64_t)floor(v + dv)};
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) {
             const int ib = !(px < xs[a] - r || px > xs[a] + r || py < ys[b] - r || py > ys[b] + r);
             if (ib != in) *amb = 1;
         }
     return in;
+}
+
+/* box_float_decided of every Gaussian (malloc'ed; the caller frees it). */
+static uint8_t* float_decided_boxes(const or_splats* s) {
+    uint8_t* f = (uint8_t*)malloc((size_t)(s->n + 1));
+    for (int64_t k = 0; k < s->n; ++k) f[k] = (uint8_t)box_float_decided(s->uv[2 * k], s->uv[2 * k + 1]);
+    return f;
 }
 
 /* Per-pixel compositing of an ordered candidate list (Eq. 2, Eq. 3).
@@ -475,15 +496,16 @@ static int in_box(double u, double v, int64_t r, int64_t px, int64_t py, int* am
  * skipped; if T (1 - alpha) < t_eps the ray stops before this fragment is
  * blended (early termination, Eq. 3 note); colour and depth blend with the
  * same weights T alpha; the background enters with weight T_final.
- * A candidate whose box inclusion is float-decided (in_box's *amb) marks
- * the pixel marginal if it would blend there (power <= 0, alpha within the
- * margin of alpha_min or above); the float64 floors decide the fragment.
+ * A candidate whose box inclusion is float-decided (in_box's *amb, for the
+ * Gaussians flagged in fdec by box_float_decided) marks the pixel marginal
+ * if it would blend there (power <= 0, alpha within the margin of alpha_min
+ * or above); the float64 floors decide the fragment.
  * Writes the composited fragments to frags (if not NULL) and returns their
  * count.  *last_pos = list position + 1 of the last composited fragment.
  * margin accumulates whether any predicate was within a relative 1e-4 of its
  * threshold (a pixel where FP32 and FP64 may legitimately disagree). */
-static int64_t composite_pixel(const or_splats* s, const or_cfg* cfg, int64_t px, int64_t py,
-                               const int64_t* cand, int64_t ncand, or_frag* frags,
+static int64_t composite_pixel(const or_splats* s, const uint8_t* fdec, const or_cfg* cfg, int64_t px,
+                               int64_t py, const int64_t* cand, int64_t ncand, or_frag* frags,
                                double out_rgb[3], double* out_depth, double* out_T,
                                int64_t* last_pos, int* margin) {
     double T = 1.0, C[3] = {0, 0, 0}, D = 0;
@@ -497,7 +519,7 @@ static int64_t composite_pixel(const or_splats* s, const or_cfg* cfg, int64_t px
         if (r <= 0) continue;
         double u = s->uv[2 * k], v = s->uv[2 * k + 1];
         int amb;
-        const int in = in_box(u, v, r, px, py, &amb);
+        const int in = in_box(u, v, r, px, py, fdec[k], &amb);
         if (!in && !amb) continue;
         double dx = pxc - u, dy = pyc - v;
         double A = s->conic[3 * k], B = s->conic[3 * k + 1], Cc = s->conic[3 * k + 2];
@@ -556,14 +578,14 @@ static int cmp_dk(const void* pa, const void* pb) {
 /* Candidate list of a pixel by brute force: every Gaussian with radius > 0
  * whose integer box contains the pixel (or may, in float32: in_box's *amb),
  * ordered by (float32 depth bits, id). */
-static int64_t brute_candidates(const or_splats* s, int64_t px, int64_t py, int64_t* cand,
+static int64_t brute_candidates(const or_splats* s, const uint8_t* fdec, int64_t px, int64_t py, int64_t* cand,
                                 or_dk* scratch) {
     int64_t m = 0;
     for (int64_t k = 0; k < s->n; ++k) {
         int64_t r = s->radius[k];
         if (r <= 0) continue;
         int amb;
-        if (!in_box(s->uv[2 * k], s->uv[2 * k + 1], r, px, py, &amb) && !amb) continue;
+        if (!in_box(s->uv[2 * k], s->uv[2 * k + 1], r, px, py, fdec[k], &amb) && !amb) continue;
         scratch[m].dbits = f32_bits(s->depth[k]);
         scratch[m].k = k;
         ++m;
@@ -596,16 +618,17 @@ double or_render_fwd(const or_splats* s, const or_cam* cam, const or_cfg* cfg,
     int64_t* cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxc + 1));
     or_dk* scratch = vals ? NULL : (or_dk*)malloc(sizeof(or_dk) * (size_t)(s->n + 1));
     or_frag* frags = (or_frag*)malloc(sizeof(or_frag) * (size_t)(maxc + 1));
+    uint8_t* fdec = float_decided_boxes(s);
     double sig = 0;
     for (int64_t j = 0; j < Hs; ++j)
         for (int64_t i = 0; i < Ws; ++i) {
             int64_t px = i * cam->sx, py = j * cam->sy;
             int64_t nc = vals ? tile_candidates(cam, i, j, vals, ranges, cand)
-                              : brute_candidates(s, px, py, cand, scratch);
+                              : brute_candidates(s, fdec, px, py, cand, scratch);
             double c3[3], d, T;
             int64_t lp;
             int mg = 0;
-            int64_t nf = composite_pixel(s, cfg, px, py, cand, nc, frags, c3, &d, &T, &lp, &mg);
+            int64_t nf = composite_pixel(s, fdec, cfg, px, py, cand, nc, frags, c3, &d, &T, &lp, &mg);
             int64_t pix = j * Ws + i;
             for (int c = 0; c < 3; ++c) rgb[c * P + pix] = c3[c];
             depth[pix] = d;
@@ -619,6 +642,7 @@ double or_render_fwd(const or_splats* s, const or_cam* cam, const or_cfg* cfg,
     free(cand);
     free(scratch);
     free(frags);
+    free(fdec);
     return sig;
 }
 
@@ -685,17 +709,18 @@ void or_render_bwd(const or_splats* s, const or_cam* cam, const or_cfg* cfg,
     int64_t* cand = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxc + 1));
     or_dk* scratch = vals ? NULL : (or_dk*)malloc(sizeof(or_dk) * (size_t)(s->n + 1));
     or_frag* f = (or_frag*)malloc(sizeof(or_frag) * (size_t)(maxc + 1));
+    uint8_t* fdec = float_decided_boxes(s);
     double* SC = (double*)malloc(sizeof(double) * 3 * (size_t)(maxc + 1));
     double* SD = (double*)malloc(sizeof(double) * (size_t)(maxc + 1));
     for (int64_t j = 0; j < Hs; ++j)
         for (int64_t i = 0; i < Ws; ++i) {
             int64_t px = i * cam->sx, py = j * cam->sy;
             int64_t nc = vals ? tile_candidates(cam, i, j, vals, ranges, cand)
-                              : brute_candidates(s, px, py, cand, scratch);
+                              : brute_candidates(s, fdec, px, py, cand, scratch);
             double c3[3], d, Tf;
             int64_t lp;
             int mg = 0;
-            int64_t nf = composite_pixel(s, cfg, px, py, cand, nc, f, c3, &d, &Tf, &lp, &mg);
+            int64_t nf = composite_pixel(s, fdec, cfg, px, py, cand, nc, f, c3, &d, &Tf, &lp, &mg);
             int64_t pix = j * Ws + i;
             double gC[3] = {d_rgb[pix], d_rgb[P + pix], d_rgb[2 * P + pix]};
             double gD = d_depth[pix];
@@ -737,6 +762,7 @@ void or_render_bwd(const or_splats* s, const or_cam* cam, const or_cfg* cfg,
     free(cand);
     free(scratch);
     free(f);
+    free(fdec);
     free(SC);
     free(SD);
 }
