@@ -1,5 +1,6 @@
-"""Host logic of the serving form (no GPU): admission by HBM budget into
-slots, the keyframe/stride schedule of frames, Poisson arrivals."""
+"""Host logic (no GPU) of the serving form -- admission by HBM budget into
+slots, the keyframe/stride schedule of frames, Poisson arrivals -- and of
+the rasterizer's buffers and list-reuse policy."""
 import numpy as np
 import pytest
 
@@ -62,3 +63,54 @@ def test_rasterizer_result_buffer_holds_pose_gradient_and_loss():
         assert r.pose.data_ptr() == r.result.data_ptr() and r.pose.numel() == 6
         assert r.dimg["loss"].data_ptr() == r.result.data_ptr() + 6 * 8 and r.dimg["loss"].numel() == 1
         assert r.result.dtype == torch.float64
+
+
+def test_list_reuse_rebins_at_each_interval_and_follows_the_interval_rule(monkeypatch):
+    """ListReuse (Sec. 4.1, Obs. 6) with its GPU calls replaced by host
+    fakes: the first iteration of every interval bins; when an interval of K
+    iterations ends, the change ratio compares the records the lists were
+    built from with the records at the current pose, and the library's
+    gs_next_interval (checked against the oracle's rule elsewhere) sets the
+    next K: scripted ratios 0.10, 0.01, 0.01, 0.20 from K0 = 5 give
+    intervals 5, 2, 4, 8 and then 4."""
+    import torch
+    from paper_2510_06644_gb300 import build, gs
+    from paper_2510_06644_gb300.pipeline import ListReuse
+    build.build()
+    cfg = gs.default_config()
+    assert int(cfg.k0) == 5 and abs(float(cfg.change_thr) - 0.05) < 1e-7
+
+    class FakeRast:
+        def __init__(self):
+            self.cfg, self.n, self.rec_dtype, self.device = cfg, 4, gs.GS_F32, torch.device("cpu")
+            self.splats = torch.zeros(4, 12)
+            self.rebins = []
+
+        def track_step(self, g, cam, trgb, tdep, pose, adam, lr_t, lr_r, rebin=True):
+            self.rebins.append(rebin)
+            self.splats.fill_(float(len(self.rebins)))   # this iteration's records
+
+    ratios = iter([0.10, 0.01, 0.01, 0.20])
+    seen = []
+
+    def fake_project(cfg_, cam, g, rec_dtype, out):
+        out.fill_(-1.0)   # the records at the current pose
+
+    def fake_change_ratio(cam, a, b, n, rec_dtype=gs.GS_F32, out=None, stream=None, cfg=None):
+        seen.append((float(a[0, 0]), float(b[0, 0])))
+        out.fill_(next(ratios))
+        return out
+
+    monkeypatch.setattr(gs, "gs_project", fake_project)
+    monkeypatch.setattr(gs, "gs_change_ratio", fake_change_ratio)
+    r = FakeRast()
+    lr = ListReuse(r, g=None)
+    for _ in range(5 + 2 + 4 + 8):
+        lr.step(gs.gs_camera(), None, None, None, None)
+    starts = [0, 5, 7, 11]
+    assert r.rebins == [i in starts for i in range(19)]
+    assert [k for k, _ in lr.intervals] == [5, 2, 4, 8]
+    np.testing.assert_allclose([x for _, x in lr.intervals], [0.10, 0.01, 0.01, 0.20], rtol=1e-6)
+    assert lr.K == 4 and lr.i == 0
+    # each ratio: the records binned at the interval's first iteration against the current ones
+    assert seen == [(s + 1.0, -1.0) for s in starts]
