@@ -114,3 +114,120 @@ def test_list_reuse_rebins_at_each_interval_and_follows_the_interval_rule(monkey
     assert lr.K == 4 and lr.i == 0
     # each ratio: the records binned at the interval's first iteration against the current ones
     assert seen == [(s + 1.0, -1.0) for s in starts]
+
+
+def _fake_server_env(monkeypatch, n_sessions=5, n_frames=3, iters=4, weights=(5, 1, 4, 2, 3)):
+    """Sessions and CUDA streams/events replaced by host fakes (events
+    complete at once), gs_track_wave recorded; returns (sessions, log, waves)."""
+    import torch
+    from paper_2510_06644_gb300 import gs
+    from paper_2510_06644_gb300.serve import SessionSpec
+
+    class FakeStream:
+        count = 0
+
+        def __init__(self, device=None):
+            FakeStream.count += 1
+            self.idx = FakeStream.count
+
+    class FakeEvent:
+        def record(self, stream=None):
+            pass
+
+        def query(self):
+            return True
+
+    log, waves = [], []
+
+    class FakeSession:
+        def __init__(self, sid, n):
+            self.spec = SessionSpec(sid=sid, n=n * 1000, W=64, H=48, f=60.0, n_frames=n_frames, seed=sid,
+                                    iters=iters, kf_every=2)
+            self.cfg = None
+            self.pose = torch.zeros(12)
+            self.pose_log = torch.zeros(n_frames, 12)
+            self.poses = []
+
+        def launch_frame(self, fr, stream):
+            log.append(("launch", self.spec.sid, fr))
+            ev = FakeEvent()
+            ev.record(stream)
+            return ev
+
+        def start_frame(self, fr, stream):
+            log.append(("start", self.spec.sid, fr, stream.idx))
+            return fr % 2 == 0, 1, 1
+
+        def wave_job(self, sx, sy):
+            return self.spec.sid
+
+        def finish_frame(self, fr, keyframe, stream):
+            log.append(("finish", self.spec.sid, fr, keyframe))
+            return FakeEvent()
+
+    monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(gs, "gs_track_wave", lambda cfg, jobs, stream=None: waves.append((list(jobs), stream.idx)))
+    return [FakeSession(i, w) for i, w in enumerate(weights[:n_sessions])], log, waves
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_server_loops_complete_every_frame_in_order(monkeypatch, mode):
+    """The plain and stream-batched loops with fake sessions: every frame of
+    every session completes once, in frame order per session; the plain loop
+    runs one frame at a time, the batched one admits up to `slots` sessions
+    at once (never more)."""
+    from paper_2510_06644_gb300.serve import Server
+    sessions, log, _ = _fake_server_env(monkeypatch)
+    arrivals = {s.spec.sid: [0.0] * s.spec.n_frames for s in sessions}
+    srv = Server(sessions, arrivals, mode=mode, slots=3, budget_bytes=1 << 50, device="cpu")
+    st = srv.run()
+    assert st["frames"] == 15
+    for s in sessions:
+        frames = [fr for kind, sid, fr in log if sid == s.spec.sid]
+        assert frames == [0, 1, 2]
+        assert [fr for sid, fr, _ in srv.latency if sid == s.spec.sid] == [0, 1, 2]
+        assert len(s.poses) == 3
+    # sessions admitted in arrival order (ties by id), at most `slots` in progress
+    first = {}
+    for i, (_, sid, fr) in enumerate(log):
+        first.setdefault(sid, i)
+    last = {sid: max(i for i, e in enumerate(log) if e[1] == sid) for sid in first}
+    for i in range(len(log)):
+        live = sum(1 for sid in first if first[sid] <= i <= last[sid])
+        assert live <= (1 if mode == "plain" else 3)
+
+
+def test_server_waves_group_sessions_and_run_every_iteration(monkeypatch):
+    """The wave loop with fake sessions: sessions are dealt at admission to
+    the lightest of two groups by map size; every wave holds sessions of one
+    group only, on that group's stream, heaviest first; each frame of each
+    session is in exactly `iters` waves, and a keyframe's mapping step follows
+    its frame's last wave."""
+    from paper_2510_06644_gb300.serve import Server
+    sessions, log, waves = _fake_server_env(monkeypatch)
+    weights = {s.spec.sid: s.spec.n for s in sessions}
+    arrivals = {s.spec.sid: [0.0] * s.spec.n_frames for s in sessions}
+    srv = Server(sessions, arrivals, mode="wave", slots=8, budget_bytes=1 << 50, device="cpu", groups=2)
+    assert srv.run()["frames"] == 15
+    # dealing: all five arrive at once and are admitted in id order
+    load, want = [0, 0], {}
+    for sid in sorted(weights):
+        gi = min(range(2), key=lambda q: load[q])
+        want[sid] = gi
+        load[gi] += weights[sid]
+    stream_of = {}
+    for jobs, stream in waves:
+        assert jobs == sorted(jobs, key=lambda q: -weights[q])
+        for sid in jobs:
+            assert stream_of.setdefault(sid, stream) == stream
+    groups = {}
+    for sid, stream in stream_of.items():
+        groups.setdefault(stream, set()).add(sid)
+    assert sorted(map(sorted, groups.values())) == sorted(
+        sorted(q for q in want if want[q] == g) for g in (0, 1))
+    for s in sessions:
+        sid = s.spec.sid
+        assert sum(sid in jobs for jobs, _ in waves) == 3 * 4
+        fin = [e for e in log if e[0] == "finish" and e[1] == sid]
+        assert [(e[2], e[3]) for e in fin] == [(0, True), (1, False), (2, True)]
