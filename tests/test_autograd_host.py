@@ -29,9 +29,17 @@ def test_capacity_follows_the_counts(monkeypatch):
     monkeypatch.setattr(gs, "gs_status_poll", lambda blocking=True, stream=None: (status["code"], 0))
     monkeypatch.setattr(gs, "gs_status_reset", lambda stream=None: resets.append(1))
     r = _FakeRast(10000)
-    r.n_keys.fill_(8000)
+    r.n_keys.fill_(8500)
     A._settle(r)
     assert r.capacity == 10000 and r._bm is not None
+    keys = r.keys
+    A._grow(r, 10000)   # not larger: the buffers stay
+    assert r.keys is keys and r._bm is not None
+    # exactly the capacity still fits (then grows for the next call)
+    r.n_keys.fill_(10000)
+    A._settle(r)
+    assert r.capacity == int(10000 * 1.25) + 4096
+    r = _FakeRast(10000)
     r.n_keys.fill_(9500)
     A._settle(r)
     assert r.capacity == int(9500 * 1.25) + 4096 == r.keys.numel() == r.vals.numel()

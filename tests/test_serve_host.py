@@ -116,28 +116,58 @@ def test_list_reuse_rebins_at_each_interval_and_follows_the_interval_rule(monkey
     assert seen == [(s + 1.0, -1.0) for s in starts]
 
 
-def _fake_server_env(monkeypatch, n_sessions=5, n_frames=3, iters=4, weights=(5, 1, 4, 2, 3)):
-    """Sessions and CUDA streams/events replaced by host fakes (events
-    complete at once), gs_track_wave recorded; returns (sessions, log, waves)."""
+def _fake_server_env(monkeypatch, n_sessions=5, n_frames=3, iters=4, weights=(5, 1, 4, 2, 3), polls=3):
+    """Sessions, CUDA streams/events and the clock replaced by host fakes: an
+    event completes at its `polls`-th query, the clock advances 0.1 ms per
+    read (and by the slept time), gs_track_wave is recorded.  Frames of
+    session s arrive at 4 ms s + 20 ms i.  Returns (sessions, arrivals, env)
+    with env.log (launch / start / finish entries with the serving clock),
+    env.waves ((jobs, stream index, waves pending on that stream)) and
+    env.streams (stream indices in creation order)."""
+    import types
     import torch
-    from paper_2510_06644_gb300 import gs
+    from paper_2510_06644_gb300 import gs, serve
     from paper_2510_06644_gb300.serve import SessionSpec
 
-    class FakeStream:
-        count = 0
+    env = types.SimpleNamespace(log=[], waves=[], streams=[], t=1000.0, t0=None, inflight=0, max_inflight=0)
 
+    def perf_counter():
+        env.t += 1e-4
+        if env.t0 is None:
+            env.t0 = env.t
+        return env.t
+
+    def sleep(dt):
+        env.t += dt
+
+    monkeypatch.setattr(serve, "time", types.SimpleNamespace(perf_counter=perf_counter, sleep=sleep))
+
+    def now():
+        return env.t - env.t0
+
+    class FakeStream:
         def __init__(self, device=None):
-            FakeStream.count += 1
-            self.idx = FakeStream.count
+            self.idx = len(env.streams)
+            self.pending = []
+            env.streams.append(self.idx)
 
     class FakeEvent:
+        def __init__(self):
+            self.left, self.stream = polls, None
+
         def record(self, stream=None):
-            pass
+            self.stream = stream
+            if stream is not None:
+                stream.pending.append(self)
 
         def query(self):
-            return True
-
-    log, waves = [], []
+            self.left -= 1
+            if self.left == 0:
+                if self.stream is not None and self in self.stream.pending:
+                    self.stream.pending.remove(self)
+                if getattr(self, "frame", False):
+                    env.inflight -= 1
+            return self.left <= 0
 
     class FakeSession:
         def __init__(self, sid, n):
@@ -149,85 +179,113 @@ def _fake_server_env(monkeypatch, n_sessions=5, n_frames=3, iters=4, weights=(5,
             self.poses = []
 
         def launch_frame(self, fr, stream):
-            log.append(("launch", self.spec.sid, fr))
+            env.log.append(("launch", self.spec.sid, fr, now(), stream.idx))
             ev = FakeEvent()
             ev.record(stream)
+            ev.frame = True
+            env.inflight += 1
+            env.max_inflight = max(env.max_inflight, env.inflight)
             return ev
 
         def start_frame(self, fr, stream):
-            log.append(("start", self.spec.sid, fr, stream.idx))
+            env.log.append(("start", self.spec.sid, fr, now(), stream.idx))
             return fr % 2 == 0, 1, 1
 
         def wave_job(self, sx, sy):
             return self.spec.sid
 
         def finish_frame(self, fr, keyframe, stream):
-            log.append(("finish", self.spec.sid, fr, keyframe))
+            env.log.append(("finish", self.spec.sid, fr, keyframe))
             return FakeEvent()
 
     monkeypatch.setattr(torch.cuda, "Stream", FakeStream)
     monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
-    monkeypatch.setattr(gs, "gs_track_wave", lambda cfg, jobs, stream=None: waves.append((list(jobs), stream.idx)))
-    return [FakeSession(i, w) for i, w in enumerate(weights[:n_sessions])], log, waves
+    monkeypatch.setattr(gs, "gs_track_wave",
+                        lambda cfg, jobs, stream=None: env.waves.append((list(jobs), stream.idx, len(stream.pending))))
+    sessions = [FakeSession(i, w) for i, w in enumerate(weights[:n_sessions])]
+    arrivals = {s.spec.sid: [0.004 * s.spec.sid + 0.020 * i for i in range(n_frames)] for s in sessions}
+    return sessions, arrivals, env
+
+
+def _check_arrivals_and_latency(srv, arrivals, env, kind):
+    """No frame starts before it arrives; every latency lies in [0, makespan]
+    and the makespan within the serving clock's span."""
+    for e in env.log:
+        if e[0] == kind:
+            assert e[3] >= arrivals[e[1]][e[2]], e
+    lat = [x for _, _, x in srv.latency]
+    assert min(lat) >= 0 and max(lat) <= srv.makespan <= env.t - env.t0
 
 
 @pytest.mark.parametrize("mode", ["plain", "batched"])
 def test_server_loops_complete_every_frame_in_order(monkeypatch, mode):
     """The plain and stream-batched loops with fake sessions: every frame of
-    every session completes once, in frame order per session; the plain loop
-    runs one frame at a time, the batched one admits up to `slots` sessions
-    at once (never more)."""
+    every session completes once, in frame order per session, never before
+    it arrives; the plain loop runs one frame at a time on one stream, the
+    batched one admits up to `slots` sessions at once (never more), each on
+    its own stream, with frames of different sessions in flight together."""
     from paper_2510_06644_gb300.serve import Server
-    sessions, log, _ = _fake_server_env(monkeypatch)
-    arrivals = {s.spec.sid: [0.0] * s.spec.n_frames for s in sessions}
+    # batched: a frame takes about 100 polls x 0.12 ms, longer than the 4 ms
+    # between sessions' arrivals and shorter than the 20 ms between a
+    # session's frames; plain: a few polls
+    sessions, arrivals, env = _fake_server_env(monkeypatch, polls=3 if mode == "plain" else 100)
     srv = Server(sessions, arrivals, mode=mode, slots=3, budget_bytes=1 << 50, device="cpu")
     st = srv.run()
     assert st["frames"] == 15
+    log = env.log
     for s in sessions:
-        frames = [fr for kind, sid, fr in log if sid == s.spec.sid]
-        assert frames == [0, 1, 2]
+        assert [e[2] for e in log if e[1] == s.spec.sid] == [0, 1, 2]
         assert [fr for sid, fr, _ in srv.latency if sid == s.spec.sid] == [0, 1, 2]
         assert len(s.poses) == 3
-    # sessions admitted in arrival order (ties by id), at most `slots` in progress
-    first = {}
-    for i, (_, sid, fr) in enumerate(log):
-        first.setdefault(sid, i)
-    last = {sid: max(i for i, e in enumerate(log) if e[1] == sid) for sid in first}
+    _check_arrivals_and_latency(srv, arrivals, env, "launch")
+    # at most `slots` sessions in progress (one in the plain loop)
+    first, last = {}, {}
+    for i, e in enumerate(log):
+        first.setdefault(e[1], i)
+        last[e[1]] = i
     for i in range(len(log)):
         live = sum(1 for sid in first if first[sid] <= i <= last[sid])
         assert live <= (1 if mode == "plain" else 3)
+    assert [e[1] for e in log if e[2] == 0] == sorted(first, key=lambda q: arrivals[q][0])
+    stream_of = {e[1]: e[4] for e in log}
+    if mode == "plain":
+        assert env.max_inflight == 1 and len(set(stream_of.values())) == 1
+    else:
+        assert env.max_inflight >= 2 and len(set(stream_of.values())) == len(sessions)
 
 
 def test_server_waves_group_sessions_and_run_every_iteration(monkeypatch):
     """The wave loop with fake sessions: sessions are dealt at admission to
     the lightest of two groups by map size; every wave holds sessions of one
-    group only, on that group's stream, heaviest first; each frame of each
-    session is in exactly `iters` waves, and a keyframe's mapping step follows
-    its frame's last wave."""
+    group only, on that group's stream (the groups' streams are created in
+    group order), heaviest first, with fewer than `depth` = 3 waves of the
+    group pending; each frame starts no earlier than it arrives and is in
+    exactly `iters` waves, and a keyframe's mapping step follows its frame's
+    last wave."""
     from paper_2510_06644_gb300.serve import Server
-    sessions, log, waves = _fake_server_env(monkeypatch)
+    sessions, arrivals, env = _fake_server_env(monkeypatch, weights=(5, 1, 4, 2, 3), polls=6)
     weights = {s.spec.sid: s.spec.n for s in sessions}
-    arrivals = {s.spec.sid: [0.0] * s.spec.n_frames for s in sessions}
+    # all five arrive within 16 ms: dealt in arrival order
     srv = Server(sessions, arrivals, mode="wave", slots=8, budget_bytes=1 << 50, device="cpu", groups=2)
     assert srv.run()["frames"] == 15
-    # dealing: all five arrive at once and are admitted in id order
     load, want = [0, 0], {}
-    for sid in sorted(weights):
+    for sid in sorted(weights, key=lambda q: arrivals[q][0]):
         gi = min(range(2), key=lambda q: load[q])
         want[sid] = gi
         load[gi] += weights[sid]
-    stream_of = {}
-    for jobs, stream in waves:
+    group_stream = env.streams[:2]
+    assert max(p for _, _, p in env.waves) == 2   # the queue reaches the depth limit
+    for jobs, stream, pending in env.waves:
         assert jobs == sorted(jobs, key=lambda q: -weights[q])
+        assert pending < 3
         for sid in jobs:
-            assert stream_of.setdefault(sid, stream) == stream
-    groups = {}
-    for sid, stream in stream_of.items():
-        groups.setdefault(stream, set()).add(sid)
-    assert sorted(map(sorted, groups.values())) == sorted(
-        sorted(q for q in want if want[q] == g) for g in (0, 1))
+            assert stream == group_stream[want[sid]]
+    for e in env.log:
+        if e[0] == "start":
+            assert e[4] == group_stream[want[e[1]]]
+    _check_arrivals_and_latency(srv, arrivals, env, "start")
     for s in sessions:
         sid = s.spec.sid
-        assert sum(sid in jobs for jobs, _ in waves) == 3 * 4
-        fin = [e for e in log if e[0] == "finish" and e[1] == sid]
+        assert sum(sid in jobs for jobs, _, _ in env.waves) == 3 * 4
+        fin = [e for e in env.log if e[0] == "finish" and e[1] == sid]
         assert [(e[2], e[3]) for e in fin] == [(0, True), (1, False), (2, True)]
