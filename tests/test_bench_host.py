@@ -65,13 +65,14 @@ def test_clock_summary_counts_the_timed_samples():
     import datetime
     t0 = datetime.datetime(2026, 1, 1, 12, 0, 0).timestamp()
 
-    def row(dt, mhz, pcap="Not Active"):
+    def row(dt, mhz, pcap="Not Active", mx=2070, w=500.5):
         ts = datetime.datetime.fromtimestamp(t0 + dt).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
-        return f"{ts}, 0, {mhz}, 2070, 500.5, 0x0, Not Active, Not Active, Not Active, {pcap}"
+        return f"{ts}, 0, {mhz}, {mx}, {w}, 0x0, Not Active, Not Active, Not Active, {pcap}"
 
-    lines = [row(0.0, 1900), row(0.1, 2070), row(0.2, 2070, "Active"), row(0.3, 2000), "garbage line"]
+    lines = [row(0.0, 1900, mx=2055, w=300.0), row(0.1, 2070, w=612.25), row(0.2, 2070, "Active"), row(0.3, 2000),
+             "garbage line"]
     c = bench.Clocks.parse(lines, timed=[(t0 + 0.15, t0 + 0.25)])
-    assert c["samples"] == 4 and c["sm_max_mhz"] == 2070.0
+    assert c["samples"] == 4 and c["sm_max_mhz"] == 2070.0 and c["power_w_max"] == 612.25
     assert c["sm_mhz"] == pytest.approx(2035.0)
     assert c["reasons"] == ["sw_power_cap"]
     # the timed region (widened by one sampling interval) holds the samples at 0.1, 0.2 and 0.3 s
@@ -82,7 +83,9 @@ def test_mask_visits_counts_warp_entry_pairs():
     """The bench's count of the masked backward's (warp, entry) visits
     against a plain loop over tiles, warps and entries on random per-pixel
     blend-mask words (garbage past each warp's last run and past each list's
-    end must not count)."""
+    end must not count).  The words are sparse (a bit set with probability
+    1/64), so that their OR over a warp's 32 lanes depends on which words
+    are read."""
     import numpy as np
     import torch
     import bench
@@ -93,7 +96,8 @@ def test_mask_visits_counts_warp_entry_pairs():
     starts = np.concatenate([[0], np.cumsum(lens)[:-1]]) + 7
     ranges = np.stack([starts, starts + lens], 1).astype(np.int32)
     nwords = 256 * (int(starts.max()) // 32 + T) + 256 * 8 + 256
-    bm = rng.integers(0, 2 ** 32, nwords, dtype=np.uint64).astype(np.uint32).view(np.int32)
+    bits = rng.random((nwords, 32)) < 1 / 64
+    bm = (bits * (np.uint64(1) << np.arange(32, dtype=np.uint64))).sum(1).astype(np.uint32).view(np.int32)
     last = np.zeros((H, W), np.int64)
     for t in range(T):
         tx, ty = t % TX, t // TX
@@ -121,3 +125,4 @@ def test_mask_visits_counts_warp_entry_pairs():
                     want += 1
     got = bench.mask_visits(torch.from_numpy(bm), torch.from_numpy(ranges), torch.from_numpy(last), TX, TY)
     assert got == want
+    assert 0.2 * lens.sum() * 8 < want < 0.9 * lens.sum() * 8   # neither empty nor saturated
