@@ -194,6 +194,7 @@ def test_next_interval_follows_the_oracle_rule(built_lib):
         K = got
     assert K == 32   # ... 64 at the cap, then one halving
     assert gs.gs_next_interval(cfg, 0, 0.0) == 1
+    assert gs.lib().gs_next_interval(None, 5, ctypes.c_float(0.0)) == 1   # no config: the smallest interval
 
 
 def test_fused_adam_rejects_bad_arguments_on_the_host(built_lib):
@@ -215,3 +216,35 @@ def test_fused_adam_rejects_bad_arguments_on_the_host(built_lib):
     assert L.gs_project_bwd_adam(ctypes.byref(cfg), ctypes.byref(cam), ctypes.byref(g), None, ctypes.byref(a), None,
                                  None, None) == gs.GS_ERR_INVALID_ARG
     assert b"Adam" in L.gs_last_error()
+
+
+def test_downsample_schedule_follows_the_oracle(built_lib):
+    """gs_downsample's strides without a target (host only, Sec. 4.2)
+    against the oracle's schedule for frames around several keyframes and
+    every m, including the arguments both reject: m not a power of two >= 2,
+    a non-keyframe at or before its keyframe."""
+    from oracle import oracle as O
+    O.build()
+    from paper_2510_06644_gb300 import gs
+    checked = rejected = 0
+    for k in (0, 3, 10):
+        for n in range(max(0, k - 2), k + 8):
+            for m in (1, 2, 3, 4, 8):
+                for kf in (False, True):
+                    try:
+                        want = O.downsample_schedule(n, k, kf, m=m)
+                    except ValueError:
+                        want = None
+                    try:
+                        got = gs.gs_downsample(n, k, kf, m)[:2]
+                    except gs.GsError:
+                        got = None
+                    assert got == want, (n, k, m, kf, got, want)
+                    checked += 1
+                    rejected += want is None
+    assert checked == 280 and 50 < rejected < 200
+    # either stride pointer NULL is rejected
+    sx = ctypes.c_int32(0)
+    for a, b in ((None, ctypes.byref(sx)), (ctypes.byref(sx), None)):
+        rc = gs.lib().gs_downsample(6, 5, 0, 2, a, b, None, 0, 0, 0, None, None)
+        assert rc == gs.GS_ERR_INVALID_ARG
