@@ -248,3 +248,25 @@ def test_downsample_schedule_follows_the_oracle(built_lib):
     for a, b in ((None, ctypes.byref(sx)), (ctypes.byref(sx), None)):
         rc = gs.lib().gs_downsample(6, 5, 0, 2, a, b, None, 0, 0, 0, None, None)
         assert rc == gs.GS_ERR_INVALID_ARG
+
+
+def test_default_config_holds_the_papers_values_and_the_readings(built_lib):
+    """gs_default_config against the paper's fixed hyper-parameters
+    (tests/golden/hyperparams.json: Sec. 6.1, Sec. 4.1, Sec. 6.2) and the
+    oracle's configuration of the unstated thresholds (near plane,
+    dilation, alpha skip and clamp, termination, background, loss weights;
+    prune fraction 10 % per interval, K capped at 64)."""
+    import json
+    from oracle import oracle as O
+    from paper_2510_06644_gb300 import gs
+    hp = json.load(open(os.path.join(ROOT, "tests", "golden", "hyperparams.json")))
+    c = gs.default_config()
+    f32 = lambda x: float(ctypes.c_float(x).value)
+    assert c.lambda_score == f32(hp["lambda_score"]) and c.k0 == hp["k0"]
+    assert c.change_thr == f32(hp["change_ratio_threshold"]) and c.prune_cap == f32(hp["prune_cap"])
+    d = O.DEFAULT_CFG
+    for k in ("near_z", "dilation", "alpha_min", "alpha_max", "t_eps"):
+        assert getattr(c, k) == f32(d[k]), k
+    assert list(c.bg) == [f32(v) for v in d["bg"]]
+    assert (c.w_rgb, c.w_depth) == (1.0, 0.5)        # reading c10: L1 RGB + 0.5 L1 depth
+    assert c.prune_frac == f32(0.1) and c.k_max == 64  # readings c13, c15
