@@ -483,7 +483,7 @@ static int in_box(double u, double v, int64_t r, int64_t px, int64_t py, int dec
 
 /* box_float_decided of every Gaussian (malloc'ed; the caller frees it). */
 static uint8_t* float_decided_boxes(const or_splats* s) {
-    uint8_t* f = (uint8_t*)malloc((size_t)(s->n + 1));
+    uint8_t* f = (uint8_t*)calloc((size_t)(s->n + 1), 1);
     for (int64_t k = 0; k < s->n; ++k) f[k] = (uint8_t)box_float_decided(s->uv[2 * k], s->uv[2 * k + 1]);
     return f;
 }

@@ -873,11 +873,11 @@ def test_loss_hand_values(oracle_lib):
     # a negative depth residual, an invalid target and a zero residual: the
     # gradient is sign(r) w / P with P every sampled pixel, sign(0) = 0
     z = np.zeros((3, 1, 3))
-    L2, dr2, dd2 = O.loss_l1(z, np.array([[1.0, 2.0, 0.5]]), z, np.array([[1.5, 0.0, 0.5]]), w_rgb=0.9,
+    L2, dr2, dd2 = O.loss_l1(z, np.array([[0.5, 2.0, 1.0]]), z, np.array([[0.5, 0.0, 1.5]]), w_rgb=0.9,
                              w_depth=0.1)
     assert math.isclose(L2, 0.1 * 0.5 / 3, rel_tol=1e-14)
     assert not dr2.any()
-    np.testing.assert_allclose(dd2, [[-0.1 / 3, 0.0, 0.0]], rtol=1e-14)
+    np.testing.assert_allclose(dd2, [[0.0, 0.0, -0.1 / 3]], rtol=1e-14)
 
 
 # ---------------------------------------------------------------------------
@@ -977,3 +977,5 @@ def test_strided_render_equals_subsampled_full_render(oracle_lib, sx, sy):
     np.testing.assert_array_equal(sub["rgb"], full["rgb"][:, ::sy, ::sx])
     np.testing.assert_array_equal(sub["depth"], full["depth"][::sy, ::sx])
     np.testing.assert_array_equal(O.gather(full["rgb"], sx, sy), full["rgb"][:, ::sy, ::sx])
+    noise = S.rng(78).normal(0, 1, (3, 37, 29))   # every sample distinct: a shifted index shows
+    np.testing.assert_array_equal(O.gather(noise, sx, sy), noise[:, ::sy, ::sx])
